@@ -1,0 +1,216 @@
+"""CPU oracle for the cluster-relation producer (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only callers.  The product never imports
+this package; it shares no code with the CUDA path.
+
+The arithmetic lives in ``oracle.c`` (plain C, every function cites the
+passage it follows).  This module compiles it with gcc and wraps it:
+
+* ``validate``              - input checks (Section 4.3, "Input data")
+* ``canonicalize``          - canonical vertex / tet numbering, interval arrays
+                              I_V, I_T, internal rule (Section 4.3)
+* ``relations``             - VT, VV, ET, TT of the whole mesh (Section 2.2,
+                              Table 1), global formulation
+* ``cluster_relations``     - the same for one cluster, by rescanning the mesh
+* ``working_set``           - T_ex (Section 4.3, "Initialization") and the
+                              face halo of one cluster
+* ``cluster_view``          - slices a global result into one cluster's
+                              self-contained CSR (offsets starting at 0)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+
+OK, EINVAL, ENOMEM = 0, 1, 2
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (plain C, portable flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Rel(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("nt", ctypes.c_int64), ("ne", ctypes.c_int64),
+                ("vt_off", ctypes.POINTER(ctypes.c_int64)), ("vt_val", ctypes.POINTER(ctypes.c_int32)),
+                ("vv_off", ctypes.POINTER(ctypes.c_int64)), ("vv_val", ctypes.POINTER(ctypes.c_int32)),
+                ("eu_off", ctypes.POINTER(ctypes.c_int64)), ("e_w", ctypes.POINTER(ctypes.c_int32)),
+                ("et_off", ctypes.POINTER(ctypes.c_int64)), ("et_val", ctypes.POINTER(ctypes.c_int32)),
+                ("tt_off", ctypes.POINTER(ctypes.c_int64)), ("tt_val", ctypes.POINTER(ctypes.c_int32))]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        lib.oracle_validate.argtypes = [i64, i64, P, P, i32]
+        lib.oracle_canon_vertices.argtypes = [i64, P, i32, P, P, P]
+        lib.oracle_canon_tets.argtypes = [i64, P, P, P, P, i32, P, P, P]
+        lib.oracle_relations.argtypes = [i64, i64, P, ctypes.POINTER(_Rel)]
+        lib.oracle_cluster_relations.argtypes = [i64, i64, P, P, P, i32, ctypes.POINTER(_Rel)]
+        lib.oracle_working_set.argtypes = [i64, i64, P, P, P, i32, P, ctypes.POINTER(i64), P, ctypes.POINTER(i64)]
+        lib.oracle_rel_free.argtypes = [ctypes.POINTER(_Rel)]
+        lib.oracle_rel_free.restype = None
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def validate(nv: int, tv: np.ndarray, seg: np.ndarray, nclusters: int) -> int:
+    tv = np.ascontiguousarray(tv, dtype=np.int32).reshape(-1, 4)
+    seg = np.ascontiguousarray(seg, dtype=np.int32)
+    if seg.shape[0] != nv:
+        return EINVAL
+    return _load().oracle_validate(nv, tv.shape[0], _p(tv), _p(seg), nclusters)
+
+
+def canonicalize(nv: int, tv: np.ndarray, seg: np.ndarray, nclusters: int) -> dict:
+    """Canonical numbering.  Returns cid (input -> canonical vertex), vperm
+    (canonical -> input), I_V [K+1], rows [T,4] (canonical, ascending, in
+    canonical tet order), tperm (canonical -> input tet), I_T [K+1]."""
+    lib = _load()
+    tv = np.ascontiguousarray(tv, dtype=np.int32).reshape(-1, 4)
+    seg = np.ascontiguousarray(seg, dtype=np.int32)
+    nt = tv.shape[0]
+    cid = np.empty(nv, np.int32)
+    vperm = np.empty(nv, np.int32)
+    I_V = np.empty(nclusters + 1, np.int64)
+    if lib.oracle_canon_vertices(nv, _p(seg), nclusters, _p(cid), _p(vperm), _p(I_V)) != OK:
+        raise MemoryError("oracle_canon_vertices")
+    rows = np.empty((nt, 4), np.int32)
+    tperm = np.empty(nt, np.int32)
+    I_T = np.empty(nclusters + 1, np.int64)
+    if lib.oracle_canon_tets(nt, _p(tv), _p(cid), _p(vperm), _p(seg), nclusters, _p(rows), _p(tperm), _p(I_T)) != OK:
+        raise MemoryError("oracle_canon_tets")
+    return {"nv": nv, "nt": nt, "K": nclusters, "cid": cid, "vperm": vperm, "I_V": I_V, "rows": rows,
+            "tperm": tperm, "I_T": I_T}
+
+
+def _arr(ptr, n, dtype):
+    if n == 0:
+        return np.zeros(0, dtype)
+    return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
+
+
+def _unpack(r: _Rel, nrows_v: int, nrows_t: int) -> dict:
+    vt_off = _arr(r.vt_off, nrows_v + 1, np.int64)
+    vv_off = _arr(r.vv_off, nrows_v + 1, np.int64)
+    eu_off = _arr(r.eu_off, nrows_v + 1, np.int64)
+    ne = int(r.ne)
+    et_off = _arr(r.et_off, ne + 1, np.int64)
+    tt_off = _arr(r.tt_off, nrows_t + 1, np.int64)
+    return {
+        "vt_off": vt_off, "vt_val": _arr(r.vt_val, int(vt_off[-1]), np.int32),
+        "vv_off": vv_off, "vv_val": _arr(r.vv_val, int(vv_off[-1]), np.int32),
+        "eu_off": eu_off, "e_w": _arr(r.e_w, ne, np.int32),
+        "et_off": et_off, "et_val": _arr(r.et_val, int(et_off[-1]), np.int32),
+        "tt_off": tt_off, "tt_val": _arr(r.tt_val, int(tt_off[-1]), np.int32),
+        "ne": ne,
+    }
+
+
+def relations(canon: dict) -> dict:
+    """VT, VV, ET, TT of the whole mesh (global CSR, canonical ids)."""
+    lib = _load()
+    r = _Rel()
+    rows = np.ascontiguousarray(canon["rows"])
+    if lib.oracle_relations(canon["nv"], canon["nt"], _p(rows), ctypes.byref(r)) != OK:
+        raise MemoryError("oracle_relations")
+    try:
+        return _unpack(r, canon["nv"], canon["nt"])
+    finally:
+        lib.oracle_rel_free(ctypes.byref(r))
+
+
+def cluster_relations(canon: dict, k: int) -> dict:
+    """VT/VV/ET rows of cluster k's vertices and TT rows of its internal tets,
+    found by rescanning the whole mesh; offsets start at 0."""
+    lib = _load()
+    r = _Rel()
+    rows = np.ascontiguousarray(canon["rows"])
+    I_V, I_T = canon["I_V"], canon["I_T"]
+    if lib.oracle_cluster_relations(canon["nv"], canon["nt"], _p(rows), _p(I_V), _p(I_T), k, ctypes.byref(r)) != OK:
+        raise MemoryError("oracle_cluster_relations")
+    try:
+        return _unpack(r, int(I_V[k + 1] - I_V[k]), int(I_T[k + 1] - I_T[k]))
+    finally:
+        lib.oracle_rel_free(ctypes.byref(r))
+
+
+def working_set(canon: dict, k: int):
+    """(T_ex(k), halo(k)) as ascending canonical tet ids."""
+    lib = _load()
+    nt = canon["nt"]
+    ext = np.empty(max(nt, 1), np.int32)
+    halo = np.empty(max(nt, 1), np.int32)
+    ne, nh = ctypes.c_int64(0), ctypes.c_int64(0)
+    rows = np.ascontiguousarray(canon["rows"])
+    lib.oracle_working_set(canon["nv"], nt, _p(rows), _p(canon["I_V"]), _p(canon["I_T"]), k, _p(ext),
+                           ctypes.byref(ne), _p(halo), ctypes.byref(nh))
+    return ext[:ne.value].copy(), halo[:nh.value].copy()
+
+
+def cluster_view(rel: dict, canon: dict, k: int) -> dict:
+    """Cluster k's slice of a global result, as a self-contained CSR: VT/VV
+    rows for its vertices, ET edges whose lower endpoint it owns (eu_off per
+    vertex, e_w, et_off per edge), TT rows for its internal tets; every offset
+    array starts at 0."""
+    v0, v1 = int(canon["I_V"][k]), int(canon["I_V"][k + 1])
+    t0, t1 = int(canon["I_T"][k]), int(canon["I_T"][k + 1])
+
+    def sl(off, val, a, b):
+        o = off[a:b + 1]
+        return (o - o[0]).astype(np.int64), val[o[0]:o[-1]]
+
+    vt_off, vt_val = sl(rel["vt_off"], rel["vt_val"], v0, v1)
+    vv_off, vv_val = sl(rel["vv_off"], rel["vv_val"], v0, v1)
+    eu = rel["eu_off"][v0:v1 + 1]
+    e0, e1 = int(eu[0]), int(eu[-1])
+    et_off, et_val = sl(rel["et_off"], rel["et_val"], e0, e1)
+    tt_off, tt_val = sl(rel["tt_off"], rel["tt_val"], t0, t1)
+    return {"vt_off": vt_off, "vt_val": vt_val, "vv_off": vv_off, "vv_val": vv_val,
+            "eu_off": (eu - e0).astype(np.int64), "e_w": rel["e_w"][e0:e1], "et_off": et_off, "et_val": et_val,
+            "tt_off": tt_off, "tt_val": tt_val, "ne": e1 - e0}
+
+
+def cluster_sizes(rel: dict, canon: dict) -> np.ndarray:
+    """int64 [K, 5]: per cluster |VT|, |VV|, #edges, |ET|, |TT| (entries)."""
+    I_V, I_T = canon["I_V"], canon["I_T"]
+    vt = rel["vt_off"][I_V[1:]] - rel["vt_off"][I_V[:-1]]
+    vv = rel["vv_off"][I_V[1:]] - rel["vv_off"][I_V[:-1]]
+    e = rel["eu_off"][I_V[1:]] - rel["eu_off"][I_V[:-1]]
+    et = rel["et_off"][rel["eu_off"][I_V[1:]]] - rel["et_off"][rel["eu_off"][I_V[:-1]]]
+    tt = rel["tt_off"][I_T[1:]] - rel["tt_off"][I_T[:-1]]
+    return np.stack([vt, vv, e, et, tt], axis=1).astype(np.int64)
+
+
+def build_all(nv: int, tv: np.ndarray, seg: np.ndarray, nclusters: int):
+    """The whole oracle pipeline (validate, canonicalize, relations); the
+    unit the CPU baseline times."""
+    rc = validate(nv, tv, seg, nclusters)
+    if rc != OK:
+        raise ValueError(f"oracle_validate: {rc}")
+    canon = canonicalize(nv, tv, seg, nclusters)
+    return canon, relations(canon)
