@@ -1,0 +1,266 @@
+/*
+ * gale.h - C ABI of the GB300 cluster-relation producer.
+ *
+ * The library is the producer side of a GPU-aided localized data structure
+ * for tetrahedral meshes (GALE, Section 4).  Consumers ask for the
+ * coboundary / adjacency relations of whole mesh segments ("clusters", the
+ * paper's segments of Section 4.3); the library builds them on the GPU as
+ * canonical, index-sorted CSR:
+ *
+ *   VT(v)    tets incident to vertex v             (coboundary, Table 1)
+ *   VV(v)    vertices adjacent to v                (adjacency,  Table 1)
+ *   ET(u,w)  tets incident to edge (u,w), u < w    (coboundary, Table 1)
+ *   TT(t)    tets sharing a triangle with tet t    (adjacency,  Table 1)
+ *
+ * Conventions for every call:
+ *  - All ids in outputs are CANONICAL ids (see gale_load_mesh).  The
+ *    permutations back to input ids come from gale_get_permutations; applying
+ *    them is the paper's local-to-global mapping step (Section 4.5).
+ *  - Every row is ascending.  Offset arrays are int32, relative to their
+ *    cluster (the first offset of every cluster is 0).
+ *  - No call throws; every failure returns a status and sets a thread-local
+ *    message readable with gale_last_error().
+ *  - Host pointers are caller-owned and are only read during the call.
+ *    Device pointers returned by the library stay library-owned.
+ */
+#ifndef GALE_H
+#define GALE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GALE_OK = 0,
+    GALE_EINVAL = 1,    /* invalid argument or invalid mesh */
+    GALE_ENOMEM = 2,    /* device or host allocation failed, or over budget */
+    GALE_EBUSY = 3,     /* cache budget fully pinned; retry after releases */
+    GALE_ETIMEOUT = 4,  /* a wait ran past its deadline */
+    GALE_ENOTFOUND = 5, /* no such cluster / view / symbol */
+    GALE_ECUDA = 6,     /* a CUDA runtime call failed */
+    GALE_EDEVICE = 7    /* a kernel reported an error word (see message) */
+} gale_status;
+
+/* Relation mask bits. */
+enum { GALE_VT = 1u, GALE_VV = 2u, GALE_ET = 4u, GALE_TT = 8u, GALE_ALL = 15u };
+
+/* Build forms of gale_build_clusters. */
+enum {
+    GALE_MODE_PER_CLUSTER = 0, /* one kernel launch per cluster (baseline form) */
+    GALE_MODE_BATCHED = 1      /* persistent size-binned kernels, replayed from a captured CUDA graph */
+};
+
+/* Device allocator hooks: return device memory aligned to 256 bytes, or NULL. */
+typedef void *(*gale_alloc_fn)(void *alloc_ctx, size_t bytes);
+typedef void (*gale_free_fn)(void *alloc_ctx, void *ptr);
+
+typedef struct gale_ctx gale_ctx; /* opaque; one per loaded mesh */
+
+/*
+ * Mesh description (Section 4.3, "Input data"): V, T (the TV relation) and
+ * S.  All arrays are HOST memory, caller-owned, read only during
+ * gale_load_mesh.
+ *   nv, nt            vertex and tet counts (1 <= nv, 0 <= nt, both < 2^31)
+ *   xyz               float[nv*3] coordinates; may be NULL (not used by the
+ *                     producer, kept for consumers)
+ *   tv                int32[nt*4] vertex ids of each tet, any order
+ *   seg               int32[nv] segment (cluster) id of each vertex, in
+ *                     [0, nclusters)
+ *   precondition_mask relations the context will serve (Section 4.3,
+ *                     preconditioning); only their working data is built
+ *   cache_budget_bytes HBM budget of the serving relation cache
+ *                     (gale_request); 0 disables serving
+ *   stream            cudaStream_t every kernel and copy of this context is
+ *                     ordered on; NULL = a stream the library creates
+ *   alloc/free        device allocator hooks; NULL = cudaMalloc / cudaFree
+ *   device            CUDA device ordinal; -1 makes a HOST-ONLY context that
+ *                     runs the host-side initialisation and nothing else
+ *   host_threads      threads for host-side initialisation, 0 = all cores
+ */
+typedef struct {
+    int64_t nv, nt;
+    const float *xyz;
+    const int32_t *tv;
+    const int32_t *seg;
+    int32_t nclusters;
+    uint32_t precondition_mask;
+    int64_t cache_budget_bytes;
+    void *stream;
+    gale_alloc_fn alloc;
+    gale_free_fn free;
+    void *alloc_ctx;
+    int32_t device;
+    int32_t host_threads;
+} gale_mesh_desc;
+
+/*
+ * One cluster's relations.  Device pointers, valid until gale_release (views
+ * from gale_request) or until the next gale_build_clusters / gale_destroy
+ * (views from gale_bulk_view).  Pointers for relations not in `mask` are NULL.
+ *   vt_off[nv_own+1], vt_val      VT rows of vertices v_begin .. v_end-1
+ *   vv_off[nv_own+1], vv_val      VV rows of the same vertices
+ *   et_uoff[nv_own+1]             edges of each vertex u as lower endpoint
+ *   et_w[n_edges]                 upper endpoint w of each edge (u, w)
+ *   et_off[n_edges+1], et_val     ET rows of those edges
+ *   tt_off[t_end-t_begin+1], tt_val  TT rows of the cluster's internal tets
+ */
+typedef struct {
+    int32_t cluster;
+    uint32_t mask;
+    int32_t v_begin, v_end; /* canonical vertex ids of the cluster (I_V interval) */
+    int32_t t_begin, t_end; /* canonical ids of its internal tets (I_T interval) */
+    int32_t n_edges;        /* edges whose lower endpoint it owns (I_E difference) */
+    int32_t reserved;
+    const int32_t *vt_off, *vt_val, *vv_off, *vv_val;
+    const int32_t *et_uoff, *et_w, *et_off, *et_val;
+    const int32_t *tt_off, *tt_val;
+    uint64_t handle; /* non-zero for views that pin a cache entry */
+} gale_view;
+
+/* The ten output arrays of a bulk build (device or host pointers). */
+typedef struct {
+    int32_t *vt_off, *vt_val, *vv_off, *vv_val;
+    int32_t *et_uoff, *et_w, *et_off, *et_val;
+    int32_t *tt_off, *tt_val;
+} gale_arrays;
+
+/* Counts and sizes of a context. */
+typedef struct {
+    int64_t nv, nt;
+    int32_t nclusters;
+    int32_t device;
+    int64_t n_edges;           /* edges of the whole mesh */
+    int64_t total[5];          /* entries of VT, VV, edges, ET, TT over all clusters */
+    int64_t block_bytes;       /* device bytes of the cluster working sets */
+    int64_t ext_tets, halo_tets; /* sum of |T_ex(k)| and of |halo(k)| */
+    int32_t nbins;             /* size bins of the batched form */
+    int32_t max_cluster_tets;  /* largest working set (tets) */
+    double load_host_seconds;  /* host-side initialisation time */
+    double load_device_seconds;/* upload + size pass time */
+} gale_info;
+
+/* Per-call statistics of the serving path. */
+typedef struct {
+    int64_t requests, hits, misses, builds, evictions, batches;
+    int64_t cache_bytes_used, cache_bytes_budget;
+    int64_t max_batch;
+} gale_serve_stats;
+
+/*
+ * gale_load_mesh - initialisation (Section 4.3, "Initialization").
+ * Validates the input (EINVAL on an id out of range, a repeated vertex in a
+ * tet, a segment id out of range or two tets with the same vertex set) and
+ * builds the canonical numbering:
+ *   - vertices ordered by (segment, input id), so segment k owns the
+ *     contiguous interval [I_V[k], I_V[k+1]) the interval array I_V of
+ *     Section 4.3 presupposes;
+ *   - each tet row relabelled and sorted ascending; a tet is internal to the
+ *     segment of its lowest vertex (Section 4.3) and tets are ordered by
+ *     (owning segment, input index), giving I_T;
+ *   - per cluster: its internal tets, its external tets T_ex (Section 4.3),
+ *     and the halo of tets outside the cluster that share a triangle with an
+ *     internal tet (needed for complete TT rows);
+ *   - the exact size of every relation of every cluster (a counting pass on
+ *     the GPU), used for output placement and cache admission.
+ * The cluster working sets are copied to device memory once, as the paper
+ * copies its initialised arrays to GPU global memory.
+ * On success *out owns all of it; release with gale_destroy.
+ */
+gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out);
+
+/*
+ * gale_build_clusters - producer kernels (Section 4.6) for a batch of
+ * clusters.  ids: HOST int32[n] cluster ids (NULL with n <= 0 = all clusters
+ * in order); each id at most once.  mask: relations to build (GALE_* bits,
+ * within the precondition mask).  mode: GALE_MODE_PER_CLUSTER or
+ * GALE_MODE_BATCHED.  The relations are written to library-owned bulk arrays,
+ * clusters consecutively in list order.  The work is ENQUEUED on the
+ * context's stream and the call returns; gale_synchronize waits for it and
+ * reports kernel errors.  EINVAL on a bad id, mode or mask; ENOMEM if the bulk
+ * arrays cannot be allocated.
+ */
+gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask, int32_t mode);
+
+/* Wait for all work of the context's stream; EDEVICE if a kernel set its
+ * error word (the word is cleared), ECUDA on a CUDA error. */
+gale_status gale_synchronize(gale_ctx *ctx);
+
+/* View of the index-th cluster of the last bulk build (no pinning). */
+gale_status gale_bulk_view(gale_ctx *ctx, int32_t index, gale_view *out);
+
+/* Device pointers and element counts (lengths[10], same order as
+ * gale_arrays) of the last bulk build's output arrays. */
+gale_status gale_bulk_arrays(gale_ctx *ctx, gale_arrays *dev, int64_t *lengths);
+
+/* Copy the last bulk build's arrays selected by mask into caller HOST
+ * buffers (each at least the length gale_bulk_arrays reports; pinned memory
+ * is fastest).  Ordered after the build on the context stream; blocks until
+ * the copies are done. */
+gale_status gale_bulk_export(gale_ctx *ctx, uint32_t mask, const gale_arrays *host_dst);
+
+/*
+ * gale_request - a consumer's request for the relations of one cluster
+ * (Section 4.4: coboundary and adjacency relations are requested for the
+ * whole segment).  Thread safe; blocks until the relations are resident or
+ * timeout_ns passes (ETIMEOUT; timeout_ns <= 0 waits without limit).
+ * Requests from many threads are batched by the serving loop, admitted
+ * against the context's cache budget, built on the device and kept in an
+ * LRU relation cache.  On success *out pins the cache entry until
+ * gale_release.  EBUSY if the budget is pinned by other views, ENOMEM if one
+ * cluster alone exceeds the budget, EINVAL on a bad id or mask.
+ */
+gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64_t timeout_ns, gale_view *out);
+
+/* Unpin a view from gale_request; its entry becomes evictable. */
+gale_status gale_release(gale_ctx *ctx, gale_view *view);
+
+/* Serving counters (requests, hits, builds, evictions, ...). */
+gale_status gale_serve_stats_get(gale_ctx *ctx, gale_serve_stats *out);
+
+/* Canonical <-> input ids: vperm[c] = input id of canonical vertex c
+ * (int32[nv]), tperm[c] = input index of canonical tet c (int32[nt]).  Either
+ * pointer may be NULL.  Host memory. */
+gale_status gale_get_permutations(gale_ctx *ctx, int32_t *vperm, int32_t *tperm);
+
+/* Interval arrays I_V and I_T (int64[nclusters+1] each, host) and the exact
+ * per-cluster sizes (int64[nclusters*5]: VT, VV, edges, ET, TT entries; NULL
+ * allowed; zeros in a host-only context). */
+gale_status gale_get_intervals(gale_ctx *ctx, int64_t *I_V, int64_t *I_T, int64_t *sizes);
+
+/* Canonical rows (int32[nt*4], host) in canonical tet order. */
+gale_status gale_get_rows(gale_ctx *ctx, int32_t *rows);
+
+/* Working set of cluster k: T_ex(k) and halo(k) as ascending canonical tet
+ * ids (caller buffers; *n_ext / *n_halo in: capacity, out: count). */
+gale_status gale_get_working_set(gale_ctx *ctx, int32_t k, int32_t *ext, int64_t *n_ext, int32_t *halo,
+                                 int64_t *n_halo);
+
+gale_status gale_get_info(gale_ctx *ctx, gale_info *out);
+
+/* Tuning: threads per block of the batched kernels (128, 256 or 512; 0 =
+ * the autotuned or default value) and CTAs per SM of the persistent grid
+ * (0 = as many as fit). */
+gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
+
+/* Autotune the batched form on a sample of clusters; stores the choice in
+ * the context. */
+gale_status gale_autotune(gale_ctx *ctx, uint32_t mask);
+
+/* The stream of the context (cudaStream_t). */
+void *gale_stream(gale_ctx *ctx);
+
+/* Number of kernel launches the last gale_build_clusters enqueued. */
+int64_t gale_last_launch_count(gale_ctx *ctx);
+
+void gale_destroy(gale_ctx *ctx);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *gale_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GALE_H */

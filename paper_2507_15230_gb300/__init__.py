@@ -1,0 +1,379 @@
+"""GB300 cluster-relation producer (GALE, arXiv 2507.15230) - Python binding.
+
+A thin ctypes layer over the C ABI declared in ``include/gale.h``: argument
+marshalling only.  Every step of the producer runs in ``libgale.so`` (host
+runtime in C++, kernels in CUDA for sm_103a).  PyTorch supplies the CUDA
+stream and, through its caching allocator, the device memory.
+
+There is no fallback: if the library cannot be built or loaded, importing
+this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+VT, VV, ET, TT = 1, 2, 4, 8
+ALL = 15
+MODE_PER_CLUSTER, MODE_BATCHED = 0, 1
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ETIMEOUT", 5: "ENOTFOUND", 6: "ECUDA", 7: "EDEVICE"}
+ARRAYS = ("vt_off", "vt_val", "vv_off", "vv_val", "et_uoff", "et_w", "et_off", "et_val", "tt_off", "tt_val")
+ARRAY_REL = (VT, VT, VV, VV, ET, ET, ET, ET, TT, TT)
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class GaleError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("nt", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("tv", ctypes.c_void_p),
+                ("seg", ctypes.c_void_p), ("nclusters", ctypes.c_int32), ("precondition_mask", ctypes.c_uint32),
+                ("cache_budget_bytes", ctypes.c_int64), ("stream", ctypes.c_void_p), ("alloc", _ALLOC),
+                ("free", _FREE), ("alloc_ctx", ctypes.c_void_p), ("device", ctypes.c_int32),
+                ("host_threads", ctypes.c_int32)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("cluster", ctypes.c_int32), ("mask", ctypes.c_uint32), ("v_begin", ctypes.c_int32),
+                ("v_end", ctypes.c_int32), ("t_begin", ctypes.c_int32), ("t_end", ctypes.c_int32),
+                ("n_edges", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
+               [(a, ctypes.c_void_p) for a in ARRAYS] + [("handle", ctypes.c_uint64)]
+
+
+class Arrays(ctypes.Structure):
+    _fields_ = [(a, ctypes.c_void_p) for a in ARRAYS]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("nt", ctypes.c_int64), ("nclusters", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("n_edges", ctypes.c_int64), ("total", ctypes.c_int64 * 5),
+                ("block_bytes", ctypes.c_int64), ("ext_tets", ctypes.c_int64), ("halo_tets", ctypes.c_int64),
+                ("nbins", ctypes.c_int32), ("max_cluster_tets", ctypes.c_int32),
+                ("load_host_seconds", ctypes.c_double), ("load_device_seconds", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("requests", "hits", "misses", "builds", "evictions", "batches",
+                                              "cache_bytes_used", "cache_bytes_budget", "max_batch")]
+
+
+# the symbols include/gale.h declares
+EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
+           "gale_bulk_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
+           "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
+           "gale_autotune", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build: bool = True):
+    """Load (building first if needed) libgale.so; raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libgale.so not found at {path}")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    lib.gale_load_mesh.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(P)]
+    lib.gale_build_clusters.argtypes = [P, P, i32, u32, i32]
+    lib.gale_synchronize.argtypes = [P]
+    lib.gale_bulk_view.argtypes = [P, i32, ctypes.POINTER(View)]
+    lib.gale_bulk_arrays.argtypes = [P, ctypes.POINTER(Arrays), P]
+    lib.gale_bulk_export.argtypes = [P, u32, ctypes.POINTER(Arrays)]
+    lib.gale_request.argtypes = [P, i32, u32, i64, ctypes.POINTER(View)]
+    lib.gale_release.argtypes = [P, ctypes.POINTER(View)]
+    lib.gale_serve_stats_get.argtypes = [P, ctypes.POINTER(ServeStats)]
+    lib.gale_get_permutations.argtypes = [P, P, P]
+    lib.gale_get_intervals.argtypes = [P, P, P, P]
+    lib.gale_get_rows.argtypes = [P, P]
+    lib.gale_get_working_set.argtypes = [P, i32, P, ctypes.POINTER(i64), P, ctypes.POINTER(i64)]
+    lib.gale_get_info.argtypes = [P, ctypes.POINTER(Info)]
+    lib.gale_set_tuning.argtypes = [P, i32, i32]
+    lib.gale_autotune.argtypes = [P, u32]
+    lib.gale_stream.argtypes = [P]
+    lib.gale_stream.restype = P
+    lib.gale_last_launch_count.argtypes = [P]
+    lib.gale_last_launch_count.restype = i64
+    lib.gale_destroy.argtypes = [P]
+    lib.gale_destroy.restype = None
+    lib.gale_last_error.argtypes = []
+    lib.gale_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise GaleError(rc, _lib.gale_last_error().decode(errors="replace"))
+
+
+def _p(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+class _DevArray:
+    """A device int32 range exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<i4", "data": (int(ptr) if n else 0, False),
+                                         "version": 3}
+
+
+def device_tensor(ptr: int, n: int):
+    """torch int32 tensor aliasing n elements of device memory at ptr."""
+    import torch
+    if n == 0:
+        return torch.zeros(0, dtype=torch.int32, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, n), device="cuda")
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, handed to the C ABI."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+        self.device, self.stream = device, stream
+        self._torch = torch
+
+        def alloc(_ctx, nbytes):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), device, stream))
+            except Exception:
+                return None
+
+        def free(_ctx, ptr):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = _ALLOC(alloc)
+        self.free = _FREE(free)
+
+
+@dataclass
+class Mesh:
+    """Input arrays in the paper's form (Section 4.3): V, T (TV), S."""
+    xyz: np.ndarray | None
+    tv: np.ndarray
+    seg: np.ndarray
+    nclusters: int
+
+
+class Context:
+    """A loaded mesh (one gale_ctx).  Use ``Context.load``."""
+
+    def __init__(self, handle, lib, keep):
+        self._h = handle
+        self._lib = lib
+        self._keep = keep  # arrays and callbacks that must outlive the handle
+        self.nv = self.info().nv
+        self.nt = self.info().nt
+        self.K = self.info().nclusters
+
+    # ---------------- construction ----------------
+    @classmethod
+    def load(cls, mesh, precondition_mask: int = ALL, device: int = 0, stream=None, cache_budget_bytes: int = 0,
+             host_threads: int = 0, torch_alloc: bool = True) -> "Context":
+        """gale_load_mesh.  mesh: anything with tv, seg, nclusters (and
+        optionally xyz).  device=-1 makes a host-only context.  stream: a
+        torch.cuda.Stream or raw handle; defaults to torch's current stream."""
+        lib = load_library()
+        tv = np.ascontiguousarray(mesh.tv, dtype=np.int32).reshape(-1, 4)
+        seg = np.ascontiguousarray(mesh.seg, dtype=np.int32)
+        xyz = None if getattr(mesh, "xyz", None) is None else np.ascontiguousarray(mesh.xyz, dtype=np.float32)
+        d = MeshDesc()
+        d.nv, d.nt = seg.shape[0], tv.shape[0]
+        d.xyz = _p(xyz) if xyz is not None else None
+        d.tv = _p(tv) if tv.size else None
+        d.seg = _p(seg)
+        d.nclusters = int(mesh.nclusters)
+        d.precondition_mask = precondition_mask
+        d.cache_budget_bytes = cache_budget_bytes
+        d.device = device
+        d.host_threads = host_threads
+        keep = [tv, seg, xyz]
+        if device >= 0:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("CUDA device requested but torch sees no GPU")
+            torch.cuda.set_device(device)
+            if stream is None:
+                stream = torch.cuda.current_stream(device)
+            sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            d.stream = sh
+            if torch_alloc:
+                ta = _TorchAllocator(device, sh)
+                d.alloc, d.free = ta.alloc, ta.free
+                keep.append(ta)
+        h = ctypes.c_void_p()
+        _check(lib.gale_load_mesh(ctypes.byref(d), ctypes.byref(h)))
+        return cls(h, lib, keep)
+
+    def close(self):
+        if self._h:
+            self._lib.gale_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------- builds ----------------
+    def build(self, ids=None, mask: int = ALL, mode: int = MODE_BATCHED):
+        """gale_build_clusters (asynchronous on the context stream)."""
+        if ids is None:
+            _check(self._lib.gale_build_clusters(self._h, None, 0, mask, mode))
+        else:
+            ids = np.ascontiguousarray(ids, dtype=np.int32)
+            _check(self._lib.gale_build_clusters(self._h, _p(ids), ids.shape[0], mask, mode))
+
+    def synchronize(self):
+        _check(self._lib.gale_synchronize(self._h))
+
+    @property
+    def stream_handle(self) -> int:
+        return self._lib.gale_stream(self._h) or 0
+
+    def last_launch_count(self) -> int:
+        return int(self._lib.gale_last_launch_count(self._h))
+
+    def bulk_view(self, index: int) -> View:
+        v = View()
+        _check(self._lib.gale_bulk_view(self._h, index, ctypes.byref(v)))
+        return v
+
+    def bulk_arrays(self):
+        """(dict name -> device pointer, dict name -> length) of the last bulk build."""
+        a = Arrays()
+        L = np.zeros(10, np.int64)
+        _check(self._lib.gale_bulk_arrays(self._h, ctypes.byref(a), _p(L)))
+        return {n: getattr(a, n) or 0 for n in ARRAYS}, {n: int(L[i]) for i, n in enumerate(ARRAYS)}
+
+    def export(self, mask: int = ALL, out: dict | None = None) -> dict:
+        """gale_bulk_export into host numpy arrays (allocated unless given)."""
+        _, L = self.bulk_arrays()
+        if out is None:
+            out = {n: np.empty(L[n], np.int32) for i, n in enumerate(ARRAYS) if mask & ARRAY_REL[i]}
+        a = Arrays()
+        for n, arr in out.items():
+            setattr(a, n, _p(arr) if arr.size else None)
+        _check(self._lib.gale_bulk_export(self._h, mask, ctypes.byref(a)))
+        return out
+
+    def bulk_offsets(self, index: int) -> dict:
+        """Element offsets of the index-th cluster in each bulk array."""
+        ptrs, _ = self.bulk_arrays()
+        v = self.bulk_view(index)
+        res = {}
+        for n in ARRAYS:
+            p = getattr(v, n)
+            res[n] = None if not p else (p - ptrs[n]) // 4
+        return res
+
+    # ---------------- serving ----------------
+    def request(self, cluster: int, mask: int, timeout_ns: int = 0) -> View:
+        v = View()
+        _check(self._lib.gale_request(self._h, cluster, mask, timeout_ns, ctypes.byref(v)))
+        return v
+
+    def release(self, view: View):
+        _check(self._lib.gale_release(self._h, ctypes.byref(view)))
+
+    def serve_stats(self) -> ServeStats:
+        s = ServeStats()
+        _check(self._lib.gale_serve_stats_get(self._h, ctypes.byref(s)))
+        return s
+
+    # ---------------- introspection ----------------
+    def info(self) -> Info:
+        i = Info()
+        _check(self._lib.gale_get_info(self._h, ctypes.byref(i)))
+        return i
+
+    def permutations(self):
+        vp = np.empty(self.nv, np.int32)
+        tp = np.empty(max(self.nt, 1), np.int32)
+        _check(self._lib.gale_get_permutations(self._h, _p(vp), _p(tp)))
+        return vp, tp[:self.nt]
+
+    def intervals(self):
+        I_V = np.empty(self.K + 1, np.int64)
+        I_T = np.empty(self.K + 1, np.int64)
+        sizes = np.empty((self.K, 5), np.int64)
+        _check(self._lib.gale_get_intervals(self._h, _p(I_V), _p(I_T), _p(sizes)))
+        return I_V, I_T, sizes
+
+    def rows(self) -> np.ndarray:
+        r = np.empty((max(self.nt, 1), 4), np.int32)
+        _check(self._lib.gale_get_rows(self._h, _p(r)))
+        return r[:self.nt]
+
+    def working_set(self, k: int):
+        ne, nh = ctypes.c_int64(0), ctypes.c_int64(0)
+        rc = self._lib.gale_get_working_set(self._h, k, None, ctypes.byref(ne), None, ctypes.byref(nh))
+        ext = np.empty(max(ne.value, 1), np.int32)
+        halo = np.empty(max(nh.value, 1), np.int32)
+        _check(self._lib.gale_get_working_set(self._h, k, _p(ext), ctypes.byref(ne), _p(halo), ctypes.byref(nh)))
+        return ext[:ne.value], halo[:nh.value]
+
+    def set_tuning(self, threads: int = 0, ctas_per_sm: int = 0):
+        _check(self._lib.gale_set_tuning(self._h, threads, ctas_per_sm))
+
+    def autotune(self, mask: int = ALL):
+        _check(self._lib.gale_autotune(self._h, mask))
+
+
+def view_to_numpy(view: View) -> dict:
+    """Copy one view's device arrays to host numpy (through torch)."""
+    nvo = view.v_end - view.v_begin
+    nown = view.t_end - view.t_begin
+    out = {}
+
+    def grab(name, n):
+        p = getattr(view, name)
+        if not p:
+            return None
+        return device_tensor(p, n).cpu().numpy()
+
+    if view.mask & VT:
+        out["vt_off"] = grab("vt_off", nvo + 1)
+        out["vt_val"] = grab("vt_val", int(out["vt_off"][-1]))
+    if view.mask & VV:
+        out["vv_off"] = grab("vv_off", nvo + 1)
+        out["vv_val"] = grab("vv_val", int(out["vv_off"][-1]))
+    if view.mask & ET:
+        out["et_uoff"] = grab("et_uoff", nvo + 1)
+        ne = view.n_edges
+        out["et_w"] = grab("et_w", ne)
+        out["et_off"] = grab("et_off", ne + 1)
+        out["et_val"] = grab("et_val", int(out["et_off"][-1]))
+    if view.mask & TT:
+        out["tt_off"] = grab("tt_off", nown + 1)
+        out["tt_val"] = grab("tt_val", int(out["tt_off"][-1]))
+    return out

@@ -1,0 +1,656 @@
+// C ABI: context life cycle, loading, bulk builds, views and exports.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+#include <string>
+
+#include "gale_ctx.h"
+
+using gale::WorkItem;
+
+namespace gale {
+
+static thread_local std::string t_error;
+
+void set_error(const std::string &msg) { t_error = msg; }
+
+// Serving hooks (gale_serve.cpp).
+void serve_destroy(gale_ctx *ctx);
+
+}  // namespace gale
+
+namespace {
+
+gale_status fail(gale_status s, const std::string &msg) {
+    gale::set_error(msg);
+    return s;
+}
+
+gale_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(GALE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call)                                       \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);  \
+    } while (0)
+
+int64_t next_pow2(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+gale::Caps caps_of(const gale::ClusterStat &s) {
+    gale::Caps c{};
+    c.blk_words = int32_t(gale::blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo));
+    c.nv_own = s.nv_own;
+    c.n_vt = s.n_vt;
+    c.n_own = s.n_own;
+    c.nv_loc = s.nv_loc;
+    c.max_deg = s.max_deg;
+    c.max_up = std::max(1, std::min(3 * s.max_deg, s.nv_loc - 1));
+    c.hcap = int32_t(std::max<int64_t>(64, next_pow2(4 * int64_t(s.n_own) + 1)));
+    return c;
+}
+
+gale::Caps merge(const gale::Caps &a, const gale::Caps &b) {
+    gale::Caps c{};
+    c.blk_words = std::max(a.blk_words, b.blk_words);
+    c.nv_own = std::max(a.nv_own, b.nv_own);
+    c.n_vt = std::max(a.n_vt, b.n_vt);
+    c.n_own = std::max(a.n_own, b.n_own);
+    c.nv_loc = std::max(a.nv_loc, b.nv_loc);
+    c.max_deg = std::max(a.max_deg, b.max_deg);
+    c.max_up = std::max(a.max_up, b.max_up);
+    c.hcap = std::max(a.hcap, b.hcap);
+    return c;
+}
+
+// Size bins: clusters sorted by shared-memory need, cut where the merged
+// plan would cross the next occupancy tier (4, 3, 2, 1 CTAs per SM).
+gale_status plan_bins(gale_ctx *ctx) {
+    const int32_t K = ctx->hm.K;
+    const int smem_cta = gale::kernel_smem_limit();
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+    std::vector<int32_t> need(K);
+    for (int32_t k = 0; k < K; ++k) need[k] = gale::plan_smem(caps_of(ctx->hm.stats[k]), ctx->threads).total;
+    std::vector<int32_t> idx(K);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return need[a] < need[b]; });
+    std::vector<int> tiers;
+    for (int per = 4; per >= 1; --per) {
+        int t = smem_sm / per - 1024 * per;  // leave room for static smem and reservation
+        tiers.push_back(std::min(t, smem_cta));
+    }
+    ctx->bins.clear();
+    ctx->bin_of.assign(K, -1);
+    size_t tier = 0;
+    gale::Caps cur{};
+    std::vector<int32_t> members;
+    auto close = [&]() {
+        if (members.empty()) return;
+        gale::Bin b;
+        b.plan = gale::plan_smem(cur, ctx->threads);
+        // largest working sets first
+        std::stable_sort(members.begin(), members.end(),
+                         [&](int32_t a, int32_t c) { return need[a] > need[c]; });
+        b.clusters = members;
+        for (int32_t k : members) ctx->bin_of[k] = int32_t(ctx->bins.size());
+        ctx->bins.push_back(std::move(b));
+        members.clear();
+        cur = gale::Caps{};
+    };
+    for (int32_t k : idx) {
+        if (need[k] > smem_cta)
+            return fail(GALE_EINVAL, "cluster " + std::to_string(k) + " needs " + std::to_string(need[k]) +
+                                         " bytes of shared memory (limit " + std::to_string(smem_cta) +
+                                         "); use smaller clusters");
+        gale::Caps m = members.empty() ? caps_of(ctx->hm.stats[k]) : merge(cur, caps_of(ctx->hm.stats[k]));
+        int tot = gale::plan_smem(m, ctx->threads).total;
+        while (tier < tiers.size() && tot > tiers[tier]) {
+            close();
+            ++tier;
+            m = caps_of(ctx->hm.stats[k]);
+            tot = gale::plan_smem(m, ctx->threads).total;
+        }
+        if (tier >= tiers.size()) tier = tiers.size() - 1;
+        cur = m;
+        members.push_back(k);
+    }
+    close();
+    for (auto &b : ctx->bins) {
+        gale::prepare_kernels(b.plan.threads, b.plan.total);
+        int per_sm = gale::max_ctas_per_sm(b.plan);
+        if (per_sm < 1) return fail(GALE_EINVAL, "a size bin cannot be launched (shared memory or registers)");
+        if (ctx->ctas_override > 0) per_sm = std::min(per_sm, ctx->ctas_override);
+        b.grid = std::max(1, std::min<int>(int(b.clusters.size()), per_sm * ctx->sm_count));
+    }
+    return GALE_OK;
+}
+
+gale_status upload_orders(gale_ctx *ctx) {
+    std::vector<int32_t> order;  // positions in the all-clusters item list (= cluster ids)
+    ctx->order_all_off.assign(1, 0);
+    for (auto &b : ctx->bins) {
+        order.insert(order.end(), b.clusters.begin(), b.clusters.end());
+        ctx->order_all_off.push_back(int64_t(order.size()));
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_order_all, order.data(), order.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    return GALE_OK;
+}
+
+gale::DevMesh dev_mesh(gale_ctx *ctx) {
+    return gale::DevMesh{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
+}
+
+gale_status check_device_error(gale_ctx *ctx) {
+    int32_t e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (e == 0) return GALE_OK;
+    CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    std::string msg = "kernel error word " + std::to_string(e) + ":";
+    if (e & gale::ERR_CAPACITY) msg += " cluster exceeded its launch capacities;";
+    if (e & gale::ERR_NONMANIFOLD) msg += " a triangle is shared by more than two tets (TT needs a manifold mesh);";
+    if (e & gale::ERR_HASH_FULL) msg += " face hash overflow;";
+    if (e & gale::ERR_BAD_ITEM) msg += " bad cluster id in a work item;";
+    if (e & gale::ERR_TIMEOUT) msg += " a device wait timed out;";
+    return fail(GALE_EDEVICE, msg);
+}
+
+gale_status count_pass(gale_ctx *ctx) {
+    const int32_t K = ctx->hm.K;
+    CUDA_TRY(cudaMemsetAsync(ctx->d_sizes, 0, sizeof(int64_t) * 5 * K, ctx->stream));
+    for (size_t b = 0; b < ctx->bins.size(); ++b) {
+        const gale::Bin &bin = ctx->bins[b];
+        int rc = gale::launch_count_pass(dev_mesh(ctx), bin.plan, ctx->d_order_all + ctx->order_all_off[b],
+                                         int32_t(bin.clusters.size()), ctx->d_sizes, ctx->d_err,
+                                         ctx->d_tickets + b, bin.grid, ctx->stream);
+        if (rc != 0) return cuda_fail(cudaError_t(rc), "count pass launch");
+    }
+    gale_status st = check_device_error(ctx);
+    if (st != GALE_OK) return st;
+    ctx->sizes.resize(size_t(5) * K);
+    CUDA_TRY(cudaMemcpyAsync(ctx->sizes.data(), ctx->d_sizes, sizeof(int64_t) * 5 * K, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int a = 0; a < 5; ++a) ctx->totals[a] = 0;
+    for (int32_t k = 0; k < K; ++k)
+        for (int a = 0; a < 5; ++a) ctx->totals[a] += ctx->sizes[size_t(5) * k + a];
+    return GALE_OK;
+}
+
+// Lengths of the ten output arrays of cluster k under mask.
+void item_lengths(const gale_ctx *ctx, int32_t k, uint32_t mask, int64_t *L) {
+    const int64_t *sz = ctx->sizes.data() + size_t(5) * k;
+    const int64_t nvo = ctx->hm.I_V[k + 1] - ctx->hm.I_V[k];
+    const int64_t nown = ctx->hm.I_T[k + 1] - ctx->hm.I_T[k];
+    const bool vt = mask & GALE_VT, vv = mask & GALE_VV, et = mask & GALE_ET, tt = mask & GALE_TT;
+    L[0] = vt ? nvo + 1 : 0;
+    L[1] = vt ? sz[0] : 0;
+    L[2] = vv ? nvo + 1 : 0;
+    L[3] = vv ? sz[1] : 0;
+    L[4] = et ? nvo + 1 : 0;
+    L[5] = et ? sz[2] : 0;
+    L[6] = et ? sz[2] + 1 : 0;
+    L[7] = et ? sz[3] : 0;
+    L[8] = tt ? nown + 1 : 0;
+    L[9] = tt ? sz[4] : 0;
+}
+
+gale_status ensure_bulk(gale_ctx *ctx, const int64_t *need) {
+    bool realloc = false;
+    for (int a = 0; a < 10; ++a) {
+        if (need[a] <= ctx->bulk_cap[a]) continue;
+        if (ctx->bulk[a]) ctx->dfree(ctx->bulk[a]);
+        ctx->bulk[a] = nullptr;
+        ctx->bulk_cap[a] = 0;
+        const int64_t cap = need[a] + need[a] / 16 + 64;
+        ctx->bulk[a] = static_cast<int32_t *>(ctx->dalloc(size_t(cap) * 4));
+        if (!ctx->bulk[a]) return fail(GALE_ENOMEM, "device allocation of a bulk output array failed");
+        ctx->bulk_cap[a] = cap;
+        realloc = true;
+    }
+    if (realloc) {
+        for (auto &g : ctx->graphs)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+    // base pointers for every mask (unmasked arrays NULL)
+    WorkItem base[16];
+    for (uint32_t m = 0; m < 16; ++m) {
+        WorkItem &w = base[m];
+        memset(&w, 0, sizeof(w));
+        w.vt_off = (m & GALE_VT) ? ctx->bulk[0] : nullptr;
+        w.vt_val = (m & GALE_VT) ? ctx->bulk[1] : nullptr;
+        w.vv_off = (m & GALE_VV) ? ctx->bulk[2] : nullptr;
+        w.vv_val = (m & GALE_VV) ? ctx->bulk[3] : nullptr;
+        w.eu_off = (m & GALE_ET) ? ctx->bulk[4] : nullptr;
+        w.e_w = (m & GALE_ET) ? ctx->bulk[5] : nullptr;
+        w.et_off = (m & GALE_ET) ? ctx->bulk[6] : nullptr;
+        w.et_val = (m & GALE_ET) ? ctx->bulk[7] : nullptr;
+        w.tt_off = (m & GALE_TT) ? ctx->bulk[8] : nullptr;
+        w.tt_val = (m & GALE_TT) ? ctx->bulk[9] : nullptr;
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_arrays_base, base, sizeof(base), cudaMemcpyHostToDevice, ctx->stream));
+    return GALE_OK;
+}
+
+}  // namespace
+
+void *gale_ctx::dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (alloc_fn) {
+        p = alloc_fn(alloc_ctx, bytes);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) allocs.push_back(gale::DevAlloc{p, bytes});
+    return p;
+}
+
+void gale_ctx::dfree(void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < allocs.size(); ++i)
+        if (allocs[i].ptr == p) {
+            allocs.erase(allocs.begin() + i);
+            break;
+        }
+    if (free_fn) free_fn(alloc_ctx, p);
+    else cudaFree(p);
+}
+
+bool gale::HostMesh::alloc_blocks(int64_t words) {
+    free_blocks();
+    const size_t bytes = size_t(std::max<int64_t>(words, 4)) * 4;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&blocks), bytes, cudaHostAllocDefault) == cudaSuccess) {
+        blocks_pinned = true;
+        return true;
+    }
+    cudaGetLastError();
+    blocks = static_cast<int32_t *>(malloc(bytes));
+    blocks_pinned = false;
+    return blocks != nullptr;
+}
+
+void gale::HostMesh::free_blocks() {
+    if (!blocks) return;
+    if (blocks_pinned) cudaFreeHost(blocks);
+    else free(blocks);
+    blocks = nullptr;
+}
+
+extern "C" {
+
+const char *gale_last_error(void) { return gale::t_error.c_str(); }
+
+void gale_destroy(gale_ctx *ctx) {
+    if (!ctx) return;
+    gale::serve_destroy(ctx);
+    if (ctx->device >= 0) {
+        cudaSetDevice(ctx->device);
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        for (auto &g : ctx->graphs)
+            if (g) cudaGraphExecDestroy(g);
+        while (!ctx->allocs.empty()) ctx->dfree(ctx->allocs.back().ptr);
+        if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+}
+
+gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out) {
+    if (!desc || !out) return fail(GALE_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (desc->precondition_mask == 0 || (desc->precondition_mask & ~uint32_t(GALE_ALL)))
+        return fail(GALE_EINVAL, "precondition_mask must be a non-empty subset of GALE_ALL");
+    auto ctx = std::make_unique<gale_ctx>();
+    ctx->precond = desc->precondition_mask;
+    ctx->device = desc->device;
+    ctx->alloc_fn = desc->alloc;
+    ctx->free_fn = desc->free;
+    ctx->alloc_ctx = desc->alloc_ctx;
+    ctx->cache_budget = desc->cache_budget_bytes;
+    std::string err;
+    try {
+        if (!gale::prepare_host(*desc, ctx->hm, err)) return fail(GALE_EINVAL, err);
+    } catch (const std::bad_alloc &) {
+        return fail(GALE_ENOMEM, "host allocation failed during initialisation");
+    }
+    if (ctx->device < 0) {
+        *out = ctx.release();
+        return GALE_OK;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    if (desc->stream) {
+        ctx->stream = static_cast<cudaStream_t>(desc->stream);
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    ctx->sm_count = gale::device_sm_count();
+    const int32_t K = ctx->hm.K;
+    auto &hm = ctx->hm;
+    ctx->d_blocks = static_cast<int32_t *>(ctx->dalloc(size_t(hm.blocks_words) * 4));
+    ctx->d_blk_off = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * (K + 1)));
+    ctx->d_I_V = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * (K + 1)));
+    ctx->d_I_T = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * (K + 1)));
+    ctx->d_sizes = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * 5 * K));
+    ctx->d_err = static_cast<int32_t *>(ctx->dalloc(64));
+    ctx->d_tickets = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * 64));
+    ctx->d_ids = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * K));
+    ctx->d_order_all = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * K));
+    ctx->d_order_part = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * K));
+    ctx->d_items = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * K));
+    ctx->d_arrays_base = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * 16));
+    ctx->d_totals = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * 16));
+    if (!ctx->d_blocks || !ctx->d_blk_off || !ctx->d_I_V || !ctx->d_I_T || !ctx->d_sizes || !ctx->d_err ||
+        !ctx->d_tickets || !ctx->d_ids || !ctx->d_order_all || !ctx->d_order_part || !ctx->d_items ||
+        !ctx->d_arrays_base || !ctx->d_totals) {
+        gale_destroy(ctx.release());
+        return fail(GALE_ENOMEM, "device allocation failed while loading the mesh");
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_blocks, hm.blocks, size_t(hm.blocks_words) * 4, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_blk_off, hm.blk_off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice,
+                             ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_I_V, hm.I_V.data(), sizeof(int32_t) * (K + 1), cudaMemcpyHostToDevice,
+                             ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_I_T, hm.I_T.data(), sizeof(int32_t) * (K + 1), cudaMemcpyHostToDevice,
+                             ctx->stream));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 64, ctx->stream));
+    gale_status st = plan_bins(ctx.get());
+    if (st == GALE_OK) st = upload_orders(ctx.get());
+    if (st == GALE_OK) st = count_pass(ctx.get());
+    if (st != GALE_OK) {
+        std::string keep = gale::t_error;
+        gale_destroy(ctx.release());
+        return fail(st, keep);
+    }
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    // the host copy of the blocks is no longer needed
+    hm.free_blocks();
+    ctx->device_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = ctx.release();
+    return GALE_OK;
+}
+
+gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask, int32_t mode) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
+    if (mask == 0 || (mask & ~ctx->precond))
+        return fail(GALE_EINVAL, "mask must be a non-empty subset of the precondition mask");
+    if (mode != GALE_MODE_PER_CLUSTER && mode != GALE_MODE_BATCHED) return fail(GALE_EINVAL, "unknown mode");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const int32_t K = ctx->hm.K;
+    const bool all = (ids == nullptr || n <= 0);
+    const int32_t cnt = all ? K : n;
+    if (!all && n > K) return fail(GALE_EINVAL, "more ids than clusters");
+    std::vector<int32_t> list(cnt);
+    if (all) {
+        std::iota(list.begin(), list.end(), 0);
+    } else {
+        std::vector<uint8_t> seen(K, 0);
+        for (int32_t i = 0; i < n; ++i) {
+            if (ids[i] < 0 || ids[i] >= K) return fail(GALE_EINVAL, "cluster id out of range");
+            if (seen[ids[i]]++) return fail(GALE_EINVAL, "cluster id listed twice");
+            list[i] = ids[i];
+        }
+    }
+    // placement bookkeeping on the host (views); the device recomputes it
+    ctx->bulk_offs.assign(size_t(cnt) * 10, 0);
+    int64_t run[10] = {};
+    for (int32_t i = 0; i < cnt; ++i) {
+        int64_t L[10];
+        item_lengths(ctx, list[i], mask, L);
+        for (int a = 0; a < 10; ++a) {
+            ctx->bulk_offs[size_t(i) * 10 + a] = run[a];
+            run[a] += L[a];
+        }
+    }
+    gale_status st = ensure_bulk(ctx, run);
+    if (st != GALE_OK) return st;
+    for (int a = 0; a < 10; ++a) ctx->bulk_len[a] = run[a];
+    ctx->bulk_ids = list;
+    ctx->bulk_mask = mask;
+    const gale::DevMesh dm = dev_mesh(ctx);
+    const WorkItem *base = ctx->d_arrays_base + mask;
+    int64_t launches = 0;
+    if (mode == GALE_MODE_BATCHED && all) {
+        cudaGraphExec_t &g = ctx->graphs[mask];
+        if (!g) {
+            cudaGraph_t graph;
+            CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = gale::launch_bases(dm, nullptr, K, ctx->d_sizes, mask, base, ctx->d_items, ctx->d_totals,
+                                        ctx->stream);
+            for (size_t b = 0; rc == 0 && b < ctx->bins.size(); ++b) {
+                const gale::Bin &bin = ctx->bins[b];
+                rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b],
+                                        int32_t(bin.clusters.size()), ctx->d_err, ctx->d_tickets + b, bin.grid,
+                                        ctx->stream);
+            }
+            cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+            if (rc != 0) return cuda_fail(cudaError_t(rc), "capturing the batched build");
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+            ce = cudaGraphInstantiate(&g, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                g = nullptr;
+                return cuda_fail(ce, "cudaGraphInstantiate");
+            }
+        }
+        CUDA_TRY(cudaGraphLaunch(g, ctx->stream));
+        launches = 1 + int64_t(ctx->bins.size());
+    } else {
+        const int32_t *d_ids = nullptr;
+        if (!all) {
+            CUDA_TRY(cudaMemcpyAsync(ctx->d_ids, list.data(), size_t(cnt) * 4, cudaMemcpyHostToDevice, ctx->stream));
+            d_ids = ctx->d_ids;
+        }
+        int rc = gale::launch_bases(dm, d_ids, cnt, ctx->d_sizes, mask, base, ctx->d_items, ctx->d_totals,
+                                    ctx->stream);
+        if (rc != 0) return cuda_fail(cudaError_t(rc), "bases launch");
+        launches = 1;
+        if (mode == GALE_MODE_PER_CLUSTER) {
+            for (int32_t i = 0; i < cnt; ++i) {
+                const gale::Bin &bin = ctx->bins[ctx->bin_of[list[i]]];
+                rc = gale::launch_build_one(dm, bin.plan, ctx->d_items, i, ctx->d_err, ctx->stream);
+                if (rc != 0) return cuda_fail(cudaError_t(rc), "per-cluster launch");
+            }
+            launches += cnt;
+        } else {
+            // partial batched build: per-bin item orders
+            std::vector<std::vector<int32_t>> per_bin(ctx->bins.size());
+            for (int32_t i = 0; i < cnt; ++i) per_bin[ctx->bin_of[list[i]]].push_back(i);
+            std::vector<int32_t> order;
+            std::vector<int64_t> off(1, 0);
+            for (size_t b = 0; b < per_bin.size(); ++b) {
+                auto &v = per_bin[b];
+                std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t c) {
+                    return ctx->hm.stats[list[a]].n_own + ctx->hm.stats[list[a]].n_ext >
+                           ctx->hm.stats[list[c]].n_own + ctx->hm.stats[list[c]].n_ext;
+                });
+                order.insert(order.end(), v.begin(), v.end());
+                off.push_back(int64_t(order.size()));
+            }
+            CUDA_TRY(cudaMemcpyAsync(ctx->d_order_part, order.data(), order.size() * 4, cudaMemcpyHostToDevice,
+                                     ctx->stream));
+            for (size_t b = 0; b < per_bin.size(); ++b) {
+                const int32_t nb = int32_t(off[b + 1] - off[b]);
+                if (nb == 0) continue;
+                const gale::Bin &bin = ctx->bins[b];
+                rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_part + off[b], nb, ctx->d_err,
+                                        ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream);
+                if (rc != 0) return cuda_fail(cudaError_t(rc), "batched launch");
+                ++launches;
+            }
+        }
+    }
+    ctx->last_launches = launches;
+    return GALE_OK;
+}
+
+gale_status gale_synchronize(gale_ctx *ctx) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (ctx->device < 0) return GALE_OK;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return check_device_error(ctx);
+}
+
+gale_status gale_bulk_view(gale_ctx *ctx, int32_t index, gale_view *out) {
+    if (!ctx || !out) return fail(GALE_EINVAL, "NULL argument");
+    if (index < 0 || index >= int32_t(ctx->bulk_ids.size())) return fail(GALE_ENOTFOUND, "no such bulk index");
+    const int32_t k = ctx->bulk_ids[index];
+    const int64_t *o = ctx->bulk_offs.data() + size_t(index) * 10;
+    const uint32_t m = ctx->bulk_mask;
+    memset(out, 0, sizeof(*out));
+    out->cluster = k;
+    out->mask = m;
+    out->v_begin = ctx->hm.I_V[k];
+    out->v_end = ctx->hm.I_V[k + 1];
+    out->t_begin = ctx->hm.I_T[k];
+    out->t_end = ctx->hm.I_T[k + 1];
+    out->n_edges = int32_t(ctx->sizes[size_t(5) * k + 2]);
+    const int32_t *const *b = ctx->bulk;
+    if (m & GALE_VT) { out->vt_off = b[0] + o[0]; out->vt_val = b[1] + o[1]; }
+    if (m & GALE_VV) { out->vv_off = b[2] + o[2]; out->vv_val = b[3] + o[3]; }
+    if (m & GALE_ET) {
+        out->et_uoff = b[4] + o[4]; out->et_w = b[5] + o[5]; out->et_off = b[6] + o[6]; out->et_val = b[7] + o[7];
+    }
+    if (m & GALE_TT) { out->tt_off = b[8] + o[8]; out->tt_val = b[9] + o[9]; }
+    return GALE_OK;
+}
+
+gale_status gale_bulk_arrays(gale_ctx *ctx, gale_arrays *dev, int64_t *lengths) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (dev) {
+        int32_t **d = &dev->vt_off;
+        for (int a = 0; a < 10; ++a) d[a] = ctx->bulk[a];
+    }
+    if (lengths)
+        for (int a = 0; a < 10; ++a) lengths[a] = ctx->bulk_len[a];
+    return GALE_OK;
+}
+
+gale_status gale_bulk_export(gale_ctx *ctx, uint32_t mask, const gale_arrays *host_dst) {
+    if (!ctx || !host_dst) return fail(GALE_EINVAL, "NULL argument");
+    if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    int32_t *const *h = &host_dst->vt_off;
+    const uint32_t rel_of[10] = {GALE_VT, GALE_VT, GALE_VV, GALE_VV, GALE_ET, GALE_ET, GALE_ET, GALE_ET, GALE_TT, GALE_TT};
+    for (int a = 0; a < 10; ++a) {
+        if (!(mask & rel_of[a] & ctx->bulk_mask) || ctx->bulk_len[a] == 0) continue;
+        if (!h[a]) return fail(GALE_EINVAL, "NULL host buffer for a requested array");
+        CUDA_TRY(cudaMemcpyAsync(h[a], ctx->bulk[a], size_t(ctx->bulk_len[a]) * 4, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GALE_OK;
+}
+
+gale_status gale_get_permutations(gale_ctx *ctx, int32_t *vperm, int32_t *tperm) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (vperm) memcpy(vperm, ctx->hm.vperm.data(), sizeof(int32_t) * ctx->hm.nv);
+    if (tperm) memcpy(tperm, ctx->hm.tperm.data(), sizeof(int32_t) * ctx->hm.nt);
+    return GALE_OK;
+}
+
+gale_status gale_get_intervals(gale_ctx *ctx, int64_t *I_V, int64_t *I_T, int64_t *sizes) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    const int32_t K = ctx->hm.K;
+    for (int32_t k = 0; k <= K; ++k) {
+        if (I_V) I_V[k] = ctx->hm.I_V[k];
+        if (I_T) I_T[k] = ctx->hm.I_T[k];
+    }
+    if (sizes) {
+        if (ctx->sizes.empty()) memset(sizes, 0, sizeof(int64_t) * 5 * K);
+        else memcpy(sizes, ctx->sizes.data(), sizeof(int64_t) * 5 * K);
+    }
+    return GALE_OK;
+}
+
+gale_status gale_get_rows(gale_ctx *ctx, int32_t *rows) {
+    if (!ctx || !rows) return fail(GALE_EINVAL, "NULL argument");
+    memcpy(rows, ctx->hm.rows.data(), sizeof(int32_t) * 4 * ctx->hm.nt);
+    return GALE_OK;
+}
+
+gale_status gale_get_working_set(gale_ctx *ctx, int32_t k, int32_t *ext, int64_t *n_ext, int32_t *halo,
+                                 int64_t *n_halo) {
+    if (!ctx || !n_ext || !n_halo) return fail(GALE_EINVAL, "NULL argument");
+    if (k < 0 || k >= ctx->hm.K) return fail(GALE_ENOTFOUND, "no such cluster");
+    const auto &hm = ctx->hm;
+    const int64_t ne = hm.ext_off[k + 1] - hm.ext_off[k], nh = hm.halo_off[k + 1] - hm.halo_off[k];
+    if (*n_ext < ne || *n_halo < nh) {
+        *n_ext = ne;
+        *n_halo = nh;
+        return fail(GALE_EINVAL, "buffers too small");
+    }
+    if (ext) memcpy(ext, hm.ext.data() + hm.ext_off[k], sizeof(int32_t) * ne);
+    if (halo) memcpy(halo, hm.halo.data() + hm.halo_off[k], sizeof(int32_t) * nh);
+    *n_ext = ne;
+    *n_halo = nh;
+    return GALE_OK;
+}
+
+gale_status gale_get_info(gale_ctx *ctx, gale_info *out) {
+    if (!ctx || !out) return fail(GALE_EINVAL, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->nv = ctx->hm.nv;
+    out->nt = ctx->hm.nt;
+    out->nclusters = ctx->hm.K;
+    out->device = ctx->device;
+    out->n_edges = ctx->totals[2];
+    for (int a = 0; a < 5; ++a) out->total[a] = ctx->totals[a];
+    out->block_bytes = ctx->hm.blocks_words * 4;
+    out->ext_tets = ctx->hm.ext_total;
+    out->halo_tets = ctx->hm.halo_total;
+    out->nbins = int32_t(ctx->bins.size());
+    int32_t mx = 0;
+    for (auto &s : ctx->hm.stats) mx = std::max(mx, s.n_ext + s.n_own + s.n_halo);
+    out->max_cluster_tets = mx;
+    out->load_host_seconds = ctx->hm.host_seconds;
+    out->load_device_seconds = ctx->device_seconds;
+    return GALE_OK;
+}
+
+gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
+        return fail(GALE_EINVAL, "threads must be 0, 128, 256 or 512");
+    if (ctx->device < 0) return GALE_OK;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->threads = threads ? threads : 256;
+    ctx->ctas_override = ctas_per_sm;
+    gale_status st = plan_bins(ctx);
+    if (st != GALE_OK) return st;
+    st = upload_orders(ctx);
+    for (auto &g : ctx->graphs)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return st;
+}
+
+void *gale_stream(gale_ctx *ctx) { return ctx ? static_cast<void *>(ctx->stream) : nullptr; }
+
+int64_t gale_last_launch_count(gale_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// The context behind the opaque gale_ctx handle (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gale_host.h"
+
+namespace gale {
+
+struct Serve;  // serving loop state (gale_serve.cpp)
+
+struct Bin {
+    SmemPlan plan;
+    std::vector<int32_t> clusters;  // members, largest working set first
+    int grid = 0;                   // persistent CTAs
+};
+
+struct DevAlloc {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+void set_error(const std::string &msg);
+
+}  // namespace gale
+
+struct gale_ctx {
+    gale::HostMesh hm;
+    uint32_t precond = 0;
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    gale_alloc_fn alloc_fn = nullptr;
+    gale_free_fn free_fn = nullptr;
+    void *alloc_ctx = nullptr;
+    int64_t cache_budget = 0;
+
+    // device copies of the initialised arrays
+    int32_t *d_blocks = nullptr;
+    int64_t *d_blk_off = nullptr;
+    int32_t *d_I_V = nullptr, *d_I_T = nullptr;
+    int64_t *d_sizes = nullptr;  // [K*5]
+    int32_t *d_err = nullptr;
+    int32_t *d_tickets = nullptr;  // one per bin (+ spare)
+    int32_t *d_ids = nullptr;      // [K] ids of a partial build
+    int32_t *d_order_all = nullptr;   // [K] per-bin LPT order of a full build
+    int32_t *d_order_part = nullptr;  // [K] order of a partial build
+    gale::WorkItem *d_items = nullptr;      // [K]
+    gale::WorkItem *d_arrays_base = nullptr;  // [16] base pointers per mask
+    int64_t *d_totals = nullptr;            // [10]
+    std::vector<int64_t> sizes;             // host [K*5]
+    int64_t totals[5] = {0, 0, 0, 0, 0};
+    double device_seconds = 0;
+
+    // size bins
+    std::vector<gale::Bin> bins;
+    std::vector<int32_t> bin_of;        // [K]
+    std::vector<int64_t> order_all_off; // [nbins+1] offsets into d_order_all
+    int threads = 256;
+    int ctas_override = 0;
+    int sm_count = 0;
+
+    // bulk output arrays
+    int32_t *bulk[10] = {};
+    int64_t bulk_cap[10] = {};
+    int64_t bulk_len[10] = {};
+    std::vector<int64_t> bulk_offs;  // [n*10]
+    std::vector<int32_t> bulk_ids;
+    uint32_t bulk_mask = 0;
+
+    // captured full builds, one per mask
+    cudaGraphExec_t graphs[16] = {};
+    int64_t last_launches = 0;
+
+    std::vector<gale::DevAlloc> allocs;
+    std::mutex mu;  // guards builds and the bulk state
+
+    gale::Serve *serve = nullptr;
+
+    void *dalloc(size_t bytes);
+    void dfree(void *p);
+};

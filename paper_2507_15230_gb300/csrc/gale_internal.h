@@ -1,0 +1,145 @@
+// Internal layout shared by the host runtime (gale_*.cpp) and the kernels
+// (gale_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <stdint.h>
+#include <stddef.h>
+
+#if defined(__CUDACC__)
+#define GALE_HD __host__ __device__
+#else
+#define GALE_HD
+#endif
+
+namespace gale {
+
+// ---------------------------------------------------------------------------
+// Cluster working set ("block"), one per cluster, contiguous in device memory
+// and 16-byte aligned.  All sections are int32 words; every section starts on
+// a multiple of 4 words so the block can be moved with 16-byte vector loads
+// or one bulk copy.
+//
+//   [0, 8)                header (BlockHdr)
+//   [8, 8 + a4(nv_loc))   vmap: canonical id of each local vertex, ascending
+//   next a4(n_ext+n_halo) tmap: canonical ids of the external tets (ascending,
+//                         all below the cluster's first internal tet) then of
+//                         the halo tets (ascending)
+//   next a4(2 * n_tot)    rows: 4 x uint16 local vertex ids per tet (ascending
+//                         within the row), tets in local order
+//                         [external | internal | halo]
+//
+// Local vertex ids are ranks in vmap, so local order equals canonical order;
+// the cluster's own vertices are the local interval [own_lo, own_lo+nv_own)
+// and canonical interval [v_base, v_base+nv_own).  Local tet i maps to
+//   i <  n_ext                tmap[i]
+//   i <  n_ext + n_own        t_base + (i - n_ext)
+//   otherwise                 tmap[i - n_own]
+// and since external tets precede the internal ones in canonical order, the
+// local order of [external | internal] is canonical order too.
+// ---------------------------------------------------------------------------
+struct BlockHdr {
+    int32_t n_ext, n_own, n_halo, nv_loc;
+    int32_t own_lo, nv_own, t_base, v_base;
+};
+static_assert(sizeof(BlockHdr) == 32, "header is 8 words");
+
+GALE_HD inline int64_t a4(int64_t x) { return (x + 3) & ~int64_t(3); }
+GALE_HD inline int64_t blk_words(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo) {
+    return 8 + a4(nv_loc) + a4(int64_t(n_ext) + n_halo) + a4(2 * (int64_t(n_ext) + n_own + n_halo));
+}
+GALE_HD inline int64_t blk_tmap_off(int32_t nv_loc) { return 8 + a4(nv_loc); }
+GALE_HD inline int64_t blk_rows_off(int32_t nv_loc, int32_t n_ext, int32_t n_halo) {
+    return 8 + a4(nv_loc) + a4(int64_t(n_ext) + n_halo);
+}
+
+// Largest local id space a block can address (uint16 local ids).
+constexpr int32_t kMaxLocal = 65535;
+
+// Per-cluster sizes (entries) found by the counting pass.
+enum { SZ_VT = 0, SZ_VV = 1, SZ_E = 2, SZ_ET = 3, SZ_TT = 4, SZ_N = 5 };
+
+// Relation mask bits (same values as the public GALE_* bits).
+enum : uint32_t { R_VT = 1u, R_VV = 2u, R_ET = 4u, R_TT = 8u };
+
+// One unit of kernel work: a cluster, which relations, where its block is,
+// and where each output array of this cluster starts (NULL = not built).
+struct WorkItem {
+    int32_t k;
+    uint32_t mask;
+    int64_t blk;  // word offset of the cluster's block
+    int32_t *vt_off, *vt_val, *vv_off, *vv_val;
+    int32_t *eu_off, *e_w, *et_off, *et_val;
+    int32_t *tt_off, *tt_val;
+};
+static_assert(sizeof(WorkItem) == 96, "work item is 96 bytes");
+
+// Per-cluster facts the host learns at load time, used for bins and bounds.
+struct ClusterStat {
+    int32_t n_ext, n_own, n_halo, nv_loc, nv_own;
+    int32_t n_vt;     // incidences of own vertices in [external | internal]
+    int32_t max_deg;  // largest VT row
+    int32_t pad;
+};
+
+// Capacities a launch is planned for (maxima over the clusters it serves).
+struct Caps {
+    int32_t blk_words;  // largest block
+    int32_t nv_own;     // largest own vertex count
+    int32_t n_vt;       // largest sum of VT rows
+    int32_t n_own;      // largest internal tet count
+    int32_t nv_loc;     // largest local vertex count
+    int32_t max_deg;    // largest VT row
+    int32_t max_up;     // bound on VV row length / upper edges per vertex
+    int32_t hcap;       // face hash capacity (power of two)
+};
+
+// Byte offsets of the shared-memory regions of one CTA (all 16-aligned).
+struct SmemPlan {
+    int32_t threads;
+    int32_t blk;        // block copy
+    int32_t vt_off;     // int32[nv_own+1]
+    int32_t cur;        // int32[nv_own] fill cursors
+    int32_t vt_list;    // uint16[n_vt]
+    int32_t scan;       // scan scratch
+    int32_t uni;        // phase-B masks / phase-C warp scratch
+    int32_t warp_words; // words of phase-C scratch per warp
+    int32_t hash;       // phase D: uint32[hcap]  (overlaps vt_off..)
+    int32_t nbr;        // phase D: uint32[4*n_own]
+    int32_t total;      // bytes
+    Caps caps;
+};
+
+// Device error word bits.
+enum : int32_t {
+    ERR_CAPACITY = 1,      // a cluster exceeded the capacities of its launch
+    ERR_NONMANIFOLD = 2,   // a triangle is shared by more than two tets
+    ERR_HASH_FULL = 4,     // face hash probe ran past its capacity
+    ERR_BAD_ITEM = 8,      // a work item referenced a bad cluster
+    ERR_TIMEOUT = 16,      // a bounded device wait ran out
+};
+
+SmemPlan plan_smem(const Caps &c, int threads);
+
+// Kernel launchers (gale_kernels.cu).  All asynchronous on `stream`.
+struct DevMesh {
+    const int32_t *blocks;      // all cluster blocks
+    const int64_t *blk_off;     // [K] word offset of each block
+    const int32_t *I_V;         // [K+1]
+    const int32_t *I_T;         // [K+1]
+    int32_t K;
+};
+
+int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
+                      int32_t *err, int32_t *ticket, int grid, void *stream);
+int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t *sizes, uint32_t mask,
+                 const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, void *stream);
+int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
+                 int32_t *err, int32_t *ticket, int grid, void *stream);
+int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,
+                     void *stream);
+int kernel_smem_limit();
+int max_ctas_per_sm(const SmemPlan &plan);
+void prepare_kernels(int threads, int smem);
+int device_sm_count();
+
+}  // namespace gale

@@ -1,0 +1,415 @@
+// Host-side initialisation (Section 4.3, "Initialization"): input checks,
+// canonical numbering, per-cluster working sets (internal tets, external
+// tets T_ex, face halo) and their packing into 16-bit local blocks.
+//
+// Everything here is O(nv + nt) work split over std::thread workers:
+// counting sorts instead of comparison sorts, and per-cluster work done
+// cluster-parallel.  The result is uploaded once and never changes.
+#include "gale_host.h"
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <mutex>
+#include <thread>
+
+namespace gale {
+
+namespace {
+
+template <class F>
+void parallel_for(int64_t n, int nthreads, F &&f) {
+    if (n <= 0) return;
+    int p = nthreads;
+    if (int64_t(p) > n) p = int(n);
+    if (p <= 1) {
+        f(int64_t(0), n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(p);
+    for (int i = 0; i < p; ++i) {
+        const int64_t b = n * i / p, e = n * (i + 1) / p;
+        th.emplace_back([&f, b, e, i] { f(b, e, i); });
+    }
+    for (auto &t : th) t.join();
+}
+
+// Work-stealing loop over [0, n) in small grains (uneven per-item cost).
+template <class F>
+void parallel_dynamic(int64_t n, int nthreads, int64_t grain, F &&f) {
+    if (n <= 0) return;
+    std::atomic<int64_t> next{0};
+    int p = nthreads;
+    if (int64_t(p) > (n + grain - 1) / grain) p = int((n + grain - 1) / grain);
+    auto body = [&](int tid) {
+        for (;;) {
+            int64_t b = next.fetch_add(grain);
+            if (b >= n) break;
+            int64_t e = std::min(n, b + grain);
+            for (int64_t i = b; i < e; ++i) f(i, tid);
+        }
+    };
+    if (p <= 1) {
+        body(0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int i = 0; i < p; ++i) th.emplace_back(body, i);
+    for (auto &t : th) t.join();
+}
+
+inline void sort4(int32_t *r) {
+    auto cs = [](int32_t &a, int32_t &b) {
+        if (b < a) std::swap(a, b);
+    };
+    cs(r[0], r[1]); cs(r[2], r[3]); cs(r[0], r[2]); cs(r[1], r[3]); cs(r[1], r[2]);
+}
+
+// Stable counting sort of items [0, n) by key(i) in [0, nkeys).  Writes
+// out[pos] = i and start[k] = first position of key k (start[nkeys] = n).
+template <class Key>
+void counting_sort(int64_t n, int32_t nkeys, int nthreads, Key key, int32_t *out, std::vector<int64_t> &start) {
+    int p = nthreads;
+    // per-chunk histograms: keep their memory bounded
+    while (p > 1 && int64_t(p) * nkeys > (int64_t(1) << 26)) p /= 2;
+    if (int64_t(p) > n) p = int(std::max<int64_t>(1, n));
+    std::vector<int64_t> hist(size_t(p) * nkeys, 0);
+    parallel_for(n, p, [&](int64_t b, int64_t e, int t) {
+        int64_t *h = hist.data() + size_t(t) * nkeys;
+        for (int64_t i = b; i < e; ++i) h[key(i)]++;
+    });
+    start.assign(size_t(nkeys) + 1, 0);
+    int64_t run = 0;
+    for (int32_t k = 0; k < nkeys; ++k) {
+        start[k] = run;
+        for (int t = 0; t < p; ++t) {
+            int64_t c = hist[size_t(t) * nkeys + k];
+            hist[size_t(t) * nkeys + k] = run;
+            run += c;
+        }
+    }
+    start[nkeys] = run;
+    parallel_for(n, p, [&](int64_t b, int64_t e, int t) {
+        int64_t *h = hist.data() + size_t(t) * nkeys;
+        for (int64_t i = b; i < e; ++i) out[h[key(i)]++] = int32_t(i);
+    });
+}
+
+}  // namespace
+
+int host_threads(int requested) {
+    if (requested > 0) return requested;
+    unsigned h = std::thread::hardware_concurrency();
+    return h ? int(h) : 1;
+}
+
+bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
+    using clk = std::chrono::steady_clock;
+    auto t0 = clk::now();
+    const int P = host_threads(d.host_threads);
+    const int64_t nv = d.nv, nt = d.nt;
+    const int32_t K = d.nclusters;
+    if (nv < 1 || nt < 0 || nv > INT32_MAX || nt > INT32_MAX - 1 || K < 1 || K > nv) {
+        err = "invalid sizes (need 1 <= nv < 2^31, 0 <= nt < 2^31, 1 <= nclusters <= nv)";
+        return false;
+    }
+    if (!d.seg || (nt > 0 && !d.tv)) {
+        err = "tv and seg must be non-NULL host pointers";
+        return false;
+    }
+    hm.nv = nv;
+    hm.nt = nt;
+    hm.K = K;
+    const int32_t *seg = d.seg, *tv = d.tv;
+
+    // ---- 1. input checks ----
+    std::atomic<int64_t> bad_v{-1}, bad_t{-1};
+    parallel_for(nv, P, [&](int64_t b, int64_t e, int) {
+        for (int64_t v = b; v < e; ++v)
+            if (seg[v] < 0 || seg[v] >= K) {
+                bad_v = v;
+                return;
+            }
+    });
+    if (bad_v >= 0) {
+        err = "segment id out of range at vertex " + std::to_string(bad_v.load());
+        return false;
+    }
+    parallel_for(nt, P, [&](int64_t b, int64_t e, int) {
+        for (int64_t t = b; t < e; ++t) {
+            int32_t r[4];
+            for (int j = 0; j < 4; ++j) {
+                r[j] = tv[4 * t + j];
+                if (r[j] < 0 || r[j] >= nv) {
+                    bad_t = t;
+                    return;
+                }
+            }
+            sort4(r);
+            if (r[0] == r[1] || r[1] == r[2] || r[2] == r[3]) {
+                bad_t = t;
+                return;
+            }
+        }
+    });
+    if (bad_t >= 0) {
+        err = "tet " + std::to_string(bad_t.load()) + " has a vertex id out of range or a repeated vertex";
+        return false;
+    }
+
+    // ---- 2. canonical vertex ids: stable by (segment, input id) ----
+    hm.vperm.resize(nv);
+    hm.cid.resize(nv);
+    std::vector<int64_t> start;
+    counting_sort(nv, K, P, [&](int64_t v) { return seg[v]; }, hm.vperm.data(), start);
+    hm.I_V.resize(size_t(K) + 1);
+    for (int32_t k = 0; k <= K; ++k) hm.I_V[k] = int32_t(start[k]);
+    parallel_for(nv, P, [&](int64_t b, int64_t e, int) {
+        for (int64_t c = b; c < e; ++c) hm.cid[hm.vperm[c]] = int32_t(c);
+    });
+    std::vector<int32_t> &cl = hm.cluster_of;  // canonical vertex -> cluster (nondecreasing)
+    cl.resize(nv);
+    parallel_for(nv, P, [&](int64_t b, int64_t e, int) {
+        for (int64_t c = b; c < e; ++c) cl[c] = seg[hm.vperm[c]];
+    });
+
+    // ---- 3. canonical tets: rows relabelled and sorted, owner = cluster
+    //         of the lowest vertex, stable by (owner, input index) ----
+    std::vector<int32_t> rows_in(size_t(4) * nt);
+    std::vector<int32_t> owner(nt);
+    parallel_for(nt, P, [&](int64_t b, int64_t e, int) {
+        for (int64_t t = b; t < e; ++t) {
+            int32_t *r = rows_in.data() + 4 * t;
+            for (int j = 0; j < 4; ++j) r[j] = hm.cid[tv[4 * t + j]];
+            sort4(r);
+            owner[t] = cl[r[0]];
+        }
+    });
+    hm.tperm.resize(nt);
+    counting_sort(nt, K, P, [&](int64_t t) { return owner[t]; }, hm.tperm.data(), start);
+    hm.I_T.resize(size_t(K) + 1);
+    for (int32_t k = 0; k <= K; ++k) hm.I_T[k] = int32_t(start[k]);
+    hm.rows.resize(size_t(4) * nt);
+    parallel_for(nt, P, [&](int64_t b, int64_t e, int) {
+        for (int64_t c = b; c < e; ++c) memcpy(&hm.rows[4 * c], &rows_in[4 * int64_t(hm.tperm[c])], 16);
+    });
+    std::vector<int32_t>().swap(rows_in);
+    std::vector<int32_t>().swap(owner);
+    const int32_t *rows = hm.rows.data();
+
+    // ---- 4. T_ex: a tet is external to every other cluster it touches.
+    //         Clusters along a sorted row are nondecreasing, so the distinct
+    //         ones are where consecutive entries differ. ----
+    {
+        // (cluster, tet) incidences, counted per tet
+        std::vector<int64_t> per(nt + 1, 0);
+        parallel_for(nt, P, [&](int64_t b, int64_t e, int) {
+            for (int64_t t = b; t < e; ++t) {
+                const int32_t *r = rows + 4 * t;
+                per[t + 1] = (cl[r[1]] != cl[r[0]]) + (cl[r[2]] != cl[r[1]]) + (cl[r[3]] != cl[r[2]]);
+            }
+        });
+        for (int64_t t = 0; t < nt; ++t) per[t + 1] += per[t];
+        const int64_t ninc = per[nt];
+        std::vector<int32_t> inc_c(ninc), inc_t(ninc);
+        parallel_for(nt, P, [&](int64_t b, int64_t e, int) {
+            for (int64_t t = b; t < e; ++t) {
+                const int32_t *r = rows + 4 * t;
+                int64_t p = per[t];
+                for (int j = 1; j < 4; ++j)
+                    if (cl[r[j]] != cl[r[j - 1]]) {
+                        inc_c[p] = cl[r[j]];
+                        inc_t[p] = int32_t(t);
+                        ++p;
+                    }
+            }
+        });
+        std::vector<int32_t> order(ninc);
+        counting_sort(ninc, K, P, [&](int64_t i) { return inc_c[i]; }, order.data(), start);
+        hm.ext_off.assign(start.begin(), start.end());
+        hm.ext.resize(ninc);
+        parallel_for(ninc, P, [&](int64_t b, int64_t e, int) {
+            for (int64_t i = b; i < e; ++i) hm.ext[i] = inc_t[order[i]];
+        });
+    }
+
+    // ---- 5. halo: tets outside T_k across the face (b, c, d) of an internal
+    //         tet (a, b, c, d) whose only vertex in k is a ----
+    hm.halo_off.assign(size_t(K) + 1, 0);
+    hm.halo.clear();
+    const bool want_tt = (d.precondition_mask & 8u) != 0;
+    if (want_tt && nt > 0) {
+        // vertex stars over canonical tets (ascending)
+        std::vector<int32_t> order(size_t(4) * nt);
+        counting_sort(4 * nt, int32_t(nv), P, [&](int64_t i) { return rows[i]; }, order.data(), start);
+        std::vector<int64_t> &vs_off = start;  // star of c: order[vs_off[c] .. vs_off[c+1]) / 4
+        std::vector<std::vector<int32_t>> halo_k(K);
+        parallel_dynamic(K, P, 16, [&](int64_t k, int) {
+            std::vector<int32_t> &hk = halo_k[k];
+            for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t) {
+                const int32_t *r = rows + 4 * int64_t(t);
+                if (cl[r[1]] == int32_t(k)) continue;  // face bcd has a vertex in k
+                const int32_t b = r[1], c = r[2], dd = r[3];
+                for (int64_t q = vs_off[b]; q < vs_off[b + 1]; ++q) {
+                    const int32_t u = order[q] >> 2;
+                    if (u == t) continue;
+                    const int32_t *ru = rows + 4 * int64_t(u);
+                    bool hc = false, hd = false, ink = false;
+                    for (int j = 0; j < 4; ++j) {
+                        hc |= ru[j] == c;
+                        hd |= ru[j] == dd;
+                        ink |= cl[ru[j]] == int32_t(k);
+                    }
+                    if (hc && hd && !ink) hk.push_back(u);
+                }
+            }
+            std::sort(hk.begin(), hk.end());
+            hk.erase(std::unique(hk.begin(), hk.end()), hk.end());
+        });
+        int64_t run = 0;
+        for (int32_t k = 0; k < K; ++k) {
+            hm.halo_off[k] = run;
+            run += int64_t(halo_k[k].size());
+        }
+        hm.halo_off[K] = run;
+        hm.halo.resize(run);
+        parallel_for(K, P, [&](int64_t b, int64_t e, int) {
+            for (int64_t k = b; k < e; ++k)
+                std::copy(halo_k[k].begin(), halo_k[k].end(), hm.halo.begin() + hm.halo_off[k]);
+        });
+    }
+
+    // ---- 6. per-cluster blocks ----
+    hm.stats.assign(K, ClusterStat{});
+    std::vector<std::vector<int32_t>> vmaps(K);
+    std::atomic<int64_t> bad_k{-1};
+    std::atomic<int64_t> dup_k{-1};
+    parallel_dynamic(K, P, 16, [&](int64_t k, int) {
+        const int32_t v0 = hm.I_V[k], v1 = hm.I_V[k + 1];
+        const int64_t e0 = hm.ext_off[k], e1 = hm.ext_off[k + 1];
+        const int64_t h0 = hm.halo_off[k], h1 = hm.halo_off[k + 1];
+        const int32_t t0 = hm.I_T[k], t1 = hm.I_T[k + 1];
+        std::vector<int32_t> &vm = vmaps[k];
+        vm.clear();
+        auto add_row = [&](int32_t t) {
+            const int32_t *r = rows + 4 * int64_t(t);
+            for (int j = 0; j < 4; ++j)
+                if (r[j] < v0 || r[j] >= v1) vm.push_back(r[j]);
+        };
+        for (int64_t i = e0; i < e1; ++i) add_row(hm.ext[i]);
+        for (int32_t t = t0; t < t1; ++t) add_row(t);
+        for (int64_t i = h0; i < h1; ++i) add_row(hm.halo[i]);
+        std::sort(vm.begin(), vm.end());
+        vm.erase(std::unique(vm.begin(), vm.end()), vm.end());
+        // insert the own interval in place
+        const int64_t below = std::lower_bound(vm.begin(), vm.end(), v0) - vm.begin();
+        std::vector<int32_t> full;
+        full.reserve(vm.size() + (v1 - v0));
+        full.insert(full.end(), vm.begin(), vm.begin() + below);
+        for (int32_t v = v0; v < v1; ++v) full.push_back(v);
+        full.insert(full.end(), vm.begin() + below, vm.end());
+        vm.swap(full);
+        ClusterStat &s = hm.stats[k];
+        s.n_ext = int32_t(e1 - e0);
+        s.n_own = t1 - t0;
+        s.n_halo = int32_t(h1 - h0);
+        s.nv_loc = int32_t(vm.size());
+        s.nv_own = v1 - v0;
+        const int64_t ntot = int64_t(s.n_ext) + s.n_own + s.n_halo;
+        if (int64_t(vm.size()) > kMaxLocal || ntot > kMaxLocal - 1) {
+            bad_k = k;
+            return;
+        }
+        // degrees of own vertices over [external | internal]
+        std::vector<int32_t> deg(size_t(v1 - v0), 0);
+        auto count_row = [&](int32_t t) {
+            const int32_t *r = rows + 4 * int64_t(t);
+            for (int j = 0; j < 4; ++j)
+                if (r[j] >= v0 && r[j] < v1) deg[r[j] - v0]++;
+        };
+        for (int64_t i = e0; i < e1; ++i) count_row(hm.ext[i]);
+        for (int32_t t = t0; t < t1; ++t) count_row(t);
+        int32_t nvt = 0, mx = 0;
+        for (int32_t x : deg) {
+            nvt += x;
+            mx = std::max(mx, x);
+        }
+        s.n_vt = nvt;
+        s.max_deg = mx;
+        // two tets with the same vertex set have the same owner
+        if (t1 - t0 > 1) {
+            std::vector<std::array<int32_t, 4>> own(size_t(t1 - t0));
+            for (int32_t t = t0; t < t1; ++t) memcpy(own[t - t0].data(), rows + 4 * int64_t(t), 16);
+            std::sort(own.begin(), own.end());
+            for (size_t i = 1; i < own.size(); ++i)
+                if (own[i] == own[i - 1]) {
+                    dup_k = k;
+                    return;
+                }
+        }
+    });
+    if (dup_k >= 0) {
+        err = "two tets have the same vertex set (cluster " + std::to_string(dup_k.load()) + ")";
+        return false;
+    }
+    if (bad_k >= 0) {
+        err = "cluster " + std::to_string(bad_k.load()) +
+              " has a working set larger than 65535 local vertices or 65534 tets; use smaller clusters";
+        return false;
+    }
+    hm.blk_off.assign(size_t(K) + 1, 0);
+    int64_t run = 0;
+    hm.ext_total = 0;
+    hm.halo_total = 0;
+    for (int32_t k = 0; k < K; ++k) {
+        const ClusterStat &s = hm.stats[k];
+        hm.blk_off[k] = run;
+        run += blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo);
+        hm.ext_total += s.n_ext;
+        hm.halo_total += s.n_halo;
+    }
+    hm.blk_off[K] = run;
+    hm.blocks_words = run;
+    if (!hm.alloc_blocks(run)) {
+        err = "host allocation of the cluster blocks failed";
+        return false;
+    }
+    int32_t *blocks = hm.blocks;
+    parallel_dynamic(K, P, 16, [&](int64_t k, int) {
+        const ClusterStat &s = hm.stats[k];
+        const std::vector<int32_t> &vm = vmaps[k];
+        int32_t *blk = blocks + hm.blk_off[k];
+        const int64_t words = hm.blk_off[k + 1] - hm.blk_off[k];
+        memset(blk, 0, size_t(words) * 4);
+        const int32_t v0 = hm.I_V[k];
+        const int32_t own_lo = int32_t(std::lower_bound(vm.begin(), vm.end(), v0) - vm.begin());
+        BlockHdr hdr{s.n_ext, s.n_own, s.n_halo, s.nv_loc, own_lo, s.nv_own, hm.I_T[k], v0};
+        memcpy(blk, &hdr, sizeof(hdr));
+        memcpy(blk + 8, vm.data(), vm.size() * 4);
+        int32_t *tmap = blk + blk_tmap_off(s.nv_loc);
+        const int64_t e0 = hm.ext_off[k], h0 = hm.halo_off[k];
+        for (int32_t i = 0; i < s.n_ext; ++i) tmap[i] = hm.ext[e0 + i];
+        for (int32_t i = 0; i < s.n_halo; ++i) tmap[s.n_ext + i] = hm.halo[h0 + i];
+        uint16_t *lrows = reinterpret_cast<uint16_t *>(blk + blk_rows_off(s.nv_loc, s.n_ext, s.n_halo));
+        auto local = [&](int32_t v) -> uint16_t {
+            if (v >= v0 && v < v0 + s.nv_own) return uint16_t(own_lo + (v - v0));
+            return uint16_t(std::lower_bound(vm.begin(), vm.end(), v) - vm.begin());
+        };
+        int64_t li = 0;
+        auto put = [&](int32_t t) {
+            const int32_t *r = rows + 4 * int64_t(t);
+            for (int j = 0; j < 4; ++j) lrows[4 * li + j] = local(r[j]);
+            ++li;
+        };
+        for (int32_t i = 0; i < s.n_ext; ++i) put(hm.ext[e0 + i]);
+        for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t) put(t);
+        for (int32_t i = 0; i < s.n_halo; ++i) put(hm.halo[h0 + i]);
+    });
+    hm.host_seconds = std::chrono::duration<double>(clk::now() - t0).count();
+    return true;
+}
+
+}  // namespace gale

@@ -1,0 +1,137 @@
+"""Bit-exact parity of the CUDA producer with the CPU oracle, through the C
+ABI.  Everything is integer indexing, so the tolerance is zero: every offset
+and every id of every relation of every cluster must match."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_2507_15230_gb300 as gale
+from parity_util import assert_bulk_equal, expected_bulk
+
+pytestmark = pytest.mark.gpu
+
+MASKS = [gale.ALL, gale.VT, gale.VV, gale.ET, gale.TT, gale.VT | gale.VV | gale.TT, gale.VV | gale.ET]
+
+
+@pytest.fixture(scope="module")
+def small():
+    m = gen.small_grid()
+    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
+    ctx = gale.Context.load(m, device=0)
+    yield m, canon, rel, ctx
+    ctx.close()
+
+
+def test_sizes_match_oracle(small):
+    m, canon, rel, ctx = small
+    _, _, sizes = ctx.intervals()
+    assert np.array_equal(sizes, oracle.cluster_sizes(rel, canon))
+
+
+@pytest.mark.parametrize("mode", [gale.MODE_BATCHED, gale.MODE_PER_CLUSTER])
+@pytest.mark.parametrize("mask", MASKS)
+def test_small_all_clusters(small, mode, mask):
+    m, canon, rel, ctx = small
+    ctx.build(None, mask, mode)
+    ctx.synchronize()
+    got = ctx.export(mask)
+    assert_bulk_equal(got, expected_bulk(rel, canon, range(m.nclusters), mask))
+
+
+def test_small_subset_and_repeat(small):
+    m, canon, rel, ctx = small
+    rng = np.random.default_rng(3)
+    ids = rng.permutation(m.nclusters)[:37]
+    for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+        ctx.build(ids, gale.ALL, mode)
+        ctx.synchronize()
+        assert_bulk_equal(ctx.export(gale.ALL), expected_bulk(rel, canon, ids))
+    # graph replay of the full build, twice, bit-identical
+    ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+    ctx.synchronize()
+    a = ctx.export(gale.ALL)
+    ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+    ctx.synchronize()
+    b = ctx.export(gale.ALL)
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+    assert_bulk_equal(a, expected_bulk(rel, canon, range(m.nclusters)))
+
+
+def test_views_match_oracle(small):
+    m, canon, rel, ctx = small
+    ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+    ctx.synchronize()
+    for k in (0, 1, 63, m.nclusters - 1):
+        v = ctx.bulk_view(k)
+        got = gale.view_to_numpy(v)
+        want = oracle.cluster_view(rel, canon, k)
+        assert v.v_begin == canon["I_V"][k] and v.t_begin == canon["I_T"][k]
+        for g, w in [("vt_off", "vt_off"), ("vt_val", "vt_val"), ("vv_val", "vv_val"), ("et_w", "e_w"),
+                     ("et_val", "et_val"), ("tt_off", "tt_off"), ("tt_val", "tt_val")]:
+            assert np.array_equal(got[g], want[w]), (k, g)
+
+
+def partition_cases():
+    cases = []
+    for n, K, seed in [(3, 1, 0), (4, 1, 1), (5, 3, 2), (6, 40, 3), (8, 200, 4), (10, 17, 5)]:
+        cases.append((n, K, seed))
+    return cases
+
+
+@pytest.mark.parametrize("case", partition_cases(), ids=lambda c: f"n{c[0]}-K{c[1]}")
+def test_random_partitions(case):
+    """Random segment ids (clusters that are not spatially compact, clusters
+    owning no tets, one cluster for everything)."""
+    n, K, seed = case
+    xyz, tv = gen.freudenthal_grid(n, permute=True, seed=seed + 20)
+    nv = xyz.shape[0]
+    rng = np.random.default_rng(seed)
+    seg = rng.integers(0, K, nv).astype(np.int32)
+    m = gen.Mesh(xyz, tv, seg, K)
+    canon, rel = oracle.build_all(nv, tv, seg, K)
+    with gale.Context.load(m, device=0) as ctx:
+        _, _, sizes = ctx.intervals()
+        assert np.array_equal(sizes, oracle.cluster_sizes(rel, canon))
+        for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+            ctx.build(None, gale.ALL, mode)
+            ctx.synchronize()
+            assert_bulk_equal(ctx.export(gale.ALL), expected_bulk(rel, canon, range(K)))
+
+
+def test_empty_clusters_and_tiny_mesh():
+    """Segments with no vertices, a segment with a single isolated vertex,
+    a mesh of one tet."""
+    tv = np.array([[0, 1, 2, 3]], np.int32)
+    seg = np.array([0, 2, 2, 4, 4], np.int32)  # vertex 4 is isolated; clusters 1 and 3 empty
+    m = gen.Mesh(None, tv, seg, 5)
+    canon, rel = oracle.build_all(5, tv, seg, 5)
+    with gale.Context.load(m, device=0) as ctx:
+        for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+            ctx.build(None, gale.ALL, mode)
+            ctx.synchronize()
+            assert_bulk_equal(ctx.export(gale.ALL), expected_bulk(rel, canon, range(5)))
+
+
+def test_paper_examples():
+    """The worked examples of Sections 2.2 and 4.3 through the GPU path."""
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "mesh_input_example.json")))
+    tv, seg = np.array(g["tv"], np.int32), np.array(g["seg"], np.int32)
+    m = gen.Mesh(None, tv, seg, g["nclusters"])
+    with gale.Context.load(m, device=0) as ctx:
+        _, _, sizes = ctx.intervals()
+        assert [0] + np.cumsum(sizes[:, 2]).tolist() == g["expect"]["I_E"]
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "vv_two_tets.json")))
+    tv, seg = np.array(g["tv"], np.int32), np.array(g["seg"], np.int32)
+    m = gen.Mesh(None, tv, seg, 1)
+    with gale.Context.load(m, device=0) as ctx:
+        ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+        ctx.synchronize()
+        out = ctx.export(gale.ALL)
+        vp, _ = ctx.permutations()
+        cid = np.argsort(vp)
+        c0 = cid[0]
+        vv = out["vv_val"][out["vv_off"][c0]:out["vv_off"][c0 + 1]]
+        assert sorted(vp[vv].tolist()) == g["expect"]["VV"]["0"]
