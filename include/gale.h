@@ -240,10 +240,16 @@ gale_status gale_get_working_set(gale_ctx *ctx, int32_t k, int32_t *ext, int64_t
 
 gale_status gale_get_info(gale_ctx *ctx, gale_info *out);
 
-/* Tuning: threads per block of the batched kernels (128, 256 or 512; 0 =
- * the autotuned or default value) and CTAs per SM of the persistent grid
- * (0 = as many as fit). */
+/* Tuning: threads per block of the producer kernels (a multiple of 32 in
+ * [64, 1024]; 0 = one thread per own vertex of the largest cluster of each
+ * size bin) and CTAs per SM of the persistent grid (0 = as many as fit). */
 gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
+
+/* Size bins of the batched form: for each bin (up to max_bins) five int32
+ * values - clusters, threads per CTA, dynamic shared bytes per CTA, CTAs per
+ * SM, persistent grid size - into out[5*i .. 5*i+4].  Returns the number of
+ * bins in *nbins. */
+gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t *nbins);
 
 /* Autotune the batched form on a sample of clusters; stores the choice in
  * the context. */

@@ -71,7 +71,7 @@ class ServeStats(ctypes.Structure):
 EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
            "gale_bulk_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
-           "gale_autotune", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
+           "gale_autotune", "gale_get_bins", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
 
 _lib = None
 
@@ -106,6 +106,7 @@ def load_library(build: bool = True):
     lib.gale_get_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.gale_set_tuning.argtypes = [P, i32, i32]
     lib.gale_autotune.argtypes = [P, u32]
+    lib.gale_get_bins.argtypes = [P, P, i32, ctypes.POINTER(i32)]
     lib.gale_stream.argtypes = [P]
     lib.gale_stream.restype = P
     lib.gale_last_launch_count.argtypes = [P]
@@ -341,6 +342,15 @@ class Context:
         halo = np.empty(max(nh.value, 1), np.int32)
         _check(self._lib.gale_get_working_set(self._h, k, _p(ext), ctypes.byref(ne), _p(halo), ctypes.byref(nh)))
         return ext[:ne.value], halo[:nh.value]
+
+    def bins(self) -> list:
+        """Size bins: dicts of clusters, threads, smem bytes, CTAs per SM, grid."""
+        n = ctypes.c_int32(0)
+        _check(self._lib.gale_get_bins(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros(5 * max(n.value, 1), np.int32)
+        _check(self._lib.gale_get_bins(self._h, _p(out), n.value, ctypes.byref(n)))
+        keys = ("clusters", "threads", "smem", "ctas_per_sm", "grid")
+        return [dict(zip(keys, out[5 * i:5 * i + 5].tolist())) for i in range(n.value)]
 
     def set_tuning(self, threads: int = 0, ctas_per_sm: int = 0):
         _check(self._lib.gale_set_tuning(self._h, threads, ctas_per_sm))

@@ -45,16 +45,26 @@ int64_t next_pow2(int64_t x) {
     return p;
 }
 
-gale::Caps caps_of(const gale::ClusterStat &s) {
+// Capacities of one cluster; staging capacities come from the exact sizes
+// of the counting pass (sizes == nullptr: a counting plan, no staging).
+gale::Caps caps_of(const gale::ClusterStat &s, const int64_t *sizes) {
     gale::Caps c{};
     c.blk_words = int32_t(gale::blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo));
     c.nv_own = s.nv_own;
     c.n_vt = s.n_vt;
     c.n_own = s.n_own;
     c.nv_loc = s.nv_loc;
+    c.nv_nb = s.nv_nb;
     c.max_deg = s.max_deg;
-    c.max_up = std::max(1, std::min(3 * s.max_deg, s.nv_loc - 1));
-    c.hcap = int32_t(std::max<int64_t>(64, next_pow2(4 * int64_t(s.n_own) + 1)));
+    c.max_up = s.max_up;
+    c.max_e = s.n_e;
+    if (sizes) {
+        c.max_vv = int32_t(sizes[1]);
+        c.max_e = int32_t(sizes[2]);
+        c.max_etv = int32_t(sizes[3]);
+        c.max_tt = int32_t(sizes[4]);
+    }
+    c.hcap = int32_t(std::max<int64_t>(64, next_pow2(2 * int64_t(s.n_bnd) + 1)));
     return c;
 }
 
@@ -65,41 +75,59 @@ gale::Caps merge(const gale::Caps &a, const gale::Caps &b) {
     c.n_vt = std::max(a.n_vt, b.n_vt);
     c.n_own = std::max(a.n_own, b.n_own);
     c.nv_loc = std::max(a.nv_loc, b.nv_loc);
+    c.nv_nb = std::max(a.nv_nb, b.nv_nb);
     c.max_deg = std::max(a.max_deg, b.max_deg);
+    c.max_vv = std::max(a.max_vv, b.max_vv);
+    c.max_e = std::max(a.max_e, b.max_e);
+    c.max_etv = std::max(a.max_etv, b.max_etv);
+    c.max_tt = std::max(a.max_tt, b.max_tt);
     c.max_up = std::max(a.max_up, b.max_up);
     c.hcap = std::max(a.hcap, b.hcap);
     return c;
 }
 
+// Block size for a cluster: one thread per own vertex, a warp multiple in
+// [64, 1024] (a tuning override applies when set).
+int threads_for(const gale_ctx *ctx, int32_t nv_own) {
+    if (ctx->threads_override > 0) return ctx->threads_override;
+    int t = (nv_own + 31) / 32 * 32;
+    return std::min(1024, std::max(64, t));
+}
+
 // Size bins: clusters sorted by shared-memory need, cut where the merged
 // plan would cross the next occupancy tier (4, 3, 2, 1 CTAs per SM).
-gale_status plan_bins(gale_ctx *ctx) {
+gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     const int32_t K = ctx->hm.K;
     const int smem_cta = gale::kernel_smem_limit();
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
-    std::vector<int32_t> need(K);
-    for (int32_t k = 0; k < K; ++k) need[k] = gale::plan_smem(caps_of(ctx->hm.stats[k]), ctx->threads).total;
+    auto caps_k = [&](int32_t k) {
+        return caps_of(ctx->hm.stats[k], with_sizes ? ctx->sizes.data() + size_t(5) * k : nullptr);
+    };
+    std::vector<int32_t> need(K), thr(K);
+    for (int32_t k = 0; k < K; ++k) {
+        thr[k] = threads_for(ctx, ctx->hm.stats[k].nv_own);
+        need[k] = gale::plan_smem(caps_k(k), thr[k]).total;
+    }
     std::vector<int32_t> idx(K);
     std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return need[a] < need[b]; });
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+        return thr[a] != thr[b] ? thr[a] < thr[b] : need[a] < need[b];
+    });
     std::vector<int> tiers;
-    for (int per = 4; per >= 1; --per) {
-        int t = smem_sm / per - 1024 * per;  // leave room for static smem and reservation
-        tiers.push_back(std::min(t, smem_cta));
-    }
+    for (int per = 4; per >= 1; --per) tiers.push_back(std::min(smem_sm / per - 1024 * per, smem_cta));
     ctx->bins.clear();
     ctx->bin_of.assign(K, -1);
     size_t tier = 0;
+    int cur_thr = 0;
     gale::Caps cur{};
     std::vector<int32_t> members;
     auto close = [&]() {
         if (members.empty()) return;
         gale::Bin b;
-        b.plan = gale::plan_smem(cur, ctx->threads);
-        // largest working sets first
+        b.plan = gale::plan_smem(cur, cur_thr);
         std::stable_sort(members.begin(), members.end(),
-                         [&](int32_t a, int32_t c) { return need[a] > need[c]; });
+                         [&](int32_t a, int32_t c) { return need[a] > need[c]; });  // largest first
         b.clusters = members;
         for (int32_t k : members) ctx->bin_of[k] = int32_t(ctx->bins.size());
         ctx->bins.push_back(std::move(b));
@@ -107,28 +135,39 @@ gale_status plan_bins(gale_ctx *ctx) {
         cur = gale::Caps{};
     };
     for (int32_t k : idx) {
+        if (ctx->hm.stats[k].max_up > 255)
+            return fail(GALE_EINVAL, "cluster " + std::to_string(k) +
+                                         " has a vertex with more than 255 upper neighbours (unsupported)");
         if (need[k] > smem_cta)
             return fail(GALE_EINVAL, "cluster " + std::to_string(k) + " needs " + std::to_string(need[k]) +
                                          " bytes of shared memory (limit " + std::to_string(smem_cta) +
                                          "); use smaller clusters");
-        gale::Caps m = members.empty() ? caps_of(ctx->hm.stats[k]) : merge(cur, caps_of(ctx->hm.stats[k]));
-        int tot = gale::plan_smem(m, ctx->threads).total;
+        if (!members.empty() && thr[k] != cur_thr) {
+            close();
+            tier = 0;
+        }
+        cur_thr = thr[k];
+        gale::Caps m = members.empty() ? caps_k(k) : merge(cur, caps_k(k));
+        int tot = gale::plan_smem(m, cur_thr).total;
         while (tier < tiers.size() && tot > tiers[tier]) {
             close();
             ++tier;
-            m = caps_of(ctx->hm.stats[k]);
-            tot = gale::plan_smem(m, ctx->threads).total;
+            m = caps_k(k);
+            tot = gale::plan_smem(m, cur_thr).total;
         }
         if (tier >= tiers.size()) tier = tiers.size() - 1;
         cur = m;
         members.push_back(k);
     }
     close();
+    int max_total = 0;
+    for (auto &b : ctx->bins) max_total = std::max(max_total, b.plan.total);
+    gale::prepare_kernels(max_total);
     for (auto &b : ctx->bins) {
-        gale::prepare_kernels(b.plan.threads, b.plan.total);
         int per_sm = gale::max_ctas_per_sm(b.plan);
         if (per_sm < 1) return fail(GALE_EINVAL, "a size bin cannot be launched (shared memory or registers)");
         if (ctx->ctas_override > 0) per_sm = std::min(per_sm, ctx->ctas_override);
+        b.ctas_per_sm = per_sm;
         b.grid = std::max(1, std::min<int>(int(b.clusters.size()), per_sm * ctx->sm_count));
     }
     return GALE_OK;
@@ -370,9 +409,12 @@ gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out) {
     CUDA_TRY(cudaMemcpyAsync(ctx->d_I_T, hm.I_T.data(), sizeof(int32_t) * (K + 1), cudaMemcpyHostToDevice,
                              ctx->stream));
     CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 64, ctx->stream));
-    gale_status st = plan_bins(ctx.get());
+    gale_status st = plan_bins(ctx.get(), false);
     if (st == GALE_OK) st = upload_orders(ctx.get());
     if (st == GALE_OK) st = count_pass(ctx.get());
+    // build plans: staging capacities from the exact sizes
+    if (st == GALE_OK) st = plan_bins(ctx.get(), true);
+    if (st == GALE_OK) st = upload_orders(ctx.get());
     if (st != GALE_OK) {
         std::string keep = gale::t_error;
         gale_destroy(ctx.release());
@@ -630,15 +672,15 @@ gale_status gale_get_info(gale_ctx *ctx, gale_info *out) {
 
 gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm) {
     if (!ctx) return fail(GALE_EINVAL, "NULL context");
-    if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
-        return fail(GALE_EINVAL, "threads must be 0, 128, 256 or 512");
+    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32 != 0))
+        return fail(GALE_EINVAL, "threads must be 0 or a multiple of 32 in [64, 1024]");
     if (ctx->device < 0) return GALE_OK;
     std::lock_guard<std::mutex> lock(ctx->mu);
     CUDA_TRY(cudaSetDevice(ctx->device));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    ctx->threads = threads ? threads : 256;
+    ctx->threads_override = threads;
     ctx->ctas_override = ctas_per_sm;
-    gale_status st = plan_bins(ctx);
+    gale_status st = plan_bins(ctx, true);
     if (st != GALE_OK) return st;
     st = upload_orders(ctx);
     for (auto &g : ctx->graphs)
@@ -647,6 +689,20 @@ gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm)
             g = nullptr;
         }
     return st;
+}
+
+gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t *nbins) {
+    if (!ctx || !nbins) return fail(GALE_EINVAL, "NULL argument");
+    *nbins = int32_t(ctx->bins.size());
+    for (int32_t b = 0; b < *nbins && b < max_bins && out; ++b) {
+        const gale::Bin &bin = ctx->bins[b];
+        out[5 * b + 0] = int32_t(bin.clusters.size());
+        out[5 * b + 1] = bin.plan.threads;
+        out[5 * b + 2] = bin.plan.total;
+        out[5 * b + 3] = bin.ctas_per_sm;
+        out[5 * b + 4] = bin.grid;
+    }
+    return GALE_OK;
 }
 
 void *gale_stream(gale_ctx *ctx) { return ctx ? static_cast<void *>(ctx->stream) : nullptr; }

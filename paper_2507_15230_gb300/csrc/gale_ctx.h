@@ -19,6 +19,7 @@ struct Bin {
     SmemPlan plan;
     std::vector<int32_t> clusters;  // members, largest working set first
     int grid = 0;                   // persistent CTAs
+    int ctas_per_sm = 0;
 };
 
 struct DevAlloc {
@@ -62,7 +63,7 @@ struct gale_ctx {
     std::vector<gale::Bin> bins;
     std::vector<int32_t> bin_of;        // [K]
     std::vector<int64_t> order_all_off; // [nbins+1] offsets into d_order_all
-    int threads = 256;
+    int threads_override = 0;  // 0: one thread per own vertex
     int ctas_override = 0;
     int sm_count = 0;
 

@@ -19,8 +19,8 @@ namespace gale {
 // a multiple of 4 words so the block can be moved with 16-byte vector loads
 // or one bulk copy.
 //
-//   [0, 8)                header (BlockHdr)
-//   [8, 8 + a4(nv_loc))   vmap: canonical id of each local vertex, ascending
+//   [0, 12)               header (BlockHdr)
+//   [12, 12 + a4(nv_loc)) vmap: canonical id of each local vertex
 //   next a4(n_ext+n_halo) tmap: canonical ids of the external tets (ascending,
 //                         all below the cluster's first internal tet) then of
 //                         the halo tets (ascending)
@@ -28,28 +28,33 @@ namespace gale {
 //                         within the row), tets in local order
 //                         [external | internal | halo]
 //
-// Local vertex ids are ranks in vmap, so local order equals canonical order;
-// the cluster's own vertices are the local interval [own_lo, own_lo+nv_own)
-// and canonical interval [v_base, v_base+nv_own).  Local tet i maps to
+// Local vertex ids [0, nv_nb) are the vertices of the external and internal
+// tets in canonical order (so local order equals canonical order there);
+// they include the cluster's own vertices as the interval
+// [own_lo, own_lo + nv_own) = canonical [v_base, v_base + nv_own).  Ids
+// [nv_nb, nv_loc) are vertices that only halo tets use.  Local tet i maps to
 //   i <  n_ext                tmap[i]
 //   i <  n_ext + n_own        t_base + (i - n_ext)
 //   otherwise                 tmap[i - n_own]
 // and since external tets precede the internal ones in canonical order, the
-// local order of [external | internal] is canonical order too.
+// local order of [external | internal] is canonical order too.  n_bnd counts
+// the internal tets (a, b, c, d) whose face (b, c, d) has no own vertex.
 // ---------------------------------------------------------------------------
 struct BlockHdr {
     int32_t n_ext, n_own, n_halo, nv_loc;
     int32_t own_lo, nv_own, t_base, v_base;
+    int32_t nv_nb, n_bnd, pad0, pad1;
 };
-static_assert(sizeof(BlockHdr) == 32, "header is 8 words");
+static_assert(sizeof(BlockHdr) == 48, "header is 12 words");
+constexpr int kHdrWords = 12;
 
 GALE_HD inline int64_t a4(int64_t x) { return (x + 3) & ~int64_t(3); }
 GALE_HD inline int64_t blk_words(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo) {
-    return 8 + a4(nv_loc) + a4(int64_t(n_ext) + n_halo) + a4(2 * (int64_t(n_ext) + n_own + n_halo));
+    return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo) + a4(2 * (int64_t(n_ext) + n_own + n_halo));
 }
-GALE_HD inline int64_t blk_tmap_off(int32_t nv_loc) { return 8 + a4(nv_loc); }
+GALE_HD inline int64_t blk_tmap_off(int32_t nv_loc) { return kHdrWords + a4(nv_loc); }
 GALE_HD inline int64_t blk_rows_off(int32_t nv_loc, int32_t n_ext, int32_t n_halo) {
-    return 8 + a4(nv_loc) + a4(int64_t(n_ext) + n_halo);
+    return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo);
 }
 
 // Largest local id space a block can address (uint16 local ids).
@@ -78,6 +83,10 @@ struct ClusterStat {
     int32_t n_ext, n_own, n_halo, nv_loc, nv_own;
     int32_t n_vt;     // incidences of own vertices in [external | internal]
     int32_t max_deg;  // largest VT row
+    int32_t nv_nb;    // local vertices of the external and internal tets
+    int32_t n_bnd;    // internal tets whose face opposite their lowest vertex has no own vertex
+    int32_t max_up;   // most distinct upper neighbours of an own vertex
+    int32_t n_e;      // edges whose lower endpoint is an own vertex
     int32_t pad;
 };
 
@@ -88,23 +97,40 @@ struct Caps {
     int32_t n_vt;       // largest sum of VT rows
     int32_t n_own;      // largest internal tet count
     int32_t nv_loc;     // largest local vertex count
+    int32_t nv_nb;      // largest neighbour-universe size (bitmap bits)
     int32_t max_deg;    // largest VT row
-    int32_t max_up;     // bound on VV row length / upper edges per vertex
-    int32_t hcap;       // face hash capacity (power of two)
+    int32_t max_vv;     // largest sum of VV rows   (0 in counting plans)
+    int32_t max_e;      // largest owned edge count (0 in counting plans)
+    int32_t max_etv;    // largest sum of ET rows   (0 in counting plans)
+    int32_t max_tt;     // largest sum of TT rows   (0 in counting plans)
+    int32_t max_up;     // most upper neighbours of an own vertex (edge masks)
+    int32_t hcap;       // boundary-face hash capacity (power of two)
 };
 
 // Byte offsets of the shared-memory regions of one CTA (all 16-aligned).
+// Phase D (TT) overlays hash, tcnt and st_tt on everything from vt_off on;
+// cnt and nbr stay.
 struct SmemPlan {
     int32_t threads;
+    int32_t wp;         // words per vertex bitmap (odd, for bank spread)
+    int32_t nch;        // 32-tet chunks of the longest VT row
+    int32_t pad;
     int32_t blk;        // block copy
-    int32_t vt_off;     // int32[nv_own+1]
-    int32_t cur;        // int32[nv_own] fill cursors
-    int32_t vt_list;    // uint16[n_vt]
     int32_t scan;       // scan scratch
-    int32_t uni;        // phase-B masks / phase-C warp scratch
-    int32_t warp_words; // words of phase-C scratch per warp
-    int32_t hash;       // phase D: uint32[hcap]  (overlaps vt_off..)
-    int32_t nbr;        // phase D: uint32[4*n_own]
+    int32_t cnt;        // int32[3*nv_own] per-vertex counts
+    int32_t nbr;        // uint16[4*n_own] TT links (phases C and D)
+    int32_t vt_off;     // int32[nv_own+1]
+    int32_t vt_list;    // uint16[n_vt]
+    int32_t bmap;       // B: uint32[2*nwarp*nv_own] counters and masks;
+                        // C: uint32[nv_own*wp] bitmaps + pre, then uint16[max_etv] ET staging
+    int32_t pre;        // uint8[nv_own*wp] rank prefix per bitmap word
+    int32_t st_ew;      // uint16[max_e] upper endpoints of the owned edges
+    int32_t emask;      // uint16[max_vv] VV staging, then uint32[max_e*nch]
+                        // per-edge tet masks, then ET offsets
+    int32_t st_v;       // = emask (VV staging)
+    int32_t hash;       // uint32[hcap] boundary faces (phase D)
+    int32_t tcnt;       // int32[n_own+1] TT counts (phase D)
+    int32_t st_tt;      // int32[max_tt] TT staging (phase D)
     int32_t total;      // bytes
     Caps caps;
 };
@@ -129,17 +155,20 @@ struct DevMesh {
     int32_t K;
 };
 
+// Persistent launch over n clusters: ids[i] (count pass) or items[order[i]]
+// (build).  One CTA per cluster at a time.
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
                       int32_t *err, int32_t *ticket, int grid, void *stream);
 int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t *sizes, uint32_t mask,
                  const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, void *stream);
 int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
                  int32_t *err, int32_t *ticket, int grid, void *stream);
+// One launch, one CTA, one work item (the per-cluster baseline form).
 int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,
                      void *stream);
 int kernel_smem_limit();
 int max_ctas_per_sm(const SmemPlan &plan);
-void prepare_kernels(int threads, int smem);
+void prepare_kernels(int smem);
 int device_sm_count();
 
 }  // namespace gale

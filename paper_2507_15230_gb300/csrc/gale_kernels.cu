@@ -1,43 +1,46 @@
 // Producer kernels: per-cluster VT, VV, ET and TT as canonical sorted CSR.
 //
 // One CTA builds one cluster at a time (persistent CTAs take clusters from a
-// ticket counter).  The cluster's working set - its internal tets, its
-// external tets T_ex and its face halo (Section 4.3, "Initialization"),
-// stored as 16-bit local rows - is copied into shared memory, and every
-// relation is built there:
+// ticket counter; the per-cluster baseline launches one CTA per cluster).
+// The cluster's working set - its internal tets, its external tets T_ex and
+// its face halo (Section 4.3, "Initialization"), stored as 16-bit local rows
+// - is copied into shared memory and every relation is built there.  The
+// block has one thread per own vertex; per-vertex work is sequential in
+// that thread, and every output leaves through shared-memory staging with
+// one thread per element (coalesced stores).
 //
-//  B. VT (Section 4.6: iterate the segment's tets, test each vertex against
-//     the segment interval I_V, Algorithm 1).  Counts per own vertex by
-//     shared-memory atomics, an exclusive scan, then a deterministic fill:
-//     tets are taken in windows of one tet per thread; each warp ORs a
-//     32-bit presence mask per own vertex, and each vertex's thread walks
-//     the masks in (warp, lane) order, so every row comes out ascending
-//     without a sort.  The paper's atomicPush (Algorithm 2) gives rows in
-//     arbitrary order; this fill gives the canonical one.
-//  C. VV and ET, one warp per own vertex x: the other vertices of the tets
-//     in VT(x) are ORed into a bitmap over the cluster's local vertices
-//     (local order = canonical order, so reading the bitmap in bit order
-//     yields VV(x) sorted and deduplicated).  The bits above x are the edges
-//     (x, w) x owns; the rank of w among them comes from a popcount prefix.
-//     Each tet ORs its lane bit into the mask of each of its edges, so the
-//     position of tet j in ET(x, w) is the popcount of the lanes below j:
-//     rows come out sorted by (w, t).  Warps of a chunk of NWARP vertices
-//     get their output positions from one block scan.
-//  D. TT (Table 1; never described by the paper): the faces of the internal
-//     tets go into an open-addressing hash keyed by their three local
-//     vertex ids; a second internal tet with the same face links the pair,
-//     and the faces of the external and halo tets are probed to link the
-//     rest.  A face met a third time is reported (non-manifold input).
+//  B. VT (Section 4.6 / Algorithm 1: iterate the segment's tets and test
+//     each vertex against the segment interval).  Each warp takes a
+//     contiguous chunk of the tets (which are in canonical order) and counts
+//     its incidences per own vertex; a prefix across warps gives every
+//     (warp, vertex) its first slot, and within a warp the lanes holding the
+//     same vertex are ranked by a 32-bit lane mask.  Rows come out ascending
+//     with no sort.  (The paper's atomicPush, Algorithm 2, fills rows in
+//     arbitrary order.)
+//  C. VV, ET and most of TT, per own vertex x:
+//     - the other vertices of the tets in VT(x) are ORed into a bitmap over
+//       the cluster's neighbour universe; local order is canonical order, so
+//       the bitmap read in bit order is VV(x) sorted and deduplicated, and
+//       its bits above x are the upper endpoints w of the edges (x, w) that x
+//       owns; a byte per bitmap word holds the running count of upper bits,
+//       so the rank of w is one popcount away;
+//     - one block scan of the per-vertex counts places every row;
+//     - per upper edge a mask over VT(x) (bit j: the j-th tet contains w):
+//       its bits in order are ET(x, w), ascending, and the AND of the masks
+//       of (x, w1) and (x, w2) holds the two tets of the face (x, w1, w2), so
+//       every face whose lowest vertex is in the cluster gets its TT link.
+//  D. TT (Table 1; the paper gives no kernel for it) for the faces (b, c, d)
+//     of internal tets (a, b, c, d) with no own vertex: a small
+//     open-addressing hash of those faces is probed with the faces of the
+//     halo tets.  A face met a third time is reported (non-manifold input).
 //
-// Outputs are written with one thread per element of a contiguous range
-// (VT) or by warps over their vertex's contiguous range (VV, ET), so stores
-// are coalesced; the counting mode runs the same passes without writes and
-// returns the exact sizes used for output placement.
+// The counting mode runs the same passes without writes and returns the
+// exact sizes the host uses to place outputs and to admit cache entries.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <climits>
-#include <type_traits>
 
 #include "gale_internal.h"
 
@@ -48,26 +51,36 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 
 struct Smem {
-    int32_t *blk;
-    int32_t *scan;
+    int32_t *blk, *scan, *cnt;
+    uint16_t *nbr;
     int32_t *vt_off;
-    int32_t *cur;
     uint16_t *vt_list;
-    uint32_t *uni;
+    uint32_t *bmap;   // per own vertex bitmaps (phase B: per-warp counters and masks)
+    uint8_t *pre;     // per own vertex, per bitmap word: upper bits in earlier words
+    uint16_t *st_ew;  // upper endpoints of the owned edges
+    uint32_t *emask;  // per-edge tet masks, then ET row offsets
+    uint16_t *st_v;   // VV staging, later ET value staging
     uint32_t *hash;
-    uint32_t *nbr;
+    int32_t *tcnt;
+    int32_t *st_tt;
 };
 
 __device__ __forceinline__ Smem carve(char *base, const SmemPlan &p) {
     Smem s;
     s.blk = reinterpret_cast<int32_t *>(base + p.blk);
     s.scan = reinterpret_cast<int32_t *>(base + p.scan);
+    s.cnt = reinterpret_cast<int32_t *>(base + p.cnt);
+    s.nbr = reinterpret_cast<uint16_t *>(base + p.nbr);
     s.vt_off = reinterpret_cast<int32_t *>(base + p.vt_off);
-    s.cur = reinterpret_cast<int32_t *>(base + p.cur);
     s.vt_list = reinterpret_cast<uint16_t *>(base + p.vt_list);
-    s.uni = reinterpret_cast<uint32_t *>(base + p.uni);
+    s.bmap = reinterpret_cast<uint32_t *>(base + p.bmap);
+    s.pre = reinterpret_cast<uint8_t *>(base + p.pre);
+    s.st_ew = reinterpret_cast<uint16_t *>(base + p.st_ew);
+    s.emask = reinterpret_cast<uint32_t *>(base + p.emask);
+    s.st_v = reinterpret_cast<uint16_t *>(base + p.emask);
     s.hash = reinterpret_cast<uint32_t *>(base + p.hash);
-    s.nbr = reinterpret_cast<uint32_t *>(base + p.nbr);
+    s.tcnt = reinterpret_cast<int32_t *>(base + p.tcnt);
+    s.st_tt = reinterpret_cast<int32_t *>(base + p.st_tt);
     return s;
 }
 
@@ -84,10 +97,10 @@ __device__ __forceinline__ int32_t glob_tet(const BlockHdr &h, const int32_t *tm
 
 // Bits of `word` (word index q of a bitmap) that stand for local ids > x.
 __device__ __forceinline__ uint32_t upper_bits(uint32_t word, int q, int x) {
-    int qx = x >> 5;
+    const int qx = x >> 5;
     if (q > qx) return word;
     if (q < qx) return 0u;
-    int b = x & 31;
+    const int b = x & 31;
     return b == 31 ? 0u : (word & (FULL << (b + 1)));
 }
 
@@ -100,46 +113,37 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
-__device__ __forceinline__ int warp_sum(int v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
-// Exclusive scan of one value per thread over the block; returns the
-// thread's prefix, total in *total.  scr needs NWARP+1 words.  Contains
-// two __syncthreads.
-template <int NT>
+// Exclusive scan of one value per thread over the block (any multiple of 32
+// threads up to 1024); scr needs 33 words.  Two __syncthreads.
 __device__ __forceinline__ int block_scan_thread(int v, int32_t *scr, int *total) {
-    constexpr int NW = NT / 32;
+    const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = warp_incl_scan(v, lane);
+    const int incl = warp_incl_scan(v, lane);
     if (lane == 31) scr[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int w = lane < NW ? scr[lane] : 0;
-        int wi = warp_incl_scan(w, lane);
-        if (lane < NW) scr[lane] = wi - w;
-        if (lane == NW - 1) scr[NW] = wi;
+        const int w = lane < nw ? scr[lane] : 0;
+        const int wi = warp_incl_scan(w, lane);
+        if (lane < nw) scr[lane] = wi - w;
+        if (lane == 31) scr[32] = wi;
     }
     __syncthreads();
-    int r = scr[warp] + incl - v;
-    *total = scr[NW];
-    return r;
+    *total = scr[32];
+    return scr[warp] + incl - v;
 }
 
-// Exclusive scan in place of a[0..n) (n small); returns the total.
-template <int NT>
+// Exclusive scan in place of a[0..n); returns the total.  Ends synced.
 __device__ int block_scan_array(int32_t *a, int n, int32_t *scr) {
+    const int NT = blockDim.x;
     const int per = (n + NT - 1) / NT;
     const int b = threadIdx.x * per;
     const int e = min(n, b + per);
     int s = 0;
     for (int i = b; i < e; ++i) s += a[i];
     int total;
-    int run = block_scan_thread<NT>(s, scr, &total);
+    int run = block_scan_thread(s, scr, &total);
     for (int i = b; i < e; ++i) {
-        int v = a[i];
+        const int v = a[i];
         a[i] = run;
         run += v;
     }
@@ -147,9 +151,9 @@ __device__ int block_scan_array(int32_t *a, int n, int32_t *scr) {
     return total;
 }
 
+// The face of a packed row opposite slot s: the other three 16-bit ids,
+// ascending, packed into 48 bits.
 __device__ __forceinline__ uint64_t face_key(uint2 r, int s) {
-    // the three vertices of the row other than slot s, ascending, packed as
-    // 16-bit fields: drop field s of the packed 64-bit row
     const uint64_t row = uint64_t(r.x) | (uint64_t(r.y) << 32);
     const int sh = 16 * s;
     const uint64_t low = sh ? (row & ((uint64_t(1) << sh) - 1)) : 0ull;
@@ -158,7 +162,7 @@ __device__ __forceinline__ uint64_t face_key(uint2 r, int s) {
 }
 
 __device__ __forceinline__ uint32_t face_hash(uint64_t key, uint32_t mask) {
-    return uint32_t((key * 0x9E3779B97F4A7C15ull) >> 32) & mask;
+    return uint32_t((key * 0x9E3779B97F4A7C15ull) >> 40) & mask;
 }
 
 __device__ __forceinline__ void cswap(int32_t &a, int32_t &b) {
@@ -167,31 +171,34 @@ __device__ __forceinline__ void cswap(int32_t &a, int32_t &b) {
     b = hi;
 }
 
-// sorting network for 4 values held in registers
-__device__ __forceinline__ void sort4_net(int32_t &a, int32_t &b, int32_t &c, int32_t &d) {
-    cswap(a, b); cswap(c, d); cswap(a, c); cswap(b, d); cswap(b, c);
-}
+// hash entries: bits [0, 20) = 4 * internal-tet index + slot + 1, bits
+// [20, 32) = number of other tets matched to the face
+constexpr uint32_t kRefMask = (1u << 20) - 1u;
+constexpr uint32_t kMatch = 1u << 20;
 
 // ---------------------------------------------------------------------------
-// One cluster.  COUNT: no output writes, sizes -> sizes_out[5].
+// One cluster.  COUNT: no output writes; sizes -> sizes_out[5].
+// `it` points to a shared-memory copy of the work item.
 // ---------------------------------------------------------------------------
-template <int NT, bool COUNT>
+template <bool COUNT>
 __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, uint32_t mask,
                             const WorkItem *it, int64_t *sizes_out, int32_t *err) {
-    constexpr int NWARP = NT / 32;
+    const int NT = blockDim.x, NWARP = NT >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     const Caps &caps = plan.caps;
 
     // ---------------- A. stage the working set ----------------
-    const int32_t *g = m.blocks + blk_word;
-    if (tid < 8) S.blk[tid] = __ldg(g + tid);
+    const int32_t *__restrict__ g = m.blocks + blk_word;
+    if (tid < kHdrWords) S.blk[tid] = __ldg(g + tid);
     __syncthreads();
     const BlockHdr h = *reinterpret_cast<const BlockHdr *>(S.blk);
     const int64_t words = blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo);
-    const int W = (h.nv_loc + 31) >> 5;
+    const int W = (h.nv_nb + 31) >> 5;
     const bool fits = words <= caps.blk_words && h.nv_own <= caps.nv_own && h.n_own <= caps.n_own &&
-                      h.nv_loc <= caps.nv_loc && h.nv_own >= 0 && h.n_own >= 0 &&
-                      int64_t(4) * h.n_own + 1 <= caps.hcap;
+                      h.nv_loc <= caps.nv_loc && h.nv_nb <= caps.nv_nb && h.nv_own >= 0 && h.n_own >= 0 &&
+                      h.n_ext >= 0 && h.n_halo >= 0 && h.n_bnd >= 0 && 2 * h.n_bnd + 1 <= caps.hcap &&
+                      W <= plan.wp && h.nv_nb <= h.nv_loc;
     if (!fits) {
         if (tid == 0) atomicOr(err, ERR_CAPACITY);
         __syncthreads();
@@ -201,78 +208,94 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         const int4 *src = reinterpret_cast<const int4 *>(g);
         int4 *dst = reinterpret_cast<int4 *>(S.blk);
         const int n4 = int(words >> 2);
-        for (int i = 2 + tid; i < n4; i += NT) dst[i] = __ldg(src + i);
+        for (int i = kHdrWords / 4 + tid; i < n4; i += NT) dst[i] = __ldg(src + i);
     }
     __syncthreads();
-    const int32_t *vmap = S.blk + 8;
+    const int32_t *vmap = S.blk + kHdrWords;
     const int32_t *tmap = S.blk + blk_tmap_off(h.nv_loc);
     const uint2 *rows = reinterpret_cast<const uint2 *>(S.blk + blk_rows_off(h.nv_loc, h.n_ext, h.n_halo));
     const int nvo = h.nv_own, lo = h.own_lo;
-    const int n_vtets = h.n_ext + h.n_own;
+    const int n_ext = h.n_ext, n_own = h.n_own;
+    const int n_vtets = n_ext + n_own;
+    const bool want_tt = COUNT || (mask & R_TT);
+    const bool do_vv = !COUNT && (mask & R_VV);
+    const bool do_et = !COUNT && (mask & R_ET);
+    const uint32_t nvo_u = uint32_t(nvo);
 
-    const bool need_vt = COUNT || (mask & (R_VT | R_VV | R_ET));
-    int vt_total = 0;
-    if (need_vt) {
-        // ---------------- B. VT ----------------
-        for (int i = tid; i < nvo; i += NT) S.cur[i] = 0;
+    // ---------------- B. VT ----------------
+    {
+        const int pad = caps.nv_own;
+        uint32_t *cw = S.bmap;              // [warp][v]: counts, then next slot
+        uint32_t *mk = S.bmap + NWARP * pad;  // [warp][v]: lanes holding v
+        const int chunk = ((n_vtets + NWARP - 1) / NWARP + 31) & ~31;
+        const int c0 = min(n_vtets, warp * chunk), c1 = min(n_vtets, c0 + chunk);
+        for (int i = tid; i < 2 * NWARP * pad; i += NT) S.bmap[i] = 0u;
         __syncthreads();
-        for (int i = tid; i < n_vtets; i += NT) {
-            uint2 r = rows[i];
+        for (int i = c0 + lane; i < c1; i += 32) {
+            const uint2 r = rows[i];
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                uint32_t d = vtx(r, s) - uint32_t(lo);
-                if (d < uint32_t(nvo)) atomicAdd(&S.cur[d], 1);
+                const uint32_t d = vtx(r, s) - uint32_t(lo);
+                if (d < nvo_u) atomicAdd(&cw[warp * pad + d], 1u);
             }
         }
         __syncthreads();
-        for (int i = tid; i < nvo; i += NT) S.vt_off[i] = S.cur[i];
+        // row lengths -> offsets; every (warp, vertex) gets its first slot
+        for (int v = tid; v < nvo; v += NT) {
+            int tot = 0;
+            for (int w = 0; w < NWARP; ++w) tot += int(cw[w * pad + v]);
+            S.vt_off[v] = tot;
+        }
         __syncthreads();
-        vt_total = block_scan_array<NT>(S.vt_off, nvo, S.scan);
+        const int vt_total = block_scan_array(S.vt_off, nvo, S.scan);
         bool bad = vt_total > caps.n_vt;
-        for (int i = tid; i < nvo; i += NT) {
-            S.cur[i] = S.vt_off[i];
-            int deg = (i + 1 < nvo ? S.vt_off[i + 1] : vt_total) - S.vt_off[i];
-            if (deg > caps.max_deg) bad = true;
+        for (int v = tid; v < nvo; v += NT) {
+            int run = S.vt_off[v];
+            const int d = (v + 1 < nvo ? S.vt_off[v + 1] : vt_total) - run;
+            bad |= d > caps.max_deg;
+            for (int w = 0; w < NWARP; ++w) {
+                const int c = int(cw[w * pad + v]);
+                cw[w * pad + v] = uint32_t(run);
+                run += c;
+            }
         }
         if (tid == 0) S.vt_off[nvo] = vt_total;
         if (__syncthreads_or(bad)) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             return;
         }
-        // windowed presence masks, masks[w * pad + v]
-        uint32_t *masks = S.uni;
-        const int pad = caps.nv_own;
-        for (int i = tid; i < NWARP * pad; i += NT) masks[i] = 0;
-        __syncthreads();
-        for (int base = 0; base < n_vtets; base += NT) {
-            const int i = base + tid;
-            if (i < n_vtets) {
-                uint2 r = rows[i];
+        if (!bad) {
+            // fill in tet order, 32 tets per step of each warp
+            for (int i0 = c0; i0 < c1; i0 += 32) {
+                const int i = i0 + lane;
+                const uint2 r = i < c1 ? rows[i] : make_uint2(0xffffffffu, 0xffffffffu);
+                uint32_t d[4];
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
-                    uint32_t d = vtx(r, s) - uint32_t(lo);
-                    if (d < uint32_t(nvo)) atomicOr(&masks[warp * pad + d], 1u << lane);
+                    d[s] = vtx(r, s) - uint32_t(lo);
+                    if (d[s] < nvo_u) atomicOr(&mk[warp * pad + d[s]], 1u << lane);
                 }
-            }
-            __syncthreads();
-            for (int v = tid; v < nvo; v += NT) {
-                int c = S.cur[v];
-                for (int w = 0; w < NWARP; ++w) {
-                    uint32_t mk = masks[w * pad + v];
-                    if (mk) {
-                        masks[w * pad + v] = 0;
-                        const int tb = base + w * 32;
-                        do {
-                            int b = __ffs(mk) - 1;
-                            mk &= mk - 1;
-                            S.vt_list[c++] = uint16_t(tb + b);
-                        } while (mk);
+                __syncwarp();
+                uint32_t mm[4];
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    mm[s] = 0u;
+                    if (d[s] < nvo_u) {
+                        mm[s] = mk[warp * pad + d[s]];
+                        S.vt_list[cw[warp * pad + d[s]] + __popc(mm[s] & lt)] = uint16_t(i);
                     }
                 }
-                S.cur[v] = c;
+                __syncwarp();
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    if (d[s] < nvo_u && (mm[s] & lt) == 0u) {
+                        cw[warp * pad + d[s]] += uint32_t(__popc(mm[s]));
+                        mk[warp * pad + d[s]] = 0u;
+                    }
+                __syncwarp();
             }
-            __syncthreads();
         }
+        __syncthreads();
         if (COUNT) {
             if (tid == 0) sizes_out[SZ_VT] = vt_total;
         } else if (mask & R_VT) {
@@ -280,254 +303,242 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             for (int j = tid; j < vt_total; j += NT) it->vt_val[j] = glob_tet(h, tmap, S.vt_list[j]);
         }
     }
+    if (!(COUNT || do_vv || do_et || want_tt)) return;
 
-    if (COUNT || (mask & (R_VV | R_ET))) {
-        // ---------------- C. VV and ET ----------------
-        const int Wc = (caps.nv_loc + 31) >> 5;
-        uint32_t *bm = S.uni + warp * plan.warp_words;
-        int32_t *pre = reinterpret_cast<int32_t *>(bm + Wc);
-        uint32_t *emask = bm + 2 * Wc;
-        int32_t *ecnt = reinterpret_cast<int32_t *>(emask + caps.max_up);
-        int32_t *scnt = S.scan + (NWARP + 1);       // [NWARP][3]
-        int32_t *sbase = scnt + 3 * NWARP;          // [NWARP][3]
-        int32_t *carry = sbase + 3 * NWARP;         // [3]
-        if (tid < 3) carry[tid] = 0;
-        __syncthreads();
-        const bool do_vv = !COUNT && (mask & R_VV);
-        const bool do_et = !COUNT && (mask & R_ET);
-        for (int r0 = 0; r0 < nvo; r0 += NWARP) {
-            const int i = r0 + warp;
-            const bool active = i < nvo;
-            const int x = lo + i;
-            int vvc = 0, ec = 0, etv = 0, beg = 0, L = 0;
-            bool bad = false;
-            if (active) {
-                beg = S.vt_off[i];
-                L = S.vt_off[i + 1] - beg;
-                for (int q = lane; q < W; q += 32) bm[q] = 0;
-                __syncwarp();
-                for (int j = lane; j < L; j += 32) {
-                    uint2 r = rows[S.vt_list[beg + j]];
+    // ---------------- C. VV, ET and TT faces with an own lowest vertex ----
+    int32_t *c_vv = S.cnt, *c_e = S.cnt + caps.nv_own, *c_et = S.cnt + 2 * caps.nv_own;
+    __syncthreads();  // phase B counters and masks are dead
+    if (want_tt) {
+        uint32_t *nb32 = reinterpret_cast<uint32_t *>(S.nbr);
+        for (int i = tid; i < 2 * n_own; i += NT) nb32[i] = 0xffffffffu;
+    }
+    // pass 1: bitmaps and counts
+    for (int i = tid; i < nvo; i += NT) {
+        const int x = lo + i;
+        const int beg = S.vt_off[i], L = S.vt_off[i + 1] - beg;
+        uint32_t *bm = S.bmap + i * plan.wp;
+        for (int q = 0; q < W; ++q) bm[q] = 0u;
+        int etv = 0;
+        for (int j0 = 0; j0 < L; j0 += 4) {
+            uint2 r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) r[u] = rows[S.vt_list[beg + min(j0 + u, L - 1)]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (j0 + u < L) {
 #pragma unroll
                     for (int s = 0; s < 4; ++s) {
-                        uint32_t y = vtx(r, s);
+                        const uint32_t y = vtx(r[u], s);
                         if (int(y) != x) atomicOr(&bm[y >> 5], 1u << (y & 31));
                         etv += int(y) > x;
                     }
                 }
-                __syncwarp();
-                int run = 0;
-                for (int q0 = 0; q0 < W; q0 += 32) {
-                    const int q = q0 + lane;
-                    uint32_t word = q < W ? bm[q] : 0u;
-                    vvc += __popc(word);
-                    int c = __popc(upper_bits(word, q, x));
-                    int incl = warp_incl_scan(c, lane);
-                    if (q < W) pre[q] = run + incl - c;
-                    run += __shfl_sync(FULL, incl, 31);
+            }
+        }
+        int vv = 0, ec = 0;
+        uint8_t *pr = S.pre + i * plan.wp;
+        for (int q = 0; q < W; ++q) {
+            const uint32_t word = bm[q];
+            pr[q] = uint8_t(ec);
+            vv += __popc(word);
+            ec += __popc(upper_bits(word, q, x));
+        }
+        c_vv[i] = vv;
+        c_e[i] = ec;
+        c_et[i] = etv;
+    }
+    __syncthreads();
+    const int tot_vv = block_scan_array(c_vv, nvo, S.scan);
+    const int tot_e = block_scan_array(c_e, nvo, S.scan);
+    const int tot_et = block_scan_array(c_et, nvo, S.scan);
+    if (COUNT && tid == 0) {
+        sizes_out[SZ_VV] = tot_vv;
+        sizes_out[SZ_E] = tot_e;
+        sizes_out[SZ_ET] = tot_et;
+    }
+    if (tot_e > caps.max_e || (do_vv && tot_vv > caps.max_vv) || (do_et && tot_et > caps.max_etv)) {
+        if (tid == 0) atomicOr(err, ERR_CAPACITY);
+        return;
+    }
+    // pass 2: VV rows and the upper endpoints of the owned edges, staged
+    bool bad_up = false;
+    for (int i = tid; i < nvo; i += NT) {
+        const int x = lo + i;
+        uint32_t *bm = S.bmap + i * plan.wp;
+        int p = c_vv[i], e = c_e[i];
+        const int e_end = (i + 1 < nvo) ? c_e[i + 1] : tot_e;
+        bad_up |= (e_end - e) > caps.max_up || (e_end - e) > 255;
+        for (int q = 0; q < W; ++q) {
+            uint32_t word = bm[q];
+            uint32_t up = upper_bits(word, q, x);
+            bm[q] = up;  // from here on the bitmap holds the upper neighbours only
+            if (do_vv)
+                while (word) {
+                    const int b = __ffs(word) - 1;
+                    word &= word - 1;
+                    S.st_v[p++] = uint16_t(q * 32 + b);
                 }
-                ec = run;
-                vvc = warp_sum(vvc);
-                etv = warp_sum(etv);
-                bad = ec > caps.max_up;
+            while (up) {
+                const int b = __ffs(up) - 1;
+                up &= up - 1;
+                S.st_ew[e++] = uint16_t(q * 32 + b);
             }
-            if (lane == 0) {
-                scnt[3 * warp + 0] = active ? vvc : 0;
-                scnt[3 * warp + 1] = active ? ec : 0;
-                scnt[3 * warp + 2] = active ? etv : 0;
-            }
-            if (__syncthreads_or(bad && lane == 0)) {
-                if (tid == 0) atomicOr(err, ERR_CAPACITY);
-                return;
-            }
-            if (warp == 0) {
+        }
+    }
+    if (__syncthreads_or(bad_up)) {
+        if (tid == 0) atomicOr(err, ERR_CAPACITY);
+        return;
+    }
+    if (do_vv) {
+        for (int i = tid; i < nvo; i += NT) it->vv_off[i] = c_vv[i];
+        if (tid == 0) it->vv_off[nvo] = tot_vv;
+        for (int j = tid; j < tot_vv; j += NT) it->vv_val[j] = vmap[S.st_v[j]];
+    }
+    if (do_et) {
+        for (int i = tid; i < nvo; i += NT) it->eu_off[i] = c_e[i];
+        if (tid == 0) {
+            it->eu_off[nvo] = tot_e;
+            it->et_off[tot_e] = tot_et;
+        }
+        for (int e = tid; e < tot_e; e += NT) it->e_w[e] = vmap[S.st_ew[e]];
+    }
+    if (!(do_et || want_tt)) return;
+    __syncthreads();  // VV staging is dead: the edge masks take its place
+    {
+        // pass 3a: per-edge tet masks and TT links
+        const int nch = plan.nch;
+        int32_t flags = 0;
+        for (int i = tid; i < nvo; i += NT) {
+            const int x = lo + i;
+            const int beg = S.vt_off[i], L = S.vt_off[i + 1] - beg;
+            const int e0 = c_e[i], E = ((i + 1 < nvo) ? c_e[i + 1] : tot_e) - e0;
+            const uint32_t *bm = S.bmap + i * plan.wp;
+            const uint8_t *pr = S.pre + i * plan.wp;
+            uint32_t *em = S.emask + e0 * nch;  // em[r * nch + c]
+            for (int q = 0; q < E * nch; ++q) em[q] = 0u;
+            // rank of an upper neighbour y among x's upper neighbours
+            auto rank = [&](uint32_t y) -> int {
+                const int q = int(y >> 5);
+                return int(pr[q]) + __popc(bm[q] & ((1u << (y & 31)) - 1u));
+            };
+            for (int j0 = 0; j0 < L; j0 += 4) {
+                uint2 r[4];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    int v = lane < NWARP ? scnt[3 * lane + c] : 0;
-                    int incl = warp_incl_scan(v, lane);
-                    int tot = __shfl_sync(FULL, incl, 31);
-                    int cb = carry[c];
-                    if (lane < NWARP) sbase[3 * lane + c] = cb + incl - v;
-                    if (!COUNT && lane < NWARP && r0 + lane < nvo) {
-                        if (c == 0 && (mask & R_VV)) it->vv_off[r0 + lane] = cb + incl - v;
-                        if (c == 1 && (mask & R_ET)) it->eu_off[r0 + lane] = cb + incl - v;
+                for (int u = 0; u < 4; ++u) r[u] = rows[S.vt_list[beg + min(j0 + u, L - 1)]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    if (j < L) {
+#pragma unroll
+                        for (int s = 1; s < 4; ++s) {
+                            const uint32_t y = vtx(r[u], s);
+                            if (int(y) > x) atomicOr(&em[rank(y) * nch + (j >> 5)], 1u << (j & 31));
+                        }
                     }
-                    __syncwarp();
-                    if (lane == 0) carry[c] = cb + tot;
                 }
             }
-            __syncthreads();
-            if (active && (do_vv || do_et)) {
-                const int vbase = sbase[3 * warp + 0];
-                const int ebase = sbase[3 * warp + 1];
-                const int tbase = sbase[3 * warp + 2];
-                // VV row and the upper endpoints of x's edges, in bit order
-                int run_v = 0, run_e = 0;
-                for (int q0 = 0; q0 < W; q0 += 32) {
-                    const int q = q0 + lane;
-                    uint32_t word = q < W ? bm[q] : 0u;
-                    uint32_t up = upper_bits(word, q, x);
-                    int cv = __popc(word), cu = __popc(up);
-                    int iv = warp_incl_scan(cv, lane), iu = warp_incl_scan(cu, lane);
-                    int pv = vbase + run_v + iv - cv, pu = ebase + run_e + iu - cu;
-                    if (do_vv) {
-                        uint32_t wv = word;
-                        while (wv) {
-                            int b = __ffs(wv) - 1;
-                            wv &= wv - 1;
-                            it->vv_val[pv++] = vmap[q * 32 + b];
-                        }
-                    }
-                    if (do_et) {
-                        uint32_t wu = up;
-                        while (wu) {
-                            int b = __ffs(wu) - 1;
-                            wu &= wu - 1;
-                            it->e_w[pu++] = vmap[q * 32 + b];
-                        }
-                    }
-                    run_v += __shfl_sync(FULL, iv, 31);
-                    run_e += __shfl_sync(FULL, iu, 31);
-                }
-                if (do_et) {
-                    // ET rows of the edges (x, w): ranks from the bitmap prefix
-                    const int E = ec;
-                    auto rank = [&](uint32_t y) -> int {
-                        int q = int(y >> 5);
-                        uint32_t below = (y & 31) ? (FULL >> (32 - (y & 31))) : 0u;
-                        return pre[q] + __popc(upper_bits(bm[q], q, x) & below);
-                    };
-                    const int nch = (L + 31) >> 5;
-                    if (nch > 1) {
-                        for (int e = lane; e < E; e += 32) ecnt[e] = 0;
-                        __syncwarp();
-                        for (int j = lane; j < L; j += 32) {
-                            uint2 r = rows[S.vt_list[beg + j]];
+            if (!want_tt) continue;
+            // faces (x, w1, w2) with x lowest: the tets are the bits of
+            // em[w1] & em[w2]; links are kept for internal tets
+            for (int j0 = 0; j0 < L; j0 += 4) {
+                int tl[4];
+                uint2 r[4];
 #pragma unroll
-                            for (int s = 0; s < 4; ++s) {
-                                uint32_t y = vtx(r, s);
-                                if (int(y) > x) atomicAdd(&ecnt[rank(y)], 1);
-                            }
-                        }
-                        __syncwarp();
-                        int run = 0;
-                        for (int e0 = 0; e0 < E; e0 += 32) {
-                            const int e = e0 + lane;
-                            int c = e < E ? ecnt[e] : 0;
-                            int incl = warp_incl_scan(c, lane);
-                            if (e < E) {
-                                ecnt[e] = run + incl - c;
-                                it->et_off[ebase + e] = tbase + run + incl - c;
-                            }
-                            run += __shfl_sync(FULL, incl, 31);
-                        }
-                        __syncwarp();
-                    }
-                    for (int ch = 0; ch < nch; ++ch) {
-                        for (int e = lane; e < E; e += 32) emask[e] = 0;
-                        __syncwarp();
-                        const int j = ch * 32 + lane;
-                        uint2 r = make_uint2(0, 0);
-                        int32_t tg = 0;
-                        if (j < L) {
-                            const int tl = S.vt_list[beg + j];
-                            r = rows[tl];
-                            tg = glob_tet(h, tmap, tl);
+                for (int u = 0; u < 4; ++u) tl[u] = S.vt_list[beg + min(j0 + u, L - 1)];
 #pragma unroll
-                            for (int s = 0; s < 4; ++s) {
-                                uint32_t y = vtx(r, s);
-                                if (int(y) > x) atomicOr(&emask[rank(y)], 1u << lane);
-                            }
-                        }
-                        __syncwarp();
-                        if (nch == 1) {
-                            // single chunk: starts from the popcounts of the masks
-                            int run = 0;
-                            for (int e0 = 0; e0 < E; e0 += 32) {
-                                const int e = e0 + lane;
-                                int c = e < E ? __popc(emask[e]) : 0;
-                                int incl = warp_incl_scan(c, lane);
-                                if (e < E) {
-                                    ecnt[e] = run + incl - c;
-                                    it->et_off[ebase + e] = tbase + run + incl - c;
-                                }
-                                run += __shfl_sync(FULL, incl, 31);
-                            }
-                            __syncwarp();
-                        }
-                        if (j < L) {
-                            const uint32_t lt = (1u << lane) - 1u;
+                for (int u = 0; u < 4; ++u) r[u] = rows[tl[u]];
 #pragma unroll
-                            for (int s = 0; s < 4; ++s) {
-                                uint32_t y = vtx(r, s);
-                                if (int(y) > x) {
-                                    int e = rank(y);
-                                    it->et_val[tbase + ecnt[e] + __popc(emask[e] & lt)] = tg;
-                                }
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    const uint32_t io = uint32_t(tl[u] - n_ext);
+                    if (j >= L || io >= uint32_t(n_own)) continue;
+                    const int p = (int(vtx(r[u], 0)) == x) ? 0 : (int(vtx(r[u], 1)) == x) ? 1 : 2;
+                    if (p >= 2) continue;
+                    int rk[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int s2 = 1; s2 < 4; ++s2)
+                        if (s2 > p) rk[s2] = rank(vtx(r[u], s2));
+#pragma unroll
+                    for (int a = 1; a < 4; ++a)
+#pragma unroll
+                        for (int b2 = a + 1; b2 < 4; ++b2) {
+                            if (a <= p) continue;
+                            const int opp = 6 - p - a - b2;  // the slot outside {p, a, b2}
+                            int partner = -1, found = 0;
+                            for (int c = 0; c < nch; ++c) {
+                                uint32_t mk2 = em[rk[a] * nch + c] & em[rk[b2] * nch + c];
+                                if (c == (j >> 5)) mk2 &= ~(1u << (j & 31));
+                                found += __popc(mk2);
+                                if (mk2 && partner < 0) partner = 32 * c + __ffs(mk2) - 1;
                             }
+                            if (found > 1) flags |= ERR_NONMANIFOLD;
+                            if (partner >= 0) S.nbr[io * 4 + opp] = S.vt_list[beg + partner];
                         }
-                        __syncwarp();
-                        if (nch > 1) {
-                            for (int e = lane; e < E; e += 32) ecnt[e] += __popc(emask[e]);
-                            __syncwarp();
-                        }
-                    }
                 }
             }
         }
-        __syncthreads();
-        if (tid == 0) {
-            if (COUNT) {
-                sizes_out[SZ_VV] = carry[0];
-                sizes_out[SZ_E] = carry[1];
-                sizes_out[SZ_ET] = carry[2];
-            } else {
-                if (mask & R_VV) it->vv_off[nvo] = carry[0];
-                if (mask & R_ET) {
-                    it->eu_off[nvo] = carry[1];
-                    it->et_off[carry[1]] = carry[2];
+        if (flags) atomicOr(err, flags);
+        __syncthreads();  // bitmaps are dead: the ET value staging takes their place
+        if (do_et) {
+            // pass 3b: ET rows from the masks; each edge's first mask word
+            // then holds its row offset for the copy-out
+            uint16_t *st_et = reinterpret_cast<uint16_t *>(S.bmap);
+            for (int i = tid; i < nvo; i += NT) {
+                const int beg = S.vt_off[i];
+                const int e0 = c_e[i], E = ((i + 1 < nvo) ? c_e[i + 1] : tot_e) - e0;
+                uint32_t *em = S.emask + e0 * nch;
+                int t = c_et[i];
+                for (int rr = 0; rr < E; ++rr) {
+                    const int t0 = t;
+                    for (int c = 0; c < nch; ++c) {
+                        uint32_t mk2 = em[rr * nch + c];
+                        while (mk2) {
+                            const int b = __ffs(mk2) - 1;
+                            mk2 &= mk2 - 1;
+                            st_et[t++] = S.vt_list[beg + 32 * c + b];
+                        }
+                    }
+                    em[rr * nch] = uint32_t(t0);
                 }
             }
+            __syncthreads();
+            for (int e = tid; e < tot_e; e += NT) it->et_off[e] = int32_t(S.emask[e * nch]);
+            for (int j = tid; j < tot_et; j += NT) it->et_val[j] = glob_tet(h, tmap, st_et[j]);
         }
         __syncthreads();
     }
 
-    if (COUNT || (mask & R_TT)) {
-        // ---------------- D. TT ----------------
-        const int n_own = h.n_own, n_ext = h.n_ext;
+    if (want_tt) {
+        // ---------------- D. faces with no own vertex, against the halo ----
         const uint32_t hmask = uint32_t(caps.hcap - 1);
         uint32_t *hash = S.hash;
-        uint32_t *nbr = S.nbr;  // neighbour across face s of internal tet i: nbr[4 i + s], ~0u = none
         for (int i = tid; i < caps.hcap; i += NT) hash[i] = 0u;
-        for (int i = tid; i < 4 * n_own; i += NT) nbr[i] = 0xffffffffu;
         __syncthreads();
         int32_t flags = 0;
         for (int i = tid; i < n_own; i += NT) {
             const uint2 r = rows[n_ext + i];
-            for (int s = 0; s < 4; ++s) {
-                const uint64_t key = face_key(r, s);
-                uint32_t hp = face_hash(key, hmask);
-                int probe = 0;
-                for (; probe < caps.hcap; ++probe) {
-                    uint32_t prev = atomicCAS(&hash[hp], 0u, uint32_t(i * 4 + s + 1));
-                    if (prev == 0u) break;
-                    const uint32_t ref = prev - 1u;
-                    const int i2 = int(ref >> 2), s2 = int(ref & 3u);
-                    if (face_key(rows[n_ext + i2], s2) == key) {
-                        const uint32_t o1 = atomicCAS(&nbr[i2 * 4 + s2], 0xffffffffu, uint32_t(n_ext + i));
-                        const uint32_t o2 = atomicCAS(&nbr[i * 4 + s], 0xffffffffu, uint32_t(n_ext + i2));
-                        if (o1 != 0xffffffffu || o2 != 0xffffffffu) flags |= ERR_NONMANIFOLD;
-                        break;
-                    }
-                    hp = (hp + 1u) & hmask;
+            if (vtx(r, 1) - uint32_t(lo) < nvo_u) continue;  // face (b, c, d) has an own vertex
+            const uint64_t key = face_key(r, 0);
+            uint32_t hp = face_hash(key, hmask);
+            int probe = 0;
+            for (; probe < caps.hcap; ++probe) {
+                const uint32_t prev = atomicCAS(&hash[hp], 0u, uint32_t(i * 4 + 1));
+                if (prev == 0u) break;
+                const uint32_t ref = (prev & kRefMask) - 1u;
+                if (face_key(rows[n_ext + (ref >> 2)], 0) == key) {
+                    if (atomicAdd(&hash[hp], kMatch) >= kMatch) flags |= ERR_NONMANIFOLD;
+                    S.nbr[ref] = uint16_t(n_ext + i);
+                    S.nbr[i * 4] = uint16_t(n_ext + (ref >> 2));
+                    break;
                 }
-                if (probe == caps.hcap) flags |= ERR_HASH_FULL;
+                hp = (hp + 1u) & hmask;
             }
+            if (probe == caps.hcap) flags |= ERR_HASH_FULL;
         }
         __syncthreads();
-        const int nprobe = n_ext + h.n_halo;
-        for (int j = tid; j < nprobe; j += NT) {
-            const int tl = j < n_ext ? j : n_own + j;
+        const int n_halo = h.n_halo;
+        for (int j = tid; j < n_halo; j += NT) {
+            const int tl = n_vtets + j;
             const uint2 r = rows[tl];
             for (int s = 0; s < 4; ++s) {
                 const uint64_t key = face_key(r, s);
@@ -535,11 +546,10 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 for (int probe = 0; probe < caps.hcap; ++probe) {
                     const uint32_t e = hash[hp];
                     if (e == 0u) break;
-                    const uint32_t ref = e - 1u;
-                    const int i2 = int(ref >> 2), s2 = int(ref & 3u);
-                    if (face_key(rows[n_ext + i2], s2) == key) {
-                        const uint32_t o = atomicCAS(&nbr[i2 * 4 + s2], 0xffffffffu, uint32_t(tl));
-                        if (o != 0xffffffffu) flags |= ERR_NONMANIFOLD;
+                    const uint32_t ref = (e & kRefMask) - 1u;
+                    if (face_key(rows[n_ext + (ref >> 2)], 0) == key) {
+                        if (atomicAdd(&hash[hp], kMatch) >= kMatch) flags |= ERR_NONMANIFOLD;
+                        S.nbr[ref] = uint16_t(tl);
                         break;
                     }
                     hp = (hp + 1u) & hmask;
@@ -548,45 +558,49 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         if (flags) atomicOr(err, flags);
         __syncthreads();
-        int carry = 0;
-        const bool do_tt = !COUNT && (mask & R_TT);
-        for (int r0 = 0; r0 < n_own; r0 += NT) {
-            const int i = r0 + tid;
-            // absent neighbours sort last as INT32_MAX
-            int32_t v0 = INT32_MAX, v1 = INT32_MAX, v2 = INT32_MAX, v3 = INT32_MAX;
-            int c = 0;
-            if (i < n_own) {
-                const uint4 nb = *reinterpret_cast<const uint4 *>(&nbr[i * 4]);
-                if (nb.x != 0xffffffffu) { v0 = glob_tet(h, tmap, int32_t(nb.x)); ++c; }
-                if (nb.y != 0xffffffffu) { v1 = glob_tet(h, tmap, int32_t(nb.y)); ++c; }
-                if (nb.z != 0xffffffffu) { v2 = glob_tet(h, tmap, int32_t(nb.z)); ++c; }
-                if (nb.w != 0xffffffffu) { v3 = glob_tet(h, tmap, int32_t(nb.w)); ++c; }
-                sort4_net(v0, v1, v2, v3);
-            }
-            int tot;
-            const int pos = carry + block_scan_thread<NT>(c, S.scan, &tot);
-            if (do_tt && i < n_own) {
-                it->tt_off[i] = pos;
-                int32_t *o = it->tt_val + pos;
-                if (c > 0) o[0] = v0;
-                if (c > 1) o[1] = v1;
-                if (c > 2) o[2] = v2;
-                if (c > 3) o[3] = v3;
-            }
-            carry += tot;
-            __syncthreads();
+        // counts per internal tet -> offsets
+        int32_t *tcnt = S.tcnt;
+        for (int i = tid; i < n_own; i += NT) {
+            const uint2 nb = *reinterpret_cast<const uint2 *>(&S.nbr[i * 4]);
+            tcnt[i] = ((nb.x & 0xffffu) != 0xffffu) + ((nb.x >> 16) != 0xffffu) + ((nb.y & 0xffffu) != 0xffffu) +
+                      ((nb.y >> 16) != 0xffffu);
         }
-        if (tid == 0) {
-            if (COUNT) sizes_out[SZ_TT] = carry;
-            else if (do_tt) it->tt_off[n_own] = carry;
+        __syncthreads();
+        const int tot_tt = block_scan_array(tcnt, n_own, S.scan);
+        if (COUNT) {
+            if (tid == 0) sizes_out[SZ_TT] = tot_tt;
+        } else {
+            if (tot_tt > caps.max_tt) {
+                if (tid == 0) atomicOr(err, ERR_CAPACITY);
+                return;
+            }
+            for (int i = tid; i < n_own; i += NT) {
+                const uint2 nb = *reinterpret_cast<const uint2 *>(&S.nbr[i * 4]);
+                const uint32_t n0 = nb.x & 0xffffu, n1 = nb.x >> 16, n2 = nb.y & 0xffffu, n3 = nb.y >> 16;
+                // absent neighbours sort last as INT32_MAX
+                int32_t v0 = n0 != 0xffffu ? glob_tet(h, tmap, int32_t(n0)) : INT32_MAX;
+                int32_t v1 = n1 != 0xffffu ? glob_tet(h, tmap, int32_t(n1)) : INT32_MAX;
+                int32_t v2 = n2 != 0xffffu ? glob_tet(h, tmap, int32_t(n2)) : INT32_MAX;
+                int32_t v3 = n3 != 0xffffu ? glob_tet(h, tmap, int32_t(n3)) : INT32_MAX;
+                cswap(v0, v1); cswap(v2, v3); cswap(v0, v2); cswap(v1, v3); cswap(v1, v2);
+                const int p = tcnt[i];
+                it->tt_off[i] = p;
+                int32_t *o = S.st_tt + p;
+                if (v0 != INT32_MAX) o[0] = v0;
+                if (v1 != INT32_MAX) o[1] = v1;
+                if (v2 != INT32_MAX) o[2] = v2;
+                if (v3 != INT32_MAX) o[3] = v3;
+            }
+            if (tid == 0) it->tt_off[n_own] = tot_tt;
+            __syncthreads();
+            for (int j = tid; j < tot_tt; j += NT) it->tt_val[j] = S.st_tt[j];
         }
     }
     __syncthreads();
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) count_kernel(DevMesh m, SmemPlan plan, const int32_t *ids, int32_t n,
-                                                   int64_t *sizes, int32_t *err, int32_t *ticket) {
+__global__ void count_kernel(DevMesh m, SmemPlan plan, const int32_t *ids, int32_t n, int64_t *sizes, int32_t *err,
+                             int32_t *ticket) {
     extern __shared__ __align__(16) char smem[];
     const Smem S = carve(smem, plan);
     __shared__ int32_t s_idx;
@@ -604,57 +618,56 @@ __global__ void __launch_bounds__(NT) count_kernel(DevMesh m, SmemPlan plan, con
         }
         if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
         __syncthreads();
-        run_cluster<NT, true>(m, plan, S, m.blk_off[k], 0u, nullptr, s_sizes, err);
+        run_cluster<true>(m, plan, S, m.blk_off[k], 0u, nullptr, s_sizes, err);
         __syncthreads();
         if (threadIdx.x < SZ_N) sizes[int64_t(k) * SZ_N + threadIdx.x] = s_sizes[threadIdx.x];
     }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) build_kernel(DevMesh m, SmemPlan plan, const WorkItem *items,
-                                                   const int32_t *order, int32_t n, int32_t *err,
-                                                   int32_t *ticket) {
+__global__ void build_kernel(DevMesh m, SmemPlan plan, const WorkItem *items, const int32_t *order, int32_t n,
+                             int32_t *err, int32_t *ticket) {
     extern __shared__ __align__(16) char smem[];
     const Smem S = carve(smem, plan);
     __shared__ int32_t s_idx;
+    __shared__ WorkItem s_item;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
         __syncthreads();
         const int idx = s_idx;
         __syncthreads();
         if (idx >= n) break;
-        const WorkItem *it = items + (order ? order[idx] : idx);
-        const int k = it->k;
+        if (threadIdx.x == 0) s_item = items[order ? order[idx] : idx];
+        __syncthreads();
+        const int k = s_item.k;
         if (k < 0 || k >= m.K) {
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
-        run_cluster<NT, false>(m, plan, S, it->blk, it->mask, it, nullptr, err);
+        run_cluster<false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err);
     }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) build_one_kernel(DevMesh m, SmemPlan plan, const WorkItem *items,
-                                                       int32_t index, int32_t *err) {
+__global__ void build_one_kernel(DevMesh m, SmemPlan plan, const WorkItem *items, int32_t index, int32_t *err) {
     extern __shared__ __align__(16) char smem[];
     const Smem S = carve(smem, plan);
-    const WorkItem *it = items + index;
-    if (it->k < 0 || it->k >= m.K) {
+    __shared__ WorkItem s_item;
+    if (threadIdx.x == 0) s_item = items[index];
+    __syncthreads();
+    if (s_item.k < 0 || s_item.k >= m.K) {
         if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
         return;
     }
-    run_cluster<NT, false>(m, plan, S, it->blk, it->mask, it, nullptr, err);
+    run_cluster<false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err);
 }
 
-// Output placement (a5): exclusive scans, over the listed clusters, of every
+// Output placement: exclusive scans, over the listed clusters, of every
 // output array's length; one CTA.  arrays_base holds the base pointers of the
-// ten bulk arrays (its k/mask/blk fields are ignored).
+// ten bulk arrays (its k / mask / blk fields are ignored).
 constexpr int kBasesThreads = 1024;
 __global__ void __launch_bounds__(kBasesThreads) bases_kernel(DevMesh m, const int32_t *ids, int32_t n,
                                                               const int64_t *sizes, uint32_t mask,
                                                               const WorkItem *arrays_base, WorkItem *items,
                                                               int64_t *totals) {
-    // per item lengths of the ten arrays
     constexpr int NA = 10;
     __shared__ int64_t s_warp[kBasesThreads / 32][NA];
     __shared__ int64_t s_tot[NA];
@@ -685,12 +698,11 @@ __global__ void __launch_bounds__(kBasesThreads) bases_kernel(DevMesh m, const i
         lens(i, L);
         for (int a = 0; a < NA; ++a) acc[a] += L[a];
     }
-    // block exclusive scan of acc[]
     int64_t incl[NA];
     for (int a = 0; a < NA; ++a) {
         int64_t v = acc[a];
         for (int o = 1; o < 32; o <<= 1) {
-            int64_t y = __shfl_up_sync(FULL, v, o);
+            const int64_t y = __shfl_up_sync(FULL, v, o);
             if (lane >= o) v += y;
         }
         incl[a] = v;
@@ -699,10 +711,10 @@ __global__ void __launch_bounds__(kBasesThreads) bases_kernel(DevMesh m, const i
     __syncthreads();
     if (warp == 0) {
         for (int a = 0; a < NA; ++a) {
-            int64_t w = s_warp[lane][a];
+            const int64_t w = s_warp[lane][a];
             int64_t v = w;
             for (int o = 1; o < 32; o <<= 1) {
-                int64_t y = __shfl_up_sync(FULL, v, o);
+                const int64_t y = __shfl_up_sync(FULL, v, o);
                 if (lane >= o) v += y;
             }
             s_warp[lane][a] = v - w;
@@ -713,7 +725,7 @@ __global__ void __launch_bounds__(kBasesThreads) bases_kernel(DevMesh m, const i
     int64_t run[NA];
     for (int a = 0; a < NA; ++a) run[a] = s_warp[warp][a] + incl[a] - acc[a];
     int32_t *base[NA] = {arrays_base->vt_off, arrays_base->vt_val, arrays_base->vv_off, arrays_base->vv_val,
-                         arrays_base->eu_off, arrays_base->e_w, arrays_base->et_off, arrays_base->et_val,
+                         arrays_base->eu_off, arrays_base->e_w,    arrays_base->et_off, arrays_base->et_val,
                          arrays_base->tt_off, arrays_base->tt_val};
     for (int i = b; i < e; ++i) {
         int64_t L[NA];
@@ -747,27 +759,43 @@ SmemPlan plan_smem(const Caps &c, int threads) {
     p.threads = threads;
     p.caps = c;
     const int nwarp = threads / 32;
-    const int Wc = (c.nv_loc + 31) / 32;
+    const int W = (c.nv_nb + 31) / 32;
+    p.nch = std::max(1, (c.max_deg + 31) / 32);
+    p.wp = std::max(W, 1) | 1;
     int64_t off = 0;
     p.blk = 0;
     off = a16(int64_t(4) * c.blk_words);
     p.scan = int32_t(off);
-    off = a16(off + 4 * ((nwarp + 1) + 6 * nwarp + 3 + 8));
+    off = a16(off + 4 * 40);
+    p.cnt = int32_t(off);
+    off = a16(off + 4 * 3 * int64_t(c.nv_own));
+    p.nbr = int32_t(off);
+    off = a16(off + 8 * int64_t(c.n_own));
     p.vt_off = int32_t(off);
     off = a16(off + 4 * (int64_t(c.nv_own) + 1));
-    p.cur = int32_t(off);
-    off = a16(off + 4 * int64_t(c.nv_own));
     p.vt_list = int32_t(off);
     off = a16(off + 2 * int64_t(c.n_vt));
-    p.uni = int32_t(off);
-    p.warp_words = int32_t(((2 * Wc + 2 * c.max_up) + 3) & ~3);
-    const int64_t uni_b = 4 * int64_t(nwarp) * c.nv_own;
-    const int64_t uni_c = 4 * int64_t(nwarp) * p.warp_words;
-    const int64_t end_bc = a16(off + (uni_b > uni_c ? uni_b : uni_c));
+    p.bmap = int32_t(off);
+    // phase B: per-warp counters and masks; phase C: per-vertex bitmaps and
+    // their rank prefixes, later the ET value staging
+    const int64_t bm_b = 8 * int64_t(nwarp) * c.nv_own;
+    const int64_t bm_c = a16(4 * int64_t(c.nv_own) * p.wp) + int64_t(c.nv_own) * p.wp;
+    const int64_t st_et = 2 * int64_t(c.max_etv);
+    p.pre = int32_t(off + a16(4 * int64_t(c.nv_own) * p.wp));
+    off = a16(off + std::max(bm_b, std::max(bm_c, st_et)));
+    p.st_ew = int32_t(off);
+    off = a16(off + 2 * int64_t(c.max_e));
+    // VV staging, later the per-edge tet masks
+    p.emask = int32_t(off);
+    p.st_v = p.emask;
+    const int64_t end_c = a16(off + std::max<int64_t>(4 * int64_t(c.max_e) * p.nch, 2 * int64_t(c.max_vv)));
+    // phase D overlays from vt_off (cnt and nbr stay)
     p.hash = p.vt_off;
-    p.nbr = int32_t(a16(int64_t(p.hash) + 4 * int64_t(c.hcap)));
-    const int64_t end_d = a16(int64_t(p.nbr) + 16 * int64_t(c.n_own));
-    p.total = int32_t(end_bc > end_d ? end_bc : end_d);
+    p.tcnt = int32_t(a16(int64_t(p.hash) + 4 * int64_t(c.hcap)));
+    p.st_tt = int32_t(a16(int64_t(p.tcnt) + 4 * (int64_t(c.n_own) + 1)));
+    const int64_t end_d = a16(int64_t(p.st_tt) + 4 * int64_t(c.max_tt));
+    const int64_t tot = std::max(end_c, end_d);
+    p.total = tot > INT32_MAX ? INT32_MAX : int32_t(tot);
     return p;
 }
 
@@ -785,37 +813,27 @@ int device_sm_count() {
     return v;
 }
 
-template <int NT>
-static const void *build_fn() { return reinterpret_cast<const void *>(&build_kernel<NT>); }
-
-int max_ctas_per_sm(const SmemPlan &plan) {
-    int n = 0;
-    const void *fn = plan.threads == 128 ? build_fn<128>() : plan.threads == 256 ? build_fn<256>() : build_fn<512>();
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, plan.threads, plan.total) != cudaSuccess) return 0;
-    return n;
+void prepare_kernels(int smem) {
+    cudaFuncSetAttribute(build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(build_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-template <class F>
-static int dispatch_threads(int nt, F &&f) {
-    switch (nt) {
-        case 128: f(std::integral_constant<int, 128>{}); break;
-        case 256: f(std::integral_constant<int, 256>{}); break;
-        case 512: f(std::integral_constant<int, 512>{}); break;
-        default: return int(cudaErrorInvalidValue);
-    }
-    return int(cudaGetLastError());
+int max_ctas_per_sm(const SmemPlan &plan) {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, build_kernel, plan.threads, plan.total) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_kernel, plan.threads, plan.total) != cudaSuccess)
+        return 0;
+    return a < b ? a : b;
 }
 
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
                       int32_t *err, int32_t *ticket, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
-    return dispatch_threads(plan.threads, [&](auto ntc) {
-        constexpr int NT = decltype(ntc)::value;
-        cudaFuncSetAttribute(count_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
-        count_kernel<NT><<<grid, NT, plan.total, s>>>(m, plan, ids, n, sizes_out, err, ticket);
-    });
+    count_kernel<<<grid, plan.threads, plan.total, s>>>(m, plan, ids, n, sizes_out, err, ticket);
+    return int(cudaGetLastError());
 }
 
 int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t *sizes, uint32_t mask,
@@ -829,27 +847,15 @@ int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, 
                  int32_t *err, int32_t *ticket, int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
-    return dispatch_threads(plan.threads, [&](auto ntc) {
-        constexpr int NT = decltype(ntc)::value;
-        build_kernel<NT><<<grid, NT, plan.total, s>>>(m, plan, items, order, n, err, ticket);
-    });
+    build_kernel<<<grid, plan.threads, plan.total, s>>>(m, plan, items, order, n, err, ticket);
+    return int(cudaGetLastError());
 }
 
 int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,
                      void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return dispatch_threads(plan.threads, [&](auto ntc) {
-        constexpr int NT = decltype(ntc)::value;
-        build_one_kernel<NT><<<1, NT, plan.total, s>>>(m, plan, items, index, err);
-    });
-}
-
-void prepare_kernels(int threads, int smem) {
-    dispatch_threads(threads, [&](auto ntc) {
-        constexpr int NT = decltype(ntc)::value;
-        cudaFuncSetAttribute(build_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(build_one_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    });
+    build_one_kernel<<<1, plan.threads, plan.total, s>>>(m, plan, items, index, err);
+    return int(cudaGetLastError());
 }
 
 }  // namespace gale

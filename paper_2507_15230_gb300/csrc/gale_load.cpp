@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <array>
+#include <iterator>
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -292,53 +293,85 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         const int64_t e0 = hm.ext_off[k], e1 = hm.ext_off[k + 1];
         const int64_t h0 = hm.halo_off[k], h1 = hm.halo_off[k + 1];
         const int32_t t0 = hm.I_T[k], t1 = hm.I_T[k + 1];
-        std::vector<int32_t> &vm = vmaps[k];
-        vm.clear();
-        auto add_row = [&](int32_t t) {
+        // neighbour universe: vertices of [external | internal] tets plus
+        // the own interval, ascending; then halo-only vertices, ascending
+        std::vector<int32_t> nb, ho;
+        auto add_row = [&](std::vector<int32_t> &dst, int32_t t) {
             const int32_t *r = rows + 4 * int64_t(t);
             for (int j = 0; j < 4; ++j)
-                if (r[j] < v0 || r[j] >= v1) vm.push_back(r[j]);
+                if (r[j] < v0 || r[j] >= v1) dst.push_back(r[j]);
         };
-        for (int64_t i = e0; i < e1; ++i) add_row(hm.ext[i]);
-        for (int32_t t = t0; t < t1; ++t) add_row(t);
-        for (int64_t i = h0; i < h1; ++i) add_row(hm.halo[i]);
-        std::sort(vm.begin(), vm.end());
-        vm.erase(std::unique(vm.begin(), vm.end()), vm.end());
-        // insert the own interval in place
-        const int64_t below = std::lower_bound(vm.begin(), vm.end(), v0) - vm.begin();
-        std::vector<int32_t> full;
-        full.reserve(vm.size() + (v1 - v0));
-        full.insert(full.end(), vm.begin(), vm.begin() + below);
-        for (int32_t v = v0; v < v1; ++v) full.push_back(v);
-        full.insert(full.end(), vm.begin() + below, vm.end());
-        vm.swap(full);
+        for (int64_t i = e0; i < e1; ++i) add_row(nb, hm.ext[i]);
+        for (int32_t t = t0; t < t1; ++t) add_row(nb, t);
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        for (int64_t i = h0; i < h1; ++i) add_row(ho, hm.halo[i]);
+        std::sort(ho.begin(), ho.end());
+        ho.erase(std::unique(ho.begin(), ho.end()), ho.end());
+        {
+            std::vector<int32_t> only;
+            std::set_difference(ho.begin(), ho.end(), nb.begin(), nb.end(), std::back_inserter(only));
+            ho.swap(only);
+        }
+        const int64_t below = std::lower_bound(nb.begin(), nb.end(), v0) - nb.begin();
+        std::vector<int32_t> &vm = vmaps[k];
+        vm.clear();
+        vm.reserve(nb.size() + (v1 - v0) + ho.size());
+        vm.insert(vm.end(), nb.begin(), nb.begin() + below);
+        for (int32_t v = v0; v < v1; ++v) vm.push_back(v);
+        vm.insert(vm.end(), nb.begin() + below, nb.end());
+        const int32_t nv_nb = int32_t(vm.size());
+        vm.insert(vm.end(), ho.begin(), ho.end());
         ClusterStat &s = hm.stats[k];
         s.n_ext = int32_t(e1 - e0);
         s.n_own = t1 - t0;
         s.n_halo = int32_t(h1 - h0);
         s.nv_loc = int32_t(vm.size());
+        s.nv_nb = nv_nb;
         s.nv_own = v1 - v0;
         const int64_t ntot = int64_t(s.n_ext) + s.n_own + s.n_halo;
         if (int64_t(vm.size()) > kMaxLocal || ntot > kMaxLocal - 1) {
             bad_k = k;
             return;
         }
-        // degrees of own vertices over [external | internal]
-        std::vector<int32_t> deg(size_t(v1 - v0), 0);
+        // degrees and distinct upper neighbours of own vertices over
+        // [external | internal]; internal tets whose face opposite the lowest
+        // vertex has no own vertex
+        const int32_t own_lo = int32_t(below);
+        auto loc = [&](int32_t v) -> int32_t {
+            if (v >= v0 && v < v1) return own_lo + (v - v0);
+            return int32_t(std::lower_bound(vm.begin(), vm.begin() + nv_nb, v) - vm.begin());
+        };
+        const int32_t nvo = v1 - v0;
+        std::vector<int32_t> deg(static_cast<size_t>(nvo), 0);
+        std::vector<std::vector<int32_t>> up(static_cast<size_t>(nvo));
         auto count_row = [&](int32_t t) {
             const int32_t *r = rows + 4 * int64_t(t);
             for (int j = 0; j < 4; ++j)
-                if (r[j] >= v0 && r[j] < v1) deg[r[j] - v0]++;
+                if (r[j] >= v0 && r[j] < v1) {
+                    deg[r[j] - v0]++;
+                    for (int q = j + 1; q < 4; ++q) up[r[j] - v0].push_back(loc(r[q]));
+                }
         };
         for (int64_t i = e0; i < e1; ++i) count_row(hm.ext[i]);
         for (int32_t t = t0; t < t1; ++t) count_row(t);
-        int32_t nvt = 0, mx = 0;
-        for (int32_t x : deg) {
-            nvt += x;
-            mx = std::max(mx, x);
+        int32_t nvt = 0, mx = 0, mu = 0, ne = 0;
+        for (int32_t i = 0; i < nvo; ++i) {
+            nvt += deg[i];
+            mx = std::max(mx, deg[i]);
+            auto &u = up[i];
+            std::sort(u.begin(), u.end());
+            const int32_t nu = int32_t(std::unique(u.begin(), u.end()) - u.begin());
+            mu = std::max(mu, nu);
+            ne += nu;
         }
         s.n_vt = nvt;
         s.max_deg = mx;
+        s.max_up = mu;
+        s.n_e = ne;
+        int32_t nbnd = 0;
+        for (int32_t t = t0; t < t1; ++t) nbnd += (rows[4 * int64_t(t) + 1] >= v1);
+        s.n_bnd = nbnd;
         // two tets with the same vertex set have the same owner
         if (t1 - t0 > 1) {
             std::vector<std::array<int32_t, 4>> own(size_t(t1 - t0));
@@ -385,10 +418,10 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         const int64_t words = hm.blk_off[k + 1] - hm.blk_off[k];
         memset(blk, 0, size_t(words) * 4);
         const int32_t v0 = hm.I_V[k];
-        const int32_t own_lo = int32_t(std::lower_bound(vm.begin(), vm.end(), v0) - vm.begin());
-        BlockHdr hdr{s.n_ext, s.n_own, s.n_halo, s.nv_loc, own_lo, s.nv_own, hm.I_T[k], v0};
+        const int32_t own_lo = int32_t(std::lower_bound(vm.begin(), vm.begin() + s.nv_nb, v0) - vm.begin());
+        BlockHdr hdr{s.n_ext, s.n_own, s.n_halo, s.nv_loc, own_lo, s.nv_own, hm.I_T[k], v0, s.nv_nb, s.n_bnd, 0, 0};
         memcpy(blk, &hdr, sizeof(hdr));
-        memcpy(blk + 8, vm.data(), vm.size() * 4);
+        memcpy(blk + kHdrWords, vm.data(), vm.size() * 4);
         int32_t *tmap = blk + blk_tmap_off(s.nv_loc);
         const int64_t e0 = hm.ext_off[k], h0 = hm.halo_off[k];
         for (int32_t i = 0; i < s.n_ext; ++i) tmap[i] = hm.ext[e0 + i];
@@ -396,7 +429,9 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         uint16_t *lrows = reinterpret_cast<uint16_t *>(blk + blk_rows_off(s.nv_loc, s.n_ext, s.n_halo));
         auto local = [&](int32_t v) -> uint16_t {
             if (v >= v0 && v < v0 + s.nv_own) return uint16_t(own_lo + (v - v0));
-            return uint16_t(std::lower_bound(vm.begin(), vm.end(), v) - vm.begin());
+            auto it = std::lower_bound(vm.begin(), vm.begin() + s.nv_nb, v);
+            if (it != vm.begin() + s.nv_nb && *it == v) return uint16_t(it - vm.begin());
+            return uint16_t(std::lower_bound(vm.begin() + s.nv_nb, vm.end(), v) - vm.begin());
         };
         int64_t li = 0;
         auto put = [&](int32_t t) {
