@@ -184,6 +184,33 @@ gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out);
  */
 gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask, int32_t mode);
 
+/*
+ * gale_build_clusters_noalloc - the batched build without any allocation.
+ * The paper has no counterpart; this exists for callers that cannot allocate
+ * device memory when they need relations: a serving thread that must not
+ * synchronise the GPU (cudaMalloc / cudaFree may), an application whose own
+ * pool owns all of HBM, or code running where allocation is forbidden.
+ *   ids      HOST int32[n], 1 <= n <= 4096 cluster ids (a repeated id is
+ *            built into each of its slots); EINVAL beyond 4096
+ *   mask     relations to build (within the precondition mask)
+ *   dev_out  caller-owned DEVICE arrays, one per requested relation array,
+ *            laid out as the bulk arrays of gale_build_clusters for the same
+ *            list: clusters consecutive in list order, offsets relative to
+ *            their cluster; each array at least the summed lengths that the
+ *            sizes of gale_get_intervals give (e.g. vt_off: sum of
+ *            (v_end - v_begin + 1), vt_val: sum of the VT sizes)
+ * The work items, order lists, ticket counters and error word live in one
+ * fixed array of about 430 KB of device memory that every GPU which loads
+ * the library holds until the process exits; every call reuses it, so calls
+ * that overlap on the GPU (from several threads or contexts) race and must
+ * be serialised by the caller.  The first call on each device looks up that
+ * array's device address; make that first call before any stream capture.
+ * The call returns after the build has finished (it synchronises the
+ * context stream); EDEVICE if a kernel reported an error.
+ */
+gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask,
+                                        const gale_arrays *dev_out);
+
 /* Wait for all work of the context's stream; EDEVICE if a kernel set its
  * error word (the word is cleared), ECUDA on a CUDA error. */
 gale_status gale_synchronize(gale_ctx *ctx);

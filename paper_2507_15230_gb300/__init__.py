@@ -68,7 +68,7 @@ class ServeStats(ctypes.Structure):
 
 
 # the symbols include/gale.h declares
-EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
+EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
            "gale_bulk_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
            "gale_autotune", "gale_get_bins", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
@@ -93,6 +93,7 @@ def load_library(build: bool = True):
     lib.gale_load_mesh.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(P)]
     lib.gale_build_clusters.argtypes = [P, P, i32, u32, i32]
     lib.gale_synchronize.argtypes = [P]
+    lib.gale_build_clusters_noalloc.argtypes = [P, P, i32, u32, ctypes.POINTER(Arrays)]
     lib.gale_bulk_view.argtypes = [P, i32, ctypes.POINTER(View)]
     lib.gale_bulk_arrays.argtypes = [P, ctypes.POINTER(Arrays), P]
     lib.gale_bulk_export.argtypes = [P, u32, ctypes.POINTER(Arrays)]
@@ -253,6 +254,15 @@ class Context:
         else:
             ids = np.ascontiguousarray(ids, dtype=np.int32)
             _check(self._lib.gale_build_clusters(self._h, _p(ids), ids.shape[0], mask, mode))
+
+    def build_noalloc(self, ids, mask: int, out: dict):
+        """gale_build_clusters_noalloc: build into caller-owned device arrays
+        (out: array name -> CUDA int32 tensor) without any allocation."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        a = Arrays()
+        for n, t in out.items():
+            setattr(a, n, t.data_ptr() if t.numel() else None)
+        _check(self._lib.gale_build_clusters_noalloc(self._h, _p(ids), ids.shape[0], mask, ctypes.byref(a)))
 
     def synchronize(self):
         _check(self._lib.gale_synchronize(self._h))
