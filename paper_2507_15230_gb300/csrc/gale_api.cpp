@@ -394,9 +394,10 @@ gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out) {
     ctx->d_items = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * K));
     ctx->d_arrays_base = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * 16));
     ctx->d_totals = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * 16));
+    ctx->d_bsum = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * (gale::bases_scratch_words(K) + 16)));
     if (!ctx->d_blocks || !ctx->d_blk_off || !ctx->d_I_V || !ctx->d_I_T || !ctx->d_sizes || !ctx->d_err ||
         !ctx->d_tickets || !ctx->d_ids || !ctx->d_order_all || !ctx->d_order_part || !ctx->d_items ||
-        !ctx->d_arrays_base || !ctx->d_totals) {
+        !ctx->d_arrays_base || !ctx->d_totals || !ctx->d_bsum) {
         gale_destroy(ctx.release());
         return fail(GALE_ENOMEM, "device allocation failed while loading the mesh");
     }
@@ -476,7 +477,7 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
             cudaGraph_t graph;
             CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
             int rc = gale::launch_bases(dm, nullptr, K, ctx->d_sizes, mask, base, ctx->d_items, ctx->d_totals,
-                                        ctx->stream);
+                                        ctx->d_bsum, ctx->stream);
             for (size_t b = 0; rc == 0 && b < ctx->bins.size(); ++b) {
                 const gale::Bin &bin = ctx->bins[b];
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b],
@@ -494,7 +495,7 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
             }
         }
         CUDA_TRY(cudaGraphLaunch(g, ctx->stream));
-        launches = 1 + int64_t(ctx->bins.size());
+        launches = 3 + int64_t(ctx->bins.size());
     } else {
         const int32_t *d_ids = nullptr;
         if (!all) {
@@ -502,9 +503,9 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
             d_ids = ctx->d_ids;
         }
         int rc = gale::launch_bases(dm, d_ids, cnt, ctx->d_sizes, mask, base, ctx->d_items, ctx->d_totals,
-                                    ctx->stream);
+                                    ctx->d_bsum, ctx->stream);
         if (rc != 0) return cuda_fail(cudaError_t(rc), "bases launch");
-        launches = 1;
+        launches = 3;
         if (mode == GALE_MODE_PER_CLUSTER) {
             for (int32_t i = 0; i < cnt; ++i) {
                 const gale::Bin &bin = ctx->bins[ctx->bin_of[list[i]]];

@@ -55,6 +55,7 @@ struct gale_ctx {
     gale::WorkItem *d_items = nullptr;      // [K]
     gale::WorkItem *d_arrays_base = nullptr;  // [16] base pointers per mask
     int64_t *d_totals = nullptr;            // [10]
+    int64_t *d_bsum = nullptr;              // output placement scratch
     std::vector<int64_t> sizes;             // host [K*5]
     int64_t totals[5] = {0, 0, 0, 0, 0};
     double device_seconds = 0;

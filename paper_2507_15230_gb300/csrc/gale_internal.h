@@ -159,8 +159,11 @@ struct DevMesh {
 // (build).  One CTA per cluster at a time.
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
                       int32_t *err, int32_t *ticket, int grid, void *stream);
+// Output placement for n listed clusters (three launches).  bsum: device
+// scratch of bases_scratch_words(n) int64 words.
+int bases_scratch_words(int32_t n);
 int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t *sizes, uint32_t mask,
-                 const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, void *stream);
+                 const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, int64_t *bsum, void *stream);
 int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
                  int32_t *err, int32_t *ticket, int grid, void *stream);
 // One launch, one CTA, one work item (the per-cluster baseline form).

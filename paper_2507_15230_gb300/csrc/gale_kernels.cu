@@ -660,90 +660,133 @@ __global__ void build_one_kernel(DevMesh m, SmemPlan plan, const WorkItem *items
     run_cluster<false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err);
 }
 
-// Output placement: exclusive scans, over the listed clusters, of every
-// output array's length; one CTA.  arrays_base holds the base pointers of the
-// ten bulk arrays (its k / mask / blk fields are ignored).
-constexpr int kBasesThreads = 1024;
-__global__ void __launch_bounds__(kBasesThreads) bases_kernel(DevMesh m, const int32_t *ids, int32_t n,
-                                                              const int64_t *sizes, uint32_t mask,
-                                                              const WorkItem *arrays_base, WorkItem *items,
-                                                              int64_t *totals) {
-    constexpr int NA = 10;
-    __shared__ int64_t s_warp[kBasesThreads / 32][NA];
-    __shared__ int64_t s_tot[NA];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (n + kBasesThreads - 1) / kBasesThreads;
-    const int b = tid * per, e = min(n, b + per);
-    auto lens = [&](int idx, int64_t *L) {
-        const int k = ids ? ids[idx] : idx;
-        const int64_t *sz = sizes + int64_t(k) * SZ_N;
-        const int64_t nvo = m.I_V[k + 1] - m.I_V[k];
-        const int64_t nown = m.I_T[k + 1] - m.I_T[k];
-        const bool vt = mask & R_VT, vv = mask & R_VV, et = mask & R_ET, tt = mask & R_TT;
-        L[0] = vt ? nvo + 1 : 0;
-        L[1] = vt ? sz[SZ_VT] : 0;
-        L[2] = vv ? nvo + 1 : 0;
-        L[3] = vv ? sz[SZ_VV] : 0;
-        L[4] = et ? nvo + 1 : 0;
-        L[5] = et ? sz[SZ_E] : 0;
-        L[6] = et ? sz[SZ_E] + 1 : 0;
-        L[7] = et ? sz[SZ_ET] : 0;
-        L[8] = tt ? nown + 1 : 0;
-        L[9] = tt ? sz[SZ_TT] : 0;
-    };
-    int64_t acc[NA];
-    for (int a = 0; a < NA; ++a) acc[a] = 0;
-    for (int i = b; i < e; ++i) {
-        int64_t L[NA];
-        lens(i, L);
-        for (int a = 0; a < NA; ++a) acc[a] += L[a];
-    }
+// Output placement: exclusive scans, over the listed clusters, of the
+// lengths of the ten output arrays, then one work item per cluster with its
+// output pointers.  Three launches: block sums, a scan of the block sums,
+// then per-block scans that write the items.  arrays_base holds the base
+// pointers of the ten output arrays (its k / mask / blk fields are ignored).
+constexpr int kBasesThreads = 256;
+constexpr int NA = 10;
+
+__device__ __forceinline__ void item_lengths(const DevMesh &m, const int32_t *ids, const int64_t *sizes,
+                                             uint32_t mask, int idx, int64_t *L) {
+    const int k = ids ? ids[idx] : idx;
+    const int64_t *sz = sizes + int64_t(k) * SZ_N;
+    const int64_t nvo = m.I_V[k + 1] - m.I_V[k];
+    const int64_t nown = m.I_T[k + 1] - m.I_T[k];
+    const bool vt = mask & R_VT, vv = mask & R_VV, et = mask & R_ET, tt = mask & R_TT;
+    L[0] = vt ? nvo + 1 : 0;
+    L[1] = vt ? sz[SZ_VT] : 0;
+    L[2] = vv ? nvo + 1 : 0;
+    L[3] = vv ? sz[SZ_VV] : 0;
+    L[4] = et ? nvo + 1 : 0;
+    L[5] = et ? sz[SZ_E] : 0;
+    L[6] = et ? sz[SZ_E] + 1 : 0;
+    L[7] = et ? sz[SZ_ET] : 0;
+    L[8] = tt ? nown + 1 : 0;
+    L[9] = tt ? sz[SZ_TT] : 0;
+}
+
+// block-wide exclusive scan of NA int64 values per thread; totals -> tot[]
+__device__ __forceinline__ void block_scan_na(int64_t *v, int64_t (*s_warp)[NA], int64_t *tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int64_t incl[NA];
+#pragma unroll
     for (int a = 0; a < NA; ++a) {
-        int64_t v = acc[a];
+        int64_t x = v[a];
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(FULL, v, o);
-            if (lane >= o) v += y;
+            const int64_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
         }
-        incl[a] = v;
-        if (lane == 31) s_warp[warp][a] = v;
+        incl[a] = x;
+        if (lane == 31) s_warp[warp][a] = x;
     }
     __syncthreads();
     if (warp == 0) {
+#pragma unroll
         for (int a = 0; a < NA; ++a) {
-            const int64_t w = s_warp[lane][a];
-            int64_t v = w;
+            const int64_t w = lane < nw ? s_warp[lane][a] : 0;
+            int64_t x = w;
+#pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int64_t y = __shfl_up_sync(FULL, v, o);
-                if (lane >= o) v += y;
+                const int64_t y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
             }
-            s_warp[lane][a] = v - w;
-            if (lane == 31) s_tot[a] = v;
+            if (lane < nw) s_warp[lane][a] = x - w;
+            if (lane == 31) tot[a] = x;
         }
     }
     __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NA; ++a) v[a] = s_warp[warp][a] + incl[a] - v[a];
+}
+
+__global__ void __launch_bounds__(kBasesThreads) bases_sum_kernel(DevMesh m, const int32_t *ids, int32_t n,
+                                                                  const int64_t *sizes, uint32_t mask,
+                                                                  int64_t *bsum) {
+    __shared__ int64_t s_warp[32][NA];
+    __shared__ int64_t s_tot[NA];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t L[NA];
+    if (idx < n) item_lengths(m, ids, sizes, mask, idx, L);
+    else
+        for (int a = 0; a < NA; ++a) L[a] = 0;
+    block_scan_na(L, s_warp, s_tot);
+    if (threadIdx.x < NA) bsum[int64_t(blockIdx.x) * NA + threadIdx.x] = s_tot[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kBasesThreads) bases_scan_kernel(int32_t nblocks, int64_t *bsum,
+                                                                   int64_t *totals) {
+    __shared__ int64_t s_warp[32][NA];
+    __shared__ int64_t s_tot[NA];
+    __shared__ int64_t s_run[NA];
+    if (threadIdx.x < NA) s_run[threadIdx.x] = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblocks; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        int64_t v[NA];
+        for (int a = 0; a < NA; ++a) v[a] = b < nblocks ? bsum[int64_t(b) * NA + a] : 0;
+        block_scan_na(v, s_warp, s_tot);
+        if (b < nblocks)
+            for (int a = 0; a < NA; ++a) bsum[int64_t(b) * NA + a] = v[a] + s_run[a];
+        __syncthreads();
+        if (threadIdx.x < NA) s_run[threadIdx.x] += s_tot[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x < NA) totals[threadIdx.x] = s_run[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kBasesThreads) bases_write_kernel(DevMesh m, const int32_t *ids, int32_t n,
+                                                                    const int64_t *sizes, uint32_t mask,
+                                                                    const WorkItem *arrays_base,
+                                                                    const int64_t *bsum, WorkItem *items) {
+    __shared__ int64_t s_warp[32][NA];
+    __shared__ int64_t s_tot[NA];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t L[NA];
+    if (idx < n) item_lengths(m, ids, sizes, mask, idx, L);
+    else
+        for (int a = 0; a < NA; ++a) L[a] = 0;
     int64_t run[NA];
-    for (int a = 0; a < NA; ++a) run[a] = s_warp[warp][a] + incl[a] - acc[a];
+    for (int a = 0; a < NA; ++a) run[a] = L[a];
+    block_scan_na(run, s_warp, s_tot);
+    if (idx >= n) return;
+    const int64_t *bb = bsum + int64_t(blockIdx.x) * NA;
     int32_t *base[NA] = {arrays_base->vt_off, arrays_base->vt_val, arrays_base->vv_off, arrays_base->vv_val,
                          arrays_base->eu_off, arrays_base->e_w,    arrays_base->et_off, arrays_base->et_val,
                          arrays_base->tt_off, arrays_base->tt_val};
-    for (int i = b; i < e; ++i) {
-        int64_t L[NA];
-        lens(i, L);
-        const int k = ids ? ids[i] : i;
-        WorkItem w;
-        w.k = k;
-        w.mask = mask;
-        w.blk = m.blk_off[k];
-        int32_t *p[NA];
-        for (int a = 0; a < NA; ++a) p[a] = base[a] ? base[a] + run[a] : nullptr;
-        w.vt_off = p[0]; w.vt_val = p[1]; w.vv_off = p[2]; w.vv_val = p[3];
-        w.eu_off = p[4]; w.e_w = p[5]; w.et_off = p[6]; w.et_val = p[7];
-        w.tt_off = p[8]; w.tt_val = p[9];
-        items[i] = w;
-        for (int a = 0; a < NA; ++a) run[a] += L[a];
-    }
-    if (tid < NA) totals[tid] = s_tot[tid];
+    const int k = ids ? ids[idx] : idx;
+    WorkItem w;
+    w.k = k;
+    w.mask = mask;
+    w.blk = m.blk_off[k];
+    int32_t *p[NA];
+    for (int a = 0; a < NA; ++a) p[a] = base[a] ? base[a] + bb[a] + run[a] : nullptr;
+    w.vt_off = p[0]; w.vt_val = p[1]; w.vv_off = p[2]; w.vv_val = p[3];
+    w.eu_off = p[4]; w.e_w = p[5]; w.et_off = p[6]; w.et_val = p[7];
+    w.tt_off = p[8]; w.tt_val = p[9];
+    items[idx] = w;
 }
 
 }  // namespace
@@ -836,10 +879,16 @@ int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids
     return int(cudaGetLastError());
 }
 
+int bases_scratch_words(int32_t n) { return ((n + kBasesThreads - 1) / kBasesThreads) * NA; }
+
 int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t *sizes, uint32_t mask,
-                 const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, void *stream) {
+                 const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, int64_t *bsum, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    bases_kernel<<<1, kBasesThreads, 0, s>>>(m, ids, n, sizes, mask, arrays_base, items, totals_out);
+    const int nb = (n + kBasesThreads - 1) / kBasesThreads;
+    if (nb == 0) return 0;
+    bases_sum_kernel<<<nb, kBasesThreads, 0, s>>>(m, ids, n, sizes, mask, bsum);
+    bases_scan_kernel<<<1, kBasesThreads, 0, s>>>(nb, bsum, totals_out);
+    bases_write_kernel<<<nb, kBasesThreads, 0, s>>>(m, ids, n, sizes, mask, arrays_base, bsum, items);
     return int(cudaGetLastError());
 }
 

@@ -32,6 +32,7 @@ struct NoAllocScratch {
     int32_t err;
     int32_t pad;
     int64_t totals[16];
+    int64_t bsum[(kNoAllocMaxClusters + 255) / 256 * 10 + 16];  // output placement block sums
 };
 
 // The scratch: ~430 KB of device global memory, shared by every call.  Host
@@ -119,7 +120,9 @@ extern "C" gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t 
         (e = cudaMemcpyAsync(&S->base, &base, sizeof(base), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(GALE_ECUDA, std::string("staging the work list: ") + cudaGetErrorString(e));
     const gale::DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, K};
-    int rc = gale::launch_bases(dm, S->ids, n, ctx->d_sizes, mask, &S->base, S->items, S->totals, s);
+    if (gale::bases_scratch_words(n) > int(sizeof(S->bsum) / sizeof(int64_t)))
+        return fail(GALE_EINVAL, "placement scratch too small");
+    int rc = gale::launch_bases(dm, S->ids, n, ctx->d_sizes, mask, &S->base, S->items, S->totals, S->bsum, s);
     for (int32_t b = 0; rc == 0 && b < nb; ++b) {
         const int32_t m = cnt[b + 1] - cnt[b];
         if (m == 0) continue;
