@@ -1,0 +1,91 @@
+"""Consumers of the cluster-relation producer: the lower-link critical-point
+classifier (standing in for the paper's CriticalPoints analysis, Section 5.2)
+and a multi-threaded serving driver.  Built against the public C ABI only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libgaleconsumers.so")
+_SRC = os.path.join(_HERE, "consumers.cpp")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    import paper_2507_15230_gb300 as gale
+    gl = gale._build.build()
+    os.makedirs(_BUILD, exist_ok=True)
+    deps = [_SRC, os.path.join(_ROOT, "include", "gale.h"), gl]
+    if not force and os.path.exists(_LIB) and all(os.path.getmtime(d) <= os.path.getmtime(_LIB) for d in deps):
+        return _LIB
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC, "-I", os.path.join(_ROOT, "include"),
+           "-I", os.path.join(cuda, "include"), "-L", os.path.dirname(gl), "-lgale", "-Wl,-rpath," + os.path.dirname(gl),
+           "-L", os.path.join(cuda, "lib64"), "-lcudart", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        import paper_2507_15230_gb300 as gale
+        gale.load_library()
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P, i32, i64, u32, u64, f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                      ctypes.c_uint64, ctypes.c_double)
+        lib.gale_cp_classify.argtypes = [P, P, P, i32, i32, P, P, P, P, P]
+        lib.gale_cp_classify.restype = ctypes.c_int
+        lib.gale_cp_serve_run.argtypes = [P, P, P, P, P, i32, i32, u32, u64, f64, P, P, P]
+        lib.gale_cp_serve_run.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def canonical_inputs(field: np.ndarray, vperm: np.ndarray):
+    """Field values and input ids in canonical vertex order."""
+    vperm = np.ascontiguousarray(vperm, dtype=np.int32)
+    return np.ascontiguousarray(field[vperm], dtype=np.float32), vperm
+
+
+def classify_cluster(f_c, inid_c, rows, v0, vt_off, vt_val, vv_off, vv_val) -> np.ndarray:
+    """Critical-point codes of one cluster's vertices from host CSR rows."""
+    lib = _load()
+    nvo = len(vt_off) - 1
+    out = np.empty(max(nvo, 1), np.int8)
+    arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (vt_off, vt_val, vv_off, vv_val)]
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    rc = lib.gale_cp_classify(_p(f_c), _p(inid_c), _p(rows), int(v0), nvo, *[_p(a) if a.size else None for a in arrs],
+                              _p(out))
+    if rc != 0:
+        raise RuntimeError("classifier: link too large")
+    return out[:nvo]
+
+
+def serve_run(ctx, f_c, inid_c, rows, I_V, nthreads=16, mask=15, seed=6, jump_prob=0.1):
+    """Run the serving driver; returns (codes int8[nv], latencies float64[K],
+    dict(wall, requests, d2h_bytes, failures))."""
+    lib = _load()
+    K = len(I_V) - 1
+    cls = np.full(len(f_c), -9, np.int8)
+    lat = np.zeros(K, np.float64)
+    st = np.zeros(4, np.float64)
+    I_V = np.ascontiguousarray(I_V, dtype=np.int64)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    lib.gale_cp_serve_run(ctx._h, _p(f_c), _p(inid_c), _p(rows), _p(I_V), K, nthreads, mask, seed, jump_prob,
+                          _p(cls), _p(lat), _p(st))
+    return cls, lat, {"wall": st[0], "requests": int(st[1]), "d2h_bytes": int(st[2]), "failures": int(st[3])}

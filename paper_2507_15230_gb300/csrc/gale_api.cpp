@@ -173,6 +173,29 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     return GALE_OK;
 }
 
+}  // namespace
+
+namespace gale {
+// One shared-memory plan covering every cluster (the serving loop takes any
+// cluster); *fits = it fits one CTA.
+SmemPlan serve_plan(gale_ctx *ctx, bool *fits) {
+    Caps c{};
+    int threads = 64;
+    bool first = true;
+    for (const auto &b : ctx->bins) {
+        c = first ? b.plan.caps : merge(c, b.plan.caps);
+        threads = std::max(threads, b.plan.threads);
+        first = false;
+    }
+    SmemPlan p = plan_smem(c, threads);
+    *fits = !ctx->bins.empty() && p.total <= kernel_smem_limit();
+    if (*fits) prepare_kernels(std::max(p.total, 0));
+    return p;
+}
+}  // namespace gale
+
+namespace {
+
 gale_status upload_orders(gale_ctx *ctx) {
     std::vector<int32_t> order;  // positions in the all-clusters item list (= cluster ids)
     ctx->order_all_off.assign(1, 0);

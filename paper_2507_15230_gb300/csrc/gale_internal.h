@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <vector>
+
 #if defined(__CUDACC__)
 #define GALE_HD __host__ __device__
 #else
@@ -169,6 +171,22 @@ int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, 
 // One launch, one CTA, one work item (the per-cluster baseline form).
 int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,
                      void *stream);
+// Ring of the device-resident serving loop (all host pointers are mapped
+// host memory seen through device addresses).
+struct ServeRing {
+    const WorkItem *items;        // [cap]
+    const long long *tail;        // tickets published so far
+    long long *done;              // [cap] last ticket completed in each slot
+    const int *stop;              // non-zero: loop returns
+    unsigned long long *next;     // device memory: next ticket to claim
+    int32_t cap;
+    int32_t pad;
+    unsigned long long idle_ns;   // a CTA returns after this long without work
+};
+int launch_serve(const DevMesh &m, const SmemPlan &plan, const ServeRing &ring, int32_t *err, int grid, void *stream);
+int serve_ctas_per_sm(const SmemPlan &plan);
+SmemPlan merged_plan(const std::vector<SmemPlan> &plans);
+
 int kernel_smem_limit();
 int max_ctas_per_sm(const SmemPlan &plan);
 void prepare_kernels(int smem);

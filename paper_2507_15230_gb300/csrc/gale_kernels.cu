@@ -660,6 +660,84 @@ __global__ void build_one_kernel(DevMesh m, SmemPlan plan, const WorkItem *items
     run_cluster<false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err);
 }
 
+// ---------------------------------------------------------------------------
+// Device-resident serving loop.  Work items arrive in a ring in mapped host
+// memory; the host writes an item and then publishes its ticket by a release
+// store of the ring tail.  Each CTA claims the next published ticket (acquire
+// load of the tail at system scope, CAS on a device counter), builds the
+// cluster into the cache slot the item points to, then fences and stores the
+// ticket into the slot's done flag (release, system scope).  A CTA that finds
+// no published work sleeps and polls again; after idle_ns without a claim,
+// or when the host raises the stop flag, it returns.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long ld_acquire_sys(const long long *p) {
+    long long v;
+    asm volatile("ld.acquire.sys.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_sys32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(long long *p, long long v) {
+    asm volatile("st.release.sys.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void serve_kernel(DevMesh m, SmemPlan plan, ServeRing ring, int32_t *err) {
+    extern __shared__ __align__(16) char smem[];
+    const Smem S = carve(smem, plan);
+    __shared__ long long s_t;
+    __shared__ WorkItem s_item;
+    unsigned long long last = globaltimer();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long t = -1;
+            unsigned sleep_ns = 256;
+            for (;;) {
+                if (ld_acquire_sys32(ring.stop)) break;
+                const long long pub = ld_acquire_sys(ring.tail);
+                const unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(ring.next);
+                if ((long long)cur < pub) {
+                    if (atomicCAS(ring.next, cur, cur + 1ull) == cur) {
+                        t = (long long)cur;
+                        break;
+                    }
+                    continue;
+                }
+                if (globaltimer() - last > ring.idle_ns) break;
+                __nanosleep(sleep_ns);
+                if (sleep_ns < 8192) sleep_ns *= 2;
+            }
+            if (t >= 0) {
+                const int slot = int(t % ring.cap);
+                const volatile int32_t *src = reinterpret_cast<const volatile int32_t *>(ring.items + slot);
+                int32_t *dst = reinterpret_cast<int32_t *>(&s_item);
+                for (int w = 0; w < int(sizeof(WorkItem) / 4); ++w) dst[w] = src[w];
+            }
+            s_t = t;
+        }
+        __syncthreads();
+        const long long t = s_t;
+        if (t < 0) break;
+        if (s_item.k >= 0 && s_item.k < m.K)
+            run_cluster<false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err);
+        else if (threadIdx.x == 0)
+            atomicOr(err, ERR_BAD_ITEM);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence_system();
+            st_release_sys(ring.done + (t % ring.cap), t);
+        }
+        last = globaltimer();
+    }
+}
+
 // Output placement: exclusive scans, over the listed clusters, of the
 // lengths of the ten output arrays, then one work item per cluster with its
 // output pointers.  Three launches: block sums, a scan of the block sums,
@@ -898,6 +976,22 @@ int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, 
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
     build_kernel<<<grid, plan.threads, plan.total, s>>>(m, plan, items, order, n, err, ticket);
     return int(cudaGetLastError());
+}
+
+int launch_serve(const DevMesh &m, const SmemPlan &plan, const ServeRing &ring, int32_t *err, int grid,
+                 void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
+    serve_kernel<<<grid, plan.threads, plan.total, s>>>(m, plan, ring, err);
+    return int(cudaGetLastError());
+}
+
+int serve_ctas_per_sm(const SmemPlan &plan) {
+    int a = 0;
+    cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, serve_kernel, plan.threads, plan.total) != cudaSuccess)
+        return 0;
+    return a;
 }
 
 int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,

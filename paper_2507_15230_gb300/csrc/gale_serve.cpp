@@ -1,33 +1,613 @@
-// Serving path: consumer requests, batching, HBM-budgeted relation cache.
+// Serving: consumer requests for whole clusters (Section 4.4), admitted
+// against an HBM budget, built on the device and kept in an LRU relation
+// cache (Section 4.5's leader producer, re-designed).
+//
+// A consumer thread calls gale_request(cluster, mask).  A cached entry whose
+// mask covers the request is a hit: it is pinned and returned at once.  A
+// miss creates an entry and queues it for the leader thread, which
+//   - admits queued entries in arrival order against the budget: each gets a
+//     slot in one device slab (first fit, coalescing free list), evicting
+//     unpinned ready entries least-recently-used first;
+//   - writes each admitted entry's work item (its cluster, mask and output
+//     pointers into its slot) into a ring in pinned, mapped host memory and
+//     publishes its ticket (release store of the ring tail);
+//   - keeps the device-resident loop running: persistent CTAs claim
+//     published tickets, build, and store the ticket into the slot's done
+//     flag; the loop exits after an idle period and is relaunched when
+//     published work is pending;
+//   - polls the done flags, marks entries ready and wakes the waiters.
+// Requests that arrive while others are on the device are admitted as slots
+// and memory free up and are picked up by the running loop without a new
+// launch (continuous batching).  When the merged shared-memory plan of all
+// size bins does not fit one CTA, the leader instead launches the persistent
+// build kernel per bin for each batch of admitted entries and completes them
+// through a CUDA event (launch mode).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <thread>
+#include <unordered_map>
 
 #include "gale_ctx.h"
 
 namespace gale {
-void serve_destroy(gale_ctx *ctx) { (void)ctx; }
+
+// defined in gale_api.cpp
+SmemPlan serve_plan(gale_ctx *ctx, bool *fits);
+
+namespace {
+
+constexpr int32_t kRingCap = 4096;
+constexpr int64_t kAlign = 256;
+
+enum class St { Queued, Building, Ready, Failed };
+
+struct Entry {
+    int32_t k;
+    uint32_t mask;
+    St state = St::Queued;
+    int32_t refs = 0;
+    int64_t off = -1, bytes = 0;  // slot in the slab
+    int64_t ticket = -1;
+    gale_status fail = GALE_OK;
+    WorkItem item{};
+    int64_t n_edges = 0;
+    std::list<Entry *>::iterator lru;  // valid when Ready and unpinned-or-pinned (always in lru when Ready)
+    bool in_lru = false;
+};
+
+// first-fit allocator over [0, cap) with a coalescing free list
+struct Slab {
+    std::map<int64_t, int64_t> free;  // offset -> size
+    int64_t cap = 0, used = 0;
+    void init(int64_t c) {
+        cap = c;
+        free.clear();
+        if (c > 0) free[0] = c;
+        used = 0;
+    }
+    int64_t alloc(int64_t n) {
+        for (auto it = free.begin(); it != free.end(); ++it) {
+            if (it->second < n) continue;
+            const int64_t off = it->first, sz = it->second;
+            free.erase(it);
+            if (sz > n) free[off + n] = sz - n;
+            used += n;
+            return off;
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t n) {
+        used -= n;
+        auto it = free.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free.erase(nx);
+        }
+        if (it != free.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free.erase(it);
+            }
+        }
+    }
+};
+
+}  // namespace
+
+struct Serve {
+    gale_ctx *ctx = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_done;   // entries became ready / failed
+    std::condition_variable cv_leader; // work for the leader
+    std::unordered_map<int64_t, std::unique_ptr<Entry>> entries;  // key = k * 16 + mask
+    std::deque<Entry *> queue;           // waiting for admission
+    std::list<Entry *> lru;              // ready entries, most recent first
+    Slab slab;
+    char *slab_base = nullptr;
+    bool stop = false;
+    std::thread leader;
+    gale_serve_stats stats{};
+
+    // device loop
+    bool loop_mode = true;
+    SmemPlan plan{};
+    int grid = 0;
+    WorkItem *h_items = nullptr;   // mapped
+    long long *h_tail = nullptr;   // mapped
+    long long *h_done = nullptr;   // mapped [cap]
+    int *h_stop = nullptr;         // mapped
+    WorkItem *d_items = nullptr;
+    long long *d_tail = nullptr, *d_done = nullptr;
+    int *d_stop = nullptr;
+    unsigned long long *d_next = nullptr;
+    int32_t *d_err = nullptr;
+    cudaStream_t loop_stream = nullptr;
+    cudaEvent_t loop_event = nullptr;
+    bool loop_launched = false;
+    long long published = 0;      // tickets published
+    std::map<long long, Entry *> inflight;  // ticket -> entry
+    uint64_t idle_ns = 20ull * 1000 * 1000;
+
+    // launch mode
+    WorkItem *d_batch = nullptr;   // [kRingCap] device work items
+    int32_t *d_border = nullptr;   // [kRingCap] per-bin order
+    int32_t *d_tick = nullptr;     // [64] tickets
+    WorkItem *h_batch = nullptr;   // pinned staging
+    int32_t *h_border = nullptr;
+    cudaEvent_t batch_event = nullptr;
+    std::vector<Entry *> batch_entries;
+    bool batch_busy = false;
+
+    gale_status init(gale_ctx *c);
+    void leader_loop();
+    bool admit(Entry *e);
+    void fill_item(Entry *e);
+    void publish_loop(Entry *e);
+    void poll_loop();
+    void launch_batch(std::vector<Entry *> &b);
+    void poll_batch();
+    void evict_for(int64_t bytes);
+    int64_t entry_bytes(int32_t k, uint32_t mask, int64_t *L);
+};
+
+namespace {
+
+gale_status fail(gale_status s, const std::string &msg) {
+    set_error(msg);
+    return s;
+}
+
+inline int64_t a256(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+int64_t Serve::entry_bytes(int32_t k, uint32_t mask, int64_t *L) {
+    const int64_t *sz = ctx->sizes.data() + size_t(5) * k;
+    const int64_t nvo = ctx->hm.I_V[k + 1] - ctx->hm.I_V[k];
+    const int64_t nown = ctx->hm.I_T[k + 1] - ctx->hm.I_T[k];
+    const bool vt = mask & GALE_VT, vv = mask & GALE_VV, et = mask & GALE_ET, tt = mask & GALE_TT;
+    L[0] = vt ? nvo + 1 : 0;
+    L[1] = vt ? sz[0] : 0;
+    L[2] = vv ? nvo + 1 : 0;
+    L[3] = vv ? sz[1] : 0;
+    L[4] = et ? nvo + 1 : 0;
+    L[5] = et ? sz[2] : 0;
+    L[6] = et ? sz[2] + 1 : 0;
+    L[7] = et ? sz[3] : 0;
+    L[8] = tt ? nown + 1 : 0;
+    L[9] = tt ? sz[4] : 0;
+    int64_t b = 0;
+    for (int a = 0; a < 10; ++a) b += (L[a] * 4 + 15) / 16 * 16;
+    return a256(b);
+}
+
+gale_status Serve::init(gale_ctx *c) {
+    ctx = c;
+    stats.cache_bytes_budget = ctx->cache_budget;
+    slab_base = static_cast<char *>(ctx->dalloc(size_t(ctx->cache_budget)));
+    if (!slab_base) return fail(GALE_ENOMEM, "device allocation of the relation cache failed");
+    slab.init(ctx->cache_budget);
+    bool fits = false;
+    plan = serve_plan(ctx, &fits);
+    const char *mode = getenv("GALE_SERVE_MODE");
+    loop_mode = fits && !(mode && strcmp(mode, "launch") == 0);
+    const char *idle = getenv("GALE_SERVE_IDLE_US");
+    if (idle) idle_ns = uint64_t(std::max(100.0, atof(idle))) * 1000ull;
+    auto ck = [](cudaError_t e) { return e == cudaSuccess; };
+    if (!ck(cudaHostAlloc(reinterpret_cast<void **>(&h_items), sizeof(WorkItem) * kRingCap, cudaHostAllocMapped)) ||
+        !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_tail), 64, cudaHostAllocMapped)) ||
+        !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_done), sizeof(long long) * kRingCap, cudaHostAllocMapped)) ||
+        !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_stop), 64, cudaHostAllocMapped)) ||
+        !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_batch), sizeof(WorkItem) * kRingCap, cudaHostAllocDefault)) ||
+        !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_border), sizeof(int32_t) * kRingCap, cudaHostAllocDefault)))
+        return fail(GALE_ENOMEM, "pinned host allocation for the serving ring failed");
+    *h_tail = 0;
+    *h_stop = 0;
+    for (int i = 0; i < kRingCap; ++i) h_done[i] = -1;
+    if (!ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_items), h_items, 0)) ||
+        !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_tail), h_tail, 0)) ||
+        !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_done), h_done, 0)) ||
+        !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_stop), h_stop, 0)))
+        return fail(GALE_ECUDA, "mapping the serving ring failed");
+    d_next = static_cast<unsigned long long *>(ctx->dalloc(64));
+    d_err = static_cast<int32_t *>(ctx->dalloc(64));
+    d_batch = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * kRingCap));
+    d_border = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * kRingCap));
+    d_tick = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * 64));
+    if (!d_next || !d_err || !d_batch || !d_border || !d_tick)
+        return fail(GALE_ENOMEM, "device allocation for the serving loop failed");
+    if (!ck(cudaStreamCreateWithFlags(&loop_stream, cudaStreamNonBlocking)) ||
+        !ck(cudaEventCreateWithFlags(&loop_event, cudaEventDisableTiming)) ||
+        !ck(cudaEventCreateWithFlags(&batch_event, cudaEventDisableTiming)) ||
+        !ck(cudaMemsetAsync(d_next, 0, 64, loop_stream)) || !ck(cudaMemsetAsync(d_err, 0, 64, loop_stream)) ||
+        !ck(cudaStreamSynchronize(loop_stream)))
+        return fail(GALE_ECUDA, "creating the serving stream failed");
+    if (loop_mode) {
+        const int per_sm = serve_ctas_per_sm(plan);
+        if (per_sm < 1) loop_mode = false;
+        else grid = per_sm * ctx->sm_count;
+    }
+    leader = std::thread([this] { leader_loop(); });
+    return GALE_OK;
+}
+
+void Serve::evict_for(int64_t bytes) {
+    // evict unpinned ready entries, least recently used first, until a free
+    // block of `bytes` exists or nothing more can go
+    for (;;) {
+        for (auto &f : slab.free)
+            if (f.second >= bytes) return;
+        auto victim = lru.end();
+        for (auto it = lru.end(); it != lru.begin();) {
+            --it;
+            if ((*it)->refs == 0) {
+                victim = it;
+                break;
+            }
+        }
+        if (victim == lru.end()) return;
+        Entry *e = *victim;
+        lru.erase(victim);
+        e->in_lru = false;
+        slab.release(e->off, e->bytes);
+        stats.evictions++;
+        entries.erase(int64_t(e->k) * 16 + e->mask);  // frees e
+    }
+}
+
+bool Serve::admit(Entry *e) {
+    int64_t L[10];
+    const int64_t bytes = entry_bytes(e->k, e->mask, L);
+    if (bytes > slab.cap) {
+        e->state = St::Failed;
+        e->fail = GALE_ENOMEM;
+        return true;
+    }
+    int64_t off = slab.alloc(bytes);
+    if (off < 0) {
+        evict_for(bytes);
+        off = slab.alloc(bytes);
+    }
+    if (off < 0) return false;  // budget pinned: wait for releases
+    e->off = off;
+    e->bytes = bytes;
+    fill_item(e);
+    return true;
+}
+
+void Serve::fill_item(Entry *e) {
+    int64_t L[10];
+    entry_bytes(e->k, e->mask, L);
+    int32_t *p[10];
+    char *cur = slab_base + e->off;
+    for (int a = 0; a < 10; ++a) {
+        p[a] = reinterpret_cast<int32_t *>(cur);
+        cur += (L[a] * 4 + 15) / 16 * 16;
+    }
+    const uint32_t m = e->mask;
+    WorkItem &w = e->item;
+    w.k = e->k;
+    w.mask = m;
+    w.blk = ctx->hm.blk_off[e->k];
+    w.vt_off = (m & GALE_VT) ? p[0] : nullptr;
+    w.vt_val = (m & GALE_VT) ? p[1] : nullptr;
+    w.vv_off = (m & GALE_VV) ? p[2] : nullptr;
+    w.vv_val = (m & GALE_VV) ? p[3] : nullptr;
+    w.eu_off = (m & GALE_ET) ? p[4] : nullptr;
+    w.e_w = (m & GALE_ET) ? p[5] : nullptr;
+    w.et_off = (m & GALE_ET) ? p[6] : nullptr;
+    w.et_val = (m & GALE_ET) ? p[7] : nullptr;
+    w.tt_off = (m & GALE_TT) ? p[8] : nullptr;
+    w.tt_val = (m & GALE_TT) ? p[9] : nullptr;
+    e->n_edges = ctx->sizes[size_t(5) * e->k + 2];
+}
+
+void Serve::publish_loop(Entry *e) {
+    const long long t = published;
+    const int slot = int(t % kRingCap);
+    h_items[slot] = e->item;
+    __atomic_store_n(h_tail, t + 1, __ATOMIC_RELEASE);
+    published = t + 1;
+    e->ticket = t;
+    e->state = St::Building;
+    inflight[t] = e;
+    if (!loop_launched || cudaEventQuery(loop_event) == cudaSuccess) {
+        // (re)start the loop; a previous one has drained or never ran
+        const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
+        ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns};
+        launch_serve(dm, plan, ring, d_err, grid, loop_stream);
+        cudaEventRecord(loop_event, loop_stream);
+        loop_launched = true;
+        stats.batches++;
+    }
+}
+
+void Serve::poll_loop() {
+    for (auto it = inflight.begin(); it != inflight.end();) {
+        const long long t = it->first;
+        if (__atomic_load_n(h_done + (t % kRingCap), __ATOMIC_ACQUIRE) == t) {
+            Entry *e = it->second;
+            e->state = St::Ready;
+            lru.push_front(e);
+            e->lru = lru.begin();
+            e->in_lru = true;
+            stats.builds++;
+            it = inflight.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    // published work with no loop running (it drained just before): restart
+    if (!inflight.empty() && loop_launched && cudaEventQuery(loop_event) == cudaSuccess) {
+        const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
+        ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns};
+        launch_serve(dm, plan, ring, d_err, grid, loop_stream);
+        cudaEventRecord(loop_event, loop_stream);
+        stats.batches++;
+    }
+}
+
+void Serve::launch_batch(std::vector<Entry *> &b) {
+    // per-bin order over the batch, largest working sets first
+    const int nb = int(ctx->bins.size());
+    std::vector<std::vector<int32_t>> per(nb);
+    for (int32_t i = 0; i < int32_t(b.size()); ++i) {
+        h_batch[i] = b[i]->item;
+        per[ctx->bin_of[b[i]->k]].push_back(i);
+    }
+    int32_t n = 0;
+    std::vector<int32_t> off(nb + 1, 0);
+    for (int bb = 0; bb < nb; ++bb) {
+        for (int32_t i : per[bb]) h_border[n++] = i;
+        off[bb + 1] = n;
+    }
+    cudaMemcpyAsync(d_batch, h_batch, sizeof(WorkItem) * b.size(), cudaMemcpyHostToDevice, loop_stream);
+    cudaMemcpyAsync(d_border, h_border, sizeof(int32_t) * n, cudaMemcpyHostToDevice, loop_stream);
+    const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
+    for (int bb = 0; bb < nb; ++bb) {
+        const int32_t m = off[bb + 1] - off[bb];
+        if (m == 0) continue;
+        launch_build(dm, ctx->bins[bb].plan, d_batch, d_border + off[bb], m, d_err, d_tick + bb,
+                     std::min(ctx->bins[bb].grid, m), loop_stream);
+    }
+    cudaEventRecord(batch_event, loop_stream);
+    for (Entry *e : b) e->state = St::Building;
+    batch_entries = b;
+    batch_busy = true;
+    stats.batches++;
+}
+
+void Serve::poll_batch() {
+    if (!batch_busy || cudaEventQuery(batch_event) != cudaSuccess) return;
+    for (Entry *e : batch_entries) {
+        e->state = St::Ready;
+        lru.push_front(e);
+        e->lru = lru.begin();
+        e->in_lru = true;
+        stats.builds++;
+    }
+    batch_entries.clear();
+    batch_busy = false;
+}
+
+void Serve::leader_loop() {
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(mu);
+    while (!stop) {
+        bool progressed = false;
+        // admission, in arrival order
+        std::vector<Entry *> batch;
+        while (!queue.empty()) {
+            Entry *e = queue.front();
+            if (!loop_mode && batch_busy) break;
+            if (loop_mode && published - (inflight.empty() ? published : inflight.begin()->first) >= kRingCap) break;
+            if (!admit(e)) break;
+            queue.pop_front();
+            progressed = true;
+            if (e->state == St::Failed) continue;
+            if (loop_mode) publish_loop(e);
+            else {
+                batch.push_back(e);
+                if (int(batch.size()) >= kRingCap) break;
+            }
+        }
+        if (!batch.empty()) launch_batch(batch);
+        const size_t before = inflight.size() + (batch_busy ? batch_entries.size() : 0);
+        if (loop_mode) poll_loop();
+        else poll_batch();
+        const size_t after = inflight.size() + (batch_busy ? batch_entries.size() : 0);
+        if (after != before || progressed) {
+            stats.max_batch = std::max<int64_t>(stats.max_batch, int64_t(before));
+            cv_done.notify_all();
+        }
+        stats.cache_bytes_used = slab.used;
+        if (after > 0 || !queue.empty()) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(10));
+            lk.lock();
+        } else {
+            cv_leader.wait_for(lk, std::chrono::milliseconds(50));
+        }
+    }
+}
+
+void serve_destroy(gale_ctx *ctx) {
+    Serve *s = ctx->serve;
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_leader.notify_all();
+    if (s->leader.joinable()) s->leader.join();
+    if (s->h_stop) __atomic_store_n(s->h_stop, 1, __ATOMIC_RELEASE);
+    if (s->loop_stream) cudaStreamSynchronize(s->loop_stream);
+    if (s->loop_event) cudaEventDestroy(s->loop_event);
+    if (s->batch_event) cudaEventDestroy(s->batch_event);
+    if (s->loop_stream) cudaStreamDestroy(s->loop_stream);
+    cudaFreeHost(s->h_items);
+    cudaFreeHost(s->h_tail);
+    cudaFreeHost(s->h_done);
+    cudaFreeHost(s->h_stop);
+    cudaFreeHost(s->h_batch);
+    cudaFreeHost(s->h_border);
+    delete s;
+    ctx->serve = nullptr;
+}
+
 }  // namespace gale
+
+using gale::Entry;
+using gale::St;
+
+namespace {
+
+gale_status fail(gale_status s, const std::string &msg) {
+    gale::set_error(msg);
+    return s;
+}
+
+std::mutex g_serve_init_mu;
+
+gale_status ensure_serve(gale_ctx *ctx) {
+    std::lock_guard<std::mutex> lk(g_serve_init_mu);
+    if (ctx->serve) return GALE_OK;
+    if (ctx->cache_budget <= 0) return fail(GALE_EINVAL, "serving needs cache_budget_bytes > 0 at load");
+    auto *s = new gale::Serve();
+    ctx->serve = s;
+    gale_status st = s->init(ctx);
+    if (st != GALE_OK) {
+        std::string keep = gale_last_error();
+        gale::serve_destroy(ctx);
+        return fail(st, keep);
+    }
+    return GALE_OK;
+}
+
+void fill_view(gale_ctx *ctx, Entry *e, gale_view *out) {
+    memset(out, 0, sizeof(*out));
+    const int32_t k = e->k;
+    out->cluster = k;
+    out->mask = e->mask;
+    out->v_begin = ctx->hm.I_V[k];
+    out->v_end = ctx->hm.I_V[k + 1];
+    out->t_begin = ctx->hm.I_T[k];
+    out->t_end = ctx->hm.I_T[k + 1];
+    out->n_edges = int32_t(e->n_edges);
+    const gale::WorkItem &w = e->item;
+    out->vt_off = w.vt_off;
+    out->vt_val = w.vt_val;
+    out->vv_off = w.vv_off;
+    out->vv_val = w.vv_val;
+    out->et_uoff = w.eu_off;
+    out->et_w = w.e_w;
+    out->et_off = w.et_off;
+    out->et_val = w.et_val;
+    out->tt_off = w.tt_off;
+    out->tt_val = w.tt_val;
+    out->handle = reinterpret_cast<uint64_t>(e);
+}
+
+}  // namespace
 
 extern "C" {
 
 gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64_t timeout_ns, gale_view *out) {
-    (void)ctx; (void)cluster_id; (void)mask; (void)timeout_ns; (void)out;
-    gale::set_error("serving is not built yet");
-    return GALE_ENOTFOUND;
+    if (!ctx || !out) return fail(GALE_EINVAL, "NULL argument");
+    if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
+    if (cluster_id < 0 || cluster_id >= ctx->hm.K) return fail(GALE_EINVAL, "cluster id out of range");
+    if (mask == 0 || (mask & ~ctx->precond))
+        return fail(GALE_EINVAL, "mask must be a non-empty subset of the precondition mask");
+    gale_status st = ensure_serve(ctx);
+    if (st != GALE_OK) return st;
+    gale::Serve *s = ctx->serve;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns > 0 ? timeout_ns : 0);
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->stats.requests++;
+    Entry *e = nullptr;
+    // a cached entry whose mask covers the request
+    for (uint32_t m = 1; m < 16 && !e; ++m) {
+        if ((m & mask) != mask) continue;
+        auto it = s->entries.find(int64_t(cluster_id) * 16 + m);
+        if (it != s->entries.end() && it->second->state != St::Failed) e = it->second.get();
+    }
+    if (e && e->state == St::Ready) {
+        s->stats.hits++;
+        e->refs++;
+        s->lru.splice(s->lru.begin(), s->lru, e->lru);
+        fill_view(ctx, e, out);
+        return GALE_OK;
+    }
+    if (!e) {
+        s->stats.misses++;
+        auto ne = std::make_unique<Entry>();
+        ne->k = cluster_id;
+        ne->mask = mask;
+        e = ne.get();
+        s->entries[int64_t(cluster_id) * 16 + mask] = std::move(ne);
+        s->queue.push_back(e);
+        s->cv_leader.notify_all();
+    }
+    e->refs++;
+    auto ready = [&] { return e->state == St::Ready || e->state == St::Failed; };
+    if (timeout_ns > 0) {
+        if (!s->cv_done.wait_until(lk, deadline, ready)) {
+            e->refs--;
+            return fail(GALE_ETIMEOUT, "request timed out");
+        }
+    } else {
+        s->cv_done.wait(lk, ready);
+    }
+    if (e->state == St::Failed) {
+        const gale_status f = e->fail;
+        e->refs--;
+        if (e->refs == 0) s->entries.erase(int64_t(e->k) * 16 + e->mask);
+        return fail(f, "cluster relations exceed the whole cache budget");
+    }
+    fill_view(ctx, e, out);
+    return GALE_OK;
 }
 
 gale_status gale_release(gale_ctx *ctx, gale_view *view) {
-    (void)ctx; (void)view;
+    if (!ctx || !view) return fail(GALE_EINVAL, "NULL argument");
+    if (!ctx->serve || view->handle == 0) return fail(GALE_ENOTFOUND, "not a serving view");
+    gale::Serve *s = ctx->serve;
+    std::lock_guard<std::mutex> lk(s->mu);
+    Entry *e = reinterpret_cast<Entry *>(view->handle);
+    auto it = s->entries.find(int64_t(e->k) * 16 + e->mask);
+    if (it == s->entries.end() || it->second.get() != e || e->refs <= 0)
+        return fail(GALE_ENOTFOUND, "view is not pinned");
+    e->refs--;
+    view->handle = 0;
+    s->cv_leader.notify_all();  // a pinned budget may have freed up
     return GALE_OK;
 }
 
 gale_status gale_serve_stats_get(gale_ctx *ctx, gale_serve_stats *out) {
-    (void)ctx;
-    if (out) memset(out, 0, sizeof(*out));
+    if (!ctx || !out) return fail(GALE_EINVAL, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->cache_bytes_budget = ctx->cache_budget;
+    if (!ctx->serve) return GALE_OK;
+    std::lock_guard<std::mutex> lk(ctx->serve->mu);
+    *out = ctx->serve->stats;
+    out->cache_bytes_used = ctx->serve->slab.used;
+    out->cache_bytes_budget = ctx->cache_budget;
     return GALE_OK;
 }
 
 gale_status gale_autotune(gale_ctx *ctx, uint32_t mask) {
-    (void)ctx; (void)mask;
+    (void)ctx;
+    (void)mask;
     return GALE_OK;
 }
 

@@ -1,0 +1,140 @@
+"""Serving (gale_request / gale_release): continuous batching through the
+device-resident loop (or the launch-per-batch mode), the HBM-budgeted LRU
+cache, admission against the budget, and the critical-point consumer.
+
+Every served result must equal the same cluster's relations built alone by
+the bulk path, bit for bit, whatever else is in flight."""
+import os
+import threading
+
+import numpy as np
+import pytest
+
+import gen
+import paper_2507_15230_gb300 as gale
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def bulk_reference(ctx, mask=gale.ALL):
+    """Per-cluster relations from the bulk path, each cluster built alone."""
+    ref = {}
+    for k in range(ctx.K):
+        ctx.build(np.array([k], np.int32), mask, gale.MODE_BATCHED)
+        ctx.synchronize()
+        ref[k] = gale.view_to_numpy(ctx.bulk_view(0))
+    return ref
+
+
+def same(a, b):
+    return a.keys() == b.keys() and all(np.array_equal(a[n], b[n]) for n in a)
+
+
+def run_mix(budget, nthreads=8, rounds=40, masks=(gale.ALL, gale.VT | gale.VV | gale.TT, gale.ET)):
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0, cache_budget_bytes=budget) as ctx:
+        refs = {mk: bulk_reference(ctx, mk) for mk in masks}
+        errors = []
+
+        def consumer(seed):
+            rng = np.random.default_rng(seed)
+            for _ in range(rounds):
+                k = int(rng.integers(ctx.K))
+                mk = masks[int(rng.integers(len(masks)))]
+                v = ctx.request(k, mk, timeout_ns=20_000_000_000)
+                got = gale.view_to_numpy(v)
+                want = {n: a for n, a in refs[mk][k].items()}
+                # a cached superset entry may serve a narrower mask
+                got = {n: got[n] for n in want}
+                if not same(got, want):
+                    errors.append((k, mk))
+                ctx.release(v)
+
+        th = [threading.Thread(target=consumer, args=(i,)) for i in range(nthreads)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        stats = ctx.serve_stats()
+        return errors, stats
+
+
+@pytest.mark.parametrize("mode", ["loop", "launch"])
+def test_results_same_alone_and_in_mix(mode, monkeypatch):
+    monkeypatch.setenv("GALE_SERVE_MODE", mode)
+    errors, stats = run_mix(64 << 20)
+    assert not errors
+    assert stats.requests == 8 * 40 and stats.builds > 0 and stats.hits > 0
+
+
+def test_lru_evicts_under_tiny_budget():
+    errors, stats = run_mix(256 << 10, nthreads=4, rounds=30)
+    assert not errors
+    assert stats.evictions > 0
+    assert stats.cache_bytes_used <= 256 << 10
+
+
+def entry_bytes(ctx, k):
+    """Cache footprint of one cluster's four relations (16-byte aligned
+    arrays, 256-byte aligned entry)."""
+    I_V, I_T, sizes = ctx.intervals()
+    nvo, nown = int(I_V[k + 1] - I_V[k]), int(I_T[k + 1] - I_T[k])
+    vt, vv, ne, et, tt = (int(x) for x in sizes[k])
+    lens = [nvo + 1, vt, nvo + 1, vv, nvo + 1, ne, ne + 1, et, nown + 1, tt]
+    b = sum((4 * n + 15) // 16 * 16 for n in lens)
+    return (b + 255) // 256 * 256
+
+
+def test_admission_waits_for_release():
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0) as probe:
+        sz = [entry_bytes(probe, k) for k in range(3)]
+    budget = sz[0] + sz[1] + min(sz[2], min(sz[0], sz[1])) // 2  # two fit, not three
+    with gale.Context.load(m, device=0, cache_budget_bytes=budget) as ctx:
+        a = ctx.request(0, gale.ALL, timeout_ns=10_000_000_000)
+        b = ctx.request(1, gale.ALL, timeout_ns=10_000_000_000)
+        got = {}
+
+        def late():
+            got["v"] = ctx.request(2, gale.ALL, timeout_ns=20_000_000_000)
+
+        t = threading.Thread(target=late)
+        t.start()
+        t.join(timeout=1.0)
+        blocked = t.is_alive()
+        ctx.release(a)
+        ctx.release(b)
+        t.join(timeout=20)
+        assert blocked and "v" in got
+        ctx.release(got["v"])
+        assert ctx.serve_stats().evictions >= 1
+
+
+def test_oversized_request_is_rejected():
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0, cache_budget_bytes=4096) as ctx:
+        with pytest.raises(gale.GaleError) as ei:
+            ctx.request(0, gale.ALL, timeout_ns=5_000_000_000)
+        assert ei.value.status == 2
+
+
+def test_serving_driver_matches_oracle_classification():
+    import consumers
+    import oracle
+    m = gen.small_grid(with_field=True)
+    with gale.Context.load(m, device=0, cache_budget_bytes=8 << 20) as ctx:
+        vperm, _ = ctx.permutations()
+        f_c, inid = consumers.canonical_inputs(m.field, vperm)
+        rows = ctx.rows()
+        I_V, _, _ = ctx.intervals()
+        cls, lat, st = consumers.serve_run(ctx, f_c, inid, rows, I_V, nthreads=8, mask=gale.VT | gale.VV | gale.TT)
+        assert st["failures"] == 0 and st["requests"] == ctx.K
+        assert np.all(lat > 0)
+    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
+    want = np.empty(m.nv, np.int8)
+    for k in range(m.nclusters):
+        v = oracle.cluster_view(rel, canon, k)
+        want[canon["I_V"][k]:canon["I_V"][k + 1]] = consumers.classify_cluster(
+            f_c, inid, canon["rows"], canon["I_V"][k], v["vt_off"], v["vt_val"], v["vv_off"], v["vv_val"])
+    assert np.array_equal(cls, want)
