@@ -184,6 +184,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--per-cluster-sample", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-threads", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=8.0)
+    ap.add_argument("--serve-baseline-clusters", type=int, default=2048)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -201,7 +205,7 @@ def main():
 
     torch.cuda.set_device(local)
     mesh = gen.scale_grid(args.grid)
-    ctx = gale.Context.load(mesh, device=local)
+    ctx = gale.Context.load(mesh, device=local, cache_budget_bytes=int(args.serve_budget_gb * (1 << 30)))
     info = ctx.info()
     stream = torch.cuda.ExternalStream(ctx.stream_handle)
 
@@ -290,6 +294,10 @@ def main():
                "sample": f"{CPU_SAMPLE_N}^3 grid of the same recipe ({tets} tets, {ncl} clusters), "
                          f"whole oracle pipeline, single thread; host has {host_cores()} cores"}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serve_leg(args, mesh, ctx, gale)
+
     traffic = None
     tp = os.path.join(ROOT, "profiles", "build_kernel_traffic.json")
     if os.path.exists(tp):
@@ -321,6 +329,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
             "per_cluster": per_cluster,
+            "serving": serving,
             "load_seconds": {"host": info.load_host_seconds, "device": info.load_device_seconds},
             "bins": ctx.bins(),
         }
@@ -328,6 +337,55 @@ def main():
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def serve_leg(args, mesh, ctx, gale):
+    """Critical-point consumers (16 threads) classify every vertex through
+    gale_request (VT+VV+TT, HBM-budgeted cache, device-resident loop); the
+    baseline serves a bounded subset with one kernel launch per request."""
+    import consumers
+    import gen
+    n = args.grid
+    field = gen.gaussian_field(mesh.xyz, 16, [0, 0, 0], [n, n, n], 4)
+    vperm, _ = ctx.permutations()
+    f_c, inid = consumers.canonical_inputs(field, vperm)
+    rows = ctx.rows()
+    I_V, I_T, _ = ctx.intervals()
+    mask = gale.VT | gale.VV | gale.TT
+
+    def summarize(lat, st, nclusters):
+        lat = lat[:nclusters]
+        tets = int(I_T[nclusters] - I_T[0])
+        return {"requests": st["requests"], "failures": st["failures"],
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "wall_s": st["wall"], "tets_per_s": tets / st["wall"], "d2h_bytes": st["d2h_bytes"]}
+
+    ctx.serve_configure(gale.SERVE_LOOP)
+    cls, lat, st = consumers.serve_run(ctx, f_c, inid, rows, I_V, nthreads=args.serve_threads, mask=mask)
+    loop = summarize(lat, st, ctx.K)
+    s = ctx.serve_stats()
+    loop.update({"builds": s.builds, "hits": s.hits, "evictions": s.evictions, "loop_launches": s.batches,
+                 "critical_points": {str(c): int((cls == c).sum()) for c in (0, 1, 2, 3, 4)}})
+    base = None
+    nb = min(args.serve_baseline_clusters, ctx.K)
+    if nb > 0:
+        with gale.Context.load(mesh, device=0, cache_budget_bytes=int(args.serve_budget_gb * (1 << 30))) as c2:
+            c2.serve_configure(gale.SERVE_SINGLE)
+            _, lat2, st2 = consumers.serve_run(c2, f_c, inid, rows, I_V, nthreads=args.serve_threads, mask=mask,
+                                               max_clusters=nb)
+            base = summarize(lat2, st2, nb)
+            base["clusters"] = nb
+        # the same subset through the loop, fresh cache
+        with gale.Context.load(mesh, device=0, cache_budget_bytes=int(args.serve_budget_gb * (1 << 30))) as c3:
+            c3.serve_configure(gale.SERVE_LOOP)
+            _, lat3, st3 = consumers.serve_run(c3, f_c, inid, rows, I_V, nthreads=args.serve_threads, mask=mask,
+                                               max_clusters=nb)
+            loop_sub = summarize(lat3, st3, nb)
+            loop_sub["clusters"] = nb
+    return {"workload": f"{args.serve_threads} critical-point consumer threads, kd-order walks with 10% random "
+                        f"jumps, VT+VV+TT requests, {args.serve_budget_gb:g} GB cache budget, field = 16 Gaussians",
+            "device_loop": loop, "per_request_launch_subset": base,
+            "device_loop_same_subset": loop_sub if nb > 0 else None}
 
 
 def gale_kernel_sha() -> str:

@@ -76,11 +76,14 @@ def classify_cluster(f_c, inid_c, rows, v0, vt_off, vt_val, vv_off, vv_val) -> n
     return out[:nvo]
 
 
-def serve_run(ctx, f_c, inid_c, rows, I_V, nthreads=16, mask=15, seed=6, jump_prob=0.1):
-    """Run the serving driver; returns (codes int8[nv], latencies float64[K],
+def serve_run(ctx, f_c, inid_c, rows, I_V, nthreads=16, mask=15, seed=6, jump_prob=0.1, max_clusters=None):
+    """Run the serving driver over clusters [0, max_clusters) (all by
+    default); returns (codes int8[nv], latencies float64[K],
     dict(wall, requests, d2h_bytes, failures))."""
     lib = _load()
     K = len(I_V) - 1
+    if max_clusters is not None:
+        K = min(K, int(max_clusters))
     cls = np.full(len(f_c), -9, np.int8)
     lat = np.zeros(K, np.float64)
     st = np.zeros(4, np.float64)

@@ -109,6 +109,7 @@ int gale_cp_classify(const float *f, const int32_t *inid, const int32_t *rows, i
 int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const int32_t *rows, const int64_t *I_V,
                       int32_t K, int32_t nthreads, uint32_t mask, uint64_t seed, double jump_prob, int8_t *cls,
                       double *lat, double *stats) {
+    // K may be below the context's cluster count: only clusters [0, K) are served
     std::vector<std::atomic<uint8_t>> claimed(static_cast<size_t>(K));
     for (auto &c : claimed) c.store(0);
     std::atomic<int32_t> next_start{0};

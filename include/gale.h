@@ -241,6 +241,19 @@ gale_status gale_bulk_export(gale_ctx *ctx, uint32_t mask, const gale_arrays *ho
  */
 gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64_t timeout_ns, gale_view *out);
 
+/* Serving execution forms. */
+enum {
+    GALE_SERVE_LOOP = 0,   /* device-resident request loop (default when its plan fits one CTA) */
+    GALE_SERVE_BATCH = 1,  /* the leader launches the batched kernels for each batch of admitted requests */
+    GALE_SERVE_SINGLE = 2  /* one kernel launch per request, one at a time (the baseline form) */
+};
+
+/* Choose the serving form and the loop's idle exit (microseconds, 0 =
+ * default 20000) before the first gale_request of the context; EBUSY
+ * afterwards, EINVAL for an unknown mode or when the loop's merged plan does
+ * not fit one CTA. */
+gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us);
+
 /* Unpin a view from gale_request; its entry becomes evictable. */
 gale_status gale_release(gale_ctx *ctx, gale_view *view);
 

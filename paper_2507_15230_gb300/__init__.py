@@ -21,6 +21,7 @@ from . import _build
 VT, VV, ET, TT = 1, 2, 4, 8
 ALL = 15
 MODE_PER_CLUSTER, MODE_BATCHED = 0, 1
+SERVE_LOOP, SERVE_BATCH, SERVE_SINGLE = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ETIMEOUT", 5: "ENOTFOUND", 6: "ECUDA", 7: "EDEVICE"}
 ARRAYS = ("vt_off", "vt_val", "vv_off", "vv_val", "et_uoff", "et_w", "et_off", "et_val", "tt_off", "tt_val")
 ARRAY_REL = (VT, VT, VV, VV, ET, ET, ET, ET, TT, TT)
@@ -71,7 +72,7 @@ class ServeStats(ctypes.Structure):
 EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
            "gale_bulk_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
-           "gale_autotune", "gale_get_bins", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
+           "gale_autotune", "gale_get_bins", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
 
 _lib = None
 
@@ -108,6 +109,7 @@ def load_library(build: bool = True):
     lib.gale_set_tuning.argtypes = [P, i32, i32]
     lib.gale_autotune.argtypes = [P, u32]
     lib.gale_get_bins.argtypes = [P, P, i32, ctypes.POINTER(i32)]
+    lib.gale_serve_configure.argtypes = [P, i32, i64]
     lib.gale_stream.argtypes = [P]
     lib.gale_stream.restype = P
     lib.gale_last_launch_count.argtypes = [P]
@@ -312,6 +314,10 @@ class Context:
         v = View()
         _check(self._lib.gale_request(self._h, cluster, mask, timeout_ns, ctypes.byref(v)))
         return v
+
+    def serve_configure(self, mode: int, idle_us: int = 0):
+        """gale_serve_configure (before the first request)."""
+        _check(self._lib.gale_serve_configure(self._h, mode, idle_us))
 
     def release(self, view: View):
         _check(self._lib.gale_release(self._h, ctypes.byref(view)))

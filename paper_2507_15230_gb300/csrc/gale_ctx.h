@@ -84,6 +84,8 @@ struct gale_ctx {
     std::mutex mu;  // guards builds and the bulk state
 
     gale::Serve *serve = nullptr;
+    int32_t serve_mode = -1;          // -1: default (loop when it fits)
+    int64_t serve_idle_us = 0;
 
     void *dalloc(size_t bytes);
     void dfree(void *p);

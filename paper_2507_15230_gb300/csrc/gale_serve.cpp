@@ -120,6 +120,7 @@ struct Serve {
 
     // device loop
     bool loop_mode = true;
+    bool single_mode = false;  // one launch per request (baseline form)
     SmemPlan plan{};
     int grid = 0;
     WorkItem *h_items = nullptr;   // mapped
@@ -199,10 +200,9 @@ gale_status Serve::init(gale_ctx *c) {
     slab.init(ctx->cache_budget);
     bool fits = false;
     plan = serve_plan(ctx, &fits);
-    const char *mode = getenv("GALE_SERVE_MODE");
-    loop_mode = fits && !(mode && strcmp(mode, "launch") == 0);
-    const char *idle = getenv("GALE_SERVE_IDLE_US");
-    if (idle) idle_ns = uint64_t(std::max(100.0, atof(idle))) * 1000ull;
+    loop_mode = fits && (ctx->serve_mode < 0 || ctx->serve_mode == GALE_SERVE_LOOP);
+    single_mode = ctx->serve_mode == GALE_SERVE_SINGLE;
+    if (ctx->serve_idle_us > 0) idle_ns = uint64_t(std::max<int64_t>(100, ctx->serve_idle_us)) * 1000ull;
     auto ck = [](cudaError_t e) { return e == cudaSuccess; };
     if (!ck(cudaHostAlloc(reinterpret_cast<void **>(&h_items), sizeof(WorkItem) * kRingCap, cudaHostAllocMapped)) ||
         !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_tail), 64, cudaHostAllocMapped)) ||
@@ -377,8 +377,10 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
     for (int bb = 0; bb < nb; ++bb) {
         const int32_t m = off[bb + 1] - off[bb];
         if (m == 0) continue;
-        launch_build(dm, ctx->bins[bb].plan, d_batch, d_border + off[bb], m, d_err, d_tick + bb,
-                     std::min(ctx->bins[bb].grid, m), loop_stream);
+        if (single_mode) launch_build_one(dm, ctx->bins[bb].plan, d_batch, h_border[off[bb]], d_err, loop_stream);
+        else
+            launch_build(dm, ctx->bins[bb].plan, d_batch, d_border + off[bb], m, d_err, d_tick + bb,
+                         std::min(ctx->bins[bb].grid, m), loop_stream);
     }
     cudaEventRecord(batch_event, loop_stream);
     for (Entry *e : b) e->state = St::Building;
@@ -418,7 +420,7 @@ void Serve::leader_loop() {
             if (loop_mode) publish_loop(e);
             else {
                 batch.push_back(e);
-                if (int(batch.size()) >= kRingCap) break;
+                if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
             }
         }
         if (!batch.empty()) launch_batch(batch);
@@ -590,6 +592,21 @@ gale_status gale_release(gale_ctx *ctx, gale_view *view) {
     e->refs--;
     view->handle = 0;
     s->cv_leader.notify_all();  // a pinned budget may have freed up
+    return GALE_OK;
+}
+
+gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (mode < GALE_SERVE_LOOP || mode > GALE_SERVE_SINGLE) return fail(GALE_EINVAL, "unknown serving mode");
+    std::lock_guard<std::mutex> lk(g_serve_init_mu);
+    if (ctx->serve) return fail(GALE_EBUSY, "serving already started on this context");
+    if (mode == GALE_SERVE_LOOP && ctx->device >= 0) {
+        bool fits = false;
+        gale::serve_plan(ctx, &fits);
+        if (!fits) return fail(GALE_EINVAL, "the serving loop's merged plan does not fit one CTA");
+    }
+    ctx->serve_mode = mode;
+    ctx->serve_idle_us = idle_us;
     return GALE_OK;
 }
 

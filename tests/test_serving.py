@@ -31,9 +31,11 @@ def same(a, b):
     return a.keys() == b.keys() and all(np.array_equal(a[n], b[n]) for n in a)
 
 
-def run_mix(budget, nthreads=8, rounds=40, masks=(gale.ALL, gale.VT | gale.VV | gale.TT, gale.ET)):
+def run_mix(budget, nthreads=8, rounds=40, masks=(gale.ALL, gale.VT | gale.VV | gale.TT, gale.ET),
+            mode=gale.SERVE_LOOP):
     m = gen.small_grid(with_field=False)
     with gale.Context.load(m, device=0, cache_budget_bytes=budget) as ctx:
+        ctx.serve_configure(mode)
         refs = {mk: bulk_reference(ctx, mk) for mk in masks}
         errors = []
 
@@ -60,10 +62,9 @@ def run_mix(budget, nthreads=8, rounds=40, masks=(gale.ALL, gale.VT | gale.VV | 
         return errors, stats
 
 
-@pytest.mark.parametrize("mode", ["loop", "launch"])
-def test_results_same_alone_and_in_mix(mode, monkeypatch):
-    monkeypatch.setenv("GALE_SERVE_MODE", mode)
-    errors, stats = run_mix(64 << 20)
+@pytest.mark.parametrize("mode", [gale.SERVE_LOOP, gale.SERVE_BATCH, gale.SERVE_SINGLE])
+def test_results_same_alone_and_in_mix(mode):
+    errors, stats = run_mix(64 << 20, mode=mode)
     assert not errors
     assert stats.requests == 8 * 40 and stats.builds > 0 and stats.hits > 0
 
@@ -109,6 +110,15 @@ def test_admission_waits_for_release():
         assert blocked and "v" in got
         ctx.release(got["v"])
         assert ctx.serve_stats().evictions >= 1
+
+
+def test_serve_configure_after_start_is_busy():
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0, cache_budget_bytes=8 << 20) as ctx:
+        ctx.release(ctx.request(3, gale.VT))
+        with pytest.raises(gale.GaleError) as ei:
+            ctx.serve_configure(gale.SERVE_BATCH)
+        assert ei.value.status == 3
 
 
 def test_oversized_request_is_rejected():
