@@ -285,10 +285,11 @@ gale_status gale_get_info(gale_ctx *ctx, gale_info *out);
  * size bin) and CTAs per SM of the persistent grid (0 = as many as fit). */
 gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
 
-/* Size bins of the batched form: for each bin (up to max_bins) five int32
- * values - clusters, threads per CTA, dynamic shared bytes per CTA, CTAs per
- * SM, persistent grid size - into out[5*i .. 5*i+4].  Returns the number of
- * bins in *nbins. */
+/* Size bins of the batched form: for each bin (up to max_bins) six int32
+ * values - clusters, threads per CTA, bytes of per-CTA working memory, CTAs
+ * per SM, persistent grid size, and 1 if the working memory is global
+ * scratch (clusters too large for shared memory) else 0 - into
+ * out[6*i .. 6*i+5].  Returns the number of bins in *nbins. */
 gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t *nbins);
 
 /* Autotune the batched form on a sample of clusters; stores the choice in

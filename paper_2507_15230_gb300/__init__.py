@@ -360,13 +360,14 @@ class Context:
         return ext[:ne.value], halo[:nh.value]
 
     def bins(self) -> list:
-        """Size bins: dicts of clusters, threads, smem bytes, CTAs per SM, grid."""
+        """Size bins: clusters, threads, working bytes per CTA, CTAs per SM,
+        grid, spill (1: working memory in global scratch)."""
         n = ctypes.c_int32(0)
         _check(self._lib.gale_get_bins(self._h, None, 0, ctypes.byref(n)))
-        out = np.zeros(5 * max(n.value, 1), np.int32)
+        out = np.zeros(6 * max(n.value, 1), np.int32)
         _check(self._lib.gale_get_bins(self._h, _p(out), n.value, ctypes.byref(n)))
-        keys = ("clusters", "threads", "smem", "ctas_per_sm", "grid")
-        return [dict(zip(keys, out[5 * i:5 * i + 5].tolist())) for i in range(n.value)]
+        keys = ("clusters", "threads", "bytes", "ctas_per_sm", "grid", "spill")
+        return [dict(zip(keys, out[6 * i:6 * i + 6].tolist())) for i in range(n.value)]
 
     def set_tuning(self, threads: int = 0, ctas_per_sm: int = 0):
         _check(self._lib.gale_set_tuning(self._h, threads, ctas_per_sm))

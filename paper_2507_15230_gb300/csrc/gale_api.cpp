@@ -96,36 +96,49 @@ int threads_for(const gale_ctx *ctx, int32_t nv_own) {
 
 // Size bins: clusters sorted by shared-memory need, cut where the merged
 // plan would cross the next occupancy tier (4, 3, 2, 1 CTAs per SM).
+// Clusters whose plan exceeds the shared memory of one CTA go to spill bins:
+// the same kernel with its regions in a per-CTA slice of global scratch.
 gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     const int32_t K = ctx->hm.K;
-    const int smem_cta = gale::kernel_smem_limit();
+    // dynamic shared memory a CTA may plan for: the opt-in limit less room
+    // for the kernels' static shared memory
+    constexpr int kStaticMargin = 512;
+    const int smem_cta = gale::kernel_smem_limit() - kStaticMargin;
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
     auto caps_k = [&](int32_t k) {
         return caps_of(ctx->hm.stats[k], with_sizes ? ctx->sizes.data() + size_t(5) * k : nullptr);
     };
     std::vector<int32_t> need(K), thr(K);
+    std::vector<uint8_t> big(K);
     for (int32_t k = 0; k < K; ++k) {
+        if (ctx->hm.stats[k].max_up > 255)
+            return fail(GALE_EINVAL, "cluster " + std::to_string(k) +
+                                         " has a vertex with more than 255 upper neighbours (unsupported)");
         thr[k] = threads_for(ctx, ctx->hm.stats[k].nv_own);
         need[k] = gale::plan_smem(caps_k(k), thr[k]).total;
+        big[k] = need[k] > smem_cta;
     }
     std::vector<int32_t> idx(K);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+        if (big[a] != big[b]) return big[a] < big[b];
         return thr[a] != thr[b] ? thr[a] < thr[b] : need[a] < need[b];
     });
     std::vector<int> tiers;
-    for (int per = 4; per >= 1; --per) tiers.push_back(std::min(smem_sm / per - 1024 * per, smem_cta));
+    for (int per = 4; per >= 1; --per) tiers.push_back(std::min(smem_sm / per - 1024 - kStaticMargin, smem_cta));
     ctx->bins.clear();
     ctx->bin_of.assign(K, -1);
     size_t tier = 0;
     int cur_thr = 0;
+    bool cur_big = false;
     gale::Caps cur{};
     std::vector<int32_t> members;
     auto close = [&]() {
         if (members.empty()) return;
         gale::Bin b;
         b.plan = gale::plan_smem(cur, cur_thr);
+        b.spill = cur_big;
         std::stable_sort(members.begin(), members.end(),
                          [&](int32_t a, int32_t c) { return need[a] > need[c]; });  // largest first
         b.clusters = members;
@@ -135,43 +148,59 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         cur = gale::Caps{};
     };
     for (int32_t k : idx) {
-        if (ctx->hm.stats[k].max_up > 255)
-            return fail(GALE_EINVAL, "cluster " + std::to_string(k) +
-                                         " has a vertex with more than 255 upper neighbours (unsupported)");
-        if (need[k] > smem_cta)
-            return fail(GALE_EINVAL, "cluster " + std::to_string(k) + " needs " + std::to_string(need[k]) +
-                                         " bytes of shared memory (limit " + std::to_string(smem_cta) +
-                                         "); use smaller clusters");
-        if (!members.empty() && thr[k] != cur_thr) {
+        if (!members.empty() && (thr[k] != cur_thr || bool(big[k]) != cur_big)) {
             close();
             tier = 0;
         }
         cur_thr = thr[k];
+        cur_big = big[k];
         gale::Caps m = members.empty() ? caps_k(k) : merge(cur, caps_k(k));
-        int tot = gale::plan_smem(m, cur_thr).total;
-        while (tier < tiers.size() && tot > tiers[tier]) {
+        if (!cur_big) {
+            int tot = gale::plan_smem(m, cur_thr).total;
+            while (tier < tiers.size() && tot > tiers[tier]) {
+                close();
+                ++tier;
+                m = caps_k(k);
+                tot = gale::plan_smem(m, cur_thr).total;
+            }
+            if (tier >= tiers.size()) tier = tiers.size() - 1;
+        } else if (!members.empty() && gale::plan_smem(m, cur_thr).total > 2 * need[k]) {
+            // spill bins: keep the merged plan within twice a member's own
             close();
-            ++tier;
             m = caps_k(k);
-            tot = gale::plan_smem(m, cur_thr).total;
         }
-        if (tier >= tiers.size()) tier = tiers.size() - 1;
         cur = m;
         members.push_back(k);
     }
     close();
     int max_total = 0;
-    for (auto &b : ctx->bins) max_total = std::max(max_total, b.plan.total);
+    for (auto &b : ctx->bins)
+        if (!b.spill) max_total = std::max(max_total, b.plan.total);
     gale::prepare_kernels(max_total);
+    int64_t spill_need = 0;
     for (auto &b : ctx->bins) {
-        int per_sm = gale::max_ctas_per_sm(b.plan);
-        if (per_sm < 1) return fail(GALE_EINVAL, "a size bin cannot be launched (shared memory or registers)");
+        int per_sm = gale::max_ctas_per_sm(b.plan, b.spill);
+        if (per_sm < 1 && !b.spill) {
+            b.spill = true;  // cannot launch with this much shared memory: run in global scratch
+            per_sm = gale::max_ctas_per_sm(b.plan, true);
+        }
+        if (per_sm < 1) return fail(GALE_EINVAL, "a size bin cannot be launched (threads or registers)");
         if (ctx->ctas_override > 0) per_sm = std::min(per_sm, ctx->ctas_override);
+        if (b.spill) per_sm = std::min(per_sm, 2);  // bounds the scratch footprint
         b.ctas_per_sm = per_sm;
         b.grid = std::max(1, std::min<int>(int(b.clusters.size()), per_sm * ctx->sm_count));
+        if (b.spill) spill_need = std::max<int64_t>(spill_need, int64_t(b.grid) * b.plan.total);
+    }
+    if (spill_need > ctx->spill_bytes) {
+        if (ctx->d_spill) ctx->dfree(ctx->d_spill);
+        ctx->d_spill = static_cast<char *>(ctx->dalloc(size_t(spill_need)));
+        ctx->spill_bytes = ctx->d_spill ? spill_need : 0;
+        if (!ctx->d_spill) return fail(GALE_ENOMEM, "device allocation of the large-cluster scratch failed");
     }
     return GALE_OK;
 }
+
+char *scratch_of(gale_ctx *ctx, const gale::Bin &b) { return b.spill ? ctx->d_spill : nullptr; }
 
 }  // namespace
 
@@ -188,7 +217,9 @@ SmemPlan serve_plan(gale_ctx *ctx, bool *fits) {
         first = false;
     }
     SmemPlan p = plan_smem(c, threads);
-    *fits = !ctx->bins.empty() && p.total <= kernel_smem_limit();
+    bool any_spill = false;
+    for (const auto &b : ctx->bins) any_spill |= b.spill;
+    *fits = !ctx->bins.empty() && !any_spill && p.total <= kernel_smem_limit();
     if (*fits) prepare_kernels(std::max(p.total, 0));
     return p;
 }
@@ -234,7 +265,7 @@ gale_status count_pass(gale_ctx *ctx) {
         const gale::Bin &bin = ctx->bins[b];
         int rc = gale::launch_count_pass(dev_mesh(ctx), bin.plan, ctx->d_order_all + ctx->order_all_off[b],
                                          int32_t(bin.clusters.size()), ctx->d_sizes, ctx->d_err,
-                                         ctx->d_tickets + b, bin.grid, ctx->stream);
+                                         ctx->d_tickets + b, bin.grid, ctx->stream, scratch_of(ctx, bin));
         if (rc != 0) return cuda_fail(cudaError_t(rc), "count pass launch");
     }
     gale_status st = check_device_error(ctx);
@@ -505,7 +536,7 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
                 const gale::Bin &bin = ctx->bins[b];
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b],
                                         int32_t(bin.clusters.size()), ctx->d_err, ctx->d_tickets + b, bin.grid,
-                                        ctx->stream);
+                                        ctx->stream, scratch_of(ctx, bin));
             }
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
             if (rc != 0) return cuda_fail(cudaError_t(rc), "capturing the batched build");
@@ -532,7 +563,8 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
         if (mode == GALE_MODE_PER_CLUSTER) {
             for (int32_t i = 0; i < cnt; ++i) {
                 const gale::Bin &bin = ctx->bins[ctx->bin_of[list[i]]];
-                rc = gale::launch_build_one(dm, bin.plan, ctx->d_items, i, ctx->d_err, ctx->stream);
+                rc = gale::launch_build_one(dm, bin.plan, ctx->d_items, i, ctx->d_err, ctx->stream,
+                                            scratch_of(ctx, bin));
                 if (rc != 0) return cuda_fail(cudaError_t(rc), "per-cluster launch");
             }
             launches += cnt;
@@ -558,7 +590,8 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
                 if (nb == 0) continue;
                 const gale::Bin &bin = ctx->bins[b];
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_part + off[b], nb, ctx->d_err,
-                                        ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream);
+                                        ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream,
+                                        scratch_of(ctx, bin));
                 if (rc != 0) return cuda_fail(cudaError_t(rc), "batched launch");
                 ++launches;
             }
@@ -720,11 +753,12 @@ gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t
     *nbins = int32_t(ctx->bins.size());
     for (int32_t b = 0; b < *nbins && b < max_bins && out; ++b) {
         const gale::Bin &bin = ctx->bins[b];
-        out[5 * b + 0] = int32_t(bin.clusters.size());
-        out[5 * b + 1] = bin.plan.threads;
-        out[5 * b + 2] = bin.plan.total;
-        out[5 * b + 3] = bin.ctas_per_sm;
-        out[5 * b + 4] = bin.grid;
+        out[6 * b + 0] = int32_t(bin.clusters.size());
+        out[6 * b + 1] = bin.plan.threads;
+        out[6 * b + 2] = bin.plan.total;
+        out[6 * b + 3] = bin.ctas_per_sm;
+        out[6 * b + 4] = bin.grid;
+        out[6 * b + 5] = bin.spill ? 1 : 0;
     }
     return GALE_OK;
 }

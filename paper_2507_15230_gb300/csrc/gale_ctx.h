@@ -20,6 +20,7 @@ struct Bin {
     std::vector<int32_t> clusters;  // members, largest working set first
     int grid = 0;                   // persistent CTAs
     int ctas_per_sm = 0;
+    bool spill = false;             // regions in global scratch (working set too large for shared memory)
 };
 
 struct DevAlloc {
@@ -56,6 +57,8 @@ struct gale_ctx {
     gale::WorkItem *d_arrays_base = nullptr;  // [16] base pointers per mask
     int64_t *d_totals = nullptr;            // [10]
     int64_t *d_bsum = nullptr;              // output placement scratch
+    char *d_spill = nullptr;                // per-CTA regions of spill bins
+    int64_t spill_bytes = 0;
     std::vector<int64_t> sizes;             // host [K*5]
     int64_t totals[5] = {0, 0, 0, 0, 0};
     double device_seconds = 0;

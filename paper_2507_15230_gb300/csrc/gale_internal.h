@@ -159,18 +159,20 @@ struct DevMesh {
 
 // Persistent launch over n clusters: ids[i] (count pass) or items[order[i]]
 // (build).  One CTA per cluster at a time.
+// gscratch: NULL runs the cluster in dynamic shared memory; otherwise each
+// CTA uses the slice gscratch + blockIdx.x * plan.total of global memory.
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
-                      int32_t *err, int32_t *ticket, int grid, void *stream);
+                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch);
 // Output placement for n listed clusters (three launches).  bsum: device
 // scratch of bases_scratch_words(n) int64 words.
 int bases_scratch_words(int32_t n);
 int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t *sizes, uint32_t mask,
                  const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, int64_t *bsum, void *stream);
 int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
-                 int32_t *err, int32_t *ticket, int grid, void *stream);
+                 int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch);
 // One launch, one CTA, one work item (the per-cluster baseline form).
 int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,
-                     void *stream);
+                     void *stream, char *gscratch);
 // Ring of the device-resident serving loop (all host pointers are mapped
 // host memory seen through device addresses).
 struct ServeRing {
@@ -185,10 +187,9 @@ struct ServeRing {
 };
 int launch_serve(const DevMesh &m, const SmemPlan &plan, const ServeRing &ring, int32_t *err, int grid, void *stream);
 int serve_ctas_per_sm(const SmemPlan &plan);
-SmemPlan merged_plan(const std::vector<SmemPlan> &plans);
 
 int kernel_smem_limit();
-int max_ctas_per_sm(const SmemPlan &plan);
+int max_ctas_per_sm(const SmemPlan &plan, bool spill);
 void prepare_kernels(int smem);
 int device_sm_count();
 

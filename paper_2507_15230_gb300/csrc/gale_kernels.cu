@@ -599,10 +599,23 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     __syncthreads();
 }
 
-__global__ void count_kernel(DevMesh m, SmemPlan plan, const int32_t *ids, int32_t n, int64_t *sizes, int32_t *err,
-                             int32_t *ticket) {
+// SPILL: the cluster's regions live in a per-CTA slice of global scratch
+// (clusters whose working set exceeds shared memory); otherwise in dynamic
+// shared memory.
+template <bool SPILL>
+__device__ __forceinline__ char *region_base(char *smem, char *gscratch, const SmemPlan &plan) {
+    return SPILL ? gscratch + size_t(blockIdx.x) * size_t(plan.total) : smem;
+}
+
+// Blocks have up to 1024 threads (one per own vertex), so every cluster
+// kernel is bounded to 64 registers per thread.
+constexpr int kMaxThreads = 1024;
+
+template <bool SPILL>
+__global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan plan, const int32_t *ids, int32_t n, int64_t *sizes, int32_t *err,
+                             int32_t *ticket, char *gscratch) {
     extern __shared__ __align__(16) char smem[];
-    const Smem S = carve(smem, plan);
+    const Smem S = carve(region_base<SPILL>(smem, gscratch, plan), plan);
     __shared__ int32_t s_idx;
     __shared__ int64_t s_sizes[SZ_N];
     for (;;) {
@@ -624,10 +637,11 @@ __global__ void count_kernel(DevMesh m, SmemPlan plan, const int32_t *ids, int32
     }
 }
 
-__global__ void build_kernel(DevMesh m, SmemPlan plan, const WorkItem *items, const int32_t *order, int32_t n,
-                             int32_t *err, int32_t *ticket) {
+template <bool SPILL>
+__global__ void __launch_bounds__(kMaxThreads) build_kernel(DevMesh m, SmemPlan plan, const WorkItem *items, const int32_t *order, int32_t n,
+                             int32_t *err, int32_t *ticket, char *gscratch) {
     extern __shared__ __align__(16) char smem[];
-    const Smem S = carve(smem, plan);
+    const Smem S = carve(region_base<SPILL>(smem, gscratch, plan), plan);
     __shared__ int32_t s_idx;
     __shared__ WorkItem s_item;
     for (;;) {
@@ -647,9 +661,11 @@ __global__ void build_kernel(DevMesh m, SmemPlan plan, const WorkItem *items, co
     }
 }
 
-__global__ void build_one_kernel(DevMesh m, SmemPlan plan, const WorkItem *items, int32_t index, int32_t *err) {
+template <bool SPILL>
+__global__ void __launch_bounds__(kMaxThreads) build_one_kernel(DevMesh m, SmemPlan plan, const WorkItem *items, int32_t index, int32_t *err,
+                                 char *gscratch) {
     extern __shared__ __align__(16) char smem[];
-    const Smem S = carve(smem, plan);
+    const Smem S = carve(region_base<SPILL>(smem, gscratch, plan), plan);
     __shared__ WorkItem s_item;
     if (threadIdx.x == 0) s_item = items[index];
     __syncthreads();
@@ -689,7 +705,7 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-__global__ void serve_kernel(DevMesh m, SmemPlan plan, ServeRing ring, int32_t *err) {
+__global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, ServeRing ring, int32_t *err) {
     extern __shared__ __align__(16) char smem[];
     const Smem S = carve(smem, plan);
     __shared__ long long s_t;
@@ -935,25 +951,31 @@ int device_sm_count() {
 }
 
 void prepare_kernels(int smem) {
-    cudaFuncSetAttribute(build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(build_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(build_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(build_one_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-int max_ctas_per_sm(const SmemPlan &plan) {
+int max_ctas_per_sm(const SmemPlan &plan, bool spill) {
     int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, build_kernel, plan.threads, plan.total) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_kernel, plan.threads, plan.total) != cudaSuccess)
-        return 0;
+    cudaError_t e1, e2;
+    if (spill) {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, build_kernel<true>, plan.threads, 0);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_kernel<true>, plan.threads, 0);
+    } else {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, build_kernel<false>, plan.threads, plan.total);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_kernel<false>, plan.threads, plan.total);
+    }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return 0;
     return a < b ? a : b;
 }
 
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
-                      int32_t *err, int32_t *ticket, int grid, void *stream) {
+                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
-    count_kernel<<<grid, plan.threads, plan.total, s>>>(m, plan, ids, n, sizes_out, err, ticket);
+    if (gscratch) count_kernel<true><<<grid, plan.threads, 0, s>>>(m, plan, ids, n, sizes_out, err, ticket, gscratch);
+    else count_kernel<false><<<grid, plan.threads, plan.total, s>>>(m, plan, ids, n, sizes_out, err, ticket, nullptr);
     return int(cudaGetLastError());
 }
 
@@ -971,10 +993,11 @@ int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t 
 }
 
 int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
-                 int32_t *err, int32_t *ticket, int grid, void *stream) {
+                 int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
-    build_kernel<<<grid, plan.threads, plan.total, s>>>(m, plan, items, order, n, err, ticket);
+    if (gscratch) build_kernel<true><<<grid, plan.threads, 0, s>>>(m, plan, items, order, n, err, ticket, gscratch);
+    else build_kernel<false><<<grid, plan.threads, plan.total, s>>>(m, plan, items, order, n, err, ticket, nullptr);
     return int(cudaGetLastError());
 }
 
@@ -995,9 +1018,10 @@ int serve_ctas_per_sm(const SmemPlan &plan) {
 }
 
 int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,
-                     void *stream) {
+                     void *stream, char *gscratch) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    build_one_kernel<<<1, plan.threads, plan.total, s>>>(m, plan, items, index, err);
+    if (gscratch) build_one_kernel<true><<<1, plan.threads, 0, s>>>(m, plan, items, index, err, gscratch);
+    else build_one_kernel<false><<<1, plan.threads, plan.total, s>>>(m, plan, items, index, err, nullptr);
     return int(cudaGetLastError());
 }
 

@@ -63,8 +63,13 @@ extern "C" gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t 
     if (int32_t(ctx->bins.size()) > kNoAllocMaxBins)
         return fail(GALE_EINVAL, "the context has more than " + std::to_string(kNoAllocMaxBins) + " size bins");
     const int32_t K = ctx->hm.K;
-    for (int32_t i = 0; i < n; ++i)
+    for (int32_t i = 0; i < n; ++i) {
         if (ids[i] < 0 || ids[i] >= K) return fail(GALE_EINVAL, "cluster id out of range");
+        if (ctx->bins[ctx->bin_of[ids[i]]].spill)
+            return fail(GALE_EINVAL, "cluster " + std::to_string(ids[i]) +
+                                         " is too large for shared memory; the allocation-free build takes only "
+                                         "clusters that fit");
+    }
     int32_t *const *out = &dev_out->vt_off;
     const uint32_t rel_of[10] = {GALE_VT, GALE_VT, GALE_VV, GALE_VV, GALE_ET, GALE_ET, GALE_ET, GALE_ET, GALE_TT, GALE_TT};
     for (int a = 0; a < 10; ++a)
@@ -128,7 +133,7 @@ extern "C" gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t 
         if (m == 0) continue;
         const gale::Bin &bin = ctx->bins[b];
         rc = gale::launch_build(dm, bin.plan, S->items, S->order + cnt[b], m, &S->err, &S->tickets[b],
-                                bin.grid < m ? bin.grid : m, s);
+                                bin.grid < m ? bin.grid : m, s, nullptr);
     }
     if (rc != 0) return fail(GALE_ECUDA, std::string("launch: ") + cudaGetErrorString(cudaError_t(rc)));
     int32_t err = 0;

@@ -146,6 +146,7 @@ struct Serve {
     WorkItem *h_batch = nullptr;   // pinned staging
     int32_t *h_border = nullptr;
     cudaEvent_t batch_event = nullptr;
+    char *d_spill = nullptr;       // large-cluster scratch of the serving stream
     std::vector<Entry *> batch_entries;
     bool batch_busy = false;
 
@@ -226,6 +227,10 @@ gale_status Serve::init(gale_ctx *c) {
     d_tick = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * 64));
     if (!d_next || !d_err || !d_batch || !d_border || !d_tick)
         return fail(GALE_ENOMEM, "device allocation for the serving loop failed");
+    if (ctx->spill_bytes > 0) {
+        d_spill = static_cast<char *>(ctx->dalloc(size_t(ctx->spill_bytes)));
+        if (!d_spill) return fail(GALE_ENOMEM, "device allocation of the serving large-cluster scratch failed");
+    }
     if (!ck(cudaStreamCreateWithFlags(&loop_stream, cudaStreamNonBlocking)) ||
         !ck(cudaEventCreateWithFlags(&loop_event, cudaEventDisableTiming)) ||
         !ck(cudaEventCreateWithFlags(&batch_event, cudaEventDisableTiming)) ||
@@ -377,10 +382,12 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
     for (int bb = 0; bb < nb; ++bb) {
         const int32_t m = off[bb + 1] - off[bb];
         if (m == 0) continue;
-        if (single_mode) launch_build_one(dm, ctx->bins[bb].plan, d_batch, h_border[off[bb]], d_err, loop_stream);
+        char *scr = ctx->bins[bb].spill ? d_spill : nullptr;
+        if (single_mode)
+            launch_build_one(dm, ctx->bins[bb].plan, d_batch, h_border[off[bb]], d_err, loop_stream, scr);
         else
             launch_build(dm, ctx->bins[bb].plan, d_batch, d_border + off[bb], m, d_err, d_tick + bb,
-                         std::min(ctx->bins[bb].grid, m), loop_stream);
+                         std::min(ctx->bins[bb].grid, m), loop_stream, scr);
     }
     cudaEventRecord(batch_event, loop_stream);
     for (Entry *e : b) e->state = St::Building;

@@ -92,3 +92,13 @@ def test_host_init_rejects_bad_input():
         assert ei.value.status == 1
     with pytest.raises(gale.GaleError):
         host_ctx(ok, mask=0)
+
+
+def test_host_init_delaunay_matches_oracle():
+    m = gen.delaunay_mesh(6000, seed=3, with_field=False)
+    with host_ctx(m) as ctx:
+        canon = compare_with_oracle(m, ctx)
+        for k in range(0, m.nclusters, max(1, m.nclusters // 12)):
+            ext, halo = ctx.working_set(k)
+            oext, ohalo = oracle.working_set(canon, k)
+            assert np.array_equal(ext, oext) and np.array_equal(halo, ohalo), k

@@ -135,3 +135,22 @@ def test_paper_examples():
         c0 = cid[0]
         vv = out["vv_val"][out["vv_off"][c0]:out["vv_off"][c0 + 1]]
         assert sorted(vp[vv].tolist()) == g["expect"]["VV"]["0"]
+
+
+@pytest.mark.parametrize("npts,seed", [(20000, 5), (60000, 11)])
+def test_delaunay_uneven_clusters(npts, seed):
+    """Delaunay meshes of Gaussian-mixture points with uneven kd leaves of 32
+    to 2,048 vertices: irregular stars and clusters too large for shared
+    memory (their bins run in global scratch)."""
+    m = gen.delaunay_mesh(npts, seed=seed, with_field=False)
+    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
+    with gale.Context.load(m, device=0) as ctx:
+        bins = ctx.bins()
+        assert sum(b["clusters"] for b in bins) == m.nclusters
+        assert any(b["spill"] for b in bins), bins
+        _, _, sizes = ctx.intervals()
+        assert np.array_equal(sizes, oracle.cluster_sizes(rel, canon))
+        for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+            ctx.build(None, gale.ALL, mode)
+            ctx.synchronize()
+            assert_bulk_equal(ctx.export(gale.ALL), expected_bulk(rel, canon, range(m.nclusters)))
