@@ -65,6 +65,7 @@ gale::Caps caps_of(const gale::ClusterStat &s, const int64_t *sizes) {
         c.max_tt = int32_t(sizes[4]);
     }
     c.hcap = int32_t(std::max<int64_t>(64, next_pow2(2 * int64_t(s.n_bnd) + 1)));
+    c.n_tot = s.n_ext + s.n_own + s.n_halo;
     return c;
 }
 
@@ -83,15 +84,19 @@ gale::Caps merge(const gale::Caps &a, const gale::Caps &b) {
     c.max_tt = std::max(a.max_tt, b.max_tt);
     c.max_up = std::max(a.max_up, b.max_up);
     c.hcap = std::max(a.hcap, b.hcap);
+    c.n_tot = std::max(a.n_tot, b.n_tot);
     return c;
 }
 
-// Block size for a cluster: one thread per own vertex, a warp multiple in
-// [64, 1024] (a tuning override applies when set).
-int threads_for(const gale_ctx *ctx, int32_t nv_own) {
+// Block size for a cluster: every phase spreads its work over all threads,
+// so the size follows the cluster's tet count (about five tets per thread),
+// a power of two in [64, 512] (a tuning override applies when set).
+int threads_for(const gale_ctx *ctx, const gale::ClusterStat &s) {
     if (ctx->threads_override > 0) return ctx->threads_override;
-    int t = (nv_own + 31) / 32 * 32;
-    return std::min(1024, std::max(64, t));
+    const int64_t want = (int64_t(s.n_ext) + s.n_own) / 5;
+    int t = 64;
+    while (t < 512 && t < want) t <<= 1;
+    return t;
 }
 
 // Size bins: clusters sorted by shared-memory need, cut where the merged
@@ -115,7 +120,7 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         if (ctx->hm.stats[k].max_up > 255)
             return fail(GALE_EINVAL, "cluster " + std::to_string(k) +
                                          " has a vertex with more than 255 upper neighbours (unsupported)");
-        thr[k] = threads_for(ctx, ctx->hm.stats[k].nv_own);
+        thr[k] = threads_for(ctx, ctx->hm.stats[k]);
         need[k] = gale::plan_smem(caps_k(k), thr[k]).total;
         big[k] = need[k] > smem_cta;
     }

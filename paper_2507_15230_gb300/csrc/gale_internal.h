@@ -102,37 +102,42 @@ struct Caps {
     int32_t nv_nb;      // largest neighbour-universe size (bitmap bits)
     int32_t max_deg;    // largest VT row
     int32_t max_vv;     // largest sum of VV rows   (0 in counting plans)
-    int32_t max_e;      // largest owned edge count (0 in counting plans)
+    int32_t max_e;      // largest owned edge count
     int32_t max_etv;    // largest sum of ET rows   (0 in counting plans)
     int32_t max_tt;     // largest sum of TT rows   (0 in counting plans)
-    int32_t max_up;     // most upper neighbours of an own vertex (edge masks)
+    int32_t max_up;     // most upper neighbours of an own vertex
     int32_t hcap;       // boundary-face hash capacity (power of two)
+    int32_t n_tot;      // largest tet count of a block (external + internal + halo)
 };
 
 // Byte offsets of the shared-memory regions of one CTA (all 16-aligned).
-// Phase D (TT) overlays hash, tcnt and st_tt on everything from vt_off on;
-// cnt and nbr stay.
+// Two regions are reused from phase to phase:
+//   r2: VV and upper-endpoint staging, then the per-edge tet masks (which
+//       end up holding the ET row offsets);
+//   r1: VT per-warp counters and lane masks; then the neighbour bitmaps and
+//       their rank prefixes; then ET staging; then the boundary-face hash,
+//       the TT counts and the TT staging.
 struct SmemPlan {
     int32_t threads;
-    int32_t wp;         // words per vertex bitmap (odd, for bank spread)
+    int32_t W;          // words of the largest neighbour bitmap
     int32_t nch;        // 32-tet chunks of the longest VT row
     int32_t pad;
-    int32_t blk;        // block copy
-    int32_t scan;       // scan scratch
-    int32_t cnt;        // int32[3*nv_own] per-vertex counts
-    int32_t nbr;        // uint16[4*n_own] TT links (phases C and D)
+    int32_t hdr;        // int32[16]: header copy and per-cluster flags
+    int32_t scan;       // scan scratch (3 x 33 words)
+    int32_t rows;       // uint2[n_tot] tet rows (bulk copy of the block's rows)
     int32_t vt_off;     // int32[nv_own+1]
     int32_t vt_list;    // uint16[n_vt]
-    int32_t bmap;       // B: uint32[2*nwarp*nv_own] counters and masks;
-                        // C: uint32[nv_own*wp] bitmaps + pre, then uint16[max_etv] ET staging
-    int32_t pre;        // uint8[nv_own*wp] rank prefix per bitmap word
-    int32_t st_ew;      // uint16[max_e] upper endpoints of the owned edges
-    int32_t emask;      // uint16[max_vv] VV staging, then uint32[max_e*nch]
-                        // per-edge tet masks, then ET offsets
-    int32_t st_v;       // = emask (VV staging)
-    int32_t hash;       // uint32[hcap] boundary faces (phase D)
-    int32_t tcnt;       // int32[n_own+1] TT counts (phase D)
-    int32_t st_tt;      // int32[max_tt] TT staging (phase D)
+    int32_t c_vv;       // int32[nv_own+1] VV row offsets
+    int32_t c_e;        // int32[nv_own+1] first owned edge of each own vertex
+    int32_t nbr;        // uint16[4*n_own] TT links
+    int32_t eu;         // uint16[max_e] lower endpoint (own index) of each owned edge
+    int32_t r2;         // uint16[max_vv] VV staging | uint32[max_e*nch] edge masks
+    int32_t st_w;       // uint16[max_e] upper-endpoint staging (inside r2)
+    int32_t r1;         // see above
+    int32_t mk;         // phase B lane masks (inside r1)
+    int32_t pre;        // uint8[nv_own*W] rank prefixes (inside r1)
+    int32_t tcnt;       // int32[n_own+1] TT counts (inside r1)
+    int32_t st_tt;      // int32[max_tt] TT staging (inside r1)
     int32_t total;      // bytes
     Caps caps;
 };
@@ -144,6 +149,7 @@ enum : int32_t {
     ERR_HASH_FULL = 4,     // face hash probe ran past its capacity
     ERR_BAD_ITEM = 8,      // a work item referenced a bad cluster
     ERR_TIMEOUT = 16,      // a bounded device wait ran out
+    ERR_BAD_BLOCK = 32,    // a block broke an invariant of its layout
 };
 
 SmemPlan plan_smem(const Caps &c, int threads);

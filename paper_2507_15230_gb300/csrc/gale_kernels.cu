@@ -2,12 +2,13 @@
 //
 // One CTA builds one cluster at a time (persistent CTAs take clusters from a
 // ticket counter; the per-cluster baseline launches one CTA per cluster).
-// The cluster's working set - its internal tets, its external tets T_ex and
-// its face halo (Section 4.3, "Initialization"), stored as 16-bit local rows
-// - is copied into shared memory and every relation is built there.  The
-// block has one thread per own vertex; per-vertex work is sequential in
-// that thread, and every output leaves through shared-memory staging with
-// one thread per element (coalesced stores).
+// The rows of the cluster's working set - its internal tets, its external
+// tets T_ex and its face halo (Section 4.3, "Initialization"), as 16-bit
+// local rows - arrive in shared memory by one bulk copy, and every relation
+// is built there.  Each phase spreads its work evenly over all threads of the
+// block (over tets, bitmap words, VT incidences, edges or internal tets), so
+// the block size is free of the cluster's vertex count; every output leaves
+// through shared-memory staging with one thread per element (coalesced).
 //
 //  B. VT (Section 4.6 / Algorithm 1: iterate the segment's tets and test
 //     each vertex against the segment interval).  Each warp takes a
@@ -17,18 +18,21 @@
 //     same vertex are ranked by a 32-bit lane mask.  Rows come out ascending
 //     with no sort.  (The paper's atomicPush, Algorithm 2, fills rows in
 //     arbitrary order.)
-//  C. VV, ET and most of TT, per own vertex x:
-//     - the other vertices of the tets in VT(x) are ORed into a bitmap over
-//       the cluster's neighbour universe; local order is canonical order, so
-//       the bitmap read in bit order is VV(x) sorted and deduplicated, and
-//       its bits above x are the upper endpoints w of the edges (x, w) that x
-//       owns; a byte per bitmap word holds the running count of upper bits,
-//       so the rank of w is one popcount away;
-//     - one block scan of the per-vertex counts places every row;
-//     - per upper edge a mask over VT(x) (bit j: the j-th tet contains w):
-//       its bits in order are ET(x, w), ascending, and the AND of the masks
-//       of (x, w1) and (x, w2) holds the two tets of the face (x, w1, w2), so
-//       every face whose lowest vertex is in the cluster gets its TT link.
+//  C. VV and the edges (x, w), x < w, that an own vertex x owns:
+//     - C1, per tet: the other vertices of every tet of VT(x) are ORed into
+//       a bitmap of x over the cluster's vertex universe; local order is
+//       canonical order, so the bitmap read in bit order is VV(x), sorted and
+//       deduplicated, and its bits above x are the upper endpoints w;
+//     - C2, per bitmap word: one block scan of the word popcounts places
+//       every VV row and every edge; each word keeps the rank of its first
+//       upper bit within its vertex, so an edge's index is one popcount away;
+//     - C3, per VT incidence (x, j-th tet of VT(x)): bit j is set in the tet
+//       mask of each edge (x, w) of that tet; a mask read in bit order is
+//       ET(x, w), ascending;
+//     - C5, per internal tet (a, b, c, d): the AND of the masks of two edges
+//       (a, w1), (a, w2) holds the two tets of the face (a, w1, w2); the face
+//       (b, c, d) is matched the same way inside VT(b) when b is own;
+//     - C4, per edge: the mask bits become the ET rows.
 //  D. TT (Table 1; the paper gives no kernel for it) for the faces (b, c, d)
 //     of internal tets (a, b, c, d) with no own vertex: a small
 //     open-addressing hash of those faces is probed with the faces of the
@@ -49,50 +53,93 @@ namespace gale {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kWaitLimit = 1 << 22;  // polls of the block copy's barrier before giving up
 
 struct Smem {
-    int32_t *blk, *scan, *cnt;
-    uint16_t *nbr;
+    int32_t *hdr, *scan;
+    uint2 *rows;
     int32_t *vt_off;
     uint16_t *vt_list;
-    uint32_t *bmap;   // per own vertex bitmaps (phase B: per-warp counters and masks)
-    uint8_t *pre;     // per own vertex, per bitmap word: upper bits in earlier words
-    uint16_t *st_ew;  // upper endpoints of the owned edges
-    uint32_t *emask;  // per-edge tet masks, then ET row offsets
-    uint16_t *st_v;   // VV staging, later ET value staging
-    uint32_t *hash;
-    int32_t *tcnt;
-    int32_t *st_tt;
+    int32_t *c_vv, *c_e;
+    uint16_t *nbr, *eu;
+    uint32_t *emask;  // r2
+    uint16_t *st_v;   // r2
+    uint16_t *st_w;   // r2
+    uint32_t *cw;     // r1 (phase B)
+    uint32_t *mk;     // r1 (phase B)
+    uint32_t *bm;     // r1 (phase C)
+    uint8_t *pre;     // r1 (phase C)
+    uint16_t *st_et;  // r1 (phase C4)
+    uint32_t *hash;   // r1 (phase D)
+    int32_t *tcnt;    // r1 (phases D, E)
+    int32_t *st_tt;   // r1 (phase E)
 };
 
 __device__ __forceinline__ Smem carve(char *base, const SmemPlan &p) {
     Smem s;
-    s.blk = reinterpret_cast<int32_t *>(base + p.blk);
+    s.hdr = reinterpret_cast<int32_t *>(base + p.hdr);
     s.scan = reinterpret_cast<int32_t *>(base + p.scan);
-    s.cnt = reinterpret_cast<int32_t *>(base + p.cnt);
-    s.nbr = reinterpret_cast<uint16_t *>(base + p.nbr);
+    s.rows = reinterpret_cast<uint2 *>(base + p.rows);
     s.vt_off = reinterpret_cast<int32_t *>(base + p.vt_off);
     s.vt_list = reinterpret_cast<uint16_t *>(base + p.vt_list);
-    s.bmap = reinterpret_cast<uint32_t *>(base + p.bmap);
+    s.c_vv = reinterpret_cast<int32_t *>(base + p.c_vv);
+    s.c_e = reinterpret_cast<int32_t *>(base + p.c_e);
+    s.nbr = reinterpret_cast<uint16_t *>(base + p.nbr);
+    s.eu = reinterpret_cast<uint16_t *>(base + p.eu);
+    s.emask = reinterpret_cast<uint32_t *>(base + p.r2);
+    s.st_v = reinterpret_cast<uint16_t *>(base + p.r2);
+    s.st_w = reinterpret_cast<uint16_t *>(base + p.st_w);
+    s.cw = reinterpret_cast<uint32_t *>(base + p.r1);
+    s.mk = reinterpret_cast<uint32_t *>(base + p.mk);
+    s.bm = reinterpret_cast<uint32_t *>(base + p.r1);
     s.pre = reinterpret_cast<uint8_t *>(base + p.pre);
-    s.st_ew = reinterpret_cast<uint16_t *>(base + p.st_ew);
-    s.emask = reinterpret_cast<uint32_t *>(base + p.emask);
-    s.st_v = reinterpret_cast<uint16_t *>(base + p.emask);
-    s.hash = reinterpret_cast<uint32_t *>(base + p.hash);
+    s.st_et = reinterpret_cast<uint16_t *>(base + p.r1);
+    s.hash = reinterpret_cast<uint32_t *>(base + p.r1);
     s.tcnt = reinterpret_cast<int32_t *>(base + p.tcnt);
     s.st_tt = reinterpret_cast<int32_t *>(base + p.st_tt);
     return s;
 }
 
+// ---- bulk copy into shared memory, completion on an mbarrier ----
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    // order this CTA's earlier generic accesses of dst before the async write
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// bounded wait for the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int i = 0; i < kWaitLimit; ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
 __device__ __forceinline__ uint32_t vtx(uint2 r, int s) {
     uint32_t w = (s < 2) ? r.x : r.y;
     return (s & 1) ? (w >> 16) : (w & 0xffffu);
-}
-
-__device__ __forceinline__ int32_t glob_tet(const BlockHdr &h, const int32_t *tmap, int32_t loc) {
-    if (loc < h.n_ext) return tmap[loc];
-    if (loc < h.n_ext + h.n_own) return h.t_base + (loc - h.n_ext);
-    return tmap[loc - h.n_own];
 }
 
 // Bits of `word` (word index q of a bitmap) that stand for local ids > x.
@@ -130,6 +177,37 @@ __device__ __forceinline__ int block_scan_thread(int v, int32_t *scr, int *total
     __syncthreads();
     *total = scr[32];
     return scr[warp] + incl - v;
+}
+
+// Exclusive scans of three values per thread over the block, in place;
+// totals to t[0..2].  scr needs 99 words.  Ends synced.
+__device__ __forceinline__ void block_scan3(int &a, int &b, int &c, int32_t *scr, int *t) {
+    const int nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ia = warp_incl_scan(a, lane), ib = warp_incl_scan(b, lane), ic = warp_incl_scan(c, lane);
+    if (lane == 31) {
+        scr[warp] = ia;
+        scr[33 + warp] = ib;
+        scr[66 + warp] = ic;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int w = lane < nw ? scr[33 * s + lane] : 0;
+            const int wi = warp_incl_scan(w, lane);
+            if (lane < nw) scr[33 * s + lane] = wi - w;
+            if (lane == 31) scr[33 * s + 32] = wi;
+        }
+    }
+    __syncthreads();
+    t[0] = scr[32];
+    t[1] = scr[65];
+    t[2] = scr[98];
+    a = scr[warp] + ia - a;
+    b = scr[33 + warp] + ib - b;
+    c = scr[66 + warp] + ic - c;
+    __syncthreads();
 }
 
 // Exclusive scan in place of a[0..n); returns the total.  Ends synced.
@@ -177,59 +255,96 @@ constexpr uint32_t kRefMask = (1u << 20) - 1u;
 constexpr uint32_t kMatch = 1u << 20;
 
 // ---------------------------------------------------------------------------
-// One cluster.  COUNT: no output writes; sizes -> sizes_out[5].
-// `it` points to a shared-memory copy of the work item.
+// One cluster.  COUNT: no output writes; sizes -> sizes_out[5].  SPILL: the
+// regions are global scratch and the rows arrive by vector loads instead of
+// the bulk copy.  `it` points to a shared-memory copy of the work item; bar
+// and phase are the CTA's block-copy barrier and its next parity.  Returns
+// false when a bounded wait ran out (the CTA must stop).
 // ---------------------------------------------------------------------------
-template <bool COUNT>
-__device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, uint32_t mask,
-                            const WorkItem *it, int64_t *sizes_out, int32_t *err) {
+template <bool COUNT, bool SPILL>
+__device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, uint32_t mask,
+                            const WorkItem *it, int64_t *sizes_out, int32_t *err, uint64_t *bar, uint32_t &phase) {
     const int NT = blockDim.x, NWARP = NT >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const Caps &caps = plan.caps;
-
-    // ---------------- A. stage the working set ----------------
     const int32_t *__restrict__ g = m.blocks + blk_word;
-    if (tid < kHdrWords) S.blk[tid] = __ldg(g + tid);
+
+    // ---------------- A. header, then the rows ----------------
+    if (tid == 0) {
+        const int4 *g4 = reinterpret_cast<const int4 *>(g);
+        const int4 a = __ldg(g4), b = __ldg(g4 + 1), c = __ldg(g4 + 2);
+        int4 *h4 = reinterpret_cast<int4 *>(S.hdr);
+        h4[0] = a;
+        h4[1] = b;
+        h4[2] = c;
+        // a = (n_ext, n_own, n_halo, nv_loc), b = (own_lo, nv_own, t_base, v_base), c = (nv_nb, n_bnd, -, -)
+        const int64_t n_tot = int64_t(a.x) + a.y + a.z;
+        const bool fits = a.x >= 0 && a.y >= 0 && a.z >= 0 && a.w >= 0 && b.x >= 0 && b.y >= 0 && c.x >= 0 &&
+                          c.y >= 0 && n_tot <= caps.n_tot && a.y <= caps.n_own && a.w <= caps.nv_loc &&
+                          b.y <= caps.nv_own && c.x <= caps.nv_nb && c.x <= a.w && int64_t(b.x) + b.y <= c.x &&
+                          2 * int64_t(c.y) + 1 <= caps.hcap;
+        int issued = 0;
+        if (fits && !SPILL && n_tot > 0) {
+            bulk_load(S.rows, g + blk_rows_off(a.w, a.x, a.z), uint32_t(4 * a4(2 * n_tot)), bar);
+            issued = 1;
+        }
+        S.hdr[12] = fits;
+        S.hdr[13] = issued;
+    }
     __syncthreads();
-    const BlockHdr h = *reinterpret_cast<const BlockHdr *>(S.blk);
-    const int64_t words = blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo);
-    const int W = (h.nv_nb + 31) >> 5;
-    const bool fits = words <= caps.blk_words && h.nv_own <= caps.nv_own && h.n_own <= caps.n_own &&
-                      h.nv_loc <= caps.nv_loc && h.nv_nb <= caps.nv_nb && h.nv_own >= 0 && h.n_own >= 0 &&
-                      h.n_ext >= 0 && h.n_halo >= 0 && h.n_bnd >= 0 && 2 * h.n_bnd + 1 <= caps.hcap &&
-                      W <= plan.wp && h.nv_nb <= h.nv_loc;
+    const BlockHdr h = *reinterpret_cast<const BlockHdr *>(S.hdr);
+    const bool fits = S.hdr[12] != 0, issued = S.hdr[13] != 0;
     if (!fits) {
         if (tid == 0) atomicOr(err, ERR_CAPACITY);
         __syncthreads();
-        return;
+        return true;
     }
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(g);
-        int4 *dst = reinterpret_cast<int4 *>(S.blk);
-        const int n4 = int(words >> 2);
-        for (int i = kHdrWords / 4 + tid; i < n4; i += NT) dst[i] = __ldg(src + i);
-    }
-    __syncthreads();
-    const int32_t *vmap = S.blk + kHdrWords;
-    const int32_t *tmap = S.blk + blk_tmap_off(h.nv_loc);
-    const uint2 *rows = reinterpret_cast<const uint2 *>(S.blk + blk_rows_off(h.nv_loc, h.n_ext, h.n_halo));
-    const int nvo = h.nv_own, lo = h.own_lo;
     const int n_ext = h.n_ext, n_own = h.n_own;
-    const int n_vtets = n_ext + n_own;
+    const int n_vtets = n_ext + n_own, n_tot = n_vtets + h.n_halo;
+    if (SPILL) {
+        const int4 *src = reinterpret_cast<const int4 *>(g + blk_rows_off(h.nv_loc, n_ext, h.n_halo));
+        int4 *dst = reinterpret_cast<int4 *>(S.rows);
+        const int n4 = int(a4(2 * int64_t(n_tot)) >> 2);
+        for (int i = tid; i < n4; i += NT) dst[i] = __ldg(src + i);
+        __syncthreads();
+    } else if (issued) {
+        bool ok = mbar_wait(bar, phase);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+            if (!ok) mbar_wait(bar, phase);  // the copy may still be in flight
+            return false;
+        }
+        phase ^= 1u;
+    }
+    const uint2 *rows = S.rows;
+    const int nvo = h.nv_own, lo = h.own_lo;
+    const uint32_t nvo_u = uint32_t(nvo);
     const bool want_tt = COUNT || (mask & R_TT);
     const bool do_vv = !COUNT && (mask & R_VV);
     const bool do_et = !COUNT && (mask & R_ET);
-    const uint32_t nvo_u = uint32_t(nvo);
+    const int32_t *__restrict__ vmap_g = g + kHdrWords;
+    const int32_t *__restrict__ tmap_g = g + blk_tmap_off(h.nv_loc);
+    const int32_t t_base = h.t_base;
+    // canonical id of a local tet
+    auto gtet = [&](int loc) -> int32_t {
+        if (loc < n_ext) return __ldg(tmap_g + loc);
+        if (loc < n_vtets) return t_base + (loc - n_ext);
+        return __ldg(tmap_g + (loc - n_own));
+    };
 
     // ---------------- B. VT ----------------
+    int vt_total;
     {
         const int pad = caps.nv_own;
-        uint32_t *cw = S.bmap;              // [warp][v]: counts, then next slot
-        uint32_t *mk = S.bmap + NWARP * pad;  // [warp][v]: lanes holding v
+        uint32_t *cw = S.cw;  // [warp][v]: counts, then next slot
+        uint32_t *mk = S.mk;  // [warp][v]: lanes holding v
         const int chunk = ((n_vtets + NWARP - 1) / NWARP + 31) & ~31;
         const int c0 = min(n_vtets, warp * chunk), c1 = min(n_vtets, c0 + chunk);
-        for (int i = tid; i < 2 * NWARP * pad; i += NT) S.bmap[i] = 0u;
+        for (int i = tid; i < NWARP * pad; i += NT) {
+            cw[i] = 0u;
+            mk[i] = 0u;
+        }
         __syncthreads();
         for (int i = c0 + lane; i < c1; i += 32) {
             const uint2 r = rows[i];
@@ -247,7 +362,7 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             S.vt_off[v] = tot;
         }
         __syncthreads();
-        const int vt_total = block_scan_array(S.vt_off, nvo, S.scan);
+        vt_total = block_scan_array(S.vt_off, nvo, S.scan);
         bool bad = vt_total > caps.n_vt;
         for (int v = tid; v < nvo; v += NT) {
             int run = S.vt_off[v];
@@ -262,250 +377,318 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         if (tid == 0) S.vt_off[nvo] = vt_total;
         if (__syncthreads_or(bad)) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
-            return;
+            return true;
         }
-        if (!bad) {
-            // fill in tet order, 32 tets per step of each warp
-            for (int i0 = c0; i0 < c1; i0 += 32) {
-                const int i = i0 + lane;
-                const uint2 r = i < c1 ? rows[i] : make_uint2(0xffffffffu, 0xffffffffu);
-                uint32_t d[4];
+        // fill in tet order, 32 tets per step of each warp
+        for (int i0 = c0; i0 < c1; i0 += 32) {
+            const int i = i0 + lane;
+            const uint2 r = i < c1 ? rows[i] : make_uint2(0xffffffffu, 0xffffffffu);
+            uint32_t d[4];
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    d[s] = vtx(r, s) - uint32_t(lo);
-                    if (d[s] < nvo_u) atomicOr(&mk[warp * pad + d[s]], 1u << lane);
-                }
-                __syncwarp();
-                uint32_t mm[4];
-#pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    mm[s] = 0u;
-                    if (d[s] < nvo_u) {
-                        mm[s] = mk[warp * pad + d[s]];
-                        S.vt_list[cw[warp * pad + d[s]] + __popc(mm[s] & lt)] = uint16_t(i);
-                    }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    if (d[s] < nvo_u && (mm[s] & lt) == 0u) {
-                        cw[warp * pad + d[s]] += uint32_t(__popc(mm[s]));
-                        mk[warp * pad + d[s]] = 0u;
-                    }
-                __syncwarp();
+            for (int s = 0; s < 4; ++s) {
+                d[s] = vtx(r, s) - uint32_t(lo);
+                if (d[s] < nvo_u) atomicOr(&mk[warp * pad + d[s]], 1u << lane);
             }
+            __syncwarp();
+            uint32_t mm[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                mm[s] = 0u;
+                if (d[s] < nvo_u) {
+                    mm[s] = mk[warp * pad + d[s]];
+                    S.vt_list[cw[warp * pad + d[s]] + __popc(mm[s] & lt)] = uint16_t(i);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                if (d[s] < nvo_u && (mm[s] & lt) == 0u) {
+                    cw[warp * pad + d[s]] += uint32_t(__popc(mm[s]));
+                    mk[warp * pad + d[s]] = 0u;
+                }
+            __syncwarp();
         }
         __syncthreads();
         if (COUNT) {
             if (tid == 0) sizes_out[SZ_VT] = vt_total;
         } else if (mask & R_VT) {
             for (int i = tid; i <= nvo; i += NT) it->vt_off[i] = S.vt_off[i];
-            for (int j = tid; j < vt_total; j += NT) it->vt_val[j] = glob_tet(h, tmap, S.vt_list[j]);
+            for (int j = tid; j < vt_total; j += NT) it->vt_val[j] = gtet(S.vt_list[j]);
         }
     }
-    if (!(COUNT || do_vv || do_et || want_tt)) return;
+    if (!(COUNT || do_vv || do_et || want_tt)) return true;
 
-    // ---------------- C. VV, ET and TT faces with an own lowest vertex ----
-    int32_t *c_vv = S.cnt, *c_e = S.cnt + caps.nv_own, *c_et = S.cnt + 2 * caps.nv_own;
-    __syncthreads();  // phase B counters and masks are dead
+    // ---------------- C1. neighbour bitmaps, per tet ----------------
+    const int W = (h.nv_nb + 31) >> 5;
+    const int nitems = nvo * W;
+    uint32_t *bm = S.bm;
+    uint8_t *pre = S.pre;
+    for (int i = tid; i < nitems; i += NT) bm[i] = 0u;
     if (want_tt) {
         uint32_t *nb32 = reinterpret_cast<uint32_t *>(S.nbr);
-        for (int i = tid; i < 2 * n_own; i += NT) nb32[i] = 0xffffffffu;
-    }
-    // pass 1: bitmaps and counts
-    for (int i = tid; i < nvo; i += NT) {
-        const int x = lo + i;
-        const int beg = S.vt_off[i], L = S.vt_off[i + 1] - beg;
-        uint32_t *bm = S.bmap + i * plan.wp;
-        for (int q = 0; q < W; ++q) bm[q] = 0u;
-        int etv = 0;
-        for (int j0 = 0; j0 < L; j0 += 4) {
-            uint2 r[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) r[u] = rows[S.vt_list[beg + min(j0 + u, L - 1)]];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (j0 + u < L) {
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) {
-                        const uint32_t y = vtx(r[u], s);
-                        if (int(y) != x) atomicOr(&bm[y >> 5], 1u << (y & 31));
-                        etv += int(y) > x;
-                    }
-                }
-            }
-        }
-        int vv = 0, ec = 0;
-        uint8_t *pr = S.pre + i * plan.wp;
-        for (int q = 0; q < W; ++q) {
-            const uint32_t word = bm[q];
-            pr[q] = uint8_t(ec);
-            vv += __popc(word);
-            ec += __popc(upper_bits(word, q, x));
-        }
-        c_vv[i] = vv;
-        c_e[i] = ec;
-        c_et[i] = etv;
+        for (int i = tid; i < 2 * n_own; i += NT) nb32[i] = FULL;
     }
     __syncthreads();
-    const int tot_vv = block_scan_array(c_vv, nvo, S.scan);
-    const int tot_e = block_scan_array(c_e, nvo, S.scan);
-    const int tot_et = block_scan_array(c_et, nvo, S.scan);
-    if (COUNT && tid == 0) {
-        sizes_out[SZ_VV] = tot_vv;
-        sizes_out[SZ_E] = tot_e;
-        sizes_out[SZ_ET] = tot_et;
+    int etv = 0;  // ET entries: each own vertex of a tet, once per vertex above it
+    for (int i = tid; i < n_vtets; i += NT) {
+        const uint2 r = rows[i];
+        const uint32_t v0 = r.x & 0xffffu, v1 = r.x >> 16, v2 = r.y & 0xffffu, v3 = r.y >> 16;
+        uint32_t d = v0 - uint32_t(lo);
+        if (d < nvo_u) {
+            uint32_t *row = bm + d * W;
+            atomicOr(row + (v1 >> 5), 1u << (v1 & 31));
+            atomicOr(row + (v2 >> 5), 1u << (v2 & 31));
+            atomicOr(row + (v3 >> 5), 1u << (v3 & 31));
+            etv += 3;
+        }
+        d = v1 - uint32_t(lo);
+        if (d < nvo_u) {
+            uint32_t *row = bm + d * W;
+            atomicOr(row + (v0 >> 5), 1u << (v0 & 31));
+            atomicOr(row + (v2 >> 5), 1u << (v2 & 31));
+            atomicOr(row + (v3 >> 5), 1u << (v3 & 31));
+            etv += 2;
+        }
+        d = v2 - uint32_t(lo);
+        if (d < nvo_u) {
+            uint32_t *row = bm + d * W;
+            atomicOr(row + (v0 >> 5), 1u << (v0 & 31));
+            atomicOr(row + (v1 >> 5), 1u << (v1 & 31));
+            atomicOr(row + (v3 >> 5), 1u << (v3 & 31));
+            etv += 1;
+        }
+        d = v3 - uint32_t(lo);
+        if (d < nvo_u) {
+            uint32_t *row = bm + d * W;
+            atomicOr(row + (v0 >> 5), 1u << (v0 & 31));
+            atomicOr(row + (v1 >> 5), 1u << (v1 & 31));
+            atomicOr(row + (v2 >> 5), 1u << (v2 & 31));
+        }
     }
-    if (tot_e > caps.max_e || (do_vv && tot_vv > caps.max_vv) || (do_et && tot_et > caps.max_etv)) {
-        if (tid == 0) atomicOr(err, ERR_CAPACITY);
-        return;
-    }
-    // pass 2: VV rows and the upper endpoints of the owned edges, staged
-    bool bad_up = false;
-    for (int i = tid; i < nvo; i += NT) {
-        const int x = lo + i;
-        uint32_t *bm = S.bmap + i * plan.wp;
-        int p = c_vv[i], e = c_e[i];
-        const int e_end = (i + 1 < nvo) ? c_e[i + 1] : tot_e;
-        bad_up |= (e_end - e) > caps.max_up || (e_end - e) > 255;
-        for (int q = 0; q < W; ++q) {
-            uint32_t word = bm[q];
-            uint32_t up = upper_bits(word, q, x);
-            bm[q] = up;  // from here on the bitmap holds the upper neighbours only
-            if (do_vv)
-                while (word) {
-                    const int b = __ffs(word) - 1;
-                    word &= word - 1;
-                    S.st_v[p++] = uint16_t(q * 32 + b);
+    __syncthreads();
+
+    // ---------------- C2. VV rows and owned edges, per bitmap word ----------
+    int tot[3];  // VV entries, owned edges, ET entries
+    {
+        const int per = (nitems + NT - 1) / NT;
+        const int b0 = min(nitems, tid * per), b1 = min(nitems, b0 + per);
+        const int x0 = W ? b0 / W : 0, q0 = b0 - x0 * W;
+        int cv = 0, ce = 0;
+        {
+            int x = x0, q = q0;
+            for (int i = b0; i < b1; ++i) {
+                const uint32_t w = bm[i];
+                cv += __popc(w);
+                ce += __popc(upper_bits(w, q, lo + x));
+                if (++q == W) {
+                    q = 0;
+                    ++x;
                 }
-            while (up) {
-                const int b = __ffs(up) - 1;
-                up &= up - 1;
-                S.st_ew[e++] = uint16_t(q * 32 + b);
+            }
+        }
+        int vrun = cv, erun = ce, et0 = etv;
+        block_scan3(vrun, erun, et0, S.scan, tot);
+        if (tot[1] > caps.max_e || (do_vv && tot[0] > caps.max_vv) || (do_et && tot[2] > caps.max_etv)) {
+            if (tid == 0) atomicOr(err, ERR_CAPACITY);
+            return true;
+        }
+        // edge index of the first upper bit of the vertex this range starts in
+        int ev = erun;
+        if (b0 < b1 && q0 > 0) {
+            const uint32_t *row = bm + x0 * W;
+            int back = 0;
+            for (int q = 0; q < q0; ++q) back += __popc(upper_bits(row[q], q, lo + x0));
+            ev = erun - back;
+        }
+        bool bad = false;
+        int x = x0, q = q0;
+        for (int i = b0; i < b1; ++i) {
+            if (q == 0) {
+                ev = erun;
+                S.c_vv[x] = vrun;
+                S.c_e[x] = erun;
+            }
+            uint32_t w = bm[i];
+            uint32_t up = upper_bits(w, q, lo + x);
+            const int rk = erun - ev;
+            bad |= rk > 255;
+            pre[i] = uint8_t(rk);
+            bm[i] = up;  // from here on the bitmaps hold the upper neighbours only
+            if (do_vv) {
+                while (w) {
+                    const int b = __ffs(w) - 1;
+                    w &= w - 1;
+                    S.st_v[vrun++] = uint16_t(q * 32 + b);
+                }
+            }
+            if (do_et) {
+                while (up) {
+                    const int b = __ffs(up) - 1;
+                    up &= up - 1;
+                    S.st_w[erun] = uint16_t(q * 32 + b);
+                    S.eu[erun] = uint16_t(x);
+                    ++erun;
+                }
+            } else {
+                erun += __popc(up);
+            }
+            if (++q == W) {
+                q = 0;
+                ++x;
+            }
+        }
+        if (tid == 0) {
+            S.c_vv[nvo] = tot[0];
+            S.c_e[nvo] = tot[1];
+        }
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) atomicOr(err, ERR_CAPACITY);
+            return true;
+        }
+        if (COUNT && tid == 0) {
+            sizes_out[SZ_VV] = tot[0];
+            sizes_out[SZ_E] = tot[1];
+            sizes_out[SZ_ET] = tot[2];
+        }
+        if (do_vv) {
+            for (int i = tid; i <= nvo; i += NT) it->vv_off[i] = S.c_vv[i];
+            for (int j = tid; j < tot[0]; j += NT) it->vv_val[j] = __ldg(vmap_g + S.st_v[j]);
+        }
+        if (do_et) {
+            for (int i = tid; i <= nvo; i += NT) it->eu_off[i] = S.c_e[i];
+            for (int e = tid; e < tot[1]; e += NT) it->e_w[e] = __ldg(vmap_g + S.st_w[e]);
+            if (tid == 0) it->et_off[tot[1]] = tot[2];
+        }
+    }
+    if (!(do_et || want_tt)) return true;
+    const int tot_e = tot[1], tot_etv = tot[2];
+    const int nch = plan.nch;
+    uint32_t *em = S.emask;
+    __syncthreads();  // VV and endpoint staging are dead: r2 takes the edge masks
+    for (int i = tid; i < tot_e * nch; i += NT) em[i] = 0u;
+    __syncthreads();
+
+    // ---------------- C3. edge tet masks, per VT incidence ----------------
+    {
+        const int n_vt = vt_total;
+        const int per = (n_vt + NT - 1) / NT;
+        const int k0 = min(n_vt, tid * per), k1 = min(n_vt, k0 + per);
+        if (k0 < k1) {
+            // own vertex whose row holds entry k0
+            int x = 0, hi = nvo - 1;
+            while (x < hi) {
+                const int mid = (x + hi + 1) >> 1;
+                if (S.vt_off[mid] <= k0) x = mid;
+                else hi = mid - 1;
+            }
+            int beg = S.vt_off[x], nxt = S.vt_off[x + 1];
+            for (int k = k0; k < k1; ++k) {
+                while (k >= nxt) {
+                    ++x;
+                    beg = nxt;
+                    nxt = S.vt_off[x + 1];
+                }
+                const int j = k - beg;
+                const uint2 r = rows[S.vt_list[k]];
+                const uint32_t X = uint32_t(lo + x);
+                const uint32_t v0 = r.x & 0xffffu, v1 = r.x >> 16, v2 = r.y & 0xffffu, v3 = r.y >> 16;
+                const uint32_t *bmx = bm + x * W;
+                const uint8_t *prx = pre + x * W;
+                const int eb = S.c_e[x];
+                uint32_t *emj = em + (j >> 5);
+                const uint32_t bit = 1u << (j & 31);
+                auto mark = [&](uint32_t y) {
+                    const int q = int(y >> 5);
+                    const int e = eb + int(prx[q]) + __popc(bmx[q] & ((1u << (y & 31)) - 1u));
+                    atomicOr(emj + e * nch, bit);
+                };
+                if (v0 == X) mark(v1);
+                if (v0 == X || v1 == X) mark(v2);
+                if (v3 != X) mark(v3);
             }
         }
     }
-    if (__syncthreads_or(bad_up)) {
-        if (tid == 0) atomicOr(err, ERR_CAPACITY);
-        return;
-    }
-    if (do_vv) {
-        for (int i = tid; i < nvo; i += NT) it->vv_off[i] = c_vv[i];
-        if (tid == 0) it->vv_off[nvo] = tot_vv;
-        for (int j = tid; j < tot_vv; j += NT) it->vv_val[j] = vmap[S.st_v[j]];
-    }
-    if (do_et) {
-        for (int i = tid; i < nvo; i += NT) it->eu_off[i] = c_e[i];
-        if (tid == 0) {
-            it->eu_off[nvo] = tot_e;
-            it->et_off[tot_e] = tot_et;
-        }
-        for (int e = tid; e < tot_e; e += NT) it->e_w[e] = vmap[S.st_ew[e]];
-    }
-    if (!(do_et || want_tt)) return;
-    __syncthreads();  // VV staging is dead: the edge masks take its place
-    {
-        // pass 3a: per-edge tet masks and TT links
-        const int nch = plan.nch;
+    __syncthreads();
+
+    // ---------------- C5. TT links of faces with an own lowest vertex ------
+    if (want_tt) {
         int32_t flags = 0;
-        for (int i = tid; i < nvo; i += NT) {
-            const int x = lo + i;
-            const int beg = S.vt_off[i], L = S.vt_off[i + 1] - beg;
-            const int e0 = c_e[i], E = ((i + 1 < nvo) ? c_e[i + 1] : tot_e) - e0;
-            const uint32_t *bm = S.bmap + i * plan.wp;
-            const uint8_t *pr = S.pre + i * plan.wp;
-            uint32_t *em = S.emask + e0 * nch;  // em[r * nch + c]
-            for (int q = 0; q < E * nch; ++q) em[q] = 0u;
-            // rank of an upper neighbour y among x's upper neighbours
-            auto rank = [&](uint32_t y) -> int {
+        for (int i = tid; i < n_own; i += NT) {
+            const int li = n_ext + i;
+            const uint2 r = rows[li];
+            const uint32_t v0 = r.x & 0xffffu, v1 = r.x >> 16, v2 = r.y & 0xffffu, v3 = r.y >> 16;
+            const uint32_t a = v0 - uint32_t(lo);
+            if (a >= nvo_u) {  // an internal tet's lowest vertex is own
+                flags |= ERR_BAD_BLOCK;
+                continue;
+            }
+            auto rank = [&](uint32_t x, uint32_t y) -> int {
                 const int q = int(y >> 5);
-                return int(pr[q]) + __popc(bm[q] & ((1u << (y & 31)) - 1u));
+                return S.c_e[x] + int(pre[x * W + q]) + __popc(bm[x * W + q] & ((1u << (y & 31)) - 1u));
             };
-            for (int j0 = 0; j0 < L; j0 += 4) {
-                uint2 r[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) r[u] = rows[S.vt_list[beg + min(j0 + u, L - 1)]];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u;
-                    if (j < L) {
-#pragma unroll
-                        for (int s = 1; s < 4; ++s) {
-                            const uint32_t y = vtx(r[u], s);
-                            if (int(y) > x) atomicOr(&em[rank(y) * nch + (j >> 5)], 1u << (j & 31));
+            // partner of tet li across the face (x, w1, w2): the other set bit
+            // of mask(x, w1) & mask(x, w2), positions in VT(x)
+            auto link = [&](int e1, int e2, int base, int opp) {
+                int found = 0, partner = -1;
+                for (int c = 0; c < nch; ++c) {
+                    uint32_t mm = em[e1 * nch + c] & em[e2 * nch + c];
+                    while (mm) {
+                        const int b = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const int t = S.vt_list[base + c * 32 + b];
+                        if (t != li) {
+                            if (partner < 0) partner = t;
+                            ++found;
                         }
                     }
                 }
-            }
-            if (!want_tt) continue;
-            // faces (x, w1, w2) with x lowest: the tets are the bits of
-            // em[w1] & em[w2]; links are kept for internal tets
-            for (int j0 = 0; j0 < L; j0 += 4) {
-                int tl[4];
-                uint2 r[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) tl[u] = S.vt_list[beg + min(j0 + u, L - 1)];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) r[u] = rows[tl[u]];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u;
-                    const uint32_t io = uint32_t(tl[u] - n_ext);
-                    if (j >= L || io >= uint32_t(n_own)) continue;
-                    const int p = (int(vtx(r[u], 0)) == x) ? 0 : (int(vtx(r[u], 1)) == x) ? 1 : 2;
-                    if (p >= 2) continue;
-                    int rk[4] = {0, 0, 0, 0};
-#pragma unroll
-                    for (int s2 = 1; s2 < 4; ++s2)
-                        if (s2 > p) rk[s2] = rank(vtx(r[u], s2));
-#pragma unroll
-                    for (int a = 1; a < 4; ++a)
-#pragma unroll
-                        for (int b2 = a + 1; b2 < 4; ++b2) {
-                            if (a <= p) continue;
-                            const int opp = 6 - p - a - b2;  // the slot outside {p, a, b2}
-                            int partner = -1, found = 0;
-                            for (int c = 0; c < nch; ++c) {
-                                uint32_t mk2 = em[rk[a] * nch + c] & em[rk[b2] * nch + c];
-                                if (c == (j >> 5)) mk2 &= ~(1u << (j & 31));
-                                found += __popc(mk2);
-                                if (mk2 && partner < 0) partner = 32 * c + __ffs(mk2) - 1;
-                            }
-                            if (found > 1) flags |= ERR_NONMANIFOLD;
-                            if (partner >= 0) S.nbr[io * 4 + opp] = S.vt_list[beg + partner];
-                        }
-                }
-            }
+                if (found > 1) flags |= ERR_NONMANIFOLD;
+                if (partner >= 0) S.nbr[i * 4 + opp] = uint16_t(partner);
+            };
+            const int e1 = rank(a, v1), e2 = rank(a, v2), e3 = rank(a, v3);
+            const int base_a = S.vt_off[a];
+            link(e1, e2, base_a, 3);
+            link(e1, e3, base_a, 2);
+            link(e2, e3, base_a, 1);
+            const uint32_t b = v1 - uint32_t(lo);
+            if (b < nvo_u) link(rank(b, v2), rank(b, v3), S.vt_off[b], 0);
         }
         if (flags) atomicOr(err, flags);
-        __syncthreads();  // bitmaps are dead: the ET value staging takes their place
-        if (do_et) {
-            // pass 3b: ET rows from the masks; each edge's first mask word
-            // then holds its row offset for the copy-out
-            uint16_t *st_et = reinterpret_cast<uint16_t *>(S.bmap);
-            for (int i = tid; i < nvo; i += NT) {
-                const int beg = S.vt_off[i];
-                const int e0 = c_e[i], E = ((i + 1 < nvo) ? c_e[i + 1] : tot_e) - e0;
-                uint32_t *em = S.emask + e0 * nch;
-                int t = c_et[i];
-                for (int rr = 0; rr < E; ++rr) {
-                    const int t0 = t;
-                    for (int c = 0; c < nch; ++c) {
-                        uint32_t mk2 = em[rr * nch + c];
-                        while (mk2) {
-                            const int b = __ffs(mk2) - 1;
-                            mk2 &= mk2 - 1;
-                            st_et[t++] = S.vt_list[beg + 32 * c + b];
-                        }
-                    }
-                    em[rr * nch] = uint32_t(t0);
+    }
+    __syncthreads();  // bitmaps and rank prefixes are dead: r1 takes the ET staging
+
+    // ---------------- C4. ET rows, per edge ----------------
+    if (do_et) {
+        uint16_t *st_et = S.st_et;
+        const int per = (tot_e + NT - 1) / NT;
+        const int e0 = min(tot_e, tid * per), e1 = min(tot_e, e0 + per);
+        int cnt = 0;
+        for (int e = e0; e < e1; ++e)
+            for (int c = 0; c < nch; ++c) cnt += __popc(em[e * nch + c]);
+        int total;
+        int run = block_scan_thread(cnt, S.scan, &total);
+        if (total != tot_etv) {  // every (own vertex, tet, upper vertex) sets one distinct bit
+            if (tid == 0) atomicOr(err, ERR_BAD_BLOCK);
+            __syncthreads();
+            return true;
+        }
+        for (int e = e0; e < e1; ++e) {
+            const int base = S.vt_off[S.eu[e]];
+            const int t0 = run;
+            for (int c = 0; c < nch; ++c) {
+                uint32_t mm = em[e * nch + c];
+                while (mm) {
+                    const int b = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    st_et[run++] = S.vt_list[base + c * 32 + b];
                 }
             }
-            __syncthreads();
-            for (int e = tid; e < tot_e; e += NT) it->et_off[e] = int32_t(S.emask[e * nch]);
-            for (int j = tid; j < tot_et; j += NT) it->et_val[j] = glob_tet(h, tmap, st_et[j]);
+            em[e * nch] = uint32_t(t0);  // the edge's first mask word now holds its row offset
         }
         __syncthreads();
+        for (int e = tid; e < tot_e; e += NT) it->et_off[e] = int32_t(em[e * nch]);
+        for (int j = tid; j < tot_etv; j += NT) it->et_val[j] = gtet(st_et[j]);
+        __syncthreads();  // ET staging is dead: r1 takes the face hash
     }
 
     if (want_tt) {
@@ -558,7 +741,7 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         if (flags) atomicOr(err, flags);
         __syncthreads();
-        // counts per internal tet -> offsets
+        // ---------------- E. TT rows ----------------
         int32_t *tcnt = S.tcnt;
         for (int i = tid; i < n_own; i += NT) {
             const uint2 nb = *reinterpret_cast<const uint2 *>(&S.nbr[i * 4]);
@@ -572,24 +755,24 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         } else {
             if (tot_tt > caps.max_tt) {
                 if (tid == 0) atomicOr(err, ERR_CAPACITY);
-                return;
+                return true;
             }
             for (int i = tid; i < n_own; i += NT) {
                 const uint2 nb = *reinterpret_cast<const uint2 *>(&S.nbr[i * 4]);
                 const uint32_t n0 = nb.x & 0xffffu, n1 = nb.x >> 16, n2 = nb.y & 0xffffu, n3 = nb.y >> 16;
                 // absent neighbours sort last as INT32_MAX
-                int32_t v0 = n0 != 0xffffu ? glob_tet(h, tmap, int32_t(n0)) : INT32_MAX;
-                int32_t v1 = n1 != 0xffffu ? glob_tet(h, tmap, int32_t(n1)) : INT32_MAX;
-                int32_t v2 = n2 != 0xffffu ? glob_tet(h, tmap, int32_t(n2)) : INT32_MAX;
-                int32_t v3 = n3 != 0xffffu ? glob_tet(h, tmap, int32_t(n3)) : INT32_MAX;
-                cswap(v0, v1); cswap(v2, v3); cswap(v0, v2); cswap(v1, v3); cswap(v1, v2);
+                int32_t w0 = n0 != 0xffffu ? gtet(int32_t(n0)) : INT32_MAX;
+                int32_t w1 = n1 != 0xffffu ? gtet(int32_t(n1)) : INT32_MAX;
+                int32_t w2 = n2 != 0xffffu ? gtet(int32_t(n2)) : INT32_MAX;
+                int32_t w3 = n3 != 0xffffu ? gtet(int32_t(n3)) : INT32_MAX;
+                cswap(w0, w1); cswap(w2, w3); cswap(w0, w2); cswap(w1, w3); cswap(w1, w2);
                 const int p = tcnt[i];
                 it->tt_off[i] = p;
                 int32_t *o = S.st_tt + p;
-                if (v0 != INT32_MAX) o[0] = v0;
-                if (v1 != INT32_MAX) o[1] = v1;
-                if (v2 != INT32_MAX) o[2] = v2;
-                if (v3 != INT32_MAX) o[3] = v3;
+                if (w0 != INT32_MAX) o[0] = w0;
+                if (w1 != INT32_MAX) o[1] = w1;
+                if (w2 != INT32_MAX) o[2] = w2;
+                if (w3 != INT32_MAX) o[3] = w3;
             }
             if (tid == 0) it->tt_off[n_own] = tot_tt;
             __syncthreads();
@@ -597,6 +780,7 @@ __device__ void run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
     }
     __syncthreads();
+    return true;
 }
 
 // SPILL: the cluster's regions live in a per-CTA slice of global scratch
@@ -607,9 +791,15 @@ __device__ __forceinline__ char *region_base(char *smem, char *gscratch, const S
     return SPILL ? gscratch + size_t(blockIdx.x) * size_t(plan.total) : smem;
 }
 
-// Blocks have up to 1024 threads (one per own vertex), so every cluster
-// kernel is bounded to 64 registers per thread.
+// Blocks have up to 1024 threads, so every cluster kernel is bounded to 64
+// registers per thread.
 constexpr int kMaxThreads = 1024;
+
+template <bool SPILL>
+__device__ __forceinline__ void init_barrier(uint64_t *bar) {
+    if (!SPILL && threadIdx.x == 0) mbar_init(bar);
+    __syncthreads();
+}
 
 template <bool SPILL>
 __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan plan, const int32_t *ids, int32_t n, int64_t *sizes, int32_t *err,
@@ -618,6 +808,9 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan 
     const Smem S = carve(region_base<SPILL>(smem, gscratch, plan), plan);
     __shared__ int32_t s_idx;
     __shared__ int64_t s_sizes[SZ_N];
+    __shared__ __align__(8) uint64_t s_bar;
+    init_barrier<SPILL>(&s_bar);
+    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
         __syncthreads();
@@ -631,7 +824,7 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan 
         }
         if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
         __syncthreads();
-        run_cluster<true>(m, plan, S, m.blk_off[k], 0u, nullptr, s_sizes, err);
+        if (!run_cluster<true, SPILL>(m, plan, S, m.blk_off[k], 0u, nullptr, s_sizes, err, &s_bar, phase)) return;
         __syncthreads();
         if (threadIdx.x < SZ_N) sizes[int64_t(k) * SZ_N + threadIdx.x] = s_sizes[threadIdx.x];
     }
@@ -644,6 +837,9 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel(DevMesh m, SmemPlan 
     const Smem S = carve(region_base<SPILL>(smem, gscratch, plan), plan);
     __shared__ int32_t s_idx;
     __shared__ WorkItem s_item;
+    __shared__ __align__(8) uint64_t s_bar;
+    init_barrier<SPILL>(&s_bar);
+    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
         __syncthreads();
@@ -657,7 +853,8 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel(DevMesh m, SmemPlan 
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
-        run_cluster<false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err);
+        if (!run_cluster<false, SPILL>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err, &s_bar, phase))
+            return;
     }
 }
 
@@ -667,13 +864,16 @@ __global__ void __launch_bounds__(kMaxThreads) build_one_kernel(DevMesh m, SmemP
     extern __shared__ __align__(16) char smem[];
     const Smem S = carve(region_base<SPILL>(smem, gscratch, plan), plan);
     __shared__ WorkItem s_item;
+    __shared__ __align__(8) uint64_t s_bar;
+    init_barrier<SPILL>(&s_bar);
+    uint32_t phase = 0;
     if (threadIdx.x == 0) s_item = items[index];
     __syncthreads();
     if (s_item.k < 0 || s_item.k >= m.K) {
         if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
         return;
     }
-    run_cluster<false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err);
+    run_cluster<false, SPILL>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err, &s_bar, phase);
 }
 
 // ---------------------------------------------------------------------------
@@ -710,6 +910,9 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, S
     const Smem S = carve(smem, plan);
     __shared__ long long s_t;
     __shared__ WorkItem s_item;
+    __shared__ __align__(8) uint64_t s_bar;
+    init_barrier<false>(&s_bar);
+    uint32_t phase = 0;
     unsigned long long last = globaltimer();
     for (;;) {
         if (threadIdx.x == 0) {
@@ -741,10 +944,12 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, S
         __syncthreads();
         const long long t = s_t;
         if (t < 0) break;
+        bool go_on = true;
         if (s_item.k >= 0 && s_item.k < m.K)
-            run_cluster<false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err);
+            go_on = run_cluster<false, false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err, &s_bar, phase);
         else if (threadIdx.x == 0)
             atomicOr(err, ERR_BAD_ITEM);
+        if (!go_on) break;  // a bounded wait ran out; the slot stays not done
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence_system();
@@ -895,44 +1100,50 @@ SmemPlan plan_smem(const Caps &c, int threads) {
     SmemPlan p{};
     p.threads = threads;
     p.caps = c;
-    const int nwarp = threads / 32;
-    const int W = (c.nv_nb + 31) / 32;
+    const int64_t nwarp = threads / 32;
+    const int64_t nvo = c.nv_own;
+    p.W = std::max(1, (c.nv_nb + 31) / 32);
     p.nch = std::max(1, (c.max_deg + 31) / 32);
-    p.wp = std::max(W, 1) | 1;
     int64_t off = 0;
-    p.blk = 0;
-    off = a16(int64_t(4) * c.blk_words);
+    p.hdr = 0;
+    off = 64;
     p.scan = int32_t(off);
-    off = a16(off + 4 * 40);
-    p.cnt = int32_t(off);
-    off = a16(off + 4 * 3 * int64_t(c.nv_own));
-    p.nbr = int32_t(off);
-    off = a16(off + 8 * int64_t(c.n_own));
+    off = a16(off + 4 * 100);
+    p.rows = int32_t(off);
+    off = a16(off + 4 * a4(2 * int64_t(c.n_tot)));
     p.vt_off = int32_t(off);
-    off = a16(off + 4 * (int64_t(c.nv_own) + 1));
+    off = a16(off + 4 * (nvo + 1));
     p.vt_list = int32_t(off);
     off = a16(off + 2 * int64_t(c.n_vt));
-    p.bmap = int32_t(off);
-    // phase B: per-warp counters and masks; phase C: per-vertex bitmaps and
-    // their rank prefixes, later the ET value staging
-    const int64_t bm_b = 8 * int64_t(nwarp) * c.nv_own;
-    const int64_t bm_c = a16(4 * int64_t(c.nv_own) * p.wp) + int64_t(c.nv_own) * p.wp;
-    const int64_t st_et = 2 * int64_t(c.max_etv);
-    p.pre = int32_t(off + a16(4 * int64_t(c.nv_own) * p.wp));
-    off = a16(off + std::max(bm_b, std::max(bm_c, st_et)));
-    p.st_ew = int32_t(off);
+    p.c_vv = int32_t(off);
+    off = a16(off + 4 * (nvo + 1));
+    p.c_e = int32_t(off);
+    off = a16(off + 4 * (nvo + 1));
+    p.nbr = int32_t(off);
+    off = a16(off + 8 * int64_t(c.n_own));
+    p.eu = int32_t(off);
     off = a16(off + 2 * int64_t(c.max_e));
-    // VV staging, later the per-edge tet masks
-    p.emask = int32_t(off);
-    p.st_v = p.emask;
-    const int64_t end_c = a16(off + std::max<int64_t>(4 * int64_t(c.max_e) * p.nch, 2 * int64_t(c.max_vv)));
-    // phase D overlays from vt_off (cnt and nbr stay)
-    p.hash = p.vt_off;
-    p.tcnt = int32_t(a16(int64_t(p.hash) + 4 * int64_t(c.hcap)));
-    p.st_tt = int32_t(a16(int64_t(p.tcnt) + 4 * (int64_t(c.n_own) + 1)));
-    const int64_t end_d = a16(int64_t(p.st_tt) + 4 * int64_t(c.max_tt));
-    const int64_t tot = std::max(end_c, end_d);
-    p.total = tot > INT32_MAX ? INT32_MAX : int32_t(tot);
+    // r2: VV staging + upper-endpoint staging, then the edge masks
+    p.r2 = int32_t(off);
+    p.st_w = int32_t(a16(off + 2 * int64_t(c.max_vv)));
+    const int64_t r2 = std::max<int64_t>(4 * int64_t(c.max_e) * p.nch,
+                                         a16(2 * int64_t(c.max_vv)) + 2 * int64_t(c.max_e));
+    off = a16(off + r2);
+    // r1: phase B counters + lane masks | bitmaps + rank prefixes | ET
+    // staging | face hash + TT counts + TT staging
+    p.r1 = int32_t(off);
+    const int64_t cw = a16(4 * nwarp * nvo);
+    p.mk = int32_t(off + cw);
+    const int64_t bm = a16(4 * nvo * p.W);
+    p.pre = int32_t(off + bm);
+    const int64_t hs = a16(4 * int64_t(c.hcap));
+    p.tcnt = int32_t(off + hs);
+    const int64_t tc = a16(4 * (int64_t(c.n_own) + 1));
+    p.st_tt = int32_t(off + hs + tc);
+    const int64_t r1 = std::max(std::max(cw + 4 * nwarp * nvo, bm + nvo * p.W),
+                                std::max(2 * int64_t(c.max_etv), hs + tc + 4 * int64_t(c.max_tt)));
+    off = a16(off + r1);
+    p.total = off > INT32_MAX ? INT32_MAX : int32_t(off);
     return p;
 }
 
