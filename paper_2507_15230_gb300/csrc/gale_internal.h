@@ -119,7 +119,7 @@ struct Caps {
 //       the TT counts and the TT staging.
 struct SmemPlan {
     int32_t threads;
-    int32_t W;          // words of the largest neighbour bitmap
+    int32_t W;          // row stride (words, odd) of the neighbour bitmaps
     int32_t nch;        // 32-tet chunks of the longest VT row
     int32_t pad;
     int32_t hdr;        // int32[16]: header copy and per-cluster flags

@@ -142,15 +142,6 @@ __device__ __forceinline__ uint32_t vtx(uint2 r, int s) {
     return (s & 1) ? (w >> 16) : (w & 0xffffu);
 }
 
-// Bits of `word` (word index q of a bitmap) that stand for local ids > x.
-__device__ __forceinline__ uint32_t upper_bits(uint32_t word, int q, int x) {
-    const int qx = x >> 5;
-    if (q > qx) return word;
-    if (q < qx) return 0u;
-    const int b = x & 31;
-    return b == 31 ? 0u : (word & (FULL << (b + 1)));
-}
-
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -210,11 +201,33 @@ __device__ __forceinline__ void block_scan3(int &a, int &b, int &c, int32_t *scr
     __syncthreads();
 }
 
+// Length of each thread's contiguous range when n items are split over the
+// block: odd, so that neighbouring threads start in different banks.
+__device__ __forceinline__ int range_len(int n) {
+    const int per = (n + int(blockDim.x) - 1) / int(blockDim.x);
+    return per > 1 ? (per | 1) : per;
+}
+
+// dst[j] = f(j) for j < n over the block, four loads in flight per thread
+// before their stores (the values come through L2 from the block's maps).
+template <typename F>
+__device__ __forceinline__ void copy_out(int32_t *__restrict__ dst, int n, F f) {
+    const int NT = blockDim.x;
+    int j = threadIdx.x;
+    for (; j + 3 * NT < n; j += 4 * NT) {
+        const int32_t a = f(j), b = f(j + NT), c = f(j + 2 * NT), d = f(j + 3 * NT);
+        dst[j] = a;
+        dst[j + NT] = b;
+        dst[j + 2 * NT] = c;
+        dst[j + 3 * NT] = d;
+    }
+    for (; j < n; j += NT) dst[j] = f(j);
+}
+
 // Exclusive scan in place of a[0..n); returns the total.  Ends synced.
 __device__ int block_scan_array(int32_t *a, int n, int32_t *scr) {
-    const int NT = blockDim.x;
-    const int per = (n + NT - 1) / NT;
-    const int b = threadIdx.x * per;
+    const int per = range_len(n);
+    const int b = min(n, int(threadIdx.x) * per);
     const int e = min(n, b + per);
     int s = 0;
     for (int i = b; i < e; ++i) s += a[i];
@@ -413,17 +426,17 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             if (tid == 0) sizes_out[SZ_VT] = vt_total;
         } else if (mask & R_VT) {
             for (int i = tid; i <= nvo; i += NT) it->vt_off[i] = S.vt_off[i];
-            for (int j = tid; j < vt_total; j += NT) it->vt_val[j] = gtet(S.vt_list[j]);
+            copy_out(it->vt_val, vt_total, [&](int j) { return gtet(S.vt_list[j]); });
         }
     }
     if (!(COUNT || do_vv || do_et || want_tt)) return true;
 
     // ---------------- C1. neighbour bitmaps, per tet ----------------
-    const int W = (h.nv_nb + 31) >> 5;
-    const int nitems = nvo * W;
+    const int W = (h.nv_nb + 31) >> 5;  // bitmap words per vertex
+    const int WP = W | 1;                // row stride (odd: rows start in different banks)
     uint32_t *bm = S.bm;
     uint8_t *pre = S.pre;
-    for (int i = tid; i < nitems; i += NT) bm[i] = 0u;
+    for (int i = tid; i < nvo * WP; i += NT) bm[i] = 0u;
     if (want_tt) {
         uint32_t *nb32 = reinterpret_cast<uint32_t *>(S.nbr);
         for (int i = tid; i < 2 * n_own; i += NT) nb32[i] = FULL;
@@ -435,7 +448,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         const uint32_t v0 = r.x & 0xffffu, v1 = r.x >> 16, v2 = r.y & 0xffffu, v3 = r.y >> 16;
         uint32_t d = v0 - uint32_t(lo);
         if (d < nvo_u) {
-            uint32_t *row = bm + d * W;
+            uint32_t *row = bm + d * WP;
             atomicOr(row + (v1 >> 5), 1u << (v1 & 31));
             atomicOr(row + (v2 >> 5), 1u << (v2 & 31));
             atomicOr(row + (v3 >> 5), 1u << (v3 & 31));
@@ -443,7 +456,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         d = v1 - uint32_t(lo);
         if (d < nvo_u) {
-            uint32_t *row = bm + d * W;
+            uint32_t *row = bm + d * WP;
             atomicOr(row + (v0 >> 5), 1u << (v0 & 31));
             atomicOr(row + (v2 >> 5), 1u << (v2 & 31));
             atomicOr(row + (v3 >> 5), 1u << (v3 & 31));
@@ -451,7 +464,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         d = v2 - uint32_t(lo);
         if (d < nvo_u) {
-            uint32_t *row = bm + d * W;
+            uint32_t *row = bm + d * WP;
             atomicOr(row + (v0 >> 5), 1u << (v0 & 31));
             atomicOr(row + (v1 >> 5), 1u << (v1 & 31));
             atomicOr(row + (v3 >> 5), 1u << (v3 & 31));
@@ -459,7 +472,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         d = v3 - uint32_t(lo);
         if (d < nvo_u) {
-            uint32_t *row = bm + d * W;
+            uint32_t *row = bm + d * WP;
             atomicOr(row + (v0 >> 5), 1u << (v0 & 31));
             atomicOr(row + (v1 >> 5), 1u << (v1 & 31));
             atomicOr(row + (v2 >> 5), 1u << (v2 & 31));
@@ -467,79 +480,94 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     }
     __syncthreads();
 
-    // ---------------- C2. VV rows and owned edges, per bitmap word ----------
+    // ---------------- C2. VV rows and owned edges, per own vertex ----------
     int tot[3];  // VV entries, owned edges, ET entries
     {
-        const int per = (nitems + NT - 1) / NT;
-        const int b0 = min(nitems, tid * per), b1 = min(nitems, b0 + per);
-        const int x0 = W ? b0 / W : 0, q0 = b0 - x0 * W;
-        int cv = 0, ce = 0;
-        {
-            int x = x0, q = q0;
-            for (int i = b0; i < b1; ++i) {
-                const uint32_t w = bm[i];
+        // counts per vertex
+        for (int x = tid; x < nvo; x += NT) {
+            const uint32_t *row = bm + x * WP;
+            const int X = lo + x, qx = X >> 5;
+            const uint32_t hb = (X & 31) == 31 ? 0u : (FULL << ((X & 31) + 1));
+            int cv = 0, ce = 0;
+            for (int q = 0; q < W; ++q) {
+                const uint32_t w = row[q];
                 cv += __popc(w);
-                ce += __popc(upper_bits(w, q, lo + x));
-                if (++q == W) {
-                    q = 0;
-                    ++x;
-                }
+                ce += __popc(w & (q < qx ? 0u : (q > qx ? FULL : hb)));
+            }
+            S.c_vv[x] = cv;
+            S.c_e[x] = ce;
+        }
+        __syncthreads();
+        // exclusive scans of both count arrays, and the ET total
+        {
+            const int per = range_len(nvo);
+            const int x0 = min(nvo, tid * per), x1 = min(nvo, x0 + per);
+            int sv = 0, se = 0;
+            for (int x = x0; x < x1; ++x) {
+                sv += S.c_vv[x];
+                se += S.c_e[x];
+            }
+            int et0 = etv;
+            block_scan3(sv, se, et0, S.scan, tot);
+            for (int x = x0; x < x1; ++x) {
+                const int a = S.c_vv[x], b = S.c_e[x];
+                S.c_vv[x] = sv;
+                S.c_e[x] = se;
+                sv += a;
+                se += b;
+            }
+            if (tid == 0) {
+                S.c_vv[nvo] = tot[0];
+                S.c_e[nvo] = tot[1];
             }
         }
-        int vrun = cv, erun = ce, et0 = etv;
-        block_scan3(vrun, erun, et0, S.scan, tot);
         if (tot[1] > caps.max_e || (do_vv && tot[0] > caps.max_vv) || (do_et && tot[2] > caps.max_etv)) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             return true;
         }
-        // edge index of the first upper bit of the vertex this range starts in
-        int ev = erun;
-        if (b0 < b1 && q0 > 0) {
-            const uint32_t *row = bm + x0 * W;
-            int back = 0;
-            for (int q = 0; q < q0; ++q) back += __popc(upper_bits(row[q], q, lo + x0));
-            ev = erun - back;
-        }
+        __syncthreads();
+        // rows: one loop step per set bit, words visited through an
+        // occupancy mask; the word holding x keeps its upper bits only and
+        // every word with upper bits records the rank of its first one
         bool bad = false;
-        int x = x0, q = q0;
-        for (int i = b0; i < b1; ++i) {
-            if (q == 0) {
-                ev = erun;
-                S.c_vv[x] = vrun;
-                S.c_e[x] = erun;
-            }
-            uint32_t w = bm[i];
-            uint32_t up = upper_bits(w, q, lo + x);
-            const int rk = erun - ev;
-            bad |= rk > 255;
-            pre[i] = uint8_t(rk);
-            bm[i] = up;  // from here on the bitmaps hold the upper neighbours only
-            if (do_vv) {
-                while (w) {
-                    const int b = __ffs(w) - 1;
-                    w &= w - 1;
-                    S.st_v[vrun++] = uint16_t(q * 32 + b);
+        for (int x = tid; x < nvo; x += NT) {
+            uint32_t *row = bm + x * WP;
+            uint8_t *prx = pre + x * WP;
+            const int X = lo + x, qx = X >> 5;
+            const uint32_t hb = (X & 31) == 31 ? 0u : (FULL << ((X & 31) + 1));
+            int vrun = S.c_vv[x], erun = S.c_e[x];
+            const int e_first = erun;
+            for (int q0 = 0; q0 < W; q0 += 32) {
+                const int qn = min(32, W - q0);
+                uint32_t occ = 0u;
+                for (int u = 0; u < qn; ++u) occ |= (row[q0 + u] != 0u ? 1u : 0u) << u;
+                uint32_t w = 0u, um = 0u;
+                int q = 0;
+                for (;;) {
+                    if (w == 0u) {
+                        if (occ == 0u) break;
+                        q = q0 + __ffs(occ) - 1;
+                        occ &= occ - 1u;
+                        w = row[q];
+                        um = q < qx ? 0u : (q > qx ? FULL : hb);
+                        if (w & um) prx[q] = uint8_t(erun - e_first);
+                        if (q == qx) row[q] = w & hb;
+                    }
+                    const uint32_t bit = w & (0u - w);
+                    w ^= bit;
+                    const uint16_t id = uint16_t(q * 32 + __ffs(bit) - 1);
+                    if (do_vv) S.st_v[vrun] = id;
+                    ++vrun;
+                    if (bit & um) {
+                        if (do_et) {
+                            S.st_w[erun] = id;
+                            S.eu[erun] = uint16_t(x);
+                        }
+                        ++erun;
+                    }
                 }
             }
-            if (do_et) {
-                while (up) {
-                    const int b = __ffs(up) - 1;
-                    up &= up - 1;
-                    S.st_w[erun] = uint16_t(q * 32 + b);
-                    S.eu[erun] = uint16_t(x);
-                    ++erun;
-                }
-            } else {
-                erun += __popc(up);
-            }
-            if (++q == W) {
-                q = 0;
-                ++x;
-            }
-        }
-        if (tid == 0) {
-            S.c_vv[nvo] = tot[0];
-            S.c_e[nvo] = tot[1];
+            bad |= erun - e_first > 255;
         }
         if (__syncthreads_or(bad)) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
@@ -552,11 +580,11 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         if (do_vv) {
             for (int i = tid; i <= nvo; i += NT) it->vv_off[i] = S.c_vv[i];
-            for (int j = tid; j < tot[0]; j += NT) it->vv_val[j] = __ldg(vmap_g + S.st_v[j]);
+            copy_out(it->vv_val, tot[0], [&](int j) { return __ldg(vmap_g + S.st_v[j]); });
         }
         if (do_et) {
             for (int i = tid; i <= nvo; i += NT) it->eu_off[i] = S.c_e[i];
-            for (int e = tid; e < tot[1]; e += NT) it->e_w[e] = __ldg(vmap_g + S.st_w[e]);
+            copy_out(it->e_w, tot[1], [&](int e) { return __ldg(vmap_g + S.st_w[e]); });
             if (tid == 0) it->et_off[tot[1]] = tot[2];
         }
     }
@@ -571,7 +599,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     // ---------------- C3. edge tet masks, per VT incidence ----------------
     {
         const int n_vt = vt_total;
-        const int per = (n_vt + NT - 1) / NT;
+        const int per = range_len(n_vt);
         const int k0 = min(n_vt, tid * per), k1 = min(n_vt, k0 + per);
         if (k0 < k1) {
             // own vertex whose row holds entry k0
@@ -582,19 +610,22 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 else hi = mid - 1;
             }
             int beg = S.vt_off[x], nxt = S.vt_off[x + 1];
+            const uint32_t *bmx = bm + x * WP;
+            const uint8_t *prx = pre + x * WP;
+            int eb = S.c_e[x];
             for (int k = k0; k < k1; ++k) {
                 while (k >= nxt) {
                     ++x;
                     beg = nxt;
                     nxt = S.vt_off[x + 1];
+                    bmx += WP;
+                    prx += WP;
+                    eb = S.c_e[x];
                 }
                 const int j = k - beg;
                 const uint2 r = rows[S.vt_list[k]];
                 const uint32_t X = uint32_t(lo + x);
                 const uint32_t v0 = r.x & 0xffffu, v1 = r.x >> 16, v2 = r.y & 0xffffu, v3 = r.y >> 16;
-                const uint32_t *bmx = bm + x * W;
-                const uint8_t *prx = pre + x * W;
-                const int eb = S.c_e[x];
                 uint32_t *emj = em + (j >> 5);
                 const uint32_t bit = 1u << (j & 31);
                 auto mark = [&](uint32_t y) {
@@ -624,7 +655,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             }
             auto rank = [&](uint32_t x, uint32_t y) -> int {
                 const int q = int(y >> 5);
-                return S.c_e[x] + int(pre[x * W + q]) + __popc(bm[x * W + q] & ((1u << (y & 31)) - 1u));
+                return S.c_e[x] + int(pre[x * WP + q]) + __popc(bm[x * WP + q] & ((1u << (y & 31)) - 1u));
             };
             // partner of tet li across the face (x, w1, w2): the other set bit
             // of mask(x, w1) & mask(x, w2), positions in VT(x)
@@ -660,7 +691,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     // ---------------- C4. ET rows, per edge ----------------
     if (do_et) {
         uint16_t *st_et = S.st_et;
-        const int per = (tot_e + NT - 1) / NT;
+        const int per = range_len(tot_e);
         const int e0 = min(tot_e, tid * per), e1 = min(tot_e, e0 + per);
         int cnt = 0;
         for (int e = e0; e < e1; ++e)
@@ -687,7 +718,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         __syncthreads();
         for (int e = tid; e < tot_e; e += NT) it->et_off[e] = int32_t(em[e * nch]);
-        for (int j = tid; j < tot_etv; j += NT) it->et_val[j] = gtet(st_et[j]);
+        copy_out(it->et_val, tot_etv, [&](int j) { return gtet(st_et[j]); });
         __syncthreads();  // ET staging is dead: r1 takes the face hash
     }
 
@@ -1102,7 +1133,7 @@ SmemPlan plan_smem(const Caps &c, int threads) {
     p.caps = c;
     const int64_t nwarp = threads / 32;
     const int64_t nvo = c.nv_own;
-    p.W = std::max(1, (c.nv_nb + 31) / 32);
+    p.W = std::max(1, (c.nv_nb + 31) / 32) | 1;  // row stride of the bitmaps (odd)
     p.nch = std::max(1, (c.max_deg + 31) / 32);
     int64_t off = 0;
     p.hdr = 0;
