@@ -228,6 +228,23 @@ gale_status gale_bulk_arrays(gale_ctx *ctx, gale_arrays *dev, int64_t *lengths);
  * the copies are done. */
 gale_status gale_bulk_export(gale_ctx *ctx, uint32_t mask, const gale_arrays *host_dst);
 
+/* Build the listed clusters (ids == NULL or n <= 0: all, in id order) for
+ * the relations in mask and copy every output array to caller HOST buffers,
+ * overlapping the copy of each finished chunk of clusters with the build of
+ * the next one.  This is the paper's kernel-then-copy-back step for a whole
+ * batch ("Kernel computation", Section 4.6: the relations are computed on
+ * the GPU and returned to the consumers' host memory).
+ *   host_dst  one buffer per array of mask, laid out as a bulk build lays
+ *             out the device arrays (lengths as gale_bulk_arrays reports after
+ *             the call); pinned memory is needed for the overlap.
+ *   chunks    0 = automatic (about 256 MB of output per chunk, at most 8),
+ *             else 1..64.
+ * Afterwards the device bulk arrays hold the same result as after
+ * gale_build_clusters(ctx, ids, n, mask, GALE_MODE_BATCHED).  Blocks until
+ * the copies are done; EDEVICE if a kernel reported an error. */
+gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask,
+                              const gale_arrays *host_dst, int32_t chunks);
+
 /*
  * gale_request - a consumer's request for the relations of one cluster
  * (Section 4.4: coboundary and adjacency relations are requested for the

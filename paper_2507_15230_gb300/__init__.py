@@ -70,7 +70,7 @@ class ServeStats(ctypes.Structure):
 
 # the symbols include/gale.h declares
 EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
-           "gale_bulk_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
+           "gale_bulk_export", "gale_build_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
            "gale_autotune", "gale_get_bins", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
 
@@ -98,6 +98,7 @@ def load_library(build: bool = True):
     lib.gale_bulk_view.argtypes = [P, i32, ctypes.POINTER(View)]
     lib.gale_bulk_arrays.argtypes = [P, ctypes.POINTER(Arrays), P]
     lib.gale_bulk_export.argtypes = [P, u32, ctypes.POINTER(Arrays)]
+    lib.gale_build_export.argtypes = [P, P, ctypes.c_int32, u32, ctypes.POINTER(Arrays), ctypes.c_int32]
     lib.gale_request.argtypes = [P, i32, u32, i64, ctypes.POINTER(View)]
     lib.gale_release.argtypes = [P, ctypes.POINTER(View)]
     lib.gale_serve_stats_get.argtypes = [P, ctypes.POINTER(ServeStats)]
@@ -298,6 +299,36 @@ class Context:
             setattr(a, n, _p(arr) if arr.size else None)
         _check(self._lib.gale_bulk_export(self._h, mask, ctypes.byref(a)))
         return out
+
+    def build_export(self, ids=None, mask: int = ALL, out: dict | None = None, chunks: int = 0) -> dict:
+        """gale_build_export: build the listed clusters (None: all) and copy
+        the outputs into host numpy arrays, chunk copies overlapping the
+        build (allocated unless given; pinned buffers give the overlap)."""
+        if ids is None:
+            idp, n = None, 0
+        else:
+            ids = np.ascontiguousarray(ids, dtype=np.int32)
+            idp, n = _p(ids), int(ids.size)
+        if out is None:
+            lens = self.output_lengths(ids, mask)
+            out = {nm: np.empty(lens[nm], np.int32) for i, nm in enumerate(ARRAYS) if mask & ARRAY_REL[i]}
+        a = Arrays()
+        for nm, arr in out.items():
+            setattr(a, nm, _p(arr) if arr.size else None)
+        _check(self._lib.gale_build_export(self._h, idp, n, mask, ctypes.byref(a), chunks))
+        return out
+
+    def output_lengths(self, ids=None, mask: int = ALL) -> dict:
+        """Element counts of the ten bulk arrays a build of ids would fill."""
+        I_V, I_T, sizes = self.intervals()
+        ks = np.arange(self.K) if ids is None else np.asarray(ids, dtype=np.int64)
+        nvo = (I_V[ks + 1] - I_V[ks]).astype(np.int64)
+        nown = (I_T[ks + 1] - I_T[ks]).astype(np.int64)
+        sz = sizes[ks]
+        n_e = sz[:, 2]
+        per = [nvo + 1, sz[:, 0], nvo + 1, sz[:, 1], nvo + 1, n_e, n_e + 1, sz[:, 3], nown + 1, sz[:, 4]]
+        L = {nm: int(per[i].sum()) if mask & ARRAY_REL[i] else 0 for i, nm in enumerate(ARRAYS)}
+        return L
 
     def bulk_offsets(self, index: int) -> dict:
         """Element offsets of the index-th cluster in each bulk array."""

@@ -24,6 +24,8 @@ void serve_destroy(gale_ctx *ctx);
 
 namespace {
 
+constexpr int32_t kMaxExportChunks = 64;  // pipelined build + export
+
 gale_status fail(gale_status s, const std::string &msg) {
     gale::set_error(msg);
     return s;
@@ -401,6 +403,11 @@ void gale_destroy(gale_ctx *ctx) {
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);
         for (auto &g : ctx->graphs)
             if (g) cudaGraphExecDestroy(g);
+        if (ctx->copy_stream) {
+            cudaStreamSynchronize(ctx->copy_stream);
+            cudaStreamDestroy(ctx->copy_stream);
+        }
+        for (cudaEvent_t e : ctx->chunk_events) cudaEventDestroy(e);
         while (!ctx->allocs.empty()) ctx->dfree(ctx->allocs.back().ptr);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     }
@@ -664,6 +671,149 @@ gale_status gale_bulk_export(gale_ctx *ctx, uint32_t mask, const gale_arrays *ho
     }
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     return GALE_OK;
+}
+
+gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask,
+                              const gale_arrays *host_dst, int32_t chunks) {
+    if (!ctx || !host_dst) return fail(GALE_EINVAL, "NULL argument");
+    if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
+    if (mask == 0 || (mask & ~ctx->precond))
+        return fail(GALE_EINVAL, "mask must be a non-empty subset of the precondition mask");
+    if (chunks < 0 || chunks > kMaxExportChunks)
+        return fail(GALE_EINVAL, "chunks must be 0 (automatic) to " + std::to_string(kMaxExportChunks));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const int32_t K = ctx->hm.K;
+    const bool all = (ids == nullptr || n <= 0);
+    const int32_t cnt = all ? K : n;
+    if (!all && n > K) return fail(GALE_EINVAL, "more ids than clusters");
+    std::vector<int32_t> list(cnt);
+    if (all) {
+        std::iota(list.begin(), list.end(), 0);
+    } else {
+        std::vector<uint8_t> seen(K, 0);
+        for (int32_t i = 0; i < cnt; ++i) {
+            if (ids[i] < 0 || ids[i] >= K) return fail(GALE_EINVAL, "cluster id out of range");
+            if (seen[ids[i]]++) return fail(GALE_EINVAL, "cluster id listed twice");
+            list[i] = ids[i];
+        }
+    }
+    int32_t *const *h = &host_dst->vt_off;
+    const uint32_t rel_of[10] = {GALE_VT, GALE_VT, GALE_VV, GALE_VV, GALE_ET, GALE_ET, GALE_ET, GALE_ET, GALE_TT, GALE_TT};
+    for (int a = 0; a < 10; ++a)
+        if ((mask & rel_of[a]) && !h[a]) return fail(GALE_EINVAL, "NULL host buffer for a requested array");
+    // placement of every listed cluster, and the chunk boundaries: about
+    // equal output bytes per chunk
+    ctx->bulk_offs.assign(size_t(cnt) * 10, 0);
+    int64_t run[10] = {};
+    std::vector<int64_t> bytes_before(size_t(cnt) + 1, 0);
+    for (int32_t i = 0; i < cnt; ++i) {
+        int64_t L[10];
+        item_lengths(ctx, list[i], mask, L);
+        int64_t b = 0;
+        for (int a = 0; a < 10; ++a) {
+            ctx->bulk_offs[size_t(i) * 10 + a] = run[a];
+            run[a] += L[a];
+            b += 4 * L[a];
+        }
+        bytes_before[i + 1] = bytes_before[i] + b;
+    }
+    gale_status st = ensure_bulk(ctx, run);
+    if (st != GALE_OK) return st;
+    for (int a = 0; a < 10; ++a) ctx->bulk_len[a] = run[a];
+    ctx->bulk_ids = list;
+    ctx->bulk_mask = mask;
+    if (chunks == 0) chunks = int32_t(std::min<int64_t>(8, std::max<int64_t>(1, bytes_before[cnt] >> 28)));
+    chunks = std::max(1, std::min(chunks, cnt));
+    std::vector<int32_t> cut(size_t(chunks) + 1, cnt);
+    cut[0] = 0;
+    for (int32_t c = 1; c < chunks; ++c) {
+        const int64_t target = bytes_before[cnt] * c / chunks;
+        cut[c] = int32_t(std::lower_bound(bytes_before.begin(), bytes_before.end(), target) - bytes_before.begin());
+        cut[c] = std::max(cut[c], cut[c - 1]);
+    }
+    if (!ctx->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    while (int32_t(ctx->chunk_events.size()) < kMaxExportChunks) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->chunk_events.push_back(e);
+    }
+    if (!ctx->d_chunk_base) {
+        ctx->d_chunk_base = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * kMaxExportChunks));
+        if (!ctx->d_chunk_base) return fail(GALE_ENOMEM, "device allocation failed");
+    }
+    // per chunk: base pointers shifted to the chunk's first element, and the
+    // chunk's items grouped by size bin (largest working set first)
+    std::vector<WorkItem> cbase(chunks);
+    std::vector<int32_t> order;
+    std::vector<std::vector<int64_t>> boff(chunks);
+    std::vector<std::vector<int32_t>> per_bin(ctx->bins.size());
+    for (int32_t c = 0; c < chunks; ++c) {
+        const int32_t i0 = cut[c];
+        int32_t *ptr[10];
+        for (int a = 0; a < 10; ++a) {
+            const int64_t off = i0 < cnt ? ctx->bulk_offs[size_t(i0) * 10 + a] : run[a];
+            ptr[a] = (mask & rel_of[a]) ? ctx->bulk[a] + off : nullptr;
+        }
+        WorkItem &w = cbase[c];
+        memset(&w, 0, sizeof(w));
+        w.vt_off = ptr[0]; w.vt_val = ptr[1]; w.vv_off = ptr[2]; w.vv_val = ptr[3];
+        w.eu_off = ptr[4]; w.e_w = ptr[5]; w.et_off = ptr[6]; w.et_val = ptr[7];
+        w.tt_off = ptr[8]; w.tt_val = ptr[9];
+        for (auto &v : per_bin) v.clear();
+        for (int32_t i = i0; i < cut[c + 1]; ++i) per_bin[ctx->bin_of[list[i]]].push_back(i - i0);
+        boff[c].push_back(int64_t(order.size()));
+        for (size_t b = 0; b < per_bin.size(); ++b) {
+            // members keep the bin's largest-first order
+            auto &v = per_bin[b];
+            std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t d) {
+                return ctx->hm.stats[list[i0 + a]].n_own + ctx->hm.stats[list[i0 + a]].n_ext >
+                       ctx->hm.stats[list[i0 + d]].n_own + ctx->hm.stats[list[i0 + d]].n_ext;
+            });
+            order.insert(order.end(), v.begin(), v.end());
+            boff[c].push_back(int64_t(order.size()));
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_ids, list.data(), size_t(cnt) * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_order_part, order.data(), order.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_chunk_base, cbase.data(), sizeof(WorkItem) * chunks, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    const gale::DevMesh dm = dev_mesh(ctx);
+    int64_t launches = 0;
+    for (int32_t c = 0; c < chunks; ++c) {
+        const int32_t i0 = cut[c], nc = cut[c + 1] - i0;
+        if (nc > 0) {
+            int rc = gale::launch_bases(dm, ctx->d_ids + i0, nc, ctx->d_sizes, mask, ctx->d_chunk_base + c,
+                                        ctx->d_items + i0, ctx->d_totals, ctx->d_bsum, ctx->stream);
+            if (rc != 0) return cuda_fail(cudaError_t(rc), "bases launch");
+            launches += 3;
+            for (size_t b = 0; b < ctx->bins.size(); ++b) {
+                const int32_t nb = int32_t(boff[c][b + 1] - boff[c][b]);
+                if (nb == 0) continue;
+                const gale::Bin &bin = ctx->bins[b];
+                rc = gale::launch_build(dm, bin.plan, ctx->d_items + i0, ctx->d_order_part + boff[c][b], nb,
+                                        ctx->d_err, ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream,
+                                        scratch_of(ctx, bin));
+                if (rc != 0) return cuda_fail(cudaError_t(rc), "batched launch");
+                ++launches;
+            }
+        }
+        // the chunk's outputs leave while the next chunk builds
+        CUDA_TRY(cudaEventRecord(ctx->chunk_events[c], ctx->stream));
+        CUDA_TRY(cudaStreamWaitEvent(ctx->copy_stream, ctx->chunk_events[c], 0));
+        for (int a = 0; a < 10; ++a) {
+            if (!(mask & rel_of[a])) continue;
+            const int64_t o0 = i0 < cnt ? ctx->bulk_offs[size_t(i0) * 10 + a] : run[a];
+            const int64_t o1 = cut[c + 1] < cnt ? ctx->bulk_offs[size_t(cut[c + 1]) * 10 + a] : run[a];
+            if (o1 > o0)
+                CUDA_TRY(cudaMemcpyAsync(h[a] + o0, ctx->bulk[a] + o0, size_t(o1 - o0) * 4, cudaMemcpyDeviceToHost,
+                                         ctx->copy_stream));
+        }
+    }
+    ctx->last_launches = launches;
+    CUDA_TRY(cudaStreamSynchronize(ctx->copy_stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
 }
 
 gale_status gale_get_permutations(gale_ctx *ctx, int32_t *vperm, int32_t *tperm) {

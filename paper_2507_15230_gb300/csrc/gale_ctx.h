@@ -67,7 +67,7 @@ struct gale_ctx {
     std::vector<gale::Bin> bins;
     std::vector<int32_t> bin_of;        // [K]
     std::vector<int64_t> order_all_off; // [nbins+1] offsets into d_order_all
-    int threads_override = 0;  // 0: one thread per own vertex
+    int threads_override = 0;  // 0: chosen from the cluster's tet count
     int ctas_override = 0;
     int sm_count = 0;
 
@@ -78,6 +78,11 @@ struct gale_ctx {
     std::vector<int64_t> bulk_offs;  // [n*10]
     std::vector<int32_t> bulk_ids;
     uint32_t bulk_mask = 0;
+
+    // pipelined build + export: copy stream, chunk events, chunk base items
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> chunk_events;
+    gale::WorkItem *d_chunk_base = nullptr;  // [kMaxExportChunks]
 
     // captured full builds, one per mask
     cudaGraphExec_t graphs[16] = {};

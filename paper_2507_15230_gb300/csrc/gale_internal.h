@@ -121,15 +121,15 @@ struct SmemPlan {
     int32_t threads;
     int32_t W;          // row stride (words, odd) of the neighbour bitmaps
     int32_t nch;        // 32-tet chunks of the longest VT row
-    int32_t pad;
-    int32_t hdr;        // int32[16]: header copy and per-cluster flags
+    int32_t pad;        // per-warp counter row length (even)
     int32_t scan;       // scan scratch (3 x 33 words)
-    int32_t rows;       // uint2[n_tot] tet rows (bulk copy of the block's rows)
+    int32_t blk;        // int32[blk_words] the cluster's block (bulk copy)
     int32_t vt_off;     // int32[nv_own+1]
     int32_t vt_list;    // uint16[n_vt]
     int32_t c_vv;       // int32[nv_own+1] VV row offsets
     int32_t c_e;        // int32[nv_own+1] first owned edge of each own vertex
     int32_t nbr;        // uint16[4*n_own] TT links
+    int32_t jself;      // uint16[2*n_own] position of each internal tet in VT of its two lowest vertices
     int32_t eu;         // uint16[max_e] lower endpoint (own index) of each owned edge
     int32_t r2;         // uint16[max_vv] VV staging | uint32[max_e*nch] edge masks
     int32_t st_w;       // uint16[max_e] upper-endpoint staging (inside r2)
@@ -137,7 +137,7 @@ struct SmemPlan {
     int32_t mk;         // phase B lane masks (inside r1)
     int32_t pre;        // uint8[nv_own*W] rank prefixes (inside r1)
     int32_t tcnt;       // int32[n_own+1] TT counts (inside r1)
-    int32_t st_tt;      // int32[max_tt] TT staging (inside r1)
+    int32_t st_tt;      // uint16[max_tt] TT staging (inside r1)
     int32_t total;      // bytes
     Caps caps;
 };

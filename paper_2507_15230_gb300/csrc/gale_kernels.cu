@@ -56,47 +56,47 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWaitLimit = 1 << 22;  // polls of the block copy's barrier before giving up
 
 struct Smem {
-    int32_t *hdr, *scan;
-    uint2 *rows;
+    int32_t *scan;
+    int32_t *blk;
     int32_t *vt_off;
     uint16_t *vt_list;
     int32_t *c_vv, *c_e;
-    uint16_t *nbr, *eu;
+    uint16_t *nbr, *jself, *eu;
     uint32_t *emask;  // r2
     uint16_t *st_v;   // r2
     uint16_t *st_w;   // r2
-    uint32_t *cw;     // r1 (phase B)
+    uint16_t *cw;     // r1 (phase B)
     uint32_t *mk;     // r1 (phase B)
     uint32_t *bm;     // r1 (phase C)
     uint8_t *pre;     // r1 (phase C)
     uint16_t *st_et;  // r1 (phase C4)
     uint32_t *hash;   // r1 (phase D)
     int32_t *tcnt;    // r1 (phases D, E)
-    int32_t *st_tt;   // r1 (phase E)
+    uint16_t *st_tt;  // r1 (phase E)
 };
 
 __device__ __forceinline__ Smem carve(char *base, const SmemPlan &p) {
     Smem s;
-    s.hdr = reinterpret_cast<int32_t *>(base + p.hdr);
     s.scan = reinterpret_cast<int32_t *>(base + p.scan);
-    s.rows = reinterpret_cast<uint2 *>(base + p.rows);
+    s.blk = reinterpret_cast<int32_t *>(base + p.blk);
     s.vt_off = reinterpret_cast<int32_t *>(base + p.vt_off);
     s.vt_list = reinterpret_cast<uint16_t *>(base + p.vt_list);
     s.c_vv = reinterpret_cast<int32_t *>(base + p.c_vv);
     s.c_e = reinterpret_cast<int32_t *>(base + p.c_e);
     s.nbr = reinterpret_cast<uint16_t *>(base + p.nbr);
+    s.jself = reinterpret_cast<uint16_t *>(base + p.jself);
     s.eu = reinterpret_cast<uint16_t *>(base + p.eu);
     s.emask = reinterpret_cast<uint32_t *>(base + p.r2);
     s.st_v = reinterpret_cast<uint16_t *>(base + p.r2);
     s.st_w = reinterpret_cast<uint16_t *>(base + p.st_w);
-    s.cw = reinterpret_cast<uint32_t *>(base + p.r1);
+    s.cw = reinterpret_cast<uint16_t *>(base + p.r1);
     s.mk = reinterpret_cast<uint32_t *>(base + p.mk);
     s.bm = reinterpret_cast<uint32_t *>(base + p.r1);
     s.pre = reinterpret_cast<uint8_t *>(base + p.pre);
     s.st_et = reinterpret_cast<uint16_t *>(base + p.r1);
     s.hash = reinterpret_cast<uint32_t *>(base + p.r1);
     s.tcnt = reinterpret_cast<int32_t *>(base + p.tcnt);
-    s.st_tt = reinterpret_cast<int32_t *>(base + p.st_tt);
+    s.st_tt = reinterpret_cast<uint16_t *>(base + p.st_tt);
     return s;
 }
 
@@ -256,10 +256,15 @@ __device__ __forceinline__ uint32_t face_hash(uint64_t key, uint32_t mask) {
     return uint32_t((key * 0x9E3779B97F4A7C15ull) >> 40) & mask;
 }
 
-__device__ __forceinline__ void cswap(int32_t &a, int32_t &b) {
-    const int32_t lo = min(a, b), hi = max(a, b);
-    a = lo;
-    b = hi;
+// compare-exchange of keys a, b carrying payloads pa, pb
+__device__ __forceinline__ void cswap2(int32_t &a, int32_t &b, uint32_t &pa, uint32_t &pb) {
+    const bool sw = b < a;
+    const int32_t ka = sw ? b : a, kb = sw ? a : b;
+    const uint32_t qa = sw ? pb : pa, qb = sw ? pa : pb;
+    a = ka;
+    b = kb;
+    pa = qa;
+    pb = qb;
 }
 
 // hash entries: bits [0, 20) = 4 * internal-tet index + slot + 1, bits
@@ -275,50 +280,38 @@ constexpr uint32_t kMatch = 1u << 20;
 // false when a bounded wait ran out (the CTA must stop).
 // ---------------------------------------------------------------------------
 template <bool COUNT, bool SPILL>
-__device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, uint32_t mask,
-                            const WorkItem *it, int64_t *sizes_out, int32_t *err, uint64_t *bar, uint32_t &phase) {
+__device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, int64_t words,
+                            uint32_t mask, const WorkItem *it, int64_t *sizes_out, int32_t *err, uint64_t *bar,
+                            uint32_t &phase) {
     const int NT = blockDim.x, NWARP = NT >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const Caps &caps = plan.caps;
     const int32_t *__restrict__ g = m.blocks + blk_word;
+    int32_t *flag = S.scan + 120;  // [0] block fits, [1] bulk copy issued
 
-    // ---------------- A. header, then the rows ----------------
+    // ---------------- A. the block, by one bulk copy ----------------
     if (tid == 0) {
-        const int4 *g4 = reinterpret_cast<const int4 *>(g);
-        const int4 a = __ldg(g4), b = __ldg(g4 + 1), c = __ldg(g4 + 2);
-        int4 *h4 = reinterpret_cast<int4 *>(S.hdr);
-        h4[0] = a;
-        h4[1] = b;
-        h4[2] = c;
-        // a = (n_ext, n_own, n_halo, nv_loc), b = (own_lo, nv_own, t_base, v_base), c = (nv_nb, n_bnd, -, -)
-        const int64_t n_tot = int64_t(a.x) + a.y + a.z;
-        const bool fits = a.x >= 0 && a.y >= 0 && a.z >= 0 && a.w >= 0 && b.x >= 0 && b.y >= 0 && c.x >= 0 &&
-                          c.y >= 0 && n_tot <= caps.n_tot && a.y <= caps.n_own && a.w <= caps.nv_loc &&
-                          b.y <= caps.nv_own && c.x <= caps.nv_nb && c.x <= a.w && int64_t(b.x) + b.y <= c.x &&
-                          2 * int64_t(c.y) + 1 <= caps.hcap;
+        const bool fits = words >= kHdrWords && words <= caps.blk_words && (words & 3) == 0;
         int issued = 0;
-        if (fits && !SPILL && n_tot > 0) {
-            bulk_load(S.rows, g + blk_rows_off(a.w, a.x, a.z), uint32_t(4 * a4(2 * n_tot)), bar);
+        if (fits && !SPILL) {
+            bulk_load(S.blk, g, uint32_t(4 * words), bar);
             issued = 1;
         }
-        S.hdr[12] = fits;
-        S.hdr[13] = issued;
+        flag[0] = fits;
+        flag[1] = issued;
     }
     __syncthreads();
-    const BlockHdr h = *reinterpret_cast<const BlockHdr *>(S.hdr);
-    const bool fits = S.hdr[12] != 0, issued = S.hdr[13] != 0;
+    const bool fits = flag[0] != 0, issued = flag[1] != 0;
     if (!fits) {
         if (tid == 0) atomicOr(err, ERR_CAPACITY);
         __syncthreads();
         return true;
     }
-    const int n_ext = h.n_ext, n_own = h.n_own;
-    const int n_vtets = n_ext + n_own, n_tot = n_vtets + h.n_halo;
     if (SPILL) {
-        const int4 *src = reinterpret_cast<const int4 *>(g + blk_rows_off(h.nv_loc, n_ext, h.n_halo));
-        int4 *dst = reinterpret_cast<int4 *>(S.rows);
-        const int n4 = int(a4(2 * int64_t(n_tot)) >> 2);
+        const int4 *src = reinterpret_cast<const int4 *>(g);
+        int4 *dst = reinterpret_cast<int4 *>(S.blk);
+        const int n4 = int(words >> 2);
         for (int i = tid; i < n4; i += NT) dst[i] = __ldg(src + i);
         __syncthreads();
     } else if (issued) {
@@ -330,32 +323,50 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         phase ^= 1u;
     }
-    const uint2 *rows = S.rows;
+    const BlockHdr h = *reinterpret_cast<const BlockHdr *>(S.blk);
+    {
+        const int64_t n_tot = int64_t(h.n_ext) + h.n_own + h.n_halo;
+        const bool ok = h.n_ext >= 0 && h.n_own >= 0 && h.n_halo >= 0 && h.nv_loc >= 0 && h.own_lo >= 0 &&
+                        h.nv_own >= 0 && h.nv_nb >= 0 && h.n_bnd >= 0 && n_tot <= caps.n_tot &&
+                        h.n_own <= caps.n_own && h.nv_loc <= caps.nv_loc && h.nv_own <= caps.nv_own &&
+                        h.nv_nb <= caps.nv_nb && h.nv_nb <= h.nv_loc && int64_t(h.own_lo) + h.nv_own <= h.nv_nb &&
+                        2 * int64_t(h.n_bnd) + 1 <= caps.hcap &&
+                        blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo) == words;
+        if (!ok) {
+            if (tid == 0) atomicOr(err, ERR_CAPACITY);
+            __syncthreads();
+            return true;
+        }
+    }
+    const int n_ext = h.n_ext, n_own = h.n_own;
+    const int n_vtets = n_ext + n_own;
+    const uint2 *rows = reinterpret_cast<const uint2 *>(S.blk + blk_rows_off(h.nv_loc, n_ext, h.n_halo));
+    const int32_t *vmap = S.blk + kHdrWords;
+    const int32_t *tmap = S.blk + blk_tmap_off(h.nv_loc);
     const int nvo = h.nv_own, lo = h.own_lo;
     const uint32_t nvo_u = uint32_t(nvo);
     const bool want_tt = COUNT || (mask & R_TT);
     const bool do_vv = !COUNT && (mask & R_VV);
     const bool do_et = !COUNT && (mask & R_ET);
-    const int32_t *__restrict__ vmap_g = g + kHdrWords;
-    const int32_t *__restrict__ tmap_g = g + blk_tmap_off(h.nv_loc);
     const int32_t t_base = h.t_base;
     // canonical id of a local tet
     auto gtet = [&](int loc) -> int32_t {
-        if (loc < n_ext) return __ldg(tmap_g + loc);
+        if (loc < n_ext) return tmap[loc];
         if (loc < n_vtets) return t_base + (loc - n_ext);
-        return __ldg(tmap_g + (loc - n_own));
+        return tmap[loc - n_own];
     };
 
     // ---------------- B. VT ----------------
     int vt_total;
     {
-        const int pad = caps.nv_own;
-        uint32_t *cw = S.cw;  // [warp][v]: counts, then next slot
+        const int pad = plan.pad;
+        uint16_t *cw = S.cw;  // [warp][v]: counts, then next position within the row
+        uint32_t *cw32 = reinterpret_cast<uint32_t *>(S.cw);
         uint32_t *mk = S.mk;  // [warp][v]: lanes holding v
         const int chunk = ((n_vtets + NWARP - 1) / NWARP + 31) & ~31;
         const int c0 = min(n_vtets, warp * chunk), c1 = min(n_vtets, c0 + chunk);
         for (int i = tid; i < NWARP * pad; i += NT) {
-            cw[i] = 0u;
+            if (!(i & 1)) cw32[i >> 1] = 0u;
             mk[i] = 0u;
         }
         __syncthreads();
@@ -364,11 +375,11 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 const uint32_t d = vtx(r, s) - uint32_t(lo);
-                if (d < nvo_u) atomicAdd(&cw[warp * pad + d], 1u);
+                if (d < nvo_u) atomicAdd(&cw32[(warp * pad + int(d)) >> 1], 1u << (16 * (d & 1u)));
             }
         }
         __syncthreads();
-        // row lengths -> offsets; every (warp, vertex) gets its first slot
+        // row lengths -> offsets; every (warp, vertex) gets its first position
         for (int v = tid; v < nvo; v += NT) {
             int tot = 0;
             for (int w = 0; w < NWARP; ++w) tot += int(cw[w * pad + v]);
@@ -378,12 +389,12 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         vt_total = block_scan_array(S.vt_off, nvo, S.scan);
         bool bad = vt_total > caps.n_vt;
         for (int v = tid; v < nvo; v += NT) {
-            int run = S.vt_off[v];
-            const int d = (v + 1 < nvo ? S.vt_off[v + 1] : vt_total) - run;
+            const int d = (v + 1 < nvo ? S.vt_off[v + 1] : vt_total) - S.vt_off[v];
             bad |= d > caps.max_deg;
+            int run = 0;
             for (int w = 0; w < NWARP; ++w) {
                 const int c = int(cw[w * pad + v]);
-                cw[w * pad + v] = uint32_t(run);
+                cw[w * pad + v] = uint16_t(run);
                 run += c;
             }
         }
@@ -392,7 +403,8 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             return true;
         }
-        // fill in tet order, 32 tets per step of each warp
+        // fill in tet order, 32 tets per step of each warp; an internal
+        // tet's position in VT of its two lowest vertices is kept for TT
         for (int i0 = c0; i0 < c1; i0 += 32) {
             const int i = i0 + lane;
             const uint2 r = i < c1 ? rows[i] : make_uint2(0xffffffffu, 0xffffffffu);
@@ -409,14 +421,16 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 mm[s] = 0u;
                 if (d[s] < nvo_u) {
                     mm[s] = mk[warp * pad + d[s]];
-                    S.vt_list[cw[warp * pad + d[s]] + __popc(mm[s] & lt)] = uint16_t(i);
+                    const int pos = int(cw[warp * pad + d[s]]) + __popc(mm[s] & lt);
+                    S.vt_list[S.vt_off[d[s]] + pos] = uint16_t(i);
+                    if (s < 2 && i >= n_ext) S.jself[2 * (i - n_ext) + s] = uint16_t(pos);
                 }
             }
             __syncwarp();
 #pragma unroll
             for (int s = 0; s < 4; ++s)
                 if (d[s] < nvo_u && (mm[s] & lt) == 0u) {
-                    cw[warp * pad + d[s]] += uint32_t(__popc(mm[s]));
+                    cw[warp * pad + d[s]] += uint16_t(__popc(mm[s]));
                     mk[warp * pad + d[s]] = 0u;
                 }
             __syncwarp();
@@ -580,11 +594,11 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         if (do_vv) {
             for (int i = tid; i <= nvo; i += NT) it->vv_off[i] = S.c_vv[i];
-            copy_out(it->vv_val, tot[0], [&](int j) { return __ldg(vmap_g + S.st_v[j]); });
+            copy_out(it->vv_val, tot[0], [&](int j) { return vmap[S.st_v[j]]; });
         }
         if (do_et) {
             for (int i = tid; i <= nvo; i += NT) it->eu_off[i] = S.c_e[i];
-            copy_out(it->e_w, tot[1], [&](int e) { return __ldg(vmap_g + S.st_w[e]); });
+            copy_out(it->e_w, tot[1], [&](int e) { return vmap[S.st_w[e]]; });
             if (tid == 0) it->et_off[tot[1]] = tot[2];
         }
     }
@@ -657,32 +671,28 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 const int q = int(y >> 5);
                 return S.c_e[x] + int(pre[x * WP + q]) + __popc(bm[x * WP + q] & ((1u << (y & 31)) - 1u));
             };
-            // partner of tet li across the face (x, w1, w2): the other set bit
-            // of mask(x, w1) & mask(x, w2), positions in VT(x)
-            auto link = [&](int e1, int e2, int base, int opp) {
+            // partner of tet li across the face (x, w1, w2): the set bit of
+            // mask(x, w1) & mask(x, w2) other than li's own position js in VT(x)
+            auto link = [&](int e1, int e2, int base, int js, int opp) {
+                const int cs = js >> 5;
+                const uint32_t sb = 1u << (js & 31);
                 int found = 0, partner = -1;
                 for (int c = 0; c < nch; ++c) {
                     uint32_t mm = em[e1 * nch + c] & em[e2 * nch + c];
-                    while (mm) {
-                        const int b = __ffs(mm) - 1;
-                        mm &= mm - 1;
-                        const int t = S.vt_list[base + c * 32 + b];
-                        if (t != li) {
-                            if (partner < 0) partner = t;
-                            ++found;
-                        }
-                    }
+                    if (c == cs) mm &= ~sb;
+                    found += __popc(mm);
+                    if (mm != 0u && partner < 0) partner = S.vt_list[base + c * 32 + __ffs(mm) - 1];
                 }
                 if (found > 1) flags |= ERR_NONMANIFOLD;
                 if (partner >= 0) S.nbr[i * 4 + opp] = uint16_t(partner);
             };
             const int e1 = rank(a, v1), e2 = rank(a, v2), e3 = rank(a, v3);
-            const int base_a = S.vt_off[a];
-            link(e1, e2, base_a, 3);
-            link(e1, e3, base_a, 2);
-            link(e2, e3, base_a, 1);
+            const int base_a = S.vt_off[a], ja = S.jself[2 * i];
+            link(e1, e2, base_a, ja, 3);
+            link(e1, e3, base_a, ja, 2);
+            link(e2, e3, base_a, ja, 1);
             const uint32_t b = v1 - uint32_t(lo);
-            if (b < nvo_u) link(rank(b, v2), rank(b, v3), S.vt_off[b], 0);
+            if (b < nvo_u) link(rank(b, v2), rank(b, v3), S.vt_off[b], S.jself[2 * i + 1], 0);
         }
         if (flags) atomicOr(err, flags);
     }
@@ -751,23 +761,20 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         __syncthreads();
         const int n_halo = h.n_halo;
-        for (int j = tid; j < n_halo; j += NT) {
-            const int tl = n_vtets + j;
-            const uint2 r = rows[tl];
-            for (int s = 0; s < 4; ++s) {
-                const uint64_t key = face_key(r, s);
-                uint32_t hp = face_hash(key, hmask);
-                for (int probe = 0; probe < caps.hcap; ++probe) {
-                    const uint32_t e = hash[hp];
-                    if (e == 0u) break;
-                    const uint32_t ref = (e & kRefMask) - 1u;
-                    if (face_key(rows[n_ext + (ref >> 2)], 0) == key) {
-                        if (atomicAdd(&hash[hp], kMatch) >= kMatch) flags |= ERR_NONMANIFOLD;
-                        S.nbr[ref] = uint16_t(tl);
-                        break;
-                    }
-                    hp = (hp + 1u) & hmask;
+        for (int j = tid; j < 4 * n_halo; j += NT) {  // one (halo tet, face) per step
+            const int tl = n_vtets + (j >> 2);
+            const uint64_t key = face_key(rows[tl], j & 3);
+            uint32_t hp = face_hash(key, hmask);
+            for (int probe = 0; probe < caps.hcap; ++probe) {
+                const uint32_t e = hash[hp];
+                if (e == 0u) break;
+                const uint32_t ref = (e & kRefMask) - 1u;
+                if (face_key(rows[n_ext + (ref >> 2)], 0) == key) {
+                    if (atomicAdd(&hash[hp], kMatch) >= kMatch) flags |= ERR_NONMANIFOLD;
+                    S.nbr[ref] = uint16_t(tl);
+                    break;
                 }
+                hp = (hp + 1u) & hmask;
             }
         }
         if (flags) atomicOr(err, flags);
@@ -791,23 +798,25 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             for (int i = tid; i < n_own; i += NT) {
                 const uint2 nb = *reinterpret_cast<const uint2 *>(&S.nbr[i * 4]);
                 const uint32_t n0 = nb.x & 0xffffu, n1 = nb.x >> 16, n2 = nb.y & 0xffffu, n3 = nb.y >> 16;
-                // absent neighbours sort last as INT32_MAX
+                // local ids ordered by canonical id; absent neighbours sort last
                 int32_t w0 = n0 != 0xffffu ? gtet(int32_t(n0)) : INT32_MAX;
                 int32_t w1 = n1 != 0xffffu ? gtet(int32_t(n1)) : INT32_MAX;
                 int32_t w2 = n2 != 0xffffu ? gtet(int32_t(n2)) : INT32_MAX;
                 int32_t w3 = n3 != 0xffffu ? gtet(int32_t(n3)) : INT32_MAX;
-                cswap(w0, w1); cswap(w2, w3); cswap(w0, w2); cswap(w1, w3); cswap(w1, w2);
+                uint32_t l0 = n0, l1 = n1, l2 = n2, l3 = n3;
+                cswap2(w0, w1, l0, l1); cswap2(w2, w3, l2, l3); cswap2(w0, w2, l0, l2); cswap2(w1, w3, l1, l3);
+                cswap2(w1, w2, l1, l2);
                 const int p = tcnt[i];
                 it->tt_off[i] = p;
-                int32_t *o = S.st_tt + p;
-                if (w0 != INT32_MAX) o[0] = w0;
-                if (w1 != INT32_MAX) o[1] = w1;
-                if (w2 != INT32_MAX) o[2] = w2;
-                if (w3 != INT32_MAX) o[3] = w3;
+                uint16_t *o = S.st_tt + p;
+                if (w0 != INT32_MAX) o[0] = uint16_t(l0);
+                if (w1 != INT32_MAX) o[1] = uint16_t(l1);
+                if (w2 != INT32_MAX) o[2] = uint16_t(l2);
+                if (w3 != INT32_MAX) o[3] = uint16_t(l3);
             }
             if (tid == 0) it->tt_off[n_own] = tot_tt;
             __syncthreads();
-            for (int j = tid; j < tot_tt; j += NT) it->tt_val[j] = S.st_tt[j];
+            copy_out(it->tt_val, tot_tt, [&](int j) { return gtet(S.st_tt[j]); });
         }
     }
     __syncthreads();
@@ -855,7 +864,9 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan 
         }
         if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
         __syncthreads();
-        if (!run_cluster<true, SPILL>(m, plan, S, m.blk_off[k], 0u, nullptr, s_sizes, err, &s_bar, phase)) return;
+        if (!run_cluster<true, SPILL>(m, plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], 0u, nullptr, s_sizes,
+                                      err, &s_bar, phase))
+            return;
         __syncthreads();
         if (threadIdx.x < SZ_N) sizes[int64_t(k) * SZ_N + threadIdx.x] = s_sizes[threadIdx.x];
     }
@@ -884,7 +895,8 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel(DevMesh m, SmemPlan 
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
-        if (!run_cluster<false, SPILL>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err, &s_bar, phase))
+        if (!run_cluster<false, SPILL>(m, plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
+                                       nullptr, err, &s_bar, phase))
             return;
     }
 }
@@ -904,7 +916,8 @@ __global__ void __launch_bounds__(kMaxThreads) build_one_kernel(DevMesh m, SmemP
         if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
         return;
     }
-    run_cluster<false, SPILL>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err, &s_bar, phase);
+    run_cluster<false, SPILL>(m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k], s_item.mask,
+                              &s_item, nullptr, err, &s_bar, phase);
 }
 
 // ---------------------------------------------------------------------------
@@ -977,7 +990,8 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, S
         if (t < 0) break;
         bool go_on = true;
         if (s_item.k >= 0 && s_item.k < m.K)
-            go_on = run_cluster<false, false>(m, plan, S, s_item.blk, s_item.mask, &s_item, nullptr, err, &s_bar, phase);
+            go_on = run_cluster<false, false>(m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
+                                              s_item.mask, &s_item, nullptr, err, &s_bar, phase);
         else if (threadIdx.x == 0)
             atomicOr(err, ERR_BAD_ITEM);
         if (!go_on) break;  // a bounded wait ran out; the slot stays not done
@@ -1135,13 +1149,12 @@ SmemPlan plan_smem(const Caps &c, int threads) {
     const int64_t nvo = c.nv_own;
     p.W = std::max(1, (c.nv_nb + 31) / 32) | 1;  // row stride of the bitmaps (odd)
     p.nch = std::max(1, (c.max_deg + 31) / 32);
+    p.pad = int32_t((nvo + 1) & ~int64_t(1));
     int64_t off = 0;
-    p.hdr = 0;
-    off = 64;
-    p.scan = int32_t(off);
-    off = a16(off + 4 * 100);
-    p.rows = int32_t(off);
-    off = a16(off + 4 * a4(2 * int64_t(c.n_tot)));
+    p.scan = 0;
+    off = a16(4 * 128);
+    p.blk = int32_t(off);
+    off = a16(off + 4 * int64_t(c.blk_words));
     p.vt_off = int32_t(off);
     off = a16(off + 4 * (nvo + 1));
     p.vt_list = int32_t(off);
@@ -1152,6 +1165,8 @@ SmemPlan plan_smem(const Caps &c, int threads) {
     off = a16(off + 4 * (nvo + 1));
     p.nbr = int32_t(off);
     off = a16(off + 8 * int64_t(c.n_own));
+    p.jself = int32_t(off);
+    off = a16(off + 4 * int64_t(c.n_own));
     p.eu = int32_t(off);
     off = a16(off + 2 * int64_t(c.max_e));
     // r2: VV staging + upper-endpoint staging, then the edge masks
@@ -1163,7 +1178,7 @@ SmemPlan plan_smem(const Caps &c, int threads) {
     // r1: phase B counters + lane masks | bitmaps + rank prefixes | ET
     // staging | face hash + TT counts + TT staging
     p.r1 = int32_t(off);
-    const int64_t cw = a16(4 * nwarp * nvo);
+    const int64_t cw = a16(2 * nwarp * p.pad);
     p.mk = int32_t(off + cw);
     const int64_t bm = a16(4 * nvo * p.W);
     p.pre = int32_t(off + bm);
@@ -1171,8 +1186,8 @@ SmemPlan plan_smem(const Caps &c, int threads) {
     p.tcnt = int32_t(off + hs);
     const int64_t tc = a16(4 * (int64_t(c.n_own) + 1));
     p.st_tt = int32_t(off + hs + tc);
-    const int64_t r1 = std::max(std::max(cw + 4 * nwarp * nvo, bm + nvo * p.W),
-                                std::max(2 * int64_t(c.max_etv), hs + tc + 4 * int64_t(c.max_tt)));
+    const int64_t r1 = std::max(std::max(cw + 4 * nwarp * p.pad, bm + nvo * p.W),
+                                std::max(2 * int64_t(c.max_etv), hs + tc + 2 * int64_t(c.max_tt)));
     off = a16(off + r1);
     p.total = off > INT32_MAX ? INT32_MAX : int32_t(off);
     return p;

@@ -59,6 +59,21 @@ def test_small_subset_and_repeat(small):
     assert_bulk_equal(a, expected_bulk(rel, canon, range(m.nclusters)))
 
 
+@pytest.mark.parametrize("chunks", [0, 1, 3, 64])
+@pytest.mark.parametrize("mask", [gale.ALL, gale.VV | gale.TT])
+def test_build_export_pipelined(small, chunks, mask):
+    """gale_build_export: chunked build with overlapping copies to host gives
+    the oracle's arrays, for all clusters and for a shuffled subset, and
+    leaves the same device bulk arrays as a plain batched build."""
+    m, canon, rel, ctx = small
+    got = ctx.build_export(None, mask, chunks=chunks)
+    assert_bulk_equal(got, expected_bulk(rel, canon, range(m.nclusters), mask))
+    assert_bulk_equal(ctx.export(mask), expected_bulk(rel, canon, range(m.nclusters), mask))
+    ids = np.random.default_rng(5).permutation(m.nclusters)[:41]
+    got = ctx.build_export(ids, mask, chunks=chunks)
+    assert_bulk_equal(got, expected_bulk(rel, canon, ids, mask))
+
+
 def test_views_match_oracle(small):
     m, canon, rel, ctx = small
     ctx.build(None, gale.ALL, gale.MODE_BATCHED)
