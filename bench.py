@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--per-cluster-sample", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default block sizes")
     ap.add_argument("--serve-threads", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     ap.add_argument("--serve-baseline-clusters", type=int, default=2048)
@@ -209,6 +210,10 @@ def main():
     ctx = gale.Context.load(mesh, device=local, cache_budget_bytes=int(args.serve_budget_gb * (1 << 30)))
     info = ctx.info()
     stream = torch.cuda.ExternalStream(ctx.stream_handle)
+    tuned = None
+    if not args.no_autotune:
+        # block size and CTAs per SM of every size bin, chosen by timing
+        tuned = {"best_ms_per_bin": ctx.autotune(gale.ALL)}
 
     # warm-up (also captures the batched graph)
     for _ in range(args.warmup):
@@ -333,6 +338,7 @@ def main():
             "serving": serving,
             "load_seconds": {"host": info.load_host_seconds, "device": info.load_device_seconds},
             "bins": ctx.bins(),
+            "autotune": None if tuned is None else {"best_ms_per_bin": tuned["best_ms_per_bin"]},
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -184,12 +184,13 @@ int gen_delaunay(int64_t n, const int64_t *pts, void **handle, int64_t *nt_out) 
     qsort(order, (size_t)n, sizeof(mkey), cmp_mkey);
     uint32_t stamp = 0;
     int32_t last = r;
-    enum { kH = 4096 };
-    static uint64_t hkey[kH];
-    static int32_t hval[kH];
-    static uint32_t hst[kH];
+    /* edge table linking the new tets of a cavity; grows with the cavity */
+    uint32_t kH = 4096;
+    uint64_t *hkey = (uint64_t *)malloc(sizeof(uint64_t) * kH);
+    int32_t *hval = (int32_t *)malloc(sizeof(int32_t) * kH);
+    uint32_t *hst = (uint32_t *)calloc(kH, sizeof(uint32_t));
+    if (!hkey || !hval || !hst) return -2;
     uint32_t hstamp = 0;
-    memset(hst, 0, sizeof(hst));
     uint64_t walkrng = 0x9E3779B97F4A7C15ull;
     for (int64_t oi = 0; oi < n; ++oi) {
         const int32_t pi = order[oi].idx;
@@ -264,7 +265,18 @@ int gen_delaunay(int64_t n, const int64_t *pts, void **handle, int64_t *nt_out) 
         nbnd = nb2;
         /* new tets: each boundary face with the point replacing the cavity
          * tet's opposite vertex */
-        if (nbnd * 3 > kH / 2) return -6; /* cavity too large for the edge table */
+        if ((uint32_t)nbnd * 3u > kH / 2u) {
+            /* at most 3 edges per new tet: keep the load at or below one half */
+            while ((uint32_t)nbnd * 3u > kH / 2u) kH *= 2u;
+            free(hkey);
+            free(hval);
+            free(hst);
+            hkey = (uint64_t *)malloc(sizeof(uint64_t) * kH);
+            hval = (int32_t *)malloc(sizeof(int32_t) * kH);
+            hst = (uint32_t *)calloc(kH, sizeof(uint32_t));
+            if (!hkey || !hval || !hst) return -2;
+            hstamp = 0;
+        }
         int32_t *nt = (int32_t *)malloc(sizeof(int32_t) * (size_t)nbnd);
         for (int32_t b = 0; b < nbnd; ++b) {
             int32_t c = bnd[2 * b], i = bnd[2 * b + 1];
@@ -297,7 +309,7 @@ int gen_delaunay(int64_t n, const int64_t *pts, void **handle, int64_t *nt_out) 
                     if (q != j && q != ip) e[c2++] = T.tv[4 * x + q];
                 const uint64_t key = e[0] < e[1] ? ((uint64_t)(uint32_t)e[0] << 32 | (uint32_t)e[1])
                                                  : ((uint64_t)(uint32_t)e[1] << 32 | (uint32_t)e[0]);
-                uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 52) & (kH - 1);
+                uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (kH - 1u);
                 for (;;) {
                     if (hst[h] != hstamp) {
                         hst[h] = hstamp;
@@ -311,7 +323,7 @@ int gen_delaunay(int64_t n, const int64_t *pts, void **handle, int64_t *nt_out) 
                         T.nb[4 * y + jy] = x;
                         break;
                     }
-                    h = (h + 1) & (kH - 1);
+                    h = (h + 1u) & (kH - 1u);
                 }
             }
         }
@@ -339,6 +351,7 @@ int gen_delaunay(int64_t n, const int64_t *pts, void **handle, int64_t *nt_out) 
     *nt_out = cnt;
     free(T.p); free(T.tv); free(T.nb); free(T.mark); free(T.dead); free(T.freel);
     free(order); free(stack); free(cav); free(bnd);
+    free(hkey); free(hval); free(hst);
     return 0;
 }
 

@@ -309,9 +309,21 @@ gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm)
  * out[6*i .. 6*i+5].  Returns the number of bins in *nbins. */
 gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t *nbins);
 
-/* Autotune the batched form on a sample of clusters; stores the choice in
- * the context. */
-gale_status gale_autotune(gale_ctx *ctx, uint32_t mask);
+/* Members of the size bins: the cluster ids of bin 0, then bin 1, ... (K
+ * ids in all; the counts per bin are gale_get_bins' first values), each bin
+ * in its launch order (largest working set first).  out: K int32. */
+gale_status gale_get_bin_members(gale_ctx *ctx, int32_t *out);
+
+/* Autotune the batched form.  For every size bin, the bin's clusters are
+ * built alone (relations in mask, outputs into the bulk arrays) with every
+ * candidate block size - 128, 256, 384, 512, 768 and 1024 threads whose
+ * working memory fits - and every CTA-per-SM count that fits, each timed
+ * over reps launches (0 = 2) with CUDA events after one untimed launch; the
+ * fastest pair is kept for the bin (gale_get_bins reports it) and captured
+ * full builds are dropped so the next one captures the choice.  best_ms
+ * (optional, max_bins entries): the chosen time per bin.  A later
+ * gale_set_tuning call replaces the choice. */
+gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *best_ms, int32_t max_bins);
 
 /* The stream of the context (cudaStream_t). */
 void *gale_stream(gale_ctx *ctx);

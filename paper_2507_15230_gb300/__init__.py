@@ -72,7 +72,7 @@ class ServeStats(ctypes.Structure):
 EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
            "gale_bulk_export", "gale_build_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
-           "gale_autotune", "gale_get_bins", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
+           "gale_autotune", "gale_get_bins", "gale_get_bin_members", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
 
 _lib = None
 
@@ -108,7 +108,8 @@ def load_library(build: bool = True):
     lib.gale_get_working_set.argtypes = [P, i32, P, ctypes.POINTER(i64), P, ctypes.POINTER(i64)]
     lib.gale_get_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.gale_set_tuning.argtypes = [P, i32, i32]
-    lib.gale_autotune.argtypes = [P, u32]
+    lib.gale_autotune.argtypes = [P, u32, i32, P, i32]
+    lib.gale_get_bin_members.argtypes = [P, P]
     lib.gale_get_bins.argtypes = [P, P, i32, ctypes.POINTER(i32)]
     lib.gale_serve_configure.argtypes = [P, i32, i64]
     lib.gale_stream.argtypes = [P]
@@ -400,11 +401,22 @@ class Context:
         keys = ("clusters", "threads", "bytes", "ctas_per_sm", "grid", "spill")
         return [dict(zip(keys, out[6 * i:6 * i + 6].tolist())) for i in range(n.value)]
 
+    def bin_members(self) -> np.ndarray:
+        """Cluster ids of bin 0, bin 1, ... in launch order (K ids)."""
+        out = np.empty(max(self.K, 1), np.int32)
+        _check(self._lib.gale_get_bin_members(self._h, _p(out)))
+        return out[:self.K]
+
     def set_tuning(self, threads: int = 0, ctas_per_sm: int = 0):
         _check(self._lib.gale_set_tuning(self._h, threads, ctas_per_sm))
 
-    def autotune(self, mask: int = ALL):
-        _check(self._lib.gale_autotune(self._h, mask))
+    def autotune(self, mask: int = ALL, reps: int = 2) -> list:
+        """gale_autotune: per size bin, the fastest block size and CTAs per
+        SM; returns the chosen build time (ms) of each bin."""
+        nb = len(self.bins())
+        best = np.zeros(max(nb, 1), np.float32)
+        _check(self._lib.gale_autotune(self._h, mask, reps, _p(best), nb))
+        return [float(x) for x in best[:nb]]
 
 
 def view_to_numpy(view: View) -> dict:

@@ -107,10 +107,10 @@ int threads_for(const gale_ctx *ctx, const gale::ClusterStat &s) {
 // the same kernel with its regions in a per-CTA slice of global scratch.
 gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     const int32_t K = ctx->hm.K;
-    // dynamic shared memory a CTA may plan for: the opt-in limit less room
-    // for the kernels' static shared memory
+    // dynamic shared memory a CTA may plan for: the opt-in limit less the
+    // kernels' static shared memory
     constexpr int kStaticMargin = 512;
-    const int smem_cta = gale::kernel_smem_limit() - kStaticMargin;
+    const int smem_cta = gale::dynamic_smem_limit();
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
     auto caps_k = [&](int32_t k) {
@@ -183,7 +183,8 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     int max_total = 0;
     for (auto &b : ctx->bins)
         if (!b.spill) max_total = std::max(max_total, b.plan.total);
-    gale::prepare_kernels(max_total);
+    if (!gale::prepare_kernels(max_total))
+        return fail(GALE_ECUDA, "setting the kernels' shared memory limit failed");
     int64_t spill_need = 0;
     for (auto &b : ctx->bins) {
         int per_sm = gale::max_ctas_per_sm(b.plan, b.spill);
@@ -226,7 +227,7 @@ SmemPlan serve_plan(gale_ctx *ctx, bool *fits) {
     SmemPlan p = plan_smem(c, threads);
     bool any_spill = false;
     for (const auto &b : ctx->bins) any_spill |= b.spill;
-    *fits = !ctx->bins.empty() && !any_spill && p.total <= kernel_smem_limit();
+    *fits = !ctx->bins.empty() && !any_spill && p.total <= dynamic_smem_limit();
     if (*fits) prepare_kernels(std::max(p.total, 0));
     return p;
 }
@@ -900,6 +901,127 @@ gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm)
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    return st;
+}
+
+gale_status gale_get_bin_members(gale_ctx *ctx, int32_t *out) {
+    if (!ctx || !out) return fail(GALE_EINVAL, "NULL argument");
+    size_t w = 0;
+    for (const auto &b : ctx->bins)
+        for (int32_t k : b.clusters) out[w++] = k;
+    return GALE_OK;
+}
+
+gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *best_ms, int32_t max_bins) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
+    if (mask == 0 || (mask & ~ctx->precond))
+        return fail(GALE_EINVAL, "mask must be a non-empty subset of the precondition mask");
+    if (reps < 0) return fail(GALE_EINVAL, "reps must be >= 0");
+    if (reps == 0) reps = 2;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const int32_t K = ctx->hm.K;
+    // outputs of every cluster: one placement pass, then bins are timed alone
+    int64_t run[10] = {};
+    ctx->bulk_offs.assign(size_t(K) * 10, 0);
+    for (int32_t k = 0; k < K; ++k) {
+        int64_t L[10];
+        item_lengths(ctx, k, mask, L);
+        for (int a = 0; a < 10; ++a) {
+            ctx->bulk_offs[size_t(k) * 10 + a] = run[a];
+            run[a] += L[a];
+        }
+    }
+    gale_status st = ensure_bulk(ctx, run);
+    if (st != GALE_OK) return st;
+    for (int a = 0; a < 10; ++a) ctx->bulk_len[a] = run[a];
+    ctx->bulk_ids.resize(K);
+    std::iota(ctx->bulk_ids.begin(), ctx->bulk_ids.end(), 0);
+    ctx->bulk_mask = mask;
+    const gale::DevMesh dm = dev_mesh(ctx);
+    int rc = gale::launch_bases(dm, nullptr, K, ctx->d_sizes, mask, ctx->d_arrays_base + mask, ctx->d_items,
+                                ctx->d_totals, ctx->d_bsum, ctx->stream);
+    if (rc != 0) return cuda_fail(cudaError_t(rc), "bases launch");
+    const int smem_limit = gale::dynamic_smem_limit();
+    if (!gale::prepare_kernels(smem_limit)) return fail(GALE_ECUDA, "setting the kernels' shared memory limit failed");
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int cand_threads[] = {128, 256, 384, 512, 768, 1024};
+    for (size_t b = 0; b < ctx->bins.size(); ++b) {
+        gale::Bin &bin = ctx->bins[b];
+        const int32_t nb = int32_t(bin.clusters.size());
+        float best = -1.f;
+        gale::SmemPlan best_plan = bin.plan;
+        int best_grid = bin.grid, best_per = bin.ctas_per_sm;
+        for (int T : cand_threads) {
+            const gale::SmemPlan plan = gale::plan_smem(bin.plan.caps, T);
+            if (!bin.spill && plan.total > smem_limit) continue;
+            int max_per = gale::max_ctas_per_sm(plan, bin.spill);
+            if (bin.spill) max_per = std::min(max_per, 2);
+            for (int per = 1; per <= max_per; ++per) {
+                const int grid = std::max(1, std::min<int>(nb, per * ctx->sm_count));
+                char *scratch = nullptr;
+                if (bin.spill) {
+                    const int64_t need = int64_t(grid) * plan.total;
+                    if (need > ctx->spill_bytes) {
+                        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+                        if (ctx->d_spill) ctx->dfree(ctx->d_spill);
+                        ctx->d_spill = static_cast<char *>(ctx->dalloc(size_t(need)));
+                        ctx->spill_bytes = ctx->d_spill ? need : 0;
+                        if (!ctx->d_spill) {
+                            cudaEventDestroy(e0);
+                            cudaEventDestroy(e1);
+                            return fail(GALE_ENOMEM, "device allocation of the large-cluster scratch failed");
+                        }
+                    }
+                    scratch = ctx->d_spill;
+                }
+                auto launch = [&]() {
+                    return gale::launch_build(dm, plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b], nb,
+                                              ctx->d_err, ctx->d_tickets + b, grid, ctx->stream, scratch);
+                };
+                rc = launch();
+                CUDA_TRY(cudaEventRecord(e0, ctx->stream));
+                for (int r = 0; rc == 0 && r < reps; ++r) rc = launch();
+                CUDA_TRY(cudaEventRecord(e1, ctx->stream));
+                if (rc != 0) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return cuda_fail(cudaError_t(rc), "autotune launch");
+                }
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                ms /= float(reps);
+                if (best < 0.f || ms < best) {
+                    best = ms;
+                    best_plan = plan;
+                    best_grid = grid;
+                    best_per = per;
+                }
+            }
+        }
+        if (best >= 0.f) {
+            bin.plan = best_plan;
+            bin.grid = best_grid;
+            bin.ctas_per_sm = best_per;
+        }
+        if (best_ms && int32_t(b) < max_bins) best_ms[b] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int max_total = 0;
+    for (auto &bin : ctx->bins)
+        if (!bin.spill) max_total = std::max(max_total, bin.plan.total);
+    gale::prepare_kernels(max_total);
+    for (auto &g : ctx->graphs)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    st = check_device_error(ctx);
     return st;
 }
 

@@ -196,7 +196,10 @@ int serve_ctas_per_sm(const SmemPlan &plan);
 
 int kernel_smem_limit();
 int max_ctas_per_sm(const SmemPlan &plan, bool spill);
-void prepare_kernels(int smem);
+// Sets the dynamic shared memory limit of the cluster kernels to smem
+// (clamped to dynamic_smem_limit()); false if the runtime refused.
+bool prepare_kernels(int smem);
+int dynamic_smem_limit();
 int device_sm_count();
 
 }  // namespace gale

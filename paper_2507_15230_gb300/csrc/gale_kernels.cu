@@ -1207,10 +1207,30 @@ int device_sm_count() {
     return v;
 }
 
-void prepare_kernels(int smem) {
-    cudaFuncSetAttribute(build_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(build_one_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+// Largest dynamic shared memory a cluster kernel can be launched with: the
+// opt-in limit less the kernels' own static shared memory.
+int dynamic_smem_limit() {
+    const int optin = kernel_smem_limit();
+    int stat = 0;
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, build_kernel<false>) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
+    if (cudaFuncGetAttributes(&a, build_one_kernel<false>) == cudaSuccess)
+        stat = std::max(stat, int(a.sharedSizeBytes));
+    if (cudaFuncGetAttributes(&a, count_kernel<false>) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
+    if (cudaFuncGetAttributes(&a, serve_kernel) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
+    cudaGetLastError();
+    return optin - stat;
+}
+
+bool prepare_kernels(int smem) {
+    smem = std::min(smem, dynamic_smem_limit());
+    bool ok = cudaFuncSetAttribute(build_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+              cudaSuccess;
+    ok &= cudaFuncSetAttribute(build_one_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+          cudaSuccess;
+    ok &= cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+    cudaGetLastError();
+    return ok;
 }
 
 int max_ctas_per_sm(const SmemPlan &plan, bool spill) {

@@ -629,10 +629,4 @@ gale_status gale_serve_stats_get(gale_ctx *ctx, gale_serve_stats *out) {
     return GALE_OK;
 }
 
-gale_status gale_autotune(gale_ctx *ctx, uint32_t mask) {
-    (void)ctx;
-    (void)mask;
-    return GALE_OK;
-}
-
 }  // extern "C"

@@ -1,0 +1,137 @@
+"""Parity at the full sizes of the two build workloads, in the launch
+configuration the benchmark times (batched, graph replay, autotuned bins):
+
+* the 256^3 Freudenthal grid (100.7M tets, 65,536 kd leaves of <= 512
+  vertices), and
+* the Delaunay tetrahedralization of 2M Gaussian-mixture points (~13.5M tets,
+  uneven kd leaves of 32..2,048 vertices).
+
+The oracle cannot build whole meshes of this size in seconds, so sampled
+clusters (first, last, largest, smallest, one from every size bin, random)
+are compared bit-exactly with its per-cluster relations, and the whole
+output is checked against properties that hold at any size: the closed-form
+totals of the Freudenthal subdivision, the Euler characteristic of a
+triangulated ball, every tet in exactly four VT rows, and TT symmetry."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2507_15230_gb300 as gale
+
+pytestmark = pytest.mark.gpu
+
+
+def device_arrays(ctx):
+    ptrs, lens = ctx.bulk_arrays()
+    return {n: gale.device_tensor(ptrs[n], lens[n]) if lens[n] else torch.empty(0, dtype=torch.int32, device="cuda")
+            for n in lens}
+
+
+def global_rows(off, counts):
+    """Per-cluster offset segments (count+1 entries each) -> row lengths of
+    the concatenated rows."""
+    seg_end = torch.cumsum(torch.as_tensor(counts + 1, device=off.device), 0)
+    keep = torch.ones(off.numel(), dtype=torch.bool, device=off.device)
+    keep[seg_end - 1] = False
+    lens = off[1:].long() - off[:-1].long()
+    return lens[keep[:-1]]
+
+
+def check_tt_symmetric(d, I_T):
+    nt = int(I_T[-1])
+    lens = global_rows(d["tt_off"], np.diff(I_T))
+    assert lens.numel() == nt and int(lens.min()) >= 0 and int(lens.max()) <= 4
+    row = torch.repeat_interleave(torch.arange(nt, device=lens.device), lens)
+    val = d["tt_val"].long()
+    assert row.numel() == val.numel()
+    assert bool((val != row).all())
+    fwd = torch.sort(row * nt + val).values
+    bwd = torch.sort(val * nt + row).values
+    assert torch.equal(fwd, bwd)
+    return int(val.numel())
+
+
+def check_vt_counts(d, nt):
+    cnt = torch.bincount(d["vt_val"].long(), minlength=nt)
+    assert cnt.numel() == nt and bool((cnt == 4).all())
+
+
+def compare_sampled(ctx, canon, ks):
+    for k in ks:
+        k = int(k)
+        got = gale.view_to_numpy(ctx.bulk_view(k))
+        want = oracle.cluster_relations(canon, k)
+        for g, w in [("vt_off", "vt_off"), ("vt_val", "vt_val"), ("vv_off", "vv_off"), ("vv_val", "vv_val"),
+                     ("et_uoff", "eu_off"), ("et_w", "e_w"), ("et_off", "et_off"), ("et_val", "et_val"),
+                     ("tt_off", "tt_off"), ("tt_val", "tt_val")]:
+            assert np.array_equal(got[g].astype(np.int64), want[w].astype(np.int64)), (k, g)
+
+
+def sample_clusters(ctx, canon, rng, extra):
+    I_V = canon["I_V"]
+    size = np.diff(I_V)
+    K = size.size
+    ks = {0, K - 1, int(size.argmax()), int(size.argmin())}
+    # one member of every size bin
+    order = ctx.bin_members()
+    start = 0
+    for b in ctx.bins():
+        ks.add(int(order[start]))
+        start += b["clusters"]
+    ks.update(int(k) for k in rng.choice(K, extra, replace=False))
+    return sorted(ks)
+
+
+def test_grid256_full_size():
+    n = 256
+    m = gen.scale_grid(n)
+    with gale.Context.load(m, device=0) as ctx:
+        ctx.autotune(gale.ALL, reps=1)
+        for _ in range(2):  # the second build replays the captured graph
+            ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+        ctx.synchronize()
+        d = device_arrays(ctx)
+        T, V = 6 * n ** 3, (n + 1) ** 3
+        E = 7 * n ** 3 + 9 * n ** 2 + 3 * n
+        assert d["vt_val"].numel() == 4 * T
+        assert d["vv_val"].numel() == 2 * E
+        assert d["et_w"].numel() == E
+        assert d["et_val"].numel() == 6 * T
+        assert d["tt_val"].numel() == 4 * T - 12 * n ** 2
+        I_V, I_T, _ = ctx.intervals()
+        check_vt_counts(d, T)
+        check_tt_symmetric(d, I_T)
+        del d
+        torch.cuda.empty_cache()
+        canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
+        assert np.array_equal(canon["I_V"], I_V) and np.array_equal(canon["I_T"], I_T)
+        compare_sampled(ctx, canon, sample_clusters(ctx, canon, np.random.default_rng(7), 6))
+
+
+def test_delaunay_2m_full_size():
+    m = gen.delaunay_mesh(2_000_000, seed=5, with_field=False)
+    with gale.Context.load(m, device=0) as ctx:
+        ctx.autotune(gale.ALL, reps=1)
+        for _ in range(2):
+            ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+        ctx.synchronize()
+        d = device_arrays(ctx)
+        T, V = m.nt, m.nv
+        E = d["et_w"].numel()
+        assert d["vt_val"].numel() == 4 * T
+        assert d["vv_val"].numel() == 2 * E
+        assert d["et_val"].numel() == 6 * T
+        I_V, I_T, _ = ctx.intervals()
+        check_vt_counts(d, T)
+        sum_tt = check_tt_symmetric(d, I_T)
+        # faces: interior ones are counted twice by TT, boundary ones not at
+        # all, so F = 4T - sum|TT|/2; a triangulated ball has V - E + F - T = 1
+        F = 4 * T - sum_tt // 2
+        assert V - E + F - T == 1
+        del d
+        torch.cuda.empty_cache()
+        canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
+        assert np.array_equal(canon["I_V"], I_V) and np.array_equal(canon["I_T"], I_T)
+        compare_sampled(ctx, canon, sample_clusters(ctx, canon, np.random.default_rng(11), 10))

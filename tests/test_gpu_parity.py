@@ -169,3 +169,26 @@ def test_delaunay_uneven_clusters(npts, seed):
             ctx.build(None, gale.ALL, mode)
             ctx.synchronize()
             assert_bulk_equal(ctx.export(gale.ALL), expected_bulk(rel, canon, range(m.nclusters)))
+
+
+@pytest.mark.parametrize("which", ["grid", "delaunay"])
+def test_autotune_keeps_parity(which):
+    """gale_autotune picks a block size and CTAs per SM per size bin by
+    timing; the choice shows in the bins and the next full build (a fresh
+    graph capture) is still bit-exact."""
+    m = gen.small_grid() if which == "grid" else gen.delaunay_mesh(20000, seed=5, with_field=False)
+    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
+    with gale.Context.load(m, device=0) as ctx:
+        before = ctx.bins()
+        best = ctx.autotune(gale.ALL, reps=1)
+        after = ctx.bins()
+        assert len(best) == len(before) == len(after)
+        assert all(ms > 0 for ms in best)
+        for b0, b1 in zip(before, after):
+            assert b1["clusters"] == b0["clusters"] and b1["spill"] == b0["spill"]
+            assert b1["threads"] in (128, 256, 384, 512, 768, 1024)
+            assert 1 <= b1["grid"] <= max(b0["clusters"], 1)
+        for _ in range(2):
+            ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+            ctx.synchronize()
+            assert_bulk_equal(ctx.export(gale.ALL), expected_bulk(rel, canon, range(m.nclusters)))
