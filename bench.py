@@ -187,6 +187,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default block sizes")
+    ap.add_argument("--mixed", action="store_true", help="also run the 24-mesh mixed serving leg (minutes)")
+    ap.add_argument("--mixed-scale", type=float, default=1.0)
+    ap.add_argument("--mixed-requests", type=int, default=4000)
+    ap.add_argument("--mixed-budget-gb", type=float, default=20.0)
     ap.add_argument("--serve-threads", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     ap.add_argument("--serve-baseline-clusters", type=int, default=2048)
@@ -257,10 +261,13 @@ def main():
     host_np = {n: t.numpy() for n, t in host.items()}
     ctx.build_export(ids_np, gale.ALL, out=host_np)
     barrier(dist)
+    e2e_step_s = []
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         # ids in, every relation array out; chunk copies overlap the build
+        ts = time.perf_counter()
         ctx.build_export(ids_np, gale.ALL, out=host_np)  # blocks until the copies are done
+        e2e_step_s.append(time.perf_counter() - ts)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_s = max_over_ranks(dist, e2e_s)
     e2e_value = world * mesh.nt / e2e_s
@@ -302,6 +309,9 @@ def main():
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serve_leg(args, mesh, ctx, gale)
+    mixed = None
+    if rank == 0 and args.mixed:
+        mixed = mixed_leg(args, gale)
 
     traffic = None
     tp = os.path.join(ROOT, "profiles", "build_kernel_traffic.json")
@@ -327,7 +337,7 @@ def main():
                        "l2": f"no flush: {in_bytes / 1e9:.2f} GB of inputs and {out_bytes / 1e9:.2f} GB of outputs "
                              f"per step exceed the 129 MB L2"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(ids.numel() * 4),
-                    "d2h_bytes_per_step": int(out_bytes)},
+                    "d2h_bytes_per_step": int(out_bytes), "ms_per_step": [1e3 * x for x in e2e_step_s]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src},
@@ -336,6 +346,7 @@ def main():
             "clocks": clocks,
             "per_cluster": per_cluster,
             "serving": serving,
+            "mixed_serving": mixed,
             "load_seconds": {"host": info.load_host_seconds, "device": info.load_device_seconds},
             "bins": ctx.bins(),
             "autotune": None if tuned is None else {"best_ms_per_bin": tuned["best_ms_per_bin"]},
@@ -393,6 +404,143 @@ def serve_leg(args, mesh, ctx, gale):
                         f"jumps, VT+VV+TT requests, {args.serve_budget_gb:g} GB cache budget, field = 16 Gaussians",
             "device_loop": loop, "per_request_launch_subset": base,
             "device_loop_same_subset": loop_sub if nb > 0 else None}
+
+
+def mixed_meshes(scale: float = 1.0):
+    """The mixed serving workload: Freudenthal grids n = 32, 48, ..., 192 (kd
+    leaves <= 512, jitter 0.3, seed 7 + i) and Delaunay meshes of 100k .. 1M
+    Gaussian-mixture points, log-spaced (uneven kd leaves, seed 18 + i).
+    scale < 1 shrinks every mesh (grid edge and point count) for quick runs."""
+    import gen
+    meshes = []
+    for i, n in enumerate(range(32, 193, 16)):
+        nn = max(4, int(round(n * scale)))
+        meshes.append(gen.freudenthal_mesh(nn, 512, seed=7 + i, field_seed=100 + i, jitter=0.3, with_field=False,
+                                           name=f"grid{nn}^3"))
+    for i, p in enumerate(np.geomspace(1e5, 1e6, 13)):
+        npts = max(2000, int(p * scale ** 3))
+        meshes.append(gen.delaunay_mesh(npts, seed=18 + i, with_field=False))
+    return meshes
+
+
+def open_loop(ctxs, sizes, rate, nreq, seed, workers=64):
+    """Poisson arrivals at `rate` requests/s; each request asks one uniform
+    mesh for one uniform cluster and a mask uniform over the 15 non-empty
+    subsets of VT, VV, ET, TT.  Latency runs from the scheduled arrival to the
+    view being ready (queueing included).  rate = None: closed loop, every
+    worker requests back to back (capacity)."""
+    import queue
+    rng = np.random.default_rng(seed)
+    mi = rng.integers(len(ctxs), size=nreq)
+    ks = np.array([rng.integers(ctxs[m].K) for m in mi])
+    masks = rng.integers(1, 16, size=nreq)
+    lat = np.zeros(nreq)
+    fails = [0, None]
+    q = queue.Queue()
+    st0 = [(x.builds, x.hits) for x in (c.serve_stats() for c in ctxs)]
+
+    def serve_one(i):
+        c = ctxs[mi[i]]
+        try:
+            v = c.request(int(ks[i]), int(masks[i]), timeout_ns=120_000_000_000)
+            c.release(v)
+        except Exception as e:  # counted and reported, the run goes on
+            fails[0] += 1
+            if fails[1] is None:
+                fails[1] = f"mesh {int(mi[i])} cluster {int(ks[i])} mask {int(masks[i])}: {e}"
+
+    def worker():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            i, t_arr = item
+            serve_one(i)
+            lat[i] = time.perf_counter() - t_arr
+
+    th = [threading.Thread(target=worker) for _ in range(workers)]
+    for t in th:
+        t.start()
+    start = time.perf_counter()
+    if rate is None:
+        for i in range(nreq):
+            q.put((i, time.perf_counter()))
+    else:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+        for i, ta in enumerate(arrivals):
+            wait = start + ta - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            q.put((i, start + ta))
+    for _ in th:
+        q.put(None)
+    for t in th:
+        t.join()
+    wall = time.perf_counter() - start
+    tets = int(sum(sizes[m][k] for m, k in zip(mi, ks)))
+    st1 = [(x.builds, x.hits) for x in (c.serve_stats() for c in ctxs)]
+    return {"requests": nreq, "failures": fails[0], "first_failure": fails[1], "wall_s": wall,
+            "req_per_s": nreq / wall, "tets_per_s": tets / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "builds": int(sum(b[0] - a[0] for a, b in zip(st0, st1))),
+            "hits": int(sum(b[1] - a[1] for a, b in zip(st0, st1)))}
+
+
+def mixed_leg(args, gale):
+    """24 meshes loaded at once, Poisson-arriving requests for random masks at
+    0.25, 0.5 and 0.9 of the measured capacity of the device-loop form,
+    admitted against one budget split across the meshes in proportion to
+    their tet counts; the same arrivals then meet one kernel launch per
+    request."""
+    meshes = mixed_meshes(args.mixed_scale)
+    budget = int(args.mixed_budget_gb * (1 << 30))
+    nreq = args.mixed_requests
+
+    def load_all(mode):
+        # the budget is split in proportion to tet counts (relation bytes per
+        # tet are nearly the same across these meshes)
+        tot = sum(m.nt for m in meshes)
+        ctxs = [gale.Context.load(m, device=0, cache_budget_bytes=max(1 << 20, budget * m.nt // tot)) for m in meshes]
+        # every mesh's loop resident at once, even at one CTA per SM
+        loop_ctas = max(1, torch_sm_count() // len(ctxs))
+        for c in ctxs:
+            c.serve_configure(mode, loop_ctas=loop_ctas if mode == gale.SERVE_LOOP else 0)
+        sizes = []
+        for c in ctxs:
+            _, I_T, _ = c.intervals()
+            sizes.append(np.diff(I_T))
+        return ctxs, sizes, loop_ctas
+
+    out = {"workload": f"{len(meshes)} meshes (Freudenthal 32^3..192^3 kd<=512, Delaunay 100k..1M points "
+                       f"uneven kd) x scale {args.mixed_scale:g}, Poisson arrivals, masks uniform over 15 "
+                       f"subsets, {args.mixed_budget_gb:g} GB budget split by tet counts",
+           "tets": int(sum(m.nt for m in meshes)), "clusters": int(sum(m.nclusters for m in meshes)),
+           "requests_per_phase": nreq,
+           "phases": "warm-up (seed 1), closed-loop capacity (seed 2), then Poisson arrivals at 0.25, 0.5 and "
+                     "0.9 of the device loop's capacity (seeds 11, 12, 13); both forms see the same requests "
+                     "from a cold cache"}
+    fracs = (0.25, 0.5, 0.9)
+    rates = None
+    for mode, key in ((gale.SERVE_LOOP, "device_loop"), (gale.SERVE_SINGLE, "per_request_launch")):
+        ctxs, sizes, loop_ctas = load_all(mode)
+        res = {"loop_ctas_per_mesh": loop_ctas if mode == gale.SERVE_LOOP else None}
+        open_loop(ctxs, sizes, None, min(nreq, 1000), seed=1)
+        res["capacity"] = open_loop(ctxs, sizes, None, nreq, seed=2)
+        if rates is None:
+            rates = [f * res["capacity"]["req_per_s"] for f in fracs]
+            out["rates_req_per_s"] = rates
+        for j, (f, r) in enumerate(zip(fracs, rates)):
+            res[f"at_{f:g}"] = open_loop(ctxs, sizes, r, nreq, seed=11 + j)
+        res["evictions"] = int(sum(c.serve_stats().evictions for c in ctxs))
+        out[key] = res
+        for c in ctxs:
+            c.close()
+    return out
+
+
+def torch_sm_count() -> int:
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
 
 
 def gale_kernel_sha() -> str:

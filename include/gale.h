@@ -260,16 +260,20 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
 
 /* Serving execution forms. */
 enum {
-    GALE_SERVE_LOOP = 0,   /* device-resident request loop (default when its plan fits one CTA) */
+    GALE_SERVE_LOOP = 0,   /* device-resident request loop (default when some size bin fits it) */
     GALE_SERVE_BATCH = 1,  /* the leader launches the batched kernels for each batch of admitted requests */
     GALE_SERVE_SINGLE = 2  /* one kernel launch per request, one at a time (the baseline form) */
 };
 
-/* Choose the serving form and the loop's idle exit (microseconds, 0 =
- * default 20000) before the first gale_request of the context; EBUSY
- * afterwards, EINVAL for an unknown mode or when the loop's merged plan does
- * not fit one CTA. */
-gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us);
+/* Choose the serving form, the loop's idle exit (microseconds, 0 = default
+ * 20000) and the most CTAs the device loop may occupy (loop_ctas, 0 = as many
+ * as fit on the device; a cap lets the loops of several loaded meshes stay
+ * resident side by side) before the first gale_request of the context;
+ * EBUSY afterwards, EINVAL for an unknown mode, a negative cap, or when no
+ * size bin fits the loop.  The loop serves the size bins whose merged
+ * working-memory plan fits one CTA (smallest first); requests for clusters
+ * of the other bins are built by batched launches beside it. */
+gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, int32_t loop_ctas);
 
 /* Unpin a view from gale_request; its entry becomes evictable. */
 gale_status gale_release(gale_ctx *ctx, gale_view *view);

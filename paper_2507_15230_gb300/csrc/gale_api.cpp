@@ -213,23 +213,37 @@ char *scratch_of(gale_ctx *ctx, const gale::Bin &b) { return b.spill ? ctx->d_sp
 }  // namespace
 
 namespace gale {
-// One shared-memory plan covering every cluster (the serving loop takes any
-// cluster); *fits = it fits one CTA.
-SmemPlan serve_plan(gale_ctx *ctx, bool *fits) {
+// Shared-memory plan of the serving loop: size bins are merged, smallest
+// plan first, while the merged plan still fits one CTA; *fits = some bin
+// made it, and (*in_loop)[b] marks the bins the loop serves (the others are
+// served by batched launches).
+SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop) {
+    const size_t nb = ctx->bins.size();
+    std::vector<size_t> order;
+    for (size_t b = 0; b < nb; ++b)
+        if (!ctx->bins[b].spill) order.push_back(b);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return ctx->bins[a].plan.total < ctx->bins[b].plan.total; });
+    std::vector<uint8_t> sel(nb, 0);
     Caps c{};
     int threads = 64;
-    bool first = true;
-    for (const auto &b : ctx->bins) {
-        c = first ? b.plan.caps : merge(c, b.plan.caps);
-        threads = std::max(threads, b.plan.threads);
-        first = false;
+    bool any = false;
+    SmemPlan best{};
+    const int limit = dynamic_smem_limit();
+    for (size_t b : order) {
+        const Caps m = any ? merge(c, ctx->bins[b].plan.caps) : ctx->bins[b].plan.caps;
+        const int t = std::max(threads, ctx->bins[b].plan.threads);
+        const SmemPlan p = plan_smem(m, t);
+        if (p.total > limit || serve_ctas_per_sm(p) < 1) continue;
+        c = m;
+        threads = t;
+        best = p;
+        sel[b] = 1;
+        any = true;
     }
-    SmemPlan p = plan_smem(c, threads);
-    bool any_spill = false;
-    for (const auto &b : ctx->bins) any_spill |= b.spill;
-    *fits = !ctx->bins.empty() && !any_spill && p.total <= dynamic_smem_limit();
-    if (*fits) prepare_kernels(std::max(p.total, 0));
-    return p;
+    *fits = any;
+    if (in_loop) *in_loop = sel;
+    return best;
 }
 }  // namespace gale
 

@@ -45,6 +45,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "gale_internal.h"
 
@@ -1223,13 +1224,23 @@ int dynamic_smem_limit() {
 }
 
 bool prepare_kernels(int smem) {
-    smem = std::min(smem, dynamic_smem_limit());
+    // the attribute belongs to the kernel, shared by every context of the
+    // process on this device: it only ever grows (a larger limit does not
+    // change the occupancy of launches that ask for less)
+    static std::mutex mu;
+    static int granted[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    const int d = dev >= 0 && dev < 64 ? dev : 0;
+    smem = std::min(std::max(smem, granted[d]), dynamic_smem_limit());
     bool ok = cudaFuncSetAttribute(build_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
               cudaSuccess;
     ok &= cudaFuncSetAttribute(build_one_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
           cudaSuccess;
     ok &= cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     cudaGetLastError();
+    if (ok) granted[d] = smem;
     return ok;
 }
 
@@ -1278,17 +1289,31 @@ int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, 
     return int(cudaGetLastError());
 }
 
+// The serving kernel's shared memory limit, grown like the cluster kernels'.
+static void grow_serve_attr(int smem) {
+    static std::mutex mu;
+    static int granted[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int d = dev >= 0 && dev < 64 ? dev : 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem <= granted[d]) return;
+    if (cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess)
+        granted[d] = smem;
+    cudaGetLastError();
+}
+
 int launch_serve(const DevMesh &m, const SmemPlan &plan, const ServeRing &ring, int32_t *err, int grid,
                  void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
+    grow_serve_attr(plan.total);
     serve_kernel<<<grid, plan.threads, plan.total, s>>>(m, plan, ring, err);
     return int(cudaGetLastError());
 }
 
 int serve_ctas_per_sm(const SmemPlan &plan) {
     int a = 0;
-    cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
+    grow_serve_attr(plan.total);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, serve_kernel, plan.threads, plan.total) != cudaSuccess)
         return 0;
     return a;

@@ -40,7 +40,7 @@
 namespace gale {
 
 // defined in gale_api.cpp
-SmemPlan serve_plan(gale_ctx *ctx, bool *fits);
+SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop);
 
 namespace {
 
@@ -118,8 +118,9 @@ struct Serve {
     std::thread leader;
     gale_serve_stats stats{};
 
-    // device loop
+    // device loop (clusters of the bins it covers; the others are batched)
     bool loop_mode = true;
+    std::vector<uint8_t> in_loop;  // per size bin
     bool single_mode = false;  // one launch per request (baseline form)
     SmemPlan plan{};
     int grid = 0;
@@ -146,6 +147,7 @@ struct Serve {
     WorkItem *h_batch = nullptr;   // pinned staging
     int32_t *h_border = nullptr;
     cudaEvent_t batch_event = nullptr;
+    cudaStream_t batch_stream = nullptr;  // batched launches, beside the loop
     char *d_spill = nullptr;       // large-cluster scratch of the serving stream
     std::vector<Entry *> batch_entries;
     bool batch_busy = false;
@@ -200,7 +202,7 @@ gale_status Serve::init(gale_ctx *c) {
     if (!slab_base) return fail(GALE_ENOMEM, "device allocation of the relation cache failed");
     slab.init(ctx->cache_budget);
     bool fits = false;
-    plan = serve_plan(ctx, &fits);
+    plan = serve_plan(ctx, &fits, &in_loop);
     loop_mode = fits && (ctx->serve_mode < 0 || ctx->serve_mode == GALE_SERVE_LOOP);
     single_mode = ctx->serve_mode == GALE_SERVE_SINGLE;
     if (ctx->serve_idle_us > 0) idle_ns = uint64_t(std::max<int64_t>(100, ctx->serve_idle_us)) * 1000ull;
@@ -232,6 +234,7 @@ gale_status Serve::init(gale_ctx *c) {
         if (!d_spill) return fail(GALE_ENOMEM, "device allocation of the serving large-cluster scratch failed");
     }
     if (!ck(cudaStreamCreateWithFlags(&loop_stream, cudaStreamNonBlocking)) ||
+        !ck(cudaStreamCreateWithFlags(&batch_stream, cudaStreamNonBlocking)) ||
         !ck(cudaEventCreateWithFlags(&loop_event, cudaEventDisableTiming)) ||
         !ck(cudaEventCreateWithFlags(&batch_event, cudaEventDisableTiming)) ||
         !ck(cudaMemsetAsync(d_next, 0, 64, loop_stream)) || !ck(cudaMemsetAsync(d_err, 0, 64, loop_stream)) ||
@@ -241,6 +244,7 @@ gale_status Serve::init(gale_ctx *c) {
         const int per_sm = serve_ctas_per_sm(plan);
         if (per_sm < 1) loop_mode = false;
         else grid = per_sm * ctx->sm_count;
+        if (ctx->serve_loop_ctas > 0) grid = std::min(grid, ctx->serve_loop_ctas);
     }
     leader = std::thread([this] { leader_loop(); });
     return GALE_OK;
@@ -376,20 +380,32 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
         for (int32_t i : per[bb]) h_border[n++] = i;
         off[bb + 1] = n;
     }
-    cudaMemcpyAsync(d_batch, h_batch, sizeof(WorkItem) * b.size(), cudaMemcpyHostToDevice, loop_stream);
-    cudaMemcpyAsync(d_border, h_border, sizeof(int32_t) * n, cudaMemcpyHostToDevice, loop_stream);
+    cudaMemcpyAsync(d_batch, h_batch, sizeof(WorkItem) * b.size(), cudaMemcpyHostToDevice, batch_stream);
+    cudaMemcpyAsync(d_border, h_border, sizeof(int32_t) * n, cudaMemcpyHostToDevice, batch_stream);
     const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
-    for (int bb = 0; bb < nb; ++bb) {
+    int rc = 0;
+    for (int bb = 0; bb < nb && rc == 0; ++bb) {
         const int32_t m = off[bb + 1] - off[bb];
         if (m == 0) continue;
         char *scr = ctx->bins[bb].spill ? d_spill : nullptr;
         if (single_mode)
-            launch_build_one(dm, ctx->bins[bb].plan, d_batch, h_border[off[bb]], d_err, loop_stream, scr);
+            rc = launch_build_one(dm, ctx->bins[bb].plan, d_batch, h_border[off[bb]], d_err, batch_stream, scr);
         else
-            launch_build(dm, ctx->bins[bb].plan, d_batch, d_border + off[bb], m, d_err, d_tick + bb,
-                         std::min(ctx->bins[bb].grid, m), loop_stream, scr);
+            rc = launch_build(dm, ctx->bins[bb].plan, d_batch, d_border + off[bb], m, d_err, d_tick + bb,
+                              std::min(ctx->bins[bb].grid, m), batch_stream, scr);
     }
-    cudaEventRecord(batch_event, loop_stream);
+    if (rc != 0) {
+        // nothing of this batch is trusted: its entries fail and free their space
+        for (Entry *e : b) {
+            e->state = St::Failed;
+            e->fail = GALE_ECUDA;
+            slab.release(e->off, e->bytes);
+            e->bytes = 0;
+        }
+        cudaStreamSynchronize(batch_stream);
+        return;
+    }
+    cudaEventRecord(batch_event, batch_stream);
     for (Entry *e : b) e->state = St::Building;
     batch_entries = b;
     batch_busy = true;
@@ -418,13 +434,14 @@ void Serve::leader_loop() {
         std::vector<Entry *> batch;
         while (!queue.empty()) {
             Entry *e = queue.front();
-            if (!loop_mode && batch_busy) break;
-            if (loop_mode && published - (inflight.empty() ? published : inflight.begin()->first) >= kRingCap) break;
+            const bool via_loop = loop_mode && in_loop[ctx->bin_of[e->k]];
+            if (!via_loop && batch_busy) break;
+            if (via_loop && published - (inflight.empty() ? published : inflight.begin()->first) >= kRingCap) break;
             if (!admit(e)) break;
             queue.pop_front();
             progressed = true;
             if (e->state == St::Failed) continue;
-            if (loop_mode) publish_loop(e);
+            if (via_loop) publish_loop(e);
             else {
                 batch.push_back(e);
                 if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
@@ -433,7 +450,7 @@ void Serve::leader_loop() {
         if (!batch.empty()) launch_batch(batch);
         const size_t before = inflight.size() + (batch_busy ? batch_entries.size() : 0);
         if (loop_mode) poll_loop();
-        else poll_batch();
+        poll_batch();
         const size_t after = inflight.size() + (batch_busy ? batch_entries.size() : 0);
         if (after != before || progressed) {
             stats.max_batch = std::max<int64_t>(stats.max_batch, int64_t(before));
@@ -461,9 +478,11 @@ void serve_destroy(gale_ctx *ctx) {
     if (s->leader.joinable()) s->leader.join();
     if (s->h_stop) __atomic_store_n(s->h_stop, 1, __ATOMIC_RELEASE);
     if (s->loop_stream) cudaStreamSynchronize(s->loop_stream);
+    if (s->batch_stream) cudaStreamSynchronize(s->batch_stream);
     if (s->loop_event) cudaEventDestroy(s->loop_event);
     if (s->batch_event) cudaEventDestroy(s->batch_event);
     if (s->loop_stream) cudaStreamDestroy(s->loop_stream);
+    if (s->batch_stream) cudaStreamDestroy(s->batch_stream);
     cudaFreeHost(s->h_items);
     cudaFreeHost(s->h_tail);
     cudaFreeHost(s->h_done);
@@ -581,7 +600,8 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
         const gale_status f = e->fail;
         e->refs--;
         if (e->refs == 0) s->entries.erase(int64_t(e->k) * 16 + e->mask);
-        return fail(f, "cluster relations exceed the whole cache budget");
+        return fail(f, f == GALE_ENOMEM ? "cluster relations exceed the whole cache budget"
+                                        : "launching the cluster's build failed");
     }
     fill_view(ctx, e, out);
     return GALE_OK;
@@ -602,18 +622,20 @@ gale_status gale_release(gale_ctx *ctx, gale_view *view) {
     return GALE_OK;
 }
 
-gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us) {
+gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, int32_t loop_ctas) {
     if (!ctx) return fail(GALE_EINVAL, "NULL context");
     if (mode < GALE_SERVE_LOOP || mode > GALE_SERVE_SINGLE) return fail(GALE_EINVAL, "unknown serving mode");
+    if (loop_ctas < 0) return fail(GALE_EINVAL, "loop_ctas must be >= 0");
     std::lock_guard<std::mutex> lk(g_serve_init_mu);
     if (ctx->serve) return fail(GALE_EBUSY, "serving already started on this context");
     if (mode == GALE_SERVE_LOOP && ctx->device >= 0) {
         bool fits = false;
-        gale::serve_plan(ctx, &fits);
+        gale::serve_plan(ctx, &fits, nullptr);
         if (!fits) return fail(GALE_EINVAL, "the serving loop's merged plan does not fit one CTA");
     }
     ctx->serve_mode = mode;
     ctx->serve_idle_us = idle_us;
+    ctx->serve_loop_ctas = loop_ctas;
     return GALE_OK;
 }
 

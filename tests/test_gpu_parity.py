@@ -192,3 +192,19 @@ def test_autotune_keeps_parity(which):
             ctx.build(None, gale.ALL, gale.MODE_BATCHED)
             ctx.synchronize()
             assert_bulk_equal(ctx.export(gale.ALL), expected_bulk(rel, canon, range(m.nclusters)))
+
+
+def test_contexts_do_not_shrink_each_others_launch_limits():
+    """Kernel launch attributes are shared by every context of the process:
+    loading a small mesh after one with large shared-memory plans must not
+    stop the first one's large bins from launching."""
+    big = gen.delaunay_mesh(60000, seed=11, with_field=False)
+    canon, rel = oracle.build_all(big.nv, big.tv, big.seg, big.nclusters)
+    with gale.Context.load(big, device=0) as c1:
+        with gale.Context.load(gen.small_grid(with_field=False), device=0) as c2:
+            for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+                c1.build(None, gale.ALL, mode)
+                c1.synchronize()
+                assert_bulk_equal(c1.export(gale.ALL), expected_bulk(rel, canon, range(big.nclusters)))
+                c2.build(None, gale.ALL, mode)
+                c2.synchronize()

@@ -148,3 +148,82 @@ def test_serving_driver_matches_oracle_classification():
         want[canon["I_V"][k]:canon["I_V"][k + 1]] = consumers.classify_cluster(
             f_c, inid, canon["rows"], canon["I_V"][k], v["vt_off"], v["vt_val"], v["vv_off"], v["vv_val"])
     assert np.array_equal(cls, want)
+
+
+def test_mixed_meshes_loops_side_by_side():
+    """Four loaded meshes (two grids, two Delaunay meshes), each with its own
+    device loop capped at 8 CTAs so all stay resident, serve requests for
+    random (mesh, cluster, mask) from 12 threads under small budgets; every
+    result equals that mesh's bulk build of the cluster, bit for bit."""
+    meshes = [gen.freudenthal_mesh(6, 64, seed=7, jitter=0.3, with_field=False),
+              gen.freudenthal_mesh(9, 64, seed=8, jitter=0.3, with_field=False),
+              gen.delaunay_mesh(3000, seed=18, kd_cap=512, with_field=False),
+              gen.delaunay_mesh(6000, seed=19, kd_cap=512, with_field=False)]
+    ctxs = [gale.Context.load(m, device=0, cache_budget_bytes=1 << 20) for m in meshes]
+    try:
+        refs = [bulk_reference(c) for c in ctxs]
+        for c in ctxs:
+            c.serve_configure(gale.SERVE_LOOP, loop_ctas=8)
+        names = {gale.VT: ("vt_off", "vt_val"), gale.VV: ("vv_off", "vv_val"),
+                 gale.ET: ("et_uoff", "et_w", "et_off", "et_val"), gale.TT: ("tt_off", "tt_val")}
+        errors = []
+
+        def consumer(seed):
+            rng = np.random.default_rng(seed)
+            for _ in range(40):
+                i = int(rng.integers(len(ctxs)))
+                k = int(rng.integers(ctxs[i].K))
+                mk = int(rng.integers(1, 16))
+                v = ctxs[i].request(k, mk, timeout_ns=20_000_000_000)
+                got = gale.view_to_numpy(v)
+                for bit, arrs in names.items():
+                    if mk & bit:
+                        for n in arrs:
+                            if not np.array_equal(got[n], refs[i][k][n]):
+                                errors.append((i, k, mk, n))
+                ctxs[i].release(v)
+
+        th = [threading.Thread(target=consumer, args=(s,)) for s in range(12)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert not errors, errors[:5]
+        st = [c.serve_stats() for c in ctxs]
+        assert sum(s.requests for s in st) == 12 * 40
+        assert all(s.cache_bytes_used <= 1 << 20 for s in st)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_loop_mode_with_clusters_too_large_for_it():
+    """A Delaunay mesh whose largest clusters run in global scratch: the loop
+    serves the size bins that fit it and the leader builds the rest by
+    batched launches beside it; every result equals the bulk build."""
+    m = gen.delaunay_mesh(60000, seed=11, with_field=False)
+    with gale.Context.load(m, device=0, cache_budget_bytes=64 << 20) as ctx:
+        assert any(b["spill"] for b in ctx.bins())
+        ref = bulk_reference(ctx)
+        ctx.serve_configure(gale.SERVE_LOOP, loop_ctas=16)
+        I_V, _, _ = ctx.intervals()
+        size = np.diff(I_V)
+        big = [int(k) for k in np.argsort(size)[-6:]]
+        errors = []
+
+        def consumer(seed):
+            rng = np.random.default_rng(seed)
+            picks = big + [int(k) for k in rng.integers(ctx.K, size=20)]
+            for k in picks:
+                v = ctx.request(k, gale.ALL, timeout_ns=60_000_000_000)
+                if not same(gale.view_to_numpy(v), ref[k]):
+                    errors.append(k)
+                ctx.release(v)
+
+        th = [threading.Thread(target=consumer, args=(s,)) for s in range(6)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert not errors
+        assert ctx.serve_stats().requests == 6 * 26
