@@ -188,6 +188,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default block sizes")
     ap.add_argument("--mixed", action="store_true", help="also run the 24-mesh mixed serving leg (minutes)")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: each rank builds a balanced shard of the clusters (strong scaling) "
+                         "instead of a whole replica")
     ap.add_argument("--mixed-scale", type=float, default=1.0)
     ap.add_argument("--mixed-requests", type=int, default=4000)
     ap.add_argument("--mixed-budget-gb", type=float, default=20.0)
@@ -219,13 +222,27 @@ def main():
         # block size and CTAs per SM of every size bin, chosen by timing
         tuned = {"best_ms_per_bin": ctx.autotune(gale.ALL)}
 
+    # which clusters this rank builds: all of them (replicas, weak scaling),
+    # or its balanced contiguous shard (--shard, strong scaling)
+    shard_ids, shard_info = None, None
+    if args.shard and world > 1:
+        from paper_2507_15230_gb300 import shard as gshard
+        I_V, I_T, sizes = ctx.intervals()
+        lo_k, hi_k = gshard.shard_ranges(np.diff(I_T) + 1, world)[rank]
+        shard_ids = np.arange(lo_k, hi_k, dtype=np.int32)
+        edge0, edges = gshard.edge_base(int(sizes[lo_k:hi_k, 2].sum()), dist)
+        shard_info = {"clusters": [int(lo_k), int(hi_k)], "first_global_edge": edge0, "edges": edges}
+    my_tets = mesh.nt if shard_ids is None else int(np.diff(ctx.intervals()[1])[shard_ids].sum())
+
     # warm-up (also captures the batched graph)
     for _ in range(args.warmup):
-        ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+        ctx.build(shard_ids, gale.ALL, gale.MODE_BATCHED)
     ctx.synchronize()
     _, lens = ctx.bulk_arrays()
     out_bytes = 4 * sum(lens.values())
     in_bytes = int(info.block_bytes)
+    if shard_ids is not None:  # this rank's blocks, in proportion to its tets
+        in_bytes = int(info.block_bytes * my_tets / mesh.nt)
     alg_bytes = in_bytes + out_bytes
 
     # timed region: device throughput
@@ -239,7 +256,7 @@ def main():
         e0.record(stream)
         for a, b in step_ev:
             a.record(stream)
-            ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+            ctx.build(shard_ids, gale.ALL, gale.MODE_BATCHED)
             b.record(stream)
             launches += ctx.last_launch_count()
         e1.record(stream)
@@ -250,12 +267,15 @@ def main():
     ms = max_over_ranks(dist, ms)
     per_step = [a.elapsed_time(b) for a, b in step_ev]
     step_ms = statistics.mean(per_step)
-    value = world * mesh.nt / (ms / 1000.0)
+    # every rank's work counts: replicas build the whole mesh each, shards
+    # split it (the slowest rank's time, max over ranks)
+    value = (world * mesh.nt if shard_ids is None else mesh.nt) / (ms / 1000.0)
     peak, peak_src = load_peaks()
     achieved = alg_bytes / (step_ms / 1000.0) / 1e9
 
     # end to end through the C ABI with host buffers
-    ids = torch.arange(ctx.K, dtype=torch.int32).pin_memory()
+    ids = (torch.arange(ctx.K, dtype=torch.int32) if shard_ids is None
+           else torch.from_numpy(shard_ids.copy())).pin_memory()
     ids_np = ids.numpy()
     host = {n: torch.empty(lens[n], dtype=torch.int32).pin_memory() for n in lens}
     host_np = {n: t.numpy() for n, t in host.items()}
@@ -270,7 +290,7 @@ def main():
         e2e_step_s.append(time.perf_counter() - ts)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_s = max_over_ranks(dist, e2e_s)
-    e2e_value = world * mesh.nt / e2e_s
+    e2e_value = (world * mesh.nt if shard_ids is None else mesh.nt) / e2e_s
 
     # baseline form: one launch per cluster, on a subset
     per_cluster = None
@@ -328,12 +348,14 @@ def main():
         clocks = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak" if shard_ids is None else "strong",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"grid{args.grid}^3-jitter0.3-kd512: {mesh.nv} vertices, {mesh.nt} tets, "
                                    f"{mesh.nclusters} clusters",
                        "relations": "VT+VV+ET+TT, canonical sorted CSR", "mode": "batched persistent kernels, "
-                       "CUDA graph replay", "parallelism": f"replicas x{world}",
+                       "CUDA graph replay",
+                       "parallelism": f"replicas x{world}" if shard_ids is None else f"cluster shards x{world}",
                        "l2": f"no flush: {in_bytes / 1e9:.2f} GB of inputs and {out_bytes / 1e9:.2f} GB of outputs "
                              f"per step exceed the 129 MB L2"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(ids.numel() * 4),
@@ -347,6 +369,7 @@ def main():
             "per_cluster": per_cluster,
             "serving": serving,
             "mixed_serving": mixed,
+            "shard": shard_info,
             "load_seconds": {"host": info.load_host_seconds, "device": info.load_device_seconds},
             "bins": ctx.bins(),
             "autotune": None if tuned is None else {"best_ms_per_bin": tuned["best_ms_per_bin"]},
