@@ -197,6 +197,7 @@ def main():
     ap.add_argument("--serve-threads", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     ap.add_argument("--serve-baseline-clusters", type=int, default=2048)
+    ap.add_argument("--serve-prefetch", type=int, default=4, help="prefetch depth of the serving variant (0: off)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -407,6 +408,18 @@ def serve_leg(args, mesh, ctx, gale):
     s = ctx.serve_stats()
     loop.update({"builds": s.builds, "hits": s.hits, "evictions": s.evictions, "loop_launches": s.batches,
                  "critical_points": {str(c): int((cls == c).sum()) for c in (0, 1, 2, 3, 4)}})
+    # proactive prefetch (Section 4.5): each request also queues the next
+    # clusters, which the kd-order walks request next
+    pref = None
+    if args.serve_prefetch > 0:
+        with gale.Context.load(mesh, device=0, cache_budget_bytes=int(args.serve_budget_gb * (1 << 30))) as cp:
+            cp.serve_configure(gale.SERVE_LOOP, prefetch=args.serve_prefetch)
+            _, latp, stp = consumers.serve_run(cp, f_c, inid, rows, I_V, nthreads=args.serve_threads, mask=mask)
+            pref = summarize(latp, stp, cp.K)
+            sp = cp.serve_stats()
+            pref.update({"prefetch_depth": args.serve_prefetch, "builds": sp.builds, "hits": sp.hits,
+                         "prefetches": sp.prefetches, "prefetch_hits": sp.prefetch_hits,
+                         "prefetch_dropped": sp.prefetch_dropped, "evictions": sp.evictions})
     base = None
     nb = min(args.serve_baseline_clusters, ctx.K)
     if nb > 0:
@@ -425,7 +438,7 @@ def serve_leg(args, mesh, ctx, gale):
             loop_sub["clusters"] = nb
     return {"workload": f"{args.serve_threads} critical-point consumer threads, kd-order walks with 10% random "
                         f"jumps, VT+VV+TT requests, {args.serve_budget_gb:g} GB cache budget, field = 16 Gaussians",
-            "device_loop": loop, "per_request_launch_subset": base,
+            "device_loop": loop, "device_loop_prefetch": pref, "per_request_launch_subset": base,
             "device_loop_same_subset": loop_sub if nb > 0 else None}
 
 

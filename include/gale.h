@@ -147,6 +147,9 @@ typedef struct {
     int64_t requests, hits, misses, builds, evictions, batches;
     int64_t cache_bytes_used, cache_bytes_budget;
     int64_t max_batch;
+    int64_t prefetches;        /* entries built ahead of any request (proactive prefetch) */
+    int64_t prefetch_hits;     /* requests served by such an entry, ready or in flight */
+    int64_t prefetch_dropped;  /* prefetches dropped because the budget was pinned */
 } gale_serve_stats;
 
 /*
@@ -266,14 +269,19 @@ enum {
 };
 
 /* Choose the serving form, the loop's idle exit (microseconds, 0 = default
- * 20000) and the most CTAs the device loop may occupy (loop_ctas, 0 = as many
+ * 20000), the most CTAs the device loop may occupy (loop_ctas, 0 = as many
  * as fit on the device; a cap lets the loops of several loaded meshes stay
- * resident side by side) before the first gale_request of the context;
- * EBUSY afterwards, EINVAL for an unknown mode, a negative cap, or when no
+ * resident side by side) and the proactive prefetch depth (prefetch = m: a
+ * request for cluster k also queues clusters k+1 .. k+m with the same mask
+ * unless cached or queued, the paper's leader building the requested segment
+ * together with the following ones, Section 4.5; prefetched entries pin
+ * nothing and are dropped when the budget is pinned) before the first
+ * gale_request of the context;
+ * EBUSY afterwards, EINVAL for an unknown mode, a negative cap or depth, or when no
  * size bin fits the loop.  The loop serves the size bins whose merged
  * working-memory plan fits one CTA (smallest first); requests for clusters
  * of the other bins are built by batched launches beside it. */
-gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, int32_t loop_ctas);
+gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, int32_t loop_ctas, int32_t prefetch);
 
 /* Unpin a view from gale_request; its entry becomes evictable. */
 gale_status gale_release(gale_ctx *ctx, gale_view *view);

@@ -65,7 +65,8 @@ class Info(ctypes.Structure):
 
 class ServeStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("requests", "hits", "misses", "builds", "evictions", "batches",
-                                              "cache_bytes_used", "cache_bytes_budget", "max_batch")]
+                                              "cache_bytes_used", "cache_bytes_budget", "max_batch", "prefetches",
+                                              "prefetch_hits", "prefetch_dropped")]
 
 
 # the symbols include/gale.h declares
@@ -111,7 +112,7 @@ def load_library(build: bool = True):
     lib.gale_autotune.argtypes = [P, u32, i32, P, i32]
     lib.gale_get_bin_members.argtypes = [P, P]
     lib.gale_get_bins.argtypes = [P, P, i32, ctypes.POINTER(i32)]
-    lib.gale_serve_configure.argtypes = [P, i32, i64, i32]
+    lib.gale_serve_configure.argtypes = [P, i32, i64, i32, i32]
     lib.gale_stream.argtypes = [P]
     lib.gale_stream.restype = P
     lib.gale_last_launch_count.argtypes = [P]
@@ -347,9 +348,9 @@ class Context:
         _check(self._lib.gale_request(self._h, cluster, mask, timeout_ns, ctypes.byref(v)))
         return v
 
-    def serve_configure(self, mode: int, idle_us: int = 0, loop_ctas: int = 0):
+    def serve_configure(self, mode: int, idle_us: int = 0, loop_ctas: int = 0, prefetch: int = 0):
         """gale_serve_configure (before the first request)."""
-        _check(self._lib.gale_serve_configure(self._h, mode, idle_us, loop_ctas))
+        _check(self._lib.gale_serve_configure(self._h, mode, idle_us, loop_ctas, prefetch))
 
     def release(self, view: View):
         _check(self._lib.gale_release(self._h, ctypes.byref(view)))

@@ -95,6 +95,7 @@ struct gale_ctx {
     int32_t serve_mode = -1;          // -1: default (loop when it fits)
     int64_t serve_idle_us = 0;
     int32_t serve_loop_ctas = 0;      // 0: as many as fit
+    int32_t serve_prefetch = 0;       // clusters queued ahead of each request
 
     void *dalloc(size_t bytes);
     void dfree(void *p);

@@ -61,6 +61,8 @@ struct Entry {
     int64_t n_edges = 0;
     std::list<Entry *>::iterator lru;  // valid when Ready and unpinned-or-pinned (always in lru when Ready)
     bool in_lru = false;
+    bool prefetch = false;  // queued ahead of any request
+    bool claimed = false;   // a request has used it
 };
 
 // first-fit allocator over [0, cap) with a coalescing free list
@@ -437,10 +439,21 @@ void Serve::leader_loop() {
             const bool via_loop = loop_mode && in_loop[ctx->bin_of[e->k]];
             if (!via_loop && batch_busy) break;
             if (via_loop && published - (inflight.empty() ? published : inflight.begin()->first) >= kRingCap) break;
-            if (!admit(e)) break;
+            if (!admit(e)) {
+                if (!(e->prefetch && e->refs == 0)) break;
+                // a prefetch waits for nothing: drop it while the budget is pinned
+                queue.pop_front();
+                stats.prefetch_dropped++;
+                entries.erase(int64_t(e->k) * 16 + e->mask);  // frees e
+                progressed = true;
+                continue;
+            }
             queue.pop_front();
             progressed = true;
-            if (e->state == St::Failed) continue;
+            if (e->state == St::Failed) {
+                if (e->prefetch && e->refs == 0) entries.erase(int64_t(e->k) * 16 + e->mask);
+                continue;
+            }
             if (via_loop) publish_loop(e);
             else {
                 batch.push_back(e);
@@ -569,6 +582,10 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
         auto it = s->entries.find(int64_t(cluster_id) * 16 + m);
         if (it != s->entries.end() && it->second->state != St::Failed) e = it->second.get();
     }
+    if (e && e->prefetch && !e->claimed) {
+        e->claimed = true;
+        s->stats.prefetch_hits++;
+    }
     if (e && e->state == St::Ready) {
         s->stats.hits++;
         e->refs++;
@@ -585,6 +602,24 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
         s->entries[int64_t(cluster_id) * 16 + mask] = std::move(ne);
         s->queue.push_back(e);
         s->cv_leader.notify_all();
+    }
+    // proactive prefetch: the following clusters, queued behind the request
+    for (int32_t j = 1; j <= ctx->serve_prefetch && cluster_id + j < ctx->hm.K; ++j) {
+        const int32_t kk = cluster_id + j;
+        bool have = false;
+        for (uint32_t m = 1; m < 16 && !have; ++m) {
+            if ((m & mask) != mask) continue;
+            auto it = s->entries.find(int64_t(kk) * 16 + m);
+            have = it != s->entries.end() && it->second->state != St::Failed;
+        }
+        if (have) continue;
+        auto pe = std::make_unique<Entry>();
+        pe->k = kk;
+        pe->mask = mask;
+        pe->prefetch = true;
+        s->queue.push_back(pe.get());
+        s->entries[int64_t(kk) * 16 + mask] = std::move(pe);
+        s->stats.prefetches++;
     }
     e->refs++;
     auto ready = [&] { return e->state == St::Ready || e->state == St::Failed; };
@@ -622,10 +657,11 @@ gale_status gale_release(gale_ctx *ctx, gale_view *view) {
     return GALE_OK;
 }
 
-gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, int32_t loop_ctas) {
+gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, int32_t loop_ctas, int32_t prefetch) {
     if (!ctx) return fail(GALE_EINVAL, "NULL context");
     if (mode < GALE_SERVE_LOOP || mode > GALE_SERVE_SINGLE) return fail(GALE_EINVAL, "unknown serving mode");
     if (loop_ctas < 0) return fail(GALE_EINVAL, "loop_ctas must be >= 0");
+    if (prefetch < 0) return fail(GALE_EINVAL, "prefetch must be >= 0");
     std::lock_guard<std::mutex> lk(g_serve_init_mu);
     if (ctx->serve) return fail(GALE_EBUSY, "serving already started on this context");
     if (mode == GALE_SERVE_LOOP && ctx->device >= 0) {
@@ -636,6 +672,7 @@ gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, i
     ctx->serve_mode = mode;
     ctx->serve_idle_us = idle_us;
     ctx->serve_loop_ctas = loop_ctas;
+    ctx->serve_prefetch = prefetch;
     return GALE_OK;
 }
 

@@ -227,3 +227,54 @@ def test_loop_mode_with_clusters_too_large_for_it():
             t.join()
         assert not errors
         assert ctx.serve_stats().requests == 6 * 26
+
+
+@pytest.mark.parametrize("mode", [gale.SERVE_LOOP, gale.SERVE_BATCH])
+def test_prefetch_serves_following_clusters(mode):
+    """With prefetch depth 3, a request for cluster k also queues k+1..k+3;
+    consumers walking in cluster order then find their next clusters already
+    built or in flight.  Every result still equals the bulk build."""
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0, cache_budget_bytes=64 << 20) as ctx:
+        ref = bulk_reference(ctx)
+        ctx.serve_configure(mode, prefetch=3)
+        errors = []
+
+        def walker(start):
+            for k in range(start, min(start + 24, ctx.K)):
+                v = ctx.request(k, gale.ALL, timeout_ns=20_000_000_000)
+                if not same(gale.view_to_numpy(v), ref[k]):
+                    errors.append(k)
+                ctx.release(v)
+
+        th = [threading.Thread(target=walker, args=(s,)) for s in (0, 32, 64, 96)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert not errors
+        st = ctx.serve_stats()
+        assert st.requests == 4 * 24
+        assert st.prefetches > 0 and st.prefetch_hits > 0
+        assert st.prefetch_hits + st.misses <= st.requests + st.prefetches
+
+
+def test_prefetch_is_dropped_under_a_pinned_budget():
+    """Prefetches never wait for the budget: with most of it pinned by held
+    views they are dropped, and the held requests still complete."""
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0, cache_budget_bytes=96 << 10) as ctx:
+        ctx.serve_configure(gale.SERVE_LOOP, prefetch=8)
+        held = []
+        for k in (0, 40, 80):
+            try:
+                held.append(ctx.request(k, gale.ALL, timeout_ns=5_000_000_000))
+            except gale.GaleError:
+                break
+        assert held
+        st = ctx.serve_stats()
+        assert st.prefetches > 0
+        for v in held:
+            ctx.release(v)
+        v = ctx.request(1, gale.ALL, timeout_ns=5_000_000_000)
+        ctx.release(v)
