@@ -51,7 +51,7 @@ int64_t next_pow2(int64_t x) {
 // of the counting pass (sizes == nullptr: a counting plan, no staging).
 gale::Caps caps_of(const gale::ClusterStat &s, const int64_t *sizes) {
     gale::Caps c{};
-    c.blk_words = int32_t(gale::blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo));
+    c.blk_words = int32_t(gale::blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo, s.n_bnd));
     c.nv_own = s.nv_own;
     c.n_vt = s.n_vt;
     c.n_own = s.n_own;

@@ -29,6 +29,9 @@ namespace gale {
 //   next a4(2 * n_tot)    rows: 4 x uint16 local vertex ids per tet (ascending
 //                         within the row), tets in local order
 //                         [external | internal | halo]
+//   next a4(ceil(n_bnd/2)) bnd: uint16 internal-tet indices (0 = first
+//                         internal tet) of the internal tets (a, b, c, d)
+//                         whose face (b, c, d) has no own vertex, ascending
 //
 // Local vertex ids [0, nv_nb) are the vertices of the external and internal
 // tets in canonical order (so local order equals canonical order there);
@@ -51,12 +54,16 @@ static_assert(sizeof(BlockHdr) == 48, "header is 12 words");
 constexpr int kHdrWords = 12;
 
 GALE_HD inline int64_t a4(int64_t x) { return (x + 3) & ~int64_t(3); }
-GALE_HD inline int64_t blk_words(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo) {
-    return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo) + a4(2 * (int64_t(n_ext) + n_own + n_halo));
+GALE_HD inline int64_t blk_words(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo, int32_t n_bnd) {
+    return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo) + a4(2 * (int64_t(n_ext) + n_own + n_halo)) +
+           a4((int64_t(n_bnd) + 1) / 2);
 }
 GALE_HD inline int64_t blk_tmap_off(int32_t nv_loc) { return kHdrWords + a4(nv_loc); }
 GALE_HD inline int64_t blk_rows_off(int32_t nv_loc, int32_t n_ext, int32_t n_halo) {
     return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo);
+}
+GALE_HD inline int64_t blk_bnd_off(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo) {
+    return blk_rows_off(nv_loc, n_ext, n_halo) + a4(2 * (int64_t(n_ext) + n_own + n_halo));
 }
 
 // Largest local id space a block can address (uint16 local ids).

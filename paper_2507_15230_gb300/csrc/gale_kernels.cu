@@ -131,6 +131,11 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0u;
 }
+// bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, multiple of 16)
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // bounded wait for the phase with the given parity
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     for (int i = 0; i < kWaitLimit; ++i)
@@ -332,7 +337,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                         h.n_own <= caps.n_own && h.nv_loc <= caps.nv_loc && h.nv_own <= caps.nv_own &&
                         h.nv_nb <= caps.nv_nb && h.nv_nb <= h.nv_loc && int64_t(h.own_lo) + h.nv_own <= h.nv_nb &&
                         2 * int64_t(h.n_bnd) + 1 <= caps.hcap &&
-                        blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo) == words;
+                        blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo, h.n_bnd) == words;
         if (!ok) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             __syncthreads();
@@ -356,6 +361,13 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         if (loc < n_vtets) return t_base + (loc - n_ext);
         return tmap[loc - n_own];
     };
+
+    // The per-own-vertex passes of C2 leave whole warps idle when the cluster
+    // has fewer own vertices than the block has threads less a warp: those
+    // warps copy VT out meanwhile (vt_off and vt_list do not change after B).
+    const int copy_warp0 = (nvo + 31) >> 5;
+    const bool vt_copy_later = !COUNT && (mask & R_VT) && copy_warp0 < NWARP &&
+                               (COUNT || (mask & (R_VV | R_ET | R_TT)));
 
     // ---------------- B. VT ----------------
     int vt_total;
@@ -439,7 +451,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         __syncthreads();
         if (COUNT) {
             if (tid == 0) sizes_out[SZ_VT] = vt_total;
-        } else if (mask & R_VT) {
+        } else if ((mask & R_VT) && !vt_copy_later) {
             for (int i = tid; i <= nvo; i += NT) it->vt_off[i] = S.vt_off[i];
             copy_out(it->vt_val, vt_total, [&](int j) { return gtet(S.vt_list[j]); });
         }
@@ -541,6 +553,21 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             return true;
         }
         __syncthreads();
+        if (vt_copy_later && warp >= copy_warp0) {
+            // VT out, on the warps the per-vertex loop below leaves idle
+            const int t0 = tid - copy_warp0 * 32, nt = NT - copy_warp0 * 32;
+            for (int i = t0; i <= nvo; i += nt) it->vt_off[i] = S.vt_off[i];
+            int j = t0;
+            for (; j + 3 * nt < vt_total; j += 4 * nt) {
+                const int32_t a = gtet(S.vt_list[j]), b = gtet(S.vt_list[j + nt]);
+                const int32_t c = gtet(S.vt_list[j + 2 * nt]), d = gtet(S.vt_list[j + 3 * nt]);
+                it->vt_val[j] = a;
+                it->vt_val[j + nt] = b;
+                it->vt_val[j + 2 * nt] = c;
+                it->vt_val[j + 3 * nt] = d;
+            }
+            for (; j < vt_total; j += nt) it->vt_val[j] = gtet(S.vt_list[j]);
+        }
         // rows: one loop step per set bit, words visited through an
         // occupancy mask; the word holding x keeps its upper bits only and
         // every word with upper bits records the rank of its first one
@@ -740,9 +767,11 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         for (int i = tid; i < caps.hcap; i += NT) hash[i] = 0u;
         __syncthreads();
         int32_t flags = 0;
-        for (int i = tid; i < n_own; i += NT) {
+        // the internal tets whose face (b, c, d) has no own vertex
+        const uint16_t *bnd = reinterpret_cast<const uint16_t *>(S.blk + blk_bnd_off(h.nv_loc, n_ext, n_own, h.n_halo));
+        for (int jb = tid; jb < h.n_bnd; jb += NT) {
+            const int i = bnd[jb];
             const uint2 r = rows[n_ext + i];
-            if (vtx(r, 1) - uint32_t(lo) < nvo_u) continue;  // face (b, c, d) has an own vertex
             const uint64_t key = face_key(r, 0);
             uint32_t hp = face_hash(key, hmask);
             int probe = 0;
@@ -883,14 +912,25 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel(DevMesh m, SmemPlan 
     __shared__ __align__(8) uint64_t s_bar;
     init_barrier<SPILL>(&s_bar);
     uint32_t phase = 0;
+    if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
     for (;;) {
-        if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
         __syncthreads();
         const int idx = s_idx;
         __syncthreads();
         if (idx >= n) break;
-        if (threadIdx.x == 0) s_item = items[order ? order[idx] : idx];
+        if (threadIdx.x == 0) {
+            s_item = items[order ? order[idx] : idx];
+            s_idx = atomicAdd(ticket, 1);  // the next cluster of this CTA
+        }
         __syncthreads();
+        if (threadIdx.x == 32 && s_idx < n) {
+            // its block into L2 while this cluster builds
+            const int k2 = items[order ? order[s_idx] : s_idx].k;
+            if (k2 >= 0 && k2 < m.K) {
+                const int64_t w0 = m.blk_off[k2], w1 = m.blk_off[k2 + 1];
+                if (w1 > w0) prefetch_l2(m.blocks + w0, uint32_t(4 * (w1 - w0)));
+            }
+        }
         const int k = s_item.k;
         if (k < 0 || k >= m.K) {
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);

@@ -400,7 +400,7 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
     for (int32_t k = 0; k < K; ++k) {
         const ClusterStat &s = hm.stats[k];
         hm.blk_off[k] = run;
-        run += blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo);
+        run += blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo, s.n_bnd);
         hm.ext_total += s.n_ext;
         hm.halo_total += s.n_halo;
     }
@@ -442,6 +442,11 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         for (int32_t i = 0; i < s.n_ext; ++i) put(hm.ext[e0 + i]);
         for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t) put(t);
         for (int32_t i = 0; i < s.n_halo; ++i) put(hm.halo[h0 + i]);
+        // internal tets whose face opposite their lowest vertex has no own vertex
+        uint16_t *bnd = reinterpret_cast<uint16_t *>(blk + blk_bnd_off(s.nv_loc, s.n_ext, s.n_own, s.n_halo));
+        int32_t nb = 0;
+        for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t)
+            if (rows[4 * int64_t(t) + 1] >= v0 + s.nv_own) bnd[nb++] = uint16_t(t - hm.I_T[k]);
     });
     hm.host_seconds = std::chrono::duration<double>(clk::now() - t0).count();
     return true;
