@@ -68,6 +68,7 @@ gale::Caps caps_of(const gale::ClusterStat &s, const int64_t *sizes) {
     }
     c.hcap = int32_t(std::max<int64_t>(64, next_pow2(2 * int64_t(s.n_bnd) + 1)));
     c.n_tot = s.n_ext + s.n_own + s.n_halo;
+    c.n_star = s.n_ext + s.n_own;
     return c;
 }
 
@@ -87,6 +88,7 @@ gale::Caps merge(const gale::Caps &a, const gale::Caps &b) {
     c.max_up = std::max(a.max_up, b.max_up);
     c.hcap = std::max(a.hcap, b.hcap);
     c.n_tot = std::max(a.n_tot, b.n_tot);
+    c.n_star = std::max(a.n_star, b.n_star);
     return c;
 }
 

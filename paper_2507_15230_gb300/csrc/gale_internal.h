@@ -115,6 +115,7 @@ struct Caps {
     int32_t max_up;     // most upper neighbours of an own vertex
     int32_t hcap;       // boundary-face hash capacity (power of two)
     int32_t n_tot;      // largest tet count of a block (external + internal + halo)
+    int32_t n_star;     // largest external + internal tet count
 };
 
 // Byte offsets of the shared-memory regions of one CTA (all 16-aligned).
@@ -136,8 +137,9 @@ struct SmemPlan {
     int32_t c_vv;       // int32[nv_own+1] VV row offsets
     int32_t c_e;        // int32[nv_own+1] first owned edge of each own vertex
     int32_t nbr;        // uint16[4*n_own] TT links
-    int32_t jself;      // uint16[2*n_own] position of each internal tet in VT of its two lowest vertices
-    int32_t eu;         // uint16[max_e] lower endpoint (own index) of each owned edge
+    int32_t jpos;       // uint8 (or uint16 when jpos16)[4*n_star]: position of each
+                        // (tet, own slot) in that vertex's VT row
+    int32_t jpos16;     // 1: VT rows may exceed 256 entries, positions are 16-bit
     int32_t r2;         // uint16[max_vv] VV staging | uint32[max_e*nch] edge masks
     int32_t st_w;       // uint16[max_e] upper-endpoint staging (inside r2)
     int32_t r1;         // see above

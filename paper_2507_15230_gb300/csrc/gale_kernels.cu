@@ -62,7 +62,8 @@ struct Smem {
     int32_t *vt_off;
     uint16_t *vt_list;
     int32_t *c_vv, *c_e;
-    uint16_t *nbr, *jself, *eu;
+    uint16_t *nbr;
+    uint8_t *jpos;
     uint32_t *emask;  // r2
     uint16_t *st_v;   // r2
     uint16_t *st_w;   // r2
@@ -85,8 +86,7 @@ __device__ __forceinline__ Smem carve(char *base, const SmemPlan &p) {
     s.c_vv = reinterpret_cast<int32_t *>(base + p.c_vv);
     s.c_e = reinterpret_cast<int32_t *>(base + p.c_e);
     s.nbr = reinterpret_cast<uint16_t *>(base + p.nbr);
-    s.jself = reinterpret_cast<uint16_t *>(base + p.jself);
-    s.eu = reinterpret_cast<uint16_t *>(base + p.eu);
+    s.jpos = reinterpret_cast<uint8_t *>(base + p.jpos);
     s.emask = reinterpret_cast<uint32_t *>(base + p.r2);
     s.st_v = reinterpret_cast<uint16_t *>(base + p.r2);
     s.st_w = reinterpret_cast<uint16_t *>(base + p.st_w);
@@ -295,6 +295,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     const Caps &caps = plan.caps;
     const int32_t *__restrict__ g = m.blocks + blk_word;
     int32_t *flag = S.scan + 120;  // [0] block fits, [1] bulk copy issued
+    const bool jp16 = plan.jpos16 != 0;
 
     // ---------------- A. the block, by one bulk copy ----------------
     if (tid == 0) {
@@ -416,8 +417,8 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             return true;
         }
-        // fill in tet order, 32 tets per step of each warp; an internal
-        // tet's position in VT of its two lowest vertices is kept for TT
+        // fill in tet order, 32 tets per step of each warp; the position
+        // of every (tet, own vertex) in that vertex's row is kept for C3/C5
         for (int i0 = c0; i0 < c1; i0 += 32) {
             const int i = i0 + lane;
             const uint2 r = i < c1 ? rows[i] : make_uint2(0xffffffffu, 0xffffffffu);
@@ -436,7 +437,8 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                     mm[s] = mk[warp * pad + d[s]];
                     const int pos = int(cw[warp * pad + d[s]]) + __popc(mm[s] & lt);
                     S.vt_list[S.vt_off[d[s]] + pos] = uint16_t(i);
-                    if (s < 2 && i >= n_ext) S.jself[2 * (i - n_ext) + s] = uint16_t(pos);
+                    if (jp16) reinterpret_cast<uint16_t *>(S.jpos)[4 * i + s] = uint16_t(pos);
+                    else S.jpos[4 * i + s] = uint8_t(pos);
                 }
             }
             __syncwarp();
@@ -601,10 +603,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                     if (do_vv) S.st_v[vrun] = id;
                     ++vrun;
                     if (bit & um) {
-                        if (do_et) {
-                            S.st_w[erun] = id;
-                            S.eu[erun] = uint16_t(x);
-                        }
+                        if (do_et) S.st_w[erun] = id;
                         ++erun;
                     }
                 }
@@ -638,47 +637,41 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     for (int i = tid; i < tot_e * nch; i += NT) em[i] = 0u;
     __syncthreads();
 
-    // ---------------- C3. edge tet masks, per VT incidence ----------------
+    // ---------------- C3. edge tet masks, per tet ----------------
+    // bit j of mask(x, w): the j-th tet of VT(x) contains w; every own
+    // vertex x of a tet marks the edges to the tet's vertices above x
     {
-        const int n_vt = vt_total;
-        const int per = range_len(n_vt);
-        const int k0 = min(n_vt, tid * per), k1 = min(n_vt, k0 + per);
-        if (k0 < k1) {
-            // own vertex whose row holds entry k0
-            int x = 0, hi = nvo - 1;
-            while (x < hi) {
-                const int mid = (x + hi + 1) >> 1;
-                if (S.vt_off[mid] <= k0) x = mid;
-                else hi = mid - 1;
+        auto mark = [&](uint32_t x, uint32_t y, uint32_t j) {
+            const int q = int(y >> 5);
+            const int e = S.c_e[x] + int(pre[x * WP + q]) + __popc(bm[x * WP + q] & ((1u << (y & 31)) - 1u));
+            atomicOr(em + e * nch + (j >> 5), 1u << (j & 31));
+        };
+        for (int i = tid; i < n_vtets; i += NT) {
+            const uint2 r = rows[i];
+            const uint32_t v0 = r.x & 0xffffu, v1 = r.x >> 16, v2 = r.y & 0xffffu, v3 = r.y >> 16;
+            uint32_t j0, j1, j2;
+            if (jp16) {
+                const uint2 jw = reinterpret_cast<const uint2 *>(S.jpos)[i];
+                j0 = jw.x & 0xffffu;
+                j1 = jw.x >> 16;
+                j2 = jw.y & 0xffffu;
+            } else {
+                const uint32_t jw = reinterpret_cast<const uint32_t *>(S.jpos)[i];
+                j0 = jw & 0xffu;
+                j1 = (jw >> 8) & 0xffu;
+                j2 = (jw >> 16) & 0xffu;
             }
-            int beg = S.vt_off[x], nxt = S.vt_off[x + 1];
-            const uint32_t *bmx = bm + x * WP;
-            const uint8_t *prx = pre + x * WP;
-            int eb = S.c_e[x];
-            for (int k = k0; k < k1; ++k) {
-                while (k >= nxt) {
-                    ++x;
-                    beg = nxt;
-                    nxt = S.vt_off[x + 1];
-                    bmx += WP;
-                    prx += WP;
-                    eb = S.c_e[x];
-                }
-                const int j = k - beg;
-                const uint2 r = rows[S.vt_list[k]];
-                const uint32_t X = uint32_t(lo + x);
-                const uint32_t v0 = r.x & 0xffffu, v1 = r.x >> 16, v2 = r.y & 0xffffu, v3 = r.y >> 16;
-                uint32_t *emj = em + (j >> 5);
-                const uint32_t bit = 1u << (j & 31);
-                auto mark = [&](uint32_t y) {
-                    const int q = int(y >> 5);
-                    const int e = eb + int(prx[q]) + __popc(bmx[q] & ((1u << (y & 31)) - 1u));
-                    atomicOr(emj + e * nch, bit);
-                };
-                if (v0 == X) mark(v1);
-                if (v0 == X || v1 == X) mark(v2);
-                if (v3 != X) mark(v3);
+            const uint32_t x0 = v0 - uint32_t(lo), x1 = v1 - uint32_t(lo), x2 = v2 - uint32_t(lo);
+            if (x0 < nvo_u) {
+                mark(x0, v1, j0);
+                mark(x0, v2, j0);
+                mark(x0, v3, j0);
             }
+            if (x1 < nvo_u) {
+                mark(x1, v2, j1);
+                mark(x1, v3, j1);
+            }
+            if (x2 < nvo_u) mark(x2, v3, j2);
         }
     }
     __syncthreads();
@@ -715,12 +708,14 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 if (partner >= 0) S.nbr[i * 4 + opp] = uint16_t(partner);
             };
             const int e1 = rank(a, v1), e2 = rank(a, v2), e3 = rank(a, v3);
-            const int base_a = S.vt_off[a], ja = S.jself[2 * i];
+            const int ja = jp16 ? reinterpret_cast<const uint16_t *>(S.jpos)[4 * li] : S.jpos[4 * li];
+            const int jb = jp16 ? reinterpret_cast<const uint16_t *>(S.jpos)[4 * li + 1] : S.jpos[4 * li + 1];
+            const int base_a = S.vt_off[a];
             link(e1, e2, base_a, ja, 3);
             link(e1, e3, base_a, ja, 2);
             link(e2, e3, base_a, ja, 1);
             const uint32_t b = v1 - uint32_t(lo);
-            if (b < nvo_u) link(rank(b, v2), rank(b, v3), S.vt_off[b], S.jself[2 * i + 1], 0);
+            if (b < nvo_u) link(rank(b, v2), rank(b, v3), S.vt_off[b], jb, 0);
         }
         if (flags) atomicOr(err, flags);
     }
@@ -741,8 +736,19 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             __syncthreads();
             return true;
         }
+        // own vertex holding edge e0: the largest x with c_e[x] <= e0
+        int xe = 0;
+        if (e0 < e1) {
+            int hi = nvo - 1;
+            while (xe < hi) {
+                const int mid = (xe + hi + 1) >> 1;
+                if (S.c_e[mid] <= e0) xe = mid;
+                else hi = mid - 1;
+            }
+        }
         for (int e = e0; e < e1; ++e) {
-            const int base = S.vt_off[S.eu[e]];
+            while (S.c_e[xe + 1] <= e) ++xe;
+            const int base = S.vt_off[xe];
             const int t0 = run;
             for (int c = 0; c < nch; ++c) {
                 uint32_t mm = em[e * nch + c];
@@ -1206,10 +1212,9 @@ SmemPlan plan_smem(const Caps &c, int threads) {
     off = a16(off + 4 * (nvo + 1));
     p.nbr = int32_t(off);
     off = a16(off + 8 * int64_t(c.n_own));
-    p.jself = int32_t(off);
-    off = a16(off + 4 * int64_t(c.n_own));
-    p.eu = int32_t(off);
-    off = a16(off + 2 * int64_t(c.max_e));
+    p.jpos16 = c.max_deg > 256 ? 1 : 0;
+    p.jpos = int32_t(off);
+    off = a16(off + (p.jpos16 ? 8 : 4) * int64_t(c.n_star));
     // r2: VV staging + upper-endpoint staging, then the edge masks
     p.r2 = int32_t(off);
     p.st_w = int32_t(a16(off + 2 * int64_t(c.max_vv)));
