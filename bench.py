@@ -464,60 +464,22 @@ def open_loop(ctxs, sizes, rate, nreq, seed, workers=64):
     mesh for one uniform cluster and a mask uniform over the 15 non-empty
     subsets of VT, VV, ET, TT.  Latency runs from the scheduled arrival to the
     view being ready (queueing included).  rate = None: closed loop, every
-    worker requests back to back (capacity)."""
-    import queue
+    request at time zero (capacity).  The dispatch runs in native threads
+    (consumers.open_loop) so that the driver is not the bottleneck."""
+    import consumers
     rng = np.random.default_rng(seed)
-    mi = rng.integers(len(ctxs), size=nreq)
-    ks = np.array([rng.integers(ctxs[m].K) for m in mi])
-    masks = rng.integers(1, 16, size=nreq)
-    lat = np.zeros(nreq)
-    fails = [0, None]
-    q = queue.Queue()
+    mi = rng.integers(len(ctxs), size=nreq).astype(np.int32)
+    ks = np.array([rng.integers(ctxs[m].K) for m in mi], dtype=np.int32)
+    masks = rng.integers(1, 16, size=nreq).astype(np.uint32)
     st0 = [(x.builds, x.hits) for x in (c.serve_stats() for c in ctxs)]
-
-    def serve_one(i):
-        c = ctxs[mi[i]]
-        try:
-            v = c.request(int(ks[i]), int(masks[i]), timeout_ns=120_000_000_000)
-            c.release(v)
-        except Exception as e:  # counted and reported, the run goes on
-            fails[0] += 1
-            if fails[1] is None:
-                fails[1] = f"mesh {int(mi[i])} cluster {int(ks[i])} mask {int(masks[i])}: {e}"
-
-    def worker():
-        while True:
-            item = q.get()
-            if item is None:
-                return
-            i, t_arr = item
-            serve_one(i)
-            lat[i] = time.perf_counter() - t_arr
-
-    th = [threading.Thread(target=worker) for _ in range(workers)]
-    for t in th:
-        t.start()
-    start = time.perf_counter()
-    if rate is None:
-        for i in range(nreq):
-            q.put((i, time.perf_counter()))
-    else:
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
-        for i, ta in enumerate(arrivals):
-            wait = start + ta - time.perf_counter()
-            if wait > 0:
-                time.sleep(wait)
-            q.put((i, start + ta))
-    for _ in th:
-        q.put(None)
-    for t in th:
-        t.join()
-    wall = time.perf_counter() - start
+    lat, wall, fails, first = consumers.open_loop(ctxs, mi, ks, masks, rate, seed=seed + 1000, workers=workers)
     tets = int(sum(sizes[m][k] for m, k in zip(mi, ks)))
     st1 = [(x.builds, x.hits) for x in (c.serve_stats() for c in ctxs)]
-    return {"requests": nreq, "failures": fails[0], "first_failure": fails[1], "wall_s": wall,
-            "req_per_s": nreq / wall, "tets_per_s": tets / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+    return {"requests": nreq, "failures": fails,
+            "first_failure": None if first < 0 else f"mesh {int(mi[first])} cluster {int(ks[first])} "
+                                                      f"mask {int(masks[first])}",
+            "wall_s": wall, "req_per_s": nreq / wall, "tets_per_s": tets / wall,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "builds": int(sum(b[0] - a[0] for a, b in zip(st0, st1))),
             "hits": int(sum(b[1] - a[1] for a, b in zip(st0, st1)))}
 

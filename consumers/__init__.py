@@ -47,6 +47,8 @@ def _load():
         lib.gale_cp_classify.restype = ctypes.c_int
         lib.gale_cp_serve_run.argtypes = [P, P, P, P, P, i32, i32, u32, u64, f64, P, P, P]
         lib.gale_cp_serve_run.restype = ctypes.c_int
+        lib.gale_open_loop.argtypes = [P, i32, P, P, P, i64, f64, u64, i32, P, P]
+        lib.gale_open_loop.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -92,3 +94,23 @@ def serve_run(ctx, f_c, inid_c, rows, I_V, nthreads=16, mask=15, seed=6, jump_pr
     lib.gale_cp_serve_run(ctx._h, _p(f_c), _p(inid_c), _p(rows), _p(I_V), K, nthreads, mask, seed, jump_prob,
                           _p(cls), _p(lat), _p(st))
     return cls, lat, {"wall": st[0], "requests": int(st[1]), "d2h_bytes": int(st[2]), "failures": int(st[3])}
+
+
+def open_loop(ctxs, mi, ks, masks, rate=None, seed=0, workers=64):
+    """Native open-loop driver (gale_open_loop): Poisson arrivals at `rate`
+    requests/s (None: all at once, a capacity run) of (mesh mi[i], cluster
+    ks[i], mask masks[i]); returns (latency seconds per request, wall
+    seconds, failures, first failing request or -1)."""
+    lib = _load()
+    n = len(mi)
+    handles = (ctypes.c_void_p * len(ctxs))(*[c._h for c in ctxs])
+    mi = np.ascontiguousarray(mi, dtype=np.int32)
+    ks = np.ascontiguousarray(ks, dtype=np.int32)
+    masks = np.ascontiguousarray(masks, dtype=np.uint32)
+    lat = np.zeros(n, np.float64)
+    st = np.zeros(3, np.float64)
+    rc = lib.gale_open_loop(ctypes.cast(handles, ctypes.c_void_p), len(ctxs), _p(mi), _p(ks), _p(masks), n,
+                            float(rate) if rate else 0.0, int(seed), int(workers), _p(lat), _p(st))
+    if rc != 0:
+        raise RuntimeError("gale_open_loop failed")
+    return lat, float(st[0]), int(st[1]), int(st[2])

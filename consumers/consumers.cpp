@@ -198,4 +198,57 @@ int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const 
     return 0;
 }
 
+/*
+ * Open-loop request driver for one or more loaded meshes.  Requests arrive
+ * as a Poisson process of `rate` per second (rate <= 0: all at time zero, the
+ * closed loop that measures capacity); request i asks mesh mi[i] for cluster
+ * ks[i] with mask masks[i].  nworkers threads take the requests in arrival
+ * order: each waits for its request's arrival time (sleeping until shortly
+ * before it, then yielding), calls gale_request (no time limit) and
+ * gale_release.
+ *   lat    double[n] out: seconds from the scheduled arrival to the view
+ *   stats  double[3] out: wall seconds, failures, first failing request (-1)
+ */
+int gale_open_loop(gale_ctx *const *ctxs, int32_t nctx, const int32_t *mi, const int32_t *ks, const uint32_t *masks,
+                   int64_t n, double rate, uint64_t seed, int32_t nworkers, double *lat, double *stats) {
+    using clk = std::chrono::steady_clock;
+    std::vector<double> arr(static_cast<size_t>(n), 0.0);
+    if (rate > 0) {
+        std::mt19937_64 rng(seed);
+        std::exponential_distribution<double> gap(rate);
+        double t = 0;
+        for (int64_t i = 0; i < n; ++i) arr[i] = (t += gap(rng));
+    }
+    std::atomic<int64_t> next{0}, fails{0}, first_fail{-1};
+    const auto t0 = clk::now();
+    auto worker = [&]() {
+        for (;;) {
+            const int64_t i = next.fetch_add(1);
+            if (i >= n) return;
+            const auto due = t0 + std::chrono::duration_cast<clk::duration>(std::chrono::duration<double>(arr[i]));
+            if (clk::now() + std::chrono::microseconds(200) < due)
+                std::this_thread::sleep_until(due - std::chrono::microseconds(200));
+            while (clk::now() < due) std::this_thread::yield();
+            gale_view v;
+            const int32_t m = mi[i];
+            gale_status st = (m >= 0 && m < nctx) ? gale_request(ctxs[m], ks[i], masks[i], 0, &v) : GALE_EINVAL;
+            lat[i] = std::chrono::duration<double>(clk::now() - due).count();
+            if (st != GALE_OK) {
+                fails++;
+                int64_t none = -1;
+                first_fail.compare_exchange_strong(none, i);
+                continue;
+            }
+            gale_release(ctxs[m], &v);
+        }
+    };
+    std::vector<std::thread> th;
+    for (int w = 0; w < nworkers; ++w) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+    stats[0] = std::chrono::duration<double>(clk::now() - t0).count();
+    stats[1] = double(fails.load());
+    stats[2] = double(first_fail.load());
+    return 0;
+}
+
 }  // extern "C"

@@ -192,6 +192,17 @@ def test_mixed_meshes_loops_side_by_side():
         st = [c.serve_stats() for c in ctxs]
         assert sum(s.requests for s in st) == 12 * 40
         assert all(s.cache_bytes_used <= 1 << 20 for s in st)
+        # the native open-loop driver over the same meshes: Poisson arrivals
+        import consumers
+        rng = np.random.default_rng(4)
+        n = 400
+        mi = rng.integers(len(ctxs), size=n)
+        ks = np.array([rng.integers(ctxs[i].K) for i in mi])
+        masks = rng.integers(1, 16, size=n)
+        lat, wall, fails, first = consumers.open_loop(ctxs, mi, ks, masks, rate=20000.0, seed=9, workers=16)
+        assert fails == 0 and first == -1
+        assert lat.shape == (n,) and (lat >= 0).all() and wall > 0
+        assert sum(c.serve_stats().requests for c in ctxs) == 12 * 40 + n
     finally:
         for c in ctxs:
             c.close()
