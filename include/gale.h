@@ -166,10 +166,14 @@ typedef struct {
  *   - per cluster: its internal tets, its external tets T_ex (Section 4.3),
  *     and the halo of tets outside the cluster that share a triangle with an
  *     internal tet (needed for complete TT rows);
- *   - the exact size of every relation of every cluster (a counting pass on
- *     the GPU), used for output placement and cache admission.
+ *   - the exact size of every relation in the precondition mask of every
+ *     cluster (a counting pass on the GPU), used for output placement and
+ *     cache admission.
  * The cluster working sets are copied to device memory once, as the paper
- * copies its initialised arrays to GPU global memory.
+ * copies its initialised arrays to GPU global memory.  TT needs a manifold
+ * mesh (no triangle in more than two tets): with GALE_TT in the precondition
+ * mask, a non-manifold mesh fails with EDEVICE (non-manifold bit); without
+ * it, VT, VV and ET of such a mesh are built as usual.
  * On success *out owns all of it; release with gale_destroy.
  */
 gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out);

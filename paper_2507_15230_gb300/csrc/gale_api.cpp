@@ -289,7 +289,8 @@ gale_status count_pass(gale_ctx *ctx) {
         const gale::Bin &bin = ctx->bins[b];
         int rc = gale::launch_count_pass(dev_mesh(ctx), bin.plan, ctx->d_order_all + ctx->order_all_off[b],
                                          int32_t(bin.clusters.size()), ctx->d_sizes, ctx->d_err,
-                                         ctx->d_tickets + b, bin.grid, ctx->stream, scratch_of(ctx, bin));
+                                         ctx->d_tickets + b, bin.grid, ctx->stream, scratch_of(ctx, bin),
+                                         ctx->precond);
         if (rc != 0) return cuda_fail(cudaError_t(rc), "count pass launch");
     }
     gale_status st = check_device_error(ctx);

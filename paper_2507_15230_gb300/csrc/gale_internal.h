@@ -176,8 +176,10 @@ struct DevMesh {
 // (build).  One CTA per cluster at a time.
 // gscratch: NULL runs the cluster in dynamic shared memory; otherwise each
 // CTA uses the slice gscratch + blockIdx.x * plan.total of global memory.
+// mask: the relations the context is preconditioned for (TT sizes only
+// when it holds R_TT).
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
-                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch);
+                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, uint32_t mask);
 // Output placement for n listed clusters (three launches).  bsum: device
 // scratch of bases_scratch_words(n) int64 words.
 int bases_scratch_words(int32_t n);

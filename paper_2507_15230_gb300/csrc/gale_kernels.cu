@@ -352,7 +352,8 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     const int32_t *tmap = S.blk + blk_tmap_off(h.nv_loc);
     const int nvo = h.nv_own, lo = h.own_lo;
     const uint32_t nvo_u = uint32_t(nvo);
-    const bool want_tt = COUNT || (mask & R_TT);
+    // the counting pass sizes the relations the context is preconditioned for
+    const bool want_tt = (mask & R_TT) != 0;
     const bool do_vv = !COUNT && (mask & R_VV);
     const bool do_et = !COUNT && (mask & R_ET);
     const int32_t t_base = h.t_base;
@@ -879,7 +880,7 @@ __device__ __forceinline__ void init_barrier(uint64_t *bar) {
 
 template <bool SPILL>
 __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan plan, const int32_t *ids, int32_t n, int64_t *sizes, int32_t *err,
-                             int32_t *ticket, char *gscratch) {
+                             int32_t *ticket, char *gscratch, uint32_t mask) {
     extern __shared__ __align__(16) char smem[];
     const Smem S = carve(region_base<SPILL>(smem, gscratch, plan), plan);
     __shared__ int32_t s_idx;
@@ -900,7 +901,7 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan 
         }
         if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
         __syncthreads();
-        if (!run_cluster<true, SPILL>(m, plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], 0u, nullptr, s_sizes,
+        if (!run_cluster<true, SPILL>(m, plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr, s_sizes,
                                       err, &s_bar, phase))
             return;
         __syncthreads();
@@ -1304,11 +1305,14 @@ int max_ctas_per_sm(const SmemPlan &plan, bool spill) {
 }
 
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
-                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch) {
+                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, uint32_t mask) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
-    if (gscratch) count_kernel<true><<<grid, plan.threads, 0, s>>>(m, plan, ids, n, sizes_out, err, ticket, gscratch);
-    else count_kernel<false><<<grid, plan.threads, plan.total, s>>>(m, plan, ids, n, sizes_out, err, ticket, nullptr);
+    if (gscratch)
+        count_kernel<true><<<grid, plan.threads, 0, s>>>(m, plan, ids, n, sizes_out, err, ticket, gscratch, mask);
+    else
+        count_kernel<false><<<grid, plan.threads, plan.total, s>>>(m, plan, ids, n, sizes_out, err, ticket, nullptr,
+                                                                  mask);
     return int(cudaGetLastError());
 }
 

@@ -208,3 +208,78 @@ def test_contexts_do_not_shrink_each_others_launch_limits():
                 assert_bulk_equal(c1.export(gale.ALL), expected_bulk(rel, canon, range(big.nclusters)))
                 c2.build(None, gale.ALL, mode)
                 c2.synchronize()
+
+
+def fan_mesh(m_ring=200):
+    """A vertex of degree 2 * m_ring: the centre of a ring of m_ring vertices
+    between two poles, every tet (centre, pole, ring_i, ring_i+1).  Its VT
+    row exceeds 256 entries and spans several 32-tet chunks."""
+    ang = np.linspace(0, 2 * np.pi, m_ring, endpoint=False)
+    xyz = np.zeros((m_ring + 3, 3), np.float32)
+    xyz[1] = [0, 0, 1]
+    xyz[2] = [0, 0, -1]
+    xyz[3:, 0] = np.cos(ang)
+    xyz[3:, 1] = np.sin(ang)
+    tv = []
+    for i in range(m_ring):
+        a, b = 3 + i, 3 + (i + 1) % m_ring
+        tv.append([0, 1, a, b])
+        tv.append([0, 2, a, b])
+    return xyz, np.array(tv, np.int32)
+
+
+@pytest.mark.parametrize("K,seed", [(1, 0), (3, 1), (12, 2)])
+def test_high_degree_vertex(K, seed):
+    """A 400-tet star (16-bit star positions, masks of 13 32-tet chunks) under
+    several partitions, every mask, both modes."""
+    xyz, tv = fan_mesh()
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(xyz.shape[0]).astype(np.int32)
+    tv = perm[tv]
+    xyz = xyz[np.argsort(perm)]
+    seg = rng.integers(0, K, xyz.shape[0]).astype(np.int32)
+    seg[perm[0]] = 0
+    m = gen.Mesh(xyz, tv, seg, K)
+    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, K)
+    with gale.Context.load(m, device=0) as ctx:
+        _, _, sizes = ctx.intervals()
+        assert np.array_equal(sizes, oracle.cluster_sizes(rel, canon))
+        for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+            for mask in (gale.ALL, gale.ET, gale.TT, gale.VV | gale.ET):
+                ctx.build(None, mask, mode)
+                ctx.synchronize()
+                assert_bulk_equal(ctx.export(mask), expected_bulk(rel, canon, range(K), mask))
+
+
+@pytest.mark.parametrize("mask", [gale.VT, gale.VV, gale.ET, gale.TT, gale.VT | gale.ET])
+def test_spill_bins_every_mask(mask):
+    """Clusters too large for shared memory (global-scratch bins) under every
+    relation mask, batched and one launch per cluster."""
+    m = gen.delaunay_mesh(60000, seed=11, with_field=False)
+    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
+    with gale.Context.load(m, device=0) as ctx:
+        assert any(b["spill"] for b in ctx.bins())
+        for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+            ctx.build(None, mask, mode)
+            ctx.synchronize()
+            assert_bulk_equal(ctx.export(mask), expected_bulk(rel, canon, range(m.nclusters), mask))
+
+
+def test_non_manifold_input():
+    """Three tets on one triangle: TT needs a manifold mesh, so loading with
+    TT in the precondition mask fails with EDEVICE; without it, VT, VV and ET
+    equal the oracle's."""
+    xyz = np.random.default_rng(0).random((6, 3)).astype(np.float32)
+    tv = np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]], np.int32)
+    seg = np.array([0, 0, 1, 1, 0, 1], np.int32)
+    m = gen.Mesh(xyz, tv, seg, 2)
+    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, 2)
+    with pytest.raises(gale.GaleError) as ei:
+        gale.Context.load(m, device=0)
+    assert gale.STATUS[ei.value.status] == "EDEVICE" and "manifold" in str(ei.value)
+    pre = gale.VT | gale.VV | gale.ET
+    with gale.Context.load(m, device=0, precondition_mask=pre) as ctx:
+        for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+            ctx.build(None, pre, mode)
+            ctx.synchronize()
+            assert_bulk_equal(ctx.export(pre), expected_bulk(rel, canon, range(2), pre))
