@@ -214,3 +214,86 @@ def build_all(nv: int, tv: np.ndarray, seg: np.ndarray, nclusters: int):
         raise ValueError(f"oracle_validate: {rc}")
     canon = canonicalize(nv, tv, seg, nclusters)
     return canon, relations(canon)
+
+
+# ---------------------------------------------------------------------------
+# Edge and triangle enumeration and boundary relations (Section 4.3
+# "Initialization": E and F are enumerated on the CPU by iterating the
+# tetrahedra of each segment, all two- and three-vertex combinations, with
+# interval arrays I_E, I_F; Section 4.4: a consumer computes a boundary
+# relation such as FE by looking the combinations up in E within the owning
+# segment's interval).  An edge or triangle belongs to the segment of its
+# lowest vertex (the internal rule).  Two numberings:
+#   "sorted" - within each segment, lexicographic in canonical ids;
+#   "first"  - within each segment, in order of first appearance while the
+#              tetrahedra are visited in canonical order, each tetrahedron's
+#              combinations in combination order (the numbering of the
+#              worked example FE(f5) = {e2, e6, e9}).
+# Plain Python over the canonical rows; meant for small meshes.
+# ---------------------------------------------------------------------------
+
+def enumerate_simplices(canon: dict, order: str = "sorted") -> dict:
+    """E (list of (u, w)), F (list of (a, b, c)), I_E, I_F (length K+1)."""
+    if order not in ("sorted", "first"):
+        raise ValueError("order is 'sorted' or 'first'")
+    rows = canon["rows"]
+    I_V = np.asarray(canon["I_V"])
+    K = I_V.size - 1
+
+    def seg(v):
+        return int(np.searchsorted(I_V, v, side="right") - 1)
+
+    per_e = [[] for _ in range(K)]
+    per_f = [[] for _ in range(K)]
+    seen_e, seen_f = set(), set()
+    for t in range(rows.shape[0]):
+        r = [int(x) for x in rows[t]]  # ascending
+        for i in range(4):
+            for j in range(i + 1, 4):
+                e = (r[i], r[j])
+                if e not in seen_e:
+                    seen_e.add(e)
+                    per_e[seg(e[0])].append(e)
+        for i in range(4):
+            for j in range(i + 1, 4):
+                for k in range(j + 1, 4):
+                    f = (r[i], r[j], r[k])
+                    if f not in seen_f:
+                        seen_f.add(f)
+                        per_f[seg(f[0])].append(f)
+    if order == "sorted":
+        per_e = [sorted(x) for x in per_e]
+        per_f = [sorted(x) for x in per_f]
+    E = [e for x in per_e for e in x]
+    F = [f for x in per_f for f in x]
+    I_E = [0]
+    for x in per_e:
+        I_E.append(I_E[-1] + len(x))
+    I_F = [0]
+    for x in per_f:
+        I_F.append(I_F[-1] + len(x))
+    return {"E": E, "F": F, "I_E": I_E, "I_F": I_F}
+
+
+def boundary(canon: dict, enum: dict, relation: str, ids) -> list:
+    """Boundary relations by lookup (Section 4.4): "FE" - a triangle's edges
+    (a,b), (a,c), (b,c); "TE" - a tetrahedron's six edges in combination
+    order; "TF" - a tetrahedron's four triangles (a,b,c), (a,b,d), (a,c,d),
+    (b,c,d).  Ids are global edge / triangle ids of `enum`."""
+    eid = {e: i for i, e in enumerate(enum["E"])}
+    fid = {f: i for i, f in enumerate(enum["F"])}
+    rows = canon["rows"]
+    out = []
+    for s in ids:
+        if relation == "FE":
+            a, b, c = enum["F"][int(s)]
+            out.append([eid[(a, b)], eid[(a, c)], eid[(b, c)]])
+        elif relation == "TE":
+            r = [int(x) for x in rows[int(s)]]
+            out.append([eid[(r[i], r[j])] for i in range(4) for j in range(i + 1, 4)])
+        elif relation == "TF":
+            r = [int(x) for x in rows[int(s)]]
+            out.append([fid[(r[i], r[j], r[k])] for i in range(4) for j in range(i + 1, 4) for k in range(j + 1, 4)])
+        else:
+            raise ValueError("relation is 'FE', 'TE' or 'TF'")
+    return out

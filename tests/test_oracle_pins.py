@@ -366,3 +366,103 @@ def test_pins_catch_planted_mistakes():
     assert matches_brute(rel, brute)
     for name, bad in _mutations(rel):
         assert not matches_brute(bad, brute), name
+
+
+# ---------------------------------------------------------------------------
+# edge / triangle enumeration and boundary relations (Sections 4.3, 4.4)
+# ---------------------------------------------------------------------------
+
+def test_enumeration_paper_example():
+    """The worked example: I_E = [0, 9, 12], the triangle f5 = (v0, v3, v4)
+    and FE(f5) = {e2, e6, e9} under first-appearance numbering; sorted
+    numbering keeps I_E and the triangle sets but gives (v0, v4) the id e3."""
+    g = load_golden("mesh_input_example.json")
+    tv, seg = np.array(g["tv"], np.int32), np.array(g["seg"], np.int32)
+    canon = oracle.canonicalize(g["nv"], tv, seg, g["nclusters"])
+    first = oracle.enumerate_simplices(canon, "first")
+    assert first["I_E"] == g["expect"]["I_E"]
+    assert list(first["F"][5]) == g["expect"]["f5"]
+    assert oracle.boundary(canon, first, "FE", [5]) == [g["expect"]["FE_f5"]]
+    srt = oracle.enumerate_simplices(canon, "sorted")
+    assert srt["I_E"] == g["expect"]["I_E"]
+    f5 = srt["F"].index(tuple(g["expect"]["f5"]))
+    assert oracle.boundary(canon, srt, "FE", [f5]) == [[2, 3, 9]]
+
+
+@pytest.mark.parametrize("n,K,seed", [(1, 1, 0), (2, 3, 1), (3, 5, 2), (4, 9, 3)])
+def test_enumeration_closed_forms_and_invariants(n, K, seed):
+    xyz, tv = gen.freudenthal_grid(n, permute=True, seed=seed + 40)
+    seg = np.random.default_rng(seed).integers(0, K, xyz.shape[0]).astype(np.int32)
+    canon = oracle.canonicalize(xyz.shape[0], tv, seg, K)
+    rows = canon["rows"]
+    I_V = np.asarray(canon["I_V"])
+    all_e = {(int(r[i]), int(r[j])) for r in rows for i in range(4) for j in range(i + 1, 4)}
+    all_f = {(int(r[i]), int(r[j]), int(r[k])) for r in rows for i in range(4) for j in range(i + 1, 4)
+             for k in range(j + 1, 4)}
+    enums = {o: oracle.enumerate_simplices(canon, o) for o in ("sorted", "first")}
+    for o, en in enums.items():
+        E, F = en["E"], en["F"]
+        assert len(E) == 7 * n ** 3 + 9 * n ** 2 + 3 * n == len(all_e) and set(E) == all_e
+        assert len(F) == 12 * n ** 3 + 6 * n ** 2 == len(all_f) and set(F) == all_f
+        for k in range(K):  # ownership by the lowest vertex
+            for e in E[en["I_E"][k]:en["I_E"][k + 1]]:
+                assert I_V[k] <= e[0] < I_V[k + 1]
+            for f in F[en["I_F"][k]:en["I_F"][k + 1]]:
+                assert I_V[k] <= f[0] < I_V[k + 1]
+        te = oracle.boundary(canon, en, "TE", range(rows.shape[0]))
+        tf = oracle.boundary(canon, en, "TF", range(rows.shape[0]))
+        for t in range(rows.shape[0]):
+            r = set(int(x) for x in rows[t])
+            assert len(set(te[t])) == 6 and all(set(E[i]) <= r for i in te[t])
+            assert len(set(tf[t])) == 4 and all(set(F[i]) <= r for i in tf[t])
+            for fe in oracle.boundary(canon, en, "FE", tf[t]):  # a face's edges are edges of the tet
+                assert set(fe) <= set(te[t])
+    # the two numberings list the same simplices per segment; sorted is lexicographic
+    s, f = enums["sorted"], enums["first"]
+    assert s["I_E"] == f["I_E"] and s["I_F"] == f["I_F"]
+    for k in range(K):
+        a, b = s["I_E"][k], s["I_E"][k + 1]
+        assert s["E"][a:b] == sorted(f["E"][a:b])
+        a, b = s["I_F"][k], s["I_F"][k + 1]
+        assert s["F"][a:b] == sorted(f["F"][a:b])
+
+
+def enumeration_violations(canon, n, E, F, TE, FE):
+    """The closed-form and structural checks above, as a list of failures."""
+    rows = canon["rows"]
+    bad = []
+    if len(E) != 7 * n ** 3 + 9 * n ** 2 + 3 * n or len(set(E)) != len(E):
+        bad.append("edge count")
+    if len(F) != 12 * n ** 3 + 6 * n ** 2 or len(set(F)) != len(F):
+        bad.append("triangle count")
+    for t, te in enumerate(TE):
+        r = set(int(x) for x in rows[t])
+        if len(set(te)) != 6 or not all(0 <= i < len(E) and set(E[i]) <= r for i in te):
+            bad.append(f"TE({t})")
+            break
+    for f, fe in enumerate(FE):
+        if f >= len(F) or len(set(fe)) != 3 or not all(0 <= i < len(E) and set(E[i]) <= set(F[f]) for i in fe):
+            bad.append(f"FE({f})")
+            break
+    return bad
+
+
+def test_enumeration_planted_mistakes_fail():
+    """The checks catch a dropped edge, a repeated triangle, a tetrahedron's
+    edge list with a repeated pair, and FE ids off by one."""
+    n = 2
+    xyz, tv = gen.freudenthal_grid(n, permute=True, seed=7)
+    seg = np.random.default_rng(3).integers(0, 3, xyz.shape[0]).astype(np.int32)
+    canon = oracle.canonicalize(xyz.shape[0], tv, seg, 3)
+    en = oracle.enumerate_simplices(canon, "first")
+    E, F = en["E"], en["F"]
+    TE = oracle.boundary(canon, en, "TE", range(canon["rows"].shape[0]))
+    FE = oracle.boundary(canon, en, "FE", range(len(F)))
+    assert enumeration_violations(canon, n, E, F, TE, FE) == []
+    assert enumeration_violations(canon, n, E[:-1], F, TE, FE)  # dropped edge
+    assert enumeration_violations(canon, n, E, F[:-1] + [F[0]], TE, FE)  # repeated triangle
+    te_bad = [list(x) for x in TE]
+    te_bad[0][5] = te_bad[0][4]  # a pair listed twice
+    assert enumeration_violations(canon, n, E, F, te_bad, FE)
+    fe_bad = [[(i + 1) % len(E) for i in x] for x in FE]  # ids off by one
+    assert enumeration_violations(canon, n, E, F, TE, fe_bad)
