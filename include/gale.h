@@ -313,6 +313,43 @@ gale_status gale_get_working_set(gale_ctx *ctx, int32_t k, int32_t *ext, int64_t
 
 gale_status gale_get_info(gale_ctx *ctx, gale_info *out);
 
+/*
+ * Edge and triangle enumeration (Section 4.3, "Initialization": E and F are
+ * enumerated on the CPU, with interval arrays I_E and I_F; only when the
+ * analysis needs edges or triangles).  An edge (u, w), u < w, or a triangle
+ * (a, b, c), a < b < c, in canonical vertex ids, belongs to the segment of
+ * its lowest vertex; segment k's simplices have the global ids
+ * [I_E[k], I_E[k+1]) (resp. I_F).  Within a segment they are numbered
+ *   GALE_ENUM_SORTED            lexicographically (the (u, w) order of the
+ *                               edges of the ET relation), or
+ *   GALE_ENUM_FIRST_APPEARANCE  by first appearance while the segment's
+ *                               tetrahedra are visited in canonical order,
+ *                               each tetrahedron's vertex combinations in
+ *                               combination order (the numbering of the
+ *                               paper's worked example FE(f5) = {e2, e6, e9}).
+ * Host work, on host-only contexts too; replaces an earlier enumeration.
+ */
+enum { GALE_ENUM_SORTED = 0, GALE_ENUM_FIRST_APPEARANCE = 1 };
+gale_status gale_enumerate(gale_ctx *ctx, int32_t order);
+
+/* The enumeration (host memory; any pointer may be NULL): counts[2] = edges,
+ * triangles; edges int32[2 nE] (u, w); I_E int64[K+1]; faces int32[3 nF]
+ * (a, b, c); I_F int64[K+1].  ENOTFOUND before gale_enumerate. */
+gale_status gale_get_enumeration(gale_ctx *ctx, int64_t *counts, int32_t *edges, int64_t *I_E, int32_t *faces,
+                                 int64_t *I_F);
+
+/* Boundary relations, per simplex, by lookup in the enumeration within the
+ * owning segment's interval (Section 4.4):
+ *   GALE_REL_FE  triangle ids -> 3 edge ids each: (a,b), (a,c), (b,c)
+ *   GALE_REL_TE  canonical tet ids -> 6 edge ids each, combination order
+ *                (a,b), (a,c), (a,d), (b,c), (b,d), (c,d)
+ *   GALE_REL_TF  canonical tet ids -> 4 triangle ids each: (a,b,c),
+ *                (a,b,d), (a,c,d), (b,c,d)
+ * ids: HOST int64[n]; out: HOST int32[width * n].  EINVAL on an id out of
+ * range, ENOTFOUND before gale_enumerate. */
+enum { GALE_REL_FE = 1, GALE_REL_TE = 2, GALE_REL_TF = 3 };
+gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, int64_t n, int32_t *out);
+
 /* Tuning: threads per block of the producer kernels (a multiple of 32 in
  * [64, 1024]; 0 = one thread per own vertex of the largest cluster of each
  * size bin) and CTAs per SM of the persistent grid (0 = as many as fit). */

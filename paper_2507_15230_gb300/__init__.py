@@ -19,6 +19,8 @@ import numpy as np
 from . import _build
 
 VT, VV, ET, TT = 1, 2, 4, 8
+ENUM_SORTED, ENUM_FIRST_APPEARANCE = 0, 1
+REL_FE, REL_TE, REL_TF = 1, 2, 3
 ALL = 15
 MODE_PER_CLUSTER, MODE_BATCHED = 0, 1
 SERVE_LOOP, SERVE_BATCH, SERVE_SINGLE = 0, 1, 2
@@ -73,7 +75,8 @@ class ServeStats(ctypes.Structure):
 EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
            "gale_bulk_export", "gale_build_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
-           "gale_autotune", "gale_get_bins", "gale_get_bin_members", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
+           "gale_autotune", "gale_get_bins", "gale_get_bin_members", "gale_enumerate", "gale_get_enumeration",
+           "gale_boundary", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
 
 _lib = None
 
@@ -111,6 +114,9 @@ def load_library(build: bool = True):
     lib.gale_set_tuning.argtypes = [P, i32, i32]
     lib.gale_autotune.argtypes = [P, u32, i32, P, i32]
     lib.gale_get_bin_members.argtypes = [P, P]
+    lib.gale_enumerate.argtypes = [P, i32]
+    lib.gale_get_enumeration.argtypes = [P, P, P, P, P, P]
+    lib.gale_boundary.argtypes = [P, i32, P, i64, P]
     lib.gale_get_bins.argtypes = [P, P, i32, ctypes.POINTER(i32)]
     lib.gale_serve_configure.argtypes = [P, i32, i64, i32, i32]
     lib.gale_stream.argtypes = [P]
@@ -407,6 +413,29 @@ class Context:
         out = np.empty(max(self.K, 1), np.int32)
         _check(self._lib.gale_get_bin_members(self._h, _p(out)))
         return out[:self.K]
+
+    def enumerate(self, order: int = 0) -> dict:
+        """gale_enumerate + gale_get_enumeration: E (nE x 2), F (nF x 3),
+        I_E, I_F (K+1) in canonical ids; order ENUM_SORTED or
+        ENUM_FIRST_APPEARANCE."""
+        _check(self._lib.gale_enumerate(self._h, order))
+        counts = np.zeros(2, np.int64)
+        _check(self._lib.gale_get_enumeration(self._h, _p(counts), None, None, None, None))
+        E = np.empty((max(int(counts[0]), 1), 2), np.int32)
+        F = np.empty((max(int(counts[1]), 1), 3), np.int32)
+        I_E = np.empty(self.K + 1, np.int64)
+        I_F = np.empty(self.K + 1, np.int64)
+        _check(self._lib.gale_get_enumeration(self._h, None, _p(E), _p(I_E), _p(F), _p(I_F)))
+        return {"E": E[:counts[0]], "F": F[:counts[1]], "I_E": I_E, "I_F": I_F}
+
+    def boundary(self, relation: int, ids) -> np.ndarray:
+        """gale_boundary: REL_FE (3 per triangle), REL_TE (6 per tet) or
+        REL_TF (4 per tet)."""
+        width = {REL_FE: 3, REL_TE: 6, REL_TF: 4}[relation]
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        out = np.empty((max(ids.size, 1), width), np.int32)
+        _check(self._lib.gale_boundary(self._h, relation, _p(ids) if ids.size else None, ids.size, _p(out)))
+        return out[:ids.size]
 
     def set_tuning(self, threads: int = 0, ctas_per_sm: int = 0):
         _check(self._lib.gale_set_tuning(self._h, threads, ctas_per_sm))

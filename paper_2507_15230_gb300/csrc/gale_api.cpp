@@ -416,6 +416,7 @@ const char *gale_last_error(void) { return gale::t_error.c_str(); }
 void gale_destroy(gale_ctx *ctx) {
     if (!ctx) return;
     gale::serve_destroy(ctx);
+    gale::enumeration_destroy(ctx);
     if (ctx->device >= 0) {
         cudaSetDevice(ctx->device);
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);

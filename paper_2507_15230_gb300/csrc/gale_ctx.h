@@ -13,7 +13,8 @@
 
 namespace gale {
 
-struct Serve;  // serving loop state (gale_serve.cpp)
+struct Serve;        // serving loop state (gale_serve.cpp)
+struct Enumeration;  // edge / triangle lists (gale_enum.cpp)
 
 struct Bin {
     SmemPlan plan;
@@ -92,6 +93,7 @@ struct gale_ctx {
     std::mutex mu;  // guards builds and the bulk state
 
     gale::Serve *serve = nullptr;
+    gale::Enumeration *enm = nullptr;  // built by gale_enumerate
     int32_t serve_mode = -1;          // -1: default (loop when it fits)
     int64_t serve_idle_us = 0;
     int32_t serve_loop_ctas = 0;      // 0: as many as fit
@@ -100,3 +102,7 @@ struct gale_ctx {
     void *dalloc(size_t bytes);
     void dfree(void *p);
 };
+
+namespace gale {
+void enumeration_destroy(gale_ctx *ctx);  // gale_enum.cpp
+}  // namespace gale

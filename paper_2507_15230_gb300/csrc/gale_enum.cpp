@@ -1,0 +1,268 @@
+// Edge and triangle enumeration and boundary relations, on the host.
+//
+// Section 4.3 ("Initialization") enumerates the mesh's edges and triangles on
+// the CPU by iterating the tetrahedra of each segment and storing every two-
+// and three-vertex combination in indexed lists E and F, with interval
+// arrays I_E and I_F giving each segment's range.  An edge or triangle is
+// internal to the segment of its lowest vertex.  Section 4.4 computes a
+// boundary relation (FE, TE, TF) for one simplex by a few lookups in those
+// lists, limited to the owning segment's interval.
+//
+// Segment k's edges and triangles are found among the tetrahedra of its
+// working set (external, then internal, in canonical order): any simplex
+// whose lowest vertex is in k lies in a tetrahedron containing that vertex.
+// Two numberings within a segment: lexicographic in canonical ids, or the
+// order of first appearance over those tetrahedra with each tetrahedron's
+// combinations in combination order.  For lookups, each segment keeps a view
+// of its ids sorted by vertex tuple (binary search).
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gale_ctx.h"
+#include "gale_par.h"
+
+namespace gale {
+
+struct Enumeration {
+    int32_t order = -1;
+    std::vector<int32_t> E;          // [2 nE] (u, w), u < w
+    std::vector<int32_t> F;          // [3 nF] (a, b, c), a < b < c
+    std::vector<int64_t> I_E, I_F;   // [K+1]
+    std::vector<int32_t> e_by_key;   // [nE] per segment: ids in vertex-tuple order
+    std::vector<int32_t> f_by_key;   // [nF]
+};
+
+void enumeration_destroy(gale_ctx *ctx) {
+    delete ctx->enm;
+    ctx->enm = nullptr;
+}
+
+namespace {
+
+gale_status fail(gale_status s, const std::string &msg) {
+    set_error(msg);
+    return s;
+}
+
+struct EKey {
+    uint64_t key;  // u << 32 | w
+    int64_t pos;   // order of first appearance
+};
+struct FKey {
+    std::array<int32_t, 3> v;
+    int64_t pos;
+};
+
+// One segment's simplices, numbered in `order`.
+void segment_simplices(const HostMesh &hm, int32_t k, int32_t order, std::vector<uint64_t> &edges,
+                       std::vector<std::array<int32_t, 3>> &faces) {
+    const int32_t v0 = hm.I_V[k], v1 = hm.I_V[k + 1];
+    std::vector<EKey> ek;
+    std::vector<FKey> fk;
+    int64_t pos = 0;
+    auto visit = [&](int32_t t) {
+        const int32_t *r = hm.rows.data() + 4 * int64_t(t);
+        for (int i = 0; i < 4; ++i) {
+            if (r[i] < v0 || r[i] >= v1) continue;  // lowest vertex of the combination must be own
+            for (int j = i + 1; j < 4; ++j) {
+                ek.push_back({uint64_t(uint32_t(r[i])) << 32 | uint32_t(r[j]), pos++});
+                for (int l = j + 1; l < 4; ++l) fk.push_back({{r[i], r[j], r[l]}, pos++});
+            }
+        }
+    };
+    // combination order within a tetrahedron: (i, j) pairs and (i, j, l)
+    // triples by increasing indices; interleaving edges and triangles above
+    // keeps each kind's relative order
+    for (int64_t x = hm.ext_off[k]; x < hm.ext_off[k + 1]; ++x) visit(hm.ext[x]);
+    for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t) visit(t);
+    std::sort(ek.begin(), ek.end(),
+              [](const EKey &a, const EKey &b) { return a.key != b.key ? a.key < b.key : a.pos < b.pos; });
+    ek.erase(std::unique(ek.begin(), ek.end(), [](const EKey &a, const EKey &b) { return a.key == b.key; }),
+             ek.end());
+    std::sort(fk.begin(), fk.end(),
+              [](const FKey &a, const FKey &b) { return a.v != b.v ? a.v < b.v : a.pos < b.pos; });
+    fk.erase(std::unique(fk.begin(), fk.end(), [](const FKey &a, const FKey &b) { return a.v == b.v; }), fk.end());
+    if (order == GALE_ENUM_FIRST_APPEARANCE) {
+        std::sort(ek.begin(), ek.end(), [](const EKey &a, const EKey &b) { return a.pos < b.pos; });
+        std::sort(fk.begin(), fk.end(), [](const FKey &a, const FKey &b) { return a.pos < b.pos; });
+    }
+    edges.resize(ek.size());
+    for (size_t i = 0; i < ek.size(); ++i) edges[i] = ek[i].key;
+    faces.resize(fk.size());
+    for (size_t i = 0; i < fk.size(); ++i) faces[i] = fk[i].v;
+}
+
+// global id of edge (u, w), or -1
+int64_t edge_id(const HostMesh &hm, const Enumeration &en, int32_t u, int32_t w) {
+    if (u > w) std::swap(u, w);
+    if (u < 0 || u >= hm.nv) return -1;
+    const int32_t k = hm.cluster_of[u];
+    int64_t lo = en.I_E[k], hi = en.I_E[k + 1];  // search the segment's ids in tuple order
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t id = en.e_by_key[mid];
+        const int32_t a = en.E[2 * int64_t(id)], b = en.E[2 * int64_t(id) + 1];
+        if (a < u || (a == u && b < w)) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo >= en.I_E[k + 1]) return -1;
+    const int32_t id = en.e_by_key[lo];
+    return (en.E[2 * int64_t(id)] == u && en.E[2 * int64_t(id) + 1] == w) ? id : -1;
+}
+
+int64_t face_id(const HostMesh &hm, const Enumeration &en, std::array<int32_t, 3> f) {
+    std::sort(f.begin(), f.end());
+    if (f[0] < 0 || f[0] >= hm.nv) return -1;
+    const int32_t k = hm.cluster_of[f[0]];
+    int64_t lo = en.I_F[k], hi = en.I_F[k + 1];
+    auto at = [&](int64_t i) {
+        const int32_t id = en.f_by_key[i];
+        return std::array<int32_t, 3>{en.F[3 * int64_t(id)], en.F[3 * int64_t(id) + 1], en.F[3 * int64_t(id) + 2]};
+    };
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (at(mid) < f) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo >= en.I_F[k + 1] || at(lo) != f) return -1;
+    return en.f_by_key[lo];
+}
+
+}  // namespace
+}  // namespace gale
+
+extern "C" {
+
+gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
+    if (!ctx) return gale::fail(GALE_EINVAL, "NULL argument");
+    if (order != GALE_ENUM_SORTED && order != GALE_ENUM_FIRST_APPEARANCE)
+        return gale::fail(GALE_EINVAL, "unknown enumeration order");
+    const gale::HostMesh &hm = ctx->hm;
+    const int32_t K = hm.K;
+    if (hm.rows.size() != size_t(4) * size_t(hm.nt) || hm.cluster_of.size() != size_t(hm.nv))
+        return gale::fail(GALE_EINVAL, "the context holds no host rows");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    try {
+        std::vector<std::vector<uint64_t>> se(K);
+        std::vector<std::vector<std::array<int32_t, 3>>> sf(K);
+        gale::parallel_dynamic(K, gale::host_threads(0), 1,
+                               [&](int64_t k, int) { gale::segment_simplices(hm, int32_t(k), order, se[k], sf[k]); });
+        auto en = std::make_unique<gale::Enumeration>();
+        en->order = order;
+        en->I_E.assign(size_t(K) + 1, 0);
+        en->I_F.assign(size_t(K) + 1, 0);
+        for (int32_t k = 0; k < K; ++k) {
+            en->I_E[k + 1] = en->I_E[k] + int64_t(se[k].size());
+            en->I_F[k + 1] = en->I_F[k] + int64_t(sf[k].size());
+        }
+        if (en->I_E[K] > INT32_MAX || en->I_F[K] > INT32_MAX)
+            return gale::fail(GALE_EINVAL, "more than 2^31 edges or triangles");
+        en->E.resize(size_t(2) * size_t(en->I_E[K]));
+        en->F.resize(size_t(3) * size_t(en->I_F[K]));
+        en->e_by_key.resize(size_t(en->I_E[K]));
+        en->f_by_key.resize(size_t(en->I_F[K]));
+        gale::parallel_dynamic(K, gale::host_threads(0), 4, [&](int64_t k, int) {
+            const int64_t e0 = en->I_E[k], f0 = en->I_F[k];
+            const auto &ev = se[k];
+            const auto &fv = sf[k];
+            for (size_t i = 0; i < ev.size(); ++i) {
+                en->E[2 * (e0 + int64_t(i))] = int32_t(ev[i] >> 32);
+                en->E[2 * (e0 + int64_t(i)) + 1] = int32_t(ev[i] & 0xffffffffu);
+            }
+            for (size_t i = 0; i < fv.size(); ++i)
+                for (int c = 0; c < 3; ++c) en->F[3 * (f0 + int64_t(i)) + c] = fv[i][c];
+            // ids of the segment in tuple order (the identity for sorted numbering)
+            int32_t *eb = en->e_by_key.data() + e0;
+            for (size_t i = 0; i < ev.size(); ++i) eb[i] = int32_t(e0 + int64_t(i));
+            int32_t *fb = en->f_by_key.data() + f0;
+            for (size_t i = 0; i < fv.size(); ++i) fb[i] = int32_t(f0 + int64_t(i));
+            if (order == GALE_ENUM_FIRST_APPEARANCE) {
+                std::sort(eb, eb + ev.size(), [&](int32_t a, int32_t b) { return ev[a - e0] < ev[b - e0]; });
+                std::sort(fb, fb + fv.size(), [&](int32_t a, int32_t b) { return fv[a - f0] < fv[b - f0]; });
+            }
+        });
+        delete ctx->enm;
+        ctx->enm = en.release();
+    } catch (const std::bad_alloc &) {
+        return gale::fail(GALE_ENOMEM, "host allocation failed during enumeration");
+    }
+    return GALE_OK;
+}
+
+gale_status gale_get_enumeration(gale_ctx *ctx, int64_t *counts, int32_t *edges, int64_t *I_E, int32_t *faces,
+                                 int64_t *I_F) {
+    if (!ctx) return gale::fail(GALE_EINVAL, "NULL argument");
+    const gale::Enumeration *en = ctx->enm;
+    if (!en) return gale::fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
+    const int32_t K = ctx->hm.K;
+    if (counts) {
+        counts[0] = en->I_E[K];
+        counts[1] = en->I_F[K];
+    }
+    if (edges && !en->E.empty()) memcpy(edges, en->E.data(), en->E.size() * 4);
+    if (faces && !en->F.empty()) memcpy(faces, en->F.data(), en->F.size() * 4);
+    if (I_E) memcpy(I_E, en->I_E.data(), en->I_E.size() * 8);
+    if (I_F) memcpy(I_F, en->I_F.data(), en->I_F.size() * 8);
+    return GALE_OK;
+}
+
+gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, int64_t n, int32_t *out) {
+    if (!ctx || (n > 0 && (!ids || !out))) return gale::fail(GALE_EINVAL, "NULL argument");
+    const gale::Enumeration *en = ctx->enm;
+    if (!en) return gale::fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
+    const gale::HostMesh &hm = ctx->hm;
+    const int32_t K = hm.K;
+    int width, limit;
+    if (relation == GALE_REL_FE) {
+        width = 3;
+        limit = int32_t(std::min<int64_t>(en->I_F[K], INT32_MAX));
+    } else if (relation == GALE_REL_TE) {
+        width = 6;
+        limit = int32_t(std::min<int64_t>(hm.nt, INT32_MAX));
+    } else if (relation == GALE_REL_TF) {
+        width = 4;
+        limit = int32_t(std::min<int64_t>(hm.nt, INT32_MAX));
+    } else {
+        return gale::fail(GALE_EINVAL, "unknown boundary relation");
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (ids[i] < 0 || ids[i] >= limit) return gale::fail(GALE_EINVAL, "simplex id out of range");
+    std::atomic<int32_t> missing{0};
+    gale::parallel_for(n, gale::host_threads(0), [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; ++i) {
+            int32_t *o = out + i * width;
+            int64_t got[6];
+            if (relation == GALE_REL_FE) {
+                const int32_t *f = en->F.data() + 3 * ids[i];
+                got[0] = gale::edge_id(hm, *en, f[0], f[1]);
+                got[1] = gale::edge_id(hm, *en, f[0], f[2]);
+                got[2] = gale::edge_id(hm, *en, f[1], f[2]);
+            } else {
+                const int32_t *r = hm.rows.data() + 4 * ids[i];
+                if (relation == GALE_REL_TE) {
+                    int c = 0;
+                    for (int a = 0; a < 4; ++a)
+                        for (int d = a + 1; d < 4; ++d) got[c++] = gale::edge_id(hm, *en, r[a], r[d]);
+                } else {
+                    int c = 0;
+                    for (int a = 0; a < 4; ++a)
+                        for (int d = a + 1; d < 4; ++d)
+                            for (int g = d + 1; g < 4; ++g) got[c++] = gale::face_id(hm, *en, {r[a], r[d], r[g]});
+                }
+            }
+            for (int c = 0; c < width; ++c) {
+                if (got[c] < 0) missing++;
+                o[c] = int32_t(got[c]);
+            }
+        }
+    });
+    if (missing.load()) return gale::fail(GALE_EINVAL, "a simplex is missing from the enumeration");
+    return GALE_OK;
+}
+
+}  // extern "C"
