@@ -297,3 +297,37 @@ def boundary(canon: dict, enum: dict, relation: str, ids) -> list:
         else:
             raise ValueError("relation is 'FE', 'TE' or 'TF'")
     return out
+
+
+def coboundary(canon: dict, enum: dict) -> dict:
+    """Coboundary relations of the whole mesh in the ids of `enum` (the
+    relations Section 4.6 computes per segment on the GPU: VE, VF, EF, FT,
+    Section 5 / Table 1), each row sorted ascending:
+      VE[v] - edges containing vertex v;   VF[v] - triangles containing v;
+      EF[e] - triangles containing edge e; FT[f] - tets containing triangle f.
+    Lists of lists, rows in vertex / edge id / triangle id order."""
+    nv = int(canon["nv"])
+    rows = canon["rows"]
+    E, F = enum["E"], enum["F"]
+    fid = {f: i for i, f in enumerate(F)}
+    VE = [[] for _ in range(nv)]
+    for i, (u, w) in enumerate(E):
+        VE[u].append(i)
+        VE[w].append(i)
+    VF = [[] for _ in range(nv)]
+    EF = [[] for _ in range(len(E))]
+    eid = {e: i for i, e in enumerate(E)}
+    for i, (a, b, c) in enumerate(F):
+        for v in (a, b, c):
+            VF[v].append(i)
+        for e in ((a, b), (a, c), (b, c)):
+            EF[eid[e]].append(i)
+    FT = [[] for _ in range(len(F))]
+    for t in range(rows.shape[0]):
+        r = [int(x) for x in rows[t]]
+        for i in range(4):
+            for j in range(i + 1, 4):
+                for k in range(j + 1, 4):
+                    FT[fid[(r[i], r[j], r[k])]].append(t)
+    return {"VE": [sorted(x) for x in VE], "VF": [sorted(x) for x in VF], "EF": [sorted(x) for x in EF],
+            "FT": [sorted(x) for x in FT]}

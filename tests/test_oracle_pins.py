@@ -466,3 +466,40 @@ def test_enumeration_planted_mistakes_fail():
     assert enumeration_violations(canon, n, E, F, te_bad, FE)
     fe_bad = [[(i + 1) % len(E) for i in x] for x in FE]  # ids off by one
     assert enumeration_violations(canon, n, E, F, TE, fe_bad)
+
+
+@pytest.mark.parametrize("order", ["sorted", "first"])
+@pytest.mark.parametrize("n,K,seed", [(1, 1, 0), (2, 3, 1), (3, 7, 2)])
+def test_coboundary_closed_forms_and_transposes(order, n, K, seed):
+    """VE, VF, EF, FT: totals 2E, 3F, 3F, 2F - F_boundary (F_boundary =
+    12 n^2); interior vertices have 14 edges and 36 triangles; each is the
+    transpose of a boundary relation (EV, FV, FE, TF - the last two pinned by
+    the worked example); rows ascending."""
+    xyz, tv = gen.freudenthal_grid(n, permute=True, seed=seed + 80)
+    seg = np.random.default_rng(seed).integers(0, K, xyz.shape[0]).astype(np.int32)
+    canon = oracle.canonicalize(xyz.shape[0], tv, seg, K)
+    en = oracle.enumerate_simplices(canon, order)
+    cb = oracle.coboundary(canon, en)
+    E, F = en["E"], en["F"]
+    nE, nF, nT = len(E), len(F), canon["rows"].shape[0]
+    assert sum(map(len, cb["VE"])) == 2 * nE
+    assert sum(map(len, cb["VF"])) == 3 * nF
+    assert sum(map(len, cb["EF"])) == 3 * nF
+    assert sum(map(len, cb["FT"])) == 2 * nF - 12 * n * n
+    for key in cb:
+        assert all(r == sorted(set(r)) for r in cb[key])
+    # transposes
+    fe = oracle.boundary(canon, en, "FE", range(nF))
+    tf = oracle.boundary(canon, en, "TF", range(nT))
+    assert sorted((e, f) for f, row in enumerate(fe) for e in row) == \
+        sorted((e, f) for e, row in enumerate(cb["EF"]) for f in row)
+    assert sorted((f, t) for t, row in enumerate(tf) for f in row) == \
+        sorted((f, t) for f, row in enumerate(cb["FT"]) for t in row)
+    assert sorted((v, i) for i, e in enumerate(E) for v in e) == \
+        sorted((v, i) for v, row in enumerate(cb["VE"]) for i in row)
+    assert sorted((v, i) for i, f in enumerate(F) for v in f) == \
+        sorted((v, i) for v, row in enumerate(cb["VF"]) for i in row)
+    if n >= 3:  # an interior vertex of the grid: the lattice point nearest the centre
+        mid = int(np.argmin(np.abs(xyz - xyz.mean(axis=0)).sum(axis=1)))
+        v = int(canon["cid"][mid])
+        assert len(cb["VE"][v]) == 14 and len(cb["VF"][v]) == 36
