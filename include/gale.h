@@ -350,6 +350,30 @@ gale_status gale_get_enumeration(gale_ctx *ctx, int64_t *counts, int32_t *edges,
 enum { GALE_REL_FE = 1, GALE_REL_TE = 2, GALE_REL_TF = 3 };
 gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, int64_t n, int32_t *out);
 
+/*
+ * Coboundary relations VE, VF, EF and FT of the whole mesh, in the ids of
+ * the enumeration (gale_enumerate first), built on the GPU (Section 4.4:
+ * coboundary relations are delegated to the GPU; Section 5 evaluates VE, VF,
+ * EF and FT).  Rows ascending:
+ *   GALE_CB_VE  rows = vertices (canonical ids): the edges containing v
+ *   GALE_CB_VF  rows = vertices: the triangles containing v
+ *   GALE_CB_EF  rows = edges (enumeration ids): the triangles containing e
+ *   GALE_CB_FT  rows = triangles: the canonical tets containing f
+ * The pass first builds VT and VV of every cluster (the bulk arrays are
+ * replaced).  out receives, per relation in the order VE, VF, EF, FT, the
+ * row count, the value count and DEVICE pointers to int32 offsets[rows+1]
+ * and values, library-owned and valid until the next call or gale_destroy.
+ * EINVAL if VT and VV are not in the precondition mask, ENOTFOUND before
+ * gale_enumerate, EDEVICE if a lookup failed. */
+enum { GALE_CB_VE = 1, GALE_CB_VF = 2, GALE_CB_EF = 4, GALE_CB_FT = 8 };
+typedef struct {
+    int64_t rows[4];
+    int64_t len[4];
+    const int32_t *off[4];
+    const int32_t *val[4];
+} gale_coboundary;
+gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale_coboundary *out);
+
 /* Tuning: threads per block of the producer kernels (a multiple of 32 in
  * [64, 1024]; 0 = one thread per own vertex of the largest cluster of each
  * size bin) and CTAs per SM of the persistent grid (0 = as many as fit). */

@@ -20,6 +20,7 @@ from . import _build
 
 VT, VV, ET, TT = 1, 2, 4, 8
 ENUM_SORTED, ENUM_FIRST_APPEARANCE = 0, 1
+CB_VE, CB_VF, CB_EF, CB_FT = 1, 2, 4, 8
 REL_FE, REL_TE, REL_TF = 1, 2, 3
 ALL = 15
 MODE_PER_CLUSTER, MODE_BATCHED = 0, 1
@@ -36,6 +37,11 @@ class GaleError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class Coboundary(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64 * 4), ("len", ctypes.c_int64 * 4), ("off", ctypes.c_void_p * 4),
+                ("val", ctypes.c_void_p * 4)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -76,7 +82,7 @@ EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc
            "gale_bulk_export", "gale_build_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
            "gale_autotune", "gale_get_bins", "gale_get_bin_members", "gale_enumerate", "gale_get_enumeration",
-           "gale_boundary", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
+           "gale_boundary", "gale_build_coboundary", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
 
 _lib = None
 
@@ -117,6 +123,7 @@ def load_library(build: bool = True):
     lib.gale_enumerate.argtypes = [P, i32]
     lib.gale_get_enumeration.argtypes = [P, P, P, P, P, P]
     lib.gale_boundary.argtypes = [P, i32, P, i64, P]
+    lib.gale_build_coboundary.argtypes = [P, u32, ctypes.POINTER(Coboundary)]
     lib.gale_get_bins.argtypes = [P, P, i32, ctypes.POINTER(i32)]
     lib.gale_serve_configure.argtypes = [P, i32, i64, i32, i32]
     lib.gale_stream.argtypes = [P]
@@ -436,6 +443,20 @@ class Context:
         out = np.empty((max(ids.size, 1), width), np.int32)
         _check(self._lib.gale_boundary(self._h, relation, _p(ids) if ids.size else None, ids.size, _p(out)))
         return out[:ids.size]
+
+    def coboundary(self, which: int = CB_VE | CB_VF | CB_EF | CB_FT) -> dict:
+        """gale_build_coboundary: {"VE"|"VF"|"EF"|"FT": (offsets, values)} as
+        host numpy arrays (the device arrays copied through torch)."""
+        c = Coboundary()
+        _check(self._lib.gale_build_coboundary(self._h, which, ctypes.byref(c)))
+        out = {}
+        for i, name in enumerate(("VE", "VF", "EF", "FT")):
+            if which & (1 << i):
+                n, ln = int(c.rows[i]), int(c.len[i])
+                off = device_tensor(c.off[i], n + 1).cpu().numpy()
+                val = device_tensor(c.val[i], ln).cpu().numpy() if ln else np.empty(0, np.int32)
+                out[name] = (off, val)
+        return out
 
     def set_tuning(self, threads: int = 0, ctas_per_sm: int = 0):
         _check(self._lib.gale_set_tuning(self._h, threads, ctas_per_sm))

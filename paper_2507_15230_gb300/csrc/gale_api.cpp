@@ -417,6 +417,7 @@ void gale_destroy(gale_ctx *ctx) {
     if (!ctx) return;
     gale::serve_destroy(ctx);
     gale::enumeration_destroy(ctx);
+    gale::cobound_destroy(ctx);
     if (ctx->device >= 0) {
         cudaSetDevice(ctx->device);
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);

@@ -15,6 +15,7 @@ namespace gale {
 
 struct Serve;        // serving loop state (gale_serve.cpp)
 struct Enumeration;  // edge / triangle lists (gale_enum.cpp)
+struct Cobound;      // coboundary pass device state (gale_cobound.cu)
 
 struct Bin {
     SmemPlan plan;
@@ -94,6 +95,7 @@ struct gale_ctx {
 
     gale::Serve *serve = nullptr;
     gale::Enumeration *enm = nullptr;  // built by gale_enumerate
+    gale::Cobound *cb = nullptr;       // gale_build_coboundary
     int32_t serve_mode = -1;          // -1: default (loop when it fits)
     int64_t serve_idle_us = 0;
     int32_t serve_loop_ctas = 0;      // 0: as many as fit
@@ -105,4 +107,5 @@ struct gale_ctx {
 
 namespace gale {
 void enumeration_destroy(gale_ctx *ctx);  // gale_enum.cpp
+void cobound_destroy(gale_ctx *ctx);      // gale_cobound.cu
 }  // namespace gale

@@ -42,6 +42,19 @@ void enumeration_destroy(gale_ctx *ctx) {
     ctx->enm = nullptr;
 }
 
+bool enumeration_arrays(gale_ctx *ctx, const std::vector<int32_t> **E, const std::vector<int32_t> **F,
+                        const std::vector<int32_t> **ebk, const std::vector<int32_t> **fbk,
+                        const std::vector<int64_t> **IE, const std::vector<int64_t> **IF) {
+    if (!ctx->enm) return false;
+    *E = &ctx->enm->E;
+    *F = &ctx->enm->F;
+    *ebk = &ctx->enm->e_by_key;
+    *fbk = &ctx->enm->f_by_key;
+    *IE = &ctx->enm->I_E;
+    *IF = &ctx->enm->I_F;
+    return true;
+}
+
 namespace {
 
 gale_status fail(gale_status s, const std::string &msg) {

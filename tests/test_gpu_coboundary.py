@@ -1,0 +1,74 @@
+"""Coboundary relations VE, VF, EF, FT on the GPU (gale_build_coboundary),
+in the ids of the edge / triangle enumeration, against the oracle, bit for
+bit: the small grid under both numberings, random partitions, a 400-tet
+star and a Delaunay mesh."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_2507_15230_gb300 as gale
+
+pytestmark = pytest.mark.gpu
+
+ORDERS = [(gale.ENUM_SORTED, "sorted"), (gale.ENUM_FIRST_APPEARANCE, "first")]
+
+
+def check(m, order, oname, which=gale.CB_VE | gale.CB_VF | gale.CB_EF | gale.CB_FT):
+    canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
+    en = oracle.enumerate_simplices(canon, oname)
+    want = oracle.coboundary(canon, en)
+    with gale.Context.load(m, device=0) as ctx:
+        ctx.enumerate(order)
+        got = ctx.coboundary(which)
+        for i, name in enumerate(("VE", "VF", "EF", "FT")):
+            if not which & (1 << i):
+                assert name not in got
+                continue
+            off, val = got[name]
+            rows = want[name]
+            assert off.size == len(rows) + 1, name
+            assert off.tolist() == np.concatenate([[0], np.cumsum([len(r) for r in rows])]).tolist(), name
+            assert val.tolist() == [x for r in rows for x in r], name
+
+
+@pytest.mark.parametrize("order,oname", ORDERS)
+def test_small_grid(order, oname):
+    check(gen.small_grid(with_field=False), order, oname)
+
+
+@pytest.mark.parametrize("n,K,seed", [(3, 1, 0), (4, 7, 1), (5, 30, 2)])
+def test_random_partitions(n, K, seed):
+    xyz, tv = gen.freudenthal_grid(n, permute=True, seed=seed + 90)
+    seg = np.random.default_rng(seed).integers(0, K, xyz.shape[0]).astype(np.int32)
+    for order, oname in ORDERS:
+        check(gen.Mesh(xyz, tv, seg, K), order, oname)
+
+
+def test_high_degree_star_and_subsets():
+    from test_gpu_parity import fan_mesh
+    xyz, tv = fan_mesh()
+    seg = np.random.default_rng(4).integers(0, 3, xyz.shape[0]).astype(np.int32)
+    m = gen.Mesh(xyz, tv, seg, 3)
+    check(m, gale.ENUM_FIRST_APPEARANCE, "first")
+    check(m, gale.ENUM_SORTED, "sorted", which=gale.CB_VF | gale.CB_FT)
+
+
+def test_delaunay():
+    check(gen.delaunay_mesh(3000, seed=41, kd_cap=256, with_field=False), gale.ENUM_SORTED, "sorted")
+
+
+def test_errors():
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0) as ctx:
+        with pytest.raises(gale.GaleError) as ei:
+            ctx.coboundary()
+        assert gale.STATUS[ei.value.status] == "ENOTFOUND"
+        ctx.enumerate(gale.ENUM_SORTED)
+        with pytest.raises(gale.GaleError):
+            ctx.coboundary(16)
+    with gale.Context.load(m, device=0, precondition_mask=gale.ET | gale.TT) as ctx:
+        ctx.enumerate(gale.ENUM_SORTED)
+        with pytest.raises(gale.GaleError) as ei:
+            ctx.coboundary()
+        assert gale.STATUS[ei.value.status] == "EINVAL"
