@@ -32,6 +32,7 @@ scaling, no data-path collective; only the timing barrier).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -202,6 +203,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default block sizes")
     ap.add_argument("--mixed", action="store_true", help="also run the 24-mesh mixed serving leg (minutes)")
+    ap.add_argument("--coboundary", action="store_true", help="also time VE, VF, EF, FT")
+    ap.add_argument("--coboundary-grid", type=int, default=128)
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: each rank builds a balanced shard of the clusters (strong scaling) "
                          "instead of a whole replica")
@@ -347,6 +350,9 @@ def main():
     mixed = None
     if rank == 0 and args.mixed:
         mixed = mixed_leg(args, gale)
+    cobound = None
+    if rank == 0 and args.coboundary:
+        cobound = coboundary_leg(args, gale, gen)
 
     traffic = None
     tp = os.path.join(ROOT, "profiles", "build_kernel_traffic.json")
@@ -384,6 +390,7 @@ def main():
             "per_cluster": per_cluster,
             "serving": serving,
             "mixed_serving": mixed,
+            "coboundary": cobound,
             "shard": shard_info,
             "load_seconds": {"host": info.load_host_seconds, "device": info.load_device_seconds},
             "bins": ctx.bins(),
@@ -553,6 +560,48 @@ def mixed_leg(args, gale):
 def torch_sm_count() -> int:
     import torch
     return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def coboundary_leg(args, gale, gen):
+    """VE, VF, EF, FT (gale_build_coboundary) on a grid of the same recipe,
+    in sorted enumeration ids: device time of the whole pass (the VT + VV
+    build it starts with, the count and fill kernels), output bytes over that
+    time against the HBM copy peak, and the oracle timed on a 12^3 sample."""
+    import torch
+    n = args.coboundary_grid
+    mesh = gen.freudenthal_mesh(n, 512, seed=3, field_seed=4, jitter=0.3, with_field=False)
+    with gale.Context.load(mesh, device=0) as c:
+        t0 = time.perf_counter()
+        c.enumerate(gale.ENUM_SORTED)
+        enum_s = time.perf_counter() - t0
+        cb = gale.Coboundary()
+        lib = c._lib
+        stream = torch.cuda.ExternalStream(c.stream_handle)
+        gale._check(lib.gale_build_coboundary(c._h, 15, ctypes.byref(cb)))  # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = 3
+        a.record(stream)
+        for _ in range(steps):
+            gale._check(lib.gale_build_coboundary(c._h, 15, ctypes.byref(cb)))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out_bytes = int(sum(4 * (cb.rows[i] + 1 + cb.len[i]) for i in range(4)))
+    peak, _ = load_peaks()
+    # the oracle on a small sample of the same recipe
+    import oracle
+    small = gen.freudenthal_mesh(12, 512, seed=3, field_seed=4, jitter=0.3, with_field=False)
+    t0 = time.perf_counter()
+    canon = oracle.canonicalize(small.nv, small.tv, small.seg, small.nclusters)
+    oracle.coboundary(canon, oracle.enumerate_simplices(canon, "sorted"))
+    osec = time.perf_counter() - t0
+    return {"workload": f"grid{n}^3-jitter0.3-kd512: {mesh.nt} tets; VE+VF+EF+FT in sorted enumeration ids",
+            "ms": ms, "tets_per_s": mesh.nt / (ms / 1e3), "host_enumeration_s": enum_s,
+            "roofline": {"bound": "hbm", "achieved": out_bytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": out_bytes / (ms / 1e3) / 1e9 / peak,
+                         "algorithmic_bytes": out_bytes, "note": "output bytes only"},
+            "oracle": {"sample": f"grid12^3 ({small.nt} tets), enumeration + coboundary, Python, single thread",
+                       "tets_per_s": small.nt / osec}}
 
 
 def gale_kernel_sha() -> str:
