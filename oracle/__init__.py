@@ -17,6 +17,12 @@ passage it follows).  This module compiles it with gcc and wraps it:
                               face halo of one cluster
 * ``cluster_view``          - slices a global result into one cluster's
                               self-contained CSR (offsets starting at 0)
+* ``enumerate_simplices``   - edge / triangle enumeration E, F, I_E, I_F
+                              (Section 4.3, "Initialization"), plain Python
+* ``boundary``              - FE, TE, TF by lookup (Section 4.4)
+* ``coboundary``            - VE, VF, EF, FT of the whole mesh (Table 1)
+* ``lower_star_gradient``   - the discrete gradient of a vertex field
+                              (Section 5.1, DiscreteGradient), plain Python
 """
 from __future__ import annotations
 
@@ -331,3 +337,121 @@ def coboundary(canon: dict, enum: dict) -> dict:
                     FT[fid[(r[i], r[j], r[k])]].append(t)
     return {"VE": [sorted(x) for x in VE], "VF": [sorted(x) for x in VF], "EF": [sorted(x) for x in EF],
             "FT": [sorted(x) for x in FT]}
+
+
+# ---------------------------------------------------------------------------
+# Discrete gradient (Section 5.1, the DiscreteGradient workload: a Forman
+# discrete vector field of a vertex scalar field, built lower star by lower
+# star).  Reading: the lower star of v is every simplex that contains v and
+# whose other vertices all lie below v, "below" meaning a smaller field value
+# with ties broken by the smaller input id.  Each lower star is processed on
+# its own by the lower-star construction of Robins, Wood and Sheppard (2011,
+# "ProcessLowerStars"):
+#   * an empty lower star makes v critical;
+#   * otherwise v is paired with the lower-star edge of smallest value
+#     sequence; every other edge waits in the "zero" queue;
+#   * a simplex whose faces inside the lower star are all classified but one
+#     enters the "one" queue; popping it pairs it with that face (or, if none
+#     is left, moves it to the zero queue);
+#   * when the one queue is empty the smallest entry of the zero queue that
+#     is still unclassified becomes critical.
+# The value sequence of a simplex of the lower star of v is the list of its
+# other vertices' (value, input id) keys in decreasing order; sequences
+# compare lexicographically, a proper prefix first.  "Faces inside the lower
+# star" are the faces that contain v, not counting v itself.
+# Plain Python on vertex tuples; meant for small meshes.
+# ---------------------------------------------------------------------------
+
+def lower_star_gradient(canon: dict, field, inid, vertices=None) -> dict:
+    """{"pairs": [(face, coface), ...], "critical": [simplex, ...]}, every
+    simplex a tuple of canonical vertex ids in increasing order.
+    field, inid: per canonical vertex.  vertices: the lower stars to process
+    (default all; lower stars are disjoint, so any subset is exact)."""
+    import heapq
+    from itertools import combinations
+
+    rows = canon["rows"]
+    nv = int(canon["nv"])
+    f = [float(x) for x in np.asarray(field, dtype=np.float64)]
+    ids = [int(x) for x in np.asarray(inid)]
+
+    def key(x):
+        return (f[x], ids[x])
+
+    todo = range(nv) if vertices is None else [int(v) for v in vertices]
+    want = None if vertices is None else set(todo)
+    star = {v: [] for v in todo}
+    for t in range(rows.shape[0]):
+        for x in rows[t]:
+            if want is None or int(x) in want:
+                star[int(x)].append(t)
+
+    pairs, critical = [], []
+    for v in todo:
+        kv = key(v)
+        low = set()
+        for t in star[v]:
+            lower = [int(x) for x in rows[t] if int(x) != v and key(int(x)) < kv]
+            for r in range(1, len(lower) + 1):
+                for c in combinations(lower, r):
+                    low.add(tuple(sorted((v,) + c)))
+        if not low:
+            critical.append((v,))
+            continue
+
+        def seq(s):
+            return tuple(sorted((key(x) for x in s if x != v), reverse=True))
+
+        # faces of s inside the lower star: drop one vertex other than v
+        inner = {s: [tuple(x for x in s if x != w) for w in s if w != v] for s in low}
+        inner = {s: [g for g in fs if len(g) > 1] for s, fs in inner.items()}
+        cof = {s: [] for s in low}
+        for s, fs in inner.items():
+            for g in fs:
+                cof[g].append(s)
+        done = set()
+
+        def open_faces(s):
+            return [g for g in inner[s] if g not in done]
+
+        zero, one, in_one = [], [], set()
+
+        def offer_cofaces(s):
+            for c in cof[s]:
+                if c not in done and c not in in_one and len(open_faces(c)) == 1:
+                    heapq.heappush(one, (seq(c), c))
+                    in_one.add(c)
+
+        edges = [s for s in low if len(s) == 2]
+        first = min(edges, key=seq)
+        pairs.append(((v,), first))
+        done.add(first)
+        for e in edges:
+            if e != first:
+                heapq.heappush(zero, (seq(e), e))
+        offer_cofaces(first)
+        while one or zero:
+            while one:
+                _, a = heapq.heappop(one)
+                in_one.discard(a)
+                if a in done:
+                    continue
+                left = open_faces(a)
+                if not left:
+                    heapq.heappush(zero, (seq(a), a))
+                    continue
+                g = left[0]
+                pairs.append((g, a))
+                done.add(g)
+                done.add(a)
+                offer_cofaces(a)
+                offer_cofaces(g)
+            while zero:
+                _, g = heapq.heappop(zero)
+                if g in done:
+                    continue
+                critical.append(g)
+                done.add(g)
+                offer_cofaces(g)
+                break
+    return {"pairs": pairs, "critical": critical}
