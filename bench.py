@@ -205,6 +205,10 @@ def main():
     ap.add_argument("--mixed", action="store_true", help="also run the 24-mesh mixed serving leg (minutes)")
     ap.add_argument("--coboundary", action="store_true", help="also time VE, VF, EF, FT")
     ap.add_argument("--coboundary-grid", type=int, default=128)
+    ap.add_argument("--discrete-gradient", action="store_true",
+                    help="also time the discrete-gradient consumer and the relations it reads")
+    ap.add_argument("--dg-grid", type=int, default=128)
+    ap.add_argument("--dg-threads", type=int, default=0, help="consumer threads (0: the host's cores)")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: each rank builds a balanced shard of the clusters (strong scaling) "
                          "instead of a whole replica")
@@ -353,6 +357,9 @@ def main():
     cobound = None
     if rank == 0 and args.coboundary:
         cobound = coboundary_leg(args, gale, gen)
+    dgrad = None
+    if rank == 0 and args.discrete_gradient:
+        dgrad = gradient_leg(args, gale, gen)
 
     traffic = None
     tp = os.path.join(ROOT, "profiles", "build_kernel_traffic.json")
@@ -391,6 +398,7 @@ def main():
             "serving": serving,
             "mixed_serving": mixed,
             "coboundary": cobound,
+            "discrete_gradient": dgrad,
             "shard": shard_info,
             "load_seconds": {"host": info.load_host_seconds, "device": info.load_device_seconds},
             "bins": ctx.bins(),
@@ -602,6 +610,64 @@ def coboundary_leg(args, gale, gen):
                          "algorithmic_bytes": out_bytes, "note": "output bytes only"},
             "oracle": {"sample": f"grid12^3 ({small.nt} tets), enumeration + coboundary, Python, single thread",
                        "tets_per_s": small.nt / osec}}
+
+
+def gradient_leg(args, gale, gen):
+    """The discrete gradient of a Gaussian-mixture field on a grid of the
+    same recipe (Section 5.1, DiscreteGradient): wall time of each step -
+    the host enumeration, VE + VF on the GPU (with the VT + VV build the pass
+    starts with) and their copy to the host, the VT export, the host FE / TF
+    lookups, and the consumer threads - and the oracle on an 8^3 sample."""
+    import torch
+    import consumers
+    n = args.dg_grid
+    threads = args.dg_threads or os.cpu_count() or 1
+    mesh = gen.freudenthal_mesh(n, 512, seed=3, field_seed=4, jitter=0.3, ngauss=16)
+    out = {"workload": f"grid{n}^3-jitter0.3-kd512 + 16-Gaussian field: {mesh.nv} vertices, {mesh.nt} tets",
+           "threads": threads}
+    with gale.Context.load(mesh, device=0) as c:
+        vp, _ = c.permutations()
+        f_c, inid = consumers.canonical_inputs(mesh.field, vp)
+        consumers._load()  # builds / loads the consumer library outside the timed steps
+        t = {}
+        t0 = time.perf_counter()
+        c.enumerate(gale.ENUM_SORTED)
+        t["enumeration_host_s"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        cb = c.coboundary(gale.CB_VE | gale.CB_VF)
+        torch.cuda.synchronize()
+        t["ve_vf_gpu_and_copy_s"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        I_V, _, _ = c.intervals()
+        b = c.export(gale.VT)
+        vt = consumers.csr_from_bulk(b["vt_off"], b["vt_val"], I_V)
+        t["vt_export_s"] = time.perf_counter() - t0
+        en = c.enumeration()
+        rows = c.rows()
+        t0 = time.perf_counter()
+        fe = c.boundary(gale.REL_FE, np.arange(en["F"].shape[0], dtype=np.int64))
+        tf = c.boundary(gale.REL_TF, np.arange(rows.shape[0], dtype=np.int64))
+        t["fe_tf_host_s"] = time.perf_counter() - t0
+        g, wall = consumers.discrete_gradient_arrays(f_c, inid, cb["VE"], cb["VF"], vt, en["E"], en["F"], rows, fe,
+                                                     tf, nthreads=threads)
+        t["consumer_s"] = wall
+    crit = [int((g["v_up"] < 0).sum()), int(((g["e_down"] < 0) & (g["e_up"] < 0)).sum()),
+            int(((g["f_down"] < 0) & (g["f_up"] < 0)).sum()), int((g["t_down"] < 0).sum())]
+    out.update(t)
+    out["total_s"] = sum(t.values())
+    out["consumer_vertices_per_s"] = mesh.nv / t["consumer_s"]
+    out["critical_cells"] = crit
+    out["euler"] = crit[0] - crit[1] + crit[2] - crit[3]
+    import oracle
+    small = gen.freudenthal_mesh(8, 512, seed=3, field_seed=4, jitter=0.3, ngauss=16)
+    canon = oracle.canonicalize(small.nv, small.tv, small.seg, small.nclusters)
+    vp = np.asarray(canon["vperm"])
+    t0 = time.perf_counter()
+    oracle.lower_star_gradient(canon, np.asarray(small.field, np.float32)[vp].astype(np.float64), vp)
+    osec = time.perf_counter() - t0
+    out["oracle"] = {"sample": f"grid8^3 ({small.nv} vertices), Python, single thread",
+                     "vertices_per_s": small.nv / osec}
+    return out
 
 
 def gale_kernel_sha() -> str:

@@ -251,4 +251,304 @@ int gale_open_loop(gale_ctx *const *ctxs, int32_t nctx, const int32_t *mi, const
     return 0;
 }
 
+
+/*
+ * Discrete gradient (Section 5.1, DiscreteGradient): a Forman discrete
+ * vector field of the vertex field f, built lower star by lower star.  The
+ * lower star of v holds every simplex that contains v and whose other
+ * vertices are all below v; it is processed alone (the construction of
+ * Robins, Wood and Sheppard, 2011):
+ *   - an empty lower star makes v critical (a minimum);
+ *   - otherwise v is paired with the lower-star edge of smallest value
+ *     sequence and every other edge waits in the "zero" queue;
+ *   - a simplex all of whose faces inside the lower star but one are
+ *     classified enters the "one" queue; popping it pairs it with that face,
+ *     or moves it to the zero queue if none is left;
+ *   - when the one queue is empty, the smallest still-open entry of the zero
+ *     queue becomes critical.
+ * A simplex's value sequence lists its vertices other than v from highest to
+ * lowest; sequences compare lexicographically, a proper prefix first.  The
+ * faces inside the lower star are those that contain v, v itself excluded.
+ *
+ * The relations read are the ones the paper lists for this algorithm: the
+ * coboundary rows VE(v), VF(v), VT(v) (GPU-built), the vertex lists EV, FV,
+ * TV, and the boundary rows FE, TF (Section 4.4).
+ *   f, inid          per canonical vertex: value and input id
+ *   [v_begin, v_end) vertices whose lower stars are processed
+ *   ve/vf/vt_off,val CSR rows indexed by canonical vertex id (int64 offsets)
+ *   ev int32[2 nE], fv int32[3 nF], tv int32[4 nT]  ascending vertex ids
+ *   fe int32[3 nF]   edges (a,b), (a,c), (b,c) of triangle (a,b,c)
+ *   tf int32[4 nT]   triangles (a,b,c), (a,b,d), (a,c,d), (b,c,d)
+ * Output, one entry per simplex, -1 where unpaired (a simplex is critical
+ * when both of its entries are -1); every simplex whose highest vertex is in
+ * the range gets both of its entries written:
+ *   v_up[v]  edge paired with v        e_down[e]  vertex paired with e
+ *   e_up[e]  triangle paired with e    f_down[f]  edge paired with f
+ *   f_up[f]  tet paired with f         t_down[t]  triangle paired with t
+ * VE and VF rows must list ids in ascending order (as the coboundary pass
+ * writes them).  Returns 0, or -1 if the relations are inconsistent (a row
+ * whose simplex lacks v, or a face of a lower-star simplex missing from the
+ * lower star).
+ */
+namespace {
+
+struct LowerStar {
+    // local simplices: edges [0, ne), triangles [ne, ne + nf), tets after
+    std::vector<int32_t> gid, dim, seq, nseq, open, state, in_one, face, cof_off, cof;
+    std::vector<int32_t> heap_one, heap_zero;
+};
+
+struct DgArgs {
+    const float *f;
+    const int32_t *inid;
+    const int64_t *ve_off, *vf_off, *vt_off;
+    const int32_t *ve_val, *vf_val, *vt_val, *ev, *fv, *tv, *fe, *tf;
+    int32_t *v_up, *e_down, *e_up, *f_down, *f_up, *t_down;
+};
+
+// 0 ok, -1 inconsistent relations
+int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
+    const float *f = a.f;
+    const int32_t *inid = a.inid;
+    auto lt = [&](int32_t x, int32_t y) { return below(f, inid, x, y); };
+    L.gid.clear();
+    L.dim.clear();
+    L.seq.clear();
+    L.nseq.clear();
+    // lower-star edges, triangles and tets with their other vertices, highest first
+    auto add = [&](int32_t g, int d, int32_t *o, int n) {
+        std::sort(o, o + n, [&](int32_t x, int32_t y) { return lt(y, x); });
+        L.gid.push_back(g);
+        L.dim.push_back(d);
+        L.nseq.push_back(n);
+        for (int i = 0; i < 3; ++i) L.seq.push_back(i < n ? o[i] : -1);
+    };
+    for (int64_t q = a.ve_off[v]; q < a.ve_off[v + 1]; ++q) {
+        const int32_t e = a.ve_val[q];
+        const int32_t x = a.ev[2 * int64_t(e)], y = a.ev[2 * int64_t(e) + 1];
+        if (x != v && y != v) return -1;
+        int32_t o[1] = {x == v ? y : x};
+        if (lt(o[0], v)) add(e, 1, o, 1);
+    }
+    const int32_t ne = int32_t(L.gid.size());
+    for (int64_t q = a.vf_off[v]; q < a.vf_off[v + 1]; ++q) {
+        const int32_t t = a.vf_val[q];
+        int32_t o[3], n = 0;
+        bool ok = true;
+        for (int i = 0; i < 3; ++i) {
+            const int32_t x = a.fv[3 * int64_t(t) + i];
+            if (x == v) continue;
+            ok = ok && lt(x, v);
+            o[n++] = x;
+        }
+        if (n != 2) return -1;
+        if (ok) add(t, 2, o, 2);
+    }
+    const int32_t nf = int32_t(L.gid.size()) - ne;
+    for (int64_t q = a.vt_off[v]; q < a.vt_off[v + 1]; ++q) {
+        const int32_t t = a.vt_val[q];
+        int32_t o[4], n = 0;
+        bool ok = true;
+        for (int i = 0; i < 4; ++i) {
+            const int32_t x = a.tv[4 * int64_t(t) + i];
+            if (x == v) continue;
+            ok = ok && lt(x, v);
+            o[n++] = x;
+        }
+        if (n != 3) return -1;
+        if (ok) add(t, 3, o, 3);
+    }
+    const int32_t ns = int32_t(L.gid.size());
+    if (ne == 0) {
+        a.v_up[v] = -1;
+        return ns == 0 ? 0 : -1;
+    }
+    // faces inside the lower star: a triangle's two edges through v (FE),
+    // a tet's three triangles through v (TF); local ids by binary search
+    // over the edges / triangles, which the CSR rows list in ascending id
+    L.face.assign(size_t(ns) * 3, -1);
+    auto local = [&](int32_t lo, int32_t hi, int32_t g) -> int32_t {
+        const int32_t *b = L.gid.data() + lo, *e = L.gid.data() + hi;
+        const int32_t *p = std::lower_bound(b, e, g);
+        return (p != e && *p == g) ? int32_t(p - L.gid.data()) : -1;
+    };
+    for (int32_t s = ne; s < ns; ++s) {
+        const bool tri = L.dim[s] == 2;
+        const int32_t w = tri ? 3 : 4;
+        const int32_t *vs = (tri ? a.fv : a.tv) + int64_t(w) * L.gid[s];
+        const int32_t *fs = (tri ? a.fe : a.tf) + int64_t(w) * L.gid[s];
+        int pos = 0;
+        while (pos < w && vs[pos] != v) ++pos;
+        if (pos == w) return -1;
+        const int skip = (w - 1) - pos;  // the face opposite v
+        int c = 0;
+        for (int i = 0; i < w; ++i) {
+            if (i == skip) continue;
+            const int32_t l = tri ? local(0, ne, fs[i]) : local(ne, ne + nf, fs[i]);
+            if (l < 0) return -1;
+            L.face[3 * size_t(s) + c++] = l;
+        }
+    }
+    // cofaces inside the lower star (CSR over local ids)
+    L.cof_off.assign(size_t(ns) + 1, 0);
+    for (int32_t s = ne; s < ns; ++s)
+        for (int i = 0; i < L.dim[s]; ++i) L.cof_off[L.face[3 * size_t(s) + i] + 1]++;
+    for (int32_t s = 0; s < ns; ++s) L.cof_off[s + 1] += L.cof_off[s];
+    L.cof.assign(size_t(L.cof_off[ns]), 0);
+    {
+        std::vector<int32_t> fill(L.cof_off.begin(), L.cof_off.end() - 1);
+        for (int32_t s = ne; s < ns; ++s)
+            for (int i = 0; i < L.dim[s]; ++i) L.cof[fill[L.face[3 * size_t(s) + i]]++] = s;
+    }
+    // open = faces inside the lower star not yet classified
+    L.open.assign(size_t(ns), 0);
+    for (int32_t s = ne; s < ns; ++s) L.open[s] = L.dim[s];
+    L.state.assign(size_t(ns), 0);
+    L.in_one.assign(size_t(ns), 0);
+    // heap order: std heaps keep the largest on top, so "greater" = later
+    auto later = [&](int32_t x, int32_t y) {
+        const int32_t *sx = &L.seq[3 * size_t(x)], *sy = &L.seq[3 * size_t(y)];
+        const int32_t nx = L.nseq[x], ny = L.nseq[y];
+        for (int i = 0; i < nx && i < ny; ++i)
+            if (sx[i] != sy[i]) return lt(sy[i], sx[i]);
+        return nx > ny;
+    };
+    auto &one = L.heap_one, &zero = L.heap_zero;
+    one.clear();
+    zero.clear();
+    auto classify = [&](int32_t s) {
+        L.state[s] = 1;
+        for (int32_t q = L.cof_off[s]; q < L.cof_off[s + 1]; ++q) L.open[L.cof[q]]--;
+    };
+    auto offer_cofaces = [&](int32_t s) {
+        for (int32_t q = L.cof_off[s]; q < L.cof_off[s + 1]; ++q) {
+            const int32_t c = L.cof[q];
+            if (!L.state[c] && !L.in_one[c] && L.open[c] == 1) {
+                L.in_one[c] = 1;
+                one.push_back(c);
+                std::push_heap(one.begin(), one.end(), later);
+            }
+        }
+    };
+    int32_t first = 0;
+    for (int32_t s = 1; s < ne; ++s)
+        if (later(first, s)) first = s;
+    a.v_up[v] = L.gid[first];
+    a.e_down[L.gid[first]] = v;
+    a.e_up[L.gid[first]] = -1;
+    L.state[first] = 1;
+    for (int32_t q = L.cof_off[first]; q < L.cof_off[first + 1]; ++q) L.open[L.cof[q]]--;
+    for (int32_t s = 0; s < ne; ++s)
+        if (s != first) {
+            zero.push_back(s);
+            std::push_heap(zero.begin(), zero.end(), later);
+        }
+    offer_cofaces(first);
+    // every other simplex starts unpaired
+    for (int32_t s = 0; s < ns; ++s) {
+        if (s == first) continue;
+        const int32_t g = L.gid[s];
+        if (L.dim[s] == 1) a.e_down[g] = a.e_up[g] = -1;
+        else if (L.dim[s] == 2) a.f_down[g] = a.f_up[g] = -1;
+        else a.t_down[g] = -1;
+    }
+    auto pair = [&](int32_t lo, int32_t hi) {
+        const int32_t gl = L.gid[lo], gh = L.gid[hi];
+        if (L.dim[lo] == 1) {
+            a.e_up[gl] = gh;
+            a.f_down[gh] = gl;
+        } else {
+            a.f_up[gl] = gh;
+            a.t_down[gh] = gl;
+        }
+    };
+    while (!one.empty() || !zero.empty()) {
+        while (!one.empty()) {
+            std::pop_heap(one.begin(), one.end(), later);
+            const int32_t x = one.back();
+            one.pop_back();
+            L.in_one[x] = 0;
+            if (L.state[x]) continue;
+            if (L.open[x] == 0) {
+                zero.push_back(x);
+                std::push_heap(zero.begin(), zero.end(), later);
+                continue;
+            }
+            int32_t g = -1;
+            for (int i = 0; i < L.dim[x]; ++i)
+                if (!L.state[L.face[3 * size_t(x) + i]]) g = L.face[3 * size_t(x) + i];
+            pair(g, x);
+            classify(g);
+            classify(x);
+            offer_cofaces(x);
+            offer_cofaces(g);
+        }
+        while (!zero.empty()) {
+            std::pop_heap(zero.begin(), zero.end(), later);
+            const int32_t g = zero.back();
+            zero.pop_back();
+            if (L.state[g]) continue;
+            classify(g);  // critical
+            offer_cofaces(g);
+            break;
+        }
+    }
+    return 0;
+}
+
+}  // namespace
+
+int gale_dg_lower_stars(const float *f, const int32_t *inid, int64_t v_begin, int64_t v_end, const int64_t *ve_off,
+                        const int32_t *ve_val, const int64_t *vf_off, const int32_t *vf_val, const int64_t *vt_off,
+                        const int32_t *vt_val, const int32_t *ev, const int32_t *fv, const int32_t *tv,
+                        const int32_t *fe, const int32_t *tf, int32_t *v_up, int32_t *e_down, int32_t *e_up,
+                        int32_t *f_down, int32_t *f_up, int32_t *t_down) {
+    const DgArgs a{f, inid, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv, fe, tf,
+                   v_up, e_down, e_up, f_down, f_up, t_down};
+    LowerStar L;
+    for (int64_t v = v_begin; v < v_end; ++v)
+        if (dg_vertex(a, int32_t(v), L) != 0) return -1;
+    return 0;
+}
+
+/*
+ * The same over all nv vertices with nthreads consumer threads; each thread
+ * takes blocks of `grain` consecutive vertices from a shared counter (lower
+ * stars are disjoint, so the threads write disjoint entries).
+ * stats double[2] out: wall seconds, vertices processed.
+ */
+int gale_dg_run(const float *f, const int32_t *inid, int64_t nv, const int64_t *ve_off, const int32_t *ve_val,
+                const int64_t *vf_off, const int32_t *vf_val, const int64_t *vt_off, const int32_t *vt_val,
+                const int32_t *ev, const int32_t *fv, const int32_t *tv, const int32_t *fe, const int32_t *tf,
+                int32_t *v_up, int32_t *e_down, int32_t *e_up, int32_t *f_down, int32_t *f_up, int32_t *t_down,
+                int32_t nthreads, int64_t grain, double *stats) {
+    if (nthreads < 1) nthreads = 1;
+    if (grain < 1) grain = 1024;
+    const DgArgs a{f, inid, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv, fe, tf,
+                   v_up, e_down, e_up, f_down, f_up, t_down};
+    std::atomic<int64_t> next{0}, done{0};
+    std::atomic<int> err{0};
+    const auto t0 = std::chrono::steady_clock::now();
+    auto worker = [&]() {
+        LowerStar L;
+        for (;;) {
+            const int64_t b = next.fetch_add(grain);
+            if (b >= nv || err.load()) return;
+            const int64_t e = std::min(nv, b + grain);
+            for (int64_t v = b; v < e; ++v)
+                if (dg_vertex(a, int32_t(v), L) != 0) {
+                    err.store(1);
+                    return;
+                }
+            done += e - b;
+        }
+    };
+    std::vector<std::thread> th;
+    for (int i = 0; i < nthreads; ++i) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+    stats[0] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats[1] = double(done.load());
+    return err.load() ? -1 : 0;
+}
+
 }  // extern "C"

@@ -426,6 +426,10 @@ class Context:
         I_E, I_F (K+1) in canonical ids; order ENUM_SORTED or
         ENUM_FIRST_APPEARANCE."""
         _check(self._lib.gale_enumerate(self._h, order))
+        return self.enumeration()
+
+    def enumeration(self) -> dict:
+        """gale_get_enumeration of the last gale_enumerate (ENOTFOUND before)."""
         counts = np.zeros(2, np.int64)
         _check(self._lib.gale_get_enumeration(self._h, _p(counts), None, None, None, None))
         E = np.empty((max(int(counts[0]), 1), 2), np.int32)

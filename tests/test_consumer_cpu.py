@@ -1,6 +1,8 @@
 """The critical-point classifier against fields whose critical points are
-known, on oracle relations (no GPU)."""
+known, and the discrete-gradient consumer against the oracle, both on oracle
+relations (no GPU)."""
 import numpy as np
+import pytest
 
 import consumers
 import gen
@@ -47,3 +49,69 @@ def test_bowl_has_one_interior_minimum():
     # negated: one interior maximum
     cls2, _ = classify_all(m, -f)
     assert (cls2[inside] == 3).sum() == 1 and (cls2[inside] == 0).sum() == 0
+
+
+# ---- discrete gradient consumer (Section 5.1) on oracle relations ----
+
+def oracle_dg_relations(canon, order="sorted"):
+    en = oracle.enumerate_simplices(canon, order)
+    cb = oracle.coboundary(canon, en)
+    rel = oracle.relations(canon)
+    rows = canon["rows"]
+
+    def csr(rs):
+        return (np.concatenate([[0], np.cumsum([len(r) for r in rs])]).astype(np.int64),
+                np.array([x for r in rs for x in r], np.int32))
+    fe = np.array(oracle.boundary(canon, en, "FE", range(len(en["F"]))), np.int32).reshape(-1, 3)
+    tf = np.array(oracle.boundary(canon, en, "TF", range(rows.shape[0])), np.int32).reshape(-1, 4)
+    return en, dict(ve=csr(cb["VE"]), vf=csr(cb["VF"]), vt=(np.asarray(rel["vt_off"]), np.asarray(rel["vt_val"])),
+                    ev=np.array(en["E"], np.int32).reshape(-1, 2), fv=np.array(en["F"], np.int32).reshape(-1, 3),
+                    tv=rows, fe=fe, tf=tf)
+
+
+def dg_matches_oracle(canon, f_c, inid, order="sorted", nthreads=4):
+    from dg_util import pairs_from_ids
+    en, rel = oracle_dg_relations(canon, order)
+    g, _ = consumers.discrete_gradient_arrays(f_c, inid, **rel, nthreads=nthreads, grain=5)
+    pairs, crit = pairs_from_ids(g, en["E"], en["F"], canon["rows"])
+    want = oracle.lower_star_gradient(canon, f_c.astype(np.float64), inid)
+    assert pairs == {(tuple(a), tuple(b)) for a, b in want["pairs"]}
+    assert crit == {tuple(c) for c in want["critical"]}
+
+
+
+@pytest.mark.parametrize("n,K,seed,ties,order", [(3, 1, 0, 3, "sorted"), (4, 6, 1, 4, "first"),
+                                                 (5, 9, 2, 1000, "sorted")])
+def test_dg_consumer_equals_oracle_on_grids(n, K, seed, ties, order):
+    xyz, tv = gen.freudenthal_grid(n, permute=True, seed=seed + 30)
+    seg = np.random.default_rng(seed).integers(0, K, xyz.shape[0]).astype(np.int32)
+    canon = oracle.canonicalize(xyz.shape[0], tv, seg, K)
+    f = np.random.default_rng(seed + 3).integers(0, ties, xyz.shape[0]).astype(np.float32)
+    f_c, inid = consumers.canonical_inputs(f, canon["vperm"])
+    dg_matches_oracle(canon, f_c, inid, order)
+
+
+def test_dg_consumer_equals_oracle_on_delaunay_and_fan():
+    m = gen.delaunay_mesh(500, seed=8, kd_cap=128, with_field=True)
+    canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
+    f_c, inid = consumers.canonical_inputs(m.field, canon["vperm"])
+    dg_matches_oracle(canon, f_c, inid)
+    from test_gpu_parity import fan_mesh
+    xyz, tv = fan_mesh(60)
+    seg = np.zeros(xyz.shape[0], np.int32)
+    canon = oracle.canonicalize(xyz.shape[0], tv, seg, 1)
+    f = np.random.default_rng(2).normal(size=xyz.shape[0]).astype(np.float32)
+    f[0] = 10.0  # the high-degree centre is the maximum: its lower star is its whole star
+    f_c, inid = consumers.canonical_inputs(f, canon["vperm"])
+    dg_matches_oracle(canon, f_c, inid)
+
+
+def test_dg_consumer_rejects_inconsistent_relations():
+    xyz, tv = gen.freudenthal_grid(2, permute=True, seed=3)
+    canon = oracle.canonicalize(xyz.shape[0], tv, np.zeros(xyz.shape[0], np.int32), 1)
+    f_c, inid = consumers.canonical_inputs(np.arange(xyz.shape[0], dtype=np.float32), canon["vperm"])
+    _, rel = oracle_dg_relations(canon)
+    rel["ev"] = rel["ev"].copy()
+    rel["ev"][:, :] = rel["ev"][::-1, :]  # edges no longer match their VE rows
+    with pytest.raises(RuntimeError):
+        consumers.discrete_gradient_arrays(f_c, inid, **rel, nthreads=2)
