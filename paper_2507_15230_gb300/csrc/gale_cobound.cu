@@ -3,18 +3,34 @@
 // whole segments; Section 5 evaluates VE, VF, EF and FT among them).
 //
 // Inputs on the device: the canonical tet rows, each vertex's cluster, the
-// enumeration (E, F, their per-segment views in vertex-tuple order, I_E,
-// I_F) and the VT and VV rows of every cluster from a batched build.  One
-// thread per output row, two passes (count, then fill after an exclusive
-// scan):
-//   VE(v)  the edges {v, w} for w in VV(v), each found by binary search in
-//          its segment's slice of E;
-//   VF(v)  the triangles through v of the tets of VT(v), each taken from the
-//          first tet of VT(v) that contains it;
-//   EF(e)  for e = (u, w): the triangles (u, w, x) of the tets of VT(u) that
-//          contain w, each from the first such tet;
-//   FT(f)  for f = (a, b, c): the tets of VT(a) that contain b and c.
-// Ids found by lookup are then sorted within their row.
+// enumeration (E, F, I_E, I_F and each segment's ids in vertex-tuple order)
+// and the VT, VV and ET rows of every cluster from a batched build.
+//
+// Lookup structure, built once per enumeration: the edges and triangles in
+// vertex-tuple ("sorted") order, with
+//   eo[v]    first sorted edge position with lower vertex v (nv+1 entries),
+//   ekw[j]   upper vertex of the j-th sorted edge,
+//   feo[j]   first sorted triangle position whose first two vertices are the
+//            j-th sorted edge (nE+1 entries),
+//   fkc[p]   third vertex of the p-th sorted triangle,
+//   e2s, f2s the sorted position of every edge / triangle id.
+// An edge (a, b) is then found among a's few upper edges and a triangle
+// (a, b, c) among the few triangles over its edge (a, b).  Within a segment
+// the sorted edge order is the order of the cluster's ET rows (own lower
+// vertex, then upper vertex), so the tets around the j-th sorted edge are
+// the ET row at j - I_E[k] of its cluster k.
+//
+// One thread per output row, two passes (count, then fill after an
+// exclusive scan):
+//   VE(v)  the edges {v, w} for w in VV(v);
+//   EF(e)  the triangles (u, w, x) for the distinct third vertices x of the
+//          tets of ET(e);
+//   VF(v)  read from EF: a triangle through v has two edges through v, and
+//          is taken from the one to its smaller other vertex (so EF is built
+//          first, and whenever VF is asked for);
+//   FT(f)  for f = (a, b, c): the tets of ET(a, b) that contain c.
+// With the sorted numbering every row comes out ascending; otherwise rows
+// whose ids come from lookups are sorted in place.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,11 +47,14 @@ namespace gale {
 
 // device copies the coboundary pass keeps in the context
 struct Cobound {
-    const void *enm = nullptr;  // the enumeration the copies were made from
+    uint64_t enm_gen = 0;  // the enumeration the copies were made from
     int32_t *rows = nullptr, *cluster_of = nullptr;
     int32_t *E = nullptr, *F = nullptr, *ebk = nullptr, *fbk = nullptr;
     int64_t *IE = nullptr, *IF = nullptr;
-    int64_t *base = nullptr;       // [K][4] bulk bases of the VT / VV segments
+    int32_t *eo = nullptr, *ekw = nullptr, *feo = nullptr, *fkc = nullptr, *fo = nullptr;
+    int32_t *e2s = nullptr, *f2s = nullptr;
+    bool sorted_ids = false;
+    int64_t *base = nullptr;       // [K][10] bulk bases of every cluster's arrays
     int32_t *cnt = nullptr;        // counts of the largest relation
     int64_t *bsum = nullptr;       // scan block sums
     int64_t cnt_cap = 0, bsum_cap = 0;
@@ -53,143 +72,206 @@ namespace {
 
 constexpr int kThreads = 256;
 enum { REL_VE = 0, REL_VF = 1, REL_EF = 2, REL_FT = 3 };
+// bulk array indices (the order of gale_arrays)
+enum { B_VT_OFF = 0, B_VT_VAL = 1, B_VV_OFF = 2, B_VV_VAL = 3, B_ET_W = 5, B_ET_OFF = 6, B_ET_VAL = 7 };
 
 struct CbMesh {
-    const int32_t *rows, *cluster_of, *I_V;
+    const int4 *rows;
+    const int32_t *cluster_of, *I_V;
     const int32_t *E, *F, *ebk, *fbk;
     const int64_t *IE, *IF;
-    const int32_t *vt_off, *vt_val, *vv_off, *vv_val;
+    const int32_t *eo, *ekw, *feo, *fkc, *e2s, *f2s;
+    const int32_t *vt_off, *vt_val, *vv_off, *vv_val, *et_w, *et_off, *et_val;
+    const int32_t *ef_off, *ef_val;  // EF, once built (VF is read from it)
     const int64_t *base;
+    const int64_t *sizes;  // [K][5] per-cluster entries: VT, VV, edges, ET, TT
     int64_t nv, nE, nF;
+    bool sorted_ids;
 };
 
-__device__ __forceinline__ void seg_row(const CbMesh &m, int32_t v, int which, int64_t &b, int64_t &e) {
+// [b, e) of vertex v's row of a per-own-vertex bulk relation (VT or VV)
+__device__ __forceinline__ void vrow(const CbMesh &m, int32_t v, bool vv, int64_t &b, int64_t &e) {
     const int32_t k = m.cluster_of[v];
     const int32_t i = v - m.I_V[k];
-    const int32_t *off = which ? m.vv_off : m.vt_off;
-    const int64_t ob = m.base[4 * int64_t(k) + 2 * which], vb = m.base[4 * int64_t(k) + 2 * which + 1];
+    const int32_t *off = vv ? m.vv_off : m.vt_off;
+    const int64_t *B = m.base + 10 * int64_t(k);
+    const int64_t ob = B[vv ? B_VV_OFF : B_VT_OFF], vb = B[vv ? B_VV_VAL : B_VT_VAL];
     b = vb + off[ob + i];
     e = vb + off[ob + i + 1];
 }
 
-__device__ __forceinline__ bool has(const int32_t *r, int32_t x) {
-    return r[0] == x || r[1] == x || r[2] == x || r[3] == x;
-}
+__device__ __forceinline__ bool has4(const int4 r, int32_t x) { return r.x == x || r.y == x || r.z == x || r.w == x; }
 
-__device__ int32_t lookup_edge(const CbMesh &m, int32_t u, int32_t w) {
-    if (u > w) {
-        const int32_t t = u;
-        u = w;
-        w = t;
-    }
-    const int32_t k = m.cluster_of[u];
-    int64_t lo = m.IE[k], hi = m.IE[k + 1];
+// sorted position of edge (a, b), a < b, or -1
+__device__ int64_t epos(const CbMesh &m, int32_t a, int32_t b) {
+    int64_t lo = m.eo[a];
+    const int64_t end = m.eo[a + 1];
+    int64_t hi = end;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        const int32_t id = m.ebk[mid];
-        const int32_t a = m.E[2 * int64_t(id)], b = m.E[2 * int64_t(id) + 1];
-        if (a < u || (a == u && b < w)) lo = mid + 1;
+        if (m.ekw[mid] < b) lo = mid + 1;
         else hi = mid;
     }
-    if (lo >= m.IE[k + 1]) return -1;
-    const int32_t id = m.ebk[lo];
-    return (m.E[2 * int64_t(id)] == u && m.E[2 * int64_t(id) + 1] == w) ? id : -1;
+    return (lo < end && m.ekw[lo] == b) ? lo : -1;
 }
 
-__device__ int32_t lookup_face(const CbMesh &m, int32_t a, int32_t b, int32_t c) {
-    // sort the three ids
+// sorted position of triangle (a, b, c), a < b < c, or -1
+__device__ int64_t fpos(const CbMesh &m, int32_t a, int32_t b, int32_t c) {
+    const int64_t j = epos(m, a, b);
+    if (j < 0) return -1;
+    const int64_t end = m.feo[j + 1];
+    for (int64_t p = m.feo[j]; p < end; ++p) {
+        const int32_t x = m.fkc[p];
+        if (x == c) return p;
+        if (x > c) break;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void sort3(int32_t &a, int32_t &b, int32_t &c) {
     if (a > b) { const int32_t t = a; a = b; b = t; }
     if (b > c) { const int32_t t = b; b = c; c = t; }
     if (a > b) { const int32_t t = a; a = b; b = t; }
-    const int32_t k = m.cluster_of[a];
-    int64_t lo = m.IF[k], hi = m.IF[k + 1];
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        const int32_t *f = m.F + 3 * int64_t(m.fbk[mid]);
-        if (f[0] < a || (f[0] == a && (f[1] < b || (f[1] == b && f[2] < c)))) lo = mid + 1;
-        else hi = mid;
-    }
-    if (lo >= m.IF[k + 1]) return -1;
-    const int32_t id = m.fbk[lo];
-    const int32_t *f = m.F + 3 * int64_t(id);
-    return (f[0] == a && f[1] == b && f[2] == c) ? id : -1;
 }
 
-// One row of relation REL: count (out == nullptr) or write its entries.
+// the ET row [b, e) of the edge at sorted position j, whose vertices are
+// (a, w); false if the cluster's ET rows do not list that edge there
+__device__ bool et_row(const CbMesh &m, int64_t j, int32_t a, int32_t w, int64_t &b, int64_t &e) {
+    const int32_t k = m.cluster_of[a];
+    const int64_t le = j - m.IE[k];
+    if (le < 0 || j >= m.IE[k + 1] || le >= m.sizes[5 * int64_t(k) + 2]) return false;
+    const int64_t *B = m.base + 10 * int64_t(k);
+    if (m.et_w[B[B_ET_W] + le] != w) return false;
+    b = B[B_ET_VAL] + m.et_off[B[B_ET_OFF] + le];
+    e = B[B_ET_VAL] + m.et_off[B[B_ET_OFF] + le + 1];
+    return true;
+}
+
+__device__ __forceinline__ int32_t edge_id(const CbMesh &m, int64_t j) { return m.sorted_ids ? int32_t(j) : m.ebk[j]; }
+__device__ __forceinline__ int32_t face_id(const CbMesh &m, int64_t p) { return m.sorted_ids ? int32_t(p) : m.fbk[p]; }
+
+// One row of relation REL: count (out == nullptr) or write its entries (at
+// most cap of them; the count is returned either way).
 template <int REL>
-__device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32_t *err) {
+__device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32_t cap, int32_t *err) {
     int32_t n = 0;
     if (REL == REL_VE) {
         const int32_t v = int32_t(row);
         int64_t b, e;
-        seg_row(m, v, 1, b, e);
+        vrow(m, v, true, b, e);
+        if (!out) return int32_t(e - b);
         for (int64_t j = b; j < e; ++j) {
-            if (out) {
-                const int32_t id = lookup_edge(m, v, m.vv_val[j]);
-                if (id < 0) atomicOr(err, ERR_BAD_BLOCK);
-                out[n] = id;
-            }
+            const int32_t w = m.vv_val[j];
+            const int64_t p = v < w ? epos(m, v, w) : epos(m, w, v);
+            if (p < 0) atomicOr(err, ERR_BAD_BLOCK);
+            if (n < cap) out[n] = p < 0 ? -1 : edge_id(m, p);
             ++n;
         }
     } else if (REL == REL_VF) {
+        // every triangle through v has exactly two edges through v: take it
+        // from the one to its smaller other vertex.  With x ascending and
+        // EF rows ordered by third vertex, the sorted numbering's ids come
+        // out ascending.
         const int32_t v = int32_t(row);
         int64_t b, e;
-        seg_row(m, v, 0, b, e);
+        vrow(m, v, true, b, e);
         for (int64_t j = b; j < e; ++j) {
-            const int32_t *r = m.rows + 4 * int64_t(m.vt_val[j]);
-            int32_t o[3], c = 0;
-            for (int s = 0; s < 4; ++s)
-                if (r[s] != v) o[c++] = r[s];
-            const int32_t pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
-            for (int p = 0; p < 3; ++p) {
-                const int32_t x = o[pa[p]], y = o[pb[p]];
-                bool first = true;
-                for (int64_t jj = b; jj < j && first; ++jj) {
-                    const int32_t *q = m.rows + 4 * int64_t(m.vt_val[jj]);
-                    first = !(has(q, x) && has(q, y));
+            const int32_t x = m.vv_val[j];
+            const int64_t p = v < x ? epos(m, v, x) : epos(m, x, v);
+            if (p < 0) {
+                atomicOr(err, ERR_BAD_BLOCK);
+                return n;
+            }
+            const int32_t id = edge_id(m, p);
+            const int32_t fb = m.ef_off[id], fe = m.ef_off[id + 1];
+            if (!out) {
+                n += fe - fb;  // halved below: each triangle is met twice
+                continue;
+            }
+            for (int32_t q = fb; q < fe; ++q) {
+                const int32_t f = m.ef_val[q];
+                const int32_t a = m.F[3 * int64_t(f)], bb = m.F[3 * int64_t(f) + 1], c = m.F[3 * int64_t(f) + 2];
+                const int32_t third = (a != v && a != x) ? a : ((bb != v && bb != x) ? bb : c);
+                if (third > x) {
+                    if (n < cap) out[n] = f;
+                    ++n;
                 }
-                if (!first) continue;
-                if (out) {
-                    const int32_t id = lookup_face(m, v, x, y);
-                    if (id < 0) atomicOr(err, ERR_BAD_BLOCK);
-                    out[n] = id;
+            }
+        }
+        if (!out) n >>= 1;
+    } else if (REL == REL_EF) {
+        // the third vertices of the tets around e, sorted and deduplicated:
+        // with the sorted numbering, ascending third vertex is ascending id
+        const int64_t js = m.sorted_ids ? row : m.e2s[row];
+        const int32_t u = m.E[2 * row], w = m.E[2 * row + 1];
+        int64_t eb, ee;
+        if (!et_row(m, js, u, w, eb, ee)) {
+            atomicOr(err, ERR_BAD_BLOCK);
+            return 0;
+        }
+        constexpr int kCand = 32;
+        if (ee - eb <= kCand / 2) {
+            int32_t xs[kCand];
+            int c = 0;
+            for (int64_t j = eb; j < ee; ++j) {
+                const int4 r = m.rows[m.et_val[j]];
+#pragma unroll
+                for (int s2 = 0; s2 < 4; ++s2) {
+                    const int32_t x = s2 == 0 ? r.x : s2 == 1 ? r.y : s2 == 2 ? r.z : r.w;
+                    if (x == u || x == w || c >= kCand) continue;
+                    int q = c++;
+                    while (q > 0 && xs[q - 1] > x) {
+                        xs[q] = xs[q - 1];
+                        --q;
+                    }
+                    xs[q] = x;
+                }
+            }
+            for (int q = 0; q < c; ++q) {
+                if (q > 0 && xs[q] == xs[q - 1]) continue;
+                if (out && n < cap) {
+                    int32_t a = u, bb = w, cc = xs[q];
+                    sort3(a, bb, cc);
+                    const int64_t p = fpos(m, a, bb, cc);
+                    if (p < 0) atomicOr(err, ERR_BAD_BLOCK);
+                    out[n] = p < 0 ? -1 : face_id(m, p);
                 }
                 ++n;
             }
+            return n;
         }
-    } else if (REL == REL_EF) {
-        const int32_t u = m.E[2 * row], w = m.E[2 * row + 1];
-        int64_t b, e;
-        seg_row(m, u, 0, b, e);
-        for (int64_t j = b; j < e; ++j) {
-            const int32_t *r = m.rows + 4 * int64_t(m.vt_val[j]);
-            if (!has(r, w)) continue;
-            for (int s = 0; s < 4; ++s) {
-                const int32_t x = r[s];
+        // many tets around the edge: first-occurrence test over the row
+        for (int64_t j = eb; j < ee; ++j) {
+            const int4 r = m.rows[m.et_val[j]];
+#pragma unroll
+            for (int s2 = 0; s2 < 4; ++s2) {
+                const int32_t x = s2 == 0 ? r.x : s2 == 1 ? r.y : s2 == 2 ? r.z : r.w;
                 if (x == u || x == w) continue;
                 bool first = true;
-                for (int64_t jj = b; jj < j && first; ++jj) {
-                    const int32_t *q = m.rows + 4 * int64_t(m.vt_val[jj]);
-                    first = !(has(q, w) && has(q, x));
-                }
+                for (int64_t jj = eb; jj < j && first; ++jj) first = !has4(m.rows[m.et_val[jj]], x);
                 if (!first) continue;
-                if (out) {
-                    const int32_t id = lookup_face(m, u, w, x);
-                    if (id < 0) atomicOr(err, ERR_BAD_BLOCK);
-                    out[n] = id;
+                if (out && n < cap) {
+                    int32_t a = u, bb = w, cc = x;
+                    sort3(a, bb, cc);
+                    const int64_t p = fpos(m, a, bb, cc);
+                    if (p < 0) atomicOr(err, ERR_BAD_BLOCK);
+                    out[n] = p < 0 ? -1 : face_id(m, p);
                 }
                 ++n;
             }
         }
     } else {
         const int32_t a = m.F[3 * row], bb = m.F[3 * row + 1], cc = m.F[3 * row + 2];
-        int64_t b, e;
-        seg_row(m, a, 0, b, e);
-        for (int64_t j = b; j < e; ++j) {
-            const int32_t t = m.vt_val[j];
-            const int32_t *r = m.rows + 4 * int64_t(t);
-            if (has(r, bb) && has(r, cc)) {
-                if (out) out[n] = t;
+        const int64_t je = epos(m, a, bb);
+        int64_t eb, ee;
+        if (je < 0 || !et_row(m, je, a, bb, eb, ee)) {
+            atomicOr(err, ERR_BAD_BLOCK);
+            return 0;
+        }
+        for (int64_t j = eb; j < ee; ++j) {
+            const int32_t t = m.et_val[j];
+            if (has4(m.rows[t], cc)) {
+                if (out && n < cap) out[n] = t;
                 ++n;
             }
         }
@@ -200,7 +282,7 @@ __device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32
 template <int REL>
 __global__ void __launch_bounds__(kThreads) cb_count(CbMesh m, int64_t rows, int32_t *cnt, int32_t *err) {
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x)
-        cnt[r] = row_entries<REL>(m, r, nullptr, err);
+        cnt[r] = row_entries<REL>(m, r, nullptr, 0, err);
 }
 
 template <int REL>
@@ -208,12 +290,14 @@ __global__ void __launch_bounds__(kThreads) cb_fill(CbMesh m, int64_t rows, cons
                                                     int32_t *err) {
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
         int32_t *o = val + off[r];
-        const int32_t n = row_entries<REL>(m, r, o, err);
-        if (n != off[r + 1] - off[r]) {
+        const int32_t len = off[r + 1] - off[r];
+        const int32_t n = row_entries<REL>(m, r, o, len, err);
+        if (n != len) {
             atomicOr(err, ERR_BAD_BLOCK);
             continue;
         }
-        if (REL != REL_FT)  // ids found by lookup: sort the row (insertion sort)
+        const bool need_sort = REL == REL_VF || REL == REL_EF || (REL == REL_VE && !m.sorted_ids);
+        if (need_sort)  // ids found by lookup: sort the row (insertion sort)
             for (int32_t i = 1; i < n; ++i) {
                 const int32_t x = o[i];
                 int32_t j = i - 1;
@@ -223,6 +307,79 @@ __global__ void __launch_bounds__(kThreads) cb_fill(CbMesh m, int64_t rows, cons
                 }
                 o[j + 1] = x;
             }
+    }
+}
+
+// ---- lookup structure, once per enumeration ----
+
+// eo[v]: first sorted edge position of lower vertex v within its segment
+__global__ void __launch_bounds__(kThreads) k_eo(CbMesh m, int32_t *eo) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v <= m.nv; v += int64_t(gridDim.x) * blockDim.x) {
+        if (v == m.nv) {
+            eo[v] = int32_t(m.nE);
+            continue;
+        }
+        const int32_t k = m.cluster_of[v];
+        int64_t lo = m.IE[k], hi = m.IE[k + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (m.E[2 * int64_t(m.ebk[mid])] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        eo[v] = int32_t(lo);
+    }
+}
+
+// fo[v]: first sorted triangle position of lowest vertex v
+__global__ void __launch_bounds__(kThreads) k_fo(CbMesh m, int32_t *fo) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v <= m.nv; v += int64_t(gridDim.x) * blockDim.x) {
+        if (v == m.nv) {
+            fo[v] = int32_t(m.nF);
+            continue;
+        }
+        const int32_t k = m.cluster_of[v];
+        int64_t lo = m.IF[k], hi = m.IF[k + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (m.F[3 * int64_t(m.fbk[mid])] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        fo[v] = int32_t(lo);
+    }
+}
+
+// ekw and e2s over sorted edge positions; fkc and f2s over triangle positions
+__global__ void __launch_bounds__(kThreads) k_keys(CbMesh m, int32_t *ekw, int32_t *e2s, int32_t *fkc,
+                                                   int32_t *f2s) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < m.nE; j += stride) {
+        const int32_t id = m.ebk[j];
+        ekw[j] = m.E[2 * int64_t(id) + 1];
+        e2s[id] = int32_t(j);
+    }
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < m.nF; p += stride) {
+        const int32_t id = m.fbk[p];
+        fkc[p] = m.F[3 * int64_t(id) + 2];
+        f2s[id] = int32_t(p);
+    }
+}
+
+// feo[j]: first sorted triangle position over the j-th sorted edge (a, b)
+__global__ void __launch_bounds__(kThreads) k_feo(CbMesh m, const int32_t *fo, int32_t *feo) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j <= m.nE; j += int64_t(gridDim.x) * blockDim.x) {
+        if (j == m.nE) {
+            feo[j] = int32_t(m.nF);
+            continue;
+        }
+        const int32_t id = m.ebk[j];
+        const int32_t a = m.E[2 * int64_t(id)], b = m.E[2 * int64_t(id) + 1];
+        int64_t lo = fo[a], hi = fo[a + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (m.F[3 * int64_t(m.fbk[mid]) + 1] < b) lo = mid + 1;
+            else hi = mid;
+        }
+        feo[j] = int32_t(lo);
     }
 }
 
@@ -240,28 +397,30 @@ __global__ void __launch_bounds__(kThreads) scan_sums(const int32_t *cnt, int64_
     if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
 }
 
+// exclusive scan of the nb block sums in place (bsum[nb] = total), one
+// block: each thread sums a contiguous chunk, the chunk totals are scanned,
+// then each thread rewrites its chunk
 __global__ void __launch_bounds__(kThreads) scan_bsums(int64_t *bsum, int64_t nb) {
     __shared__ int64_t s[kThreads];
-    __shared__ int64_t carry;
-    if (threadIdx.x == 0) carry = 0;
+    const int64_t per = (nb + kThreads - 1) / kThreads;
+    const int64_t b0 = min(nb, int64_t(threadIdx.x) * per), b1 = min(nb, b0 + per);
+    int64_t sum = 0;
+    for (int64_t b = b0; b < b1; ++b) sum += bsum[b];
+    s[threadIdx.x] = sum;
     __syncthreads();
-    for (int64_t b0 = 0; b0 < nb; b0 += kThreads) {
-        const int64_t b = b0 + threadIdx.x;
-        const int64_t x = b < nb ? bsum[b] : 0;
-        s[threadIdx.x] = x;
+    for (int o = 1; o < kThreads; o <<= 1) {
+        const int64_t y = int(threadIdx.x) >= o ? s[threadIdx.x - o] : 0;
         __syncthreads();
-        for (int o = 1; o < kThreads; o <<= 1) {
-            const int64_t y = int(threadIdx.x) >= o ? s[threadIdx.x - o] : 0;
-            __syncthreads();
-            s[threadIdx.x] += y;
-            __syncthreads();
-        }
-        if (b < nb) bsum[b] = carry + s[threadIdx.x] - x;
-        __syncthreads();
-        if (threadIdx.x == kThreads - 1) carry += s[threadIdx.x];
+        s[threadIdx.x] += y;
         __syncthreads();
     }
-    if (threadIdx.x == 0) bsum[nb] = carry;
+    int64_t run = s[threadIdx.x] - sum;
+    for (int64_t b = b0; b < b1; ++b) {
+        const int64_t x = bsum[b];
+        bsum[b] = run;
+        run += x;
+    }
+    if (threadIdx.x == kThreads - 1) bsum[nb] = s[kThreads - 1];
 }
 
 __global__ void __launch_bounds__(kThreads) scan_write(const int32_t *cnt, int64_t n, const int64_t *bsum,
@@ -317,7 +476,8 @@ T *upload(gale_ctx *ctx, const std::vector<T> &h, cudaStream_t s) {
 // the enumeration's host arrays (gale_enum.cpp)
 bool enumeration_arrays(gale_ctx *ctx, const std::vector<int32_t> **E, const std::vector<int32_t> **F,
                         const std::vector<int32_t> **ebk, const std::vector<int32_t> **fbk,
-                        const std::vector<int64_t> **IE, const std::vector<int64_t> **IF);
+                        const std::vector<int64_t> **IE, const std::vector<int64_t> **IF, int32_t *order,
+                        uint64_t *gen);
 
 }  // namespace gale
 
@@ -327,14 +487,19 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
     if (which == 0 || (which & ~uint32_t(GALE_CB_VE | GALE_CB_VF | GALE_CB_EF | GALE_CB_FT)))
         return fail(GALE_EINVAL, "which must be a non-empty set of GALE_CB_* bits");
-    if ((ctx->precond & (GALE_VT | GALE_VV)) != (GALE_VT | GALE_VV))
-        return fail(GALE_EINVAL, "coboundary relations need VT and VV in the precondition mask");
+    const uint32_t need = GALE_VT | GALE_VV | GALE_ET;
+    if ((ctx->precond & need) != need)
+        return fail(GALE_EINVAL, "coboundary relations need VT, VV and ET in the precondition mask");
     const std::vector<int32_t> *E, *F, *ebk, *fbk;
     const std::vector<int64_t> *IE, *IF;
-    if (!enumeration_arrays(ctx, &E, &F, &ebk, &fbk, &IE, &IF))
+    int32_t order = 0;
+    uint64_t gen = 0;
+    if (!enumeration_arrays(ctx, &E, &F, &ebk, &fbk, &IE, &IF, &order, &gen))
         return fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
-    // the stars and neighbour sets of every vertex
-    gale_status st = gale_build_clusters(ctx, nullptr, 0, GALE_VT | GALE_VV, GALE_MODE_BATCHED);
+    const int64_t nE = int64_t(E->size() / 2), nF = int64_t(F->size() / 3);
+    if (nE >= INT32_MAX || nF >= INT32_MAX) return fail(GALE_EINVAL, "more than 2^31 - 1 edges or triangles");
+    // the stars, neighbour sets and edge stars of every vertex
+    gale_status st = gale_build_clusters(ctx, nullptr, 0, need, GALE_MODE_BATCHED);
     if (st != GALE_OK) return st;
     std::lock_guard<std::mutex> lock(ctx->mu);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(GALE_ECUDA, "cudaSetDevice");
@@ -348,45 +513,85 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
         cb.cluster_of = upload(ctx, hm.cluster_of, s);
         if (!cb.rows || !cb.cluster_of) return fail(GALE_ENOMEM, "device allocation of the mesh rows failed");
     }
-    if (cb.enm != static_cast<const void *>(ctx->enm)) {
-        for (void *p : {static_cast<void *>(cb.E), static_cast<void *>(cb.F), static_cast<void *>(cb.ebk),
-                        static_cast<void *>(cb.fbk), static_cast<void *>(cb.IE), static_cast<void *>(cb.IF)})
-            if (p) ctx->dfree(p);
+    // bases of every cluster's segments in the bulk arrays
+    std::vector<int64_t> base(ctx->bulk_offs.begin(), ctx->bulk_offs.begin() + size_t(10) * K);
+    if (cb.base) ctx->dfree(cb.base);
+    cb.base = upload(ctx, base, s);
+    if (!cb.base) return fail(GALE_ENOMEM, "device allocation failed");
+    CbMesh m{reinterpret_cast<const int4 *>(cb.rows), cb.cluster_of, ctx->d_I_V, cb.E, cb.F, cb.ebk, cb.fbk,
+             cb.IE, cb.IF, cb.eo, cb.ekw, cb.feo, cb.fkc, cb.e2s, cb.f2s,
+             ctx->bulk[B_VT_OFF], ctx->bulk[B_VT_VAL], ctx->bulk[B_VV_OFF], ctx->bulk[B_VV_VAL],
+             ctx->bulk[B_ET_W], ctx->bulk[B_ET_OFF], ctx->bulk[B_ET_VAL], nullptr, nullptr, cb.base, ctx->d_sizes,
+             hm.nv, nE, nF, cb.sorted_ids};
+    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
+    auto grid_for = [&](int64_t n) {
+        return int(std::min<int64_t>(std::max<int64_t>((n + kThreads - 1) / kThreads, 1), int64_t(sms) * 16));
+    };
+    if (cb.enm_gen != gen) {
+        int32_t **own[] = {&cb.E, &cb.F, &cb.ebk, &cb.fbk, &cb.eo, &cb.ekw, &cb.feo, &cb.fkc, &cb.fo, &cb.e2s,
+                           &cb.f2s};
+        for (int32_t **p : own)
+            if (*p) {
+                ctx->dfree(*p);
+                *p = nullptr;
+            }
+        for (int64_t **p : {&cb.IE, &cb.IF})
+            if (*p) {
+                ctx->dfree(*p);
+                *p = nullptr;
+            }
+        cb.enm_gen = 0;
         cb.E = upload(ctx, *E, s);
         cb.F = upload(ctx, *F, s);
         cb.ebk = upload(ctx, *ebk, s);
         cb.fbk = upload(ctx, *fbk, s);
         cb.IE = upload(ctx, *IE, s);
         cb.IF = upload(ctx, *IF, s);
-        if (!cb.E || !cb.F || !cb.ebk || !cb.fbk || !cb.IE || !cb.IF)
+        auto dal = [&](int64_t n) { return static_cast<int32_t *>(ctx->dalloc(size_t(std::max<int64_t>(n, 1)) * 4)); };
+        cb.eo = dal(hm.nv + 1);
+        cb.fo = dal(hm.nv + 1);
+        cb.ekw = dal(nE);
+        cb.e2s = dal(nE);
+        cb.feo = dal(nE + 1);
+        cb.fkc = dal(nF);
+        cb.f2s = dal(nF);
+        if (!cb.E || !cb.F || !cb.ebk || !cb.fbk || !cb.IE || !cb.IF || !cb.eo || !cb.fo || !cb.ekw || !cb.e2s ||
+            !cb.feo || !cb.fkc || !cb.f2s)
             return fail(GALE_ENOMEM, "device allocation of the enumeration failed");
-        cb.enm = ctx->enm;
+        cb.sorted_ids = order == GALE_ENUM_SORTED;
+        m.E = cb.E;
+        m.F = cb.F;
+        m.ebk = cb.ebk;
+        m.fbk = cb.fbk;
+        m.IE = cb.IE;
+        m.IF = cb.IF;
+        k_eo<<<grid_for(hm.nv + 1), kThreads, 0, s>>>(m, cb.eo);
+        k_fo<<<grid_for(hm.nv + 1), kThreads, 0, s>>>(m, cb.fo);
+        k_keys<<<grid_for(std::max(nE, nF)), kThreads, 0, s>>>(m, cb.ekw, cb.e2s, cb.fkc, cb.f2s);
+        k_feo<<<grid_for(nE + 1), kThreads, 0, s>>>(m, cb.fo, cb.feo);
+        if (cudaGetLastError() != cudaSuccess) return fail(GALE_ECUDA, "coboundary lookup-structure launch failed");
+        cb.enm_gen = gen;
     }
-    // bases of every cluster's VT / VV segments in the bulk arrays
-    std::vector<int64_t> base(size_t(4) * K);
-    for (int32_t k = 0; k < K; ++k) {
-        const int64_t *o = ctx->bulk_offs.data() + size_t(10) * k;
-        base[4 * size_t(k) + 0] = o[0];
-        base[4 * size_t(k) + 1] = o[1];
-        base[4 * size_t(k) + 2] = o[2];
-        base[4 * size_t(k) + 3] = o[3];
-    }
-    if (cb.base) ctx->dfree(cb.base);
-    cb.base = upload(ctx, base, s);
-    if (!cb.base) return fail(GALE_ENOMEM, "device allocation failed");
-    const int64_t nE = int64_t(E->size() / 2), nF = int64_t(F->size() / 3);
-    const CbMesh m{cb.rows, cb.cluster_of, ctx->d_I_V, cb.E, cb.F, cb.ebk, cb.fbk, cb.IE, cb.IF,
-                   ctx->bulk[0], ctx->bulk[1], ctx->bulk[2], ctx->bulk[3], cb.base, hm.nv, nE, nF};
+    m.eo = cb.eo;
+    m.ekw = cb.ekw;
+    m.feo = cb.feo;
+    m.fkc = cb.fkc;
+    m.e2s = cb.e2s;
+    m.f2s = cb.f2s;
+    m.sorted_ids = cb.sorted_ids;
     const int64_t rows_of[4] = {hm.nv, hm.nv, nE, nF};
-    int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
-    for (int rel = 0; rel < 4; ++rel) {
-        if (!(which & (1u << rel))) continue;
+    // VF is read from EF: EF first, and built whenever VF is asked for
+    const uint32_t build = which | ((which & GALE_CB_VF) ? uint32_t(GALE_CB_EF) : 0u);
+    m.ef_off = nullptr;
+    m.ef_val = nullptr;
+    for (int rel : {int(REL_EF), int(REL_VF), int(REL_VE), int(REL_FT)}) {
+        if (!(build & (1u << rel))) continue;
         const int64_t n = rows_of[rel];
         const int64_t nb = (n + kThreads - 1) / kThreads;
         if (!grow(ctx, cb.cnt, cb.cnt_cap, std::max<int64_t>(n, 1)) ||
             !grow(ctx, cb.bsum, cb.bsum_cap, nb + 1) || !grow(ctx, cb.off[rel], cb.off_cap[rel], n + 1))
             return fail(GALE_ENOMEM, "device allocation of coboundary counts failed");
-        const int grid = int(std::min<int64_t>(std::max<int64_t>(nb, 1), int64_t(sms) * 16));
+        const int grid = grid_for(n);
         switch (rel) {
             case REL_VE: cb_count<REL_VE><<<grid, kThreads, 0, s>>>(m, n, cb.cnt, ctx->d_err); break;
             case REL_VF: cb_count<REL_VF><<<grid, kThreads, 0, s>>>(m, n, cb.cnt, ctx->d_err); break;
@@ -421,6 +626,10 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
         if (cudaGetLastError() != cudaSuccess) return fail(GALE_ECUDA, "coboundary launch failed");
         cb.rows_of[rel] = n;
         cb.len[rel] = total;
+        if (rel == REL_EF) {
+            m.ef_off = cb.off[REL_EF];
+            m.ef_val = cb.val[REL_EF];
+        }
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GALE_ECUDA, "cudaStreamSynchronize");
     int32_t e = 0;

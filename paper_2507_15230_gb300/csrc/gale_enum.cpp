@@ -16,6 +16,7 @@
 // combinations in combination order.  For lookups, each segment keeps a view
 // of its ids sorted by vertex tuple (binary search).
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <cstring>
 #include <memory>
@@ -30,6 +31,7 @@ namespace gale {
 
 struct Enumeration {
     int32_t order = -1;
+    uint64_t gen = 0;                // distinct for every enumeration of the process
     std::vector<int32_t> E;          // [2 nE] (u, w), u < w
     std::vector<int32_t> F;          // [3 nF] (a, b, c), a < b < c
     std::vector<int64_t> I_E, I_F;   // [K+1]
@@ -44,8 +46,11 @@ void enumeration_destroy(gale_ctx *ctx) {
 
 bool enumeration_arrays(gale_ctx *ctx, const std::vector<int32_t> **E, const std::vector<int32_t> **F,
                         const std::vector<int32_t> **ebk, const std::vector<int32_t> **fbk,
-                        const std::vector<int64_t> **IE, const std::vector<int64_t> **IF) {
+                        const std::vector<int64_t> **IE, const std::vector<int64_t> **IF, int32_t *order,
+                        uint64_t *gen) {
     if (!ctx->enm) return false;
+    *order = ctx->enm->order;
+    *gen = ctx->enm->gen;
     *E = &ctx->enm->E;
     *F = &ctx->enm->F;
     *ebk = &ctx->enm->e_by_key;
@@ -165,8 +170,10 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
         std::vector<std::vector<std::array<int32_t, 3>>> sf(K);
         gale::parallel_dynamic(K, gale::host_threads(0), 1,
                                [&](int64_t k, int) { gale::segment_simplices(hm, int32_t(k), order, se[k], sf[k]); });
+        static std::atomic<uint64_t> next_gen{1};
         auto en = std::make_unique<gale::Enumeration>();
         en->order = order;
+        en->gen = next_gen.fetch_add(1);
         en->I_E.assign(size_t(K) + 1, 0);
         en->I_F.assign(size_t(K) + 1, 0);
         for (int32_t k = 0; k < K; ++k) {

@@ -67,8 +67,24 @@ def test_errors():
         ctx.enumerate(gale.ENUM_SORTED)
         with pytest.raises(gale.GaleError):
             ctx.coboundary(16)
-    with gale.Context.load(m, device=0, precondition_mask=gale.ET | gale.TT) as ctx:
-        ctx.enumerate(gale.ENUM_SORTED)
-        with pytest.raises(gale.GaleError) as ei:
-            ctx.coboundary()
-        assert gale.STATUS[ei.value.status] == "EINVAL"
+    for pre in (gale.ET | gale.TT, gale.VT | gale.VV):  # VT, VV and ET are all needed
+        with gale.Context.load(m, device=0, precondition_mask=pre) as ctx:
+            ctx.enumerate(gale.ENUM_SORTED)
+            with pytest.raises(gale.GaleError) as ei:
+                ctx.coboundary()
+            assert gale.STATUS[ei.value.status] == "EINVAL"
+
+
+def test_enumeration_replaced_between_calls():
+    """A new enumeration (another numbering) replaces the lookup structure."""
+    m = gen.small_grid(with_field=False)
+    canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
+    with gale.Context.load(m, device=0) as ctx:
+        for order, oname in ORDERS + ORDERS[::-1]:
+            ctx.enumerate(order)
+            ctx.enumerate(order)  # twice: the earlier enumeration's memory may be reused
+            got = ctx.coboundary(gale.CB_VE | gale.CB_EF)
+            want = oracle.coboundary(canon, oracle.enumerate_simplices(canon, oname))
+            for name in ("VE", "EF"):
+                off, val = got[name]
+                assert val.tolist() == [x for r in want[name] for x in r], (oname, name)
