@@ -59,6 +59,8 @@ struct Cobound {
     int64_t *bsum = nullptr;       // scan block sums
     int64_t cnt_cap = 0, bsum_cap = 0;
     int32_t *off[4] = {}, *val[4] = {};
+    int32_t *ef_third = nullptr;   // per EF entry: the triangle's vertex off the edge
+    int64_t ef_third_cap = 0;
     int64_t off_cap[4] = {}, val_cap[4] = {};
     int64_t rows_of[4] = {}, len[4] = {};
 };
@@ -83,6 +85,8 @@ struct CbMesh {
     const int32_t *eo, *ekw, *feo, *fkc, *e2s, *f2s;
     const int32_t *vt_off, *vt_val, *vv_off, *vv_val, *et_w, *et_off, *et_val;
     const int32_t *ef_off, *ef_val;  // EF, once built (VF is read from it)
+    const int32_t *ef_third;         // per EF entry: the triangle's vertex off the edge
+    int32_t *third_out;              // where the EF fill writes those
     const int64_t *base;
     const int64_t *sizes;  // [K][5] per-cluster entries: VT, VV, edges, ET, TT
     int64_t nv, nE, nF;
@@ -115,10 +119,9 @@ __device__ int64_t epos(const CbMesh &m, int32_t a, int32_t b) {
     return (lo < end && m.ekw[lo] == b) ? lo : -1;
 }
 
-// sorted position of triangle (a, b, c), a < b < c, or -1
-__device__ int64_t fpos(const CbMesh &m, int32_t a, int32_t b, int32_t c) {
-    const int64_t j = epos(m, a, b);
-    if (j < 0) return -1;
+// sorted position of triangle (a, b, c), a < b < c, whose edge (a, b) has
+// sorted position j, or -1
+__device__ int64_t fpos_at(const CbMesh &m, int64_t j, int32_t c) {
     const int64_t end = m.feo[j + 1];
     for (int64_t p = m.feo[j]; p < end; ++p) {
         const int32_t x = m.fkc[p];
@@ -126,6 +129,12 @@ __device__ int64_t fpos(const CbMesh &m, int32_t a, int32_t b, int32_t c) {
         if (x > c) break;
     }
     return -1;
+}
+
+// sorted position of triangle (a, b, c), a < b < c, or -1
+__device__ int64_t fpos(const CbMesh &m, int32_t a, int32_t b, int32_t c) {
+    const int64_t j = epos(m, a, b);
+    return j < 0 ? -1 : fpos_at(m, j, c);
 }
 
 __device__ __forceinline__ void sort3(int32_t &a, int32_t &b, int32_t &c) {
@@ -153,7 +162,8 @@ __device__ __forceinline__ int32_t face_id(const CbMesh &m, int64_t p) { return 
 // One row of relation REL: count (out == nullptr) or write its entries (at
 // most cap of them; the count is returned either way).
 template <int REL>
-__device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32_t cap, int32_t *err) {
+__device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32_t cap, int32_t *aux,
+                               int32_t *err) {
     int32_t n = 0;
     if (REL == REL_VE) {
         const int32_t v = int32_t(row);
@@ -188,15 +198,11 @@ __device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32
                 n += fe - fb;  // halved below: each triangle is met twice
                 continue;
             }
-            for (int32_t q = fb; q < fe; ++q) {
-                const int32_t f = m.ef_val[q];
-                const int32_t a = m.F[3 * int64_t(f)], bb = m.F[3 * int64_t(f) + 1], c = m.F[3 * int64_t(f) + 2];
-                const int32_t third = (a != v && a != x) ? a : ((bb != v && bb != x) ? bb : c);
-                if (third > x) {
-                    if (n < cap) out[n] = f;
+            for (int32_t q = fb; q < fe; ++q)
+                if (m.ef_third[q] > x) {
+                    if (n < cap) out[n] = m.ef_val[q];
                     ++n;
                 }
-            }
         }
         if (!out) n >>= 1;
     } else if (REL == REL_EF) {
@@ -230,11 +236,18 @@ __device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32
             for (int q = 0; q < c; ++q) {
                 if (q > 0 && xs[q] == xs[q - 1]) continue;
                 if (out && n < cap) {
-                    int32_t a = u, bb = w, cc = xs[q];
-                    sort3(a, bb, cc);
-                    const int64_t p = fpos(m, a, bb, cc);
+                    const int32_t x = xs[q];
+                    int64_t p;
+                    if (x > w) {
+                        p = fpos_at(m, js, x);  // (u, w, x): over this edge
+                    } else {
+                        int32_t a = u, bb = w, cc = x;
+                        sort3(a, bb, cc);
+                        p = fpos(m, a, bb, cc);
+                    }
                     if (p < 0) atomicOr(err, ERR_BAD_BLOCK);
                     out[n] = p < 0 ? -1 : face_id(m, p);
+                    if (aux) aux[n] = x;
                 }
                 ++n;
             }
@@ -256,6 +269,7 @@ __device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32
                     const int64_t p = fpos(m, a, bb, cc);
                     if (p < 0) atomicOr(err, ERR_BAD_BLOCK);
                     out[n] = p < 0 ? -1 : face_id(m, p);
+                    if (aux) aux[n] = x;
                 }
                 ++n;
             }
@@ -282,7 +296,7 @@ __device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32
 template <int REL>
 __global__ void __launch_bounds__(kThreads) cb_count(CbMesh m, int64_t rows, int32_t *cnt, int32_t *err) {
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x)
-        cnt[r] = row_entries<REL>(m, r, nullptr, 0, err);
+        cnt[r] = row_entries<REL>(m, r, nullptr, 0, nullptr, err);
 }
 
 template <int REL>
@@ -291,7 +305,8 @@ __global__ void __launch_bounds__(kThreads) cb_fill(CbMesh m, int64_t rows, cons
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
         int32_t *o = val + off[r];
         const int32_t len = off[r + 1] - off[r];
-        const int32_t n = row_entries<REL>(m, r, o, len, err);
+        int32_t *ax = REL == REL_EF ? m.third_out + off[r] : nullptr;
+        const int32_t n = row_entries<REL>(m, r, o, len, ax, err);
         if (n != len) {
             atomicOr(err, ERR_BAD_BLOCK);
             continue;
@@ -300,12 +315,15 @@ __global__ void __launch_bounds__(kThreads) cb_fill(CbMesh m, int64_t rows, cons
         if (need_sort)  // ids found by lookup: sort the row (insertion sort)
             for (int32_t i = 1; i < n; ++i) {
                 const int32_t x = o[i];
+                const int32_t y = ax ? ax[i] : 0;
                 int32_t j = i - 1;
                 while (j >= 0 && o[j] > x) {
                     o[j + 1] = o[j];
+                    if (ax) ax[j + 1] = ax[j];
                     --j;
                 }
                 o[j + 1] = x;
+                if (ax) ax[j + 1] = y;
             }
     }
 }
@@ -521,7 +539,7 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     CbMesh m{reinterpret_cast<const int4 *>(cb.rows), cb.cluster_of, ctx->d_I_V, cb.E, cb.F, cb.ebk, cb.fbk,
              cb.IE, cb.IF, cb.eo, cb.ekw, cb.feo, cb.fkc, cb.e2s, cb.f2s,
              ctx->bulk[B_VT_OFF], ctx->bulk[B_VT_VAL], ctx->bulk[B_VV_OFF], ctx->bulk[B_VV_VAL],
-             ctx->bulk[B_ET_W], ctx->bulk[B_ET_OFF], ctx->bulk[B_ET_VAL], nullptr, nullptr, cb.base, ctx->d_sizes,
+             ctx->bulk[B_ET_W], ctx->bulk[B_ET_OFF], ctx->bulk[B_ET_VAL], nullptr, nullptr, nullptr, nullptr, cb.base, ctx->d_sizes,
              hm.nv, nE, nF, cb.sorted_ids};
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
     auto grid_for = [&](int64_t n) {
@@ -584,6 +602,8 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     const uint32_t build = which | ((which & GALE_CB_VF) ? uint32_t(GALE_CB_EF) : 0u);
     m.ef_off = nullptr;
     m.ef_val = nullptr;
+    m.ef_third = nullptr;
+    m.third_out = nullptr;
     for (int rel : {int(REL_EF), int(REL_VF), int(REL_VE), int(REL_FT)}) {
         if (!(build & (1u << rel))) continue;
         const int64_t n = rows_of[rel];
@@ -615,8 +635,10 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
             cudaMemset(ctx->d_err, 0, sizeof(int32_t));
             return fail(GALE_EDEVICE, "coboundary count pass: error word " + std::to_string(e));
         }
-        if (!grow(ctx, cb.val[rel], cb.val_cap[rel], std::max<int64_t>(total, 1)))
+        if (!grow(ctx, cb.val[rel], cb.val_cap[rel], std::max<int64_t>(total, 1)) ||
+            (rel == REL_EF && !grow(ctx, cb.ef_third, cb.ef_third_cap, std::max<int64_t>(total, 1))))
             return fail(GALE_ENOMEM, "device allocation of coboundary values failed");
+        m.third_out = cb.ef_third;
         switch (rel) {
             case REL_VE: cb_fill<REL_VE><<<grid, kThreads, 0, s>>>(m, n, cb.off[rel], cb.val[rel], ctx->d_err); break;
             case REL_VF: cb_fill<REL_VF><<<grid, kThreads, 0, s>>>(m, n, cb.off[rel], cb.val[rel], ctx->d_err); break;
@@ -629,6 +651,7 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
         if (rel == REL_EF) {
             m.ef_off = cb.off[REL_EF];
             m.ef_val = cb.val[REL_EF];
+            m.ef_third = cb.ef_third;
         }
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GALE_ECUDA, "cudaStreamSynchronize");
