@@ -138,12 +138,13 @@ def max_over_ranks(dist, x: float) -> float:
     return float(t.item())
 
 
-def time_oracle(n: int, seed: int = 3):
+def time_oracle(n: int, seed: int = 3, mesh=None):
     """Whole oracle pipeline (checks, canonical numbering, VT/VV/ET/TT) on an
-    n^3 grid of the same recipe; returns (tets, seconds)."""
+    n^3 grid of the same recipe (or on `mesh`); returns (tets, seconds,
+    clusters)."""
     import gen
     import oracle
-    m = gen.freudenthal_mesh(n, 512, seed=seed, jitter=0.3, with_field=False)
+    m = mesh if mesh is not None else gen.freudenthal_mesh(n, 512, seed=seed, jitter=0.3, with_field=False)
     t0 = time.perf_counter()
     oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
     return m.nt, time.perf_counter() - t0, m.nclusters
@@ -170,11 +171,17 @@ def ref_config(args) -> dict:
 def run_reference(args, rank, dist):
     if rank != 0:
         return
+    import gen
+    # each step is the oracle on one grid sample, sized so that the whole run
+    # stays near a minute of CPU time (the oracle runs ~1M tets/s)
+    budget_s = 60.0 / max(1, args.steps + args.warmup)
+    n = int(max(16, min(REF_SAMPLE_N, round((budget_s * 1e6 / 6.0) ** (1.0 / 3.0)))))
+    mesh = gen.freudenthal_mesh(n, 512, seed=3, jitter=0.3, with_field=False)
     for _ in range(args.warmup):
-        time_oracle(REF_SAMPLE_N)
+        time_oracle(n, mesh=mesh)
     tets, secs = 0, 0.0
     for _ in range(args.steps):
-        t, s, _ = time_oracle(REF_SAMPLE_N)
+        t, s, _ = time_oracle(n, mesh=mesh)
         tets += t
         secs += s
     v = tets / secs
@@ -184,7 +191,7 @@ def run_reference(args, rank, dist):
             "data": "synthetic",
             "config": ref_config(args),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the whole oracle pipeline on a {REF_SAMPLE_N}^3 grid of the same "
+                             "sample": f"each step: the whole oracle pipeline on a {n}^3 grid of the same "
                                        f"recipe ({tets // args.steps} tets), single thread"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -193,7 +200,8 @@ def run_reference(args, rank, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100,
+                    help="timed build steps (100 x ~9 ms keeps the clock sampler running through about a second)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid cubes per axis (256 = the at-scale workload)")
@@ -217,6 +225,8 @@ def main():
     ap.add_argument("--mixed-budget-gb", type=float, default=20.0)
     ap.add_argument("--serve-threads", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
+    ap.add_argument("--serve-stress-gb", type=float, default=1.0,
+                    help="cache budget of the LRU stress variant of the serving leg (0: skip it)")
     ap.add_argument("--serve-baseline-clusters", type=int, default=2048)
     ap.add_argument("--serve-prefetch", type=int, default=4, help="prefetch depth of the serving variant (0: off)")
     args = ap.parse_args()
@@ -449,6 +459,17 @@ def serve_leg(args, mesh, ctx, gale):
             pref.update({"prefetch_depth": args.serve_prefetch, "builds": sp.builds, "hits": sp.hits,
                          "prefetches": sp.prefetches, "prefetch_hits": sp.prefetch_hits,
                          "prefetch_dropped": sp.prefetch_dropped, "evictions": sp.evictions})
+    # LRU stress: the same walk under a small budget, so finished clusters
+    # are evicted to admit new ones
+    stress = None
+    if args.serve_stress_gb > 0:
+        with gale.Context.load(mesh, device=0, cache_budget_bytes=int(args.serve_stress_gb * (1 << 30))) as cs:
+            cs.serve_configure(gale.SERVE_LOOP)
+            _, lats, sts = consumers.serve_run(cs, f_c, inid, rows, I_V, nthreads=args.serve_threads, mask=mask)
+            stress = summarize(lats, sts, cs.K)
+            ss = cs.serve_stats()
+            stress.update({"budget_gb": args.serve_stress_gb, "builds": ss.builds, "hits": ss.hits,
+                           "evictions": ss.evictions})
     base = None
     nb = min(args.serve_baseline_clusters, ctx.K)
     if nb > 0:
@@ -467,7 +488,8 @@ def serve_leg(args, mesh, ctx, gale):
             loop_sub["clusters"] = nb
     return {"workload": f"{args.serve_threads} critical-point consumer threads, kd-order walks with 10% random "
                         f"jumps, VT+VV+TT requests, {args.serve_budget_gb:g} GB cache budget, field = 16 Gaussians",
-            "device_loop": loop, "device_loop_prefetch": pref, "per_request_launch_subset": base,
+            "device_loop": loop, "device_loop_prefetch": pref, "device_loop_lru_stress": stress,
+            "per_request_launch_subset": base,
             "device_loop_same_subset": loop_sub if nb > 0 else None}
 
 
