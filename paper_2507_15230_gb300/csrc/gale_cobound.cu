@@ -85,6 +85,7 @@ struct CbMesh {
     const int32_t *eo, *ekw, *feo, *fkc, *e2s, *f2s;
     const int32_t *vt_off, *vt_val, *vv_off, *vv_val, *et_w, *et_off, *et_val;
     const int32_t *ef_off, *ef_val;  // EF, once built (VF is read from it)
+    const int32_t *ve_off, *ve_val;  // VE in VV order, once built (VF is read from it)
     const int32_t *ef_third;         // per EF entry: the triangle's vertex off the edge
     int32_t *third_out;              // where the EF fill writes those
     const int64_t *base;
@@ -182,17 +183,23 @@ __device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32
         // from the one to its smaller other vertex.  With x ascending and
         // EF rows ordered by third vertex, the sorted numbering's ids come
         // out ascending.
+        // VE(v) is still in VV(v)'s order here: entry i is the edge to the
+        // i-th neighbour
         const int32_t v = int32_t(row);
         int64_t b, e;
         vrow(m, v, true, b, e);
+        const int64_t vb = m.ve_off[v];
+        if (m.ve_off[v + 1] - vb != e - b) {
+            atomicOr(err, ERR_BAD_BLOCK);
+            return 0;
+        }
         for (int64_t j = b; j < e; ++j) {
             const int32_t x = m.vv_val[j];
-            const int64_t p = v < x ? epos(m, v, x) : epos(m, x, v);
-            if (p < 0) {
+            const int32_t id = m.ve_val[vb + (j - b)];
+            if (id < 0) {
                 atomicOr(err, ERR_BAD_BLOCK);
                 return n;
             }
-            const int32_t id = edge_id(m, p);
             const int32_t fb = m.ef_off[id], fe = m.ef_off[id + 1];
             if (!out) {
                 n += fe - fb;  // halved below: each triangle is met twice
@@ -311,7 +318,8 @@ __global__ void __launch_bounds__(kThreads) cb_fill(CbMesh m, int64_t rows, cons
             atomicOr(err, ERR_BAD_BLOCK);
             continue;
         }
-        const bool need_sort = REL == REL_VF || REL == REL_EF || (REL == REL_VE && !m.sorted_ids);
+        // VE stays in VV order until VF has read it (cb_sort_rows sorts it)
+        const bool need_sort = REL == REL_VF || REL == REL_EF;
         if (need_sort)  // ids found by lookup: sort the row (insertion sort)
             for (int32_t i = 1; i < n; ++i) {
                 const int32_t x = o[i];
@@ -325,6 +333,23 @@ __global__ void __launch_bounds__(kThreads) cb_fill(CbMesh m, int64_t rows, cons
                 o[j + 1] = x;
                 if (ax) ax[j + 1] = y;
             }
+    }
+}
+
+// sort every row of a CSR relation in place (insertion sort; rows are short)
+__global__ void __launch_bounds__(kThreads) cb_sort_rows(int64_t rows, const int32_t *off, int32_t *val) {
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
+        int32_t *o = val + off[r];
+        const int32_t n = off[r + 1] - off[r];
+        for (int32_t i = 1; i < n; ++i) {
+            const int32_t x = o[i];
+            int32_t j = i - 1;
+            while (j >= 0 && o[j] > x) {
+                o[j + 1] = o[j];
+                --j;
+            }
+            o[j + 1] = x;
+        }
     }
 }
 
@@ -539,7 +564,7 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     CbMesh m{reinterpret_cast<const int4 *>(cb.rows), cb.cluster_of, ctx->d_I_V, cb.E, cb.F, cb.ebk, cb.fbk,
              cb.IE, cb.IF, cb.eo, cb.ekw, cb.feo, cb.fkc, cb.e2s, cb.f2s,
              ctx->bulk[B_VT_OFF], ctx->bulk[B_VT_VAL], ctx->bulk[B_VV_OFF], ctx->bulk[B_VV_VAL],
-             ctx->bulk[B_ET_W], ctx->bulk[B_ET_OFF], ctx->bulk[B_ET_VAL], nullptr, nullptr, nullptr, nullptr, cb.base, ctx->d_sizes,
+             ctx->bulk[B_ET_W], ctx->bulk[B_ET_OFF], ctx->bulk[B_ET_VAL], nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cb.base, ctx->d_sizes,
              hm.nv, nE, nF, cb.sorted_ids};
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
     auto grid_for = [&](int64_t n) {
@@ -598,13 +623,16 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     m.f2s = cb.f2s;
     m.sorted_ids = cb.sorted_ids;
     const int64_t rows_of[4] = {hm.nv, hm.nv, nE, nF};
-    // VF is read from EF: EF first, and built whenever VF is asked for
-    const uint32_t build = which | ((which & GALE_CB_VF) ? uint32_t(GALE_CB_EF) : 0u);
+    // VF is read from VE (in VV order) and EF: those two first, and built
+    // whenever VF is asked for
+    const uint32_t build = which | ((which & GALE_CB_VF) ? uint32_t(GALE_CB_VE | GALE_CB_EF) : 0u);
     m.ef_off = nullptr;
     m.ef_val = nullptr;
+    m.ve_off = nullptr;
+    m.ve_val = nullptr;
     m.ef_third = nullptr;
     m.third_out = nullptr;
-    for (int rel : {int(REL_EF), int(REL_VF), int(REL_VE), int(REL_FT)}) {
+    for (int rel : {int(REL_VE), int(REL_EF), int(REL_VF), int(REL_FT)}) {
         if (!(build & (1u << rel))) continue;
         const int64_t n = rows_of[rel];
         const int64_t nb = (n + kThreads - 1) / kThreads;
@@ -653,7 +681,14 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
             m.ef_val = cb.val[REL_EF];
             m.ef_third = cb.ef_third;
         }
+        if (rel == REL_VE) {
+            m.ve_off = cb.off[REL_VE];
+            m.ve_val = cb.val[REL_VE];
+        }
     }
+    // VE rows are ascending already with the sorted numbering
+    if ((build & GALE_CB_VE) && !cb.sorted_ids && hm.nv > 0)
+        cb_sort_rows<<<grid_for(hm.nv), kThreads, 0, s>>>(hm.nv, cb.off[REL_VE], cb.val[REL_VE]);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GALE_ECUDA, "cudaStreamSynchronize");
     int32_t e = 0;
     cudaMemcpy(&e, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
