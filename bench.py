@@ -441,12 +441,25 @@ def serve_leg(args, mesh, ctx, gale):
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "wall_s": st["wall"], "tets_per_s": tets / st["wall"], "d2h_bytes": st["d2h_bytes"]}
 
+    def breakdown(s, st):
+        """Mean waiting time per request by stage, the stages of the paper's
+        breakdown (Section 5.3): enqueue, in queue, preparation, device
+        (kernel), copy to host, integration; plus the request's whole wait."""
+        n = max(1, int(s.requests))
+        us = lambda ns: ns / n / 1e3
+        return {"per_request_us": {"enqueue": us(s.t_enqueue_ns), "in_queue": us(s.t_queue_ns),
+                                   "preparation": us(s.t_prepare_ns), "device": us(s.t_build_ns),
+                                   "copy_to_host": st["copy_s"] * 1e6 / n, "integration": st["integrate_s"] * 1e6 / n,
+                                   "request_wait": us(s.t_wait_ns)},
+                "max_request_wait_ms": s.max_wait_ns / 1e6}
+
     ctx.serve_configure(gale.SERVE_LOOP)
     cls, lat, st = consumers.serve_run(ctx, f_c, inid, rows, I_V, nthreads=args.serve_threads, mask=mask)
     loop = summarize(lat, st, ctx.K)
     s = ctx.serve_stats()
     loop.update({"builds": s.builds, "hits": s.hits, "evictions": s.evictions, "loop_launches": s.batches,
-                 "critical_points": {str(c): int((cls == c).sum()) for c in (0, 1, 2, 3, 4)}})
+                 "critical_points": {str(c): int((cls == c).sum()) for c in (0, 1, 2, 3, 4)},
+                 "wait_breakdown": breakdown(s, st)})
     # proactive prefetch (Section 4.5): each request also queues the next
     # clusters, which the kd-order walks request next
     pref = None
@@ -458,7 +471,8 @@ def serve_leg(args, mesh, ctx, gale):
             sp = cp.serve_stats()
             pref.update({"prefetch_depth": args.serve_prefetch, "builds": sp.builds, "hits": sp.hits,
                          "prefetches": sp.prefetches, "prefetch_hits": sp.prefetch_hits,
-                         "prefetch_dropped": sp.prefetch_dropped, "evictions": sp.evictions})
+                         "prefetch_dropped": sp.prefetch_dropped, "evictions": sp.evictions,
+                         "wait_breakdown": breakdown(sp, stp)})
     # LRU stress: the same walk under a small budget, so finished clusters
     # are evicted to admit new ones
     stress = None
@@ -469,7 +483,7 @@ def serve_leg(args, mesh, ctx, gale):
             stress = summarize(lats, sts, cs.K)
             ss = cs.serve_stats()
             stress.update({"budget_gb": args.serve_stress_gb, "builds": ss.builds, "hits": ss.hits,
-                           "evictions": ss.evictions})
+                           "evictions": ss.evictions, "wait_breakdown": breakdown(ss, sts)})
     base = None
     nb = min(args.serve_baseline_clusters, ctx.K)
     if nb > 0:
@@ -479,6 +493,7 @@ def serve_leg(args, mesh, ctx, gale):
                                                max_clusters=nb)
             base = summarize(lat2, st2, nb)
             base["clusters"] = nb
+            base["wait_breakdown"] = breakdown(c2.serve_stats(), st2)
         # the same subset through the loop, fresh cache
         with gale.Context.load(mesh, device=0, cache_budget_bytes=int(args.serve_budget_gb * (1 << 30))) as c3:
             c3.serve_configure(gale.SERVE_LOOP)
@@ -486,6 +501,7 @@ def serve_leg(args, mesh, ctx, gale):
                                                max_clusters=nb)
             loop_sub = summarize(lat3, st3, nb)
             loop_sub["clusters"] = nb
+            loop_sub["wait_breakdown"] = breakdown(c3.serve_stats(), st3)
     return {"workload": f"{args.serve_threads} critical-point consumer threads, kd-order walks with 10% random "
                         f"jumps, VT+VV+TT requests, {args.serve_budget_gb:g} GB cache budget, field = 16 Gaussians",
             "device_loop": loop, "device_loop_prefetch": pref, "device_loop_lru_stress": stress,

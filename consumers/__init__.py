@@ -85,19 +85,20 @@ def classify_cluster(f_c, inid_c, rows, v0, vt_off, vt_val, vv_off, vv_val) -> n
 def serve_run(ctx, f_c, inid_c, rows, I_V, nthreads=16, mask=15, seed=6, jump_prob=0.1, max_clusters=None):
     """Run the serving driver over clusters [0, max_clusters) (all by
     default); returns (codes int8[nv], latencies float64[K],
-    dict(wall, requests, d2h_bytes, failures))."""
+    dict(wall, requests, d2h_bytes, failures, copy_s, integrate_s))."""
     lib = _load()
     K = len(I_V) - 1
     if max_clusters is not None:
         K = min(K, int(max_clusters))
     cls = np.full(len(f_c), -9, np.int8)
     lat = np.zeros(K, np.float64)
-    st = np.zeros(4, np.float64)
+    st = np.zeros(6, np.float64)
     I_V = np.ascontiguousarray(I_V, dtype=np.int64)
     rows = np.ascontiguousarray(rows, dtype=np.int32)
     lib.gale_cp_serve_run(ctx._h, _p(f_c), _p(inid_c), _p(rows), _p(I_V), K, nthreads, mask, seed, jump_prob,
                           _p(cls), _p(lat), _p(st))
-    return cls, lat, {"wall": st[0], "requests": int(st[1]), "d2h_bytes": int(st[2]), "failures": int(st[3])}
+    return cls, lat, {"wall": st[0], "requests": int(st[1]), "d2h_bytes": int(st[2]), "failures": int(st[3]),
+                      "copy_s": float(st[4]), "integrate_s": float(st[5])}
 
 
 def open_loop(ctxs, mi, ks, masks, rate=None, seed=0, workers=64):

@@ -104,7 +104,9 @@ int gale_cp_classify(const float *f, const int32_t *inid, const int32_t *rows, i
  *   f, inid, rows, I_V   host arrays in canonical order
  *   cls                  int8[nv] out (canonical order)
  *   lat                  double[K] out: seconds from request to view
- *   stats                double[4] out: wall seconds, requests, bytes D2H, failures
+ *   stats                double[6] out: wall seconds, requests, bytes D2H, failures,
+ *                        and summed over requests the seconds of the copy to host
+ *                        and of the classification (the paper's "data integration")
  */
 int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const int32_t *rows, const int64_t *I_V,
                       int32_t K, int32_t nthreads, uint32_t mask, uint64_t seed, double jump_prob, int8_t *cls,
@@ -113,7 +115,7 @@ int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const 
     std::vector<std::atomic<uint8_t>> claimed(static_cast<size_t>(K));
     for (auto &c : claimed) c.store(0);
     std::atomic<int32_t> next_start{0};
-    std::atomic<int64_t> done{0}, fails{0}, bytes{0};
+    std::atomic<int64_t> done{0}, fails{0}, bytes{0}, copy_ns{0}, use_ns{0};
     const uint32_t m = mask | GALE_VT | GALE_VV;
     auto t0 = std::chrono::steady_clock::now();
     auto worker = [&](int tid) {
@@ -154,7 +156,8 @@ int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const 
                 fails++;
                 continue;
             }
-            lat[k] = std::chrono::duration<double>(std::chrono::steady_clock::now() - r0).count();
+            const auto r1 = std::chrono::steady_clock::now();
+            lat[k] = std::chrono::duration<double>(r1 - r0).count();
             const int32_t nvo = v.v_end - v.v_begin;
             // offsets first, then values
             const size_t need = size_t(2 * (nvo + 1));
@@ -180,9 +183,13 @@ int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const 
             cudaStreamSynchronize(st);
             bytes += 4 * int64_t(need2);
             gale_release(ctx, &v);
+            const auto r2 = std::chrono::steady_clock::now();
             if (gale_cp_classify(f, inid, rows, int32_t(I_V[k]), nvo, pin, pin + need, pin + nvo + 1,
                                  pin + need + nvt, cls + I_V[k]) != 0)
                 fails++;
+            const auto r3 = std::chrono::steady_clock::now();
+            copy_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(r2 - r1).count();
+            use_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(r3 - r2).count();
             done++;
         }
         if (pin) cudaFreeHost(pin);
@@ -195,6 +202,8 @@ int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const 
     stats[1] = double(done.load());
     stats[2] = double(bytes.load());
     stats[3] = double(fails.load());
+    stats[4] = 1e-9 * double(copy_ns.load());
+    stats[5] = 1e-9 * double(use_ns.load());
     return 0;
 }
 

@@ -150,6 +150,15 @@ typedef struct {
     int64_t prefetches;        /* entries built ahead of any request (proactive prefetch) */
     int64_t prefetch_hits;     /* requests served by such an entry, ready or in flight */
     int64_t prefetch_dropped;  /* prefetches dropped because the budget was pinned */
+    int64_t leases_expired;    /* pins revoked because their lease ran out (gale_serve_set_lease) */
+    /* Waiting time by stage (the stages of Section 5.3's breakdown), in
+     * nanoseconds summed over requests or over entries built for a request: */
+    int64_t t_enqueue_ns;      /* per request: taking the serving lock, finding or queueing its entry */
+    int64_t t_queue_ns;        /* per built entry: queued until admitted (budget, ring space, leader) */
+    int64_t t_prepare_ns;      /* per built entry: admission, slot placement, publication or launch */
+    int64_t t_build_ns;        /* per built entry: on the device until the leader saw it done */
+    int64_t t_wait_ns;         /* per request: from the call to its return */
+    int64_t max_wait_ns;       /* the longest single request */
 } gale_serve_stats;
 
 /*
@@ -287,8 +296,17 @@ enum {
  * of the other bins are built by batched launches beside it. */
 gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, int32_t loop_ctas, int32_t prefetch);
 
-/* Unpin a view from gale_request; its entry becomes evictable. */
+/* Unpin a view from gale_request; its entry becomes evictable.  The view's
+ * handle names its pin, not the entry: releasing a view twice, or after its
+ * lease ran out, returns ENOTFOUND and touches nothing. */
 gale_status gale_release(gale_ctx *ctx, gale_view *view);
+
+/* Lease of the pins that later gale_request calls hand out: a view not
+ * released within lease_ns nanoseconds is unpinned by the serving leader
+ * (its entry becomes evictable, leases_expired counts it), so a consumer
+ * thread that dies holding views cannot keep the budget pinned.  0 (the
+ * default) = no limit.  A consumer must not read a view after its lease. */
+gale_status gale_serve_set_lease(gale_ctx *ctx, int64_t lease_ns);
 
 /* Serving counters (requests, hits, builds, evictions, ...). */
 gale_status gale_serve_stats_get(gale_ctx *ctx, gale_serve_stats *out);

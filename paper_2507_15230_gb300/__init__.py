@@ -74,7 +74,9 @@ class Info(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("requests", "hits", "misses", "builds", "evictions", "batches",
                                               "cache_bytes_used", "cache_bytes_budget", "max_batch", "prefetches",
-                                              "prefetch_hits", "prefetch_dropped")]
+                                              "prefetch_hits", "prefetch_dropped", "leases_expired",
+                                              "t_enqueue_ns", "t_queue_ns", "t_prepare_ns", "t_build_ns",
+                                              "t_wait_ns", "max_wait_ns")]
 
 
 # the symbols include/gale.h declares
@@ -82,7 +84,7 @@ EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc
            "gale_bulk_export", "gale_build_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
            "gale_autotune", "gale_get_bins", "gale_get_bin_members", "gale_enumerate", "gale_get_enumeration",
-           "gale_boundary", "gale_build_coboundary", "gale_serve_configure", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
+           "gale_boundary", "gale_build_coboundary", "gale_serve_configure", "gale_serve_set_lease", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
 
 _lib = None
 
@@ -126,6 +128,7 @@ def load_library(build: bool = True):
     lib.gale_build_coboundary.argtypes = [P, u32, ctypes.POINTER(Coboundary)]
     lib.gale_get_bins.argtypes = [P, P, i32, ctypes.POINTER(i32)]
     lib.gale_serve_configure.argtypes = [P, i32, i64, i32, i32]
+    lib.gale_serve_set_lease.argtypes = [P, i64]
     lib.gale_stream.argtypes = [P]
     lib.gale_stream.restype = P
     lib.gale_last_launch_count.argtypes = [P]
@@ -364,6 +367,10 @@ class Context:
     def serve_configure(self, mode: int, idle_us: int = 0, loop_ctas: int = 0, prefetch: int = 0):
         """gale_serve_configure (before the first request)."""
         _check(self._lib.gale_serve_configure(self._h, mode, idle_us, loop_ctas, prefetch))
+
+    def serve_set_lease(self, lease_ns: int):
+        """gale_serve_set_lease: pins of later requests expire after lease_ns (0: never)."""
+        _check(self._lib.gale_serve_set_lease(self._h, int(lease_ns)))
 
     def release(self, view: View):
         _check(self._lib.gale_release(self._h, ctypes.byref(view)))

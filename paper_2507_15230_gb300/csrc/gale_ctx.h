@@ -100,6 +100,7 @@ struct gale_ctx {
     int64_t serve_idle_us = 0;
     int32_t serve_loop_ctas = 0;      // 0: as many as fit
     int32_t serve_prefetch = 0;       // clusters queued ahead of each request
+    int64_t serve_lease_ns = 0;       // 0: pins never expire
 
     void *dalloc(size_t bytes);
     void dfree(void *p);

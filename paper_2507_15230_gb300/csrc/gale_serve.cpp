@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -47,6 +48,11 @@ namespace {
 constexpr int32_t kRingCap = 4096;
 constexpr int64_t kAlign = 256;
 
+inline int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
 enum class St { Queued, Building, Ready, Failed };
 
 struct Entry {
@@ -63,6 +69,13 @@ struct Entry {
     bool in_lru = false;
     bool prefetch = false;  // queued ahead of any request
     bool claimed = false;   // a request has used it
+    int64_t t_queued = 0, t_admitted = 0, t_published = 0;  // steady-clock ns of each stage
+};
+
+// one view handed out by gale_request
+struct Pin {
+    Entry *e;
+    int64_t deadline;  // steady-clock ns; INT64_MAX without a lease
 };
 
 // first-fit allocator over [0, cap) with a coalescing free list
@@ -119,6 +132,10 @@ struct Serve {
     bool stop = false;
     std::thread leader;
     gale_serve_stats stats{};
+    std::unordered_map<uint64_t, Pin> pins;  // handle -> pinned entry
+    uint64_t next_pin = 1;
+    int64_t lease_ns = 0;
+    int64_t next_lease_scan = 0;
 
     // device loop (clusters of the bins it covers; the others are batched)
     bool loop_mode = true;
@@ -163,6 +180,8 @@ struct Serve {
     void launch_batch(std::vector<Entry *> &b);
     void poll_batch();
     void evict_for(int64_t bytes);
+    bool expire_leases();
+    void stage_done(Entry *e);
     int64_t entry_bytes(int32_t k, uint32_t mask, int64_t *L);
 };
 
@@ -208,6 +227,7 @@ gale_status Serve::init(gale_ctx *c) {
     loop_mode = fits && (ctx->serve_mode < 0 || ctx->serve_mode == GALE_SERVE_LOOP);
     single_mode = ctx->serve_mode == GALE_SERVE_SINGLE;
     if (ctx->serve_idle_us > 0) idle_ns = uint64_t(std::max<int64_t>(100, ctx->serve_idle_us)) * 1000ull;
+    lease_ns = ctx->serve_lease_ns;
     auto ck = [](cudaError_t e) { return e == cudaSuccess; };
     if (!ck(cudaHostAlloc(reinterpret_cast<void **>(&h_items), sizeof(WorkItem) * kRingCap, cudaHostAllocMapped)) ||
         !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_tail), 64, cudaHostAllocMapped)) ||
@@ -293,7 +313,39 @@ bool Serve::admit(Entry *e) {
     e->off = off;
     e->bytes = bytes;
     fill_item(e);
+    e->t_admitted = now_ns();
+    if (!e->prefetch) stats.t_queue_ns += e->t_admitted - e->t_queued;
     return true;
+}
+
+// an entry's build finished: it joins the LRU list
+void Serve::stage_done(Entry *e) {
+    e->state = St::Ready;
+    lru.push_front(e);
+    e->lru = lru.begin();
+    e->in_lru = true;
+    stats.builds++;
+    if (!e->prefetch) stats.t_build_ns += now_ns() - e->t_published;
+}
+
+// revoke the pins whose lease ran out; true if any was
+bool Serve::expire_leases() {
+    if (lease_ns <= 0 || pins.empty()) return false;
+    const int64_t now = now_ns();
+    if (now < next_lease_scan) return false;
+    next_lease_scan = now + std::min<int64_t>(lease_ns / 4 + 1, 1000000);
+    bool any = false;
+    for (auto it = pins.begin(); it != pins.end();) {
+        if (it->second.deadline <= now) {
+            it->second.e->refs--;
+            stats.leases_expired++;
+            it = pins.erase(it);
+            any = true;
+        } else {
+            ++it;
+        }
+    }
+    return any;
 }
 
 void Serve::fill_item(Entry *e) {
@@ -331,6 +383,8 @@ void Serve::publish_loop(Entry *e) {
     published = t + 1;
     e->ticket = t;
     e->state = St::Building;
+    e->t_published = now_ns();
+    if (!e->prefetch) stats.t_prepare_ns += e->t_published - e->t_admitted;
     inflight[t] = e;
     if (!loop_launched || cudaEventQuery(loop_event) == cudaSuccess) {
         // (re)start the loop; a previous one has drained or never ran
@@ -347,12 +401,7 @@ void Serve::poll_loop() {
     for (auto it = inflight.begin(); it != inflight.end();) {
         const long long t = it->first;
         if (__atomic_load_n(h_done + (t % kRingCap), __ATOMIC_ACQUIRE) == t) {
-            Entry *e = it->second;
-            e->state = St::Ready;
-            lru.push_front(e);
-            e->lru = lru.begin();
-            e->in_lru = true;
-            stats.builds++;
+            stage_done(it->second);
             it = inflight.erase(it);
         } else {
             ++it;
@@ -408,7 +457,12 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
         return;
     }
     cudaEventRecord(batch_event, batch_stream);
-    for (Entry *e : b) e->state = St::Building;
+    const int64_t tp = now_ns();
+    for (Entry *e : b) {
+        e->state = St::Building;
+        e->t_published = tp;
+        if (!e->prefetch) stats.t_prepare_ns += tp - e->t_admitted;
+    }
     batch_entries = b;
     batch_busy = true;
     stats.batches++;
@@ -416,13 +470,7 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
 
 void Serve::poll_batch() {
     if (!batch_busy || cudaEventQuery(batch_event) != cudaSuccess) return;
-    for (Entry *e : batch_entries) {
-        e->state = St::Ready;
-        lru.push_front(e);
-        e->lru = lru.begin();
-        e->in_lru = true;
-        stats.builds++;
-    }
+    for (Entry *e : batch_entries) stage_done(e);
     batch_entries.clear();
     batch_busy = false;
 }
@@ -431,7 +479,7 @@ void Serve::leader_loop() {
     cudaSetDevice(ctx->device);
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
-        bool progressed = false;
+        bool progressed = expire_leases();
         // admission, in arrival order
         std::vector<Entry *> batch;
         while (!queue.empty()) {
@@ -556,7 +604,17 @@ void fill_view(gale_ctx *ctx, Entry *e, gale_view *out) {
     out->et_val = w.et_val;
     out->tt_off = w.tt_off;
     out->tt_val = w.tt_val;
-    out->handle = reinterpret_cast<uint64_t>(e);
+}
+
+// hand out a pin of e (whose refs the caller has already counted)
+void issue(gale_ctx *ctx, gale::Serve *s, Entry *e, gale_view *out, int64_t t0) {
+    fill_view(ctx, e, out);
+    const uint64_t id = s->next_pin++;
+    const int64_t now = gale::now_ns();
+    s->pins[id] = gale::Pin{e, s->lease_ns > 0 ? now + s->lease_ns : INT64_MAX};
+    out->handle = id;
+    s->stats.t_wait_ns += now - t0;
+    s->stats.max_wait_ns = std::max<int64_t>(s->stats.max_wait_ns, now - t0);
 }
 
 }  // namespace
@@ -572,6 +630,7 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
     gale_status st = ensure_serve(ctx);
     if (st != GALE_OK) return st;
     gale::Serve *s = ctx->serve;
+    const int64_t t0 = gale::now_ns();
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns > 0 ? timeout_ns : 0);
     std::unique_lock<std::mutex> lk(s->mu);
     s->stats.requests++;
@@ -590,7 +649,8 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
         s->stats.hits++;
         e->refs++;
         s->lru.splice(s->lru.begin(), s->lru, e->lru);
-        fill_view(ctx, e, out);
+        s->stats.t_enqueue_ns += gale::now_ns() - t0;
+        issue(ctx, s, e, out, t0);
         return GALE_OK;
     }
     if (!e) {
@@ -599,10 +659,12 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
         ne->k = cluster_id;
         ne->mask = mask;
         e = ne.get();
+        e->t_queued = gale::now_ns();
         s->entries[int64_t(cluster_id) * 16 + mask] = std::move(ne);
         s->queue.push_back(e);
         s->cv_leader.notify_all();
     }
+    s->stats.t_enqueue_ns += gale::now_ns() - t0;
     // proactive prefetch: the following clusters, queued behind the request
     for (int32_t j = 1; j <= ctx->serve_prefetch && cluster_id + j < ctx->hm.K; ++j) {
         const int32_t kk = cluster_id + j;
@@ -617,6 +679,7 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
         pe->k = kk;
         pe->mask = mask;
         pe->prefetch = true;
+        pe->t_queued = gale::now_ns();
         s->queue.push_back(pe.get());
         s->entries[int64_t(kk) * 16 + mask] = std::move(pe);
         s->stats.prefetches++;
@@ -626,6 +689,7 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
     if (timeout_ns > 0) {
         if (!s->cv_done.wait_until(lk, deadline, ready)) {
             e->refs--;
+            s->stats.t_wait_ns += gale::now_ns() - t0;
             return fail(GALE_ETIMEOUT, "request timed out");
         }
     } else {
@@ -638,7 +702,7 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
         return fail(f, f == GALE_ENOMEM ? "cluster relations exceed the whole cache budget"
                                         : "launching the cluster's build failed");
     }
-    fill_view(ctx, e, out);
+    issue(ctx, s, e, out, t0);
     return GALE_OK;
 }
 
@@ -647,11 +711,10 @@ gale_status gale_release(gale_ctx *ctx, gale_view *view) {
     if (!ctx->serve || view->handle == 0) return fail(GALE_ENOTFOUND, "not a serving view");
     gale::Serve *s = ctx->serve;
     std::lock_guard<std::mutex> lk(s->mu);
-    Entry *e = reinterpret_cast<Entry *>(view->handle);
-    auto it = s->entries.find(int64_t(e->k) * 16 + e->mask);
-    if (it == s->entries.end() || it->second.get() != e || e->refs <= 0)
-        return fail(GALE_ENOTFOUND, "view is not pinned");
-    e->refs--;
+    auto it = s->pins.find(view->handle);
+    if (it == s->pins.end()) return fail(GALE_ENOTFOUND, "view is not pinned (released, or its lease ran out)");
+    it->second.e->refs--;
+    s->pins.erase(it);
     view->handle = 0;
     s->cv_leader.notify_all();  // a pinned budget may have freed up
     return GALE_OK;
@@ -673,6 +736,18 @@ gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, i
     ctx->serve_idle_us = idle_us;
     ctx->serve_loop_ctas = loop_ctas;
     ctx->serve_prefetch = prefetch;
+    return GALE_OK;
+}
+
+gale_status gale_serve_set_lease(gale_ctx *ctx, int64_t lease_ns) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (lease_ns < 0) return fail(GALE_EINVAL, "lease_ns must be >= 0");
+    std::lock_guard<std::mutex> lk(g_serve_init_mu);
+    ctx->serve_lease_ns = lease_ns;
+    if (ctx->serve) {
+        std::lock_guard<std::mutex> lk2(ctx->serve->mu);
+        ctx->serve->lease_ns = lease_ns;
+    }
     return GALE_OK;
 }
 

@@ -289,3 +289,69 @@ def test_prefetch_is_dropped_under_a_pinned_budget():
             ctx.release(v)
         v = ctx.request(1, gale.ALL, timeout_ns=5_000_000_000)
         ctx.release(v)
+
+
+def test_lease_unpins_the_views_of_a_dead_consumer():
+    """A consumer thread that exits holding views (the failure is made on the
+    host: the thread simply ends) does not keep the budget pinned once the
+    lease runs out; its stale views can no longer be released."""
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0) as probe:
+        sz = [entry_bytes(probe, k) for k in range(3)]
+    budget = sz[0] + sz[1] + min(sz[2], min(sz[0], sz[1])) // 2  # two fit, not three
+    with gale.Context.load(m, device=0, cache_budget_bytes=budget) as ctx:
+        ctx.serve_set_lease(300_000_000)  # 0.3 s
+        dead = {}
+
+        def consumer():
+            dead["a"] = ctx.request(0, gale.ALL, timeout_ns=10_000_000_000)
+            dead["b"] = ctx.request(1, gale.ALL, timeout_ns=10_000_000_000)
+            # ends without gale_release
+
+        t = threading.Thread(target=consumer)
+        t.start()
+        t.join(timeout=30)
+        assert "b" in dead
+        v = ctx.request(2, gale.ALL, timeout_ns=20_000_000_000)  # admitted once the lease has run out
+        ctx.release(v)
+        st = ctx.serve_stats()
+        assert st.leases_expired >= 2 and st.evictions >= 1
+        for stale in (dead["a"], dead["b"]):
+            with pytest.raises(gale.GaleError) as ei:
+                ctx.release(stale)
+            assert gale.STATUS[ei.value.status] == "ENOTFOUND"
+
+
+def test_release_twice_is_rejected_without_touching_the_entry():
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0, cache_budget_bytes=8 << 20) as ctx:
+        v = ctx.request(5, gale.VT | gale.VV, timeout_ns=10_000_000_000)
+        copy = gale.View.from_buffer_copy(v)
+        w = ctx.request(5, gale.VT | gale.VV, timeout_ns=10_000_000_000)  # a second pin of the same entry
+        ctx.release(v)
+        with pytest.raises(gale.GaleError) as ei:
+            ctx.release(copy)  # the same pin again
+        assert gale.STATUS[ei.value.status] == "ENOTFOUND"
+        ctx.release(w)  # the other pin is still valid
+        with pytest.raises(gale.GaleError):
+            ctx.serve_set_lease(-1)
+
+
+def test_wait_breakdown_is_consistent():
+    """The per-stage waiting times (Section 5.3's breakdown) are non-negative
+    and bounded by the requests' total wait."""
+    import consumers
+    m = gen.small_grid(with_field=True)
+    with gale.Context.load(m, device=0, cache_budget_bytes=64 << 20) as ctx:
+        vperm, _ = ctx.permutations()
+        f_c, inid = consumers.canonical_inputs(m.field, vperm)
+        I_V, _, _ = ctx.intervals()
+        _, lat, st = consumers.serve_run(ctx, f_c, inid, ctx.rows(), I_V, nthreads=4,
+                                         mask=gale.VT | gale.VV | gale.TT)
+        s = ctx.serve_stats()
+        parts = (s.t_enqueue_ns, s.t_queue_ns, s.t_prepare_ns, s.t_build_ns)
+        assert all(p >= 0 for p in parts) and s.t_build_ns > 0
+        assert s.t_queue_ns + s.t_prepare_ns + s.t_build_ns <= s.t_wait_ns + 1_000_000
+        assert 0 < s.max_wait_ns <= s.t_wait_ns
+        assert abs(s.t_wait_ns * 1e-9 - float(lat.sum())) < 0.5 * float(lat.sum()) + 0.05
+        assert st["copy_s"] > 0 and st["integrate_s"] > 0
