@@ -355,3 +355,21 @@ def test_wait_breakdown_is_consistent():
         assert 0 < s.max_wait_ns <= s.t_wait_ns
         assert abs(s.t_wait_ns * 1e-9 - float(lat.sum())) < 0.5 * float(lat.sum()) + 0.05
         assert st["copy_s"] > 0 and st["integrate_s"] > 0
+
+
+def test_idle_loop_wait_runs_out_and_the_context_stays_usable():
+    """The device loop's CTAs wait on the ring tail, a flag that nothing sets
+    while no request comes; that wait is bounded by the idle limit, after
+    which the loop returns by itself.  The next request relaunches it."""
+    import time
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0, cache_budget_bytes=8 << 20) as ctx:
+        ctx.serve_configure(gale.SERVE_LOOP, idle_us=2000)
+        ctx.release(ctx.request(0, gale.VT, timeout_ns=10_000_000_000))
+        first = ctx.serve_stats().batches
+        assert first >= 1
+        time.sleep(0.3)  # far past the 2 ms idle limit: the loop has returned
+        ctx.release(ctx.request(1, gale.VT, timeout_ns=10_000_000_000))
+        st = ctx.serve_stats()
+        assert st.batches == first + 1 and st.builds == 2
+        ctx.synchronize()
