@@ -449,6 +449,7 @@ def serve_leg(args, mesh, ctx, gale):
         us = lambda ns: ns / n / 1e3
         return {"per_request_us": {"enqueue": us(s.t_enqueue_ns), "in_queue": us(s.t_queue_ns),
                                    "preparation": us(s.t_prepare_ns), "device": us(s.t_build_ns),
+                                   "device_build_alone": us(s.t_kernel_ns),
                                    "copy_to_host": st["copy_s"] * 1e6 / n, "integration": st["integrate_s"] * 1e6 / n,
                                    "request_wait": us(s.t_wait_ns)},
                 "max_request_wait_ms": s.max_wait_ns / 1e6}

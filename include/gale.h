@@ -157,6 +157,8 @@ typedef struct {
     int64_t t_queue_ns;        /* per built entry: queued until admitted (budget, ring space, leader) */
     int64_t t_prepare_ns;      /* per built entry: admission, slot placement, publication or launch */
     int64_t t_build_ns;        /* per built entry: on the device until the leader saw it done */
+    int64_t t_kernel_ns;       /* per entry built by the device loop: its build alone, from the
+                                  CTA's claim to its completion (device clock) */
     int64_t t_wait_ns;         /* per request: from the call to its return */
     int64_t max_wait_ns;       /* the longest single request */
 } gale_serve_stats;

@@ -201,6 +201,7 @@ struct ServeRing {
     int32_t cap;
     int32_t pad;
     unsigned long long idle_ns;   // a CTA returns after this long without work
+    long long *times;             // [2 cap] device clock (ns) at a ticket's claim and completion
 };
 int launch_serve(const DevMesh &m, const SmemPlan &plan, const ServeRing &ring, int32_t *err, int grid, void *stream);
 int serve_ctas_per_sm(const SmemPlan &plan);

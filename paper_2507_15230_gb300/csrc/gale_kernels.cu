@@ -1006,6 +1006,7 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, S
     init_barrier<false>(&s_bar);
     uint32_t phase = 0;
     unsigned long long last = globaltimer();
+    __shared__ unsigned long long s_claim;
     for (;;) {
         if (threadIdx.x == 0) {
             long long t = -1;
@@ -1026,6 +1027,7 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, S
                 if (sleep_ns < 8192) sleep_ns *= 2;
             }
             if (t >= 0) {
+                s_claim = globaltimer();
                 const int slot = int(t % ring.cap);
                 const volatile int32_t *src = reinterpret_cast<const volatile int32_t *>(ring.items + slot);
                 int32_t *dst = reinterpret_cast<int32_t *>(&s_item);
@@ -1045,8 +1047,11 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, S
         if (!go_on) break;  // a bounded wait ran out; the slot stays not done
         __syncthreads();
         if (threadIdx.x == 0) {
+            const int slot = int(t % ring.cap);
+            ring.times[2 * slot] = (long long)s_claim;
+            ring.times[2 * slot + 1] = (long long)globaltimer();
             __threadfence_system();
-            st_release_sys(ring.done + (t % ring.cap), t);
+            st_release_sys(ring.done + slot, t);
         }
         last = globaltimer();
     }

@@ -36,6 +36,10 @@
 #include <thread>
 #include <unordered_map>
 
+#ifdef __linux__
+#include <sys/prctl.h>
+#endif
+
 #include "gale_ctx.h"
 
 namespace gale {
@@ -70,6 +74,7 @@ struct Entry {
     bool prefetch = false;  // queued ahead of any request
     bool claimed = false;   // a request has used it
     int64_t t_queued = 0, t_admitted = 0, t_published = 0;  // steady-clock ns of each stage
+    std::condition_variable cv;  // its waiters: woken when it becomes ready or fails
 };
 
 // one view handed out by gale_request
@@ -122,7 +127,6 @@ struct Slab {
 struct Serve {
     gale_ctx *ctx = nullptr;
     std::mutex mu;
-    std::condition_variable cv_done;   // entries became ready / failed
     std::condition_variable cv_leader; // work for the leader
     std::unordered_map<int64_t, std::unique_ptr<Entry>> entries;  // key = k * 16 + mask
     std::deque<Entry *> queue;           // waiting for admission
@@ -146,9 +150,10 @@ struct Serve {
     WorkItem *h_items = nullptr;   // mapped
     long long *h_tail = nullptr;   // mapped
     long long *h_done = nullptr;   // mapped [cap]
+    long long *h_times = nullptr;  // mapped [2 cap]: device clock at claim and completion
     int *h_stop = nullptr;         // mapped
     WorkItem *d_items = nullptr;
-    long long *d_tail = nullptr, *d_done = nullptr;
+    long long *d_tail = nullptr, *d_done = nullptr, *d_times = nullptr;
     int *d_stop = nullptr;
     unsigned long long *d_next = nullptr;
     int32_t *d_err = nullptr;
@@ -233,6 +238,8 @@ gale_status Serve::init(gale_ctx *c) {
         !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_tail), 64, cudaHostAllocMapped)) ||
         !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_done), sizeof(long long) * kRingCap, cudaHostAllocMapped)) ||
         !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_stop), 64, cudaHostAllocMapped)) ||
+        !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_times), sizeof(long long) * 2 * kRingCap,
+                          cudaHostAllocMapped)) ||
         !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_batch), sizeof(WorkItem) * kRingCap, cudaHostAllocDefault)) ||
         !ck(cudaHostAlloc(reinterpret_cast<void **>(&h_border), sizeof(int32_t) * kRingCap, cudaHostAllocDefault)))
         return fail(GALE_ENOMEM, "pinned host allocation for the serving ring failed");
@@ -242,7 +249,8 @@ gale_status Serve::init(gale_ctx *c) {
     if (!ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_items), h_items, 0)) ||
         !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_tail), h_tail, 0)) ||
         !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_done), h_done, 0)) ||
-        !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_stop), h_stop, 0)))
+        !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_stop), h_stop, 0)) ||
+        !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_times), h_times, 0)))
         return fail(GALE_ECUDA, "mapping the serving ring failed");
     d_next = static_cast<unsigned long long *>(ctx->dalloc(64));
     d_err = static_cast<int32_t *>(ctx->dalloc(64));
@@ -302,6 +310,7 @@ bool Serve::admit(Entry *e) {
     if (bytes > slab.cap) {
         e->state = St::Failed;
         e->fail = GALE_ENOMEM;
+        e->cv.notify_all();
         return true;
     }
     int64_t off = slab.alloc(bytes);
@@ -325,6 +334,7 @@ void Serve::stage_done(Entry *e) {
     e->lru = lru.begin();
     e->in_lru = true;
     stats.builds++;
+    e->cv.notify_all();
     if (!e->prefetch) stats.t_build_ns += now_ns() - e->t_published;
 }
 
@@ -389,7 +399,7 @@ void Serve::publish_loop(Entry *e) {
     if (!loop_launched || cudaEventQuery(loop_event) == cudaSuccess) {
         // (re)start the loop; a previous one has drained or never ran
         const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
-        ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns};
+        ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns, d_times};
         launch_serve(dm, plan, ring, d_err, grid, loop_stream);
         cudaEventRecord(loop_event, loop_stream);
         loop_launched = true;
@@ -401,7 +411,12 @@ void Serve::poll_loop() {
     for (auto it = inflight.begin(); it != inflight.end();) {
         const long long t = it->first;
         if (__atomic_load_n(h_done + (t % kRingCap), __ATOMIC_ACQUIRE) == t) {
-            stage_done(it->second);
+            Entry *e = it->second;
+            if (!e->prefetch) {
+                const int slot = int(t % kRingCap);
+                stats.t_kernel_ns += h_times[2 * slot + 1] - h_times[2 * slot];
+            }
+            stage_done(e);
             it = inflight.erase(it);
         } else {
             ++it;
@@ -410,7 +425,7 @@ void Serve::poll_loop() {
     // published work with no loop running (it drained just before): restart
     if (!inflight.empty() && loop_launched && cudaEventQuery(loop_event) == cudaSuccess) {
         const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
-        ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns};
+        ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns, d_times};
         launch_serve(dm, plan, ring, d_err, grid, loop_stream);
         cudaEventRecord(loop_event, loop_stream);
         stats.batches++;
@@ -450,6 +465,7 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
         for (Entry *e : b) {
             e->state = St::Failed;
             e->fail = GALE_ECUDA;
+            e->cv.notify_all();
             slab.release(e->off, e->bytes);
             e->bytes = 0;
         }
@@ -477,6 +493,12 @@ void Serve::poll_batch() {
 
 void Serve::leader_loop() {
     cudaSetDevice(ctx->device);
+#ifdef __linux__
+    // the leader sleeps ~10 us between polls while work is in flight (with
+    // the lock released, so requests queue meanwhile); the default 50 us
+    // timer slack would stretch every such sleep to ~60 us
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+#endif
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
         bool progressed = expire_leases();
@@ -513,10 +535,7 @@ void Serve::leader_loop() {
         if (loop_mode) poll_loop();
         poll_batch();
         const size_t after = inflight.size() + (batch_busy ? batch_entries.size() : 0);
-        if (after != before || progressed) {
-            stats.max_batch = std::max<int64_t>(stats.max_batch, int64_t(before));
-            cv_done.notify_all();
-        }
+        if (after != before || progressed) stats.max_batch = std::max<int64_t>(stats.max_batch, int64_t(before));
         stats.cache_bytes_used = slab.used;
         if (after > 0 || !queue.empty()) {
             lk.unlock();
@@ -548,6 +567,7 @@ void serve_destroy(gale_ctx *ctx) {
     cudaFreeHost(s->h_tail);
     cudaFreeHost(s->h_done);
     cudaFreeHost(s->h_stop);
+    cudaFreeHost(s->h_times);
     cudaFreeHost(s->h_batch);
     cudaFreeHost(s->h_border);
     delete s;
@@ -687,13 +707,13 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
     e->refs++;
     auto ready = [&] { return e->state == St::Ready || e->state == St::Failed; };
     if (timeout_ns > 0) {
-        if (!s->cv_done.wait_until(lk, deadline, ready)) {
+        if (!e->cv.wait_until(lk, deadline, ready)) {
             e->refs--;
             s->stats.t_wait_ns += gale::now_ns() - t0;
             return fail(GALE_ETIMEOUT, "request timed out");
         }
     } else {
-        s->cv_done.wait(lk, ready);
+        e->cv.wait(lk, ready);
     }
     if (e->state == St::Failed) {
         const gale_status f = e->fail;

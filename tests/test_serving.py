@@ -353,6 +353,7 @@ def test_wait_breakdown_is_consistent():
         assert all(p >= 0 for p in parts) and s.t_build_ns > 0
         assert s.t_queue_ns + s.t_prepare_ns + s.t_build_ns <= s.t_wait_ns + 1_000_000
         assert 0 < s.max_wait_ns <= s.t_wait_ns
+        assert 0 < s.t_kernel_ns <= s.t_build_ns + 1_000_000  # the build alone, inside the device stage
         assert abs(s.t_wait_ns * 1e-9 - float(lat.sum())) < 0.5 * float(lat.sum()) + 0.05
         assert st["copy_s"] > 0 and st["integrate_s"] > 0
 
