@@ -13,10 +13,18 @@ datasets (Section 5.1, Table 2), which are not available here:
   (Section 4.3 "Input data"); a kd-tree replaces the paper's PR octree.
 * ``gaussian_field`` - a float32 scalar field (sum of Gaussians) for the
   critical-point consumer.
+
+Generated meshes can be kept on disk so that 100M-tet inputs are not rebuilt
+on every run: with ``GALE_GEN_CACHE`` set to a directory, ``freudenthal_mesh``
+and ``delaunay_mesh`` store each mesh as ``.npz`` arrays plus a JSON header of
+the generator's parameters, and load it back when every parameter matches.
+A file that cannot be read or whose header differs is rebuilt.
 """
 from __future__ import annotations
 
 import ctypes
+import hashlib
+import json
 import os
 import subprocess
 from dataclasses import dataclass, field as dc_field
@@ -145,11 +153,55 @@ def permutation(n: int, seed: int) -> np.ndarray:
     return p
 
 
+_CACHE_FORMAT = 1
+
+
+def _cache_path(params: dict):
+    d = os.environ.get("GALE_GEN_CACHE")
+    if not d:
+        return None
+    key = hashlib.sha1(json.dumps(params, sort_keys=True).encode()).hexdigest()[:20]
+    return os.path.join(d, f"{params['kind']}-{key}.npz")
+
+
+def _cached(params: dict, make):
+    """make() -> Mesh, through the on-disk cache when GALE_GEN_CACHE is set."""
+    path = _cache_path(params)
+    if path and os.path.exists(path):
+        try:
+            with np.load(path, allow_pickle=False) as z:
+                head = json.loads(str(z["header"]))
+                if head.get("format") == _CACHE_FORMAT and head.get("params") == params:
+                    f = z["field"] if bool(head["has_field"]) else None
+                    return Mesh(z["xyz"], z["tv"], z["seg"], int(head["nclusters"]), f, head["name"],
+                                head["meta"])
+        except Exception:
+            pass  # unreadable or stale: rebuilt below
+    m = make()
+    if path:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        head = {"format": _CACHE_FORMAT, "params": params, "nclusters": m.nclusters, "name": m.name,
+                "meta": m.meta, "has_field": m.field is not None}
+        tmp = f"{path}.tmp{os.getpid()}.npz"
+        np.savez(tmp, xyz=m.xyz, tv=m.tv, seg=m.seg,
+                 field=m.field if m.field is not None else np.zeros(0, np.float32),
+                 header=np.array(json.dumps(head)))
+        os.replace(tmp, path)
+    return m
+
+
 def freudenthal_mesh(n: int, kd_cap: int, seed: int = 1, field_seed: int = 2, jitter: float = 0.0,
                      ngauss: int = 4, with_field: bool = True, name: str = "") -> Mesh:
     """Freudenthal grid, permuted ids, kd-tree leaves of <= kd_cap vertices,
     sum-of-Gaussians field.  The small workload is n=16, cap 64; the
     at-scale workload n=256, jitter 0.3, cap 512."""
+    params = {"kind": "freudenthal", "n": n, "kd_cap": kd_cap, "seed": seed, "field_seed": field_seed,
+              "jitter": jitter, "ngauss": ngauss, "with_field": with_field, "name": name}
+    return _cached(params, lambda: _freudenthal_mesh(n, kd_cap, seed, field_seed, jitter, ngauss, with_field,
+                                                     name))
+
+
+def _freudenthal_mesh(n, kd_cap, seed, field_seed, jitter, ngauss, with_field, name) -> Mesh:
     xyz, tv = freudenthal_grid(n, True, jitter, seed)
     seg, k = kdtree_partition(xyz, kd_cap)
     f = gaussian_field(xyz, ngauss, [0, 0, 0], [n, n, n], field_seed) if with_field else None
@@ -191,6 +243,14 @@ def delaunay_mesh(npts: int, seed: int, kd_cap: int = 2048, uneven: bool = True,
                   name: str = "") -> Mesh:
     """Delaunay mesh of a Gaussian-mixture point cloud with an uneven kd-tree
     partition (leaves of 32 .. 2048 vertices)."""
+    params = {"kind": "delaunay", "npts": npts, "seed": seed, "kd_cap": kd_cap, "uneven": uneven,
+              "min_leaf": min_leaf, "min_cap": min_cap, "bits": bits, "ngauss_field": ngauss_field,
+              "with_field": with_field, "name": name}
+    return _cached(params, lambda: _delaunay_mesh(npts, seed, kd_cap, uneven, min_leaf, min_cap, bits,
+                                                  ngauss_field, with_field, name))
+
+
+def _delaunay_mesh(npts, seed, kd_cap, uneven, min_leaf, min_cap, bits, ngauss_field, with_field, name) -> Mesh:
     pts = delaunay_points(npts, seed, bits=bits)
     tv = delaunay_tets(pts)
     xyz = (pts.astype(np.float64) / float(1 << bits)).astype(np.float32)
