@@ -452,7 +452,9 @@ def serve_leg(args, mesh, ctx, gale):
                                    "device_build_alone": us(s.t_kernel_ns),
                                    "copy_to_host": st["copy_s"] * 1e6 / n, "integration": st["integrate_s"] * 1e6 / n,
                                    "request_wait": us(s.t_wait_ns)},
-                "max_request_wait_ms": s.max_wait_ns / 1e6}
+                "max_request_wait_ms": s.max_wait_ns / 1e6,
+                "queue_depth_hist": {f"{1 << b}-{(2 << b) - 1}" if b < 11 else "2048+": int(s.depth_hist[b])
+                                     for b in range(12) if s.depth_hist[b]}}
 
     ctx.serve_configure(gale.SERVE_LOOP)
     cls, lat, st = consumers.serve_run(ctx, f_c, inid, rows, I_V, nthreads=args.serve_threads, mask=mask)

@@ -161,6 +161,11 @@ typedef struct {
                                   CTA's claim to its completion (device clock) */
     int64_t t_wait_ns;         /* per request: from the call to its return */
     int64_t max_wait_ns;       /* the longest single request */
+    /* Queue length (the paper's queue statistics, Section 4.5): each leader
+     * pass with work pending counts once in bucket b of the number of
+     * entries queued or in flight, b = 0 for 1, 1 for 2-3, 2 for 4-7, ...,
+     * 11 for 2048 and more. */
+    int64_t depth_hist[12];
 } gale_serve_stats;
 
 /*

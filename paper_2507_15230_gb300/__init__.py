@@ -76,7 +76,7 @@ class ServeStats(ctypes.Structure):
                                               "cache_bytes_used", "cache_bytes_budget", "max_batch", "prefetches",
                                               "prefetch_hits", "prefetch_dropped", "leases_expired",
                                               "t_enqueue_ns", "t_queue_ns", "t_prepare_ns", "t_build_ns", "t_kernel_ns",
-                                              "t_wait_ns", "max_wait_ns")]
+                                              "t_wait_ns", "max_wait_ns")] + [("depth_hist", ctypes.c_int64 * 12)]
 
 
 # the symbols include/gale.h declares

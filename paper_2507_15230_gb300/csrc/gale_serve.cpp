@@ -536,6 +536,11 @@ void Serve::leader_loop() {
         poll_batch();
         const size_t after = inflight.size() + (batch_busy ? batch_entries.size() : 0);
         if (after != before || progressed) stats.max_batch = std::max<int64_t>(stats.max_batch, int64_t(before));
+        if (const size_t pending = queue.size() + after) {
+            int b = 0;
+            while (b < 11 && (size_t(2) << b) <= pending) ++b;
+            stats.depth_hist[b]++;
+        }
         stats.cache_bytes_used = slab.used;
         if (after > 0 || !queue.empty()) {
             lk.unlock();

@@ -356,6 +356,9 @@ def test_wait_breakdown_is_consistent():
         assert 0 < s.t_kernel_ns <= s.t_build_ns + 1_000_000  # the build alone, inside the device stage
         assert abs(s.t_wait_ns * 1e-9 - float(lat.sum())) < 0.5 * float(lat.sum()) + 0.05
         assert st["copy_s"] > 0 and st["integrate_s"] > 0
+        hist = list(s.depth_hist)
+        assert sum(hist) > 0 and all(h >= 0 for h in hist)
+        assert sum(hist[5:]) == 0  # 4 consumer threads, no prefetch: never 32 or more pending
 
 
 def test_idle_loop_wait_runs_out_and_the_context_stays_usable():
