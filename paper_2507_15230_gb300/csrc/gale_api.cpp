@@ -323,6 +323,54 @@ void item_lengths(const gale_ctx *ctx, int32_t k, uint32_t mask, int64_t *L) {
     L[9] = tt ? sz[4] : 0;
 }
 
+// Launch order of listed clusters, chunk by chunk and, within a chunk, bin by
+// bin, each bin's members in the bin's largest-first order: the positions of
+// chunk c's members relative to cut[c], in order[boff[c][b] .. boff[c][b+1]).
+// One pass over the bins' member lists, no sorting (list positions are
+// pos_of[k], or k itself when the list is every cluster in id order).
+// False if some listed cluster is in no bin.
+bool chunk_bin_orders(const gale_ctx *ctx, const std::vector<int32_t> &list, bool all,
+                      const std::vector<int32_t> &cut, std::vector<int32_t> &order,
+                      std::vector<std::vector<int64_t>> &boff) {
+    const int32_t K = ctx->hm.K, cnt = int32_t(list.size());
+    const int32_t chunks = int32_t(cut.size()) - 1;
+    const size_t nb = ctx->bins.size();
+    std::vector<int32_t> pos_of;
+    if (!all) {
+        pos_of.assign(K, -1);
+        for (int32_t i = 0; i < cnt; ++i) pos_of[list[i]] = i;
+    }
+    std::vector<int32_t> chunk_of(cnt);
+    for (int32_t c = 0; c < chunks; ++c)
+        for (int32_t i = cut[c]; i < cut[c + 1]; ++i) chunk_of[i] = c;
+    std::vector<int64_t> count(size_t(chunks) * nb, 0);
+    for (size_t b = 0; b < nb; ++b)
+        for (int32_t k : ctx->bins[b].clusters) {
+            const int32_t p = all ? k : pos_of[k];
+            if (p >= 0 && p < cnt) count[size_t(chunk_of[p]) * nb + b]++;
+        }
+    boff.assign(chunks, std::vector<int64_t>(nb + 1, 0));
+    std::vector<int64_t> fill(size_t(chunks) * nb);
+    int64_t run = 0;
+    for (int32_t c = 0; c < chunks; ++c) {
+        for (size_t b = 0; b < nb; ++b) {
+            boff[c][b] = run;
+            fill[size_t(c) * nb + b] = run;
+            run += count[size_t(c) * nb + b];
+        }
+        boff[c][nb] = run;
+    }
+    order.assign(size_t(run), 0);
+    for (size_t b = 0; b < nb; ++b)
+        for (int32_t k : ctx->bins[b].clusters) {
+            const int32_t p = all ? k : pos_of[k];
+            if (p < 0 || p >= cnt) continue;
+            const int32_t c = chunk_of[p];
+            order[size_t(fill[size_t(c) * nb + b]++)] = p - cut[c];
+        }
+    return run == cnt;
+}
+
 gale_status ensure_bulk(gale_ctx *ctx, const int64_t *need) {
     bool realloc = false;
     for (int a = 0; a < 10; ++a) {
@@ -602,22 +650,14 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
             launches += cnt;
         } else {
             // partial batched build: per-bin item orders
-            std::vector<std::vector<int32_t>> per_bin(ctx->bins.size());
-            for (int32_t i = 0; i < cnt; ++i) per_bin[ctx->bin_of[list[i]]].push_back(i);
             std::vector<int32_t> order;
-            std::vector<int64_t> off(1, 0);
-            for (size_t b = 0; b < per_bin.size(); ++b) {
-                auto &v = per_bin[b];
-                std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t c) {
-                    return ctx->hm.stats[list[a]].n_own + ctx->hm.stats[list[a]].n_ext >
-                           ctx->hm.stats[list[c]].n_own + ctx->hm.stats[list[c]].n_ext;
-                });
-                order.insert(order.end(), v.begin(), v.end());
-                off.push_back(int64_t(order.size()));
-            }
+            std::vector<std::vector<int64_t>> boff;
+            if (!chunk_bin_orders(ctx, list, false, {0, cnt}, order, boff))
+                return fail(GALE_EINVAL, "a listed cluster is in no size bin");
+            const std::vector<int64_t> &off = boff[0];
             CUDA_TRY(cudaMemcpyAsync(ctx->d_order_part, order.data(), order.size() * 4, cudaMemcpyHostToDevice,
                                      ctx->stream));
-            for (size_t b = 0; b < per_bin.size(); ++b) {
+            for (size_t b = 0; b < ctx->bins.size(); ++b) {
                 const int32_t nb = int32_t(off[b + 1] - off[b]);
                 if (nb == 0) continue;
                 const gale::Bin &bin = ctx->bins[b];
@@ -766,8 +806,9 @@ gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint
     // chunk's items grouped by size bin (largest working set first)
     std::vector<WorkItem> cbase(chunks);
     std::vector<int32_t> order;
-    std::vector<std::vector<int64_t>> boff(chunks);
-    std::vector<std::vector<int32_t>> per_bin(ctx->bins.size());
+    std::vector<std::vector<int64_t>> boff;
+    if (!chunk_bin_orders(ctx, list, all, cut, order, boff))
+        return fail(GALE_EINVAL, "a listed cluster is in no size bin");
     for (int32_t c = 0; c < chunks; ++c) {
         const int32_t i0 = cut[c];
         int32_t *ptr[10];
@@ -780,19 +821,6 @@ gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint
         w.vt_off = ptr[0]; w.vt_val = ptr[1]; w.vv_off = ptr[2]; w.vv_val = ptr[3];
         w.eu_off = ptr[4]; w.e_w = ptr[5]; w.et_off = ptr[6]; w.et_val = ptr[7];
         w.tt_off = ptr[8]; w.tt_val = ptr[9];
-        for (auto &v : per_bin) v.clear();
-        for (int32_t i = i0; i < cut[c + 1]; ++i) per_bin[ctx->bin_of[list[i]]].push_back(i - i0);
-        boff[c].push_back(int64_t(order.size()));
-        for (size_t b = 0; b < per_bin.size(); ++b) {
-            // members keep the bin's largest-first order
-            auto &v = per_bin[b];
-            std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t d) {
-                return ctx->hm.stats[list[i0 + a]].n_own + ctx->hm.stats[list[i0 + a]].n_ext >
-                       ctx->hm.stats[list[i0 + d]].n_own + ctx->hm.stats[list[i0 + d]].n_ext;
-            });
-            order.insert(order.end(), v.begin(), v.end());
-            boff[c].push_back(int64_t(order.size()));
-        }
     }
     CUDA_TRY(cudaMemcpyAsync(ctx->d_ids, list.data(), size_t(cnt) * 4, cudaMemcpyHostToDevice, ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->d_order_part, order.data(), order.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
