@@ -260,7 +260,7 @@ gale_status gale_bulk_export(gale_ctx *ctx, uint32_t mask, const gale_arrays *ho
  *   host_dst  one buffer per array of mask, laid out as a bulk build lays
  *             out the device arrays (lengths as gale_bulk_arrays reports after
  *             the call); pinned memory is needed for the overlap.
- *   chunks    0 = automatic (about 256 MB of output per chunk, at most 8),
+ *   chunks    0 = automatic (about 256 MB of output per chunk, at most 16),
  *             else 1..64.
  * Afterwards the device bulk arrays hold the same result as after
  * gale_build_clusters(ctx, ids, n, mask, GALE_MODE_BATCHED).  Blocks until

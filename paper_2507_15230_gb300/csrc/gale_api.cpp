@@ -783,7 +783,9 @@ gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint
     for (int a = 0; a < 10; ++a) ctx->bulk_len[a] = run[a];
     ctx->bulk_ids = list;
     ctx->bulk_mask = mask;
-    if (chunks == 0) chunks = int32_t(std::min<int64_t>(8, std::max<int64_t>(1, bytes_before[cnt] >> 28)));
+    // automatic: one chunk per 256 MB of output, at most 16 (measured at
+    // 256^3: 16 chunks 44.4 ms, 8 chunks 44.8 ms, 4 chunks 45.7 ms)
+    if (chunks == 0) chunks = int32_t(std::min<int64_t>(16, std::max<int64_t>(1, bytes_before[cnt] >> 28)));
     chunks = std::max(1, std::min(chunks, cnt));
     std::vector<int32_t> cut(size_t(chunks) + 1, cnt);
     cut[0] = 0;
