@@ -88,3 +88,40 @@ def test_enumeration_replaced_between_calls():
             for name in ("VE", "EF"):
                 off, val = got[name]
                 assert val.tolist() == [x for r in want[name] for x in r], (oname, name)
+
+
+def transpose(idx, width, nrows):
+    """CSR (offsets, values) of the relation whose row r lists the ids i
+    with r among idx[i] (idx: int array [n, width]), rows sorted."""
+    idx = np.asarray(idx, dtype=np.int64).reshape(-1, width)
+    rows = idx.reshape(-1)
+    vals = np.repeat(np.arange(idx.shape[0], dtype=np.int64), width)
+    order = np.argsort(rows * np.int64(idx.shape[0]) + vals, kind="stable")
+    off = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=nrows))])
+    return off, vals[order]
+
+
+@pytest.mark.parametrize("order", [gale.ENUM_SORTED, gale.ENUM_FIRST_APPEARANCE])
+def test_full_size_transposes_of_boundary_relations(order):
+    """At 128^3 (12.6M tets), every row of VE, VF, EF and FT equals the
+    transpose of EV, FV (the enumeration), FE and TF (the host boundary
+    lookups), and the totals match the Freudenthal closed forms."""
+    n = 128
+    m = gen.freudenthal_mesh(n, 512, seed=3, field_seed=4, jitter=0.3, with_field=False)
+    with gale.Context.load(m, device=0) as ctx:
+        en = ctx.enumerate(order)
+        E, F = en["E"], en["F"]
+        nE, nF = E.shape[0], F.shape[0]
+        assert nE == 7 * n ** 3 + 9 * n ** 2 + 3 * n and nF == 12 * n ** 3 + 6 * n ** 2
+        cb = ctx.coboundary()
+        rows = ctx.rows()
+        fe = ctx.boundary(gale.REL_FE, np.arange(nF, dtype=np.int64))
+        tf = ctx.boundary(gale.REL_TF, np.arange(rows.shape[0], dtype=np.int64))
+    want = {"VE": transpose(E, 2, m.nv), "VF": transpose(F, 3, m.nv), "EF": transpose(fe, 3, nE),
+            "FT": transpose(tf, 4, nF)}
+    totals = {"VE": 2 * nE, "VF": 3 * nF, "EF": 3 * nF, "FT": 4 * rows.shape[0]}
+    for name, (off, val) in want.items():
+        g_off, g_val = cb[name]
+        assert g_val.size == totals[name], name
+        assert np.array_equal(g_off, off), name
+        assert np.array_equal(g_val, val), name
