@@ -37,6 +37,12 @@ struct Enumeration {
     std::vector<int64_t> I_E, I_F;   // [K+1]
     std::vector<int32_t> e_by_key;   // [nE] per segment: ids in vertex-tuple order
     std::vector<int32_t> f_by_key;   // [nF]
+    // index inside each segment's interval, over the tuple order: a vertex's
+    // upper edges and an edge's upper triangles are short runs
+    std::vector<int32_t> v_eo;       // [nv+1] first tuple position of lower vertex v
+    std::vector<int32_t> ekw;        // [nE] upper vertex of each tuple position
+    std::vector<int32_t> e_feo;      // [nE+1] first triangle tuple position over each edge
+    std::vector<int32_t> fkc;        // [nF] third vertex of each triangle tuple position
 };
 
 void enumeration_destroy(gale_ctx *ctx) {
@@ -116,39 +122,30 @@ void segment_simplices(const HostMesh &hm, int32_t k, int32_t order, std::vector
 }
 
 // global id of edge (u, w), or -1
+// tuple position of edge (u, w), u < w, or -1: a search among u's upper
+// edges, which lie inside the interval of u's segment
+int64_t edge_pos(const HostMesh &hm, const Enumeration &en, int32_t u, int32_t w) {
+    if (u < 0 || u >= hm.nv) return -1;
+    const int64_t b = en.v_eo[u], e = en.v_eo[u + 1];
+    const int32_t *p = std::lower_bound(en.ekw.data() + b, en.ekw.data() + e, w);
+    return (p != en.ekw.data() + e && *p == w) ? int64_t(p - en.ekw.data()) : -1;
+}
+
 int64_t edge_id(const HostMesh &hm, const Enumeration &en, int32_t u, int32_t w) {
     if (u > w) std::swap(u, w);
-    if (u < 0 || u >= hm.nv) return -1;
-    const int32_t k = hm.cluster_of[u];
-    int64_t lo = en.I_E[k], hi = en.I_E[k + 1];  // search the segment's ids in tuple order
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        const int32_t id = en.e_by_key[mid];
-        const int32_t a = en.E[2 * int64_t(id)], b = en.E[2 * int64_t(id) + 1];
-        if (a < u || (a == u && b < w)) lo = mid + 1;
-        else hi = mid;
-    }
-    if (lo >= en.I_E[k + 1]) return -1;
-    const int32_t id = en.e_by_key[lo];
-    return (en.E[2 * int64_t(id)] == u && en.E[2 * int64_t(id) + 1] == w) ? id : -1;
+    const int64_t j = edge_pos(hm, en, u, w);
+    return j < 0 ? -1 : en.e_by_key[j];
 }
 
 int64_t face_id(const HostMesh &hm, const Enumeration &en, std::array<int32_t, 3> f) {
     std::sort(f.begin(), f.end());
-    if (f[0] < 0 || f[0] >= hm.nv) return -1;
-    const int32_t k = hm.cluster_of[f[0]];
-    int64_t lo = en.I_F[k], hi = en.I_F[k + 1];
-    auto at = [&](int64_t i) {
-        const int32_t id = en.f_by_key[i];
-        return std::array<int32_t, 3>{en.F[3 * int64_t(id)], en.F[3 * int64_t(id) + 1], en.F[3 * int64_t(id) + 2]};
-    };
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (at(mid) < f) lo = mid + 1;
-        else hi = mid;
+    const int64_t j = edge_pos(hm, en, f[0], f[1]);
+    if (j < 0) return -1;
+    for (int64_t p = en.e_feo[j]; p < en.e_feo[j + 1]; ++p) {
+        if (en.fkc[p] == f[2]) return en.f_by_key[p];
+        if (en.fkc[p] > f[2]) break;
     }
-    if (lo >= en.I_F[k + 1] || at(lo) != f) return -1;
-    return en.f_by_key[lo];
+    return -1;
 }
 
 }  // namespace
@@ -186,6 +183,10 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
         en->F.resize(size_t(3) * size_t(en->I_F[K]));
         en->e_by_key.resize(size_t(en->I_E[K]));
         en->f_by_key.resize(size_t(en->I_F[K]));
+        en->v_eo.assign(size_t(hm.nv) + 1, int32_t(en->I_E[K]));
+        en->ekw.resize(size_t(en->I_E[K]));
+        en->e_feo.assign(size_t(en->I_E[K]) + 1, int32_t(en->I_F[K]));
+        en->fkc.resize(size_t(en->I_F[K]));
         gale::parallel_dynamic(K, gale::host_threads(0), 4, [&](int64_t k, int) {
             const int64_t e0 = en->I_E[k], f0 = en->I_F[k];
             const auto &ev = se[k];
@@ -205,6 +206,26 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
                 std::sort(eb, eb + ev.size(), [&](int32_t a, int32_t b) { return ev[a - e0] < ev[b - e0]; });
                 std::sort(fb, fb + fv.size(), [&](int32_t a, int32_t b) { return fv[a - f0] < fv[b - f0]; });
             }
+            // the index over the tuple order: one sweep over the segment's
+            // vertices, edges and triangles
+            const int64_t ne = int64_t(ev.size()), nf = int64_t(fv.size());
+            int64_t i = 0, q = 0;
+            for (int32_t v = hm.I_V[k]; v < hm.I_V[k + 1]; ++v) {
+                while (i < ne && int32_t(ev[eb[i] - e0] >> 32) < v) ++i;
+                en->v_eo[v] = int32_t(e0 + i);
+            }
+            for (i = 0; i < ne; ++i) {
+                const uint64_t key = ev[eb[i] - e0];
+                const int32_t a = int32_t(key >> 32), b = int32_t(key & 0xffffffffu);
+                en->ekw[e0 + i] = b;
+                while (q < nf) {
+                    const auto &f = fv[fb[q] - f0];
+                    if (f[0] < a || (f[0] == a && f[1] < b)) ++q;
+                    else break;
+                }
+                en->e_feo[e0 + i] = int32_t(f0 + q);
+            }
+            for (q = 0; q < nf; ++q) en->fkc[f0 + q] = fv[fb[q] - f0][2];
         });
         delete ctx->enm;
         ctx->enm = en.release();
