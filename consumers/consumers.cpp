@@ -303,7 +303,7 @@ namespace {
 
 struct LowerStar {
     // local simplices: edges [0, ne), triangles [ne, ne + nf), tets after
-    std::vector<int32_t> gid, dim, seq, nseq, open, state, in_one, face, cof_off, cof;
+    std::vector<int32_t> gid, dim, seq, nseq, open, state, in_one, face, cof_off, cof, fill;
     std::vector<int32_t> heap_one, heap_zero;
 };
 
@@ -404,11 +404,9 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
         for (int i = 0; i < L.dim[s]; ++i) L.cof_off[L.face[3 * size_t(s) + i] + 1]++;
     for (int32_t s = 0; s < ns; ++s) L.cof_off[s + 1] += L.cof_off[s];
     L.cof.assign(size_t(L.cof_off[ns]), 0);
-    {
-        std::vector<int32_t> fill(L.cof_off.begin(), L.cof_off.end() - 1);
-        for (int32_t s = ne; s < ns; ++s)
-            for (int i = 0; i < L.dim[s]; ++i) L.cof[fill[L.face[3 * size_t(s) + i]]++] = s;
-    }
+    L.fill.assign(L.cof_off.begin(), L.cof_off.end() - 1);
+    for (int32_t s = ne; s < ns; ++s)
+        for (int i = 0; i < L.dim[s]; ++i) L.cof[L.fill[L.face[3 * size_t(s) + i]]++] = s;
     // open = faces inside the lower star not yet classified
     L.open.assign(size_t(ns), 0);
     for (int32_t s = ne; s < ns; ++s) L.open[s] = L.dim[s];
