@@ -75,7 +75,7 @@ namespace {
 constexpr int kThreads = 256;
 enum { REL_VE = 0, REL_VF = 1, REL_EF = 2, REL_FT = 3 };
 // bulk array indices (the order of gale_arrays)
-enum { B_VT_OFF = 0, B_VT_VAL = 1, B_VV_OFF = 2, B_VV_VAL = 3, B_ET_W = 5, B_ET_OFF = 6, B_ET_VAL = 7 };
+enum { B_VT_OFF = 0, B_VT_VAL = 1, B_VV_OFF = 2, B_VV_VAL = 3, B_ET_UOFF = 4, B_ET_W = 5, B_ET_OFF = 6, B_ET_VAL = 7 };
 
 struct CbMesh {
     const int4 *rows;
@@ -84,6 +84,7 @@ struct CbMesh {
     const int64_t *IE, *IF;
     const int32_t *eo, *ekw, *feo, *fkc, *e2s, *f2s;
     const int32_t *vt_off, *vt_val, *vv_off, *vv_val, *et_w, *et_off, *et_val;
+    const int32_t *et_uoff;          // ET edges per own lower vertex (the sorted enumeration reads it)
     const int32_t *ef_off, *ef_val;  // EF, once built (VF is read from it)
     const int32_t *ve_off, *ve_val;  // VE in VV order, once built (VF is read from it)
     const int32_t *ef_third;         // per EF entry: the triangle's vertex off the edge
@@ -353,6 +354,101 @@ __global__ void __launch_bounds__(kThreads) cb_sort_rows(int64_t rows, const int
     }
 }
 
+// ---- sorted enumeration on the device ----
+// A segment's edges in vertex-tuple order are its cluster's ET edges (own
+// lower vertex u, then upper vertex w): E is written straight from the ET
+// rows.  Its triangles over an edge (a, b) are (a, b, c) for the distinct
+// vertices c > b of the tets of ET(a, b), ascending.
+
+// E pairs of every cluster's edges, at I_E[k] + local edge index
+__global__ void __launch_bounds__(kThreads) k_enum_edges(CbMesh m, int32_t *E) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < m.nv; v += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t k = m.cluster_of[v];
+        const int32_t i = int32_t(v) - m.I_V[k];
+        const int64_t *B = m.base + 10 * int64_t(k);
+        const int32_t e0 = m.et_uoff[B[B_ET_UOFF] + i], e1 = m.et_uoff[B[B_ET_UOFF] + i + 1];
+        for (int32_t e = e0; e < e1; ++e) {
+            const int64_t j = m.IE[k] + e;
+            E[2 * j] = int32_t(v);
+            E[2 * j + 1] = m.et_w[B[B_ET_W] + e];
+        }
+    }
+}
+
+// triangles over each edge: count (F == nullptr) or write at FS[j]
+template <bool WRITE>
+__global__ void __launch_bounds__(kThreads) k_enum_faces(CbMesh m, const int32_t *E, int32_t *nf, const int32_t *FS,
+                                                         int32_t *F, int32_t *err) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < m.nE; j += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t a = E[2 * j], b = E[2 * j + 1];
+        int64_t eb, ee;
+        if (!et_row(m, j, a, b, eb, ee)) {
+            atomicOr(err, ERR_BAD_BLOCK);
+            if (!WRITE) nf[j] = 0;
+            continue;
+        }
+        int32_t n = 0;
+        int64_t out = WRITE ? FS[j] : 0;
+        const int64_t cap = WRITE ? FS[j + 1] - FS[j] : 0;
+        constexpr int kCand = 32;
+        if (ee - eb <= kCand / 2) {
+            int32_t xs[kCand];
+            int c = 0;
+            for (int64_t q = eb; q < ee; ++q) {
+                const int4 r = m.rows[m.et_val[q]];
+#pragma unroll
+                for (int s2 = 0; s2 < 4; ++s2) {
+                    const int32_t x = s2 == 0 ? r.x : s2 == 1 ? r.y : s2 == 2 ? r.z : r.w;
+                    if (x <= b || c >= kCand) continue;
+                    int p = c++;
+                    while (p > 0 && xs[p - 1] > x) {
+                        xs[p] = xs[p - 1];
+                        --p;
+                    }
+                    xs[p] = x;
+                }
+            }
+            for (int p = 0; p < c; ++p) {
+                if (p > 0 && xs[p] == xs[p - 1]) continue;
+                if (WRITE && n < cap) {
+                    F[3 * (out + n)] = a;
+                    F[3 * (out + n) + 1] = b;
+                    F[3 * (out + n) + 2] = xs[p];
+                }
+                ++n;
+            }
+        } else {
+            // many tets around the edge: emit each c once, in increasing order
+            int32_t last = b;
+            for (;;) {
+                int32_t next = INT32_MAX;
+                for (int64_t q = eb; q < ee; ++q) {
+                    const int4 r = m.rows[m.et_val[q]];
+                    const int32_t xv[4] = {r.x, r.y, r.z, r.w};
+                    for (int s2 = 0; s2 < 4; ++s2)
+                        if (xv[s2] > last && xv[s2] < next) next = xv[s2];
+                }
+                if (next == INT32_MAX) break;
+                if (WRITE && n < cap) {
+                    F[3 * (out + n)] = a;
+                    F[3 * (out + n) + 1] = b;
+                    F[3 * (out + n) + 2] = next;
+                }
+                ++n;
+                last = next;
+            }
+        }
+        if (!WRITE) nf[j] = n;
+        else if (n != cap) atomicOr(err, ERR_BAD_BLOCK);
+    }
+}
+
+// I_F[k] = FS[I_E[k]] for k = 0..K
+__global__ void __launch_bounds__(kThreads) k_enum_if(const int64_t *IE, const int32_t *FS, int64_t K, int64_t *IF) {
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k <= K; k += int64_t(gridDim.x) * blockDim.x)
+        IF[k] = FS[IE[k]];
+}
+
 // ---- lookup structure, once per enumeration ----
 
 // eo[v]: first sorted edge position of lower vertex v within its segment
@@ -522,6 +618,119 @@ bool enumeration_arrays(gale_ctx *ctx, const std::vector<int32_t> **E, const std
                         const std::vector<int64_t> **IE, const std::vector<int64_t> **IF, int32_t *order,
                         uint64_t *gen);
 
+// Sorted enumeration on the device: E, F, I_E, I_F into host vectors.
+// Builds the ET rows of every cluster first.  ENOTFOUND (nothing done) when
+// the context cannot: no device or ET not preconditioned.
+gale_status enumerate_sorted_device(gale_ctx *ctx, std::vector<int32_t> &E, std::vector<int32_t> &F,
+                                    std::vector<int64_t> &IE, std::vector<int64_t> &IF) {
+    if (ctx->device < 0 || (ctx->precond & GALE_ET) == 0) return GALE_ENOTFOUND;
+    gale_status st = gale_build_clusters(ctx, nullptr, 0, GALE_ET, GALE_MODE_BATCHED);
+    if (st == GALE_OK) st = gale_synchronize(ctx);
+    if (st != GALE_OK) return st;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(GALE_ECUDA, "cudaSetDevice");
+    cudaStream_t s = ctx->stream;
+    const HostMesh &hm = ctx->hm;
+    const int32_t K = hm.K;
+    IE.assign(size_t(K) + 1, 0);
+    for (int32_t k = 0; k < K; ++k) IE[k + 1] = IE[k] + ctx->sizes[size_t(5) * k + 2];
+    const int64_t nE = IE[K];
+    if (nE >= INT32_MAX) return fail(GALE_EINVAL, "more than 2^31 - 1 edges");
+    if (!ctx->cb) ctx->cb = new Cobound();
+    Cobound &cb = *ctx->cb;
+    if (!cb.rows) {
+        cb.rows = upload(ctx, hm.rows, s);
+        cb.cluster_of = upload(ctx, hm.cluster_of, s);
+        if (!cb.rows || !cb.cluster_of) return fail(GALE_ENOMEM, "device allocation of the mesh rows failed");
+    }
+    std::vector<int64_t> base(ctx->bulk_offs.begin(), ctx->bulk_offs.begin() + size_t(10) * K);
+    std::vector<void *> tmp;
+    auto dal = [&](size_t bytes) {
+        void *p = ctx->dalloc(std::max<size_t>(bytes, 16));
+        if (p) tmp.push_back(p);
+        return p;
+    };
+    auto release = [&]() {
+        for (void *p : tmp) ctx->dfree(p);
+        tmp.clear();
+    };
+    int64_t *d_base = static_cast<int64_t *>(dal(base.size() * 8));
+    int64_t *d_IE = static_cast<int64_t *>(dal(IE.size() * 8));
+    int32_t *d_E = static_cast<int32_t *>(dal(size_t(2) * nE * 4));
+    int32_t *d_nf = static_cast<int32_t *>(dal(size_t(nE) * 4 + 4));
+    int32_t *d_FS = static_cast<int32_t *>(dal((size_t(nE) + 1) * 4));
+    int64_t *d_IF = static_cast<int64_t *>(dal((size_t(K) + 1) * 8));
+    const int64_t nb = (nE + kThreads - 1) / kThreads;
+    int64_t *d_bsum = static_cast<int64_t *>(dal((size_t(nb) + 1) * 8));
+    if (!d_base || !d_IE || !d_E || !d_nf || !d_FS || !d_IF || !d_bsum) {
+        release();
+        return fail(GALE_ENOMEM, "device allocation for the enumeration failed");
+    }
+    cudaMemcpyAsync(d_base, base.data(), base.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_IE, IE.data(), IE.size() * 8, cudaMemcpyHostToDevice, s);
+    CbMesh m{};
+    m.rows = reinterpret_cast<const int4 *>(cb.rows);
+    m.cluster_of = cb.cluster_of;
+    m.I_V = ctx->d_I_V;
+    m.IE = d_IE;
+    m.et_uoff = ctx->bulk[B_ET_UOFF];
+    m.et_w = ctx->bulk[B_ET_W];
+    m.et_off = ctx->bulk[B_ET_OFF];
+    m.et_val = ctx->bulk[B_ET_VAL];
+    m.base = d_base;
+    m.sizes = ctx->d_sizes;
+    m.nv = hm.nv;
+    m.nE = nE;
+    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
+    auto grid_for = [&](int64_t n) {
+        return int(std::min<int64_t>(std::max<int64_t>((n + kThreads - 1) / kThreads, 1), int64_t(sms) * 16));
+    };
+    k_enum_edges<<<grid_for(hm.nv), kThreads, 0, s>>>(m, d_E);
+    k_enum_faces<false><<<grid_for(nE), kThreads, 0, s>>>(m, d_E, d_nf, nullptr, nullptr, ctx->d_err);
+    if (nb > 0) {
+        scan_sums<<<int(nb), kThreads, 0, s>>>(d_nf, nE, d_bsum);
+        scan_bsums<<<1, kThreads, 0, s>>>(d_bsum, nb);
+        scan_write<<<int(nb), kThreads, 0, s>>>(d_nf, nE, d_bsum, d_FS, nb, ctx->d_err);
+    } else {
+        cudaMemsetAsync(d_FS, 0, 4, s);
+    }
+    int32_t nF = 0;
+    if (cudaMemcpyAsync(&nF, d_FS + nE, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        release();
+        return fail(GALE_ECUDA, "enumeration count pass failed");
+    }
+    int32_t e = 0;
+    cudaMemcpy(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost);
+    if (e) {
+        cudaMemset(ctx->d_err, 0, 4);
+        release();
+        return fail(GALE_EDEVICE, "enumeration count pass: error word " + std::to_string(e));
+    }
+    int32_t *d_F = static_cast<int32_t *>(dal(size_t(3) * nF * 4));
+    if (!d_F) {
+        release();
+        return fail(GALE_ENOMEM, "device allocation of the triangle list failed");
+    }
+    k_enum_faces<true><<<grid_for(nE), kThreads, 0, s>>>(m, d_E, nullptr, d_FS, d_F, ctx->d_err);
+    k_enum_if<<<grid_for(K + 1), kThreads, 0, s>>>(d_IE, d_FS, K, d_IF);
+    E.resize(size_t(2) * nE);
+    F.resize(size_t(3) * nF);
+    IF.assign(size_t(K) + 1, 0);
+    bool ok = cudaMemcpyAsync(E.data(), d_E, E.size() * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+              cudaMemcpyAsync(F.data(), d_F, F.size() * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+              cudaMemcpyAsync(IF.data(), d_IF, IF.size() * 8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+              cudaStreamSynchronize(s) == cudaSuccess;
+    release();
+    if (!ok) return fail(GALE_ECUDA, "enumeration fill pass failed");
+    cudaMemcpy(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost);
+    if (e) {
+        cudaMemset(ctx->d_err, 0, 4);
+        return fail(GALE_EDEVICE, "enumeration fill pass: error word " + std::to_string(e));
+    }
+    return GALE_OK;
+}
+
 }  // namespace gale
 
 extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale_coboundary *out) {
@@ -564,7 +773,7 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     CbMesh m{reinterpret_cast<const int4 *>(cb.rows), cb.cluster_of, ctx->d_I_V, cb.E, cb.F, cb.ebk, cb.fbk,
              cb.IE, cb.IF, cb.eo, cb.ekw, cb.feo, cb.fkc, cb.e2s, cb.f2s,
              ctx->bulk[B_VT_OFF], ctx->bulk[B_VT_VAL], ctx->bulk[B_VV_OFF], ctx->bulk[B_VV_VAL],
-             ctx->bulk[B_ET_W], ctx->bulk[B_ET_OFF], ctx->bulk[B_ET_VAL], nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cb.base, ctx->d_sizes,
+             ctx->bulk[B_ET_W], ctx->bulk[B_ET_OFF], ctx->bulk[B_ET_VAL], ctx->bulk[B_ET_UOFF], nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cb.base, ctx->d_sizes,
              hm.nv, nE, nF, cb.sorted_ids};
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
     auto grid_for = [&](int64_t n) {

@@ -21,6 +21,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -149,6 +150,44 @@ int64_t face_id(const HostMesh &hm, const Enumeration &en, std::array<int32_t, 3
 }
 
 }  // namespace
+
+// the sorted enumeration on the device (gale_cobound.cu); ENOTFOUND when the
+// context has no device or no ET preconditioning
+gale_status enumerate_sorted_device(gale_ctx *ctx, std::vector<int32_t> &E, std::vector<int32_t> &F,
+                                    std::vector<int64_t> &IE, std::vector<int64_t> &IF);
+
+namespace {
+
+// The index over each segment's vertex-tuple order, from the enumeration's
+// lists: one sweep per segment over its vertices, edges and triangles.
+void build_index(Enumeration &en, const HostMesh &hm) {
+    const int32_t K = hm.K;
+    const int64_t nE = en.I_E[K], nF = en.I_F[K];
+    en.v_eo.assign(size_t(hm.nv) + 1, int32_t(nE));
+    en.ekw.resize(size_t(nE));
+    en.e_feo.assign(size_t(nE) + 1, int32_t(nF));
+    en.fkc.resize(size_t(nF));
+    parallel_dynamic(K, host_threads(0), 16, [&](int64_t k, int) {
+        const int64_t e0 = en.I_E[k], e1 = en.I_E[k + 1], f0 = en.I_F[k], f1 = en.I_F[k + 1];
+        auto eu = [&](int64_t j) { return en.E[2 * int64_t(en.e_by_key[j])]; };
+        auto ew = [&](int64_t j) { return en.E[2 * int64_t(en.e_by_key[j]) + 1]; };
+        auto fa = [&](int64_t p, int c) { return en.F[3 * int64_t(en.f_by_key[p]) + c]; };
+        int64_t j = e0, q = f0;
+        for (int32_t v = hm.I_V[k]; v < hm.I_V[k + 1]; ++v) {
+            while (j < e1 && eu(j) < v) ++j;
+            en.v_eo[v] = int32_t(j);
+        }
+        for (j = e0; j < e1; ++j) {
+            const int32_t a = eu(j), b = ew(j);
+            en.ekw[j] = b;
+            while (q < f1 && (fa(q, 0) < a || (fa(q, 0) == a && fa(q, 1) < b))) ++q;
+            en.e_feo[j] = int32_t(q);
+        }
+        for (q = f0; q < f1; ++q) en.fkc[q] = fa(q, 2);
+    });
+}
+
+}  // namespace
 }  // namespace gale
 
 extern "C" {
@@ -161,13 +200,39 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
     const int32_t K = hm.K;
     if (hm.rows.size() != size_t(4) * size_t(hm.nt) || hm.cluster_of.size() != size_t(hm.nv))
         return gale::fail(GALE_EINVAL, "the context holds no host rows");
+    static std::atomic<uint64_t> next_gen{1};
+    if (order == GALE_ENUM_SORTED) {
+        // on a device context the sorted lists come from the GPU: a segment's
+        // edges in tuple order are its ET edges, and the triangles over an
+        // edge (a, b) the distinct vertices c > b of the tets of ET(a, b)
+        try {
+            auto en = std::make_unique<gale::Enumeration>();
+            const gale_status st = gale::enumerate_sorted_device(ctx, en->E, en->F, en->I_E, en->I_F);
+            if (st == GALE_OK) {
+                std::lock_guard<std::mutex> lock(ctx->mu);
+                if (en->I_F[K] > INT32_MAX) return gale::fail(GALE_EINVAL, "more than 2^31 triangles");
+                en->order = order;
+                en->gen = next_gen.fetch_add(1);
+                en->e_by_key.resize(size_t(en->I_E[K]));
+                en->f_by_key.resize(size_t(en->I_F[K]));
+                std::iota(en->e_by_key.begin(), en->e_by_key.end(), 0);
+                std::iota(en->f_by_key.begin(), en->f_by_key.end(), 0);
+                gale::build_index(*en, hm);
+                delete ctx->enm;
+                ctx->enm = en.release();
+                return GALE_OK;
+            }
+            if (st != GALE_ENOTFOUND) return st;  // a device failure, not a missing device
+        } catch (const std::bad_alloc &) {
+            return gale::fail(GALE_ENOMEM, "host allocation failed during enumeration");
+        }
+    }
     std::lock_guard<std::mutex> lock(ctx->mu);
     try {
         std::vector<std::vector<uint64_t>> se(K);
         std::vector<std::vector<std::array<int32_t, 3>>> sf(K);
         gale::parallel_dynamic(K, gale::host_threads(0), 1,
                                [&](int64_t k, int) { gale::segment_simplices(hm, int32_t(k), order, se[k], sf[k]); });
-        static std::atomic<uint64_t> next_gen{1};
         auto en = std::make_unique<gale::Enumeration>();
         en->order = order;
         en->gen = next_gen.fetch_add(1);
@@ -183,10 +248,6 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
         en->F.resize(size_t(3) * size_t(en->I_F[K]));
         en->e_by_key.resize(size_t(en->I_E[K]));
         en->f_by_key.resize(size_t(en->I_F[K]));
-        en->v_eo.assign(size_t(hm.nv) + 1, int32_t(en->I_E[K]));
-        en->ekw.resize(size_t(en->I_E[K]));
-        en->e_feo.assign(size_t(en->I_E[K]) + 1, int32_t(en->I_F[K]));
-        en->fkc.resize(size_t(en->I_F[K]));
         gale::parallel_dynamic(K, gale::host_threads(0), 4, [&](int64_t k, int) {
             const int64_t e0 = en->I_E[k], f0 = en->I_F[k];
             const auto &ev = se[k];
@@ -206,27 +267,8 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
                 std::sort(eb, eb + ev.size(), [&](int32_t a, int32_t b) { return ev[a - e0] < ev[b - e0]; });
                 std::sort(fb, fb + fv.size(), [&](int32_t a, int32_t b) { return fv[a - f0] < fv[b - f0]; });
             }
-            // the index over the tuple order: one sweep over the segment's
-            // vertices, edges and triangles
-            const int64_t ne = int64_t(ev.size()), nf = int64_t(fv.size());
-            int64_t i = 0, q = 0;
-            for (int32_t v = hm.I_V[k]; v < hm.I_V[k + 1]; ++v) {
-                while (i < ne && int32_t(ev[eb[i] - e0] >> 32) < v) ++i;
-                en->v_eo[v] = int32_t(e0 + i);
-            }
-            for (i = 0; i < ne; ++i) {
-                const uint64_t key = ev[eb[i] - e0];
-                const int32_t a = int32_t(key >> 32), b = int32_t(key & 0xffffffffu);
-                en->ekw[e0 + i] = b;
-                while (q < nf) {
-                    const auto &f = fv[fb[q] - f0];
-                    if (f[0] < a || (f[0] == a && f[1] < b)) ++q;
-                    else break;
-                }
-                en->e_feo[e0 + i] = int32_t(f0 + q);
-            }
-            for (q = 0; q < nf; ++q) en->fkc[f0 + q] = fv[fb[q] - f0][2];
         });
+        gale::build_index(*en, hm);
         delete ctx->enm;
         ctx->enm = en.release();
     } catch (const std::bad_alloc &) {
