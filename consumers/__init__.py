@@ -51,7 +51,7 @@ def _load():
         lib.gale_cp_serve_run.restype = ctypes.c_int
         lib.gale_open_loop.argtypes = [P, i32, P, P, P, i64, f64, u64, i32, P, P]
         lib.gale_open_loop.restype = ctypes.c_int
-        lib.gale_dg_run.argtypes = [P, P, i64] + [P] * 17 + [i32, i64, P]
+        lib.gale_dg_run.argtypes = [P, P, i64] + [P] * 15 + [i32, i64, P]
         lib.gale_dg_run.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -136,17 +136,16 @@ def csr_from_bulk(off_b, val_b, I_V):
     return np.concatenate([off, [int(counts.sum())]]).astype(np.int64), np.ascontiguousarray(val_b, dtype=np.int32)
 
 
-def discrete_gradient_arrays(f_c, inid_c, ve, vf, vt, ev, fv, tv, fe, tf, nthreads=16, grain=1024):
+def discrete_gradient_arrays(f_c, inid_c, ve, vf, vt, ev, fv, tv, nthreads=16, grain=1024):
     """gale_dg_run on host arrays: ve, vf, vt are (offsets, values) CSR pairs
-    indexed by canonical vertex; ev, fv, tv, fe, tf as in consumers.cpp.
+    indexed by canonical vertex; ev, fv, tv the vertex lists (consumers.cpp).
     Returns (dict v_up, e_down, e_up, f_down, f_up, t_down; wall seconds)."""
     lib = _load()
     nv = len(f_c)
     nE, nF, nT = np.asarray(ev).size // 2, np.asarray(fv).size // 3, np.asarray(tv).size // 4
     i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32).reshape(-1)
     i64 = lambda a: np.ascontiguousarray(a, dtype=np.int64)
-    rel = [i64(ve[0]), i32(ve[1]), i64(vf[0]), i32(vf[1]), i64(vt[0]), i32(vt[1]),
-           i32(ev), i32(fv), i32(tv), i32(fe), i32(tf)]
+    rel = [i64(ve[0]), i32(ve[1]), i64(vf[0]), i32(vf[1]), i64(vt[0]), i32(vt[1]), i32(ev), i32(fv), i32(tv)]
     out = {"v_up": np.empty(nv, np.int32), "e_down": np.empty(nE, np.int32), "e_up": np.empty(nE, np.int32),
            "f_down": np.empty(nF, np.int32), "f_up": np.empty(nF, np.int32), "t_down": np.empty(nT, np.int32)}
     st = np.zeros(2, np.float64)
@@ -162,9 +161,9 @@ def discrete_gradient_arrays(f_c, inid_c, ve, vf, vt, ev, fv, tv, fe, tf, nthrea
 
 def gather_gradient_relations(ctx, order=None):
     """The relations the discrete gradient reads, from a loaded context:
-    the enumeration (gale_enumerate, host), VE and VF from the GPU
-    coboundary pass, VT from the bulk build that pass leaves behind, FE and
-    TF from the host boundary relations.  Returns a dict of host arrays."""
+    the enumeration (gale_enumerate), VE and VF from the GPU coboundary pass,
+    VT from the bulk build that pass leaves behind, and TV.  (FE and TF are
+    looked up by the consumer itself.)  Returns a dict of host arrays."""
     import paper_2507_15230_gb300 as gale
     if order is not None:
         ctx.enumerate(order)
@@ -174,11 +173,7 @@ def gather_gradient_relations(ctx, order=None):
     b = ctx.export(gale.VT)
     vt = csr_from_bulk(b["vt_off"], b["vt_val"], I_V)
     rows = ctx.rows()
-    nF, nT = en["F"].shape[0], rows.shape[0]
-    fe = ctx.boundary(gale.REL_FE, np.arange(nF, dtype=np.int64)) if nF else np.zeros((0, 3), np.int32)
-    tf = ctx.boundary(gale.REL_TF, np.arange(nT, dtype=np.int64)) if nT else np.zeros((0, 4), np.int32)
-    return {"ve": cb["VE"], "vf": cb["VF"], "vt": vt, "ev": en["E"], "fv": en["F"], "tv": rows,
-            "fe": fe, "tf": tf}
+    return {"ve": cb["VE"], "vf": cb["VF"], "vt": vt, "ev": en["E"], "fv": en["F"], "tv": rows}
 
 
 def discrete_gradient(ctx, f_c, inid_c, rel=None, nthreads=16, order=None):
@@ -187,4 +182,4 @@ def discrete_gradient(ctx, f_c, inid_c, rel=None, nthreads=16, order=None):
     if rel is None:
         rel = gather_gradient_relations(ctx, order)
     return discrete_gradient_arrays(f_c, inid_c, rel["ve"], rel["vf"], rel["vt"], rel["ev"], rel["fv"], rel["tv"],
-                                    rel["fe"], rel["tf"], nthreads=nthreads)
+                                    nthreads=nthreads)

@@ -280,14 +280,14 @@ int gale_open_loop(gale_ctx *const *ctxs, int32_t nctx, const int32_t *mi, const
  * faces inside the lower star are those that contain v, v itself excluded.
  *
  * The relations read are the ones the paper lists for this algorithm: the
- * coboundary rows VE(v), VF(v), VT(v) (GPU-built), the vertex lists EV, FV,
- * TV, and the boundary rows FE, TF (Section 4.4).
+ * coboundary rows VE(v), VF(v), VT(v) (GPU-built) and the vertex lists EV,
+ * FV, TV.  The boundary relations FE and TF are answered by the consumer
+ * itself, as Section 4.4 has consumers do, by a lookup among the lower
+ * star's own simplices: a face through v is identified by its vertices.
  *   f, inid          per canonical vertex: value and input id
  *   [v_begin, v_end) vertices whose lower stars are processed
  *   ve/vf/vt_off,val CSR rows indexed by canonical vertex id (int64 offsets)
  *   ev int32[2 nE], fv int32[3 nF], tv int32[4 nT]  ascending vertex ids
- *   fe int32[3 nF]   edges (a,b), (a,c), (b,c) of triangle (a,b,c)
- *   tf int32[4 nT]   triangles (a,b,c), (a,b,d), (a,c,d), (b,c,d)
  * Output, one entry per simplex, -1 where unpaired (a simplex is critical
  * when both of its entries are -1); every simplex whose highest vertex is in
  * the range gets both of its entries written:
@@ -311,7 +311,7 @@ struct DgArgs {
     const float *f;
     const int32_t *inid;
     const int64_t *ve_off, *vf_off, *vt_off;
-    const int32_t *ve_val, *vf_val, *vt_val, *ev, *fv, *tv, *fe, *tf;
+    const int32_t *ve_val, *vf_val, *vt_val, *ev, *fv, *tv;
     int32_t *v_up, *e_down, *e_up, *f_down, *f_up, *t_down;
 };
 
@@ -372,30 +372,37 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
         a.v_up[v] = -1;
         return ns == 0 ? 0 : -1;
     }
-    // faces inside the lower star: a triangle's two edges through v (FE),
-    // a tet's three triangles through v (TF); local ids by binary search
-    // over the edges / triangles, which the CSR rows list in ascending id
+    // faces inside the lower star (the consumer's own FE / TF lookups): a
+    // triangle (v, x, y) has the edges to x and to y, a tet (v, x, y, z) the
+    // triangles on each pair of x, y, z; each is found among the lower
+    // star's edges / triangles by its other vertices
     L.face.assign(size_t(ns) * 3, -1);
-    auto local = [&](int32_t lo, int32_t hi, int32_t g) -> int32_t {
-        const int32_t *b = L.gid.data() + lo, *e = L.gid.data() + hi;
-        const int32_t *p = std::lower_bound(b, e, g);
-        return (p != e && *p == g) ? int32_t(p - L.gid.data()) : -1;
+    auto edge_to = [&](int32_t x) -> int32_t {
+        for (int32_t e = 0; e < ne; ++e)
+            if (L.seq[3 * size_t(e)] == x) return e;
+        return -1;
+    };
+    auto tri_on = [&](int32_t x, int32_t y) -> int32_t {
+        for (int32_t t = ne; t < ne + nf; ++t) {
+            const int32_t p = L.seq[3 * size_t(t)], q = L.seq[3 * size_t(t) + 1];
+            if ((p == x && q == y) || (p == y && q == x)) return t;
+        }
+        return -1;
     };
     for (int32_t s = ne; s < ns; ++s) {
-        const bool tri = L.dim[s] == 2;
-        const int32_t w = tri ? 3 : 4;
-        const int32_t *vs = (tri ? a.fv : a.tv) + int64_t(w) * L.gid[s];
-        const int32_t *fs = (tri ? a.fe : a.tf) + int64_t(w) * L.gid[s];
-        int pos = 0;
-        while (pos < w && vs[pos] != v) ++pos;
-        if (pos == w) return -1;
-        const int skip = (w - 1) - pos;  // the face opposite v
-        int c = 0;
-        for (int i = 0; i < w; ++i) {
-            if (i == skip) continue;
-            const int32_t l = tri ? local(0, ne, fs[i]) : local(ne, ne + nf, fs[i]);
-            if (l < 0) return -1;
-            L.face[3 * size_t(s) + c++] = l;
+        const int32_t *o = &L.seq[3 * size_t(s)];
+        int32_t l[3];
+        if (L.dim[s] == 2) {
+            l[0] = edge_to(o[0]);
+            l[1] = edge_to(o[1]);
+        } else {
+            l[0] = tri_on(o[0], o[1]);
+            l[1] = tri_on(o[0], o[2]);
+            l[2] = tri_on(o[1], o[2]);
+        }
+        for (int i = 0; i < L.dim[s]; ++i) {
+            if (l[i] < 0) return -1;
+            L.face[3 * size_t(s) + i] = l[i];
         }
     }
     // cofaces inside the lower star (CSR over local ids)
@@ -508,9 +515,9 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
 int gale_dg_lower_stars(const float *f, const int32_t *inid, int64_t v_begin, int64_t v_end, const int64_t *ve_off,
                         const int32_t *ve_val, const int64_t *vf_off, const int32_t *vf_val, const int64_t *vt_off,
                         const int32_t *vt_val, const int32_t *ev, const int32_t *fv, const int32_t *tv,
-                        const int32_t *fe, const int32_t *tf, int32_t *v_up, int32_t *e_down, int32_t *e_up,
+                        int32_t *v_up, int32_t *e_down, int32_t *e_up,
                         int32_t *f_down, int32_t *f_up, int32_t *t_down) {
-    const DgArgs a{f, inid, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv, fe, tf,
+    const DgArgs a{f, inid, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv,
                    v_up, e_down, e_up, f_down, f_up, t_down};
     LowerStar L;
     for (int64_t v = v_begin; v < v_end; ++v)
@@ -526,12 +533,12 @@ int gale_dg_lower_stars(const float *f, const int32_t *inid, int64_t v_begin, in
  */
 int gale_dg_run(const float *f, const int32_t *inid, int64_t nv, const int64_t *ve_off, const int32_t *ve_val,
                 const int64_t *vf_off, const int32_t *vf_val, const int64_t *vt_off, const int32_t *vt_val,
-                const int32_t *ev, const int32_t *fv, const int32_t *tv, const int32_t *fe, const int32_t *tf,
-                int32_t *v_up, int32_t *e_down, int32_t *e_up, int32_t *f_down, int32_t *f_up, int32_t *t_down,
-                int32_t nthreads, int64_t grain, double *stats) {
+                const int32_t *ev, const int32_t *fv, const int32_t *tv, int32_t *v_up, int32_t *e_down,
+                int32_t *e_up, int32_t *f_down, int32_t *f_up, int32_t *t_down, int32_t nthreads, int64_t grain,
+                double *stats) {
     if (nthreads < 1) nthreads = 1;
     if (grain < 1) grain = 1024;
-    const DgArgs a{f, inid, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv, fe, tf,
+    const DgArgs a{f, inid, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv,
                    v_up, e_down, e_up, f_down, f_up, t_down};
     std::atomic<int64_t> next{0}, done{0};
     std::atomic<int> err{0};

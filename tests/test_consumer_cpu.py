@@ -62,11 +62,9 @@ def oracle_dg_relations(canon, order="sorted"):
     def csr(rs):
         return (np.concatenate([[0], np.cumsum([len(r) for r in rs])]).astype(np.int64),
                 np.array([x for r in rs for x in r], np.int32))
-    fe = np.array(oracle.boundary(canon, en, "FE", range(len(en["F"]))), np.int32).reshape(-1, 3)
-    tf = np.array(oracle.boundary(canon, en, "TF", range(rows.shape[0])), np.int32).reshape(-1, 4)
     return en, dict(ve=csr(cb["VE"]), vf=csr(cb["VF"]), vt=(np.asarray(rel["vt_off"]), np.asarray(rel["vt_val"])),
                     ev=np.array(en["E"], np.int32).reshape(-1, 2), fv=np.array(en["F"], np.int32).reshape(-1, 3),
-                    tv=rows, fe=fe, tf=tf)
+                    tv=rows)
 
 
 def dg_matches_oracle(canon, f_c, inid, order="sorted", nthreads=4):
