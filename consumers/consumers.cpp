@@ -304,7 +304,13 @@ namespace {
 struct LowerStar {
     // local simplices: edges [0, ne), triangles [ne, ne + nf), tets after
     std::vector<int32_t> gid, dim, seq, nseq, open, state, in_one, face, cof_off, cof, fill;
-    std::vector<int32_t> heap_one, heap_zero;
+    std::vector<int32_t> heap_one, heap_zero, order, rank, eidx;
+    std::vector<uint32_t> key;  // packed value sequence (ranks of the other vertices, highest first)
+    // small lower stars (at most kSmall edges): vertex -> edge hash and
+    // edge pair -> triangle table
+    static constexpr int kSmall = 32, kHash = 64;
+    int32_t hkey[kHash], hval[kHash];
+    int32_t tri2[kSmall * kSmall];
 };
 
 struct DgArgs {
@@ -324,9 +330,8 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     L.dim.clear();
     L.seq.clear();
     L.nseq.clear();
-    // lower-star edges, triangles and tets with their other vertices, highest first
+    // lower-star edges, triangles and tets with their other vertices
     auto add = [&](int32_t g, int d, int32_t *o, int n) {
-        std::sort(o, o + n, [&](int32_t x, int32_t y) { return lt(y, x); });
         L.gid.push_back(g);
         L.dim.push_back(d);
         L.nseq.push_back(n);
@@ -374,36 +379,99 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     }
     // faces inside the lower star (the consumer's own FE / TF lookups): a
     // triangle (v, x, y) has the edges to x and to y, a tet (v, x, y, z) the
-    // triangles on each pair of x, y, z; each is found among the lower
-    // star's edges / triangles by its other vertices
+    // triangles on each pair of x, y, z.  Every other vertex is the far end
+    // of a lower-star edge: eidx holds that edge per (simplex, other vertex),
+    // found through a small hash (or a scan in large lower stars), and a
+    // triangle is found from its two edges.
     L.face.assign(size_t(ns) * 3, -1);
+    L.eidx.assign(size_t(ns) * 3, -1);
+    const bool small = ne <= LowerStar::kSmall;
+    if (small) {
+        for (int i = 0; i < LowerStar::kHash; ++i) L.hkey[i] = -1;
+        for (int32_t e = 0; e < ne; ++e) {
+            const int32_t x = L.seq[3 * size_t(e)];
+            uint32_t h = (uint32_t(x) * 2654435761u) >> 26;
+            while (L.hkey[h] >= 0) h = (h + 1) & (LowerStar::kHash - 1);
+            L.hkey[h] = x;
+            L.hval[h] = e;
+        }
+        for (int i = 0; i < ne * LowerStar::kSmall; ++i) L.tri2[i] = -1;
+    }
     auto edge_to = [&](int32_t x) -> int32_t {
+        if (small) {
+            uint32_t h = (uint32_t(x) * 2654435761u) >> 26;
+            for (int probe = 0; probe < LowerStar::kHash && L.hkey[h] >= 0; ++probe) {
+                if (L.hkey[h] == x) return L.hval[h];
+                h = (h + 1) & (LowerStar::kHash - 1);
+            }
+            return -1;
+        }
         for (int32_t e = 0; e < ne; ++e)
             if (L.seq[3 * size_t(e)] == x) return e;
         return -1;
     };
-    auto tri_on = [&](int32_t x, int32_t y) -> int32_t {
+    for (int32_t s = 0; s < ns; ++s) {
+        if (L.dim[s] == 1) {
+            L.eidx[3 * size_t(s)] = s;
+            continue;
+        }
+        for (int i = 0; i < L.nseq[s]; ++i) {
+            const int32_t e = edge_to(L.seq[3 * size_t(s) + i]);
+            if (e < 0) return -1;
+            L.eidx[3 * size_t(s) + i] = e;
+        }
+        if (L.dim[s] == 2) {
+            L.face[3 * size_t(s)] = L.eidx[3 * size_t(s)];
+            L.face[3 * size_t(s) + 1] = L.eidx[3 * size_t(s) + 1];
+            if (small) {
+                const int32_t i = L.eidx[3 * size_t(s)], j = L.eidx[3 * size_t(s) + 1];
+                L.tri2[i * LowerStar::kSmall + j] = s;
+                L.tri2[j * LowerStar::kSmall + i] = s;
+            }
+        }
+    }
+    auto tri_on = [&](int32_t i, int32_t j) -> int32_t {  // edge indices
+        if (small) return L.tri2[i * LowerStar::kSmall + j];
         for (int32_t t = ne; t < ne + nf; ++t) {
-            const int32_t p = L.seq[3 * size_t(t)], q = L.seq[3 * size_t(t) + 1];
-            if ((p == x && q == y) || (p == y && q == x)) return t;
+            const int32_t p = L.eidx[3 * size_t(t)], q = L.eidx[3 * size_t(t) + 1];
+            if ((p == i && q == j) || (p == j && q == i)) return t;
         }
         return -1;
     };
-    for (int32_t s = ne; s < ns; ++s) {
-        const int32_t *o = &L.seq[3 * size_t(s)];
-        int32_t l[3];
-        if (L.dim[s] == 2) {
-            l[0] = edge_to(o[0]);
-            l[1] = edge_to(o[1]);
-        } else {
-            l[0] = tri_on(o[0], o[1]);
-            l[1] = tri_on(o[0], o[2]);
-            l[2] = tri_on(o[1], o[2]);
-        }
-        for (int i = 0; i < L.dim[s]; ++i) {
+    for (int32_t s = ne + nf; s < ns; ++s) {
+        const int32_t *e = &L.eidx[3 * size_t(s)];
+        const int32_t l[3] = {tri_on(e[0], e[1]), tri_on(e[0], e[2]), tri_on(e[1], e[2])};
+        for (int i = 0; i < 3; ++i) {
             if (l[i] < 0) return -1;
             L.face[3 * size_t(s) + i] = l[i];
         }
+    }
+    // value sequences.  Every other vertex of a lower-star simplex is the
+    // far end of a lower-star edge, so the edges, ordered by value, rank
+    // them 1..ne; a simplex's sequence is then its ranks, highest first,
+    // packed 10 bits each (a proper prefix leaves zeros, so it compares
+    // first).  Beyond 1023 lower neighbours the sequences compare by value.
+    const bool packed = ne < 1024;
+    L.order.resize(size_t(ne));
+    for (int32_t e = 0; e < ne; ++e) L.order[e] = e;
+    std::sort(L.order.begin(), L.order.end(),
+              [&](int32_t x, int32_t y) { return lt(L.seq[3 * size_t(x)], L.seq[3 * size_t(y)]); });
+    L.rank.resize(size_t(ne));
+    for (int32_t i = 0; i < ne; ++i) L.rank[L.order[i]] = i + 1;
+    if (packed) {
+        L.key.resize(size_t(ns));
+        for (int32_t s = 0; s < ns; ++s) {
+            uint32_t r[3] = {0u, 0u, 0u};
+            for (int i = 0; i < L.nseq[s]; ++i) r[i] = uint32_t(L.rank[L.eidx[3 * size_t(s) + i]]);
+            if (r[0] < r[1]) std::swap(r[0], r[1]);
+            if (r[1] < r[2]) std::swap(r[1], r[2]);
+            if (r[0] < r[1]) std::swap(r[0], r[1]);
+            L.key[s] = r[0] << 20 | r[1] << 10 | r[2];
+        }
+    } else {
+        for (int32_t s = 0; s < ns; ++s)
+            std::sort(&L.seq[3 * size_t(s)], &L.seq[3 * size_t(s)] + L.nseq[s],
+                      [&](int32_t x, int32_t y) { return lt(y, x); });
     }
     // cofaces inside the lower star (CSR over local ids)
     L.cof_off.assign(size_t(ns) + 1, 0);
@@ -421,6 +489,7 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     L.in_one.assign(size_t(ns), 0);
     // heap order: std heaps keep the largest on top, so "greater" = later
     auto later = [&](int32_t x, int32_t y) {
+        if (packed) return L.key[x] > L.key[y];
         const int32_t *sx = &L.seq[3 * size_t(x)], *sy = &L.seq[3 * size_t(y)];
         const int32_t nx = L.nseq[x], ny = L.nseq[y];
         for (int i = 0; i < nx && i < ny; ++i)
