@@ -113,3 +113,20 @@ def test_dg_consumer_rejects_inconsistent_relations():
     rel["ev"][:, :] = rel["ev"][::-1, :]  # edges no longer match their VE rows
     with pytest.raises(RuntimeError):
         consumers.discrete_gradient_arrays(f_c, inid, **rel, nthreads=2)
+
+
+def test_csr_from_bulk_stitches_cluster_rows():
+    """Per-cluster CSR pieces (offsets from 0 each) become one CSR over all
+    vertices; the oracle's per-cluster VT rows give the global VT."""
+    xyz, tv = gen.freudenthal_grid(3, permute=True, seed=5)
+    K = 4
+    seg = np.random.default_rng(2).integers(0, K, xyz.shape[0]).astype(np.int32)
+    canon, rel = oracle.build_all(xyz.shape[0], tv, seg, K)
+    offs, vals = [], []
+    for k in range(K):
+        v = oracle.cluster_view(rel, canon, k)
+        offs.append(np.asarray(v["vt_off"], np.int32))
+        vals.append(np.asarray(v["vt_val"], np.int32))
+    off, val = consumers.csr_from_bulk(np.concatenate(offs), np.concatenate(vals), canon["I_V"])
+    assert np.array_equal(off, np.asarray(rel["vt_off"], np.int64))
+    assert np.array_equal(val, np.asarray(rel["vt_val"], np.int32))
