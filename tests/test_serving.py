@@ -377,3 +377,51 @@ def test_idle_loop_wait_runs_out_and_the_context_stays_usable():
         st = ctx.serve_stats()
         assert st.batches == first + 1 and st.builds == 2
         ctx.synchronize()
+
+
+def test_served_rows_match_the_bulk_build_at_128cubed():
+    """At the 128^3 grid (12.6M tets, 8,192 clusters): 16 threads request a
+    random sample of clusters under every relation mask through the device
+    loop, with a budget that forces evictions; every served view equals the
+    same cluster from one bulk build of all clusters, bit for bit."""
+    m = gen.freudenthal_mesh(128, 512, seed=3, field_seed=4, jitter=0.3, with_field=False)
+    rng = np.random.default_rng(8)
+    with gale.Context.load(m, device=0, cache_budget_bytes=64 << 20) as ctx:
+        ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+        ctx.synchronize()
+        bulk = ctx.export(gale.ALL)
+        offs = [ctx.bulk_offsets(k) for k in range(ctx.K)]
+        I_V, I_T, sizes = ctx.intervals()
+        sample = rng.choice(ctx.K, 400, replace=False)
+        masks = list(range(1, 16))
+
+        def want(k, mk):
+            nvo, nown, ne = int(I_V[k + 1] - I_V[k]), int(I_T[k + 1] - I_T[k]), int(sizes[k, 2])
+            lens = {"vt_off": nvo + 1, "vt_val": sizes[k, 0], "vv_off": nvo + 1, "vv_val": sizes[k, 1],
+                    "et_uoff": nvo + 1, "et_w": ne, "et_off": ne + 1, "et_val": sizes[k, 3], "tt_off": nown + 1,
+                    "tt_val": sizes[k, 4]}
+            rel = {"vt_off": gale.VT, "vt_val": gale.VT, "vv_off": gale.VV, "vv_val": gale.VV, "et_uoff": gale.ET,
+                   "et_w": gale.ET, "et_off": gale.ET, "et_val": gale.ET, "tt_off": gale.TT, "tt_val": gale.TT}
+            return {n: bulk[n][offs[k][n]:offs[k][n] + int(lens[n])] for n in lens if mk & rel[n]}
+
+        errors = []
+
+        def consumer(seed):
+            r = np.random.default_rng(seed)
+            for k in r.permutation(sample)[:100]:
+                mk = masks[int(r.integers(len(masks)))]
+                v = ctx.request(int(k), mk, timeout_ns=60_000_000_000)
+                got = gale.view_to_numpy(v)
+                w = want(int(k), mk)
+                if not same({n: got[n] for n in w}, w):
+                    errors.append((int(k), mk))
+                ctx.release(v)
+
+        th = [threading.Thread(target=consumer, args=(i,)) for i in range(16)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        st = ctx.serve_stats()
+    assert not errors, errors[:5]
+    assert st.requests == 1600 and st.evictions > 0
