@@ -59,3 +59,19 @@ def test_first_appearance_stays_on_the_host_and_matches():
     assert [tuple(e) for e in got["E"].tolist()] == want["E"]
     assert [tuple(f) for f in got["F"].tolist()] == want["F"]
     assert [tuple(e) for e in again["E"].tolist()] == sorted(want["E"])
+
+
+def test_empty_clusters():
+    """Cluster ids that own no vertex: empty intervals in I_E and I_F."""
+    xyz, tv = gen.freudenthal_grid(4, permute=True, seed=77)
+    seg = np.random.default_rng(3).choice(np.array([0, 2, 5, 7, 11], np.int32), xyz.shape[0]).astype(np.int32)
+    m = gen.Mesh(xyz, tv, seg, 12)
+    check(m)
+    canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
+    want = oracle.coboundary(canon, oracle.enumerate_simplices(canon, "sorted"))
+    with gale.Context.load(m, device=0) as ctx:
+        ctx.enumerate(gale.ENUM_SORTED)
+        got = ctx.coboundary()
+    for name in ("VE", "VF", "EF", "FT"):
+        off, val = got[name]
+        assert val.tolist() == [x for r in want[name] for x in r], name
