@@ -28,7 +28,7 @@ def build(force: bool = False) -> str:
         return _LIB
     cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC, "-I", os.path.join(_ROOT, "include"),
+    cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC, "-I", os.path.join(_ROOT, "include"),
            "-I", os.path.join(cuda, "include"), "-L", os.path.dirname(gl), "-lgale", "-Wl,-rpath," + os.path.dirname(gl),
            "-L", os.path.join(cuda, "lib64"), "-lcudart", "-lpthread"]
     subprocess.run(cmd, check=True)

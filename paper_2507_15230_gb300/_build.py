@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     + inc + ["-c", os.path.join(CSRC, f), "-o", o])
     for f in cpp:
         o = os.path.join(BUILD, f + ".o")
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function"] + inc
+        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function"] + inc
                     + ["-c", os.path.join(CSRC, f), "-o", o])
 
     def run(cmd):
