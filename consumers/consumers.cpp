@@ -303,8 +303,13 @@ namespace {
 
 struct LowerStar {
     // local simplices: edges [0, ne), triangles [ne, ne + nf), tets after
-    std::vector<int32_t> gid, dim, seq, nseq, open, state, in_one, face, cof_off, cof, fill;
-    std::vector<int32_t> heap_one, heap_zero, order, rank, eidx;
+    std::vector<int32_t> gid, dim, seq, nseq, open, state, face, cof_off, cof, fill;
+    std::vector<int32_t> order, rank, eidx, at, pos;  // at: simplex at each queue position; pos: its inverse
+    std::vector<uint64_t> kidx, one, zero;            // sort keys; the two queues as position bitsets
+    // dense ordering of small lower stars: one bit per rank triple
+    static constexpr int kDense = 1 << 14;
+    uint64_t dbits[kDense / 64];
+    std::vector<int32_t> dslot = std::vector<int32_t>(kDense);
     std::vector<uint32_t> key;  // packed value sequence (ranks of the other vertices, highest first)
     // small lower stars (at most kSmall edges): vertex -> edge hash and
     // edge pair -> triangle table
@@ -326,53 +331,67 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     const float *f = a.f;
     const int32_t *inid = a.inid;
     auto lt = [&](int32_t x, int32_t y) { return below(f, inid, x, y); };
-    L.gid.clear();
-    L.dim.clear();
-    L.seq.clear();
-    L.nseq.clear();
-    // lower-star edges, triangles and tets with their other vertices
-    auto add = [&](int32_t g, int d, int32_t *o, int n) {
-        L.gid.push_back(g);
-        L.dim.push_back(d);
-        L.nseq.push_back(n);
-        for (int i = 0; i < 3; ++i) L.seq.push_back(i < n ? o[i] : -1);
+    // lower-star edges, triangles and tets with their other vertices.  Every
+    // row entry is written to the next slot and the slot is kept only when
+    // all its other vertices are below v (no data-dependent branch).
+    const int64_t ve0 = a.ve_off[v], ve1 = a.ve_off[v + 1], vf0 = a.vf_off[v], vf1 = a.vf_off[v + 1];
+    const int64_t vt0 = a.vt_off[v], vt1 = a.vt_off[v + 1];
+    const size_t cap = size_t((ve1 - ve0) + (vf1 - vf0) + (vt1 - vt0));
+    if (L.gid.size() < cap) {
+        L.gid.resize(cap);
+        L.dim.resize(cap);
+        L.nseq.resize(cap);
+        L.seq.resize(3 * cap);
+    }
+    int32_t *gid = L.gid.data(), *dim = L.dim.data(), *nseq = L.nseq.data(), *seq = L.seq.data();
+    const float fv0 = f[v];
+    const int32_t iv0 = inid[v];
+    auto low = [&](int32_t x) -> int32_t {  // below(x, v)
+        const float fx = f[x];
+        return int32_t(fx < fv0) | (int32_t(fx == fv0) & int32_t(inid[x] < iv0));
     };
-    for (int64_t q = a.ve_off[v]; q < a.ve_off[v + 1]; ++q) {
+    int32_t n = 0, bad = 0;
+    for (int64_t q = ve0; q < ve1; ++q) {
         const int32_t e = a.ve_val[q];
         const int32_t x = a.ev[2 * int64_t(e)], y = a.ev[2 * int64_t(e) + 1];
-        if (x != v && y != v) return -1;
-        int32_t o[1] = {x == v ? y : x};
-        if (lt(o[0], v)) add(e, 1, o, 1);
+        bad |= int32_t(x != v) & int32_t(y != v);
+        const int32_t o = x == v ? y : x;
+        gid[n] = e;
+        dim[n] = nseq[n] = 1;
+        seq[3 * n] = o;
+        seq[3 * n + 1] = seq[3 * n + 2] = -1;
+        n += low(o);
     }
-    const int32_t ne = int32_t(L.gid.size());
-    for (int64_t q = a.vf_off[v]; q < a.vf_off[v + 1]; ++q) {
+    const int32_t ne = n;
+    for (int64_t q = vf0; q < vf1; ++q) {
         const int32_t t = a.vf_val[q];
-        int32_t o[3], n = 0;
-        bool ok = true;
-        for (int i = 0; i < 3; ++i) {
-            const int32_t x = a.fv[3 * int64_t(t) + i];
-            if (x == v) continue;
-            ok = ok && lt(x, v);
-            o[n++] = x;
-        }
-        if (n != 2) return -1;
-        if (ok) add(t, 2, o, 2);
+        const int32_t *x = a.fv + 3 * int64_t(t);
+        bad |= int32_t((x[0] == v) + (x[1] == v) + (x[2] == v) != 1);
+        const int32_t o0 = x[0] == v ? x[1] : x[0], o1 = x[2] == v ? x[1] : x[2];
+        gid[n] = t;
+        dim[n] = nseq[n] = 2;
+        seq[3 * n] = o0;
+        seq[3 * n + 1] = o1;
+        seq[3 * n + 2] = -1;
+        n += low(o0) & low(o1);
     }
-    const int32_t nf = int32_t(L.gid.size()) - ne;
-    for (int64_t q = a.vt_off[v]; q < a.vt_off[v + 1]; ++q) {
+    const int32_t nf = n - ne;
+    for (int64_t q = vt0; q < vt1; ++q) {
         const int32_t t = a.vt_val[q];
-        int32_t o[4], n = 0;
-        bool ok = true;
-        for (int i = 0; i < 4; ++i) {
-            const int32_t x = a.tv[4 * int64_t(t) + i];
-            if (x == v) continue;
-            ok = ok && lt(x, v);
-            o[n++] = x;
-        }
-        if (n != 3) return -1;
-        if (ok) add(t, 3, o, 3);
+        const int32_t *x = a.tv + 4 * int64_t(t);
+        bad |= int32_t((x[0] == v) + (x[1] == v) + (x[2] == v) + (x[3] == v) != 1);
+        const int32_t o0 = x[0] == v ? x[1] : x[0];
+        const int32_t o1 = (x[0] == v) | (x[1] == v) ? x[2] : x[1];
+        const int32_t o2 = x[3] == v ? x[2] : x[3];
+        gid[n] = t;
+        dim[n] = nseq[n] = 3;
+        seq[3 * n] = o0;
+        seq[3 * n + 1] = o1;
+        seq[3 * n + 2] = o2;
+        n += low(o0) & low(o1) & low(o2);
     }
-    const int32_t ns = int32_t(L.gid.size());
+    if (bad) return -1;
+    const int32_t ns = n;
     if (ne == 0) {
         a.v_up[v] = -1;
         return ns == 0 ? 0 : -1;
@@ -452,21 +471,39 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     // packed 10 bits each (a proper prefix leaves zeros, so it compares
     // first).  Beyond 1023 lower neighbours the sequences compare by value.
     const bool packed = ne < 1024;
-    L.order.resize(size_t(ne));
-    for (int32_t e = 0; e < ne; ++e) L.order[e] = e;
-    std::sort(L.order.begin(), L.order.end(),
-              [&](int32_t x, int32_t y) { return lt(L.seq[3 * size_t(x)], L.seq[3 * size_t(y)]); });
     L.rank.resize(size_t(ne));
-    for (int32_t i = 0; i < ne; ++i) L.rank[L.order[i]] = i + 1;
+    if (ne <= 32) {
+        // few lower neighbours: rank = 1 + the number of edges whose far end
+        // is lower, counted over (value, input id) in one integer each;
+        // -0 and +0 are the same value, as in below()
+        uint64_t vk[32];
+        for (int32_t e = 0; e < ne; ++e) {
+            const int32_t x = L.seq[3 * size_t(e)];
+            uint32_t u;
+            const float fx = f[x] + 0.0f;
+            std::memcpy(&u, &fx, 4);
+            u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+            vk[e] = uint64_t(u) << 32 | (uint32_t(inid[x]) ^ 0x80000000u);
+        }
+        for (int32_t e = 0; e < ne; ++e) {
+            int32_t r = 1;
+            for (int32_t j = 0; j < ne; ++j) r += int32_t(vk[j] < vk[e]);
+            L.rank[e] = r;
+        }
+    } else {
+        L.order.resize(size_t(ne));
+        for (int32_t e = 0; e < ne; ++e) L.order[e] = e;
+        std::sort(L.order.begin(), L.order.end(),
+                  [&](int32_t x, int32_t y) { return lt(L.seq[3 * size_t(x)], L.seq[3 * size_t(y)]); });
+        for (int32_t i = 0; i < ne; ++i) L.rank[L.order[i]] = i + 1;
+    }
     if (packed) {
         L.key.resize(size_t(ns));
         for (int32_t s = 0; s < ns; ++s) {
             uint32_t r[3] = {0u, 0u, 0u};
             for (int i = 0; i < L.nseq[s]; ++i) r[i] = uint32_t(L.rank[L.eidx[3 * size_t(s) + i]]);
-            if (r[0] < r[1]) std::swap(r[0], r[1]);
-            if (r[1] < r[2]) std::swap(r[1], r[2]);
-            if (r[0] < r[1]) std::swap(r[0], r[1]);
-            L.key[s] = r[0] << 20 | r[1] << 10 | r[2];
+            const uint32_t hi = std::max(r[0], std::max(r[1], r[2])), lo = std::min(r[0], std::min(r[1], r[2]));
+            L.key[s] = hi << 20 | (r[0] + r[1] + r[2] - hi - lo) << 10 | lo;
         }
     } else {
         for (int32_t s = 0; s < ns; ++s)
@@ -486,19 +523,69 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     L.open.assign(size_t(ns), 0);
     for (int32_t s = ne; s < ns; ++s) L.open[s] = L.dim[s];
     L.state.assign(size_t(ns), 0);
-    L.in_one.assign(size_t(ns), 0);
-    // heap order: std heaps keep the largest on top, so "greater" = later
-    auto later = [&](int32_t x, int32_t y) {
-        if (packed) return L.key[x] > L.key[y];
+    // Two simplices of one lower star never share a value sequence (their
+    // vertex sets differ), so one ascending sort gives each a distinct
+    // position.  Both queues are bitsets over positions: the smallest entry
+    // is the lowest set bit.
+    auto earlier = [&](int32_t x, int32_t y) {
+        if (packed) return L.key[x] < L.key[y];
         const int32_t *sx = &L.seq[3 * size_t(x)], *sy = &L.seq[3 * size_t(y)];
         const int32_t nx = L.nseq[x], ny = L.nseq[y];
         for (int i = 0; i < nx && i < ny; ++i)
-            if (sx[i] != sy[i]) return lt(sy[i], sx[i]);
-        return nx > ny;
+            if (sx[i] != sy[i]) return lt(sx[i], sy[i]);
+        return nx < ny;
     };
-    auto &one = L.heap_one, &zero = L.heap_zero;
-    one.clear();
-    zero.clear();
+    L.at.resize(size_t(ns));
+    const uint32_t B = uint32_t(ne) + 1;  // rank digits 0..ne
+    if (packed && B * B * B <= uint32_t(LowerStar::kDense)) {
+        // few lower neighbours: the ranks (r0, r1, r2) index a dense bitmap
+        // in lexicographic order; its set bits, in order, are the sort
+        const int32_t nwd = int32_t((B * B * B + 63) >> 6);
+        for (int32_t i = 0; i < nwd; ++i) L.dbits[i] = 0u;
+        for (int32_t s = 0; s < ns; ++s) {
+            const uint32_t k = L.key[s];
+            const uint32_t d = ((k >> 20) * B + ((k >> 10) & 1023u)) * B + (k & 1023u);
+            L.dbits[d >> 6] |= uint64_t(1) << (d & 63);
+            L.dslot[d] = s;
+        }
+        int32_t i = 0;
+        for (int32_t w = 0; w < nwd; ++w)
+            for (uint64_t m = L.dbits[w]; m; m &= m - 1u) L.at[i++] = L.dslot[64 * w + __builtin_ctzll(m)];
+        if (i != ns) return -1;  // two simplices with one vertex set: a repeated row entry
+    } else if (packed) {
+        L.kidx.resize(size_t(ns));
+        for (int32_t s = 0; s < ns; ++s) L.kidx[s] = uint64_t(L.key[s]) << 32 | uint32_t(s);
+        std::sort(L.kidx.begin(), L.kidx.end());
+        for (int32_t i = 0; i < ns; ++i) L.at[i] = int32_t(L.kidx[i] & 0xffffffffu);
+    } else {
+        for (int32_t s = 0; s < ns; ++s) L.at[s] = s;
+        std::sort(L.at.begin(), L.at.end(), earlier);
+    }
+    L.pos.resize(size_t(ns));
+    for (int32_t i = 0; i < ns; ++i) L.pos[L.at[i]] = i;
+    const int32_t nw = (ns + 63) >> 6;
+    L.one.assign(size_t(nw), 0u);
+    L.zero.assign(size_t(nw), 0u);
+    int32_t n_one = 0, n_zero = 0;
+    auto has = [&](const std::vector<uint64_t> &q, int32_t s) { return (q[L.pos[s] >> 6] >> (L.pos[s] & 63)) & 1u; };
+    auto push = [&](std::vector<uint64_t> &q, int32_t &n, int32_t s) {
+        const uint64_t bit = uint64_t(1) << (L.pos[s] & 63);
+        uint64_t &w = q[L.pos[s] >> 6];
+        if (!(w & bit)) {
+            w |= bit;
+            ++n;
+        }
+    };
+    auto pop = [&](std::vector<uint64_t> &q, int32_t &n) -> int32_t {
+        for (int32_t i = 0; i < nw; ++i)
+            if (q[i]) {
+                const int b = __builtin_ctzll(q[i]);
+                q[i] &= q[i] - 1u;
+                --n;
+                return L.at[64 * i + b];
+            }
+        return -1;
+    };
     auto classify = [&](int32_t s) {
         L.state[s] = 1;
         for (int32_t q = L.cof_off[s]; q < L.cof_off[s + 1]; ++q) L.open[L.cof[q]]--;
@@ -506,26 +593,18 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     auto offer_cofaces = [&](int32_t s) {
         for (int32_t q = L.cof_off[s]; q < L.cof_off[s + 1]; ++q) {
             const int32_t c = L.cof[q];
-            if (!L.state[c] && !L.in_one[c] && L.open[c] == 1) {
-                L.in_one[c] = 1;
-                one.push_back(c);
-                std::push_heap(one.begin(), one.end(), later);
-            }
+            if (!L.state[c] && L.open[c] == 1 && !has(L.one, c)) push(L.one, n_one, c);
         }
     };
     int32_t first = 0;
     for (int32_t s = 1; s < ne; ++s)
-        if (later(first, s)) first = s;
+        if (L.pos[s] < L.pos[first]) first = s;
     a.v_up[v] = L.gid[first];
     a.e_down[L.gid[first]] = v;
     a.e_up[L.gid[first]] = -1;
-    L.state[first] = 1;
-    for (int32_t q = L.cof_off[first]; q < L.cof_off[first + 1]; ++q) L.open[L.cof[q]]--;
+    classify(first);
     for (int32_t s = 0; s < ne; ++s)
-        if (s != first) {
-            zero.push_back(s);
-            std::push_heap(zero.begin(), zero.end(), later);
-        }
+        if (s != first) push(L.zero, n_zero, s);
     offer_cofaces(first);
     // every other simplex starts unpaired
     for (int32_t s = 0; s < ns; ++s) {
@@ -545,16 +624,12 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
             a.t_down[gh] = gl;
         }
     };
-    while (!one.empty() || !zero.empty()) {
-        while (!one.empty()) {
-            std::pop_heap(one.begin(), one.end(), later);
-            const int32_t x = one.back();
-            one.pop_back();
-            L.in_one[x] = 0;
+    while (n_one || n_zero) {
+        while (n_one) {
+            const int32_t x = pop(L.one, n_one);
             if (L.state[x]) continue;
             if (L.open[x] == 0) {
-                zero.push_back(x);
-                std::push_heap(zero.begin(), zero.end(), later);
+                push(L.zero, n_zero, x);
                 continue;
             }
             int32_t g = -1;
@@ -566,10 +641,8 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
             offer_cofaces(x);
             offer_cofaces(g);
         }
-        while (!zero.empty()) {
-            std::pop_heap(zero.begin(), zero.end(), later);
-            const int32_t g = zero.back();
-            zero.pop_back();
+        while (n_zero) {
+            const int32_t g = pop(L.zero, n_zero);
             if (L.state[g]) continue;
             classify(g);  // critical
             offer_cofaces(g);

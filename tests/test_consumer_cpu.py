@@ -104,6 +104,26 @@ def test_dg_consumer_equals_oracle_on_delaunay_and_fan():
     dg_matches_oracle(canon, f_c, inid)
 
 
+@pytest.mark.parametrize("m_ring", [20, 22, 23, 29, 31])
+@pytest.mark.parametrize("centre_top", [True, False])
+def test_dg_consumer_lower_star_sizes_and_signed_zeros(m_ring, centre_top):
+    """A fan centre with m_ring + 2 neighbours: its lower star spans the
+    consumer's small-star orderings (22..33 lower edges when the centre is
+    the maximum) and the general one.  Values repeat and include -0.0 next
+    to +0.0, which are one value, so input ids break those ties."""
+    from test_gpu_parity import fan_mesh
+    xyz, tv = fan_mesh(m_ring)
+    canon = oracle.canonicalize(xyz.shape[0], tv, np.zeros(xyz.shape[0], np.int32), 1)
+    rng = np.random.default_rng(m_ring)
+    f = rng.integers(-2, 3, xyz.shape[0]).astype(np.float32)
+    f[rng.random(xyz.shape[0]) < 0.3] = -0.0
+    f[rng.random(xyz.shape[0]) < 0.3] = 0.0
+    if centre_top:
+        f[0] = 10.0
+    f_c, inid = consumers.canonical_inputs(f, canon["vperm"])
+    dg_matches_oracle(canon, f_c, inid)
+
+
 def test_dg_consumer_rejects_inconsistent_relations():
     xyz, tv = gen.freudenthal_grid(2, permute=True, seed=3)
     canon = oracle.canonicalize(xyz.shape[0], tv, np.zeros(xyz.shape[0], np.int32), 1)
