@@ -679,10 +679,10 @@ def coboundary_leg(args, gale, gen):
 def gradient_leg(args, gale, gen):
     """The discrete gradient of a Gaussian-mixture field on a grid of the
     same recipe (Section 5.1, DiscreteGradient): wall time of each step -
-    the enumeration, VE + VF on the GPU (with the VT + VV + ET build the pass
-    starts with) and their copy to the host, the VT export, and the consumer
-    threads (which answer FE / TF themselves) - and the oracle on an 8^3
-    sample."""
+    the enumeration with its lists fetched into host arrays, VE + VF on the
+    GPU (with the VT + VV + ET build the pass starts with) and their copy to
+    the host, the VT export with the TV rows, and the consumer threads
+    (which answer FE / TF themselves) - and the oracle on an 8^3 sample."""
     import torch
     import consumers
     n = args.dg_grid
@@ -697,6 +697,7 @@ def gradient_leg(args, gale, gen):
         t = {}
         t0 = time.perf_counter()
         c.enumerate(gale.ENUM_SORTED)
+        en = c.enumeration()
         t["enumeration_s"] = time.perf_counter() - t0
         t0 = time.perf_counter()
         cb = c.coboundary(gale.CB_VE | gale.CB_VF)
@@ -706,9 +707,8 @@ def gradient_leg(args, gale, gen):
         I_V, _, _ = c.intervals()
         b = c.export(gale.VT)
         vt = consumers.csr_from_bulk(b["vt_off"], b["vt_val"], I_V)
-        t["vt_export_s"] = time.perf_counter() - t0
-        en = c.enumeration()
         rows = c.rows()
+        t["vt_export_s"] = time.perf_counter() - t0
         g, wall = consumers.discrete_gradient_arrays(f_c, inid, cb["VE"], cb["VF"], vt, en["E"], en["F"], rows,
                                                      nthreads=threads)
         t["consumer_s"] = wall

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "gale_ctx.h"
+#include "gale_par.h"
 
 using gale::WorkItem;
 
@@ -889,7 +890,7 @@ gale_status gale_get_intervals(gale_ctx *ctx, int64_t *I_V, int64_t *I_T, int64_
 
 gale_status gale_get_rows(gale_ctx *ctx, int32_t *rows) {
     if (!ctx || !rows) return fail(GALE_EINVAL, "NULL argument");
-    memcpy(rows, ctx->hm.rows.data(), sizeof(int32_t) * 4 * ctx->hm.nt);
+    gale::parallel_copy(rows, ctx->hm.rows.data(), 4 * ctx->hm.nt, gale::host_threads(0));
     return GALE_OK;
 }
 

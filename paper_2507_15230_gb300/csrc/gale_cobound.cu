@@ -42,12 +42,14 @@
 #include <vector>
 
 #include "gale_ctx.h"
+#include "gale_enum.h"
 
 namespace gale {
 
 // device copies the coboundary pass keeps in the context
 struct Cobound {
-    uint64_t enm_gen = 0;  // the enumeration the copies were made from
+    uint64_t enm_gen = 0;  // the enumeration the lookup index was made from
+    uint64_t dev_gen = 0;  // the enumeration E, F, IE, IF (and ebk, fbk) hold
     int32_t *rows = nullptr, *cluster_of = nullptr;
     int32_t *E = nullptr, *F = nullptr, *ebk = nullptr, *fbk = nullptr;
     int64_t *IE = nullptr, *IF = nullptr;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(kThreads) k_eo(CbMesh m, int32_t *eo) {
         int64_t lo = m.IE[k], hi = m.IE[k + 1];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (m.E[2 * int64_t(m.ebk[mid])] < v) lo = mid + 1;
+            if (m.E[2 * int64_t(edge_id(m, mid))] < v) lo = mid + 1;
             else hi = mid;
         }
         eo[v] = int32_t(lo);
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(kThreads) k_fo(CbMesh m, int32_t *fo) {
         int64_t lo = m.IF[k], hi = m.IF[k + 1];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (m.F[3 * int64_t(m.fbk[mid])] < v) lo = mid + 1;
+            if (m.F[3 * int64_t(face_id(m, mid))] < v) lo = mid + 1;
             else hi = mid;
         }
         fo[v] = int32_t(lo);
@@ -492,12 +494,12 @@ __global__ void __launch_bounds__(kThreads) k_keys(CbMesh m, int32_t *ekw, int32
                                                    int32_t *f2s) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < m.nE; j += stride) {
-        const int32_t id = m.ebk[j];
+        const int32_t id = edge_id(m, j);
         ekw[j] = m.E[2 * int64_t(id) + 1];
         e2s[id] = int32_t(j);
     }
     for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < m.nF; p += stride) {
-        const int32_t id = m.fbk[p];
+        const int32_t id = face_id(m, p);
         fkc[p] = m.F[3 * int64_t(id) + 2];
         f2s[id] = int32_t(p);
     }
@@ -510,12 +512,12 @@ __global__ void __launch_bounds__(kThreads) k_feo(CbMesh m, const int32_t *fo, i
             feo[j] = int32_t(m.nF);
             continue;
         }
-        const int32_t id = m.ebk[j];
+        const int32_t id = edge_id(m, j);
         const int32_t a = m.E[2 * int64_t(id)], b = m.E[2 * int64_t(id) + 1];
         int64_t lo = fo[a], hi = fo[a + 1];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (m.F[3 * int64_t(m.fbk[mid]) + 1] < b) lo = mid + 1;
+            if (m.F[3 * int64_t(face_id(m, mid)) + 1] < b) lo = mid + 1;
             else hi = mid;
         }
         feo[j] = int32_t(lo);
@@ -604,24 +606,20 @@ bool grow(gale_ctx *ctx, T *&p, int64_t &cap, int64_t need) {
 }
 
 template <class T>
-T *upload(gale_ctx *ctx, const std::vector<T> &h, cudaStream_t s) {
-    T *d = static_cast<T *>(ctx->dalloc(std::max<size_t>(h.size(), 1) * sizeof(T)));
-    if (d && !h.empty()) cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+T *upload(gale_ctx *ctx, const T *h, size_t n, cudaStream_t s) {
+    T *d = static_cast<T *>(ctx->dalloc(std::max<size_t>(n, 1) * sizeof(T)));
+    if (d && n) cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, s);
     return d;
+}
+template <class T>
+T *upload(gale_ctx *ctx, const std::vector<T> &h, cudaStream_t s) {
+    return upload(ctx, h.data(), h.size(), s);
 }
 
 }  // namespace
 
-// the enumeration's host arrays (gale_enum.cpp)
-bool enumeration_arrays(gale_ctx *ctx, const std::vector<int32_t> **E, const std::vector<int32_t> **F,
-                        const std::vector<int32_t> **ebk, const std::vector<int32_t> **fbk,
-                        const std::vector<int64_t> **IE, const std::vector<int64_t> **IF, int32_t *order,
-                        uint64_t *gen);
-
-// Sorted enumeration on the device: E, F, I_E, I_F into host vectors.
-// Builds the ET rows of every cluster first.  ENOTFOUND (nothing done) when
-// the context cannot: no device or ET not preconditioned.
-gale_status enumerate_sorted_device(gale_ctx *ctx, std::vector<int32_t> &E, std::vector<int32_t> &F,
+// Sorted enumeration on the device (declared in gale_enum.h).
+gale_status enumerate_sorted_device(gale_ctx *ctx, uint64_t gen, raw_vector<int32_t> &E, raw_vector<int32_t> &F,
                                     std::vector<int64_t> &IE, std::vector<int64_t> &IF) {
     if (ctx->device < 0 || (ctx->precond & GALE_ET) == 0) return GALE_ENOTFOUND;
     gale_status st = gale_build_clusters(ctx, nullptr, 0, GALE_ET, GALE_MODE_BATCHED);
@@ -714,20 +712,47 @@ gale_status enumerate_sorted_device(gale_ctx *ctx, std::vector<int32_t> &E, std:
     }
     k_enum_faces<true><<<grid_for(nE), kThreads, 0, s>>>(m, d_E, nullptr, d_FS, d_F, ctx->d_err);
     k_enum_if<<<grid_for(K + 1), kThreads, 0, s>>>(d_IE, d_FS, K, d_IF);
-    E.resize(size_t(2) * nE);
-    F.resize(size_t(3) * nF);
+    // the host arrays' pages are touched by all host threads while the
+    // fill pass runs, so the copies below take no page faults
+    const int th = host_threads(0);
+    parallel_resize(E, size_t(2) * nE, th);
+    parallel_resize(F, size_t(3) * nF, th);
     IF.assign(size_t(K) + 1, 0);
     bool ok = cudaMemcpyAsync(E.data(), d_E, E.size() * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
               cudaMemcpyAsync(F.data(), d_F, F.size() * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
               cudaMemcpyAsync(IF.data(), d_IF, IF.size() * 8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
               cudaStreamSynchronize(s) == cudaSuccess;
-    release();
-    if (!ok) return fail(GALE_ECUDA, "enumeration fill pass failed");
+    if (!ok) {
+        release();
+        return fail(GALE_ECUDA, "enumeration fill pass failed");
+    }
     cudaMemcpy(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost);
     if (e) {
         cudaMemset(ctx->d_err, 0, 4);
+        release();
         return fail(GALE_EDEVICE, "enumeration fill pass: error word " + std::to_string(e));
     }
+    // the device lists stay with the coboundary pass, which would otherwise
+    // upload the same arrays again
+    for (int32_t **p : {&cb.E, &cb.F, &cb.ebk, &cb.fbk})
+        if (*p) {
+            ctx->dfree(*p);
+            *p = nullptr;
+        }
+    for (int64_t **p : {&cb.IE, &cb.IF})
+        if (*p) {
+            ctx->dfree(*p);
+            *p = nullptr;
+        }
+    cb.E = d_E;
+    cb.F = d_F;
+    cb.IE = d_IE;
+    cb.IF = d_IF;
+    cb.dev_gen = gen;
+    tmp.erase(std::remove_if(tmp.begin(), tmp.end(),
+                             [&](void *p) { return p == d_E || p == d_F || p == d_IE || p == d_IF; }),
+              tmp.end());
+    release();
     return GALE_OK;
 }
 
@@ -742,13 +767,10 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     const uint32_t need = GALE_VT | GALE_VV | GALE_ET;
     if ((ctx->precond & need) != need)
         return fail(GALE_EINVAL, "coboundary relations need VT, VV and ET in the precondition mask");
-    const std::vector<int32_t> *E, *F, *ebk, *fbk;
-    const std::vector<int64_t> *IE, *IF;
-    int32_t order = 0;
-    uint64_t gen = 0;
-    if (!enumeration_arrays(ctx, &E, &F, &ebk, &fbk, &IE, &IF, &order, &gen))
-        return fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
-    const int64_t nE = int64_t(E->size() / 2), nF = int64_t(F->size() / 3);
+    EnumView ev{};
+    if (!enumeration_view(ctx, &ev)) return fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
+    const int64_t nE = ev.nE, nF = ev.nF;
+    const uint64_t gen = ev.gen;
     if (nE >= INT32_MAX || nF >= INT32_MAX) return fail(GALE_EINVAL, "more than 2^31 - 1 edges or triangles");
     // the stars, neighbour sets and edge stars of every vertex
     gale_status st = gale_build_clusters(ctx, nullptr, 0, need, GALE_MODE_BATCHED);
@@ -780,25 +802,34 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
         return int(std::min<int64_t>(std::max<int64_t>((n + kThreads - 1) / kThreads, 1), int64_t(sms) * 16));
     };
     if (cb.enm_gen != gen) {
-        int32_t **own[] = {&cb.E, &cb.F, &cb.ebk, &cb.fbk, &cb.eo, &cb.ekw, &cb.feo, &cb.fkc, &cb.fo, &cb.e2s,
-                           &cb.f2s};
-        for (int32_t **p : own)
-            if (*p) {
-                ctx->dfree(*p);
-                *p = nullptr;
-            }
-        for (int64_t **p : {&cb.IE, &cb.IF})
+        for (int32_t **p : {&cb.eo, &cb.ekw, &cb.feo, &cb.fkc, &cb.fo, &cb.e2s, &cb.f2s})
             if (*p) {
                 ctx->dfree(*p);
                 *p = nullptr;
             }
         cb.enm_gen = 0;
-        cb.E = upload(ctx, *E, s);
-        cb.F = upload(ctx, *F, s);
-        cb.ebk = upload(ctx, *ebk, s);
-        cb.fbk = upload(ctx, *fbk, s);
-        cb.IE = upload(ctx, *IE, s);
-        cb.IF = upload(ctx, *IF, s);
+        if (cb.dev_gen != gen) {  // the lists are not on the device yet
+            for (int32_t **p : {&cb.E, &cb.F, &cb.ebk, &cb.fbk})
+                if (*p) {
+                    ctx->dfree(*p);
+                    *p = nullptr;
+                }
+            for (int64_t **p : {&cb.IE, &cb.IF})
+                if (*p) {
+                    ctx->dfree(*p);
+                    *p = nullptr;
+                }
+            cb.dev_gen = 0;
+            cb.E = upload(ctx, ev.E, size_t(2) * nE, s);
+            cb.F = upload(ctx, ev.F, size_t(3) * nF, s);
+            if (ev.ebk) cb.ebk = upload(ctx, ev.ebk, size_t(nE), s);
+            if (ev.fbk) cb.fbk = upload(ctx, ev.fbk, size_t(nF), s);
+            cb.IE = upload(ctx, ev.IE, size_t(K) + 1, s);
+            cb.IF = upload(ctx, ev.IF, size_t(K) + 1, s);
+            if (!cb.E || !cb.F || (ev.ebk && !cb.ebk) || (ev.fbk && !cb.fbk) || !cb.IE || !cb.IF)
+                return fail(GALE_ENOMEM, "device allocation of the enumeration failed");
+            cb.dev_gen = gen;
+        }
         auto dal = [&](int64_t n) { return static_cast<int32_t *>(ctx->dalloc(size_t(std::max<int64_t>(n, 1)) * 4)); };
         cb.eo = dal(hm.nv + 1);
         cb.fo = dal(hm.nv + 1);
@@ -807,16 +838,17 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
         cb.feo = dal(nE + 1);
         cb.fkc = dal(nF);
         cb.f2s = dal(nF);
-        if (!cb.E || !cb.F || !cb.ebk || !cb.fbk || !cb.IE || !cb.IF || !cb.eo || !cb.fo || !cb.ekw || !cb.e2s ||
-            !cb.feo || !cb.fkc || !cb.f2s)
-            return fail(GALE_ENOMEM, "device allocation of the enumeration failed");
-        cb.sorted_ids = order == GALE_ENUM_SORTED;
+        if (!cb.eo || !cb.fo || !cb.ekw || !cb.e2s || !cb.feo || !cb.fkc || !cb.f2s)
+            return fail(GALE_ENOMEM, "device allocation of the enumeration index failed");
+        // ids follow the vertex-tuple order exactly when no key arrays exist
+        cb.sorted_ids = ev.ebk == nullptr;
         m.E = cb.E;
         m.F = cb.F;
         m.ebk = cb.ebk;
         m.fbk = cb.fbk;
         m.IE = cb.IE;
         m.IF = cb.IF;
+        m.sorted_ids = cb.sorted_ids;
         k_eo<<<grid_for(hm.nv + 1), kThreads, 0, s>>>(m, cb.eo);
         k_fo<<<grid_for(hm.nv + 1), kThreads, 0, s>>>(m, cb.fo);
         k_keys<<<grid_for(std::max(nE, nF)), kThreads, 0, s>>>(m, cb.ekw, cb.e2s, cb.fkc, cb.f2s);

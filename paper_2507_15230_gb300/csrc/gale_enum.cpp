@@ -14,7 +14,8 @@
 // Two numberings within a segment: lexicographic in canonical ids, or the
 // order of first appearance over those tetrahedra with each tetrahedron's
 // combinations in combination order.  For lookups, each segment keeps a view
-// of its ids sorted by vertex tuple (binary search).
+// of its ids sorted by vertex tuple (binary search), built on the first
+// boundary query; in the lexicographic numbering that view is the identity.
 #include <algorithm>
 #include <atomic>
 #include <array>
@@ -26,6 +27,7 @@
 #include <vector>
 
 #include "gale_ctx.h"
+#include "gale_enum.h"
 #include "gale_par.h"
 
 namespace gale {
@@ -33,13 +35,21 @@ namespace gale {
 struct Enumeration {
     int32_t order = -1;
     uint64_t gen = 0;                // distinct for every enumeration of the process
-    std::vector<int32_t> E;          // [2 nE] (u, w), u < w
-    std::vector<int32_t> F;          // [3 nF] (a, b, c), a < b < c
+    raw_vector<int32_t> E;           // [2 nE] (u, w), u < w
+    raw_vector<int32_t> F;           // [3 nF] (a, b, c), a < b < c
     std::vector<int64_t> I_E, I_F;   // [K+1]
-    std::vector<int32_t> e_by_key;   // [nE] per segment: ids in vertex-tuple order
-    std::vector<int32_t> f_by_key;   // [nF]
+    // ids in vertex-tuple order per segment; empty when the numbering is
+    // lexicographic (identity)
+    bool identity = false;
+    raw_vector<int32_t> e_by_key;    // [nE]
+    raw_vector<int32_t> f_by_key;    // [nF]
+    int32_t ebk(int64_t j) const { return identity ? int32_t(j) : e_by_key[size_t(j)]; }
+    int32_t fbk(int64_t p) const { return identity ? int32_t(p) : f_by_key[size_t(p)]; }
     // index inside each segment's interval, over the tuple order: a vertex's
-    // upper edges and an edge's upper triangles are short runs
+    // upper edges and an edge's upper triangles are short runs.  Built by the
+    // first boundary query (ensure_index).
+    std::mutex index_mu;
+    std::atomic<bool> indexed{false};
     std::vector<int32_t> v_eo;       // [nv+1] first tuple position of lower vertex v
     std::vector<int32_t> ekw;        // [nE] upper vertex of each tuple position
     std::vector<int32_t> e_feo;      // [nE+1] first triangle tuple position over each edge
@@ -51,19 +61,21 @@ void enumeration_destroy(gale_ctx *ctx) {
     ctx->enm = nullptr;
 }
 
-bool enumeration_arrays(gale_ctx *ctx, const std::vector<int32_t> **E, const std::vector<int32_t> **F,
-                        const std::vector<int32_t> **ebk, const std::vector<int32_t> **fbk,
-                        const std::vector<int64_t> **IE, const std::vector<int64_t> **IF, int32_t *order,
-                        uint64_t *gen) {
-    if (!ctx->enm) return false;
-    *order = ctx->enm->order;
-    *gen = ctx->enm->gen;
-    *E = &ctx->enm->E;
-    *F = &ctx->enm->F;
-    *ebk = &ctx->enm->e_by_key;
-    *fbk = &ctx->enm->f_by_key;
-    *IE = &ctx->enm->I_E;
-    *IF = &ctx->enm->I_F;
+bool enumeration_view(gale_ctx *ctx, EnumView *v) {
+    const Enumeration *en = ctx->enm;
+    if (!en) return false;
+    const int32_t K = ctx->hm.K;
+    v->order = en->order;
+    v->gen = en->gen;
+    v->nE = en->I_E[size_t(K)];
+    v->nF = en->I_F[size_t(K)];
+    v->E = en->E.data();
+    v->F = en->F.data();
+    v->ebk = en->identity ? nullptr : en->e_by_key.data();
+    v->fbk = en->identity ? nullptr : en->f_by_key.data();
+    v->IE = en->I_E.data();
+    v->IF = en->I_F.data();
+    v->K = K;
     return true;
 }
 
@@ -135,7 +147,7 @@ int64_t edge_pos(const HostMesh &hm, const Enumeration &en, int32_t u, int32_t w
 int64_t edge_id(const HostMesh &hm, const Enumeration &en, int32_t u, int32_t w) {
     if (u > w) std::swap(u, w);
     const int64_t j = edge_pos(hm, en, u, w);
-    return j < 0 ? -1 : en.e_by_key[j];
+    return j < 0 ? -1 : en.ebk(j);
 }
 
 int64_t face_id(const HostMesh &hm, const Enumeration &en, std::array<int32_t, 3> f) {
@@ -143,20 +155,11 @@ int64_t face_id(const HostMesh &hm, const Enumeration &en, std::array<int32_t, 3
     const int64_t j = edge_pos(hm, en, f[0], f[1]);
     if (j < 0) return -1;
     for (int64_t p = en.e_feo[j]; p < en.e_feo[j + 1]; ++p) {
-        if (en.fkc[p] == f[2]) return en.f_by_key[p];
+        if (en.fkc[p] == f[2]) return en.fbk(p);
         if (en.fkc[p] > f[2]) break;
     }
     return -1;
 }
-
-}  // namespace
-
-// the sorted enumeration on the device (gale_cobound.cu); ENOTFOUND when the
-// context has no device or no ET preconditioning
-gale_status enumerate_sorted_device(gale_ctx *ctx, std::vector<int32_t> &E, std::vector<int32_t> &F,
-                                    std::vector<int64_t> &IE, std::vector<int64_t> &IF);
-
-namespace {
 
 // The index over each segment's vertex-tuple order, from the enumeration's
 // lists: one sweep per segment over its vertices, edges and triangles.
@@ -169,9 +172,9 @@ void build_index(Enumeration &en, const HostMesh &hm) {
     en.fkc.resize(size_t(nF));
     parallel_dynamic(K, host_threads(0), 16, [&](int64_t k, int) {
         const int64_t e0 = en.I_E[k], e1 = en.I_E[k + 1], f0 = en.I_F[k], f1 = en.I_F[k + 1];
-        auto eu = [&](int64_t j) { return en.E[2 * int64_t(en.e_by_key[j])]; };
-        auto ew = [&](int64_t j) { return en.E[2 * int64_t(en.e_by_key[j]) + 1]; };
-        auto fa = [&](int64_t p, int c) { return en.F[3 * int64_t(en.f_by_key[p]) + c]; };
+        auto eu = [&](int64_t j) { return en.E[2 * size_t(en.ebk(j))]; };
+        auto ew = [&](int64_t j) { return en.E[2 * size_t(en.ebk(j)) + 1]; };
+        auto fa = [&](int64_t p, int c) { return en.F[3 * size_t(en.fbk(p)) + size_t(c)]; };
         int64_t j = e0, q = f0;
         for (int32_t v = hm.I_V[k]; v < hm.I_V[k + 1]; ++v) {
             while (j < e1 && eu(j) < v) ++j;
@@ -185,6 +188,14 @@ void build_index(Enumeration &en, const HostMesh &hm) {
         }
         for (q = f0; q < f1; ++q) en.fkc[q] = fa(q, 2);
     });
+}
+
+void ensure_index(Enumeration &en, const HostMesh &hm) {
+    if (en.indexed.load(std::memory_order_acquire)) return;
+    std::lock_guard<std::mutex> lock(en.index_mu);
+    if (en.indexed.load(std::memory_order_relaxed)) return;
+    build_index(en, hm);
+    en.indexed.store(true, std::memory_order_release);
 }
 
 }  // namespace
@@ -207,17 +218,13 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
         // edge (a, b) the distinct vertices c > b of the tets of ET(a, b)
         try {
             auto en = std::make_unique<gale::Enumeration>();
-            const gale_status st = gale::enumerate_sorted_device(ctx, en->E, en->F, en->I_E, en->I_F);
+            en->gen = next_gen.fetch_add(1);
+            const gale_status st = gale::enumerate_sorted_device(ctx, en->gen, en->E, en->F, en->I_E, en->I_F);
             if (st == GALE_OK) {
                 std::lock_guard<std::mutex> lock(ctx->mu);
                 if (en->I_F[K] > INT32_MAX) return gale::fail(GALE_EINVAL, "more than 2^31 triangles");
                 en->order = order;
-                en->gen = next_gen.fetch_add(1);
-                en->e_by_key.resize(size_t(en->I_E[K]));
-                en->f_by_key.resize(size_t(en->I_F[K]));
-                std::iota(en->e_by_key.begin(), en->e_by_key.end(), 0);
-                std::iota(en->f_by_key.begin(), en->f_by_key.end(), 0);
-                gale::build_index(*en, hm);
+                en->identity = true;
                 delete ctx->enm;
                 ctx->enm = en.release();
                 return GALE_OK;
@@ -246,8 +253,11 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
             return gale::fail(GALE_EINVAL, "more than 2^31 edges or triangles");
         en->E.resize(size_t(2) * size_t(en->I_E[K]));
         en->F.resize(size_t(3) * size_t(en->I_F[K]));
-        en->e_by_key.resize(size_t(en->I_E[K]));
-        en->f_by_key.resize(size_t(en->I_F[K]));
+        en->identity = order == GALE_ENUM_SORTED;
+        if (!en->identity) {
+            en->e_by_key.resize(size_t(en->I_E[K]));
+            en->f_by_key.resize(size_t(en->I_F[K]));
+        }
         gale::parallel_dynamic(K, gale::host_threads(0), 4, [&](int64_t k, int) {
             const int64_t e0 = en->I_E[k], f0 = en->I_F[k];
             const auto &ev = se[k];
@@ -258,17 +268,15 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
             }
             for (size_t i = 0; i < fv.size(); ++i)
                 for (int c = 0; c < 3; ++c) en->F[3 * (f0 + int64_t(i)) + c] = fv[i][c];
-            // ids of the segment in tuple order (the identity for sorted numbering)
+            if (en->identity) return;
+            // ids of the segment in tuple order
             int32_t *eb = en->e_by_key.data() + e0;
             for (size_t i = 0; i < ev.size(); ++i) eb[i] = int32_t(e0 + int64_t(i));
             int32_t *fb = en->f_by_key.data() + f0;
             for (size_t i = 0; i < fv.size(); ++i) fb[i] = int32_t(f0 + int64_t(i));
-            if (order == GALE_ENUM_FIRST_APPEARANCE) {
-                std::sort(eb, eb + ev.size(), [&](int32_t a, int32_t b) { return ev[a - e0] < ev[b - e0]; });
-                std::sort(fb, fb + fv.size(), [&](int32_t a, int32_t b) { return fv[a - f0] < fv[b - f0]; });
-            }
+            std::sort(eb, eb + ev.size(), [&](int32_t a, int32_t b) { return ev[a - e0] < ev[b - e0]; });
+            std::sort(fb, fb + fv.size(), [&](int32_t a, int32_t b) { return fv[a - f0] < fv[b - f0]; });
         });
-        gale::build_index(*en, hm);
         delete ctx->enm;
         ctx->enm = en.release();
     } catch (const std::bad_alloc &) {
@@ -287,8 +295,9 @@ gale_status gale_get_enumeration(gale_ctx *ctx, int64_t *counts, int32_t *edges,
         counts[0] = en->I_E[K];
         counts[1] = en->I_F[K];
     }
-    if (edges && !en->E.empty()) memcpy(edges, en->E.data(), en->E.size() * 4);
-    if (faces && !en->F.empty()) memcpy(faces, en->F.data(), en->F.size() * 4);
+    const int th = gale::host_threads(0);
+    if (edges && !en->E.empty()) gale::parallel_copy(edges, en->E.data(), int64_t(en->E.size()), th);
+    if (faces && !en->F.empty()) gale::parallel_copy(faces, en->F.data(), int64_t(en->F.size()), th);
     if (I_E) memcpy(I_E, en->I_E.data(), en->I_E.size() * 8);
     if (I_F) memcpy(I_F, en->I_F.data(), en->I_F.size() * 8);
     return GALE_OK;
@@ -296,7 +305,7 @@ gale_status gale_get_enumeration(gale_ctx *ctx, int64_t *counts, int32_t *edges,
 
 gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, int64_t n, int32_t *out) {
     if (!ctx || (n > 0 && (!ids || !out))) return gale::fail(GALE_EINVAL, "NULL argument");
-    const gale::Enumeration *en = ctx->enm;
+    gale::Enumeration *en = ctx->enm;
     if (!en) return gale::fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
     const gale::HostMesh &hm = ctx->hm;
     const int32_t K = hm.K;
@@ -315,6 +324,11 @@ gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, i
     }
     for (int64_t i = 0; i < n; ++i)
         if (ids[i] < 0 || ids[i] >= limit) return gale::fail(GALE_EINVAL, "simplex id out of range");
+    try {
+        gale::ensure_index(*en, hm);
+    } catch (const std::bad_alloc &) {
+        return gale::fail(GALE_ENOMEM, "host allocation of the enumeration index failed");
+    }
     std::atomic<int32_t> missing{0};
     gale::parallel_for(n, gale::host_threads(0), [&](int64_t b, int64_t e, int) {
         for (int64_t i = b; i < e; ++i) {

@@ -1,0 +1,34 @@
+// The enumeration as the coboundary pass reads it, and the device
+// enumeration the host side calls (internal).
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "gale_ctx.h"
+#include "gale_par.h"
+
+namespace gale {
+
+// Host arrays of the current enumeration (gale_enum.cpp), valid while the
+// context holds it.  ebk / fbk are null when ids follow the vertex-tuple
+// order (the lexicographic numbering).
+struct EnumView {
+    int32_t order;
+    uint64_t gen;
+    int32_t K;
+    int64_t nE, nF;
+    const int32_t *E, *F, *ebk, *fbk;
+    const int64_t *IE, *IF;
+};
+bool enumeration_view(gale_ctx *ctx, EnumView *v);
+
+// Sorted enumeration on the device (gale_cobound.cu): E, F, I_E, I_F into
+// host vectors; the device copies stay with the coboundary pass, tagged with
+// gen.  Builds the ET rows of every cluster first.  ENOTFOUND (nothing done)
+// when the context cannot: no device or ET not preconditioned.
+gale_status enumerate_sorted_device(gale_ctx *ctx, uint64_t gen, raw_vector<int32_t> &E, raw_vector<int32_t> &F,
+                                    std::vector<int64_t> &IE, std::vector<int64_t> &IF);
+
+}  // namespace gale

@@ -6,7 +6,11 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstring>
+#include <memory>
+#include <new>
 #include <thread>
+#include <utility>
 #include <vector>
 
 namespace gale {
@@ -53,6 +57,60 @@ void parallel_dynamic(int64_t n, int nthreads, int64_t grain, F &&f) {
     std::vector<std::thread> th;
     for (int i = 0; i < p; ++i) th.emplace_back(body, i);
     for (auto &t : th) t.join();
+}
+
+// An allocator whose value-initialisation leaves trivial elements
+// uninitialised: resize() of a raw_vector only reserves the pages, which the
+// caller then fills (a parallel first touch, a copy from the device).
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U> &) noexcept {}
+    template <class U>
+    void construct(U *p) noexcept {
+        ::new (static_cast<void *>(p)) U;
+    }
+    template <class U, class... A>
+    void construct(U *p, A &&...a) {
+        ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using raw_vector = std::vector<T, NoInitAlloc<T>>;
+
+// Copy n trivially copyable elements with up to nthreads threads, one piece
+// of at least 4M elements each (each thread also takes the first touch of
+// its piece of dst).
+template <class T>
+void parallel_copy(T *dst, const T *src, int64_t n, int nthreads) {
+    const int p = int(std::min<int64_t>(nthreads, std::max<int64_t>(1, n >> 22)));
+    parallel_for(p, p, [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; ++i) {
+            const int64_t lo = n * i / p, hi = n * (i + 1) / p;
+            if (hi > lo) std::memcpy(static_cast<void *>(dst + lo), src + lo, size_t(hi - lo) * sizeof(T));
+        }
+    });
+}
+
+// resize(n) of a raw_vector with its pages first touched (zeroed) by
+// nthreads threads.
+template <class T>
+void parallel_resize(raw_vector<T> &v, size_t n, int nthreads) {
+    v.resize(n);
+    T *d = v.data();
+    const int64_t m = int64_t(n);
+    const int p = int(std::min<int64_t>(nthreads, std::max<int64_t>(1, m >> 22)));
+    parallel_for(p, p, [&](int64_t b, int64_t e, int) {
+        for (int64_t i = b; i < e; ++i) {
+            const int64_t lo = m * i / p, hi = m * (i + 1) / p;
+            if (hi > lo) std::memset(static_cast<void *>(d + lo), 0, size_t(hi - lo) * sizeof(T));
+        }
+    });
 }
 
 }  // namespace gale
