@@ -251,6 +251,18 @@ gale_status gale_bulk_arrays(gale_ctx *ctx, gale_arrays *dev, int64_t *lengths);
  * the copies are done. */
 gale_status gale_bulk_export(gale_ctx *ctx, uint32_t mask, const gale_arrays *host_dst);
 
+/* Copy `bytes` from device memory `src` (an array the library handed out:
+ * a gale_view, gale_bulk_arrays or gale_coboundary pointer) to caller HOST
+ * memory `dst`, ordered after earlier work on the context stream; returns
+ * when the copy is complete.  Page-locked destinations take one copy.
+ * Pageable ones of 32 MB or more go through two 128 MB pinned staging
+ * buffers that the context allocates on first use and keeps until
+ * gale_destroy: the copy engine fills one while the host threads move the
+ * other into place.  gale_bulk_export copies the same way.  EINVAL for
+ * NULL pointers with bytes > 0 or a host-only context; ENOMEM if the
+ * staging buffers cannot be allocated; ECUDA if a copy fails. */
+gale_status gale_copy_to_host(gale_ctx *ctx, void *dst, const void *src, size_t bytes);
+
 /* Build the listed clusters (ids == NULL or n <= 0: all, in id order) for
  * the relations in mask and copy every output array to caller HOST buffers,
  * overlapping the copy of each finished chunk of clusters with the build of

@@ -81,7 +81,7 @@ class ServeStats(ctypes.Structure):
 
 # the symbols include/gale.h declares
 EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
-           "gale_bulk_export", "gale_build_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
+           "gale_bulk_export", "gale_copy_to_host", "gale_build_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
            "gale_autotune", "gale_get_bins", "gale_get_bin_members", "gale_enumerate", "gale_get_enumeration",
            "gale_boundary", "gale_build_coboundary", "gale_serve_configure", "gale_serve_set_lease", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
@@ -110,6 +110,7 @@ def load_library(build: bool = True):
     lib.gale_bulk_view.argtypes = [P, i32, ctypes.POINTER(View)]
     lib.gale_bulk_arrays.argtypes = [P, ctypes.POINTER(Arrays), P]
     lib.gale_bulk_export.argtypes = [P, u32, ctypes.POINTER(Arrays)]
+    lib.gale_copy_to_host.argtypes = [P, P, P, ctypes.c_size_t]
     lib.gale_build_export.argtypes = [P, P, ctypes.c_int32, u32, ctypes.POINTER(Arrays), ctypes.c_int32]
     lib.gale_request.argtypes = [P, i32, u32, i64, ctypes.POINTER(View)]
     lib.gale_release.argtypes = [P, ctypes.POINTER(View)]
@@ -455,18 +456,26 @@ class Context:
         _check(self._lib.gale_boundary(self._h, relation, _p(ids) if ids.size else None, ids.size, _p(out)))
         return out[:ids.size]
 
+    def copy_to_host(self, dev_ptr: int, n: int, out: np.ndarray | None = None) -> np.ndarray:
+        """gale_copy_to_host of n int32 elements at a device pointer the
+        library handed out, into `out` (a new array unless given)."""
+        if out is None:
+            out = np.empty(n, np.int32)
+        assert out.dtype == np.int32 and out.size >= n and out.flags["C_CONTIGUOUS"]
+        if n:
+            _check(self._lib.gale_copy_to_host(self._h, _p(out), dev_ptr, 4 * n))
+        return out[:n]
+
     def coboundary(self, which: int = CB_VE | CB_VF | CB_EF | CB_FT) -> dict:
         """gale_build_coboundary: {"VE"|"VF"|"EF"|"FT": (offsets, values)} as
-        host numpy arrays (the device arrays copied through torch)."""
+        host numpy arrays (copied with gale_copy_to_host)."""
         c = Coboundary()
         _check(self._lib.gale_build_coboundary(self._h, which, ctypes.byref(c)))
         out = {}
         for i, name in enumerate(("VE", "VF", "EF", "FT")):
             if which & (1 << i):
                 n, ln = int(c.rows[i]), int(c.len[i])
-                off = device_tensor(c.off[i], n + 1).cpu().numpy()
-                val = device_tensor(c.val[i], ln).cpu().numpy() if ln else np.empty(0, np.int32)
-                out[name] = (off, val)
+                out[name] = (self.copy_to_host(c.off[i], n + 1), self.copy_to_host(c.val[i], ln))
         return out
 
     def set_tuning(self, threads: int = 0, ctas_per_sm: int = 0):

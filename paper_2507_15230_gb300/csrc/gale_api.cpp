@@ -2,10 +2,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 
 #include "gale_ctx.h"
 #include "gale_par.h"
@@ -458,6 +460,88 @@ void gale::HostMesh::free_blocks() {
     blocks = nullptr;
 }
 
+namespace gale {
+
+namespace {
+constexpr size_t kStageBytes = size_t(128) << 20;  // each of the two staging buffers
+constexpr size_t kDirectBytes = size_t(32) << 20;  // below this a pageable copy goes straight through
+}  // namespace
+
+// Pageable destinations: the copy engine fills one staging buffer while the
+// host threads move the other into place, each thread a fixed slice of every
+// chunk (so the threads also share the first touch of the destination pages).
+gale_status copy_to_host(gale_ctx *ctx, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return GALE_OK;
+    cudaStream_t s = ctx->stream;
+    cudaPointerAttributes at{};
+    const bool locked = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // an unregistered pointer may leave an error behind
+    if (locked || bytes < kDirectBytes) {
+        if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(GALE_ECUDA, "device to host copy failed");
+        return GALE_OK;
+    }
+    std::lock_guard<std::mutex> lock(ctx->stage_mu);
+    for (int b = 0; b < 2; ++b) {
+        if (!ctx->stage[b] && cudaHostAlloc(&ctx->stage[b], kStageBytes, cudaHostAllocDefault) != cudaSuccess) {
+            ctx->stage[b] = nullptr;
+            cudaGetLastError();
+            return fail(GALE_ENOMEM, "pinned staging allocation failed");
+        }
+        if (!ctx->stage_ev[b] && cudaEventCreateWithFlags(&ctx->stage_ev[b], cudaEventDisableTiming) != cudaSuccess) {
+            ctx->stage_ev[b] = nullptr;
+            return fail(GALE_ECUDA, "staging event creation failed");
+        }
+    }
+    const int64_t nch = int64_t((bytes + kStageBytes - 1) / kStageBytes);
+    const int T = std::max(1, std::min(host_threads(0), 32));
+    auto chunk_len = [&](int64_t c) { return std::min(kStageBytes, bytes - size_t(c) * kStageBytes); };
+    auto issue = [&](int64_t c) {
+        return cudaMemcpyAsync(ctx->stage[c & 1], static_cast<const char *>(src) + size_t(c) * kStageBytes,
+                               chunk_len(c), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+               cudaEventRecord(ctx->stage_ev[c & 1], s) == cudaSuccess;
+    };
+    std::atomic<int64_t> ready{-1};  // last chunk whose staging copy is complete
+    std::atomic<int64_t> moved{0};   // slices moved into dst
+    std::atomic<bool> stop{false};
+    auto worker = [&](int t) {
+        for (int64_t c = 0; c < nch; ++c) {
+            while (ready.load(std::memory_order_acquire) < c) {
+                if (stop.load(std::memory_order_acquire)) return;
+                std::this_thread::yield();
+            }
+            const size_t len = chunk_len(c), lo = len * size_t(t) / size_t(T), hi = len * size_t(t + 1) / size_t(T);
+            std::memcpy(static_cast<char *>(dst) + size_t(c) * kStageBytes + lo,
+                        static_cast<const char *>(ctx->stage[c & 1]) + lo, hi - lo);
+            moved.fetch_add(1, std::memory_order_acq_rel);
+        }
+    };
+    bool ok = issue(0) && (nch < 2 || issue(1));
+    std::vector<std::thread> th;
+    th.reserve(size_t(T));
+    for (int t = 0; t < T; ++t) th.emplace_back(worker, t);
+    for (int64_t c = 0; ok && c < nch; ++c) {
+        if (cudaEventSynchronize(ctx->stage_ev[c & 1]) != cudaSuccess) {
+            ok = false;
+            break;
+        }
+        ready.store(c, std::memory_order_release);
+        // the buffer of chunk c takes chunk c + 2 once every thread moved its slice
+        while (moved.load(std::memory_order_acquire) < int64_t(T) * (c + 1)) std::this_thread::yield();
+        if (c + 2 < nch) ok = issue(c + 2);
+    }
+    if (!ok) stop.store(true, std::memory_order_release);
+    for (auto &x : th) x.join();
+    if (!ok) {
+        cudaStreamSynchronize(s);
+        return fail(GALE_ECUDA, "staged device to host copy failed");
+    }
+    return GALE_OK;
+}
+
+}  // namespace gale
+
 extern "C" {
 
 const char *gale_last_error(void) { return gale::t_error.c_str(); }
@@ -477,6 +561,10 @@ void gale_destroy(gale_ctx *ctx) {
             cudaStreamDestroy(ctx->copy_stream);
         }
         for (cudaEvent_t e : ctx->chunk_events) cudaEventDestroy(e);
+        for (int b = 0; b < 2; ++b) {
+            if (ctx->stage[b]) cudaFreeHost(ctx->stage[b]);
+            if (ctx->stage_ev[b]) cudaEventDestroy(ctx->stage_ev[b]);
+        }
         while (!ctx->allocs.empty()) ctx->dfree(ctx->allocs.back().ptr);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     }
@@ -727,11 +815,17 @@ gale_status gale_bulk_export(gale_ctx *ctx, uint32_t mask, const gale_arrays *ho
     for (int a = 0; a < 10; ++a) {
         if (!(mask & rel_of[a] & ctx->bulk_mask) || ctx->bulk_len[a] == 0) continue;
         if (!h[a]) return fail(GALE_EINVAL, "NULL host buffer for a requested array");
-        CUDA_TRY(cudaMemcpyAsync(h[a], ctx->bulk[a], size_t(ctx->bulk_len[a]) * 4, cudaMemcpyDeviceToHost,
-                                 ctx->stream));
+        const gale_status st = gale::copy_to_host(ctx, h[a], ctx->bulk[a], size_t(ctx->bulk_len[a]) * 4);
+        if (st != GALE_OK) return st;
     }
-    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     return GALE_OK;
+}
+
+gale_status gale_copy_to_host(gale_ctx *ctx, void *dst, const void *src, size_t bytes) {
+    if (!ctx || (bytes > 0 && (!dst || !src))) return fail(GALE_EINVAL, "NULL argument");
+    if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    return gale::copy_to_host(ctx, dst, src, bytes);
 }
 
 gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask,

@@ -712,19 +712,17 @@ gale_status enumerate_sorted_device(gale_ctx *ctx, uint64_t gen, raw_vector<int3
     }
     k_enum_faces<true><<<grid_for(nE), kThreads, 0, s>>>(m, d_E, nullptr, d_FS, d_F, ctx->d_err);
     k_enum_if<<<grid_for(K + 1), kThreads, 0, s>>>(d_IE, d_FS, K, d_IF);
-    // the host arrays' pages are touched by all host threads while the
-    // fill pass runs, so the copies below take no page faults
-    const int th = host_threads(0);
-    parallel_resize(E, size_t(2) * nE, th);
-    parallel_resize(F, size_t(3) * nF, th);
+    // the host arrays are left uninitialised: the staged copies write
+    // (and first touch) them from all host threads
+    E.resize(size_t(2) * nE);
+    F.resize(size_t(3) * nF);
     IF.assign(size_t(K) + 1, 0);
-    bool ok = cudaMemcpyAsync(E.data(), d_E, E.size() * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-              cudaMemcpyAsync(F.data(), d_F, F.size() * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-              cudaMemcpyAsync(IF.data(), d_IF, IF.size() * 8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-              cudaStreamSynchronize(s) == cudaSuccess;
-    if (!ok) {
+    gale_status cst = copy_to_host(ctx, E.data(), d_E, E.size() * 4);
+    if (cst == GALE_OK) cst = copy_to_host(ctx, F.data(), d_F, F.size() * 4);
+    if (cst == GALE_OK) cst = copy_to_host(ctx, IF.data(), d_IF, IF.size() * 8);
+    if (cst != GALE_OK) {
         release();
-        return fail(GALE_ECUDA, "enumeration fill pass failed");
+        return cst;
     }
     cudaMemcpy(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost);
     if (e) {

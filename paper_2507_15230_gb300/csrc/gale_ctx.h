@@ -86,6 +86,12 @@ struct gale_ctx {
     std::vector<cudaEvent_t> chunk_events;
     gale::WorkItem *d_chunk_base = nullptr;  // [kMaxExportChunks]
 
+    // device -> host copies into pageable memory (gale::copy_to_host): two
+    // pinned staging buffers, allocated on first use
+    void *stage[2] = {};
+    cudaEvent_t stage_ev[2] = {};
+    std::mutex stage_mu;
+
     // captured full builds, one per mask
     cudaGraphExec_t graphs[16] = {};
     int64_t last_launches = 0;
@@ -107,6 +113,10 @@ struct gale_ctx {
 };
 
 namespace gale {
+// Synchronous device -> host copy of `bytes` on the context stream: one copy
+// into page-locked memory; into pageable memory through the staging buffers,
+// moved into place by the host threads (gale_api.cpp).
+gale_status copy_to_host(gale_ctx *ctx, void *dst, const void *src, size_t bytes);
 void enumeration_destroy(gale_ctx *ctx);  // gale_enum.cpp
 void cobound_destroy(gale_ctx *ctx);      // gale_cobound.cu
 }  // namespace gale

@@ -97,20 +97,4 @@ void parallel_copy(T *dst, const T *src, int64_t n, int nthreads) {
     });
 }
 
-// resize(n) of a raw_vector with its pages first touched (zeroed) by
-// nthreads threads.
-template <class T>
-void parallel_resize(raw_vector<T> &v, size_t n, int nthreads) {
-    v.resize(n);
-    T *d = v.data();
-    const int64_t m = int64_t(n);
-    const int p = int(std::min<int64_t>(nthreads, std::max<int64_t>(1, m >> 22)));
-    parallel_for(p, p, [&](int64_t b, int64_t e, int) {
-        for (int64_t i = b; i < e; ++i) {
-            const int64_t lo = m * i / p, hi = m * (i + 1) / p;
-            if (hi > lo) std::memset(static_cast<void *>(d + lo), 0, size_t(hi - lo) * sizeof(T));
-        }
-    });
-}
-
 }  // namespace gale

@@ -102,3 +102,16 @@ def test_host_init_delaunay_matches_oracle():
             ext, halo = ctx.working_set(k)
             oext, ohalo = oracle.working_set(canon, k)
             assert np.array_equal(ext, oext) and np.array_equal(halo, ohalo), k
+
+
+def test_copy_to_host_refuses_host_only_and_null(small_mesh):
+    """gale_copy_to_host needs a device context and non-NULL pointers; a
+    zero-byte copy of NULL is still refused on a host-only context."""
+    lib = gale.load_library()
+    with host_ctx(small_mesh) as ctx:
+        buf = np.zeros(4, np.int32)
+        assert lib.gale_copy_to_host(ctx._h, buf.ctypes.data, None, 16) == 1  # EINVAL
+        assert lib.gale_copy_to_host(ctx._h, None, None, 0) == 1  # EINVAL
+        assert lib.gale_copy_to_host(None, buf.ctypes.data, 1, 16) == 1  # EINVAL
+        with pytest.raises(gale.GaleError):
+            ctx.copy_to_host(1 << 20, 4, out=buf)
