@@ -10,6 +10,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <random>
 #include <thread>
@@ -22,6 +23,17 @@ namespace {
 // Vertex w is below v when f(w) < f(v), ties broken by input id.
 inline bool below(const float *f, const int32_t *inid, int32_t w, int32_t v) {
     return f[w] < f[v] || (f[w] == f[v] && inid[w] < inid[v]);
+}
+
+// (value, input id) as one unsigned integer ordered like below(): the
+// float's bits made monotone (-0 and +0 made one value first), the id
+// offset to unsigned.  Values must not be NaN.
+inline uint64_t order_key(float fx, int32_t id) {
+    fx += 0.0f;
+    uint32_t u;
+    std::memcpy(&u, &fx, 4);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return uint64_t(u) << 32 | (uint32_t(id) ^ 0x80000000u);
 }
 
 struct DSU {
@@ -303,7 +315,7 @@ namespace {
 
 struct LowerStar {
     // local simplices: edges [0, ne), triangles [ne, ne + nf), tets after
-    std::vector<int32_t> gid, dim, seq, nseq, open, state, face, cof_off, cof, fill;
+    std::vector<int32_t> gid, seq, open, state, face, cof_off, cof, fill;
     std::vector<int32_t> order, rank, eidx, at, pos;  // at: simplex at each queue position; pos: its inverse
     std::vector<uint64_t> kidx, one, zero;            // sort keys; the two queues as position bitsets
     // dense ordering of small lower stars: one bit per rank triple
@@ -321,6 +333,7 @@ struct LowerStar {
 struct DgArgs {
     const float *f;
     const int32_t *inid;
+    const uint64_t *vk;  // order_key of every vertex, or null (computed on the fly)
     const int64_t *ve_off, *vf_off, *vt_off;
     const int32_t *ve_val, *vf_val, *vt_val, *ev, *fv, *tv;
     int32_t *v_up, *e_down, *e_up, *f_down, *f_up, *t_down;
@@ -339,25 +352,24 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     const size_t cap = size_t((ve1 - ve0) + (vf1 - vf0) + (vt1 - vt0));
     if (L.gid.size() < cap) {
         L.gid.resize(cap);
-        L.dim.resize(cap);
-        L.nseq.resize(cap);
         L.seq.resize(3 * cap);
     }
-    int32_t *gid = L.gid.data(), *dim = L.dim.data(), *nseq = L.nseq.data(), *seq = L.seq.data();
-    const float fv0 = f[v];
-    const int32_t iv0 = inid[v];
-    auto low = [&](int32_t x) -> int32_t {  // below(x, v)
-        const float fx = f[x];
-        return int32_t(fx < fv0) | (int32_t(fx == fv0) & int32_t(inid[x] < iv0));
-    };
+    int32_t *gid = L.gid.data(), *seq = L.seq.data();
+    const uint64_t *vk = a.vk;
+    auto key = [&](int32_t x) { return vk ? vk[x] : order_key(f[x], inid[x]); };
+    const uint64_t kv = key(v);
+    auto low = [&](int32_t x) -> int32_t { return int32_t(key(x) < kv); };  // below(x, v)
+    // The output entries of every star simplex are written below, at ids
+    // spread over the whole mesh: their lines are requested here already.
     int32_t n = 0, bad = 0;
     for (int64_t q = ve0; q < ve1; ++q) {
         const int32_t e = a.ve_val[q];
+        __builtin_prefetch(a.e_down + e, 1);
+        __builtin_prefetch(a.e_up + e, 1);
         const int32_t x = a.ev[2 * int64_t(e)], y = a.ev[2 * int64_t(e) + 1];
         bad |= int32_t(x != v) & int32_t(y != v);
         const int32_t o = x == v ? y : x;
         gid[n] = e;
-        dim[n] = nseq[n] = 1;
         seq[3 * n] = o;
         seq[3 * n + 1] = seq[3 * n + 2] = -1;
         n += low(o);
@@ -365,11 +377,12 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     const int32_t ne = n;
     for (int64_t q = vf0; q < vf1; ++q) {
         const int32_t t = a.vf_val[q];
+        __builtin_prefetch(a.f_down + t, 1);
+        __builtin_prefetch(a.f_up + t, 1);
         const int32_t *x = a.fv + 3 * int64_t(t);
         bad |= int32_t((x[0] == v) + (x[1] == v) + (x[2] == v) != 1);
         const int32_t o0 = x[0] == v ? x[1] : x[0], o1 = x[2] == v ? x[1] : x[2];
         gid[n] = t;
-        dim[n] = nseq[n] = 2;
         seq[3 * n] = o0;
         seq[3 * n + 1] = o1;
         seq[3 * n + 2] = -1;
@@ -378,13 +391,13 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     const int32_t nf = n - ne;
     for (int64_t q = vt0; q < vt1; ++q) {
         const int32_t t = a.vt_val[q];
+        __builtin_prefetch(a.t_down + t, 1);
         const int32_t *x = a.tv + 4 * int64_t(t);
         bad |= int32_t((x[0] == v) + (x[1] == v) + (x[2] == v) + (x[3] == v) != 1);
         const int32_t o0 = x[0] == v ? x[1] : x[0];
         const int32_t o1 = (x[0] == v) | (x[1] == v) ? x[2] : x[1];
         const int32_t o2 = x[3] == v ? x[2] : x[3];
         gid[n] = t;
-        dim[n] = nseq[n] = 3;
         seq[3 * n] = o0;
         seq[3 * n + 1] = o1;
         seq[3 * n + 2] = o2;
@@ -392,6 +405,9 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     }
     if (bad) return -1;
     const int32_t ns = n;
+    // edges [0, ne), triangles [ne, ne + nf), tets after: a simplex's
+    // dimension is also the number of its vertices other than v
+    auto dim_of = [&](int32_t s) { return 1 + int32_t(s >= ne) + int32_t(s >= ne + nf); };
     if (ne == 0) {
         a.v_up[v] = -1;
         return ns == 0 ? 0 : -1;
@@ -430,16 +446,16 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
         return -1;
     };
     for (int32_t s = 0; s < ns; ++s) {
-        if (L.dim[s] == 1) {
+        if (dim_of(s) == 1) {
             L.eidx[3 * size_t(s)] = s;
             continue;
         }
-        for (int i = 0; i < L.nseq[s]; ++i) {
+        for (int i = 0; i < dim_of(s); ++i) {
             const int32_t e = edge_to(L.seq[3 * size_t(s) + i]);
             if (e < 0) return -1;
             L.eidx[3 * size_t(s) + i] = e;
         }
-        if (L.dim[s] == 2) {
+        if (dim_of(s) == 2) {
             L.face[3 * size_t(s)] = L.eidx[3 * size_t(s)];
             L.face[3 * size_t(s) + 1] = L.eidx[3 * size_t(s) + 1];
             if (small) {
@@ -476,18 +492,11 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
         // few lower neighbours: rank = 1 + the number of edges whose far end
         // is lower, counted over (value, input id) in one integer each;
         // -0 and +0 are the same value, as in below()
-        uint64_t vk[32];
-        for (int32_t e = 0; e < ne; ++e) {
-            const int32_t x = L.seq[3 * size_t(e)];
-            uint32_t u;
-            const float fx = f[x] + 0.0f;
-            std::memcpy(&u, &fx, 4);
-            u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-            vk[e] = uint64_t(u) << 32 | (uint32_t(inid[x]) ^ 0x80000000u);
-        }
+        uint64_t ek[32];
+        for (int32_t e = 0; e < ne; ++e) ek[e] = key(L.seq[3 * size_t(e)]);
         for (int32_t e = 0; e < ne; ++e) {
             int32_t r = 1;
-            for (int32_t j = 0; j < ne; ++j) r += int32_t(vk[j] < vk[e]);
+            for (int32_t j = 0; j < ne; ++j) r += int32_t(ek[j] < ek[e]);
             L.rank[e] = r;
         }
     } else {
@@ -501,27 +510,27 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
         L.key.resize(size_t(ns));
         for (int32_t s = 0; s < ns; ++s) {
             uint32_t r[3] = {0u, 0u, 0u};
-            for (int i = 0; i < L.nseq[s]; ++i) r[i] = uint32_t(L.rank[L.eidx[3 * size_t(s) + i]]);
+            for (int i = 0; i < dim_of(s); ++i) r[i] = uint32_t(L.rank[L.eidx[3 * size_t(s) + i]]);
             const uint32_t hi = std::max(r[0], std::max(r[1], r[2])), lo = std::min(r[0], std::min(r[1], r[2]));
             L.key[s] = hi << 20 | (r[0] + r[1] + r[2] - hi - lo) << 10 | lo;
         }
     } else {
         for (int32_t s = 0; s < ns; ++s)
-            std::sort(&L.seq[3 * size_t(s)], &L.seq[3 * size_t(s)] + L.nseq[s],
+            std::sort(&L.seq[3 * size_t(s)], &L.seq[3 * size_t(s)] + dim_of(s),
                       [&](int32_t x, int32_t y) { return lt(y, x); });
     }
     // cofaces inside the lower star (CSR over local ids)
     L.cof_off.assign(size_t(ns) + 1, 0);
     for (int32_t s = ne; s < ns; ++s)
-        for (int i = 0; i < L.dim[s]; ++i) L.cof_off[L.face[3 * size_t(s) + i] + 1]++;
+        for (int i = 0; i < dim_of(s); ++i) L.cof_off[L.face[3 * size_t(s) + i] + 1]++;
     for (int32_t s = 0; s < ns; ++s) L.cof_off[s + 1] += L.cof_off[s];
     L.cof.assign(size_t(L.cof_off[ns]), 0);
     L.fill.assign(L.cof_off.begin(), L.cof_off.end() - 1);
     for (int32_t s = ne; s < ns; ++s)
-        for (int i = 0; i < L.dim[s]; ++i) L.cof[L.fill[L.face[3 * size_t(s) + i]]++] = s;
+        for (int i = 0; i < dim_of(s); ++i) L.cof[L.fill[L.face[3 * size_t(s) + i]]++] = s;
     // open = faces inside the lower star not yet classified
     L.open.assign(size_t(ns), 0);
-    for (int32_t s = ne; s < ns; ++s) L.open[s] = L.dim[s];
+    for (int32_t s = ne; s < ns; ++s) L.open[s] = dim_of(s);
     L.state.assign(size_t(ns), 0);
     // Two simplices of one lower star never share a value sequence (their
     // vertex sets differ), so one ascending sort gives each a distinct
@@ -530,7 +539,7 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     auto earlier = [&](int32_t x, int32_t y) {
         if (packed) return L.key[x] < L.key[y];
         const int32_t *sx = &L.seq[3 * size_t(x)], *sy = &L.seq[3 * size_t(y)];
-        const int32_t nx = L.nseq[x], ny = L.nseq[y];
+        const int32_t nx = dim_of(x), ny = dim_of(y);
         for (int i = 0; i < nx && i < ny; ++i)
             if (sx[i] != sy[i]) return lt(sx[i], sy[i]);
         return nx < ny;
@@ -610,13 +619,13 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     for (int32_t s = 0; s < ns; ++s) {
         if (s == first) continue;
         const int32_t g = L.gid[s];
-        if (L.dim[s] == 1) a.e_down[g] = a.e_up[g] = -1;
-        else if (L.dim[s] == 2) a.f_down[g] = a.f_up[g] = -1;
+        if (dim_of(s) == 1) a.e_down[g] = a.e_up[g] = -1;
+        else if (dim_of(s) == 2) a.f_down[g] = a.f_up[g] = -1;
         else a.t_down[g] = -1;
     }
     auto pair = [&](int32_t lo, int32_t hi) {
         const int32_t gl = L.gid[lo], gh = L.gid[hi];
-        if (L.dim[lo] == 1) {
+        if (dim_of(lo) == 1) {
             a.e_up[gl] = gh;
             a.f_down[gh] = gl;
         } else {
@@ -633,7 +642,7 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
                 continue;
             }
             int32_t g = -1;
-            for (int i = 0; i < L.dim[x]; ++i)
+            for (int i = 0; i < dim_of(x); ++i)
                 if (!L.state[L.face[3 * size_t(x) + i]]) g = L.face[3 * size_t(x) + i];
             pair(g, x);
             classify(g);
@@ -659,7 +668,7 @@ int gale_dg_lower_stars(const float *f, const int32_t *inid, int64_t v_begin, in
                         const int32_t *vt_val, const int32_t *ev, const int32_t *fv, const int32_t *tv,
                         int32_t *v_up, int32_t *e_down, int32_t *e_up,
                         int32_t *f_down, int32_t *f_up, int32_t *t_down) {
-    const DgArgs a{f, inid, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv,
+    const DgArgs a{f, inid, nullptr, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv,
                    v_up, e_down, e_up, f_down, f_up, t_down};
     LowerStar L;
     for (int64_t v = v_begin; v < v_end; ++v)
@@ -680,11 +689,22 @@ int gale_dg_run(const float *f, const int32_t *inid, int64_t nv, const int64_t *
                 double *stats) {
     if (nthreads < 1) nthreads = 1;
     if (grain < 1) grain = 1024;
-    const DgArgs a{f, inid, ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv,
-                   v_up, e_down, e_up, f_down, f_up, t_down};
     std::atomic<int64_t> next{0}, done{0};
     std::atomic<int> err{0};
     const auto t0 = std::chrono::steady_clock::now();
+    // every vertex's order key, once (each is read by about 15 lower stars)
+    std::unique_ptr<uint64_t[]> vk(new uint64_t[size_t(std::max<int64_t>(nv, 1))]);  // pages touched by the fill
+    {
+        std::vector<std::thread> th;
+        for (int i = 0; i < nthreads; ++i)
+            th.emplace_back([&, i] {
+                const int64_t b = nv * i / nthreads, e = nv * (i + 1) / nthreads;
+                for (int64_t x = b; x < e; ++x) vk[size_t(x)] = order_key(f[x], inid[x]);
+            });
+        for (auto &t : th) t.join();
+    }
+    const DgArgs a{f, inid, vk.get(), ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv,
+                   v_up, e_down, e_up, f_down, f_up, t_down};
     auto worker = [&]() {
         LowerStar L;
         for (;;) {
