@@ -696,8 +696,7 @@ def gradient_leg(args, gale, gen):
         consumers._load()  # builds / loads the consumer library outside the timed steps
         t = {}
         t0 = time.perf_counter()
-        c.enumerate(gale.ENUM_SORTED)
-        en = c.enumeration()
+        en = c.enumerate(gale.ENUM_SORTED)
         t["enumeration_s"] = time.perf_counter() - t0
         t0 = time.perf_counter()
         cb = c.coboundary(gale.CB_VE | gale.CB_VF)

@@ -165,10 +165,10 @@ def gather_gradient_relations(ctx, order=None):
     VT from the bulk build that pass leaves behind, and TV.  (FE and TF are
     looked up by the consumer itself.)  Returns a dict of host arrays."""
     import paper_2507_15230_gb300 as gale
-    if order is not None:
-        ctx.enumerate(order)
+    en = ctx.enumerate(order) if order is not None else None
     cb = ctx.coboundary(gale.CB_VE | gale.CB_VF)
-    en = ctx.enumeration()
+    if en is None:
+        en = ctx.enumeration()
     I_V, _, _ = ctx.intervals()
     b = ctx.export(gale.VT)
     vt = csr_from_bulk(b["vt_off"], b["vt_val"], I_V)

@@ -618,9 +618,16 @@ T *upload(gale_ctx *ctx, const std::vector<T> &h, cudaStream_t s) {
 
 }  // namespace
 
+bool device_enumeration(gale_ctx *ctx, uint64_t gen, const int32_t **E, const int32_t **F) {
+    if (!ctx->cb || ctx->cb->dev_gen != gen || !ctx->cb->E || !ctx->cb->F) return false;
+    *E = ctx->cb->E;
+    *F = ctx->cb->F;
+    return true;
+}
+
 // Sorted enumeration on the device (declared in gale_enum.h).
-gale_status enumerate_sorted_device(gale_ctx *ctx, uint64_t gen, raw_vector<int32_t> &E, raw_vector<int32_t> &F,
-                                    std::vector<int64_t> &IE, std::vector<int64_t> &IF) {
+gale_status enumerate_sorted_device(gale_ctx *ctx, uint64_t gen, std::vector<int64_t> &IE,
+                                    std::vector<int64_t> &IF) {
     if (ctx->device < 0 || (ctx->precond & GALE_ET) == 0) return GALE_ENOTFOUND;
     gale_status st = gale_build_clusters(ctx, nullptr, 0, GALE_ET, GALE_MODE_BATCHED);
     if (st == GALE_OK) st = gale_synchronize(ctx);
@@ -712,14 +719,10 @@ gale_status enumerate_sorted_device(gale_ctx *ctx, uint64_t gen, raw_vector<int3
     }
     k_enum_faces<true><<<grid_for(nE), kThreads, 0, s>>>(m, d_E, nullptr, d_FS, d_F, ctx->d_err);
     k_enum_if<<<grid_for(K + 1), kThreads, 0, s>>>(d_IE, d_FS, K, d_IF);
-    // the host arrays are left uninitialised: the staged copies write
-    // (and first touch) them from all host threads
-    E.resize(size_t(2) * nE);
-    F.resize(size_t(3) * nF);
+    // only the intervals come to the host; E and F are copied by the
+    // queries that need them (gale_get_enumeration, gale_boundary)
     IF.assign(size_t(K) + 1, 0);
-    gale_status cst = copy_to_host(ctx, E.data(), d_E, E.size() * 4);
-    if (cst == GALE_OK) cst = copy_to_host(ctx, F.data(), d_F, F.size() * 4);
-    if (cst == GALE_OK) cst = copy_to_host(ctx, IF.data(), d_IF, IF.size() * 8);
+    const gale_status cst = copy_to_host(ctx, IF.data(), d_IF, IF.size() * 8);
     if (cst != GALE_OK) {
         release();
         return cst;
@@ -807,6 +810,7 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
             }
         cb.enm_gen = 0;
         if (cb.dev_gen != gen) {  // the lists are not on the device yet
+            if (!ev.E || !ev.F) return fail(GALE_EINVAL, "the enumeration's lists are gone from the device");
             for (int32_t **p : {&cb.E, &cb.F, &cb.ebk, &cb.fbk})
                 if (*p) {
                     ctx->dfree(*p);

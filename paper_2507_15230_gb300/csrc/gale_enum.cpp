@@ -45,6 +45,10 @@ struct Enumeration {
     raw_vector<int32_t> f_by_key;    // [nF]
     int32_t ebk(int64_t j) const { return identity ? int32_t(j) : e_by_key[size_t(j)]; }
     int32_t fbk(int64_t p) const { return identity ? int32_t(p) : f_by_key[size_t(p)]; }
+    // false while E and F exist only on the device (the sorted enumeration
+    // of a device context); the first host query copies them (ensure_host_lists)
+    std::atomic<bool> host_lists{true};
+    std::mutex host_mu;
     // index inside each segment's interval, over the tuple order: a vertex's
     // upper edges and an edge's upper triangles are short runs.  Built by the
     // first boundary query (ensure_index).
@@ -69,8 +73,9 @@ bool enumeration_view(gale_ctx *ctx, EnumView *v) {
     v->gen = en->gen;
     v->nE = en->I_E[size_t(K)];
     v->nF = en->I_F[size_t(K)];
-    v->E = en->E.data();
-    v->F = en->F.data();
+    const bool h = en->host_lists.load(std::memory_order_acquire);
+    v->E = h ? en->E.data() : nullptr;
+    v->F = h ? en->F.data() : nullptr;
     v->ebk = en->identity ? nullptr : en->e_by_key.data();
     v->fbk = en->identity ? nullptr : en->f_by_key.data();
     v->IE = en->I_E.data();
@@ -190,6 +195,24 @@ void build_index(Enumeration &en, const HostMesh &hm) {
     });
 }
 
+gale_status ensure_host_lists(gale_ctx *ctx, Enumeration &en) {
+    if (en.host_lists.load(std::memory_order_acquire)) return GALE_OK;
+    std::lock_guard<std::mutex> lock(en.host_mu);
+    if (en.host_lists.load(std::memory_order_relaxed)) return GALE_OK;
+    const int32_t *dE = nullptr, *dF = nullptr;
+    if (!device_enumeration(ctx, en.gen, &dE, &dF))
+        return fail(GALE_ENOTFOUND, "the enumeration's lists are gone from the device");
+    const int32_t K = ctx->hm.K;
+    en.E.resize(size_t(2) * size_t(en.I_E[K]));
+    en.F.resize(size_t(3) * size_t(en.I_F[K]));
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(GALE_ECUDA, "cudaSetDevice");
+    gale_status st = copy_to_host(ctx, en.E.data(), dE, en.E.size() * 4);
+    if (st == GALE_OK) st = copy_to_host(ctx, en.F.data(), dF, en.F.size() * 4);
+    if (st != GALE_OK) return st;
+    en.host_lists.store(true, std::memory_order_release);
+    return GALE_OK;
+}
+
 void ensure_index(Enumeration &en, const HostMesh &hm) {
     if (en.indexed.load(std::memory_order_acquire)) return;
     std::lock_guard<std::mutex> lock(en.index_mu);
@@ -219,12 +242,12 @@ gale_status gale_enumerate(gale_ctx *ctx, int32_t order) {
         try {
             auto en = std::make_unique<gale::Enumeration>();
             en->gen = next_gen.fetch_add(1);
-            const gale_status st = gale::enumerate_sorted_device(ctx, en->gen, en->E, en->F, en->I_E, en->I_F);
+            const gale_status st = gale::enumerate_sorted_device(ctx, en->gen, en->I_E, en->I_F);
             if (st == GALE_OK) {
                 std::lock_guard<std::mutex> lock(ctx->mu);
-                if (en->I_F[K] > INT32_MAX) return gale::fail(GALE_EINVAL, "more than 2^31 triangles");
                 en->order = order;
                 en->identity = true;
+                en->host_lists.store(false);
                 delete ctx->enm;
                 ctx->enm = en.release();
                 return GALE_OK;
@@ -295,9 +318,24 @@ gale_status gale_get_enumeration(gale_ctx *ctx, int64_t *counts, int32_t *edges,
         counts[0] = en->I_E[K];
         counts[1] = en->I_F[K];
     }
-    const int th = gale::host_threads(0);
-    if (edges && !en->E.empty()) gale::parallel_copy(edges, en->E.data(), int64_t(en->E.size()), th);
-    if (faces && !en->F.empty()) gale::parallel_copy(faces, en->F.data(), int64_t(en->F.size()), th);
+    const int64_t nE = en->I_E[K], nF = en->I_F[K];
+    if (!en->host_lists.load(std::memory_order_acquire)) {
+        // lists still only on the device: copy them straight to the caller
+        const int32_t *dE = nullptr, *dF = nullptr;
+        if ((edges && nE) || (faces && nF)) {
+            if (!gale::device_enumeration(ctx, en->gen, &dE, &dF))
+                return gale::fail(GALE_ENOTFOUND, "the enumeration's lists are gone from the device");
+            if (cudaSetDevice(ctx->device) != cudaSuccess) return gale::fail(GALE_ECUDA, "cudaSetDevice");
+        }
+        gale_status st = GALE_OK;
+        if (edges && nE) st = gale::copy_to_host(ctx, edges, dE, size_t(nE) * 8);
+        if (st == GALE_OK && faces && nF) st = gale::copy_to_host(ctx, faces, dF, size_t(nF) * 12);
+        if (st != GALE_OK) return st;
+    } else {
+        const int th = gale::host_threads(0);
+        if (edges && nE) gale::parallel_copy(edges, en->E.data(), 2 * nE, th);
+        if (faces && nF) gale::parallel_copy(faces, en->F.data(), 3 * nF, th);
+    }
     if (I_E) memcpy(I_E, en->I_E.data(), en->I_E.size() * 8);
     if (I_F) memcpy(I_F, en->I_F.data(), en->I_F.size() * 8);
     return GALE_OK;
@@ -325,6 +363,8 @@ gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, i
     for (int64_t i = 0; i < n; ++i)
         if (ids[i] < 0 || ids[i] >= limit) return gale::fail(GALE_EINVAL, "simplex id out of range");
     try {
+        const gale_status st = gale::ensure_host_lists(ctx, *en);
+        if (st != GALE_OK) return st;
         gale::ensure_index(*en, hm);
     } catch (const std::bad_alloc &) {
         return gale::fail(GALE_ENOMEM, "host allocation of the enumeration index failed");

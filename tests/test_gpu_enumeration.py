@@ -75,3 +75,32 @@ def test_empty_clusters():
     for name in ("VE", "VF", "EF", "FT"):
         off, val = got[name]
         assert val.tolist() == [x for r in want[name] for x in r], name
+
+
+def test_device_lists_reach_the_host_in_any_query_order():
+    """The sorted lists stay on the device until a query needs them: a
+    boundary query first (the host copy and index), the lists after it
+    (from the host copy), and the coboundary pass, which reuses the device
+    copy; and the other order, with the lists straight from the device."""
+    m = gen.small_grid(with_field=False)
+    canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
+    want = oracle.enumerate_simplices(canon, "sorted")
+    cbw = oracle.coboundary(canon, want)
+    lib = gale.load_library()
+    for boundary_first in (True, False):
+        with gale.Context.load(m, device=0) as ctx:
+            assert lib.gale_enumerate(ctx._h, gale.ENUM_SORTED) == 0
+            nF = len(want["F"])
+            if boundary_first:
+                fe = ctx.boundary(gale.REL_FE, np.arange(nF, dtype=np.int64))
+                got = ctx.enumeration()
+                cb = ctx.coboundary()
+            else:
+                cb = ctx.coboundary()
+                got = ctx.enumeration()
+                fe = ctx.boundary(gale.REL_FE, np.arange(nF, dtype=np.int64))
+            assert [tuple(e) for e in got["E"].tolist()] == want["E"]
+            assert [tuple(f) for f in got["F"].tolist()] == want["F"]
+            assert fe.tolist() == oracle.boundary(canon, want, "FE", range(nF))
+            for name in ("VE", "VF", "EF", "FT"):
+                assert cb[name][1].tolist() == [x for r in cbw[name] for x in r], name
