@@ -154,6 +154,8 @@ def discrete_gradient_arrays(f_c, inid_c, ve, vf, vt, ev, fv, tv, nthreads=16, g
     inid_c = np.ascontiguousarray(inid_c, dtype=np.int32)
     rc = lib.gale_dg_run(_p(f_c), _p(inid_c), nv, *[ptr(a) for a in rel], *[ptr(a) for a in out.values()],
                          int(nthreads), int(grain), _p(st))
+    if rc == -2:
+        raise MemoryError("discrete gradient: the vertex key array cannot be allocated")
     if rc != 0:
         raise RuntimeError("discrete gradient: inconsistent relations")
     return out, float(st[0])

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <random>
 #include <thread>
 #include <vector>
@@ -19,6 +20,21 @@
 #include "gale.h"  // public C ABI only
 
 namespace {
+
+// fn(i) for i in [0, n) on up to n threads; the calling thread runs the
+// ranks whose thread could not be started.
+template <class F>
+void run_on_threads(int n, F &&fn) {
+    std::vector<std::thread> th;
+    int started = 0;
+    try {
+        th.reserve(size_t(n));
+        for (; started < n; ++started) th.emplace_back(fn, started);
+    } catch (const std::exception &) {
+    }
+    for (int i = started; i < n; ++i) fn(i);
+    for (auto &t : th) t.join();
+}
 
 // Vertex w is below v when f(w) < f(v), ties broken by input id.
 inline bool below(const float *f, const int32_t *inid, int32_t w, int32_t v) {
@@ -680,7 +696,8 @@ int gale_dg_lower_stars(const float *f, const int32_t *inid, int64_t v_begin, in
  * The same over all nv vertices with nthreads consumer threads; each thread
  * takes blocks of `grain` consecutive vertices from a shared counter (lower
  * stars are disjoint, so the threads write disjoint entries).
- * stats double[2] out: wall seconds, vertices processed.
+ * stats double[2] out: wall seconds, vertices processed.  Returns 0, -1 for
+ * inconsistent relations, -2 if the key array cannot be allocated.
  */
 int gale_dg_run(const float *f, const int32_t *inid, int64_t nv, const int64_t *ve_off, const int32_t *ve_val,
                 const int64_t *vf_off, const int32_t *vf_val, const int64_t *vt_off, const int32_t *vt_val,
@@ -693,19 +710,15 @@ int gale_dg_run(const float *f, const int32_t *inid, int64_t nv, const int64_t *
     std::atomic<int> err{0};
     const auto t0 = std::chrono::steady_clock::now();
     // every vertex's order key, once (each is read by about 15 lower stars)
-    std::unique_ptr<uint64_t[]> vk(new uint64_t[size_t(std::max<int64_t>(nv, 1))]);  // pages touched by the fill
-    {
-        std::vector<std::thread> th;
-        for (int i = 0; i < nthreads; ++i)
-            th.emplace_back([&, i] {
-                const int64_t b = nv * i / nthreads, e = nv * (i + 1) / nthreads;
-                for (int64_t x = b; x < e; ++x) vk[size_t(x)] = order_key(f[x], inid[x]);
-            });
-        for (auto &t : th) t.join();
-    }
+    std::unique_ptr<uint64_t[]> vk(new (std::nothrow) uint64_t[size_t(std::max<int64_t>(nv, 1))]);
+    if (!vk) return -2;
+    run_on_threads(nthreads, [&](int i) {  // the fill also takes the pages' first touch
+        const int64_t b = nv * i / nthreads, e = nv * (i + 1) / nthreads;
+        for (int64_t x = b; x < e; ++x) vk[size_t(x)] = order_key(f[x], inid[x]);
+    });
     const DgArgs a{f, inid, vk.get(), ve_off, vf_off, vt_off, ve_val, vf_val, vt_val, ev, fv, tv,
                    v_up, e_down, e_up, f_down, f_up, t_down};
-    auto worker = [&]() {
+    auto worker = [&](int) {
         LowerStar L;
         for (;;) {
             const int64_t b = next.fetch_add(grain);
@@ -719,9 +732,7 @@ int gale_dg_run(const float *f, const int32_t *inid, int64_t nv, const int64_t *
             done += e - b;
         }
     };
-    std::vector<std::thread> th;
-    for (int i = 0; i < nthreads; ++i) th.emplace_back(worker);
-    for (auto &t : th) t.join();
+    run_on_threads(nthreads, worker);
     stats[0] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     stats[1] = double(done.load());
     return err.load() ? -1 : 0;

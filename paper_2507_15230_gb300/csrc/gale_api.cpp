@@ -519,8 +519,18 @@ gale_status copy_to_host(gale_ctx *ctx, void *dst, const void *src, size_t bytes
     };
     bool ok = issue(0) && (nch < 2 || issue(1));
     std::vector<std::thread> th;
-    th.reserve(size_t(T));
-    for (int t = 0; t < T; ++t) th.emplace_back(worker, t);
+    try {
+        th.reserve(size_t(T));
+        for (int t = 0; t < T; ++t) th.emplace_back(worker, t);
+    } catch (const std::exception &) {  // no threads to be had: copy straight through
+        stop.store(true, std::memory_order_release);
+        for (auto &x : th) x.join();
+        cudaStreamSynchronize(s);
+        if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(GALE_ECUDA, "device to host copy failed");
+        return GALE_OK;
+    }
     for (int64_t c = 0; ok && c < nch; ++c) {
         if (cudaEventSynchronize(ctx->stage_ev[c & 1]) != cudaSuccess) {
             ok = false;
