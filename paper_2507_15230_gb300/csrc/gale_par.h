@@ -15,6 +15,22 @@
 
 namespace gale {
 
+// fn(tid) for tid in [0, p) on p threads.  Ranks whose thread cannot be
+// started (no resources) run on the calling thread afterwards, so no
+// exception leaves a C-ABI call and every rank still runs exactly once.
+template <class F>
+void run_ranks(int p, F &&fn) {
+    std::vector<std::thread> th;
+    int started = 0;
+    try {
+        th.reserve(size_t(p));
+        for (; started < p; ++started) th.emplace_back([&fn, started] { fn(started); });
+    } catch (const std::exception &) {
+    }
+    for (int i = started; i < p; ++i) fn(i);
+    for (auto &t : th) t.join();
+}
+
 // Static split of [0, n) into nthreads contiguous ranges: f(begin, end, tid).
 template <class F>
 void parallel_for(int64_t n, int nthreads, F &&f) {
@@ -25,13 +41,7 @@ void parallel_for(int64_t n, int nthreads, F &&f) {
         f(int64_t(0), n, 0);
         return;
     }
-    std::vector<std::thread> th;
-    th.reserve(p);
-    for (int i = 0; i < p; ++i) {
-        const int64_t b = n * i / p, e = n * (i + 1) / p;
-        th.emplace_back([&f, b, e, i] { f(b, e, i); });
-    }
-    for (auto &t : th) t.join();
+    run_ranks(p, [&](int i) { f(n * i / p, n * (i + 1) / p, i); });
 }
 
 // Work-stealing loop over [0, n) in small grains (uneven per-item cost):
@@ -54,9 +64,7 @@ void parallel_dynamic(int64_t n, int nthreads, int64_t grain, F &&f) {
         body(0);
         return;
     }
-    std::vector<std::thread> th;
-    for (int i = 0; i < p; ++i) th.emplace_back(body, i);
-    for (auto &t : th) t.join();
+    run_ranks(p, body);
 }
 
 // An allocator whose value-initialisation leaves trivial elements

@@ -276,7 +276,11 @@ gale_status Serve::init(gale_ctx *c) {
         else grid = per_sm * ctx->sm_count;
         if (ctx->serve_loop_ctas > 0) grid = std::min(grid, ctx->serve_loop_ctas);
     }
-    leader = std::thread([this] { leader_loop(); });
+    try {
+        leader = std::thread([this] { leader_loop(); });
+    } catch (const std::exception &) {
+        return fail(GALE_ENOMEM, "the serving leader thread could not be started");
+    }
     return GALE_OK;
 }
 
