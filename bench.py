@@ -222,7 +222,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid cubes per axis (256 = the at-scale workload)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--per-cluster-sample", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -328,7 +328,7 @@ def main():
     ids_np = ids.numpy()
     host = {n: torch.empty(lens[n], dtype=torch.int32).pin_memory() for n in lens}
     host_np = {n: t.numpy() for n, t in host.items()}
-    for _ in range(2):  # untimed: first touch of the pinned pages, warm paths
+    for _ in range(5):  # untimed: first touch of the pinned pages, warm paths
         ctx.build_export(ids_np, gale.ALL, out=host_np)
     barrier(dist)
     e2e_step_s = []
