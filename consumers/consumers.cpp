@@ -434,8 +434,11 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
     // of a lower-star edge: eidx holds that edge per (simplex, other vertex),
     // found through a small hash (or a scan in large lower stars), and a
     // triangle is found from its two edges.
-    L.face.assign(size_t(ns) * 3, -1);
-    L.eidx.assign(size_t(ns) * 3, -1);
+    // every entry read below is written first: a simplex's first dim_of(s)
+    if (L.face.size() < size_t(ns) * 3) {
+        L.face.resize(size_t(ns) * 3);
+        L.eidx.resize(size_t(ns) * 3);
+    }
     const bool small = ne <= LowerStar::kSmall;
     if (small) {
         for (int i = 0; i < LowerStar::kHash; ++i) L.hkey[i] = -1;
@@ -446,7 +449,7 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
             L.hkey[h] = x;
             L.hval[h] = e;
         }
-        for (int i = 0; i < ne * LowerStar::kSmall; ++i) L.tri2[i] = -1;
+        for (int i = 0; i < ne * ne; ++i) L.tri2[i] = -1;
     }
     auto edge_to = [&](int32_t x) -> int32_t {
         if (small) {
@@ -476,13 +479,13 @@ int dg_vertex(const DgArgs &a, int32_t v, LowerStar &L) {
             L.face[3 * size_t(s) + 1] = L.eidx[3 * size_t(s) + 1];
             if (small) {
                 const int32_t i = L.eidx[3 * size_t(s)], j = L.eidx[3 * size_t(s) + 1];
-                L.tri2[i * LowerStar::kSmall + j] = s;
-                L.tri2[j * LowerStar::kSmall + i] = s;
+                L.tri2[i * ne + j] = s;
+                L.tri2[j * ne + i] = s;
             }
         }
     }
     auto tri_on = [&](int32_t i, int32_t j) -> int32_t {  // edge indices
-        if (small) return L.tri2[i * LowerStar::kSmall + j];
+        if (small) return L.tri2[i * ne + j];
         for (int32_t t = ne; t < ne + nf; ++t) {
             const int32_t p = L.eidx[3 * size_t(t)], q = L.eidx[3 * size_t(t) + 1];
             if ((p == i && q == j) || (p == j && q == i)) return t;
