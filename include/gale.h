@@ -365,13 +365,19 @@ gale_status gale_get_info(gale_ctx *ctx, gale_info *out);
  *                               combination order (the numbering of the
  *                               paper's worked example FE(f5) = {e2, e6, e9}).
  * Host work, on host-only contexts too; replaces an earlier enumeration.
+ * On a device context with ET preconditioned, GALE_ENUM_SORTED is built on
+ * the GPU instead: only I_E and I_F come to the host, and the lists stay in
+ * device memory (held for gale_build_coboundary) until gale_get_enumeration
+ * copies them to the caller or gale_boundary makes its host copy.
  */
 enum { GALE_ENUM_SORTED = 0, GALE_ENUM_FIRST_APPEARANCE = 1 };
 gale_status gale_enumerate(gale_ctx *ctx, int32_t order);
 
 /* The enumeration (host memory; any pointer may be NULL): counts[2] = edges,
  * triangles; edges int32[2 nE] (u, w); I_E int64[K+1]; faces int32[3 nF]
- * (a, b, c); I_F int64[K+1].  ENOTFOUND before gale_enumerate. */
+ * (a, b, c); I_F int64[K+1].  Lists still on the device are copied straight
+ * into edges / faces (as gale_copy_to_host does).  ENOTFOUND before
+ * gale_enumerate; ECUDA if a device copy fails. */
 gale_status gale_get_enumeration(gale_ctx *ctx, int64_t *counts, int32_t *edges, int64_t *I_E, int32_t *faces,
                                  int64_t *I_F);
 
@@ -382,8 +388,10 @@ gale_status gale_get_enumeration(gale_ctx *ctx, int64_t *counts, int32_t *edges,
  *                (a,b), (a,c), (a,d), (b,c), (b,d), (c,d)
  *   GALE_REL_TF  canonical tet ids -> 4 triangle ids each: (a,b,c),
  *                (a,b,d), (a,c,d), (b,c,d)
- * ids: HOST int64[n]; out: HOST int32[width * n].  EINVAL on an id out of
- * range, ENOTFOUND before gale_enumerate. */
+ * ids: HOST int64[n]; out: HOST int32[width * n].  The first call after a
+ * device enumeration copies the lists to the host and builds the lookup
+ * index.  EINVAL on an id out of range, ENOTFOUND before gale_enumerate,
+ * ENOMEM if the host copy or index cannot be allocated. */
 enum { GALE_REL_FE = 1, GALE_REL_TE = 2, GALE_REL_TF = 3 };
 gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, int64_t n, int32_t *out);
 
