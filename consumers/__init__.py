@@ -53,6 +53,8 @@ def _load():
         lib.gale_open_loop.restype = ctypes.c_int
         lib.gale_dg_run.argtypes = [P, P, i64] + [P] * 15 + [i32, i64, P]
         lib.gale_dg_run.restype = ctypes.c_int
+        lib.gale_dg_lower_stars.argtypes = [P, P, i64, i64] + [P] * 15
+        lib.gale_dg_lower_stars.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -159,6 +161,27 @@ def discrete_gradient_arrays(f_c, inid_c, ve, vf, vt, ev, fv, tv, nthreads=16, g
     if rc != 0:
         raise RuntimeError("discrete gradient: inconsistent relations")
     return out, float(st[0])
+
+
+def lower_stars_into(out, f_c, inid_c, v_begin, v_end, ve, vf, vt, ev, fv, tv):
+    """gale_dg_lower_stars: the lower stars of vertices [v_begin, v_end) on
+    the calling thread, written into `out` (the dict discrete_gradient_arrays
+    returns: every simplex whose highest vertex is in the range gets both
+    of its entries)."""
+    lib = _load()
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32).reshape(-1)
+    i64 = lambda a: np.ascontiguousarray(a, dtype=np.int64)
+    rel = [i64(ve[0]), i32(ve[1]), i64(vf[0]), i32(vf[1]), i64(vt[0]), i32(vt[1]), i32(ev), i32(fv), i32(tv)]
+    ptr = lambda a: a.ctypes.data if a.size else None
+    f_c = np.ascontiguousarray(f_c, dtype=np.float32)
+    inid_c = np.ascontiguousarray(inid_c, dtype=np.int32)
+    names = ("v_up", "e_down", "e_up", "f_down", "f_up", "t_down")
+    assert all(out[k].dtype == np.int32 and out[k].flags["C_CONTIGUOUS"] for k in names)
+    rc = lib.gale_dg_lower_stars(_p(f_c), _p(inid_c), int(v_begin), int(v_end), *[ptr(a) for a in rel],
+                                 *[ptr(out[k]) for k in names])
+    if rc != 0:
+        raise RuntimeError("discrete gradient: inconsistent relations")
+    return out
 
 
 def gather_gradient_relations(ctx, order=None):

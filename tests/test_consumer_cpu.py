@@ -124,6 +124,24 @@ def test_dg_consumer_lower_star_sizes_and_signed_zeros(m_ring, centre_top):
     dg_matches_oracle(canon, f_c, inid)
 
 
+def test_dg_lower_stars_by_ranges_equal_the_threaded_run():
+    """gale_dg_lower_stars over consecutive vertex ranges (keys computed on
+    the fly) fills the same arrays as gale_dg_run (keys precomputed)."""
+    xyz, tv = gen.freudenthal_grid(5, permute=True, seed=41)
+    seg = np.random.default_rng(5).integers(0, 7, xyz.shape[0]).astype(np.int32)
+    canon = oracle.canonicalize(xyz.shape[0], tv, seg, 7)
+    f = np.random.default_rng(6).integers(-3, 4, xyz.shape[0]).astype(np.float32)
+    f_c, inid = consumers.canonical_inputs(f, canon["vperm"])
+    _, rel = oracle_dg_relations(canon)
+    want, _ = consumers.discrete_gradient_arrays(f_c, inid, **rel, nthreads=3, grain=7)
+    got = {k: np.full_like(v, -7) for k, v in want.items()}
+    cuts = [0, 1, 50, 51, 130, len(f_c)]
+    for b, e in zip(cuts[:-1], cuts[1:]):
+        consumers.lower_stars_into(got, f_c, inid, b, e, **rel)
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+
+
 def test_dg_consumer_rejects_inconsistent_relations():
     xyz, tv = gen.freudenthal_grid(2, permute=True, seed=3)
     canon = oracle.canonicalize(xyz.shape[0], tv, np.zeros(xyz.shape[0], np.int32), 1)
