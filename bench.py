@@ -179,7 +179,8 @@ def ref_config(args) -> dict:
     while nv / k > 512:
         k *= 2
     return {"workload": f"grid{n}^3-jitter0.3-kd512: {nv} vertices, {nt} tets, {k} clusters",
-            "relations": "VT+VV+ET+TT, canonical sorted CSR", "mode": "CPU oracle, single thread",
+            "relations": "VT+VV+ET+TT, canonical sorted CSR",
+            "mode": "CPU oracle, one copy per host thread, on bounded grid samples of the same recipe",
             "parallelism": "rank 0 only"}
 
 
