@@ -214,25 +214,34 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
  * synchronise the GPU (cudaMalloc / cudaFree may), an application whose own
  * pool owns all of HBM, or code running where allocation is forbidden.
  *   ids      HOST int32[n], 1 <= n <= 4096 cluster ids (a repeated id is
- *            built into each of its slots); EINVAL beyond 4096
+ *            built into each of its slots); EINVAL beyond 4096.  Only
+ *            clusters whose size bin runs in shared memory are accepted:
+ *            EINVAL for a cluster of a spill bin (gale_get_bins reports 1 as
+ *            a bin's sixth value; gale_get_bin_members lists its clusters)
  *   mask     relations to build (within the precondition mask)
  *   dev_out  caller-owned DEVICE arrays, one per requested relation array,
  *            laid out as the bulk arrays of gale_build_clusters for the same
  *            list: clusters consecutive in list order, offsets relative to
- *            their cluster; each array at least the summed lengths that the
- *            sizes of gale_get_intervals give (e.g. vt_off: sum of
- *            (v_end - v_begin + 1), vt_val: sum of the VT sizes)
+ *            their cluster; the arrays of relations outside mask may be NULL
+ *   lengths  HOST int64[10]: how many int32 elements each dev_out array
+ *            holds (same order as gale_arrays; entries of relations outside
+ *            mask are ignored).  Each requested array must hold at least the
+ *            summed lengths that the sizes of gale_get_intervals give for
+ *            the list (e.g. vt_off: sum of (v_end - v_begin + 1), vt_val: sum
+ *            of the VT sizes); EINVAL otherwise, before anything is copied or
+ *            launched
  * The work items, order lists, ticket counters and error word live in one
  * fixed array of about 430 KB of device memory that every GPU which loads
  * the library holds until the process exits; every call reuses it, so calls
- * that overlap on the GPU (from several threads or contexts) race and must
- * be serialised by the caller.  The first call on each device looks up that
- * array's device address; make that first call before any stream capture.
- * The call returns after the build has finished (it synchronises the
- * context stream); EDEVICE if a kernel reported an error.
+ * that overlap on the GPU of one device (from several threads, or from
+ * several contexts on that device) race and must be serialised by the
+ * caller.  The first call on each device looks up that array's device
+ * address; make that first call before any stream capture.  The call returns
+ * after the build has finished (it synchronises the context stream); EDEVICE
+ * if a kernel reported an error.
  */
 gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask,
-                                        const gale_arrays *dev_out);
+                                        const gale_arrays *dev_out, const int64_t *lengths);
 
 /* Wait for all work of the context's stream; EDEVICE if a kernel set its
  * error word (the word is cleared), ECUDA on a CUDA error. */

@@ -106,7 +106,7 @@ def load_library(build: bool = True):
     lib.gale_load_mesh.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(P)]
     lib.gale_build_clusters.argtypes = [P, P, i32, u32, i32]
     lib.gale_synchronize.argtypes = [P]
-    lib.gale_build_clusters_noalloc.argtypes = [P, P, i32, u32, ctypes.POINTER(Arrays)]
+    lib.gale_build_clusters_noalloc.argtypes = [P, P, i32, u32, ctypes.POINTER(Arrays), P]
     lib.gale_bulk_view.argtypes = [P, i32, ctypes.POINTER(View)]
     lib.gale_bulk_arrays.argtypes = [P, ctypes.POINTER(Arrays), P]
     lib.gale_bulk_export.argtypes = [P, u32, ctypes.POINTER(Arrays)]
@@ -279,12 +279,18 @@ class Context:
 
     def build_noalloc(self, ids, mask: int, out: dict):
         """gale_build_clusters_noalloc: build into caller-owned device arrays
-        (out: array name -> CUDA int32 tensor) without any allocation."""
+        (out: array name -> CUDA int32 tensor or None) without any allocation;
+        each tensor's element count is passed as that array's capacity."""
         ids = np.ascontiguousarray(ids, dtype=np.int32)
         a = Arrays()
+        lengths = np.zeros(len(ARRAYS), dtype=np.int64)
         for n, t in out.items():
+            if t is None:
+                continue
             setattr(a, n, t.data_ptr() if t.numel() else None)
-        _check(self._lib.gale_build_clusters_noalloc(self._h, _p(ids), ids.shape[0], mask, ctypes.byref(a)))
+            lengths[ARRAYS.index(n)] = t.numel()
+        _check(self._lib.gale_build_clusters_noalloc(self._h, _p(ids), ids.shape[0], mask, ctypes.byref(a),
+                                                     _p(lengths)))
 
     def synchronize(self):
         _check(self._lib.gale_synchronize(self._h))

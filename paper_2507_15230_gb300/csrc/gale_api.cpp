@@ -250,6 +250,23 @@ SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop) {
     if (in_loop) *in_loop = sel;
     return best;
 }
+// Lengths of the ten output arrays of cluster k under mask.
+void item_lengths(const gale_ctx *ctx, int32_t k, uint32_t mask, int64_t *L) {
+    const int64_t *sz = ctx->sizes.data() + size_t(5) * k;
+    const int64_t nvo = ctx->hm.I_V[k + 1] - ctx->hm.I_V[k];
+    const int64_t nown = ctx->hm.I_T[k + 1] - ctx->hm.I_T[k];
+    const bool vt = mask & GALE_VT, vv = mask & GALE_VV, et = mask & GALE_ET, tt = mask & GALE_TT;
+    L[0] = vt ? nvo + 1 : 0;
+    L[1] = vt ? sz[0] : 0;
+    L[2] = vv ? nvo + 1 : 0;
+    L[3] = vv ? sz[1] : 0;
+    L[4] = et ? nvo + 1 : 0;
+    L[5] = et ? sz[2] : 0;
+    L[6] = et ? sz[2] + 1 : 0;
+    L[7] = et ? sz[3] : 0;
+    L[8] = tt ? nown + 1 : 0;
+    L[9] = tt ? sz[4] : 0;
+}
 }  // namespace gale
 
 namespace {
@@ -308,23 +325,6 @@ gale_status count_pass(gale_ctx *ctx) {
     return GALE_OK;
 }
 
-// Lengths of the ten output arrays of cluster k under mask.
-void item_lengths(const gale_ctx *ctx, int32_t k, uint32_t mask, int64_t *L) {
-    const int64_t *sz = ctx->sizes.data() + size_t(5) * k;
-    const int64_t nvo = ctx->hm.I_V[k + 1] - ctx->hm.I_V[k];
-    const int64_t nown = ctx->hm.I_T[k + 1] - ctx->hm.I_T[k];
-    const bool vt = mask & GALE_VT, vv = mask & GALE_VV, et = mask & GALE_ET, tt = mask & GALE_TT;
-    L[0] = vt ? nvo + 1 : 0;
-    L[1] = vt ? sz[0] : 0;
-    L[2] = vv ? nvo + 1 : 0;
-    L[3] = vv ? sz[1] : 0;
-    L[4] = et ? nvo + 1 : 0;
-    L[5] = et ? sz[2] : 0;
-    L[6] = et ? sz[2] + 1 : 0;
-    L[7] = et ? sz[3] : 0;
-    L[8] = tt ? nown + 1 : 0;
-    L[9] = tt ? sz[4] : 0;
-}
 
 // Launch order of listed clusters, chunk by chunk and, within a chunk, bin by
 // bin, each bin's members in the bin's largest-first order: the positions of
@@ -690,7 +690,7 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
     int64_t run[10] = {};
     for (int32_t i = 0; i < cnt; ++i) {
         int64_t L[10];
-        item_lengths(ctx, list[i], mask, L);
+        gale::item_lengths(ctx, list[i], mask, L);
         for (int a = 0; a < 10; ++a) {
             ctx->bulk_offs[size_t(i) * 10 + a] = run[a];
             run[a] += L[a];
@@ -874,7 +874,7 @@ gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint
     std::vector<int64_t> bytes_before(size_t(cnt) + 1, 0);
     for (int32_t i = 0; i < cnt; ++i) {
         int64_t L[10];
-        item_lengths(ctx, list[i], mask, L);
+        gale::item_lengths(ctx, list[i], mask, L);
         int64_t b = 0;
         for (int a = 0; a < 10; ++a) {
             ctx->bulk_offs[size_t(i) * 10 + a] = run[a];
@@ -1081,7 +1081,7 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
     ctx->bulk_offs.assign(size_t(K) * 10, 0);
     for (int32_t k = 0; k < K; ++k) {
         int64_t L[10];
-        item_lengths(ctx, k, mask, L);
+        gale::item_lengths(ctx, k, mask, L);
         for (int a = 0; a < 10; ++a) {
             ctx->bulk_offs[size_t(k) * 10 + a] = run[a];
             run[a] += L[a];

@@ -117,6 +117,8 @@ namespace gale {
 // into page-locked memory; into pageable memory through the staging buffers,
 // moved into place by the host threads (gale_api.cpp).
 gale_status copy_to_host(gale_ctx *ctx, void *dst, const void *src, size_t bytes);
+// Lengths of the ten output arrays of cluster k under mask (gale_api.cpp).
+void item_lengths(const gale_ctx *ctx, int32_t k, uint32_t mask, int64_t *L);
 void enumeration_destroy(gale_ctx *ctx);  // gale_enum.cpp
 void cobound_destroy(gale_ctx *ctx);      // gale_cobound.cu
 }  // namespace gale

@@ -41,8 +41,7 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc;
 
 NoAllocScratch *g_addr[kMaxDevices] = {};  // device address of g_noalloc, per device
-std::mutex g_setup_mu;
-int32_t g_order_host[kNoAllocMaxClusters];  // host staging of the per-bin order
+std::mutex g_setup_mu;                      // guards the one-time address lookup
 
 gale_status fail(gale_status s, const std::string &msg) {
     gale::set_error(msg);
@@ -52,8 +51,8 @@ gale_status fail(gale_status s, const std::string &msg) {
 }  // namespace
 
 extern "C" gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t *ids, int32_t n, uint32_t mask,
-                                                   const gale_arrays *dev_out) {
-    if (!ctx || !ids || !dev_out) return fail(GALE_EINVAL, "NULL argument");
+                                                   const gale_arrays *dev_out, const int64_t *lengths) {
+    if (!ctx || !ids || !dev_out || !lengths) return fail(GALE_EINVAL, "NULL argument");
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(GALE_EINVAL, "not a device context");
     if (mask == 0 || (mask & ~ctx->precond))
         return fail(GALE_EINVAL, "mask must be a non-empty subset of the precondition mask");
@@ -74,6 +73,23 @@ extern "C" gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t 
     const uint32_t rel_of[10] = {GALE_VT, GALE_VT, GALE_VV, GALE_VV, GALE_ET, GALE_ET, GALE_ET, GALE_ET, GALE_TT, GALE_TT};
     for (int a = 0; a < 10; ++a)
         if ((mask & rel_of[a]) && !out[a]) return fail(GALE_EINVAL, "NULL device array for a requested relation");
+    // every requested array must hold the list's output: the kernels place
+    // each cluster at its offset in the caller's arrays without bounds
+    {
+        static const char *names[10] = {"vt_off", "vt_val", "vv_off", "vv_val", "et_uoff",
+                                        "et_w",   "et_off", "et_val", "tt_off", "tt_val"};
+        int64_t need[10] = {};
+        for (int32_t i = 0; i < n; ++i) {
+            int64_t L[10];
+            gale::item_lengths(ctx, ids[i], mask, L);
+            for (int a = 0; a < 10; ++a) need[a] += L[a];
+        }
+        for (int a = 0; a < 10; ++a)
+            if ((mask & rel_of[a]) && lengths[a] < need[a])
+                return fail(GALE_EINVAL, std::string("device array ") + names[a] + " holds " +
+                                             std::to_string(lengths[a]) + " elements, the list needs " +
+                                             std::to_string(need[a]));
+    }
 
     std::lock_guard<std::mutex> lock(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -91,16 +107,16 @@ extern "C" gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t 
         }
         S = g_addr[ctx->device];
     }
-    // work order: items grouped by size bin (the host staging buffer is
-    // shared by all contexts; the copy below has consumed it on return)
-    std::lock_guard<std::mutex> order_lock(g_setup_mu);
+    // work order: items grouped by size bin (staged on this call's stack;
+    // the copy below has consumed it before the call returns)
+    int32_t order[kNoAllocMaxClusters];
     int32_t cnt[kNoAllocMaxBins + 1] = {};
     const int32_t nb = int32_t(ctx->bins.size());
     for (int32_t i = 0; i < n; ++i) cnt[ctx->bin_of[ids[i]] + 1]++;
     for (int32_t b = 0; b < nb; ++b) cnt[b + 1] += cnt[b];
     int32_t cur[kNoAllocMaxBins];
     for (int32_t b = 0; b < nb; ++b) cur[b] = cnt[b];
-    for (int32_t i = 0; i < n; ++i) g_order_host[cur[ctx->bin_of[ids[i]]]++] = i;
+    for (int32_t i = 0; i < n; ++i) order[cur[ctx->bin_of[ids[i]]]++] = i;
 
     gale::WorkItem base;
     memset(&base, 0, sizeof(base));
@@ -120,7 +136,7 @@ extern "C" gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t 
     // start at zero (ticket counters are reset by each launch)
     if ((e = cudaMemsetAsync(&S->err, 0, sizeof(int32_t), s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(S->ids, ids, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(S->order, g_order_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) !=
+        (e = cudaMemcpyAsync(S->order, order, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||
         (e = cudaMemcpyAsync(&S->base, &base, sizeof(base), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(GALE_ECUDA, std::string("staging the work list: ") + cudaGetErrorString(e));
