@@ -47,7 +47,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC], check=True)
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lpthread"], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -73,6 +73,8 @@ def _load():
         lib.oracle_relations.argtypes = [i64, i64, P, ctypes.POINTER(_Rel)]
         lib.oracle_cluster_relations.argtypes = [i64, i64, P, P, P, i32, ctypes.POINTER(_Rel)]
         lib.oracle_working_set.argtypes = [i64, i64, P, P, P, i32, P, ctypes.POINTER(i64), P, ctypes.POINTER(i64)]
+        lib.oracle_localized_build.argtypes = [i64, i64, P, P, P, i32, i32, P, P, P]
+        lib.oracle_localized_cluster.argtypes = [i64, i64, P, P, P, i32, i32, ctypes.POINTER(_Rel)]
         lib.oracle_rel_free.argtypes = [ctypes.POINTER(_Rel)]
         lib.oracle_rel_free.restype = None
         _lib = lib
@@ -163,6 +165,59 @@ def cluster_relations(canon: dict, k: int) -> dict:
         return _unpack(r, int(I_V[k + 1] - I_V[k]), int(I_T[k + 1] - I_T[k]))
     finally:
         lib.oracle_rel_free(ctypes.byref(r))
+
+
+def localized_build(canon: dict, nthreads: int = 1, digests: bool = True):
+    """Per-cluster localized producer: every cluster's working set (T_k and
+    its face halo) gathered once, then VT, VV, ET and TT of each cluster
+    built from its working set alone, nthreads threads over the clusters.
+    Returns (sizes int64[K, 5] as cluster_sizes gives them, digests uint64[K]
+    as relation_digest gives them (or None), (init seconds, build seconds))."""
+    lib = _load()
+    rows = np.ascontiguousarray(canon["rows"])
+    K = int(canon["K"])
+    sizes = np.zeros((K, 5), np.int64)
+    dig = np.zeros(K, np.uint64) if digests else None
+    sec = np.zeros(2, np.float64)
+    rc = lib.oracle_localized_build(canon["nv"], canon["nt"], _p(rows), _p(canon["I_V"]), _p(canon["I_T"]), K,
+                                    int(nthreads), _p(sizes), _p(dig) if digests else None, _p(sec))
+    if rc != OK:
+        raise RuntimeError(f"oracle_localized_build: status {rc}")
+    return sizes, dig, (float(sec[0]), float(sec[1]))
+
+
+def localized_cluster(canon: dict, k: int) -> dict:
+    """Cluster k's relations by the localized producer (offsets start at 0),
+    in the layout of cluster_relations."""
+    lib = _load()
+    r = _Rel()
+    rows = np.ascontiguousarray(canon["rows"])
+    I_V, I_T = canon["I_V"], canon["I_T"]
+    if lib.oracle_localized_cluster(canon["nv"], canon["nt"], _p(rows), _p(I_V), _p(I_T), int(canon["K"]), k,
+                                    ctypes.byref(r)) != OK:
+        raise RuntimeError("oracle_localized_cluster")
+    try:
+        return _unpack(r, int(I_V[k + 1] - I_V[k]), int(I_T[k + 1] - I_T[k]))
+    finally:
+        lib.oracle_rel_free(ctypes.byref(r))
+
+
+_DIGEST_P = (1000003, 1000033, 1000037, 1000039, 1000081, 1000099, 1000117, 1000121, 1000133, 1000151)
+_DIGEST_KEYS = ("vt_off", "vt_val", "vv_off", "vv_val", "eu_off", "e_w", "et_off", "et_val", "tt_off", "tt_val")
+
+
+def relation_digest(v: dict) -> int:
+    """Order-sensitive digest of one cluster's ten arrays (the definition the
+    localized producer uses): for array a of length n, P_a (n + 1) plus the
+    sum over i of (x_i + 7)(i + 1) P_a, modulo 2^64."""
+    d = 0
+    for key, p in zip(_DIGEST_KEYS, _DIGEST_P):
+        x = np.asarray(v[key]).astype(np.int64).astype(np.uint64)
+        n = x.size
+        i = np.arange(1, n + 1, dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            d += int((((x + np.uint64(7)) * i) * np.uint64(p)).sum(dtype=np.uint64)) + p * (n + 1)
+    return d % (1 << 64)
 
 
 def working_set(canon: dict, k: int):

@@ -459,3 +459,279 @@ int oracle_working_set(int64_t nv, int64_t nt, const int32_t *rows, const int64_
     *n_ext = ne; *n_halo = nh;
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Per-cluster localized producer                                      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The producer's shape on the CPU (Sections 4.3-4.4): an initialisation
+ * gathers every cluster's working set once - the tets with a vertex in it
+ * (T_k = internal tets + T_ex, Section 4.3) and the face halo that TT needs
+ * (tets outside T_k sharing a triangle with an internal tet) - and then each
+ * cluster's VT, VV, ET and TT are built from its working set alone, by the
+ * same plain definitions as above applied to the working set with its
+ * vertices renumbered compactly (an order-preserving map, so every row keeps
+ * its ascending order).  Clusters are independent, so nthreads POSIX threads
+ * take them from a shared counter.
+ */
+#include <pthread.h>
+#include <time.h>
+
+typedef struct {
+    int64_t nv, nt;
+    const int32_t *rows;
+    const int64_t *I_V, *I_T;
+    int32_t K;
+    int64_t *ws_off;   /* [K+1] working set of cluster k: ws_val[ws_off[k], ws_off[k+1]) ascending */
+    int32_t *ws_val;
+} loc_mesh;
+
+static double now_s(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* order-sensitive digest of the ten arrays of one cluster's relations */
+static const uint64_t kDigestP[10] = {1000003ull, 1000033ull, 1000037ull, 1000039ull, 1000081ull,
+                                      1000099ull, 1000117ull, 1000121ull, 1000133ull, 1000151ull};
+static uint64_t digest64(const int64_t *a, int64_t n, int which) {
+    uint64_t d = kDigestP[which] * (uint64_t)(n + 1);
+    for (int64_t i = 0; i < n; ++i) d += ((uint64_t)a[i] + 7ull) * (uint64_t)(i + 1) * kDigestP[which];
+    return d;
+}
+static uint64_t digest32(const int32_t *a, int64_t n, int which) {
+    uint64_t d = kDigestP[which] * (uint64_t)(n + 1);
+    for (int64_t i = 0; i < n; ++i) d += ((uint64_t)(int64_t)a[i] + 7ull) * (uint64_t)(i + 1) * kDigestP[which];
+    return d;
+}
+
+/* Working sets of all clusters (the initialisation).  T_k from one pass over
+ * the tets; the halo from the global vertex stars: the tet across the face
+ * (b, c, d) of an internal tet whose b is not in the cluster is the other
+ * tet of star(b) holding c and d. */
+static int loc_working_sets(loc_mesh *m) {
+    const int64_t nv = m->nv, nt = m->nt;
+    const int32_t *rows = m->rows;
+    const int32_t K = m->K;
+    int32_t *vc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv ? nv : 1));
+    int64_t *cnt = (int64_t *)calloc((size_t)K + 1, sizeof(int64_t));
+    int64_t *soff = NULL; int32_t *sval = NULL;
+    int64_t *hoff = NULL; int32_t *hval = NULL;
+    if (!vc || !cnt) { free(vc); free(cnt); return OR_ENOMEM; }
+    for (int32_t k = 0; k < K; ++k)
+        for (int64_t v = m->I_V[k]; v < m->I_V[k + 1]; ++v) vc[v] = k;
+    /* global vertex stars */
+    int32_t *all = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nt ? nt : 1));
+    if (!all) { free(vc); free(cnt); return OR_ENOMEM; }
+    for (int64_t t = 0; t < nt; ++t) all[t] = (int32_t)t;
+    int rc = vt_rows(rows, all, nt, 0, nv, &soff, &sval);
+    free(all);
+    if (rc != OR_OK) { free(vc); free(cnt); return rc; }
+    /* halo lists: count, then fill (duplicates removed per cluster later) */
+    hoff = (int64_t *)calloc((size_t)K + 1, sizeof(int64_t));
+    if (!hoff) { free(vc); free(cnt); free(soff); free(sval); return OR_ENOMEM; }
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t *fillp = NULL;
+        if (pass == 1) {
+            for (int32_t k = 0; k < K; ++k) hoff[k + 1] += hoff[k];
+            hval = (int32_t *)malloc(sizeof(int32_t) * (size_t)(hoff[K] ? hoff[K] : 1));
+            fillp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K ? K : 1));
+            if (!hval || !fillp) { free(fillp); free(vc); free(cnt); free(soff); free(sval); free(hoff); free(hval); return OR_ENOMEM; }
+            for (int32_t k = 0; k < K; ++k) fillp[k] = hoff[k];
+        }
+        for (int32_t k = 0; k < K; ++k)
+            for (int64_t t = m->I_T[k]; t < m->I_T[k + 1]; ++t) {
+                const int32_t *r = rows + 4 * t;
+                if (vc[r[1]] == k) continue; /* face (b, c, d) has an own vertex: inside T_k */
+                const int32_t b = r[1];
+                for (int64_t q = soff[b]; q < soff[b + 1]; ++q) {
+                    const int32_t u = sval[q];
+                    if (u == (int32_t)t) continue;
+                    const int32_t *ru = rows + 4 * (int64_t)u;
+                    int hc = 0, hd = 0, in_k = 0;
+                    for (int j = 0; j < 4; ++j) {
+                        hc |= ru[j] == r[2];
+                        hd |= ru[j] == r[3];
+                        in_k |= vc[ru[j]] == k;
+                    }
+                    if (hc && hd && !in_k) {
+                        if (pass == 0) hoff[k + 1]++;
+                        else hval[fillp[k]++] = u;
+                    }
+                }
+            }
+        free(fillp);
+    }
+    free(soff); free(sval);
+    /* T_k: each tet, once for each distinct cluster among its vertices */
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t *fillp = NULL;
+        if (pass == 1) {
+            m->ws_off = (int64_t *)calloc((size_t)K + 1, sizeof(int64_t));
+            if (!m->ws_off) { free(vc); free(cnt); free(hoff); free(hval); return OR_ENOMEM; }
+            for (int32_t k = 0; k < K; ++k) m->ws_off[k + 1] = m->ws_off[k] + cnt[k] + (hoff[k + 1] - hoff[k]);
+            m->ws_val = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m->ws_off[K] ? m->ws_off[K] : 1));
+            fillp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K ? K : 1));
+            if (!m->ws_val || !fillp) { free(fillp); free(vc); free(cnt); free(hoff); free(hval); return OR_ENOMEM; }
+            for (int32_t k = 0; k < K; ++k) fillp[k] = m->ws_off[k];
+        }
+        for (int64_t t = 0; t < nt; ++t) {
+            int32_t seen[4];
+            int ns = 0;
+            for (int j = 0; j < 4; ++j) {
+                const int32_t c = vc[rows[4 * t + j]];
+                int dup = 0;
+                for (int i = 0; i < ns; ++i) dup |= seen[i] == c;
+                if (dup) continue;
+                seen[ns++] = c;
+                if (pass == 0) cnt[c]++;
+                else m->ws_val[fillp[c]++] = (int32_t)t;
+            }
+        }
+        if (pass == 1) {
+            /* halo after T_k, then the whole working set ascending and unique */
+            for (int32_t k = 0; k < K; ++k) {
+                for (int64_t q = hoff[k]; q < hoff[k + 1]; ++q) m->ws_val[fillp[k]++] = hval[q];
+                const int64_t n = fillp[k] - m->ws_off[k];
+                const int64_t u = sort_unique(m->ws_val + m->ws_off[k], n);
+                for (int64_t q = m->ws_off[k] + u; q < fillp[k]; ++q) m->ws_val[q] = INT32_MAX;
+            }
+        }
+        free(fillp);
+    }
+    free(vc); free(cnt); free(hoff); free(hval);
+    return OR_OK;
+}
+
+static int cmp_i32p(const void *a, const void *b) { return cmp_i32(a, b); }
+
+/* The four relations of cluster k from its working set alone; offsets start
+ * at 0 for the cluster (the layout of oracle_cluster_relations). */
+static int loc_cluster(const loc_mesh *m, int32_t k, oracle_rel *out) {
+    memset(out, 0, sizeof(*out));
+    const int32_t *ws = m->ws_val + m->ws_off[k];
+    int64_t nws = m->ws_off[k + 1] - m->ws_off[k];
+    while (nws > 0 && ws[nws - 1] == INT32_MAX) --nws;
+    const int64_t v0 = m->I_V[k], v1 = m->I_V[k + 1];
+    const int64_t t0 = m->I_T[k], t1 = m->I_T[k + 1];
+    out->nv = v1 - v0; out->nt = t1 - t0;
+    /* compact vertex numbering of the working set (order preserving) */
+    int32_t *vmap = (int32_t *)malloc(sizeof(int32_t) * (size_t)(4 * nws + 1));
+    int32_t *lrows = (int32_t *)malloc(sizeof(int32_t) * (size_t)(4 * nws + 1));
+    int32_t *lt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nws + 1));
+    int32_t *own = (int32_t *)malloc(sizeof(int32_t) * (size_t)(out->nt + 1));
+    if (!vmap || !lrows || !lt || !own) { free(vmap); free(lrows); free(lt); free(own); return OR_ENOMEM; }
+    for (int64_t i = 0; i < nws; ++i)
+        for (int j = 0; j < 4; ++j) vmap[4 * i + j] = m->rows[4 * (int64_t)ws[i] + j];
+    const int64_t nloc = sort_unique(vmap, 4 * nws);
+    for (int64_t i = 0; i < 4 * nws; ++i) {
+        const int32_t g = m->rows[4 * (int64_t)ws[i / 4] + (i % 4)];
+        const int32_t *p = (const int32_t *)bsearch(&g, vmap, (size_t)nloc, sizeof(int32_t), cmp_i32p);
+        lrows[i] = (int32_t)(p - vmap);
+    }
+    int64_t n_own = 0;
+    for (int64_t i = 0; i < nws; ++i) {
+        lt[i] = (int32_t)i;
+        if (ws[i] >= t0 && ws[i] < t1) own[n_own++] = (int32_t)i;
+    }
+    int32_t lo = 0;
+    while (lo < nloc && vmap[lo] < v0) ++lo;
+    const int64_t nvo = v1 - v0;
+    int rc = OR_OK;
+    if (n_own != out->nt || (nvo > 0 && (lo + nvo > nloc || vmap[lo] != v0))) rc = OR_EINVAL;
+    int64_t *soff = NULL; int32_t *sval = NULL;
+    if (rc == OR_OK) rc = vt_rows(lrows, lt, nws, lo, lo + nvo, &out->vt_off, &out->vt_val);
+    if (rc == OR_OK) rc = vv_from_vt(lrows, lo, nvo, out->vt_off, out->vt_val, &out->vv_off, &out->vv_val);
+    if (rc == OR_OK)
+        rc = et_from_vt(lrows, lo, nvo, out->vt_off, out->vt_val, &out->eu_off, &out->e_w, &out->et_off,
+                        &out->et_val, &out->ne);
+    /* TT of the internal tets: stars of every working-set vertex */
+    if (rc == OR_OK) rc = vt_rows(lrows, lt, nws, 0, nloc, &soff, &sval);
+    if (rc == OR_OK) rc = tt_rows(lrows, own, n_own, 0, soff, sval, &out->tt_off, &out->tt_val);
+    free(soff); free(sval);
+    if (rc == OR_OK) {
+        /* back to canonical ids */
+        for (int64_t q = 0; q < out->vt_off[nvo]; ++q) out->vt_val[q] = ws[out->vt_val[q]];
+        for (int64_t q = 0; q < out->vv_off[nvo]; ++q) out->vv_val[q] = vmap[out->vv_val[q]];
+        for (int64_t q = 0; q < out->ne; ++q) out->e_w[q] = vmap[out->e_w[q]];
+        for (int64_t q = 0; q < out->et_off[out->ne]; ++q) out->et_val[q] = ws[out->et_val[q]];
+        for (int64_t q = 0; q < out->tt_off[n_own]; ++q) out->tt_val[q] = ws[out->tt_val[q]];
+    }
+    free(vmap); free(lrows); free(lt); free(own);
+    if (rc != OR_OK) oracle_rel_free(out);
+    return rc;
+}
+
+typedef struct {
+    const loc_mesh *m;
+    int64_t *next;   /* shared cluster counter */
+    int64_t *sizes;  /* [K][5] */
+    uint64_t *digests;
+    int err;
+} loc_job;
+
+static void *loc_worker(void *arg) {
+    loc_job *j = (loc_job *)arg;
+    for (;;) {
+        const int64_t k = __atomic_fetch_add(j->next, 1, __ATOMIC_RELAXED);
+        if (k >= j->m->K) break;
+        oracle_rel r;
+        if (loc_cluster(j->m, (int32_t)k, &r) != OR_OK) { j->err = 1; continue; }
+        const int64_t nvo = r.nv, nown = r.nt;
+        int64_t *s = j->sizes + 5 * k;
+        s[0] = r.vt_off[nvo]; s[1] = r.vv_off[nvo]; s[2] = r.ne; s[3] = r.et_off[r.ne]; s[4] = r.tt_off[nown];
+        if (j->digests)
+            j->digests[k] = digest64(r.vt_off, nvo + 1, 0) + digest32(r.vt_val, s[0], 1) + digest64(r.vv_off, nvo + 1, 2) +
+                            digest32(r.vv_val, s[1], 3) + digest64(r.eu_off, nvo + 1, 4) + digest32(r.e_w, s[2], 5) +
+                            digest64(r.et_off, s[2] + 1, 6) + digest32(r.et_val, s[3], 7) +
+                            digest64(r.tt_off, nown + 1, 8) + digest32(r.tt_val, s[4], 9);
+        oracle_rel_free(&r);
+    }
+    return NULL;
+}
+
+/*
+ * Build every cluster from its working set with nthreads threads.
+ *   sizes    int64[K*5] out: per cluster |VT|, |VV|, #edges, |ET|, |TT|
+ *   digests  uint64[K] out (may be NULL): digest of the cluster's ten arrays
+ *   seconds  double[2] out: initialisation, then the per-cluster builds
+ */
+int oracle_localized_build(int64_t nv, int64_t nt, const int32_t *rows, const int64_t *I_V, const int64_t *I_T,
+                           int32_t K, int32_t nthreads, int64_t *sizes, uint64_t *digests, double *seconds) {
+    loc_mesh m = {nv, nt, rows, I_V, I_T, K, NULL, NULL};
+    double t0 = now_s();
+    int rc = loc_working_sets(&m);
+    double t1 = now_s();
+    if (rc != OR_OK) return rc;
+    if (nthreads < 1) nthreads = 1;
+    int64_t next = 0;
+    loc_job *jobs = (loc_job *)calloc((size_t)nthreads, sizeof(loc_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); free(m.ws_off); free(m.ws_val); return OR_ENOMEM; }
+    int started = 0;
+    for (int i = 0; i < nthreads; ++i) {
+        jobs[i] = (loc_job){&m, &next, sizes, digests, 0};
+        if (i == 0 || pthread_create(&th[i], NULL, loc_worker, &jobs[i]) == 0) started = i + 1;
+        else break;
+    }
+    loc_worker(&jobs[0]);  /* the caller's thread is worker 0 */
+    for (int i = 1; i < started; ++i) pthread_join(th[i], NULL);
+    double t2 = now_s();
+    for (int i = 0; i < started; ++i) rc |= jobs[i].err ? OR_EINVAL : OR_OK;
+    free(jobs); free(th); free(m.ws_off); free(m.ws_val);
+    if (seconds) { seconds[0] = t1 - t0; seconds[1] = t2 - t1; }
+    return rc == OR_OK ? OR_OK : OR_EINVAL;
+}
+
+/* One cluster of the localized producer, with its working sets gathered
+ * first (for tests: the same code path as oracle_localized_build). */
+int oracle_localized_cluster(int64_t nv, int64_t nt, const int32_t *rows, const int64_t *I_V, const int64_t *I_T,
+                             int32_t K, int32_t k, oracle_rel *out) {
+    loc_mesh m = {nv, nt, rows, I_V, I_T, K, NULL, NULL};
+    int rc = loc_working_sets(&m);
+    if (rc == OR_OK) rc = loc_cluster(&m, k, out);
+    free(m.ws_off); free(m.ws_val);
+    return rc;
+}
