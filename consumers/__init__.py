@@ -47,7 +47,7 @@ def _load():
                                       ctypes.c_uint64, ctypes.c_double)
         lib.gale_cp_classify.argtypes = [P, P, P, i32, i32, P, P, P, P, P]
         lib.gale_cp_classify.restype = ctypes.c_int
-        lib.gale_cp_serve_run.argtypes = [P, P, P, P, P, i32, i32, u32, u64, f64, P, P, P]
+        lib.gale_cp_serve_run.argtypes = [P, P, P, P, P, i32, i32, u32, u64, f64, i32, P, P, P]
         lib.gale_cp_serve_run.restype = ctypes.c_int
         lib.gale_open_loop.argtypes = [P, i32, P, P, P, i64, f64, u64, i32, P, P]
         lib.gale_open_loop.restype = ctypes.c_int
@@ -84,10 +84,13 @@ def classify_cluster(f_c, inid_c, rows, v0, vt_off, vt_val, vv_off, vv_val) -> n
     return out[:nvo]
 
 
-def serve_run(ctx, f_c, inid_c, rows, I_V, nthreads=16, mask=15, seed=6, jump_prob=0.1, max_clusters=None):
+def serve_run(ctx, f_c, inid_c, rows, I_V, nthreads=16, mask=15, seed=6, jump_prob=0.1, max_clusters=None,
+              null_work=False):
     """Run the serving driver over clusters [0, max_clusters) (all by
     default); returns (codes int8[nv], latencies float64[K],
-    dict(wall, requests, d2h_bytes, failures, copy_s, integrate_s))."""
+    dict(wall, requests, d2h_bytes, failures, copy_s, integrate_s)).
+    null_work: each view is released as soon as it is served (no copy, no
+    classification; the codes stay -9), to measure the producer alone."""
     lib = _load()
     K = len(I_V) - 1
     if max_clusters is not None:
@@ -98,7 +101,7 @@ def serve_run(ctx, f_c, inid_c, rows, I_V, nthreads=16, mask=15, seed=6, jump_pr
     I_V = np.ascontiguousarray(I_V, dtype=np.int64)
     rows = np.ascontiguousarray(rows, dtype=np.int32)
     lib.gale_cp_serve_run(ctx._h, _p(f_c), _p(inid_c), _p(rows), _p(I_V), K, nthreads, mask, seed, jump_prob,
-                          _p(cls), _p(lat), _p(st))
+                          1 if null_work else 0, _p(cls), _p(lat), _p(st))
     return cls, lat, {"wall": st[0], "requests": int(st[1]), "d2h_bytes": int(st[2]), "failures": int(st[3]),
                       "copy_s": float(st[4]), "integrate_s": float(st[5])}
 

@@ -128,7 +128,9 @@ int gale_cp_classify(const float *f, const int32_t *inid, const int32_t *rows, i
  * spatially coherent) and with probability jump_prob jumps to a random
  * cluster; a cluster is claimed through an atomic bitmap so each is
  * classified once.  Per cluster: gale_request(mask | VT | VV), copy the VT
- * and VV rows to pinned host memory, classify, gale_release.
+ * and VV rows to pinned host memory, classify, gale_release.  With null_work
+ * set, each view is released as soon as it is served (no copy, no
+ * classification): the producer measured without the consumers' own work.
  *   f, inid, rows, I_V   host arrays in canonical order
  *   cls                  int8[nv] out (canonical order)
  *   lat                  double[K] out: seconds from request to view
@@ -137,8 +139,8 @@ int gale_cp_classify(const float *f, const int32_t *inid, const int32_t *rows, i
  *                        and of the classification (the paper's "data integration")
  */
 int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const int32_t *rows, const int64_t *I_V,
-                      int32_t K, int32_t nthreads, uint32_t mask, uint64_t seed, double jump_prob, int8_t *cls,
-                      double *lat, double *stats) {
+                      int32_t K, int32_t nthreads, uint32_t mask, uint64_t seed, double jump_prob, int32_t null_work,
+                      int8_t *cls, double *lat, double *stats) {
     // K may be below the context's cluster count: only clusters [0, K) are served
     std::vector<std::atomic<uint8_t>> claimed(static_cast<size_t>(K));
     for (auto &c : claimed) c.store(0);
@@ -187,6 +189,11 @@ int gale_cp_serve_run(gale_ctx *ctx, const float *f, const int32_t *inid, const 
             const auto r1 = std::chrono::steady_clock::now();
             lat[k] = std::chrono::duration<double>(r1 - r0).count();
             const int32_t nvo = v.v_end - v.v_begin;
+            if (null_work) {  // the producer alone: the view is taken and handed back
+                gale_release(ctx, &v);
+                done++;
+                continue;
+            }
             // offsets first, then values
             const size_t need = size_t(2 * (nvo + 1));
             if (pin_cap < need) {

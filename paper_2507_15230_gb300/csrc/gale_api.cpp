@@ -5,6 +5,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -185,6 +186,50 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         members.push_back(k);
     }
     close();
+    // The bins of the one-CTA-per-SM tier hold the largest clusters: merged
+    // caps (each field's maximum over the members) soon exceed a CTA's shared
+    // memory, which leaves many bins of a few clusters each, launched one
+    // after another.  They become one bin per block size whose members each
+    // keep their own plan (one persistent launch, the largest member's
+    // shared memory).
+    ctx->h_plans.assign(size_t(K), gale::SmemPlan{});
+    {
+        std::vector<gale::Bin> kept;
+        std::map<int, gale::Bin> top;  // block size -> merged bin
+        for (auto &b : ctx->bins) {
+            if (b.spill || b.plan.total <= tiers[2]) {
+                kept.push_back(std::move(b));
+                continue;
+            }
+            gale::Bin &t = top[b.plan.threads];
+            const bool first = t.clusters.empty();
+            for (int32_t k : b.clusters) {
+                ctx->h_plans[k] = gale::plan_smem(caps_k(k), b.plan.threads);
+                if (first && t.clusters.empty()) t.plan = ctx->h_plans[k];
+                else t.plan.caps = merge(t.plan.caps, ctx->h_plans[k].caps);
+                t.plan.total = std::max(t.plan.total, ctx->h_plans[k].total);
+                t.clusters.push_back(k);
+            }
+            t.per_item = true;
+        }
+        for (auto &kv : top) {
+            gale::Bin &t = kv.second;
+            std::stable_sort(t.clusters.begin(), t.clusters.end(),
+                             [&](int32_t a, int32_t c) { return need[a] > need[c]; });  // largest first
+            kept.push_back(std::move(t));
+        }
+        ctx->bins = std::move(kept);
+        for (size_t b = 0; b < ctx->bins.size(); ++b)
+            for (int32_t k : ctx->bins[b].clusters) ctx->bin_of[k] = int32_t(b);
+    }
+    if (!ctx->d_plans) {
+        ctx->d_plans = static_cast<gale::SmemPlan *>(ctx->dalloc(sizeof(gale::SmemPlan) * size_t(std::max(K, 1))));
+        if (!ctx->d_plans) return fail(GALE_ENOMEM, "device allocation of the per-cluster plans failed");
+    }
+    if (K > 0 &&
+        cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * size_t(K), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return fail(GALE_ECUDA, "uploading the per-cluster plans failed");
     int max_total = 0;
     for (auto &b : ctx->bins)
         if (!b.spill) max_total = std::max(max_total, b.plan.total);
@@ -192,8 +237,8 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         return fail(GALE_ECUDA, "setting the kernels' shared memory limit failed");
     int64_t spill_need = 0;
     for (auto &b : ctx->bins) {
-        int per_sm = gale::max_ctas_per_sm(b.plan, b.spill);
-        if (per_sm < 1 && !b.spill) {
+        int per_sm = gale::max_ctas_per_sm(b.plan, b.spill, b.per_item);
+        if (per_sm < 1 && !b.spill && !b.per_item) {
             b.spill = true;  // cannot launch with this much shared memory: run in global scratch
             per_sm = gale::max_ctas_per_sm(b.plan, true);
         }
@@ -214,6 +259,11 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
 }
 
 char *scratch_of(gale_ctx *ctx, const gale::Bin &b) { return b.spill ? ctx->d_spill : nullptr; }
+// build capacities of cluster k (its exact sizes known)
+gale::Caps bin_caps(const gale_ctx *ctx, int32_t k) {
+    return caps_of(ctx->hm.stats[k], ctx->sizes.data() + size_t(5) * k);
+}
+const gale::SmemPlan *plans_of(gale_ctx *ctx, const gale::Bin &b) { return b.per_item ? ctx->d_plans : nullptr; }
 
 }  // namespace
 
@@ -226,7 +276,7 @@ SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop) {
     const size_t nb = ctx->bins.size();
     std::vector<size_t> order;
     for (size_t b = 0; b < nb; ++b)
-        if (!ctx->bins[b].spill) order.push_back(b);
+        if (!ctx->bins[b].spill && !ctx->bins[b].per_item) order.push_back(b);
     std::stable_sort(order.begin(), order.end(),
                      [&](size_t a, size_t b) { return ctx->bins[a].plan.total < ctx->bins[b].plan.total; });
     std::vector<uint8_t> sel(nb, 0);
@@ -310,7 +360,7 @@ gale_status count_pass(gale_ctx *ctx) {
         int rc = gale::launch_count_pass(dev_mesh(ctx), bin.plan, ctx->d_order_all + ctx->order_all_off[b],
                                          int32_t(bin.clusters.size()), ctx->d_sizes, ctx->d_err,
                                          ctx->d_tickets + b, bin.grid, ctx->stream, scratch_of(ctx, bin),
-                                         ctx->precond);
+                                         ctx->precond, plans_of(ctx, bin));
         if (rc != 0) return cuda_fail(cudaError_t(rc), "count pass launch");
     }
     gale_status st = check_device_error(ctx);
@@ -715,7 +765,7 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
                 const gale::Bin &bin = ctx->bins[b];
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b],
                                         int32_t(bin.clusters.size()), ctx->d_err, ctx->d_tickets + b, bin.grid,
-                                        ctx->stream, scratch_of(ctx, bin));
+                                        ctx->stream, scratch_of(ctx, bin), plans_of(ctx, bin));
             }
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
             if (rc != 0) return cuda_fail(cudaError_t(rc), "capturing the batched build");
@@ -742,8 +792,8 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
         if (mode == GALE_MODE_PER_CLUSTER) {
             for (int32_t i = 0; i < cnt; ++i) {
                 const gale::Bin &bin = ctx->bins[ctx->bin_of[list[i]]];
-                rc = gale::launch_build_one(dm, bin.plan, ctx->d_items, i, ctx->d_err, ctx->stream,
-                                            scratch_of(ctx, bin));
+                rc = gale::launch_build_one(dm, bin.per_item ? ctx->h_plans[list[i]] : bin.plan, ctx->d_items, i,
+                                            ctx->d_err, ctx->stream, scratch_of(ctx, bin));
                 if (rc != 0) return cuda_fail(cudaError_t(rc), "per-cluster launch");
             }
             launches += cnt;
@@ -762,7 +812,7 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
                 const gale::Bin &bin = ctx->bins[b];
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_part + off[b], nb, ctx->d_err,
                                         ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream,
-                                        scratch_of(ctx, bin));
+                                        scratch_of(ctx, bin), plans_of(ctx, bin));
                 if (rc != 0) return cuda_fail(cudaError_t(rc), "batched launch");
                 ++launches;
             }
@@ -948,7 +998,7 @@ gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint
                 const gale::Bin &bin = ctx->bins[b];
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items + i0, ctx->d_order_part + boff[c][b], nb,
                                         ctx->d_err, ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream,
-                                        scratch_of(ctx, bin));
+                                        scratch_of(ctx, bin), plans_of(ctx, bin));
                 if (rc != 0) return cuda_fail(cudaError_t(rc), "batched launch");
                 ++launches;
             }
@@ -1109,10 +1159,25 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
         float best = -1.f;
         gale::SmemPlan best_plan = bin.plan;
         int best_grid = bin.grid, best_per = bin.ctas_per_sm;
+        std::vector<gale::SmemPlan> best_members;
         for (int T : cand_threads) {
-            const gale::SmemPlan plan = gale::plan_smem(bin.plan.caps, T);
+            gale::SmemPlan plan = gale::plan_smem(bin.plan.caps, T);
+            if (bin.per_item) {
+                // the members' own plans at this block size; the envelope
+                // takes the largest shared memory
+                int top = 0;
+                for (int32_t k : bin.clusters) {
+                    ctx->h_plans[k] = gale::plan_smem(bin_caps(ctx, k), T);
+                    top = std::max(top, ctx->h_plans[k].total);
+                }
+                plan.threads = T;
+                plan.total = top;
+                CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+                CUDA_TRY(cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * size_t(K),
+                                    cudaMemcpyHostToDevice));
+            }
             if (!bin.spill && plan.total > smem_limit) continue;
-            int max_per = gale::max_ctas_per_sm(plan, bin.spill);
+            int max_per = gale::max_ctas_per_sm(plan, bin.spill, bin.per_item);
             if (bin.spill) max_per = std::min(max_per, 2);
             for (int per = 1; per <= max_per; ++per) {
                 const int grid = std::max(1, std::min<int>(nb, per * ctx->sm_count));
@@ -1134,7 +1199,8 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
                 }
                 auto launch = [&]() {
                     return gale::launch_build(dm, plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b], nb,
-                                              ctx->d_err, ctx->d_tickets + b, grid, ctx->stream, scratch);
+                                              ctx->d_err, ctx->d_tickets + b, grid, ctx->stream, scratch,
+                                              plans_of(ctx, bin));
                 };
                 rc = launch();
                 CUDA_TRY(cudaEventRecord(e0, ctx->stream));
@@ -1154,6 +1220,10 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
                     best_plan = plan;
                     best_grid = grid;
                     best_per = per;
+                    if (bin.per_item) {
+                        best_members.clear();
+                        for (int32_t k : bin.clusters) best_members.push_back(ctx->h_plans[k]);
+                    }
                 }
             }
         }
@@ -1161,6 +1231,12 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
             bin.plan = best_plan;
             bin.grid = best_grid;
             bin.ctas_per_sm = best_per;
+        }
+        if (bin.per_item && !best_members.empty()) {
+            for (size_t i = 0; i < bin.clusters.size(); ++i) ctx->h_plans[bin.clusters[i]] = best_members[i];
+            CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            CUDA_TRY(cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * size_t(K),
+                                cudaMemcpyHostToDevice));
         }
         if (best_ms && int32_t(b) < max_bins) best_ms[b] = best;
     }

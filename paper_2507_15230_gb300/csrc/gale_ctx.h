@@ -23,6 +23,8 @@ struct Bin {
     int grid = 0;                   // persistent CTAs
     int ctas_per_sm = 0;
     bool spill = false;             // regions in global scratch (working set too large for shared memory)
+    bool per_item = false;          // each member runs under its own plan (gale_ctx::d_plans); `plan` is the
+                                    // launch envelope: block size and the largest member's shared memory
 };
 
 struct DevAlloc {
@@ -60,6 +62,8 @@ struct gale_ctx {
     int64_t *d_totals = nullptr;            // [10]
     int64_t *d_bsum = nullptr;              // output placement scratch
     char *d_spill = nullptr;                // per-CTA regions of spill bins
+    gale::SmemPlan *d_plans = nullptr;      // [K] own plans of the members of per-item bins
+    std::vector<gale::SmemPlan> h_plans;    // host copy
     int64_t spill_bytes = 0;
     std::vector<int64_t> sizes;             // host [K*5]
     int64_t totals[5] = {0, 0, 0, 0, 0};

@@ -178,15 +178,20 @@ struct DevMesh {
 // CTA uses the slice gscratch + blockIdx.x * plan.total of global memory.
 // mask: the relations the context is preconditioned for (TT sizes only
 // when it holds R_TT).
+// plans (non-NULL): every cluster k runs under its own plan plans[k] (device
+// memory), and `plan` only gives the launch's block size and the dynamic
+// shared memory (the largest of the plans); never with gscratch.
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
-                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, uint32_t mask);
+                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, uint32_t mask,
+                      const SmemPlan *plans = nullptr);
 // Output placement for n listed clusters (three launches).  bsum: device
 // scratch of bases_scratch_words(n) int64 words.
 int bases_scratch_words(int32_t n);
 int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t *sizes, uint32_t mask,
                  const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, int64_t *bsum, void *stream);
 int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
-                 int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch);
+                 int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch,
+                 const SmemPlan *plans = nullptr);
 // One launch, one CTA, one work item (the per-cluster baseline form).
 int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,
                      void *stream, char *gscratch);
@@ -207,7 +212,7 @@ int launch_serve(const DevMesh &m, const SmemPlan &plan, const ServeRing &ring, 
 int serve_ctas_per_sm(const SmemPlan &plan);
 
 int kernel_smem_limit();
-int max_ctas_per_sm(const SmemPlan &plan, bool spill);
+int max_ctas_per_sm(const SmemPlan &plan, bool spill, bool per_item = false);
 // Sets the dynamic shared memory limit of the cluster kernels to smem
 // (clamped to dynamic_smem_limit()); false if the runtime refused.
 bool prepare_kernels(int smem);

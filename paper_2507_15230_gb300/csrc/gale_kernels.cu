@@ -969,6 +969,95 @@ __global__ void __launch_bounds__(kMaxThreads) build_one_kernel(DevMesh m, SmemP
 }
 
 // ---------------------------------------------------------------------------
+// Clusters that each carry their own shared-memory plan (plans[k]), for the
+// largest clusters, whose plans cannot be merged under one launch plan
+// without exceeding a CTA's shared memory: every CTA copies its cluster's
+// plan into shared memory and carves its regions from it, so such clusters
+// of uneven sizes still share one persistent launch, with the dynamic shared
+// memory of the largest.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_plan(SmemPlan &dst, const SmemPlan *src) {
+    constexpr int kWords = int(sizeof(SmemPlan) / 4);
+    for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+        reinterpret_cast<int32_t *>(&dst)[i] = reinterpret_cast<const int32_t *>(src)[i];
+}
+
+__global__ void __launch_bounds__(kMaxThreads) count_kernel_pi(DevMesh m, const SmemPlan *plans, const int32_t *ids,
+                                                              int32_t n, int64_t *sizes, int32_t *err, int32_t *ticket,
+                                                              uint32_t mask) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int32_t s_idx;
+    __shared__ int64_t s_sizes[SZ_N];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(16) SmemPlan s_plan;
+    init_barrier<false>(&s_bar);
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= n) break;
+        const int k = ids ? ids[idx] : idx;
+        if (k < 0 || k >= m.K) {
+            if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
+            continue;
+        }
+        load_plan(s_plan, plans + k);
+        if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
+        __syncthreads();
+        const Smem S = carve(smem, s_plan);
+        if (!run_cluster<true, false>(m, s_plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr,
+                                      s_sizes, err, &s_bar, phase))
+            return;
+        __syncthreads();
+        if (threadIdx.x < SZ_N) sizes[int64_t(k) * SZ_N + threadIdx.x] = s_sizes[threadIdx.x];
+    }
+}
+
+__global__ void __launch_bounds__(kMaxThreads) build_kernel_pi(DevMesh m, const SmemPlan *plans, const WorkItem *items,
+                                                              const int32_t *order, int32_t n, int32_t *err,
+                                                              int32_t *ticket) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int32_t s_idx;
+    __shared__ WorkItem s_item;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(16) SmemPlan s_plan;
+    init_barrier<false>(&s_bar);
+    uint32_t phase = 0;
+    if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
+    for (;;) {
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= n) break;
+        if (threadIdx.x == 0) {
+            s_item = items[order ? order[idx] : idx];
+            s_idx = atomicAdd(ticket, 1);  // the next cluster of this CTA
+        }
+        __syncthreads();
+        if (threadIdx.x == 32 && s_idx < n) {
+            const int k2 = items[order ? order[s_idx] : s_idx].k;
+            if (k2 >= 0 && k2 < m.K) {
+                const int64_t w0 = m.blk_off[k2], w1 = m.blk_off[k2 + 1];
+                if (w1 > w0) prefetch_l2(m.blocks + w0, uint32_t(4 * (w1 - w0)));
+            }
+        }
+        const int k = s_item.k;
+        if (k < 0 || k >= m.K) {
+            if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
+            continue;
+        }
+        load_plan(s_plan, plans + k);
+        __syncthreads();
+        const Smem S = carve(smem, s_plan);
+        if (!run_cluster<false, false>(m, s_plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
+                                       nullptr, err, &s_bar, phase))
+            return;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Device-resident serving loop.  Work items arrive in a ring in mapped host
 // memory; the host writes an item and then publishes its ticket by a release
 // store of the ring tail.  Each CTA claims the next published ticket (acquire
@@ -1024,7 +1113,7 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, S
                 }
                 if (globaltimer() - last > ring.idle_ns) break;
                 __nanosleep(sleep_ns);
-                if (sleep_ns < 8192) sleep_ns *= 2;
+                if (sleep_ns < 2048) sleep_ns *= 2;
             }
             if (t >= 0) {
                 s_claim = globaltimer();
@@ -1270,6 +1359,8 @@ int dynamic_smem_limit() {
         stat = std::max(stat, int(a.sharedSizeBytes));
     if (cudaFuncGetAttributes(&a, count_kernel<false>) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
     if (cudaFuncGetAttributes(&a, serve_kernel) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
+    if (cudaFuncGetAttributes(&a, build_kernel_pi) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
+    if (cudaFuncGetAttributes(&a, count_kernel_pi) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
     cudaGetLastError();
     return optin - stat;
 }
@@ -1290,15 +1381,20 @@ bool prepare_kernels(int smem) {
     ok &= cudaFuncSetAttribute(build_one_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
           cudaSuccess;
     ok &= cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(build_kernel_pi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(count_kernel_pi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     cudaGetLastError();
     if (ok) granted[d] = smem;
     return ok;
 }
 
-int max_ctas_per_sm(const SmemPlan &plan, bool spill) {
+int max_ctas_per_sm(const SmemPlan &plan, bool spill, bool per_item) {
     int a = 0, b = 0;
     cudaError_t e1, e2;
-    if (spill) {
+    if (per_item) {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, build_kernel_pi, plan.threads, plan.total);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_kernel_pi, plan.threads, plan.total);
+    } else if (spill) {
         e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, build_kernel<true>, plan.threads, 0);
         e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_kernel<true>, plan.threads, 0);
     } else {
@@ -1310,10 +1406,13 @@ int max_ctas_per_sm(const SmemPlan &plan, bool spill) {
 }
 
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
-                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, uint32_t mask) {
+                      int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, uint32_t mask,
+                      const SmemPlan *plans) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
-    if (gscratch)
+    if (plans)
+        count_kernel_pi<<<grid, plan.threads, plan.total, s>>>(m, plans, ids, n, sizes_out, err, ticket, mask);
+    else if (gscratch)
         count_kernel<true><<<grid, plan.threads, 0, s>>>(m, plan, ids, n, sizes_out, err, ticket, gscratch, mask);
     else
         count_kernel<false><<<grid, plan.threads, plan.total, s>>>(m, plan, ids, n, sizes_out, err, ticket, nullptr,
@@ -1335,10 +1434,11 @@ int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t 
 }
 
 int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
-                 int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch) {
+                 int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, const SmemPlan *plans) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
-    if (gscratch) build_kernel<true><<<grid, plan.threads, 0, s>>>(m, plan, items, order, n, err, ticket, gscratch);
+    if (plans) build_kernel_pi<<<grid, plan.threads, plan.total, s>>>(m, plans, items, order, n, err, ticket);
+    else if (gscratch) build_kernel<true><<<grid, plan.threads, 0, s>>>(m, plan, items, order, n, err, ticket, gscratch);
     else build_kernel<false><<<grid, plan.threads, plan.total, s>>>(m, plan, items, order, n, err, ticket, nullptr);
     return int(cudaGetLastError());
 }

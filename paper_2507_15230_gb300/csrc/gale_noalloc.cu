@@ -149,7 +149,7 @@ extern "C" gale_status gale_build_clusters_noalloc(gale_ctx *ctx, const int32_t 
         if (m == 0) continue;
         const gale::Bin &bin = ctx->bins[b];
         rc = gale::launch_build(dm, bin.plan, S->items, S->order + cnt[b], m, &S->err, &S->tickets[b],
-                                bin.grid < m ? bin.grid : m, s, nullptr);
+                                bin.grid < m ? bin.grid : m, s, nullptr, bin.per_item ? ctx->d_plans : nullptr);
     }
     if (rc != 0) return fail(GALE_ECUDA, std::string("launch: ") + cudaGetErrorString(cudaError_t(rc)));
     int32_t err = 0;

@@ -7,7 +7,11 @@
 // miss creates an entry and queues it for the leader thread, which
 //   - admits queued entries in arrival order against the budget: each gets a
 //     slot in one device slab (first fit, coalescing free list), evicting
-//     unpinned ready entries least-recently-used first;
+//     unpinned ready entries least-recently-used first; prefetched clusters
+//     (Section 4.5's proactive computation) wait in a queue of their own and
+//     are admitted only while no request waits, with at most half the loop's
+//     CTAs busy on them, and a request for a cluster still queued as a
+//     prefetch moves it to the request queue;
 //   - writes each admitted entry's work item (its cluster, mask and output
 //     pointers into its slot) into a ring in pinned, mapped host memory and
 //     publishes its ticket (release store of the ring tail);
@@ -129,7 +133,9 @@ struct Serve {
     std::mutex mu;
     std::condition_variable cv_leader; // work for the leader
     std::unordered_map<int64_t, std::unique_ptr<Entry>> entries;  // key = k * 16 + mask
-    std::deque<Entry *> queue;           // waiting for admission
+    std::deque<Entry *> queue;           // requested entries waiting for admission, in arrival order
+    std::deque<Entry *> pqueue;          // prefetch entries waiting for admission
+    int64_t inflight_prefetch = 0;       // prefetch entries on the device
     std::list<Entry *> lru;              // ready entries, most recent first
     Slab slab;
     char *slab_base = nullptr;
@@ -160,6 +166,7 @@ struct Serve {
     cudaStream_t loop_stream = nullptr;
     cudaEvent_t loop_event = nullptr;
     bool loop_launched = false;
+    bool loop_seen_running = false;  // this leader iteration found the loop still running
     long long published = 0;      // tickets published
     std::map<long long, Entry *> inflight;  // ticket -> entry
     uint64_t idle_ns = 20ull * 1000 * 1000;
@@ -333,6 +340,7 @@ bool Serve::admit(Entry *e) {
 
 // an entry's build finished: it joins the LRU list
 void Serve::stage_done(Entry *e) {
+    if (e->prefetch) inflight_prefetch--;
     e->state = St::Ready;
     lru.push_front(e);
     e->lru = lru.begin();
@@ -397,10 +405,13 @@ void Serve::publish_loop(Entry *e) {
     published = t + 1;
     e->ticket = t;
     e->state = St::Building;
+    if (e->prefetch) inflight_prefetch++;
     e->t_published = now_ns();
     if (!e->prefetch) stats.t_prepare_ns += e->t_published - e->t_admitted;
     inflight[t] = e;
-    if (!loop_launched || cudaEventQuery(loop_event) == cudaSuccess) {
+    // one event query per leader iteration: a running loop claims every
+    // ticket published while it runs
+    if (!loop_launched || (!loop_seen_running && cudaEventQuery(loop_event) == cudaSuccess)) {
         // (re)start the loop; a previous one has drained or never ran
         const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
         ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns, d_times};
@@ -409,6 +420,7 @@ void Serve::publish_loop(Entry *e) {
         loop_launched = true;
         stats.batches++;
     }
+    loop_seen_running = true;
 }
 
 void Serve::poll_loop() {
@@ -459,10 +471,12 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
         if (m == 0) continue;
         char *scr = ctx->bins[bb].spill ? d_spill : nullptr;
         if (single_mode)
-            rc = launch_build_one(dm, ctx->bins[bb].plan, d_batch, h_border[off[bb]], d_err, batch_stream, scr);
+            rc = launch_build_one(dm, ctx->bins[bb].per_item ? ctx->h_plans[b[h_border[off[bb]]]->k] : ctx->bins[bb].plan,
+                                  d_batch, h_border[off[bb]], d_err, batch_stream, scr);
         else
             rc = launch_build(dm, ctx->bins[bb].plan, d_batch, d_border + off[bb], m, d_err, d_tick + bb,
-                              std::min(ctx->bins[bb].grid, m), batch_stream, scr);
+                              std::min(ctx->bins[bb].grid, m), batch_stream, scr,
+                              ctx->bins[bb].per_item ? ctx->d_plans : nullptr);
     }
     if (rc != 0) {
         // nothing of this batch is trusted: its entries fail and free their space
@@ -472,6 +486,7 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
             e->cv.notify_all();
             slab.release(e->off, e->bytes);
             e->bytes = 0;
+            if (e->prefetch && e->refs == 0) entries.erase(int64_t(e->k) * 16 + e->mask);  // frees e
         }
         cudaStreamSynchronize(batch_stream);
         return;
@@ -481,6 +496,7 @@ void Serve::launch_batch(std::vector<Entry *> &b) {
     for (Entry *e : b) {
         e->state = St::Building;
         e->t_published = tp;
+        if (e->prefetch) inflight_prefetch++;
         if (!e->prefetch) stats.t_prepare_ns += tp - e->t_admitted;
     }
     batch_entries = b;
@@ -505,34 +521,45 @@ void Serve::leader_loop() {
 #endif
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
+        loop_seen_running = false;
         bool progressed = expire_leases();
-        // admission, in arrival order
+        // admission: requested entries in arrival order, then prefetches while
+        // no request waits and few prefetches occupy the device, so that a
+        // request never queues behind work nobody has asked for yet
         std::vector<Entry *> batch;
-        while (!queue.empty()) {
-            Entry *e = queue.front();
-            const bool via_loop = loop_mode && in_loop[ctx->bin_of[e->k]];
-            if (!via_loop && batch_busy) break;
-            if (via_loop && published - (inflight.empty() ? published : inflight.begin()->first) >= kRingCap) break;
-            if (!admit(e)) {
-                if (!(e->prefetch && e->refs == 0)) break;
-                // a prefetch waits for nothing: drop it while the budget is pinned
-                queue.pop_front();
-                stats.prefetch_dropped++;
-                entries.erase(int64_t(e->k) * 16 + e->mask);  // frees e
+        const int64_t prefetch_cap = loop_mode ? std::max(1, grid / 2) : kRingCap / 2;
+        for (int pass = 0; pass < 2; ++pass) {
+            std::deque<Entry *> &q = pass == 0 ? queue : pqueue;
+            if (pass == 1 && !queue.empty()) break;
+            while (!q.empty()) {
+                Entry *e = q.front();
+                if (pass == 1 && inflight_prefetch + int64_t(batch.size()) >= prefetch_cap) break;
+                const bool via_loop = loop_mode && in_loop[ctx->bin_of[e->k]];
+                if (!via_loop && batch_busy) break;
+                if (via_loop && published - (inflight.empty() ? published : inflight.begin()->first) >= kRingCap)
+                    break;
+                if (!admit(e)) {
+                    if (!(e->prefetch && e->refs == 0)) break;
+                    // a prefetch waits for nothing: drop it while the budget is pinned
+                    q.pop_front();
+                    stats.prefetch_dropped++;
+                    entries.erase(int64_t(e->k) * 16 + e->mask);  // frees e
+                    progressed = true;
+                    continue;
+                }
+                q.pop_front();
                 progressed = true;
-                continue;
+                if (e->state == St::Failed) {
+                    if (e->prefetch && e->refs == 0) entries.erase(int64_t(e->k) * 16 + e->mask);
+                    continue;
+                }
+                if (via_loop) publish_loop(e);
+                else {
+                    batch.push_back(e);
+                    if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
+                }
             }
-            queue.pop_front();
-            progressed = true;
-            if (e->state == St::Failed) {
-                if (e->prefetch && e->refs == 0) entries.erase(int64_t(e->k) * 16 + e->mask);
-                continue;
-            }
-            if (via_loop) publish_loop(e);
-            else {
-                batch.push_back(e);
-                if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
-            }
+            if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
         }
         if (!batch.empty()) launch_batch(batch);
         const size_t before = inflight.size() + (batch_busy ? batch_entries.size() : 0);
@@ -540,15 +567,15 @@ void Serve::leader_loop() {
         poll_batch();
         const size_t after = inflight.size() + (batch_busy ? batch_entries.size() : 0);
         if (after != before || progressed) stats.max_batch = std::max<int64_t>(stats.max_batch, int64_t(before));
-        if (const size_t pending = queue.size() + after) {
+        if (const size_t pending = queue.size() + pqueue.size() + after) {
             int b = 0;
             while (b < 11 && (size_t(2) << b) <= pending) ++b;
             stats.depth_hist[b]++;
         }
         stats.cache_bytes_used = slab.used;
-        if (after > 0 || !queue.empty()) {
+        if (after > 0 || !queue.empty() || !pqueue.empty()) {
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(10));
+            std::this_thread::sleep_for(std::chrono::microseconds(2));
             lk.lock();
         } else {
             cv_leader.wait_for(lk, std::chrono::milliseconds(50));
@@ -673,6 +700,15 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
     if (e && e->prefetch && !e->claimed) {
         e->claimed = true;
         s->stats.prefetch_hits++;
+        if (e->state == St::Queued) {
+            // still waiting as a prefetch: it becomes a request, queued now
+            auto pit = std::find(s->pqueue.begin(), s->pqueue.end(), e);
+            if (pit != s->pqueue.end()) s->pqueue.erase(pit);
+            e->prefetch = false;
+            e->t_queued = gale::now_ns();
+            s->queue.push_back(e);
+            s->cv_leader.notify_all();
+        }
     }
     if (e && e->state == St::Ready) {
         s->stats.hits++;
@@ -709,7 +745,7 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
         pe->mask = mask;
         pe->prefetch = true;
         pe->t_queued = gale::now_ns();
-        s->queue.push_back(pe.get());
+        s->pqueue.push_back(pe.get());
         s->entries[int64_t(kk) * 16 + mask] = std::move(pe);
         s->stats.prefetches++;
     }

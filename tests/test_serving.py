@@ -2,8 +2,9 @@
 device-resident loop (or the launch-per-batch mode), the HBM-budgeted LRU
 cache, admission against the budget, and the critical-point consumer.
 
-Every served result must equal the same cluster's relations built alone by
-the bulk path, bit for bit, whatever else is in flight."""
+Every served result must equal the CPU oracle's relations of that cluster,
+bit for bit, whatever else is in flight; the same cluster built alone by the
+bulk path is checked as well ("the same alone and in the mix")."""
 import os
 import threading
 
@@ -11,7 +12,9 @@ import numpy as np
 import pytest
 
 import gen
+import oracle
 import paper_2507_15230_gb300 as gale
+from parity_util import expected_bulk
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -31,12 +34,23 @@ def same(a, b):
     return a.keys() == b.keys() and all(np.array_equal(a[n], b[n]) for n in a)
 
 
+def oracle_reference(m, mask=gale.ALL):
+    """Per-cluster relations of the CPU oracle (global definitions, sliced
+    per cluster), in the layout of a served view."""
+    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
+    return {k: expected_bulk(rel, canon, [k], mask) for k in range(m.nclusters)}
+
+
 def run_mix(budget, nthreads=8, rounds=40, masks=(gale.ALL, gale.VT | gale.VV | gale.TT, gale.ET),
             mode=gale.SERVE_LOOP):
     m = gen.small_grid(with_field=False)
+    orefs = {mk: oracle_reference(m, mk) for mk in masks}
     with gale.Context.load(m, device=0, cache_budget_bytes=budget) as ctx:
         ctx.serve_configure(mode)
         refs = {mk: bulk_reference(ctx, mk) for mk in masks}
+        for mk in masks:  # alone = the oracle
+            for k in range(ctx.K):
+                assert same(refs[mk][k], orefs[mk][k]), (mk, k)
         errors = []
 
         def consumer(seed):
@@ -49,7 +63,7 @@ def run_mix(budget, nthreads=8, rounds=40, masks=(gale.ALL, gale.VT | gale.VV | 
                 want = {n: a for n, a in refs[mk][k].items()}
                 # a cached superset entry may serve a narrower mask
                 got = {n: got[n] for n in want}
-                if not same(got, want):
+                if not same(got, want) or not same(got, orefs[mk][k]):
                     errors.append((k, mk))
                 ctx.release(v)
 
@@ -159,9 +173,12 @@ def test_mixed_meshes_loops_side_by_side():
               gen.freudenthal_mesh(9, 64, seed=8, jitter=0.3, with_field=False),
               gen.delaunay_mesh(3000, seed=18, kd_cap=512, with_field=False),
               gen.delaunay_mesh(6000, seed=19, kd_cap=512, with_field=False)]
+    orefs = [oracle_reference(m) for m in meshes]
     ctxs = [gale.Context.load(m, device=0, cache_budget_bytes=1 << 20) for m in meshes]
     try:
         refs = [bulk_reference(c) for c in ctxs]
+        for r, o in zip(refs, orefs):
+            assert all(same(r[k], o[k]) for k in o)
         for c in ctxs:
             c.serve_configure(gale.SERVE_LOOP, loop_ctas=8)
         names = {gale.VT: ("vt_off", "vt_val"), gale.VV: ("vv_off", "vv_val"),
@@ -179,7 +196,7 @@ def test_mixed_meshes_loops_side_by_side():
                 for bit, arrs in names.items():
                     if mk & bit:
                         for n in arrs:
-                            if not np.array_equal(got[n], refs[i][k][n]):
+                            if not np.array_equal(got[n], refs[i][k][n]) or not np.array_equal(got[n], orefs[i][k][n]):
                                 errors.append((i, k, mk, n))
                 ctxs[i].release(v)
 
@@ -213,9 +230,11 @@ def test_loop_mode_with_clusters_too_large_for_it():
     serves the size bins that fit it and the leader builds the rest by
     batched launches beside it; every result equals the bulk build."""
     m = gen.delaunay_mesh(60000, seed=11, with_field=False)
+    oref = oracle_reference(m)
     with gale.Context.load(m, device=0, cache_budget_bytes=64 << 20) as ctx:
         assert any(b["spill"] for b in ctx.bins())
         ref = bulk_reference(ctx)
+        assert all(same(ref[k], oref[k]) for k in oref)
         ctx.serve_configure(gale.SERVE_LOOP, loop_ctas=16)
         I_V, _, _ = ctx.intervals()
         size = np.diff(I_V)
@@ -227,7 +246,8 @@ def test_loop_mode_with_clusters_too_large_for_it():
             picks = big + [int(k) for k in rng.integers(ctx.K, size=20)]
             for k in picks:
                 v = ctx.request(k, gale.ALL, timeout_ns=60_000_000_000)
-                if not same(gale.view_to_numpy(v), ref[k]):
+                got = gale.view_to_numpy(v)
+                if not same(got, ref[k]) or not same(got, oref[k]):
                     errors.append(k)
                 ctx.release(v)
 
@@ -246,8 +266,10 @@ def test_prefetch_serves_following_clusters(mode):
     consumers walking in cluster order then find their next clusters already
     built or in flight.  Every result still equals the bulk build."""
     m = gen.small_grid(with_field=False)
+    oref = oracle_reference(m)
     with gale.Context.load(m, device=0, cache_budget_bytes=64 << 20) as ctx:
         ref = bulk_reference(ctx)
+        assert all(same(ref[k], oref[k]) for k in oref)
         ctx.serve_configure(mode, prefetch=3)
         errors = []
 
@@ -423,5 +445,39 @@ def test_served_rows_match_the_bulk_build_at_128cubed():
         for t in th:
             t.join()
         st = ctx.serve_stats()
+        # a sample of the served clusters, fresh from the loop, against the
+        # oracle's per-cluster producer
+        canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
+        for k in (int(x) for x in sample[:8]):
+            want_o = expected_bulk(None, canon, [k], gale.ALL, per_cluster=True)
+            v = ctx.request(k, gale.ALL, timeout_ns=60_000_000_000)
+            got = gale.view_to_numpy(v)
+            ctx.release(v)
+            assert same(got, want_o), k
     assert not errors, errors[:5]
     assert st.requests == 1600 and st.evictions > 0
+
+
+def test_request_promotes_a_queued_prefetch_and_null_consumers_walk_every_cluster():
+    """With a deep prefetch, requests for clusters that are still queued as
+    prefetches move them to the request queue; null consumers (view taken and
+    released, no work) walk every cluster, and a final sample of views equals
+    the oracle."""
+    import consumers
+    m = gen.small_grid(with_field=True)
+    oref = oracle_reference(m)
+    with gale.Context.load(m, device=0, cache_budget_bytes=64 << 20) as ctx:
+        ctx.serve_configure(gale.SERVE_LOOP, prefetch=8, loop_ctas=2)
+        vperm, _ = ctx.permutations()
+        f_c, inid = consumers.canonical_inputs(m.field, vperm)
+        I_V, _, _ = ctx.intervals()
+        _, lat, st = consumers.serve_run(ctx, f_c, inid, ctx.rows(), I_V, nthreads=8,
+                                         mask=gale.VT | gale.VV | gale.TT, null_work=True)
+        assert st["failures"] == 0 and st["requests"] == ctx.K and (lat > 0).all()
+        s = ctx.serve_stats()
+        assert s.prefetches > 0 and s.prefetch_hits > 0
+        for k in range(0, ctx.K, 7):
+            v = ctx.request(k, gale.ALL, timeout_ns=20_000_000_000)
+            got = gale.view_to_numpy(v)
+            ctx.release(v)
+            assert same(got, oref[k]), k
