@@ -149,7 +149,7 @@ typedef struct {
     int64_t max_batch;
     int64_t prefetches;        /* entries built ahead of any request (proactive prefetch) */
     int64_t prefetch_hits;     /* requests served by such an entry, ready or in flight */
-    int64_t prefetch_dropped;  /* prefetches dropped because the budget was pinned */
+    int64_t prefetch_dropped;  /* prefetches dropped because the budget was full (a prefetch never evicts) */
     int64_t leases_expired;    /* pins revoked because their lease ran out (gale_serve_set_lease) */
     /* Waiting time by stage (the stages of Section 5.3's breakdown), in
      * nanoseconds summed over requests or over entries built for a request: */
@@ -166,6 +166,16 @@ typedef struct {
      * entries queued or in flight, b = 0 for 1, 1 for 2-3, 2 for 4-7, ...,
      * 11 for 2048 and more. */
     int64_t depth_hist[12];
+    /* The leader's own timing: */
+    int64_t max_queue_ns;      /* the longest admission wait of an entry built for a request */
+    int64_t queue_hist[16];    /* admission waits of entries built for a request: bucket b counts
+                                  waits of [2^b, 2^(b+1)) microseconds (b = 0 also below 1 us) */
+    int64_t leader_passes;     /* passes of the leader loop */
+    int64_t leader_hold_ns;    /* summed time the leader held the serving lock in its passes */
+    int64_t max_leader_hold_ns;/* the longest single pass */
+    int64_t promotions;        /* queued prefetches a request moved to the request queue */
+    int64_t max_prefetch_queue;/* the longest prefetch queue seen */
+    int64_t requester_pumps;   /* steps of the serving state machine run by waiting requests */
 } gale_serve_stats;
 
 /*
@@ -316,12 +326,17 @@ enum {
  * request for cluster k also queues clusters k+1 .. k+m with the same mask
  * unless cached or queued, the paper's leader building the requested segment
  * together with the following ones, Section 4.5; prefetched entries pin
- * nothing and are dropped when the budget is pinned) before the first
- * gale_request of the context;
+ * nothing, are admitted only while no request waits and only into free
+ * cache space, never evicting, and are dropped when the budget is full)
+ * before the first gale_request of the context;
  * EBUSY afterwards, EINVAL for an unknown mode, a negative cap or depth, or when no
- * size bin fits the loop.  The loop serves the size bins whose merged
- * working-memory plan fits one CTA (smallest first); requests for clusters
- * of the other bins are built by batched launches beside it. */
+ * size bin fits the loop.  The loop builds every cluster under the
+ * cluster's own working-memory plan at one block size, and serves the size
+ * bins whose clusters each fit one CTA; requests for clusters of the other
+ * bins (global-scratch bins) are built by batched launches beside it.  A
+ * thread waiting in gale_request advances admission, publication and
+ * completion itself whenever the leader thread has not lately, so requests
+ * progress even while consumer threads occupy every host core. */
 gale_status gale_serve_configure(gale_ctx *ctx, int32_t mode, int64_t idle_us, int32_t loop_ctas, int32_t prefetch);
 
 /* Unpin a view from gale_request; its entry becomes evictable.  The view's
@@ -437,11 +452,13 @@ gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale_coboundary
  * size bin) and CTAs per SM of the persistent grid (0 = as many as fit). */
 gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
 
-/* Size bins of the batched form: for each bin (up to max_bins) six int32
+/* Size bins of the batched form: for each bin (up to max_bins) seven int32
  * values - clusters, threads per CTA, bytes of per-CTA working memory, CTAs
- * per SM, persistent grid size, and 1 if the working memory is global
- * scratch (clusters too large for shared memory) else 0 - into
- * out[6*i .. 6*i+5].  Returns the number of bins in *nbins. */
+ * per SM, persistent grid size, 1 if the working memory is global scratch
+ * (clusters too large for shared memory) else 0, and 1 if every member runs
+ * under its own shared-memory plan (the largest clusters, whose plans do not
+ * merge) else 0 - into out[7*i .. 7*i+6].  Returns the number of bins in
+ * *nbins. */
 gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t *nbins);
 
 /* Members of the size bins: the cluster ids of bin 0, then bin 1, ... (K

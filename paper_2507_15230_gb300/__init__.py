@@ -76,7 +76,10 @@ class ServeStats(ctypes.Structure):
                                               "cache_bytes_used", "cache_bytes_budget", "max_batch", "prefetches",
                                               "prefetch_hits", "prefetch_dropped", "leases_expired",
                                               "t_enqueue_ns", "t_queue_ns", "t_prepare_ns", "t_build_ns", "t_kernel_ns",
-                                              "t_wait_ns", "max_wait_ns")] + [("depth_hist", ctypes.c_int64 * 12)]
+                                              "t_wait_ns", "max_wait_ns")] + [("depth_hist", ctypes.c_int64 * 12)] + \
+               [("max_queue_ns", ctypes.c_int64), ("queue_hist", ctypes.c_int64 * 16)] + \
+               [(n, ctypes.c_int64) for n in ("leader_passes", "leader_hold_ns", "max_leader_hold_ns", "promotions",
+                                              "max_prefetch_queue", "requester_pumps")]
 
 
 # the symbols include/gale.h declares
@@ -421,13 +424,14 @@ class Context:
 
     def bins(self) -> list:
         """Size bins: clusters, threads, working bytes per CTA, CTAs per SM,
-        grid, spill (1: working memory in global scratch)."""
+        grid, spill (1: working memory in global scratch), per_item (1: each
+        member runs under its own plan)."""
         n = ctypes.c_int32(0)
         _check(self._lib.gale_get_bins(self._h, None, 0, ctypes.byref(n)))
-        out = np.zeros(6 * max(n.value, 1), np.int32)
+        out = np.zeros(7 * max(n.value, 1), np.int32)
         _check(self._lib.gale_get_bins(self._h, _p(out), n.value, ctypes.byref(n)))
-        keys = ("clusters", "threads", "bytes", "ctas_per_sm", "grid", "spill")
-        return [dict(zip(keys, out[6 * i:6 * i + 6].tolist())) for i in range(n.value)]
+        keys = ("clusters", "threads", "bytes", "ctas_per_sm", "grid", "spill", "per_item")
+        return [dict(zip(keys, out[7 * i:7 * i + 7].tolist())) for i in range(n.value)]
 
     def bin_members(self) -> np.ndarray:
         """Cluster ids of bin 0, bin 1, ... in launch order (K ids)."""

@@ -194,10 +194,13 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     // shared memory).
     ctx->h_plans.assign(size_t(K), gale::SmemPlan{});
     {
+        std::map<int, int> ntop;  // block size -> bins of the top tier
+        for (auto &b : ctx->bins)
+            if (!b.spill && b.plan.total > tiers[2]) ntop[b.plan.threads]++;
         std::vector<gale::Bin> kept;
         std::map<int, gale::Bin> top;  // block size -> merged bin
         for (auto &b : ctx->bins) {
-            if (b.spill || b.plan.total <= tiers[2]) {
+            if (b.spill || b.plan.total <= tiers[2] || ntop[b.plan.threads] < 2) {
                 kept.push_back(std::move(b));
                 continue;
             }
@@ -268,37 +271,43 @@ const gale::SmemPlan *plans_of(gale_ctx *ctx, const gale::Bin &b) { return b.per
 }  // namespace
 
 namespace gale {
-// Shared-memory plan of the serving loop: size bins are merged, smallest
-// plan first, while the merged plan still fits one CTA; *fits = some bin
-// made it, and (*in_loop)[b] marks the bins the loop serves (the others are
-// served by batched launches).
-SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop) {
+// Plans of the serving loop.  The loop's CTAs build any cluster under the
+// cluster's own plan at one block size (the largest of the size bins), so
+// every bin whose members each fit one CTA is served by the loop; the others
+// (global-scratch bins) are served by batched launches beside it.  Returns
+// the launch envelope (block size, the largest member's shared memory);
+// *fits = some bin made it; (*in_loop)[b] marks the bins the loop serves;
+// own (optional, K entries) receives the plans of their members.
+SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop, std::vector<SmemPlan> *own) {
     const size_t nb = ctx->bins.size();
-    std::vector<size_t> order;
-    for (size_t b = 0; b < nb; ++b)
-        if (!ctx->bins[b].spill && !ctx->bins[b].per_item) order.push_back(b);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t a, size_t b) { return ctx->bins[a].plan.total < ctx->bins[b].plan.total; });
-    std::vector<uint8_t> sel(nb, 0);
-    Caps c{};
-    int threads = 64;
-    bool any = false;
-    SmemPlan best{};
+    const int32_t K = ctx->hm.K;
     const int limit = dynamic_smem_limit();
-    for (size_t b : order) {
-        const Caps m = any ? merge(c, ctx->bins[b].plan.caps) : ctx->bins[b].plan.caps;
-        const int t = std::max(threads, ctx->bins[b].plan.threads);
-        const SmemPlan p = plan_smem(m, t);
-        if (p.total > limit || serve_ctas_per_sm(p) < 1) continue;
-        c = m;
-        threads = t;
-        best = p;
+    int threads = 64;
+    for (size_t b = 0; b < nb; ++b)
+        if (!ctx->bins[b].spill) threads = std::max(threads, ctx->bins[b].plan.threads);
+    std::vector<uint8_t> sel(nb, 0);
+    if (own) own->assign(size_t(K), SmemPlan{});
+    SmemPlan env = plan_smem(Caps{}, threads);
+    env.total = 0;
+    bool any = false;
+    for (size_t b = 0; b < nb; ++b) {
+        const Bin &bin = ctx->bins[b];
+        if (bin.spill) continue;
+        int top = 0;
+        for (int32_t k : bin.clusters) top = std::max(top, plan_smem(bin_caps(ctx, k), threads).total);
+        if (top > limit) continue;
+        SmemPlan probe = env;
+        probe.total = std::max(env.total, top);
+        if (serve_ctas_per_sm(probe) < 1) continue;
+        env.total = probe.total;
         sel[b] = 1;
         any = true;
+        if (own)
+            for (int32_t k : bin.clusters) (*own)[k] = plan_smem(bin_caps(ctx, k), threads);
     }
     *fits = any;
     if (in_loop) *in_loop = sel;
-    return best;
+    return env;
 }
 // Lengths of the ten output arrays of cluster k under mask.
 void item_lengths(const gale_ctx *ctx, int32_t k, uint32_t mask, int64_t *L) {
@@ -1260,12 +1269,13 @@ gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t
     *nbins = int32_t(ctx->bins.size());
     for (int32_t b = 0; b < *nbins && b < max_bins && out; ++b) {
         const gale::Bin &bin = ctx->bins[b];
-        out[6 * b + 0] = int32_t(bin.clusters.size());
-        out[6 * b + 1] = bin.plan.threads;
-        out[6 * b + 2] = bin.plan.total;
-        out[6 * b + 3] = bin.ctas_per_sm;
-        out[6 * b + 4] = bin.grid;
-        out[6 * b + 5] = bin.spill ? 1 : 0;
+        out[7 * b + 0] = int32_t(bin.clusters.size());
+        out[7 * b + 1] = bin.plan.threads;
+        out[7 * b + 2] = bin.plan.total;
+        out[7 * b + 3] = bin.ctas_per_sm;
+        out[7 * b + 4] = bin.grid;
+        out[7 * b + 5] = bin.spill ? 1 : 0;
+        out[7 * b + 6] = bin.per_item ? 1 : 0;
     }
     return GALE_OK;
 }

@@ -208,7 +208,10 @@ struct ServeRing {
     unsigned long long idle_ns;   // a CTA returns after this long without work
     long long *times;             // [2 cap] device clock (ns) at a ticket's claim and completion
 };
-int launch_serve(const DevMesh &m, const SmemPlan &plan, const ServeRing &ring, int32_t *err, int grid, void *stream);
+// plans: the plan each cluster is built under (device memory, indexed by
+// cluster id); `plan` gives the block size and the dynamic shared memory.
+int launch_serve(const DevMesh &m, const SmemPlan &plan, const SmemPlan *plans, const ServeRing &ring, int32_t *err,
+                 int grid, void *stream);
 int serve_ctas_per_sm(const SmemPlan &plan);
 
 int kernel_smem_limit();

@@ -1086,9 +1086,10 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-__global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, ServeRing ring, int32_t *err) {
+__global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, const SmemPlan *plans, ServeRing ring,
+                                                     int32_t *err) {
     extern __shared__ __align__(16) char smem[];
-    const Smem S = carve(smem, plan);
+    __shared__ __align__(16) SmemPlan s_plan;
     __shared__ long long s_t;
     __shared__ WorkItem s_item;
     __shared__ __align__(8) uint64_t s_bar;
@@ -1128,11 +1129,15 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, SmemPlan plan, S
         const long long t = s_t;
         if (t < 0) break;
         bool go_on = true;
-        if (s_item.k >= 0 && s_item.k < m.K)
-            go_on = run_cluster<false, false>(m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
+        if (s_item.k >= 0 && s_item.k < m.K) {
+            load_plan(s_plan, plans + s_item.k);  // the cluster's own plan
+            __syncthreads();
+            const Smem S = carve(smem, s_plan);
+            go_on = run_cluster<false, false>(m, s_plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
                                               s_item.mask, &s_item, nullptr, err, &s_bar, phase);
-        else if (threadIdx.x == 0)
+        } else if (threadIdx.x == 0) {
             atomicOr(err, ERR_BAD_ITEM);
+        }
         if (!go_on) break;  // a bounded wait ran out; the slot stays not done
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1457,11 +1462,11 @@ static void grow_serve_attr(int smem) {
     cudaGetLastError();
 }
 
-int launch_serve(const DevMesh &m, const SmemPlan &plan, const ServeRing &ring, int32_t *err, int grid,
-                 void *stream) {
+int launch_serve(const DevMesh &m, const SmemPlan &plan, const SmemPlan *plans, const ServeRing &ring, int32_t *err,
+                 int grid, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     grow_serve_attr(plan.total);
-    serve_kernel<<<grid, plan.threads, plan.total, s>>>(m, plan, ring, err);
+    serve_kernel<<<grid, plan.threads, plan.total, s>>>(m, plans, ring, err);
     return int(cudaGetLastError());
 }
 

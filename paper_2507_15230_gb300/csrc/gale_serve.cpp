@@ -10,8 +10,9 @@
 //     unpinned ready entries least-recently-used first; prefetched clusters
 //     (Section 4.5's proactive computation) wait in a queue of their own and
 //     are admitted only while no request waits, with at most half the loop's
-//     CTAs busy on them, and a request for a cluster still queued as a
-//     prefetch moves it to the request queue;
+//     CTAs busy on them, into free space only (a prefetch never evicts, and
+//     is dropped when the budget is full), and a request for a cluster still
+//     queued as a prefetch moves it to the request queue;
 //   - writes each admitted entry's work item (its cluster, mask and output
 //     pointers into its slot) into a ring in pinned, mapped host memory and
 //     publishes its ticket (release store of the ring tail);
@@ -49,7 +50,7 @@
 namespace gale {
 
 // defined in gale_api.cpp
-SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop);
+SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop, std::vector<SmemPlan> *own = nullptr);
 
 namespace {
 
@@ -151,7 +152,8 @@ struct Serve {
     bool loop_mode = true;
     std::vector<uint8_t> in_loop;  // per size bin
     bool single_mode = false;  // one launch per request (baseline form)
-    SmemPlan plan{};
+    SmemPlan plan{};               // launch envelope of the loop
+    SmemPlan *d_plans = nullptr;   // [K] the plan each cluster the loop serves is built under
     int grid = 0;
     WorkItem *h_items = nullptr;   // mapped
     long long *h_tail = nullptr;   // mapped
@@ -167,6 +169,7 @@ struct Serve {
     cudaEvent_t loop_event = nullptr;
     bool loop_launched = false;
     bool loop_seen_running = false;  // this leader iteration found the loop still running
+    int64_t last_leader_ns = 0;      // end of the leader thread's last step of the state machine
     long long published = 0;      // tickets published
     std::map<long long, Entry *> inflight;  // ticket -> entry
     uint64_t idle_ns = 20ull * 1000 * 1000;
@@ -185,6 +188,7 @@ struct Serve {
 
     gale_status init(gale_ctx *c);
     void leader_loop();
+    bool pump(bool poll = true);
     bool admit(Entry *e);
     void fill_item(Entry *e);
     void publish_loop(Entry *e);
@@ -235,7 +239,8 @@ gale_status Serve::init(gale_ctx *c) {
     if (!slab_base) return fail(GALE_ENOMEM, "device allocation of the relation cache failed");
     slab.init(ctx->cache_budget);
     bool fits = false;
-    plan = serve_plan(ctx, &fits, &in_loop);
+    std::vector<SmemPlan> own;
+    plan = serve_plan(ctx, &fits, &in_loop, &own);
     loop_mode = fits && (ctx->serve_mode < 0 || ctx->serve_mode == GALE_SERVE_LOOP);
     single_mode = ctx->serve_mode == GALE_SERVE_SINGLE;
     if (ctx->serve_idle_us > 0) idle_ns = uint64_t(std::max<int64_t>(100, ctx->serve_idle_us)) * 1000ull;
@@ -259,6 +264,11 @@ gale_status Serve::init(gale_ctx *c) {
         !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_stop), h_stop, 0)) ||
         !ck(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_times), h_times, 0)))
         return fail(GALE_ECUDA, "mapping the serving ring failed");
+    d_plans = static_cast<SmemPlan *>(ctx->dalloc(sizeof(SmemPlan) * size_t(std::max(ctx->hm.K, 1))));
+    if (!d_plans) return fail(GALE_ENOMEM, "device allocation of the serving plans failed");
+    if (ctx->hm.K > 0 &&
+        cudaMemcpy(d_plans, own.data(), sizeof(SmemPlan) * size_t(ctx->hm.K), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(GALE_ECUDA, "uploading the serving plans failed");
     d_next = static_cast<unsigned long long *>(ctx->dalloc(64));
     d_err = static_cast<int32_t *>(ctx->dalloc(64));
     d_batch = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * kRingCap));
@@ -325,16 +335,23 @@ bool Serve::admit(Entry *e) {
         return true;
     }
     int64_t off = slab.alloc(bytes);
-    if (off < 0) {
+    if (off < 0 && !e->prefetch) {  // a prefetch takes free space only: it never evicts
         evict_for(bytes);
         off = slab.alloc(bytes);
     }
-    if (off < 0) return false;  // budget pinned: wait for releases
+    if (off < 0) return false;  // budget full (or pinned): wait for releases, or drop a prefetch
     e->off = off;
     e->bytes = bytes;
     fill_item(e);
     e->t_admitted = now_ns();
-    if (!e->prefetch) stats.t_queue_ns += e->t_admitted - e->t_queued;
+    if (!e->prefetch) {
+        const int64_t w = e->t_admitted - e->t_queued;
+        stats.t_queue_ns += w;
+        stats.max_queue_ns = std::max(stats.max_queue_ns, w);
+        int b = 0;
+        while (b < 15 && (int64_t(2000) << b) <= w) ++b;
+        stats.queue_hist[b]++;
+    }
     return true;
 }
 
@@ -415,7 +432,7 @@ void Serve::publish_loop(Entry *e) {
         // (re)start the loop; a previous one has drained or never ran
         const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
         ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns, d_times};
-        launch_serve(dm, plan, ring, d_err, grid, loop_stream);
+        launch_serve(dm, plan, d_plans, ring, d_err, grid, loop_stream);
         cudaEventRecord(loop_event, loop_stream);
         loop_launched = true;
         stats.batches++;
@@ -442,7 +459,7 @@ void Serve::poll_loop() {
     if (!inflight.empty() && loop_launched && cudaEventQuery(loop_event) == cudaSuccess) {
         const DevMesh dm{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
         ServeRing ring{d_items, d_tail, d_done, d_stop, d_next, kRingCap, 0, idle_ns, d_times};
-        launch_serve(dm, plan, ring, d_err, grid, loop_stream);
+        launch_serve(dm, plan, d_plans, ring, d_err, grid, loop_stream);
         cudaEventRecord(loop_event, loop_stream);
         stats.batches++;
     }
@@ -511,69 +528,92 @@ void Serve::poll_batch() {
     batch_busy = false;
 }
 
+// One step of the serving state machine, with mu held: admission (requested
+// entries in arrival order, then prefetches while no request waits and few
+// prefetches occupy the device, so that a request never queues behind work
+// nobody has asked for yet), publication or batched launches, and polling of
+// the device for finished entries (unless poll is false).  The leader thread
+// runs it in a loop, and so does every requesting thread while it waits: a
+// request's progress never depends on the leader thread getting a core
+// (consumer threads that compute between requests can fill every core of the
+// host).  Returns true while work is queued or on the device.
+bool Serve::pump(bool poll) {
+    int dev_before = -1;
+    cudaGetDevice(&dev_before);
+    if (dev_before != ctx->device) cudaSetDevice(ctx->device);
+    loop_seen_running = false;
+    bool progressed = expire_leases();
+    std::vector<Entry *> batch;
+    const int64_t prefetch_cap = loop_mode ? std::max(1, grid / 2) : kRingCap / 2;
+    for (int pass = 0; pass < 2; ++pass) {
+        std::deque<Entry *> &q = pass == 0 ? queue : pqueue;
+        if (pass == 1 && !queue.empty()) break;
+        while (!q.empty()) {
+            Entry *e = q.front();
+            if (pass == 1 && inflight_prefetch + int64_t(batch.size()) >= prefetch_cap) break;
+            const bool via_loop = loop_mode && in_loop[ctx->bin_of[e->k]];
+            if (!via_loop && batch_busy) break;
+            if (via_loop && published - (inflight.empty() ? published : inflight.begin()->first) >= kRingCap) break;
+            if (!admit(e)) {
+                if (!(e->prefetch && e->refs == 0)) break;
+                // a prefetch waits for nothing: drop it while the budget is full
+                q.pop_front();
+                stats.prefetch_dropped++;
+                entries.erase(int64_t(e->k) * 16 + e->mask);  // frees e
+                progressed = true;
+                continue;
+            }
+            q.pop_front();
+            progressed = true;
+            if (e->state == St::Failed) {
+                if (e->prefetch && e->refs == 0) entries.erase(int64_t(e->k) * 16 + e->mask);
+                continue;
+            }
+            if (via_loop) publish_loop(e);
+            else {
+                batch.push_back(e);
+                if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
+            }
+        }
+        if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
+    }
+    if (!batch.empty()) launch_batch(batch);
+    const size_t before = inflight.size() + (batch_busy ? batch_entries.size() : 0);
+    if (poll) {
+        if (loop_mode) poll_loop();
+        poll_batch();
+    }
+    const size_t after = inflight.size() + (batch_busy ? batch_entries.size() : 0);
+    if (after != before || progressed) stats.max_batch = std::max<int64_t>(stats.max_batch, int64_t(before));
+    if (const size_t pending = queue.size() + pqueue.size() + after) {
+        int b = 0;
+        while (b < 11 && (size_t(2) << b) <= pending) ++b;
+        stats.depth_hist[b]++;
+    }
+    stats.cache_bytes_used = slab.used;
+    stats.max_prefetch_queue = std::max<int64_t>(stats.max_prefetch_queue, int64_t(pqueue.size()));
+    if (dev_before >= 0 && dev_before != ctx->device) cudaSetDevice(dev_before);
+    return after > 0 || !queue.empty() || !pqueue.empty();
+}
+
 void Serve::leader_loop() {
     cudaSetDevice(ctx->device);
 #ifdef __linux__
-    // the leader sleeps ~10 us between polls while work is in flight (with
+    // the leader sleeps a few us between polls while work is in flight (with
     // the lock released, so requests queue meanwhile); the default 50 us
     // timer slack would stretch every such sleep to ~60 us
     prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
 #endif
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
-        loop_seen_running = false;
-        bool progressed = expire_leases();
-        // admission: requested entries in arrival order, then prefetches while
-        // no request waits and few prefetches occupy the device, so that a
-        // request never queues behind work nobody has asked for yet
-        std::vector<Entry *> batch;
-        const int64_t prefetch_cap = loop_mode ? std::max(1, grid / 2) : kRingCap / 2;
-        for (int pass = 0; pass < 2; ++pass) {
-            std::deque<Entry *> &q = pass == 0 ? queue : pqueue;
-            if (pass == 1 && !queue.empty()) break;
-            while (!q.empty()) {
-                Entry *e = q.front();
-                if (pass == 1 && inflight_prefetch + int64_t(batch.size()) >= prefetch_cap) break;
-                const bool via_loop = loop_mode && in_loop[ctx->bin_of[e->k]];
-                if (!via_loop && batch_busy) break;
-                if (via_loop && published - (inflight.empty() ? published : inflight.begin()->first) >= kRingCap)
-                    break;
-                if (!admit(e)) {
-                    if (!(e->prefetch && e->refs == 0)) break;
-                    // a prefetch waits for nothing: drop it while the budget is pinned
-                    q.pop_front();
-                    stats.prefetch_dropped++;
-                    entries.erase(int64_t(e->k) * 16 + e->mask);  // frees e
-                    progressed = true;
-                    continue;
-                }
-                q.pop_front();
-                progressed = true;
-                if (e->state == St::Failed) {
-                    if (e->prefetch && e->refs == 0) entries.erase(int64_t(e->k) * 16 + e->mask);
-                    continue;
-                }
-                if (via_loop) publish_loop(e);
-                else {
-                    batch.push_back(e);
-                    if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
-                }
-            }
-            if (int(batch.size()) >= (single_mode ? 1 : kRingCap)) break;
-        }
-        if (!batch.empty()) launch_batch(batch);
-        const size_t before = inflight.size() + (batch_busy ? batch_entries.size() : 0);
-        if (loop_mode) poll_loop();
-        poll_batch();
-        const size_t after = inflight.size() + (batch_busy ? batch_entries.size() : 0);
-        if (after != before || progressed) stats.max_batch = std::max<int64_t>(stats.max_batch, int64_t(before));
-        if (const size_t pending = queue.size() + pqueue.size() + after) {
-            int b = 0;
-            while (b < 11 && (size_t(2) << b) <= pending) ++b;
-            stats.depth_hist[b]++;
-        }
-        stats.cache_bytes_used = slab.used;
-        if (after > 0 || !queue.empty() || !pqueue.empty()) {
+        const int64_t pass_t0 = now_ns();
+        const bool busy = pump();
+        last_leader_ns = now_ns();
+        const int64_t hold = last_leader_ns - pass_t0;
+        stats.leader_passes++;
+        stats.leader_hold_ns += hold;
+        stats.max_leader_hold_ns = std::max(stats.max_leader_hold_ns, hold);
+        if (busy) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(2));
             lk.lock();
@@ -706,6 +746,7 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
             if (pit != s->pqueue.end()) s->pqueue.erase(pit);
             e->prefetch = false;
             e->t_queued = gale::now_ns();
+            s->stats.promotions++;
             s->queue.push_back(e);
             s->cv_leader.notify_all();
         }
@@ -751,14 +792,25 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
     }
     e->refs++;
     auto ready = [&] { return e->state == St::Ready || e->state == St::Failed; };
-    if (timeout_ns > 0) {
-        if (!e->cv.wait_until(lk, deadline, ready)) {
+    // between short waits (woken early when another thread completes the
+    // entry), the waiting thread drives the serving state machine itself
+    // whenever the leader thread has not done so lately, and right away the
+    // first time (so that its own entry is admitted and published without a
+    // hand-off):
+    // consumer threads that compute between requests can fill every core
+    constexpr int64_t kLeaderGapNs = 20000;
+    for (bool first = true; !ready(); first = false) {
+        if (first || gale::now_ns() - s->last_leader_ns > kLeaderGapNs) {
+            s->pump();
+            s->stats.requester_pumps++;
+        }
+        if (ready()) break;
+        if (timeout_ns > 0 && std::chrono::steady_clock::now() >= deadline) {
             e->refs--;
             s->stats.t_wait_ns += gale::now_ns() - t0;
             return fail(GALE_ETIMEOUT, "request timed out");
         }
-    } else {
-        e->cv.wait(lk, ready);
+        e->cv.wait_for(lk, std::chrono::microseconds(20));
     }
     if (e->state == St::Failed) {
         const gale_status f = e->fail;

@@ -111,9 +111,21 @@ def test_grid256_full_size():
 
 
 def test_delaunay_2m_full_size():
+    """Besides the whole-output properties and sampled clusters, the largest
+    clusters that still fit shared memory, which share one persistent launch
+    with each cluster under its own plan, are checked in the batched,
+    per-cluster and served forms."""
+    import threading
     m = gen.delaunay_mesh(2_000_000, seed=5, with_field=False)
-    with gale.Context.load(m, device=0) as ctx:
+    with gale.Context.load(m, device=0, cache_budget_bytes=1 << 30) as ctx:
+        bins0 = ctx.bins()
+        pi = [i for i, b in enumerate(bins0) if b["per_item"]]
+        assert pi, bins0
+        members = ctx.bin_members()
+        starts = np.concatenate([[0], np.cumsum([b["clusters"] for b in bins0])])
+        pi_ids = np.concatenate([members[starts[i]:starts[i + 1]] for i in pi])
         ctx.autotune(gale.ALL, reps=1)
+        assert [b["per_item"] for b in ctx.bins()] == [b["per_item"] for b in bins0]
         for _ in range(2):
             ctx.build(None, gale.ALL, gale.MODE_BATCHED)
         ctx.synchronize()
@@ -134,4 +146,35 @@ def test_delaunay_2m_full_size():
         torch.cuda.empty_cache()
         canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
         assert np.array_equal(canon["I_V"], I_V) and np.array_equal(canon["I_T"], I_T)
-        compare_sampled(ctx, canon, sample_clusters(ctx, canon, np.random.default_rng(11), 10))
+        rng = np.random.default_rng(11)
+        compare_sampled(ctx, canon, sample_clusters(ctx, canon, rng, 10))
+        picks = sorted(int(k) for k in rng.choice(pi_ids, 12, replace=False))
+        compare_sampled(ctx, canon, picks)
+        # the same clusters, one launch each, then served by gale_request
+        sub = np.array(picks, np.int32)
+        ctx.build(sub, gale.ALL, gale.MODE_PER_CLUSTER)
+        ctx.synchronize()
+        want = {k: oracle.cluster_relations(canon, k) for k in picks}
+        keys = [("vt_off", "vt_off"), ("vt_val", "vt_val"), ("vv_off", "vv_off"), ("vv_val", "vv_val"),
+                ("et_uoff", "eu_off"), ("et_w", "e_w"), ("et_off", "et_off"), ("et_val", "et_val"),
+                ("tt_off", "tt_off"), ("tt_val", "tt_val")]
+        for i, k in enumerate(picks):
+            got = gale.view_to_numpy(ctx.bulk_view(i))
+            for g, w in keys:
+                assert np.array_equal(got[g].astype(np.int64), want[k][w].astype(np.int64)), (k, g)
+        errors = []
+
+        def consumer(ks):
+            for k in ks:
+                v = ctx.request(k, gale.ALL, timeout_ns=60_000_000_000)
+                got = gale.view_to_numpy(v)
+                ctx.release(v)
+                if not all(np.array_equal(got[g].astype(np.int64), want[k][w].astype(np.int64)) for g, w in keys):
+                    errors.append(k)
+
+        th = [threading.Thread(target=consumer, args=(picks[j::3],)) for j in range(3)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert not errors, errors
