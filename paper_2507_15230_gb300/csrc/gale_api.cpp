@@ -1188,8 +1188,16 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
             if (!bin.spill && plan.total > smem_limit) continue;
             int max_per = gale::max_ctas_per_sm(plan, bin.spill, bin.per_item);
             if (bin.spill) max_per = std::min(max_per, 2);
-            for (int per = 1; per <= max_per; ++per) {
-                const int grid = std::max(1, std::min<int>(nb, per * ctx->sm_count));
+            // persistent grids of 1 .. max_per CTAs per SM; a global-scratch
+            // bin also tries a half and a quarter of the SMs, whose scratch
+            // may stay in L2
+            std::vector<std::pair<int, int>> cands;  // (CTAs per SM, grid)
+            for (int per = 1; per <= max_per; ++per) cands.push_back({per, per * ctx->sm_count});
+            if (bin.spill && max_per >= 1)
+                for (int div : {2, 4}) cands.push_back({1, std::max(1, ctx->sm_count / div)});
+            for (const auto &pc : cands) {
+                const int per = pc.first;
+                const int grid = std::max(1, std::min<int>(nb, pc.second));
                 char *scratch = nullptr;
                 if (bin.spill) {
                     const int64_t need = int64_t(grid) * plan.total;

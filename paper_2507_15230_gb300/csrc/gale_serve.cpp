@@ -37,6 +37,7 @@
 #include <deque>
 #include <list>
 #include <map>
+#include <set>
 #include <memory>
 #include <thread>
 #include <unordered_map>
@@ -88,42 +89,55 @@ struct Pin {
     int64_t deadline;  // steady-clock ns; INT64_MAX without a lease
 };
 
-// first-fit allocator over [0, cap) with a coalescing free list
+// best-fit allocator over [0, cap): free blocks by offset (to coalesce a
+// released block with its neighbours) and by size (to find the smallest
+// block that fits, and whether any does, in logarithmic time)
 struct Slab {
-    std::map<int64_t, int64_t> free;  // offset -> size
+    std::map<int64_t, int64_t> free;             // offset -> size
+    std::set<std::pair<int64_t, int64_t>> by_size;  // (size, offset)
     int64_t cap = 0, used = 0;
     void init(int64_t c) {
         cap = c;
         free.clear();
-        if (c > 0) free[0] = c;
+        by_size.clear();
+        if (c > 0) add(0, c);
         used = 0;
     }
+    void add(int64_t off, int64_t n) {
+        free[off] = n;
+        by_size.insert({n, off});
+    }
+    void drop(std::map<int64_t, int64_t>::iterator it) {
+        by_size.erase({it->second, it->first});
+        free.erase(it);
+    }
+    bool fits(int64_t n) const { return !by_size.empty() && by_size.rbegin()->first >= n; }
     int64_t alloc(int64_t n) {
-        for (auto it = free.begin(); it != free.end(); ++it) {
-            if (it->second < n) continue;
-            const int64_t off = it->first, sz = it->second;
-            free.erase(it);
-            if (sz > n) free[off + n] = sz - n;
-            used += n;
-            return off;
-        }
-        return -1;
+        auto b = by_size.lower_bound({n, INT64_MIN});
+        if (b == by_size.end()) return -1;
+        const int64_t sz = b->first, off = b->second;
+        drop(free.find(off));
+        if (sz > n) add(off + n, sz - n);
+        used += n;
+        return off;
     }
     void release(int64_t off, int64_t n) {
         used -= n;
-        auto it = free.emplace(off, n).first;
-        auto nx = std::next(it);
-        if (nx != free.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free.erase(nx);
+        auto nx = free.lower_bound(off);
+        if (nx != free.end() && off + n == nx->first) {
+            n += nx->second;
+            auto del = nx++;
+            drop(del);
         }
-        if (it != free.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free.erase(it);
+        if (nx != free.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                off = pv->first;
+                n += pv->second;
+                drop(pv);
             }
         }
+        add(off, n);
     }
 };
 
@@ -305,8 +319,7 @@ void Serve::evict_for(int64_t bytes) {
     // evict unpinned ready entries, least recently used first, until a free
     // block of `bytes` exists or nothing more can go
     for (;;) {
-        for (auto &f : slab.free)
-            if (f.second >= bytes) return;
+        if (slab.fits(bytes)) return;
         auto victim = lru.end();
         for (auto it = lru.end(); it != lru.begin();) {
             --it;
