@@ -57,6 +57,13 @@ LOCAL_SINGLE_N = 64      # ... and on one core
 REF_SAMPLE_N = 64
 
 
+def read_bytes(info):
+    """Algorithmic reads of a full build: every owned tet row once (16 B),
+    and for every external and halo tet its index and its gathered row
+    (4 + 16 B).  The writes are the relation arrays themselves."""
+    return 16 * int(info.nt) + 20 * int(info.ext_tets) + 20 * int(info.halo_tets)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -78,25 +85,35 @@ class ClockSampler:
         self.rows = []
         self._stop = threading.Event()
         self._th = None
+        self._proc = None
 
     def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                for line in out.stdout.strip().splitlines():
-                    self.rows.append([c.strip() for c in line.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        for line in self._proc.stdout:
+            row = [c.strip() for c in line.split(",")]
+            if len(row) >= 5 and not self._stop.is_set():
+                self.rows.append(row)
 
     def __enter__(self):
+        # one nvidia-smi process that prints a line every 50 ms
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                           "--format=csv,noheader,nounits", "-lms", "50"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return self
         self._th = threading.Thread(target=self._run, daemon=True)
         self._th.start()
         return self
 
     def __exit__(self, *a):
         self._stop.set()
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
         if self._th:
             self._th.join(timeout=10)
 
@@ -311,9 +328,9 @@ def main():
     ctx.synchronize()
     _, lens = ctx.bulk_arrays()
     out_bytes = 4 * sum(lens.values())
-    in_bytes = int(info.block_bytes)
-    if shard_ids is not None:  # this rank's blocks, in proportion to its tets
-        in_bytes = int(info.block_bytes * my_tets / mesh.nt)
+    in_bytes = read_bytes(info)
+    if shard_ids is not None:  # this rank's working sets, in proportion to its tets
+        in_bytes = int(in_bytes * my_tets / mesh.nt)
     alg_bytes = in_bytes + out_bytes
 
     # timed region: device throughput
@@ -354,13 +371,14 @@ def main():
         ctx.build_export(ids_np, gale.ALL, out=host_np)
     barrier(dist)
     e2e_step_s = []
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        # ids in, every relation array out; chunk copies overlap the build
-        ts = time.perf_counter()
-        ctx.build_export(ids_np, gale.ALL, out=host_np)  # blocks until the copies are done
-        e2e_step_s.append(time.perf_counter() - ts)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    with ClockSampler(local) as clk_e2e:
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            # ids in, every relation array out; chunk copies overlap the build
+            ts = time.perf_counter()
+            ctx.build_export(ids_np, gale.ALL, out=host_np)  # blocks until the copies are done
+            e2e_step_s.append(time.perf_counter() - ts)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_s = max_over_ranks(dist, e2e_s)
     e2e_value = (world * mesh.nt if shard_ids is None else mesh.nt) / e2e_s
 
@@ -444,6 +462,10 @@ def main():
 
     if rank == 0:
         clocks = clk.summary()
+        clocks["e2e_region"] = clk_e2e.summary()
+        clk.rows += clk_e2e.rows
+        both = clk.summary()
+        clocks["both_regions"] = {"sm_mhz": both["sm_mhz"], "samples": both["samples"], "reasons": both["reasons"]}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -639,7 +661,7 @@ def config3_leg(args, gale, gen):
             c.build(None, gale.ALL, gale.MODE_BATCHED)
         c.synchronize()
         _, lens = c.bulk_arrays()
-        alg = int(info.block_bytes) + 4 * sum(lens.values())
+        alg = read_bytes(info) + 4 * sum(lens.values())
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         steps = 20
         a.record(stream)

@@ -79,6 +79,13 @@ typedef struct gale_ctx gale_ctx; /* opaque; one per loaded mesh */
  *   device            CUDA device ordinal; -1 makes a HOST-ONLY context that
  *                     runs the host-side initialisation and nothing else
  *   host_threads      threads for host-side initialisation, 0 = all cores
+ *   part_vertices     a cluster whose working set would not fit one CTA's
+ *                     shared memory (estimated shared memory above cut_bytes)
+ *                     is also cut into parts of about this many own vertices
+ *                     (contiguous canonical ranges); batched builds build the
+ *                     parts, each on its own CTA, straight into the cluster's
+ *                     outputs.  0 = 256; negative = never cut
+ *   cut_bytes         0 = 160 KB
  */
 typedef struct {
     int64_t nv, nt;
@@ -94,6 +101,8 @@ typedef struct {
     void *alloc_ctx;
     int32_t device;
     int32_t host_threads;
+    int32_t part_vertices;
+    int32_t cut_bytes;
 } gale_mesh_desc;
 
 /*
@@ -140,6 +149,8 @@ typedef struct {
     int32_t max_cluster_tets;  /* largest working set (tets) */
     double load_host_seconds;  /* host-side initialisation time */
     double load_device_seconds;/* upload + size pass time */
+    int32_t nparts;            /* parts of the clusters cut for batched builds */
+    int32_t cut_clusters;      /* clusters cut into parts */
 } gale_info;
 
 /* Per-call statistics of the serving path. */
@@ -452,18 +463,23 @@ gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale_coboundary
  * size bin) and CTAs per SM of the persistent grid (0 = as many as fit). */
 gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
 
-/* Size bins of the batched form: for each bin (up to max_bins) seven int32
- * values - clusters, threads per CTA, bytes of per-CTA working memory, CTAs
- * per SM, persistent grid size, 1 if the working memory is global scratch
- * (clusters too large for shared memory) else 0, and 1 if every member runs
- * under its own shared-memory plan (the largest clusters, whose plans do not
- * merge) else 0 - into out[7*i .. 7*i+6].  Returns the number of bins in
- * *nbins. */
+/* Size bins: for each bin (up to max_bins) eight int32 values - members,
+ * threads per CTA, bytes of per-CTA working memory, CTAs per SM, persistent
+ * grid size, 1 if the working memory is global scratch (too large for
+ * shared memory) else 0, 1 if every member runs under its own shared-memory
+ * plan (the largest clusters, whose plans do not merge) else 0, and the
+ * number of members that are parts of cut clusters (gale_mesh_desc
+ * part_vertices), or -1 for a bin of cut clusters themselves, which batched
+ * builds skip (they build the parts) and the per-cluster form, serving and
+ * gale_build_clusters_noalloc use - into out[8*i .. 8*i+7].  Returns the
+ * number of bins in *nbins. */
 gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t *nbins);
 
-/* Members of the size bins: the cluster ids of bin 0, then bin 1, ... (K
- * ids in all; the counts per bin are gale_get_bins' first values), each bin
- * in its launch order (largest working set first).  out: K int32. */
+/* Members of the size bins: the work item ids of bin 0, then bin 1, ...
+ * (K + nparts ids in all, gale_info; the counts per bin are gale_get_bins'
+ * first values), each bin in its launch order (largest working set first).
+ * Ids below K are clusters; id K + p is part p (parts are numbered cluster
+ * by cluster, in vertex order).  out: K + nparts int32. */
 gale_status gale_get_bin_members(gale_ctx *ctx, int32_t *out);
 
 /* Autotune the batched form.  For every size bin, the bin's clusters are

@@ -49,7 +49,7 @@ class MeshDesc(ctypes.Structure):
                 ("seg", ctypes.c_void_p), ("nclusters", ctypes.c_int32), ("precondition_mask", ctypes.c_uint32),
                 ("cache_budget_bytes", ctypes.c_int64), ("stream", ctypes.c_void_p), ("alloc", _ALLOC),
                 ("free", _FREE), ("alloc_ctx", ctypes.c_void_p), ("device", ctypes.c_int32),
-                ("host_threads", ctypes.c_int32)]
+                ("host_threads", ctypes.c_int32), ("part_vertices", ctypes.c_int32), ("cut_bytes", ctypes.c_int32)]
 
 
 class View(ctypes.Structure):
@@ -68,7 +68,8 @@ class Info(ctypes.Structure):
                 ("device", ctypes.c_int32), ("n_edges", ctypes.c_int64), ("total", ctypes.c_int64 * 5),
                 ("block_bytes", ctypes.c_int64), ("ext_tets", ctypes.c_int64), ("halo_tets", ctypes.c_int64),
                 ("nbins", ctypes.c_int32), ("max_cluster_tets", ctypes.c_int32),
-                ("load_host_seconds", ctypes.c_double), ("load_device_seconds", ctypes.c_double)]
+                ("load_host_seconds", ctypes.c_double), ("load_device_seconds", ctypes.c_double),
+                ("nparts", ctypes.c_int32), ("cut_clusters", ctypes.c_int32)]
 
 
 class ServeStats(ctypes.Structure):
@@ -218,10 +219,14 @@ class Context:
     # ---------------- construction ----------------
     @classmethod
     def load(cls, mesh, precondition_mask: int = ALL, device: int = 0, stream=None, cache_budget_bytes: int = 0,
-             host_threads: int = 0, torch_alloc: bool = True) -> "Context":
+             host_threads: int = 0, torch_alloc: bool = True, part_vertices: int = 0,
+             cut_bytes: int = 0) -> "Context":
         """gale_load_mesh.  mesh: anything with tv, seg, nclusters (and
         optionally xyz).  device=-1 makes a host-only context.  stream: a
-        torch.cuda.Stream or raw handle; defaults to torch's current stream."""
+        torch.cuda.Stream or raw handle; defaults to torch's current stream.
+        part_vertices / cut_bytes: how clusters too large for one CTA are cut
+        into parts for batched builds (0 = defaults, part_vertices < 0 =
+        never)."""
         lib = load_library()
         tv = np.ascontiguousarray(mesh.tv, dtype=np.int32).reshape(-1, 4)
         seg = np.ascontiguousarray(mesh.seg, dtype=np.int32)
@@ -236,6 +241,8 @@ class Context:
         d.cache_budget_bytes = cache_budget_bytes
         d.device = device
         d.host_threads = host_threads
+        d.part_vertices = part_vertices
+        d.cut_bytes = cut_bytes
         keep = [tv, seg, xyz]
         if device >= 0:
             import torch
@@ -423,21 +430,25 @@ class Context:
         return ext[:ne.value], halo[:nh.value]
 
     def bins(self) -> list:
-        """Size bins: clusters, threads, working bytes per CTA, CTAs per SM,
+        """Size bins: members, threads, working bytes per CTA, CTAs per SM,
         grid, spill (1: working memory in global scratch), per_item (1: each
-        member runs under its own plan)."""
+        member runs under its own plan), parts (members that are parts of cut
+        clusters; -1: a bin of the cut clusters themselves, which batched
+        builds skip)."""
         n = ctypes.c_int32(0)
         _check(self._lib.gale_get_bins(self._h, None, 0, ctypes.byref(n)))
-        out = np.zeros(7 * max(n.value, 1), np.int32)
+        out = np.zeros(8 * max(n.value, 1), np.int32)
         _check(self._lib.gale_get_bins(self._h, _p(out), n.value, ctypes.byref(n)))
-        keys = ("clusters", "threads", "bytes", "ctas_per_sm", "grid", "spill", "per_item")
-        return [dict(zip(keys, out[7 * i:7 * i + 7].tolist())) for i in range(n.value)]
+        keys = ("clusters", "threads", "bytes", "ctas_per_sm", "grid", "spill", "per_item", "parts")
+        return [dict(zip(keys, out[8 * i:8 * i + 8].tolist())) for i in range(n.value)]
 
     def bin_members(self) -> np.ndarray:
-        """Cluster ids of bin 0, bin 1, ... in launch order (K ids)."""
-        out = np.empty(max(self.K, 1), np.int32)
+        """Work item ids of bin 0, bin 1, ... in launch order: clusters
+        (ids below K), then parts of cut clusters (id K + p)."""
+        n = self.K + int(self.info().nparts)
+        out = np.empty(max(n, 1), np.int32)
         _check(self._lib.gale_get_bin_members(self._h, _p(out)))
-        return out[:self.K]
+        return out[:n]
 
     def enumerate(self, order: int = 0) -> dict:
         """gale_enumerate + gale_get_enumeration: E (nE x 2), F (nF x 3),

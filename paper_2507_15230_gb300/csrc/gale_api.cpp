@@ -51,31 +51,6 @@ int64_t next_pow2(int64_t x) {
     return p;
 }
 
-// Capacities of one cluster; staging capacities come from the exact sizes
-// of the counting pass (sizes == nullptr: a counting plan, no staging).
-gale::Caps caps_of(const gale::ClusterStat &s, const int64_t *sizes) {
-    gale::Caps c{};
-    c.blk_words = int32_t(gale::blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo, s.n_bnd));
-    c.nv_own = s.nv_own;
-    c.n_vt = s.n_vt;
-    c.n_own = s.n_own;
-    c.nv_loc = s.nv_loc;
-    c.nv_nb = s.nv_nb;
-    c.max_deg = s.max_deg;
-    c.max_up = s.max_up;
-    c.max_e = s.n_e;
-    if (sizes) {
-        c.max_vv = int32_t(sizes[1]);
-        c.max_e = int32_t(sizes[2]);
-        c.max_etv = int32_t(sizes[3]);
-        c.max_tt = int32_t(sizes[4]);
-    }
-    c.hcap = int32_t(std::max<int64_t>(64, next_pow2(2 * int64_t(s.n_bnd) + 1)));
-    c.n_tot = s.n_ext + s.n_own + s.n_halo;
-    c.n_star = s.n_ext + s.n_own;
-    return c;
-}
-
 gale::Caps merge(const gale::Caps &a, const gale::Caps &b) {
     gale::Caps c{};
     c.blk_words = std::max(a.blk_words, b.blk_words);
@@ -107,12 +82,15 @@ int threads_for(const gale_ctx *ctx, const gale::ClusterStat &s) {
     return t;
 }
 
-// Size bins: clusters sorted by shared-memory need, cut where the merged
-// plan would cross the next occupancy tier (4, 3, 2, 1 CTAs per SM).
-// Clusters whose plan exceeds the shared memory of one CTA go to spill bins:
-// the same kernel with its regions in a per-CTA slice of global scratch.
+// Size bins: work items (clusters, then the parts of cut clusters) sorted by
+// shared-memory need, cut where the merged plan would cross the next
+// occupancy tier (4, 3, 2, 1 CTAs per SM).  Items whose plan exceeds the
+// shared memory of one CTA go to spill bins: the same kernel with its
+// regions in a per-CTA slice of global scratch.  Cut clusters get bins of
+// their own, which batched builds skip (they run the parts).
 gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     const int32_t K = ctx->hm.K;
+    const int32_t NI = K + ctx->hm.NP;
     // dynamic shared memory a CTA may plan for: the opt-in limit less the
     // kernels' static shared memory
     constexpr int kStaticMargin = 512;
@@ -120,31 +98,33 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
     auto caps_k = [&](int32_t k) {
-        return caps_of(ctx->hm.stats[k], with_sizes ? ctx->sizes.data() + size_t(5) * k : nullptr);
+        return gale::caps_of(ctx->hm.stats[k], with_sizes ? ctx->sizes.data() + size_t(5) * k : nullptr);
     };
-    std::vector<int32_t> need(K), thr(K);
-    std::vector<uint8_t> big(K);
-    for (int32_t k = 0; k < K; ++k) {
+    std::vector<int32_t> need(NI), thr(NI);
+    std::vector<uint8_t> big(NI), cut(NI, 0);
+    for (int32_t k = 0; k < NI; ++k) {
         if (ctx->hm.stats[k].max_up > 255)
-            return fail(GALE_EINVAL, "cluster " + std::to_string(k) +
+            return fail(GALE_EINVAL, "cluster " + std::to_string(k < K ? k : ctx->hm.parts[k - K].k) +
                                          " has a vertex with more than 255 upper neighbours (unsupported)");
         thr[k] = threads_for(ctx, ctx->hm.stats[k]);
         need[k] = gale::plan_smem(caps_k(k), thr[k]).total;
         big[k] = need[k] > smem_cta;
+        if (k < K) cut[k] = ctx->hm.part_first[k + 1] > ctx->hm.part_first[k];
     }
-    std::vector<int32_t> idx(K);
+    std::vector<int32_t> idx(NI);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+        if (cut[a] != cut[b]) return cut[a] < cut[b];
         if (big[a] != big[b]) return big[a] < big[b];
         return thr[a] != thr[b] ? thr[a] < thr[b] : need[a] < need[b];
     });
     std::vector<int> tiers;
     for (int per = 4; per >= 1; --per) tiers.push_back(std::min(smem_sm / per - 1024 - kStaticMargin, smem_cta));
     ctx->bins.clear();
-    ctx->bin_of.assign(K, -1);
+    ctx->bin_of.assign(NI, -1);
     size_t tier = 0;
     int cur_thr = 0;
-    bool cur_big = false;
+    bool cur_big = false, cur_cut = false;
     gale::Caps cur{};
     std::vector<int32_t> members;
     auto close = [&]() {
@@ -152,6 +132,7 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         gale::Bin b;
         b.plan = gale::plan_smem(cur, cur_thr);
         b.spill = cur_big;
+        b.cut = cur_cut;
         std::stable_sort(members.begin(), members.end(),
                          [&](int32_t a, int32_t c) { return need[a] > need[c]; });  // largest first
         b.clusters = members;
@@ -161,12 +142,13 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         cur = gale::Caps{};
     };
     for (int32_t k : idx) {
-        if (!members.empty() && (thr[k] != cur_thr || bool(big[k]) != cur_big)) {
+        if (!members.empty() && (thr[k] != cur_thr || bool(big[k]) != cur_big || bool(cut[k]) != cur_cut)) {
             close();
             tier = 0;
         }
         cur_thr = thr[k];
         cur_big = big[k];
+        cur_cut = cut[k];
         gale::Caps m = members.empty() ? caps_k(k) : merge(cur, caps_k(k));
         if (!cur_big) {
             int tot = gale::plan_smem(m, cur_thr).total;
@@ -192,19 +174,22 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     // after another.  They become one bin per block size whose members each
     // keep their own plan (one persistent launch, the largest member's
     // shared memory).
-    ctx->h_plans.assign(size_t(K), gale::SmemPlan{});
+    ctx->h_plans.assign(size_t(NI), gale::SmemPlan{});
     {
-        std::map<int, int> ntop;  // block size -> bins of the top tier
+        // (block size, bin of cut clusters) -> bins of the top tier
+        using Key = std::pair<int, bool>;
+        std::map<Key, int> ntop;
         for (auto &b : ctx->bins)
-            if (!b.spill && b.plan.total > tiers[2]) ntop[b.plan.threads]++;
+            if (!b.spill && b.plan.total > tiers[2]) ntop[Key(b.plan.threads, b.cut)]++;
         std::vector<gale::Bin> kept;
-        std::map<int, gale::Bin> top;  // block size -> merged bin
+        std::map<Key, gale::Bin> top;  // merged bins
         for (auto &b : ctx->bins) {
-            if (b.spill || b.plan.total <= tiers[2] || ntop[b.plan.threads] < 2) {
+            if (b.spill || b.plan.total <= tiers[2] || ntop[Key(b.plan.threads, b.cut)] < 2) {
                 kept.push_back(std::move(b));
                 continue;
             }
-            gale::Bin &t = top[b.plan.threads];
+            gale::Bin &t = top[Key(b.plan.threads, b.cut)];
+            t.cut = b.cut;
             const bool first = t.clusters.empty();
             for (int32_t k : b.clusters) {
                 ctx->h_plans[k] = gale::plan_smem(caps_k(k), b.plan.threads);
@@ -226,13 +211,16 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
             for (int32_t k : ctx->bins[b].clusters) ctx->bin_of[k] = int32_t(b);
     }
     if (!ctx->d_plans) {
-        ctx->d_plans = static_cast<gale::SmemPlan *>(ctx->dalloc(sizeof(gale::SmemPlan) * size_t(std::max(K, 1))));
+        ctx->d_plans = static_cast<gale::SmemPlan *>(ctx->dalloc(sizeof(gale::SmemPlan) * size_t(std::max(NI, 1))));
         if (!ctx->d_plans) return fail(GALE_ENOMEM, "device allocation of the per-cluster plans failed");
     }
-    if (K > 0 &&
-        cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * size_t(K), cudaMemcpyHostToDevice) !=
+    if (NI > 0 &&
+        cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * size_t(NI), cudaMemcpyHostToDevice) !=
             cudaSuccess)
         return fail(GALE_ECUDA, "uploading the per-cluster plans failed");
+    if (int(ctx->bins.size()) > gale::kMaxBins)
+        return fail(GALE_EINVAL, "the working sets fall into more than " + std::to_string(gale::kMaxBins) +
+                                     " size bins; use more even clusters");
     int max_total = 0;
     for (auto &b : ctx->bins)
         if (!b.spill) max_total = std::max(max_total, b.plan.total);
@@ -264,7 +252,7 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
 char *scratch_of(gale_ctx *ctx, const gale::Bin &b) { return b.spill ? ctx->d_spill : nullptr; }
 // build capacities of cluster k (its exact sizes known)
 gale::Caps bin_caps(const gale_ctx *ctx, int32_t k) {
-    return caps_of(ctx->hm.stats[k], ctx->sizes.data() + size_t(5) * k);
+    return gale::caps_of(ctx->hm.stats[k], ctx->sizes.data() + size_t(5) * k);
 }
 const gale::SmemPlan *plans_of(gale_ctx *ctx, const gale::Bin &b) { return b.per_item ? ctx->d_plans : nullptr; }
 
@@ -294,7 +282,8 @@ SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop, st
         const Bin &bin = ctx->bins[b];
         if (bin.spill) continue;
         int top = 0;
-        for (int32_t k : bin.clusters) top = std::max(top, plan_smem(bin_caps(ctx, k), threads).total);
+        for (int32_t k : bin.clusters)
+            if (k < K) top = std::max(top, plan_smem(bin_caps(ctx, k), threads).total);
         if (top > limit) continue;
         SmemPlan probe = env;
         probe.total = std::max(env.total, top);
@@ -303,7 +292,8 @@ SmemPlan serve_plan(gale_ctx *ctx, bool *fits, std::vector<uint8_t> *in_loop, st
         sel[b] = 1;
         any = true;
         if (own)
-            for (int32_t k : bin.clusters) (*own)[k] = plan_smem(bin_caps(ctx, k), threads);
+            for (int32_t k : bin.clusters)
+                if (k < K) (*own)[k] = plan_smem(bin_caps(ctx, k), threads);
     }
     *fits = any;
     if (in_loop) *in_loop = sel;
@@ -330,19 +320,46 @@ void item_lengths(const gale_ctx *ctx, int32_t k, uint32_t mask, int64_t *L) {
 
 namespace {
 
+// Per bin, its members' item ids (the counting pass) and their positions in
+// the full build's item list (batched full builds; -1 for cut clusters,
+// whose bins those builds skip).
 gale_status upload_orders(gale_ctx *ctx) {
-    std::vector<int32_t> order;  // positions in the all-clusters item list (= cluster ids)
+    std::vector<int32_t> ids, pos;
     ctx->order_all_off.assign(1, 0);
     for (auto &b : ctx->bins) {
-        order.insert(order.end(), b.clusters.begin(), b.clusters.end());
-        ctx->order_all_off.push_back(int64_t(order.size()));
+        for (int32_t k : b.clusters) {
+            ids.push_back(k);
+            pos.push_back(ctx->pos_all[k]);
+        }
+        ctx->order_all_off.push_back(int64_t(ids.size()));
     }
-    CUDA_TRY(cudaMemcpyAsync(ctx->d_order_all, order.data(), order.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_order_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_order_all, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));  // the host vectors go out of scope
     return GALE_OK;
 }
 
 gale::DevMesh dev_mesh(gale_ctx *ctx) {
-    return gale::DevMesh{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
+    gale::DevMesh m{ctx->d_blocks, ctx->d_blk_off, ctx->d_I_V, ctx->d_I_T, ctx->hm.K};
+    m.NP = ctx->hm.NP;
+    m.parts = ctx->d_parts;
+    m.tt_pos = ctx->d_tt_pos;
+    return m;
+}
+
+// The item list of a batched build of the listed clusters: every cut
+// cluster replaced by its parts, in order.
+std::vector<int32_t> expand_items(const gale_ctx *ctx, const std::vector<int32_t> &list) {
+    if (ctx->hm.NP == 0) return list;
+    std::vector<int32_t> out;
+    out.reserve(list.size());
+    const int32_t K = ctx->hm.K;
+    for (int32_t k : list) {
+        const int32_t p0 = ctx->hm.part_first[k], p1 = ctx->hm.part_first[k + 1];
+        if (p1 == p0) out.push_back(k);
+        for (int32_t p = p0; p < p1; ++p) out.push_back(K + p);
+    }
+    return out;
 }
 
 gale_status check_device_error(gale_ctx *ctx) {
@@ -362,11 +379,11 @@ gale_status check_device_error(gale_ctx *ctx) {
 }
 
 gale_status count_pass(gale_ctx *ctx) {
-    const int32_t K = ctx->hm.K;
-    CUDA_TRY(cudaMemsetAsync(ctx->d_sizes, 0, sizeof(int64_t) * 5 * K, ctx->stream));
+    const int32_t K = ctx->hm.K, NP = ctx->hm.NP, NI = K + NP;
+    CUDA_TRY(cudaMemsetAsync(ctx->d_sizes, 0, sizeof(int64_t) * 5 * NI, ctx->stream));
     for (size_t b = 0; b < ctx->bins.size(); ++b) {
         const gale::Bin &bin = ctx->bins[b];
-        int rc = gale::launch_count_pass(dev_mesh(ctx), bin.plan, ctx->d_order_all + ctx->order_all_off[b],
+        int rc = gale::launch_count_pass(dev_mesh(ctx), bin.plan, ctx->d_order_ids + ctx->order_all_off[b],
                                          int32_t(bin.clusters.size()), ctx->d_sizes, ctx->d_err,
                                          ctx->d_tickets + b, bin.grid, ctx->stream, scratch_of(ctx, bin),
                                          ctx->precond, plans_of(ctx, bin));
@@ -374,43 +391,96 @@ gale_status count_pass(gale_ctx *ctx) {
     }
     gale_status st = check_device_error(ctx);
     if (st != GALE_OK) return st;
-    ctx->sizes.resize(size_t(5) * K);
-    CUDA_TRY(cudaMemcpyAsync(ctx->sizes.data(), ctx->d_sizes, sizeof(int64_t) * 5 * K, cudaMemcpyDeviceToHost,
+    ctx->sizes.resize(size_t(5) * NI);
+    CUDA_TRY(cudaMemcpyAsync(ctx->sizes.data(), ctx->d_sizes, sizeof(int64_t) * 5 * NI, cudaMemcpyDeviceToHost,
                              ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     for (int a = 0; a < 5; ++a) ctx->totals[a] = 0;
     for (int32_t k = 0; k < K; ++k)
         for (int a = 0; a < 5; ++a) ctx->totals[a] += ctx->sizes[size_t(5) * k + a];
+    if (NP == 0) return GALE_OK;
+    // Parts: the cluster-level values at each part's start, checked against
+    // the cluster's own count; the TT row offsets of every internal tet of a
+    // cut cluster from the row lengths the parts counted.
+    auto &hm = ctx->hm;
+    const bool tt = (ctx->precond & GALE_TT) != 0;
+    std::vector<int32_t> len;
+    if (tt) {
+        len.resize(size_t(hm.nt));
+        CUDA_TRY(cudaMemcpy(len.data(), ctx->d_tt_pos, sizeof(int32_t) * size_t(hm.nt), cudaMemcpyDeviceToHost));
+    }
+    for (int32_t k = 0; k < K; ++k) {
+        const int32_t p0 = hm.part_first[k], p1 = hm.part_first[k + 1];
+        if (p1 == p0) continue;
+        int64_t run[5] = {}, rows = 0;
+        for (int32_t p = p0; p < p1; ++p) {
+            gale::PartInfo &pi = hm.parts[p];
+            const int64_t *sz = ctx->sizes.data() + size_t(5) * (K + p);
+            pi.b_vt = int32_t(run[0]);
+            pi.b_vv = int32_t(run[1]);
+            pi.b_e = int32_t(run[2]);
+            pi.b_et = int32_t(run[3]);
+            pi.b_tt = int32_t(run[4]);
+            pi.b_to = int32_t(rows);
+            for (int a = 0; a < 5; ++a) run[a] += sz[a];
+            rows += pi.n_rows;
+            pi.tt_total = int32_t(ctx->sizes[size_t(5) * k + 4]);
+        }
+        for (int a = 0; a < 5; ++a)
+            if (run[a] != ctx->sizes[size_t(5) * k + a] && (a < 4 || tt))
+                return fail(GALE_EDEVICE, "the parts of cluster " + std::to_string(k) +
+                                              " disagree with the cluster's own sizes");
+        if (rows != hm.I_T[k + 1] - hm.I_T[k])
+            return fail(GALE_EDEVICE, "the parts of cluster " + std::to_string(k) + " miss internal tets");
+        if (tt) {
+            int64_t pos = 0;
+            for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t) {
+                const int32_t l = len[t];
+                if (l < 0 || l > 4) return fail(GALE_EDEVICE, "a part reported a bad TT row length");
+                len[t] = int32_t(pos);
+                pos += l;
+            }
+            if (pos != ctx->sizes[size_t(5) * k + 4])
+                return fail(GALE_EDEVICE, "the parts of cluster " + std::to_string(k) + " disagree on TT");
+        }
+    }
+    if (tt)
+        CUDA_TRY(cudaMemcpy(ctx->d_tt_pos, len.data(), sizeof(int32_t) * size_t(hm.nt), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(ctx->d_parts, hm.parts.data(), sizeof(gale::PartInfo) * size_t(NP), cudaMemcpyHostToDevice));
     return GALE_OK;
 }
 
 
-// Launch order of listed clusters, chunk by chunk and, within a chunk, bin by
-// bin, each bin's members in the bin's largest-first order: the positions of
-// chunk c's members relative to cut[c], in order[boff[c][b] .. boff[c][b+1]).
-// One pass over the bins' member lists, no sorting (list positions are
-// pos_of[k], or k itself when the list is every cluster in id order).
-// False if some listed cluster is in no bin.
+// Launch order of listed items (clusters, and the parts that stand for cut
+// clusters), chunk by chunk and, within a chunk, bin by bin, each bin's
+// members in the bin's largest-first order: the positions of chunk c's
+// members relative to cut[c], in order[boff[c][b] .. boff[c][b+1]).  Bins of
+// cut clusters get no entries.  One pass over the bins' member lists, no
+// sorting (list positions are pos_of[k], or pos_all[k] when the list is the
+// full build's).  False if some listed item is in no bin.
 bool chunk_bin_orders(const gale_ctx *ctx, const std::vector<int32_t> &list, bool all,
                       const std::vector<int32_t> &cut, std::vector<int32_t> &order,
                       std::vector<std::vector<int64_t>> &boff) {
-    const int32_t K = ctx->hm.K, cnt = int32_t(list.size());
+    const int32_t NI = ctx->hm.K + ctx->hm.NP, cnt = int32_t(list.size());
     const int32_t chunks = int32_t(cut.size()) - 1;
     const size_t nb = ctx->bins.size();
-    std::vector<int32_t> pos_of;
+    std::vector<int32_t> own_pos;
     if (!all) {
-        pos_of.assign(K, -1);
-        for (int32_t i = 0; i < cnt; ++i) pos_of[list[i]] = i;
+        own_pos.assign(NI, -1);
+        for (int32_t i = 0; i < cnt; ++i) own_pos[list[i]] = i;
     }
+    const std::vector<int32_t> &pos_of = all ? ctx->pos_all : own_pos;
     std::vector<int32_t> chunk_of(cnt);
     for (int32_t c = 0; c < chunks; ++c)
         for (int32_t i = cut[c]; i < cut[c + 1]; ++i) chunk_of[i] = c;
     std::vector<int64_t> count(size_t(chunks) * nb, 0);
-    for (size_t b = 0; b < nb; ++b)
+    for (size_t b = 0; b < nb; ++b) {
+        if (ctx->bins[b].cut) continue;
         for (int32_t k : ctx->bins[b].clusters) {
-            const int32_t p = all ? k : pos_of[k];
+            const int32_t p = pos_of[k];
             if (p >= 0 && p < cnt) count[size_t(chunk_of[p]) * nb + b]++;
         }
+    }
     boff.assign(chunks, std::vector<int64_t>(nb + 1, 0));
     std::vector<int64_t> fill(size_t(chunks) * nb);
     int64_t run = 0;
@@ -423,13 +493,15 @@ bool chunk_bin_orders(const gale_ctx *ctx, const std::vector<int32_t> &list, boo
         boff[c][nb] = run;
     }
     order.assign(size_t(run), 0);
-    for (size_t b = 0; b < nb; ++b)
+    for (size_t b = 0; b < nb; ++b) {
+        if (ctx->bins[b].cut) continue;
         for (int32_t k : ctx->bins[b].clusters) {
-            const int32_t p = all ? k : pos_of[k];
+            const int32_t p = pos_of[k];
             if (p < 0 || p >= cnt) continue;
             const int32_t c = chunk_of[p];
             order[size_t(fill[size_t(c) * nb + b]++)] = p - cut[c];
         }
+    }
     return run == cnt;
 }
 
@@ -673,30 +745,56 @@ gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out) {
     ctx->sm_count = gale::device_sm_count();
     const int32_t K = ctx->hm.K;
     auto &hm = ctx->hm;
+    const int32_t NP = hm.NP, NI = K + NP;  // work items: clusters, then parts
+    // the full build's item list: cut clusters replaced by their parts
+    {
+        std::vector<int32_t> all(K);
+        std::iota(all.begin(), all.end(), 0);
+        ctx->all_items = expand_items(ctx.get(), all);
+        ctx->pos_all.assign(NI, -1);
+        for (size_t i = 0; i < ctx->all_items.size(); ++i) ctx->pos_all[ctx->all_items[i]] = int32_t(i);
+    }
     ctx->d_blocks = static_cast<int32_t *>(ctx->dalloc(size_t(hm.blocks_words) * 4));
-    ctx->d_blk_off = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * (K + 1)));
+    ctx->d_blk_off = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * (NI + 1)));
     ctx->d_I_V = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * (K + 1)));
     ctx->d_I_T = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * (K + 1)));
-    ctx->d_sizes = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * 5 * K));
+    ctx->d_sizes = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * 5 * NI));
     ctx->d_err = static_cast<int32_t *>(ctx->dalloc(64));
-    ctx->d_tickets = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * 64));
-    ctx->d_ids = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * K));
-    ctx->d_order_all = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * K));
-    ctx->d_order_part = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * K));
-    ctx->d_items = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * K));
+    ctx->d_tickets = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * gale::kMaxBins));
+    ctx->d_ids = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * NI));
+    ctx->d_order_all = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * NI));
+    ctx->d_order_ids = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * NI));
+    ctx->d_order_part = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * NI));
+    ctx->d_items = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * NI));
     ctx->d_arrays_base = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * 16));
     ctx->d_totals = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * 16));
-    ctx->d_bsum = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * (gale::bases_scratch_words(K) + 16)));
+    ctx->d_bsum = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * (gale::bases_scratch_words(NI) + 16)));
+    if (NP > 0) {
+        ctx->d_parts = static_cast<gale::PartInfo *>(ctx->dalloc(sizeof(gale::PartInfo) * NP));
+        ctx->d_tt_pos = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * std::max<int64_t>(1, hm.nt)));
+        ctx->d_all_items = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * ctx->all_items.size()));
+    }
     if (!ctx->d_blocks || !ctx->d_blk_off || !ctx->d_I_V || !ctx->d_I_T || !ctx->d_sizes || !ctx->d_err ||
-        !ctx->d_tickets || !ctx->d_ids || !ctx->d_order_all || !ctx->d_order_part || !ctx->d_items ||
-        !ctx->d_arrays_base || !ctx->d_totals || !ctx->d_bsum) {
+        !ctx->d_tickets || !ctx->d_ids || !ctx->d_order_all || !ctx->d_order_ids || !ctx->d_order_part ||
+        !ctx->d_items || !ctx->d_arrays_base || !ctx->d_totals || !ctx->d_bsum ||
+        (NP > 0 && (!ctx->d_parts || !ctx->d_tt_pos || !ctx->d_all_items))) {
         gale_destroy(ctx.release());
         return fail(GALE_ENOMEM, "device allocation failed while loading the mesh");
     }
     CUDA_TRY(cudaMemcpyAsync(ctx->d_blocks, hm.blocks, size_t(hm.blocks_words) * 4, cudaMemcpyHostToDevice,
                              ctx->stream));
-    CUDA_TRY(cudaMemcpyAsync(ctx->d_blk_off, hm.blk_off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice,
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_blk_off, hm.blk_off.data(), sizeof(int64_t) * (NI + 1), cudaMemcpyHostToDevice,
                              ctx->stream));
+    if (NP > 0) {
+        // part records without the counted offsets (the counting pass reads
+        // none of them), the full build's item list, and TT row lengths
+        // marked unset
+        CUDA_TRY(cudaMemcpyAsync(ctx->d_parts, hm.parts.data(), sizeof(gale::PartInfo) * NP, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+        CUDA_TRY(cudaMemcpyAsync(ctx->d_all_items, ctx->all_items.data(), 4 * ctx->all_items.size(),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+        CUDA_TRY(cudaMemsetAsync(ctx->d_tt_pos, 0xff, sizeof(int32_t) * std::max<int64_t>(1, hm.nt), ctx->stream));
+    }
     CUDA_TRY(cudaMemcpyAsync(ctx->d_I_V, hm.I_V.data(), sizeof(int32_t) * (K + 1), cudaMemcpyHostToDevice,
                              ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->d_I_T, hm.I_T.data(), sizeof(int32_t) * (K + 1), cudaMemcpyHostToDevice,
@@ -768,10 +866,12 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
         if (!g) {
             cudaGraph_t graph;
             CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            int rc = gale::launch_bases(dm, nullptr, K, ctx->d_sizes, mask, base, ctx->d_items, ctx->d_totals,
-                                        ctx->d_bsum, ctx->stream);
+            int rc = gale::launch_bases(dm, ctx->hm.NP ? ctx->d_all_items : nullptr, int32_t(ctx->all_items.size()),
+                                        ctx->d_sizes, mask, base, ctx->d_items, ctx->d_totals, ctx->d_bsum,
+                                        ctx->stream);
             for (size_t b = 0; rc == 0 && b < ctx->bins.size(); ++b) {
                 const gale::Bin &bin = ctx->bins[b];
+                if (bin.cut) continue;  // its clusters' parts are in other bins
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b],
                                         int32_t(bin.clusters.size()), ctx->d_err, ctx->d_tickets + b, bin.grid,
                                         ctx->stream, scratch_of(ctx, bin), plans_of(ctx, bin));
@@ -787,14 +887,18 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
             }
         }
         CUDA_TRY(cudaGraphLaunch(g, ctx->stream));
-        launches = 3 + int64_t(ctx->bins.size());
+        launches = 3;
+        for (const auto &bin : ctx->bins) launches += !bin.cut;
     } else {
+        // a partial batched build lists the parts of cut clusters in their place
+        const std::vector<int32_t> items = mode == GALE_MODE_BATCHED ? expand_items(ctx, list) : list;
+        const int32_t ni = int32_t(items.size());
         const int32_t *d_ids = nullptr;
-        if (!all) {
-            CUDA_TRY(cudaMemcpyAsync(ctx->d_ids, list.data(), size_t(cnt) * 4, cudaMemcpyHostToDevice, ctx->stream));
+        if (!all || ctx->hm.NP) {
+            CUDA_TRY(cudaMemcpyAsync(ctx->d_ids, items.data(), size_t(ni) * 4, cudaMemcpyHostToDevice, ctx->stream));
             d_ids = ctx->d_ids;
         }
-        int rc = gale::launch_bases(dm, d_ids, cnt, ctx->d_sizes, mask, base, ctx->d_items, ctx->d_totals,
+        int rc = gale::launch_bases(dm, d_ids, ni, ctx->d_sizes, mask, base, ctx->d_items, ctx->d_totals,
                                     ctx->d_bsum, ctx->stream);
         if (rc != 0) return cuda_fail(cudaError_t(rc), "bases launch");
         launches = 3;
@@ -810,7 +914,7 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
             // partial batched build: per-bin item orders
             std::vector<int32_t> order;
             std::vector<std::vector<int64_t>> boff;
-            if (!chunk_bin_orders(ctx, list, false, {0, cnt}, order, boff))
+            if (!chunk_bin_orders(ctx, items, false, {0, ni}, order, boff))
                 return fail(GALE_EINVAL, "a listed cluster is in no size bin");
             const std::vector<int64_t> &off = boff[0];
             CUDA_TRY(cudaMemcpyAsync(ctx->d_order_part, order.data(), order.size() * 4, cudaMemcpyHostToDevice,
@@ -969,11 +1073,24 @@ gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint
         if (!ctx->d_chunk_base) return fail(GALE_ENOMEM, "device allocation failed");
     }
     // per chunk: base pointers shifted to the chunk's first element, and the
-    // chunk's items grouped by size bin (largest working set first)
+    // chunk's items (cut clusters replaced by their parts) grouped by size
+    // bin (largest working set first)
     std::vector<WorkItem> cbase(chunks);
     std::vector<int32_t> order;
     std::vector<std::vector<int64_t>> boff;
-    if (!chunk_bin_orders(ctx, list, all, cut, order, boff))
+    std::vector<int32_t> items = expand_items(ctx, list);
+    std::vector<int32_t> icut(cut);  // chunk boundaries in the item list
+    if (ctx->hm.NP) {
+        std::vector<int32_t> first(size_t(cnt) + 1, 0);  // item position of each listed cluster
+        for (int32_t i = 0; i < cnt; ++i) {
+            const int32_t k = list[i];
+            const int32_t np = ctx->hm.part_first[k + 1] - ctx->hm.part_first[k];
+            first[i + 1] = first[i] + std::max(np, 1);
+        }
+        for (auto &c : icut) c = first[c];
+    }
+    const int32_t ni = int32_t(items.size());
+    if (!chunk_bin_orders(ctx, items, all && ctx->hm.NP == 0, icut, order, boff))
         return fail(GALE_EINVAL, "a listed cluster is in no size bin");
     for (int32_t c = 0; c < chunks; ++c) {
         const int32_t i0 = cut[c];
@@ -988,24 +1105,25 @@ gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint
         w.eu_off = ptr[4]; w.e_w = ptr[5]; w.et_off = ptr[6]; w.et_val = ptr[7];
         w.tt_off = ptr[8]; w.tt_val = ptr[9];
     }
-    CUDA_TRY(cudaMemcpyAsync(ctx->d_ids, list.data(), size_t(cnt) * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_ids, items.data(), size_t(ni) * 4, cudaMemcpyHostToDevice, ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->d_order_part, order.data(), order.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->d_chunk_base, cbase.data(), sizeof(WorkItem) * chunks, cudaMemcpyHostToDevice,
                              ctx->stream));
     const gale::DevMesh dm = dev_mesh(ctx);
     int64_t launches = 0;
     for (int32_t c = 0; c < chunks; ++c) {
-        const int32_t i0 = cut[c], nc = cut[c + 1] - i0;
+        const int32_t i0 = cut[c];
+        const int32_t j0 = icut[c], nc = icut[c + 1] - j0;
         if (nc > 0) {
-            int rc = gale::launch_bases(dm, ctx->d_ids + i0, nc, ctx->d_sizes, mask, ctx->d_chunk_base + c,
-                                        ctx->d_items + i0, ctx->d_totals, ctx->d_bsum, ctx->stream);
+            int rc = gale::launch_bases(dm, ctx->d_ids + j0, nc, ctx->d_sizes, mask, ctx->d_chunk_base + c,
+                                        ctx->d_items + j0, ctx->d_totals, ctx->d_bsum, ctx->stream);
             if (rc != 0) return cuda_fail(cudaError_t(rc), "bases launch");
             launches += 3;
             for (size_t b = 0; b < ctx->bins.size(); ++b) {
                 const int32_t nb = int32_t(boff[c][b + 1] - boff[c][b]);
                 if (nb == 0) continue;
                 const gale::Bin &bin = ctx->bins[b];
-                rc = gale::launch_build(dm, bin.plan, ctx->d_items + i0, ctx->d_order_part + boff[c][b], nb,
+                rc = gale::launch_build(dm, bin.plan, ctx->d_items + j0, ctx->d_order_part + boff[c][b], nb,
                                         ctx->d_err, ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream,
                                         scratch_of(ctx, bin), plans_of(ctx, bin));
                 if (rc != 0) return cuda_fail(cudaError_t(rc), "batched launch");
@@ -1089,10 +1207,17 @@ gale_status gale_get_info(gale_ctx *ctx, gale_info *out) {
     out->halo_tets = ctx->hm.halo_total;
     out->nbins = int32_t(ctx->bins.size());
     int32_t mx = 0;
-    for (auto &s : ctx->hm.stats) mx = std::max(mx, s.n_ext + s.n_own + s.n_halo);
+    for (int32_t k = 0; k < ctx->hm.K; ++k) {
+        const gale::ClusterStat &s = ctx->hm.stats[k];
+        mx = std::max(mx, s.n_ext + s.n_own + s.n_halo);
+    }
     out->max_cluster_tets = mx;
     out->load_host_seconds = ctx->hm.host_seconds;
     out->load_device_seconds = ctx->device_seconds;
+    out->nparts = ctx->hm.NP;
+    int32_t cut = 0;
+    for (int32_t k = 0; k < ctx->hm.K; ++k) cut += ctx->hm.part_first[k + 1] > ctx->hm.part_first[k];
+    out->cut_clusters = cut;
     return GALE_OK;
 }
 
@@ -1153,8 +1278,9 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
     std::iota(ctx->bulk_ids.begin(), ctx->bulk_ids.end(), 0);
     ctx->bulk_mask = mask;
     const gale::DevMesh dm = dev_mesh(ctx);
-    int rc = gale::launch_bases(dm, nullptr, K, ctx->d_sizes, mask, ctx->d_arrays_base + mask, ctx->d_items,
-                                ctx->d_totals, ctx->d_bsum, ctx->stream);
+    int rc = gale::launch_bases(dm, ctx->hm.NP ? ctx->d_all_items : nullptr, int32_t(ctx->all_items.size()),
+                                ctx->d_sizes, mask, ctx->d_arrays_base + mask, ctx->d_items, ctx->d_totals,
+                                ctx->d_bsum, ctx->stream);
     if (rc != 0) return cuda_fail(cudaError_t(rc), "bases launch");
     const int smem_limit = gale::dynamic_smem_limit();
     if (!gale::prepare_kernels(smem_limit)) return fail(GALE_ECUDA, "setting the kernels' shared memory limit failed");
@@ -1165,6 +1291,10 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
     for (size_t b = 0; b < ctx->bins.size(); ++b) {
         gale::Bin &bin = ctx->bins[b];
         const int32_t nb = int32_t(bin.clusters.size());
+        if (bin.cut) {  // batched builds run these clusters' parts instead
+            if (best_ms && int32_t(b) < max_bins) best_ms[b] = 0.f;
+            continue;
+        }
         float best = -1.f;
         gale::SmemPlan best_plan = bin.plan;
         int best_grid = bin.grid, best_per = bin.ctas_per_sm;
@@ -1182,7 +1312,7 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
                 plan.threads = T;
                 plan.total = top;
                 CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-                CUDA_TRY(cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * size_t(K),
+                CUDA_TRY(cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * ctx->h_plans.size(),
                                     cudaMemcpyHostToDevice));
             }
             if (!bin.spill && plan.total > smem_limit) continue;
@@ -1252,7 +1382,7 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
         if (bin.per_item && !best_members.empty()) {
             for (size_t i = 0; i < bin.clusters.size(); ++i) ctx->h_plans[bin.clusters[i]] = best_members[i];
             CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-            CUDA_TRY(cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * size_t(K),
+            CUDA_TRY(cudaMemcpy(ctx->d_plans, ctx->h_plans.data(), sizeof(gale::SmemPlan) * ctx->h_plans.size(),
                                 cudaMemcpyHostToDevice));
         }
         if (best_ms && int32_t(b) < max_bins) best_ms[b] = best;
@@ -1277,13 +1407,16 @@ gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t
     *nbins = int32_t(ctx->bins.size());
     for (int32_t b = 0; b < *nbins && b < max_bins && out; ++b) {
         const gale::Bin &bin = ctx->bins[b];
-        out[7 * b + 0] = int32_t(bin.clusters.size());
-        out[7 * b + 1] = bin.plan.threads;
-        out[7 * b + 2] = bin.plan.total;
-        out[7 * b + 3] = bin.ctas_per_sm;
-        out[7 * b + 4] = bin.grid;
-        out[7 * b + 5] = bin.spill ? 1 : 0;
-        out[7 * b + 6] = bin.per_item ? 1 : 0;
+        out[8 * b + 0] = int32_t(bin.clusters.size());
+        out[8 * b + 1] = bin.plan.threads;
+        out[8 * b + 2] = bin.plan.total;
+        out[8 * b + 3] = bin.ctas_per_sm;
+        out[8 * b + 4] = bin.grid;
+        out[8 * b + 5] = bin.spill ? 1 : 0;
+        out[8 * b + 6] = bin.per_item ? 1 : 0;
+        int32_t parts = 0;
+        for (int32_t k : bin.clusters) parts += k >= ctx->hm.K;
+        out[8 * b + 7] = bin.cut ? -1 : parts;
     }
     return GALE_OK;
 }

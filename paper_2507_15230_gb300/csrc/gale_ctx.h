@@ -25,6 +25,8 @@ struct Bin {
     bool spill = false;             // regions in global scratch (working set too large for shared memory)
     bool per_item = false;          // each member runs under its own plan (gale_ctx::d_plans); `plan` is the
                                     // launch envelope: block size and the largest member's shared memory
+    bool cut = false;               // members are clusters cut into parts: batched builds run the parts
+                                    // (items K..K+NP-1, in other bins) instead; the other forms use this bin
 };
 
 struct DevAlloc {
@@ -51,27 +53,33 @@ struct gale_ctx {
     int32_t *d_blocks = nullptr;
     int64_t *d_blk_off = nullptr;
     int32_t *d_I_V = nullptr, *d_I_T = nullptr;
-    int64_t *d_sizes = nullptr;  // [K*5]
+    int64_t *d_sizes = nullptr;  // [(K+NP)*5] clusters, then parts
+    gale::PartInfo *d_parts = nullptr;  // [NP]
+    int32_t *d_tt_pos = nullptr;        // [nt] TT row offsets of the cut clusters' internal tets
+    int32_t *d_all_items = nullptr;     // [n_all] the full build's item list (cut clusters replaced by their parts)
+    std::vector<int32_t> all_items;     // host copy
+    std::vector<int32_t> pos_all;       // [K+NP] position of each item in all_items (-1: a cut cluster)
     int32_t *d_err = nullptr;
     int32_t *d_tickets = nullptr;  // one per bin (+ spare)
-    int32_t *d_ids = nullptr;      // [K] ids of a partial build
-    int32_t *d_order_all = nullptr;   // [K] per-bin LPT order of a full build
-    int32_t *d_order_part = nullptr;  // [K] order of a partial build
-    gale::WorkItem *d_items = nullptr;      // [K]
+    int32_t *d_ids = nullptr;      // [K+NP] item ids of a partial build
+    int32_t *d_order_all = nullptr;   // [K+NP] per bin: positions in all_items (largest first)
+    int32_t *d_order_ids = nullptr;   // [K+NP] per bin: item ids (the counting pass)
+    int32_t *d_order_part = nullptr;  // [K+NP] order of a partial build
+    gale::WorkItem *d_items = nullptr;      // [K+NP]
     gale::WorkItem *d_arrays_base = nullptr;  // [16] base pointers per mask
     int64_t *d_totals = nullptr;            // [10]
     int64_t *d_bsum = nullptr;              // output placement scratch
     char *d_spill = nullptr;                // per-CTA regions of spill bins
-    gale::SmemPlan *d_plans = nullptr;      // [K] own plans of the members of per-item bins
+    gale::SmemPlan *d_plans = nullptr;      // [K+NP] own plans of the members of per-item bins
     std::vector<gale::SmemPlan> h_plans;    // host copy
     int64_t spill_bytes = 0;
-    std::vector<int64_t> sizes;             // host [K*5]
+    std::vector<int64_t> sizes;             // host [(K+NP)*5]
     int64_t totals[5] = {0, 0, 0, 0, 0};
     double device_seconds = 0;
 
     // size bins
     std::vector<gale::Bin> bins;
-    std::vector<int32_t> bin_of;        // [K]
+    std::vector<int32_t> bin_of;        // [K+NP]
     std::vector<int64_t> order_all_off; // [nbins+1] offsets into d_order_all
     int threads_override = 0;  // 0: chosen from the cluster's tet count
     int ctas_override = 0;

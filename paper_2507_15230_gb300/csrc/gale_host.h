@@ -24,8 +24,11 @@ struct HostMesh {
     std::vector<int32_t> ext;         // T_ex lists, ascending per cluster
     std::vector<int64_t> halo_off;    // [K+1]
     std::vector<int32_t> halo;        // halo lists, ascending per cluster
-    std::vector<ClusterStat> stats;   // [K]
-    std::vector<int64_t> blk_off;     // [K+1] word offsets
+    std::vector<ClusterStat> stats;   // [K+NP] clusters, then parts
+    std::vector<int64_t> blk_off;     // [K+NP+1] word offsets
+    int32_t NP = 0;                   // parts of the cut clusters
+    std::vector<PartInfo> parts;      // [NP] (the b_* fields are set after the counting pass)
+    std::vector<int32_t> part_first;  // [K+1] parts of cluster k: part_first[k] .. part_first[k+1]-1
     int32_t *blocks = nullptr;        // blocks_words words (pinned when possible)
     int64_t blocks_words = 0;
     bool blocks_pinned = false;

@@ -44,26 +44,38 @@ namespace gale {
 // and since external tets precede the internal ones in canonical order, the
 // local order of [external | internal] is canonical order too.  n_bnd counts
 // the internal tets (a, b, c, d) whose face (b, c, d) has no own vertex.
+//
+// Part blocks (part != 0).  A cluster too large for one CTA's shared memory
+// is also cut into parts: contiguous ranges of its own vertices, each built
+// by its own CTA straight into the cluster's output arrays.  A part's own
+// vertices are its range; its external tets are the cluster's external tets
+// that touch the range, and its internal tets are the cluster's internal tets
+// that touch the range, in canonical order (not a contiguous id range, so
+// their ids follow the halo ids in tmap: tmap has n_ext + n_halo + n_own
+// words).  The part builds VT, VV and ET of its own vertices and the TT rows
+// of the internal tets whose lowest vertex is its own; n_bnd counts those.
 // ---------------------------------------------------------------------------
 struct BlockHdr {
     int32_t n_ext, n_own, n_halo, nv_loc;
     int32_t own_lo, nv_own, t_base, v_base;
-    int32_t nv_nb, n_bnd, pad0, pad1;
+    int32_t nv_nb, n_bnd, part, pad1;  // part: 0, or 1 + the part's index
 };
 static_assert(sizeof(BlockHdr) == 48, "header is 12 words");
 constexpr int kHdrWords = 12;
 
 GALE_HD inline int64_t a4(int64_t x) { return (x + 3) & ~int64_t(3); }
-GALE_HD inline int64_t blk_words(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo, int32_t n_bnd) {
-    return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo) + a4(2 * (int64_t(n_ext) + n_own + n_halo)) +
+// n_xmap: extra tmap words (a part block's internal tet ids; 0 otherwise)
+GALE_HD inline int64_t blk_words(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo, int32_t n_bnd,
+                                 int32_t n_xmap = 0) {
+    return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo + n_xmap) + a4(2 * (int64_t(n_ext) + n_own + n_halo)) +
            a4((int64_t(n_bnd) + 1) / 2);
 }
 GALE_HD inline int64_t blk_tmap_off(int32_t nv_loc) { return kHdrWords + a4(nv_loc); }
-GALE_HD inline int64_t blk_rows_off(int32_t nv_loc, int32_t n_ext, int32_t n_halo) {
-    return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo);
+GALE_HD inline int64_t blk_rows_off(int32_t nv_loc, int32_t n_ext, int32_t n_halo, int32_t n_xmap = 0) {
+    return kHdrWords + a4(nv_loc) + a4(int64_t(n_ext) + n_halo + n_xmap);
 }
-GALE_HD inline int64_t blk_bnd_off(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo) {
-    return blk_rows_off(nv_loc, n_ext, n_halo) + a4(2 * (int64_t(n_ext) + n_own + n_halo));
+GALE_HD inline int64_t blk_bnd_off(int32_t nv_loc, int32_t n_ext, int32_t n_own, int32_t n_halo, int32_t n_xmap = 0) {
+    return blk_rows_off(nv_loc, n_ext, n_halo, n_xmap) + a4(2 * (int64_t(n_ext) + n_own + n_halo));
 }
 
 // Largest local id space a block can address (uint16 local ids).
@@ -87,6 +99,28 @@ struct WorkItem {
 };
 static_assert(sizeof(WorkItem) == 96, "work item is 96 bytes");
 
+// One part of a cut cluster (see the block layout above).  Work items are
+// numbered clusters first, then parts: item K + p is part p.  A batched
+// build lists a cut cluster's parts in order in place of the cluster, so the
+// output placement of consecutive parts is the cluster's own: each part's
+// offset arrays hold its own entries and the last part's also the final
+// one.  The b_* fields are the cluster-level values at the part's start.
+struct PartInfo {
+    int32_t k;        // the cluster
+    int32_t x0;       // first own vertex, relative to the cluster's
+    int32_t nvo;      // own vertices
+    int32_t last;     // 1 for the cluster's last part
+    int32_t b_vt, b_vv, b_e, b_et;  // VT, VV, owned-edge and ET entries of the earlier parts
+    int32_t b_tt;     // TT entries of the earlier parts
+    int32_t b_to;     // TT rows (internal tets) of the earlier parts
+    int32_t n_rows;   // internal tets whose lowest vertex is the part's (its TT rows)
+    int32_t tt_total; // the cluster's TT entries
+    int32_t n_own_c;  // the cluster's internal tets
+    int32_t t_base_c; // the cluster's first internal tet
+    int32_t pad[2];
+};
+static_assert(sizeof(PartInfo) == 64, "part record is 64 bytes");
+
 // Per-cluster facts the host learns at load time, used for bins and bounds.
 struct ClusterStat {
     int32_t n_ext, n_own, n_halo, nv_loc, nv_own;
@@ -96,7 +130,7 @@ struct ClusterStat {
     int32_t n_bnd;    // internal tets whose face opposite their lowest vertex has no own vertex
     int32_t max_up;   // most distinct upper neighbours of an own vertex
     int32_t n_e;      // edges whose lower endpoint is an own vertex
-    int32_t pad;
+    int32_t xmap;     // extra tmap words of the block (a part's internal tet ids; 0 for a cluster)
 };
 
 // Capacities a launch is planned for (maxima over the clusters it serves).
@@ -162,14 +196,35 @@ enum : int32_t {
 };
 
 SmemPlan plan_smem(const Caps &c, int threads);
+// Capacities of one cluster or part; staging capacities come from the exact
+// sizes of the counting pass (sizes == nullptr: a counting plan, no staging).
+Caps caps_of(const ClusterStat &s, const int64_t *sizes);
+// Shared memory a build plan of this working set would take at the given
+// block size, with its staging sized from estimates (the counting pass has
+// not run yet): used to decide which clusters to cut into parts.
+int64_t estimate_smem(const ClusterStat &s, int threads);
+
+// Size bins a context may have (one ticket counter each in the build and
+// serving paths).
+constexpr int kMaxBins = 64;
+
+// A cluster is cut into parts of about kPartVertices own vertices when the
+// estimate exceeds kCutBytes (both overridable at load time).
+constexpr int32_t kPartVertices = 256;
+constexpr int64_t kCutBytes = 160 * 1024;
 
 // Kernel launchers (gale_kernels.cu).  All asynchronous on `stream`.
 struct DevMesh {
-    const int32_t *blocks;      // all cluster blocks
-    const int64_t *blk_off;     // [K] word offset of each block
+    const int32_t *blocks;      // all cluster blocks, then all part blocks
+    const int64_t *blk_off;     // [K+NP+1] word offset of each block
     const int32_t *I_V;         // [K+1]
     const int32_t *I_T;         // [K+1]
     int32_t K;
+    int32_t NP;                 // parts of cut clusters (work items K .. K+NP-1)
+    const PartInfo *parts;      // [NP]
+    int32_t *tt_pos;            // [nt] per internal tet of a cut cluster: its TT row's
+                                // offset in the cluster (the counting pass writes
+                                // the row lengths here first)
 };
 
 // Persistent launch over n clusters: ids[i] (count pass) or items[order[i]]

@@ -331,14 +331,17 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         phase ^= 1u;
     }
     const BlockHdr h = *reinterpret_cast<const BlockHdr *>(S.blk);
+    // a part block: its record, and the extra tmap words of its internal tets
+    const PartInfo *part = (h.part > 0 && h.part <= m.NP) ? m.parts + (h.part - 1) : nullptr;
+    const int32_t xmap = part ? h.n_own : 0;
     {
         const int64_t n_tot = int64_t(h.n_ext) + h.n_own + h.n_halo;
         const bool ok = h.n_ext >= 0 && h.n_own >= 0 && h.n_halo >= 0 && h.nv_loc >= 0 && h.own_lo >= 0 &&
                         h.nv_own >= 0 && h.nv_nb >= 0 && h.n_bnd >= 0 && n_tot <= caps.n_tot &&
                         h.n_own <= caps.n_own && h.nv_loc <= caps.nv_loc && h.nv_own <= caps.nv_own &&
                         h.nv_nb <= caps.nv_nb && h.nv_nb <= h.nv_loc && int64_t(h.own_lo) + h.nv_own <= h.nv_nb &&
-                        2 * int64_t(h.n_bnd) + 1 <= caps.hcap &&
-                        blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo, h.n_bnd) == words;
+                        2 * int64_t(h.n_bnd) + 1 <= caps.hcap && (h.part == 0 || part != nullptr) &&
+                        blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo, h.n_bnd, xmap) == words;
         if (!ok) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             __syncthreads();
@@ -347,7 +350,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     }
     const int n_ext = h.n_ext, n_own = h.n_own;
     const int n_vtets = n_ext + n_own;
-    const uint2 *rows = reinterpret_cast<const uint2 *>(S.blk + blk_rows_off(h.nv_loc, n_ext, h.n_halo));
+    const uint2 *rows = reinterpret_cast<const uint2 *>(S.blk + blk_rows_off(h.nv_loc, n_ext, h.n_halo, xmap));
     const int32_t *vmap = S.blk + kHdrWords;
     const int32_t *tmap = S.blk + blk_tmap_off(h.nv_loc);
     const int nvo = h.nv_own, lo = h.own_lo;
@@ -357,12 +360,22 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     const bool do_vv = !COUNT && (mask & R_VV);
     const bool do_et = !COUNT && (mask & R_ET);
     const int32_t t_base = h.t_base;
+    const int n_halo_b = h.n_halo;
     // canonical id of a local tet
     auto gtet = [&](int loc) -> int32_t {
         if (loc < n_ext) return tmap[loc];
-        if (loc < n_vtets) return t_base + (loc - n_ext);
+        if (loc < n_vtets) return part ? tmap[n_halo_b + loc] : t_base + (loc - n_ext);
         return tmap[loc - n_own];
     };
+    // a part writes cluster-level offset values: its entries are shifted by
+    // those of the cluster's earlier parts
+    int32_t b_vt = 0, b_vv = 0, b_e = 0, b_et = 0;
+    if (part && !COUNT) {
+        b_vt = __ldg(&part->b_vt);
+        b_vv = __ldg(&part->b_vv);
+        b_e = __ldg(&part->b_e);
+        b_et = __ldg(&part->b_et);
+    }
 
     // The per-own-vertex passes of C2 leave whole warps idle when the cluster
     // has fewer own vertices than the block has threads less a warp: those
@@ -455,7 +468,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         if (COUNT) {
             if (tid == 0) sizes_out[SZ_VT] = vt_total;
         } else if ((mask & R_VT) && !vt_copy_later) {
-            for (int i = tid; i <= nvo; i += NT) it->vt_off[i] = S.vt_off[i];
+            for (int i = tid; i <= nvo; i += NT) it->vt_off[i] = S.vt_off[i] + b_vt;
             copy_out(it->vt_val, vt_total, [&](int j) { return gtet(S.vt_list[j]); });
         }
     }
@@ -559,7 +572,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         if (vt_copy_later && warp >= copy_warp0) {
             // VT out, on the warps the per-vertex loop below leaves idle
             const int t0 = tid - copy_warp0 * 32, nt = NT - copy_warp0 * 32;
-            for (int i = t0; i <= nvo; i += nt) it->vt_off[i] = S.vt_off[i];
+            for (int i = t0; i <= nvo; i += nt) it->vt_off[i] = S.vt_off[i] + b_vt;
             int j = t0;
             for (; j + 3 * nt < vt_total; j += 4 * nt) {
                 const int32_t a = gtet(S.vt_list[j]), b = gtet(S.vt_list[j + nt]);
@@ -621,13 +634,13 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             sizes_out[SZ_ET] = tot[2];
         }
         if (do_vv) {
-            for (int i = tid; i <= nvo; i += NT) it->vv_off[i] = S.c_vv[i];
+            for (int i = tid; i <= nvo; i += NT) it->vv_off[i] = S.c_vv[i] + b_vv;
             copy_out(it->vv_val, tot[0], [&](int j) { return vmap[S.st_v[j]]; });
         }
         if (do_et) {
-            for (int i = tid; i <= nvo; i += NT) it->eu_off[i] = S.c_e[i];
+            for (int i = tid; i <= nvo; i += NT) it->eu_off[i] = S.c_e[i] + b_e;
             copy_out(it->e_w, tot[1], [&](int e) { return vmap[S.st_w[e]]; });
-            if (tid == 0) it->et_off[tot[1]] = tot[2];
+            if (tid == 0) it->et_off[tot[1]] = tot[2] + b_et;
         }
     }
     if (!(do_et || want_tt)) return true;
@@ -685,8 +698,8 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             const uint2 r = rows[li];
             const uint32_t v0 = r.x & 0xffffu, v1 = r.x >> 16, v2 = r.y & 0xffffu, v3 = r.y >> 16;
             const uint32_t a = v0 - uint32_t(lo);
-            if (a >= nvo_u) {  // an internal tet's lowest vertex is own
-                flags |= ERR_BAD_BLOCK;
+            if (a >= nvo_u) {  // an internal tet's lowest vertex is own (a part's: an earlier part's)
+                if (!part) flags |= ERR_BAD_BLOCK;
                 continue;
             }
             auto rank = [&](uint32_t x, uint32_t y) -> int {
@@ -762,7 +775,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             em[e * nch] = uint32_t(t0);  // the edge's first mask word now holds its row offset
         }
         __syncthreads();
-        for (int e = tid; e < tot_e; e += NT) it->et_off[e] = int32_t(em[e * nch]);
+        for (int e = tid; e < tot_e; e += NT) it->et_off[e] = int32_t(em[e * nch]) + b_et;
         copy_out(it->et_val, tot_etv, [&](int j) { return gtet(st_et[j]); });
         __syncthreads();  // ET staging is dead: r1 takes the face hash
     }
@@ -775,7 +788,8 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         __syncthreads();
         int32_t flags = 0;
         // the internal tets whose face (b, c, d) has no own vertex
-        const uint16_t *bnd = reinterpret_cast<const uint16_t *>(S.blk + blk_bnd_off(h.nv_loc, n_ext, n_own, h.n_halo));
+        const uint16_t *bnd =
+            reinterpret_cast<const uint16_t *>(S.blk + blk_bnd_off(h.nv_loc, n_ext, n_own, h.n_halo, xmap));
         for (int jb = tid; jb < h.n_bnd; jb += NT) {
             const int i = bnd[jb];
             const uint2 r = rows[n_ext + i];
@@ -824,9 +838,45 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                       ((nb.y >> 16) != 0xffffu);
         }
         __syncthreads();
+        if (COUNT && part) {
+            // row lengths of the part's own internal tets, by canonical id
+            for (int i = tid; i < n_own; i += NT)
+                if ((rows[n_ext + i].x & 0xffffu) - uint32_t(lo) < nvo_u) m.tt_pos[gtet(n_ext + i)] = tcnt[i];
+            __syncthreads();
+        }
         const int tot_tt = block_scan_array(tcnt, n_own, S.scan);
         if (COUNT) {
             if (tid == 0) sizes_out[SZ_TT] = tot_tt;
+        } else if (part) {
+            // rows straight to their cluster-level offsets (the earlier parts'
+            // rows of the same cluster precede this part's in the list)
+            if (tot_tt > caps.max_tt) {
+                if (tid == 0) atomicOr(err, ERR_CAPACITY);
+                return true;
+            }
+            int32_t *const c_off = it->tt_off - __ldg(&part->b_to);
+            int32_t *const c_val = it->tt_val - __ldg(&part->b_tt);
+            const int32_t tb = __ldg(&part->t_base_c);
+            for (int i = tid; i < n_own; i += NT) {
+                if ((rows[n_ext + i].x & 0xffffu) - uint32_t(lo) >= nvo_u) continue;  // an earlier part's row
+                const uint2 nb = *reinterpret_cast<const uint2 *>(&S.nbr[i * 4]);
+                const uint32_t n0 = nb.x & 0xffffu, n1 = nb.x >> 16, n2 = nb.y & 0xffffu, n3 = nb.y >> 16;
+                int32_t w0 = n0 != 0xffffu ? gtet(int32_t(n0)) : INT32_MAX;
+                int32_t w1 = n1 != 0xffffu ? gtet(int32_t(n1)) : INT32_MAX;
+                int32_t w2 = n2 != 0xffffu ? gtet(int32_t(n2)) : INT32_MAX;
+                int32_t w3 = n3 != 0xffffu ? gtet(int32_t(n3)) : INT32_MAX;
+                uint32_t l0 = n0, l1 = n1, l2 = n2, l3 = n3;
+                cswap2(w0, w1, l0, l1); cswap2(w2, w3, l2, l3); cswap2(w0, w2, l0, l2); cswap2(w1, w3, l1, l3);
+                cswap2(w1, w2, l1, l2);
+                const int32_t gt = gtet(n_ext + i);
+                const int32_t p = m.tt_pos[gt];
+                c_off[gt - tb] = p;
+                if (w0 != INT32_MAX) c_val[p] = w0;
+                if (w1 != INT32_MAX) c_val[p + 1] = w1;
+                if (w2 != INT32_MAX) c_val[p + 2] = w2;
+                if (w3 != INT32_MAX) c_val[p + 3] = w3;
+            }
+            if (tid == 0 && __ldg(&part->last)) c_off[__ldg(&part->n_own_c)] = __ldg(&part->tt_total);
         } else {
             if (tot_tt > caps.max_tt) {
                 if (tid == 0) atomicOr(err, ERR_CAPACITY);
@@ -895,7 +945,7 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan 
         __syncthreads();
         if (idx >= n) break;
         const int k = ids ? ids[idx] : idx;
-        if (k < 0 || k >= m.K) {
+        if (k < 0 || k >= m.K + m.NP) {
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
@@ -933,13 +983,13 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel(DevMesh m, SmemPlan 
         if (threadIdx.x == 32 && s_idx < n) {
             // its block into L2 while this cluster builds
             const int k2 = items[order ? order[s_idx] : s_idx].k;
-            if (k2 >= 0 && k2 < m.K) {
+            if (k2 >= 0 && k2 < m.K + m.NP) {
                 const int64_t w0 = m.blk_off[k2], w1 = m.blk_off[k2 + 1];
                 if (w1 > w0) prefetch_l2(m.blocks + w0, uint32_t(4 * (w1 - w0)));
             }
         }
         const int k = s_item.k;
-        if (k < 0 || k >= m.K) {
+        if (k < 0 || k >= m.K + m.NP) {
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
@@ -960,7 +1010,7 @@ __global__ void __launch_bounds__(kMaxThreads) build_one_kernel(DevMesh m, SmemP
     uint32_t phase = 0;
     if (threadIdx.x == 0) s_item = items[index];
     __syncthreads();
-    if (s_item.k < 0 || s_item.k >= m.K) {
+    if (s_item.k < 0 || s_item.k >= m.K + m.NP) {
         if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
         return;
     }
@@ -999,7 +1049,7 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel_pi(DevMesh m, const 
         __syncthreads();
         if (idx >= n) break;
         const int k = ids ? ids[idx] : idx;
-        if (k < 0 || k >= m.K) {
+        if (k < 0 || k >= m.K + m.NP) {
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
@@ -1038,13 +1088,13 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel_pi(DevMesh m, const 
         __syncthreads();
         if (threadIdx.x == 32 && s_idx < n) {
             const int k2 = items[order ? order[s_idx] : s_idx].k;
-            if (k2 >= 0 && k2 < m.K) {
+            if (k2 >= 0 && k2 < m.K + m.NP) {
                 const int64_t w0 = m.blk_off[k2], w1 = m.blk_off[k2 + 1];
                 if (w1 > w0) prefetch_l2(m.blocks + w0, uint32_t(4 * (w1 - w0)));
             }
         }
         const int k = s_item.k;
-        if (k < 0 || k >= m.K) {
+        if (k < 0 || k >= m.K + m.NP) {
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
@@ -1163,18 +1213,29 @@ __device__ __forceinline__ void item_lengths(const DevMesh &m, const int32_t *id
                                              uint32_t mask, int idx, int64_t *L) {
     const int k = ids ? ids[idx] : idx;
     const int64_t *sz = sizes + int64_t(k) * SZ_N;
-    const int64_t nvo = m.I_V[k + 1] - m.I_V[k];
-    const int64_t nown = m.I_T[k + 1] - m.I_T[k];
+    // a cluster's offset arrays end with one extra entry; a part's only when
+    // it is its cluster's last
+    int64_t nvo, nown, fin;
+    if (k < m.K) {
+        nvo = m.I_V[k + 1] - m.I_V[k];
+        nown = m.I_T[k + 1] - m.I_T[k];
+        fin = 1;
+    } else {
+        const PartInfo &p = m.parts[k - m.K];
+        nvo = p.nvo;
+        nown = p.n_rows;
+        fin = p.last;
+    }
     const bool vt = mask & R_VT, vv = mask & R_VV, et = mask & R_ET, tt = mask & R_TT;
-    L[0] = vt ? nvo + 1 : 0;
+    L[0] = vt ? nvo + fin : 0;
     L[1] = vt ? sz[SZ_VT] : 0;
-    L[2] = vv ? nvo + 1 : 0;
+    L[2] = vv ? nvo + fin : 0;
     L[3] = vv ? sz[SZ_VV] : 0;
-    L[4] = et ? nvo + 1 : 0;
+    L[4] = et ? nvo + fin : 0;
     L[5] = et ? sz[SZ_E] : 0;
-    L[6] = et ? sz[SZ_E] + 1 : 0;
+    L[6] = et ? sz[SZ_E] + fin : 0;
     L[7] = et ? sz[SZ_ET] : 0;
-    L[8] = tt ? nown + 1 : 0;
+    L[8] = tt ? nown + fin : 0;
     L[9] = tt ? sz[SZ_TT] : 0;
 }
 
@@ -1287,6 +1348,43 @@ __global__ void __launch_bounds__(kBasesThreads) bases_write_kernel(DevMesh m, c
 // ---------------------------------------------------------------------------
 
 static int64_t a16(int64_t x) { return (x + 15) & ~int64_t(15); }
+
+static int64_t pow2_at_least(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+Caps caps_of(const ClusterStat &s, const int64_t *sizes) {
+    Caps c{};
+    c.blk_words = int32_t(blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo, s.n_bnd, s.xmap));
+    c.nv_own = s.nv_own;
+    c.n_vt = s.n_vt;
+    c.n_own = s.n_own;
+    c.nv_loc = s.nv_loc;
+    c.nv_nb = s.nv_nb;
+    c.max_deg = s.max_deg;
+    c.max_up = s.max_up;
+    c.max_e = s.n_e;
+    if (sizes) {
+        c.max_vv = int32_t(sizes[SZ_VV]);
+        c.max_e = int32_t(sizes[SZ_E]);
+        c.max_etv = int32_t(sizes[SZ_ET]);
+        c.max_tt = int32_t(sizes[SZ_TT]);
+    }
+    c.hcap = int32_t(std::max<int64_t>(64, pow2_at_least(2 * int64_t(s.n_bnd) + 1)));
+    c.n_tot = s.n_ext + s.n_own + s.n_halo;
+    c.n_star = s.n_ext + s.n_own;
+    return c;
+}
+
+int64_t estimate_smem(const ClusterStat &s, int threads) {
+    Caps c = caps_of(s, nullptr);
+    c.max_vv = 2 * s.n_e;           // each edge is in two VV rows (within the working set, about)
+    c.max_etv = s.n_vt + s.n_vt / 2;  // an incidence (x, t) meets 1.5 vertices of t above x on average
+    c.max_tt = 4 * s.n_own;
+    return plan_smem(c, threads).total;
+}
 
 SmemPlan plan_smem(const Caps &c, int threads) {
     SmemPlan p{};

@@ -201,11 +201,12 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
     hm.halo_off.assign(size_t(K) + 1, 0);
     hm.halo.clear();
     const bool want_tt = (d.precondition_mask & 8u) != 0;
+    // vertex stars over canonical tets (ascending), kept for the parts' halos
+    std::vector<int32_t> order;
+    std::vector<int64_t> vs_off;  // star of c: order[vs_off[c] .. vs_off[c+1]) / 4
     if (want_tt && nt > 0) {
-        // vertex stars over canonical tets (ascending)
-        std::vector<int32_t> order(size_t(4) * nt);
-        counting_sort(4 * nt, int32_t(nv), P, [&](int64_t i) { return rows[i]; }, order.data(), start);
-        std::vector<int64_t> &vs_off = start;  // star of c: order[vs_off[c] .. vs_off[c+1]) / 4
+        order.resize(size_t(4) * nt);
+        counting_sort(4 * nt, int32_t(nv), P, [&](int64_t i) { return rows[i]; }, order.data(), vs_off);
         std::vector<std::vector<int32_t>> halo_k(K);
         parallel_dynamic(K, P, 16, [&](int64_t k, int) {
             std::vector<int32_t> &hk = halo_k[k];
@@ -242,29 +243,41 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         });
     }
 
-    // ---- 6. per-cluster blocks ----
-    hm.stats.assign(K, ClusterStat{});
-    std::vector<std::vector<int32_t>> vmaps(K);
-    std::atomic<int64_t> bad_k{-1};
-    std::atomic<int64_t> dup_k{-1};
-    parallel_dynamic(K, P, 16, [&](int64_t k, int) {
-        const int32_t v0 = hm.I_V[k], v1 = hm.I_V[k + 1];
-        const int64_t e0 = hm.ext_off[k], e1 = hm.ext_off[k + 1];
-        const int64_t h0 = hm.halo_off[k], h1 = hm.halo_off[k + 1];
-        const int32_t t0 = hm.I_T[k], t1 = hm.I_T[k + 1];
-        // neighbour universe: vertices of [external | internal] tets plus
-        // the own interval, ascending; then halo-only vertices, ascending
+    // ---- 6. working sets and their blocks: every cluster, then the parts of
+    //         the clusters too large for one CTA's shared memory ----
+    // A working set: own vertices [v0, v1); external tets (ascending, below
+    // every internal one); internal tets (the id range [t0, t1), or for a
+    // part an ascending list); halo tets (ascending).
+    struct WSet {
+        int32_t v0 = 0, v1 = 0;
+        const int32_t *ext = nullptr;
+        int64_t n_ext = 0;
+        int32_t t0 = 0, t1 = 0;
+        const int32_t *ilist = nullptr;
+        int64_t n_int = 0;
+        const int32_t *halo = nullptr;
+        int64_t n_halo = 0;
+        int32_t part = 0;  // 0, or 1 + the part's index
+        int32_t t_base = 0;
+        int32_t itet(int64_t i) const { return ilist ? ilist[i] : t0 + int32_t(i); }
+    };
+    // vertex map and facts of a working set: 0 ok, 1 too large for 16-bit
+    // local ids, 2 two internal tets with the same vertex set
+    auto ws_scan = [&](const WSet &w, ClusterStat &s, std::vector<int32_t> &vm) -> int {
+        const int32_t v0 = w.v0, v1 = w.v1;
+        // neighbour universe: vertices of [external | internal] tets plus the
+        // own interval, ascending; then halo-only vertices, ascending
         std::vector<int32_t> nb, ho;
         auto add_row = [&](std::vector<int32_t> &dst, int32_t t) {
             const int32_t *r = rows + 4 * int64_t(t);
             for (int j = 0; j < 4; ++j)
                 if (r[j] < v0 || r[j] >= v1) dst.push_back(r[j]);
         };
-        for (int64_t i = e0; i < e1; ++i) add_row(nb, hm.ext[i]);
-        for (int32_t t = t0; t < t1; ++t) add_row(nb, t);
+        for (int64_t i = 0; i < w.n_ext; ++i) add_row(nb, w.ext[i]);
+        for (int64_t i = 0; i < w.n_int; ++i) add_row(nb, w.itet(i));
         std::sort(nb.begin(), nb.end());
         nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
-        for (int64_t i = h0; i < h1; ++i) add_row(ho, hm.halo[i]);
+        for (int64_t i = 0; i < w.n_halo; ++i) add_row(ho, w.halo[i]);
         std::sort(ho.begin(), ho.end());
         ho.erase(std::unique(ho.begin(), ho.end()), ho.end());
         {
@@ -273,7 +286,6 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
             ho.swap(only);
         }
         const int64_t below = std::lower_bound(nb.begin(), nb.end(), v0) - nb.begin();
-        std::vector<int32_t> &vm = vmaps[k];
         vm.clear();
         vm.reserve(nb.size() + (v1 - v0) + ho.size());
         vm.insert(vm.end(), nb.begin(), nb.begin() + below);
@@ -281,21 +293,18 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         vm.insert(vm.end(), nb.begin() + below, nb.end());
         const int32_t nv_nb = int32_t(vm.size());
         vm.insert(vm.end(), ho.begin(), ho.end());
-        ClusterStat &s = hm.stats[k];
-        s.n_ext = int32_t(e1 - e0);
-        s.n_own = t1 - t0;
-        s.n_halo = int32_t(h1 - h0);
+        s = ClusterStat{};
+        s.n_ext = int32_t(w.n_ext);
+        s.n_own = int32_t(w.n_int);
+        s.n_halo = int32_t(w.n_halo);
         s.nv_loc = int32_t(vm.size());
         s.nv_nb = nv_nb;
         s.nv_own = v1 - v0;
-        const int64_t ntot = int64_t(s.n_ext) + s.n_own + s.n_halo;
-        if (int64_t(vm.size()) > kMaxLocal || ntot > kMaxLocal - 1) {
-            bad_k = k;
-            return;
-        }
+        s.xmap = w.part ? s.n_own : 0;
+        const int64_t ntot = w.n_ext + w.n_int + w.n_halo;
+        if (int64_t(vm.size()) > kMaxLocal || ntot > kMaxLocal - 1) return 1;
         // degrees and distinct upper neighbours of own vertices over
-        // [external | internal]; internal tets whose face opposite the lowest
-        // vertex has no own vertex
+        // [external | internal]
         const int32_t own_lo = int32_t(below);
         auto loc = [&](int32_t v) -> int32_t {
             if (v >= v0 && v < v1) return own_lo + (v - v0);
@@ -312,8 +321,8 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
                     for (int q = j + 1; q < 4; ++q) up[r[j] - v0].push_back(loc(r[q]));
                 }
         };
-        for (int64_t i = e0; i < e1; ++i) count_row(hm.ext[i]);
-        for (int32_t t = t0; t < t1; ++t) count_row(t);
+        for (int64_t i = 0; i < w.n_ext; ++i) count_row(w.ext[i]);
+        for (int64_t i = 0; i < w.n_int; ++i) count_row(w.itet(i));
         int32_t nvt = 0, mx = 0, mu = 0, ne = 0;
         for (int32_t i = 0; i < nvo; ++i) {
             nvt += deg[i];
@@ -328,64 +337,39 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         s.max_deg = mx;
         s.max_up = mu;
         s.n_e = ne;
+        // internal tets with an own lowest vertex whose face opposite it has
+        // no own vertex
         int32_t nbnd = 0;
-        for (int32_t t = t0; t < t1; ++t) nbnd += (rows[4 * int64_t(t) + 1] >= v1);
+        for (int64_t i = 0; i < w.n_int; ++i) {
+            const int32_t *r = rows + 4 * int64_t(w.itet(i));
+            nbnd += (r[0] >= v0 && r[0] < v1 && r[1] >= v1);
+        }
         s.n_bnd = nbnd;
         // two tets with the same vertex set have the same owner
-        if (t1 - t0 > 1) {
-            std::vector<std::array<int32_t, 4>> own(size_t(t1 - t0));
-            for (int32_t t = t0; t < t1; ++t) memcpy(own[t - t0].data(), rows + 4 * int64_t(t), 16);
+        if (!w.part && w.n_int > 1) {
+            std::vector<std::array<int32_t, 4>> own(size_t(w.n_int));
+            for (int64_t i = 0; i < w.n_int; ++i) memcpy(own[i].data(), rows + 4 * int64_t(w.itet(i)), 16);
             std::sort(own.begin(), own.end());
             for (size_t i = 1; i < own.size(); ++i)
-                if (own[i] == own[i - 1]) {
-                    dup_k = k;
-                    return;
-                }
+                if (own[i] == own[i - 1]) return 2;
         }
-    });
-    if (dup_k >= 0) {
-        err = "two tets have the same vertex set (cluster " + std::to_string(dup_k.load()) + ")";
-        return false;
-    }
-    if (bad_k >= 0) {
-        err = "cluster " + std::to_string(bad_k.load()) +
-              " has a working set larger than 65535 local vertices or 65534 tets; use smaller clusters";
-        return false;
-    }
-    hm.blk_off.assign(size_t(K) + 1, 0);
-    int64_t run = 0;
-    hm.ext_total = 0;
-    hm.halo_total = 0;
-    for (int32_t k = 0; k < K; ++k) {
-        const ClusterStat &s = hm.stats[k];
-        hm.blk_off[k] = run;
-        run += blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo, s.n_bnd);
-        hm.ext_total += s.n_ext;
-        hm.halo_total += s.n_halo;
-    }
-    hm.blk_off[K] = run;
-    hm.blocks_words = run;
-    if (!hm.alloc_blocks(run)) {
-        err = "host allocation of the cluster blocks failed";
-        return false;
-    }
-    int32_t *blocks = hm.blocks;
-    parallel_dynamic(K, P, 16, [&](int64_t k, int) {
-        const ClusterStat &s = hm.stats[k];
-        const std::vector<int32_t> &vm = vmaps[k];
-        int32_t *blk = blocks + hm.blk_off[k];
-        const int64_t words = hm.blk_off[k + 1] - hm.blk_off[k];
+        return 0;
+    };
+    auto ws_fill = [&](const WSet &w, const ClusterStat &s, const std::vector<int32_t> &vm, int32_t *blk,
+                       int64_t words) {
         memset(blk, 0, size_t(words) * 4);
-        const int32_t v0 = hm.I_V[k];
+        const int32_t v0 = w.v0;
         const int32_t own_lo = int32_t(std::lower_bound(vm.begin(), vm.begin() + s.nv_nb, v0) - vm.begin());
-        BlockHdr hdr{s.n_ext, s.n_own, s.n_halo, s.nv_loc, own_lo, s.nv_own, hm.I_T[k], v0, s.nv_nb, s.n_bnd, 0, 0};
+        BlockHdr hdr{s.n_ext, s.n_own, s.n_halo, s.nv_loc, own_lo, s.nv_own, w.t_base, v0, s.nv_nb, s.n_bnd,
+                     w.part, 0};
         memcpy(blk, &hdr, sizeof(hdr));
         memcpy(blk + kHdrWords, vm.data(), vm.size() * 4);
         int32_t *tmap = blk + blk_tmap_off(s.nv_loc);
-        const int64_t e0 = hm.ext_off[k], h0 = hm.halo_off[k];
-        for (int32_t i = 0; i < s.n_ext; ++i) tmap[i] = hm.ext[e0 + i];
-        for (int32_t i = 0; i < s.n_halo; ++i) tmap[s.n_ext + i] = hm.halo[h0 + i];
-        uint16_t *lrows = reinterpret_cast<uint16_t *>(blk + blk_rows_off(s.nv_loc, s.n_ext, s.n_halo));
+        for (int64_t i = 0; i < w.n_ext; ++i) tmap[i] = w.ext[i];
+        for (int64_t i = 0; i < w.n_halo; ++i) tmap[w.n_ext + i] = w.halo[i];
+        if (w.part)
+            for (int64_t i = 0; i < w.n_int; ++i) tmap[w.n_ext + w.n_halo + i] = w.itet(i);
+        uint16_t *lrows = reinterpret_cast<uint16_t *>(blk + blk_rows_off(s.nv_loc, s.n_ext, s.n_halo, s.xmap));
         auto local = [&](int32_t v) -> uint16_t {
             if (v >= v0 && v < v0 + s.nv_own) return uint16_t(own_lo + (v - v0));
             auto it = std::lower_bound(vm.begin(), vm.begin() + s.nv_nb, v);
@@ -398,14 +382,169 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
             for (int j = 0; j < 4; ++j) lrows[4 * li + j] = local(r[j]);
             ++li;
         };
-        for (int32_t i = 0; i < s.n_ext; ++i) put(hm.ext[e0 + i]);
-        for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t) put(t);
-        for (int32_t i = 0; i < s.n_halo; ++i) put(hm.halo[h0 + i]);
-        // internal tets whose face opposite their lowest vertex has no own vertex
-        uint16_t *bnd = reinterpret_cast<uint16_t *>(blk + blk_bnd_off(s.nv_loc, s.n_ext, s.n_own, s.n_halo));
+        for (int64_t i = 0; i < w.n_ext; ++i) put(w.ext[i]);
+        for (int64_t i = 0; i < w.n_int; ++i) put(w.itet(i));
+        for (int64_t i = 0; i < w.n_halo; ++i) put(w.halo[i]);
+        uint16_t *bnd =
+            reinterpret_cast<uint16_t *>(blk + blk_bnd_off(s.nv_loc, s.n_ext, s.n_own, s.n_halo, s.xmap));
         int32_t nb = 0;
+        const int32_t v1 = v0 + s.nv_own;
+        for (int64_t i = 0; i < w.n_int; ++i) {
+            const int32_t *r = rows + 4 * int64_t(w.itet(i));
+            if (r[0] >= v0 && r[0] < v1 && r[1] >= v1) bnd[nb++] = uint16_t(i);
+        }
+    };
+    auto cluster_set = [&](int32_t k) {
+        WSet w;
+        w.v0 = hm.I_V[k];
+        w.v1 = hm.I_V[k + 1];
+        w.ext = hm.ext.data() + hm.ext_off[k];
+        w.n_ext = hm.ext_off[k + 1] - hm.ext_off[k];
+        w.t0 = hm.I_T[k];
+        w.t1 = hm.I_T[k + 1];
+        w.n_int = w.t1 - w.t0;
+        w.halo = hm.halo.data() + hm.halo_off[k];
+        w.n_halo = hm.halo_off[k + 1] - hm.halo_off[k];
+        w.t_base = hm.I_T[k];
+        return w;
+    };
+    hm.stats.assign(K, ClusterStat{});
+    std::vector<std::vector<int32_t>> vmaps(K);
+    std::atomic<int64_t> bad_k{-1};
+    std::atomic<int64_t> dup_k{-1};
+    parallel_dynamic(K, P, 16, [&](int64_t k, int) {
+        const int rc = ws_scan(cluster_set(int32_t(k)), hm.stats[k], vmaps[k]);
+        if (rc == 1) bad_k = k;
+        if (rc == 2) dup_k = k;
+    });
+    if (dup_k >= 0) {
+        err = "two tets have the same vertex set (cluster " + std::to_string(dup_k.load()) + ")";
+        return false;
+    }
+    if (bad_k >= 0) {
+        err = "cluster " + std::to_string(bad_k.load()) +
+              " has a working set larger than 65535 local vertices or 65534 tets; use smaller clusters";
+        return false;
+    }
+
+    // Clusters whose working set would not fit one CTA's shared memory are
+    // also cut into parts of about part_v own vertices (contiguous ranges),
+    // whose working sets do; batched builds run the parts, each on its own
+    // CTA, instead of the cluster.
+    const int32_t part_v = d.part_vertices > 0 ? d.part_vertices : kPartVertices;
+    const int64_t cut_bytes = d.cut_bytes > 0 ? d.cut_bytes : kCutBytes;
+    hm.part_first.assign(size_t(K) + 1, 0);
+    std::vector<std::array<int32_t, 3>> pr;  // (cluster, first own vertex, end)
+    for (int32_t k = 0; k < K; ++k) {
+        hm.part_first[k] = int32_t(pr.size());
+        const ClusterStat &s = hm.stats[k];
+        if (d.part_vertices < 0 || s.nv_own < 2 || estimate_smem(s, 512) <= cut_bytes) continue;
+        const int32_t S = std::max(2, (s.nv_own + part_v - 1) / part_v), v0 = hm.I_V[k];
+        for (int32_t j = 0; j < S; ++j)
+            pr.push_back({k, v0 + int32_t(int64_t(s.nv_own) * j / S), v0 + int32_t(int64_t(s.nv_own) * (j + 1) / S)});
+    }
+    hm.part_first[K] = int32_t(pr.size());
+    const int32_t NP = int32_t(pr.size());
+    hm.NP = NP;
+    hm.parts.assign(size_t(NP), PartInfo{});
+    hm.stats.resize(size_t(K) + NP);
+    vmaps.resize(size_t(K) + NP);
+    std::vector<std::vector<int32_t>> pext(NP), pint(NP), phalo(NP);
+    auto part_set = [&](int32_t p) {
+        WSet w;
+        w.v0 = pr[p][1];
+        w.v1 = pr[p][2];
+        w.ext = pext[p].data();
+        w.n_ext = int64_t(pext[p].size());
+        w.ilist = pint[p].data();
+        w.n_int = int64_t(pint[p].size());
+        w.halo = phalo[p].data();
+        w.n_halo = int64_t(phalo[p].size());
+        w.part = p + 1;
+        w.t_base = hm.I_T[pr[p][0]];
+        return w;
+    };
+    std::atomic<int64_t> bad_p{-1};
+    parallel_dynamic(NP, P, 4, [&](int64_t p, int) {
+        const int32_t k = pr[p][0], a0 = pr[p][1], a1 = pr[p][2];
+        auto touches = [&](int32_t t) {
+            const int32_t *r = rows + 4 * int64_t(t);
+            return (r[0] >= a0 && r[0] < a1) || (r[1] >= a0 && r[1] < a1) || (r[2] >= a0 && r[2] < a1) ||
+                   (r[3] >= a0 && r[3] < a1);
+        };
+        for (int64_t i = hm.ext_off[k]; i < hm.ext_off[k + 1]; ++i)
+            if (touches(hm.ext[i])) pext[p].push_back(hm.ext[i]);
+        int32_t n_rows = 0;
         for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t)
-            if (rows[4 * int64_t(t) + 1] >= v0 + s.nv_own) bnd[nb++] = uint16_t(t - hm.I_T[k]);
+            if (touches(t)) {
+                pint[p].push_back(t);
+                const int32_t *r = rows + 4 * int64_t(t);
+                n_rows += (r[0] >= a0 && r[0] < a1);
+            }
+        if (want_tt) {
+            // tets across the face (b, c, d) of a row's tet (a, b, c, d) when
+            // that face has no vertex in the part and they have none either
+            std::vector<int32_t> &hp = phalo[p];
+            for (int32_t t : pint[p]) {
+                const int32_t *r = rows + 4 * int64_t(t);
+                if (r[0] < a0 || r[0] >= a1 || r[1] < a1) continue;
+                const int32_t b = r[1], c = r[2], dd = r[3];
+                for (int64_t q = vs_off[b]; q < vs_off[b + 1]; ++q) {
+                    const int32_t u = order[q] >> 2;
+                    if (u == t) continue;
+                    const int32_t *ru = rows + 4 * int64_t(u);
+                    bool hc = false, hd = false, inp = false;
+                    for (int j = 0; j < 4; ++j) {
+                        hc |= ru[j] == c;
+                        hd |= ru[j] == dd;
+                        inp |= ru[j] >= a0 && ru[j] < a1;
+                    }
+                    if (hc && hd && !inp) hp.push_back(u);
+                }
+            }
+            std::sort(hp.begin(), hp.end());
+            hp.erase(std::unique(hp.begin(), hp.end()), hp.end());
+        }
+        if (ws_scan(part_set(int32_t(p)), hm.stats[size_t(K) + p], vmaps[size_t(K) + p]) != 0) bad_p = p;
+        PartInfo &pi = hm.parts[p];
+        pi.k = k;
+        pi.x0 = a0 - hm.I_V[k];
+        pi.nvo = a1 - a0;
+        pi.last = int32_t(p) + 1 == hm.part_first[k + 1] ? 1 : 0;
+        pi.n_rows = n_rows;
+        pi.n_own_c = hm.I_T[k + 1] - hm.I_T[k];
+        pi.t_base_c = hm.I_T[k];
+    });
+    if (bad_p >= 0) {
+        err = "a part of cluster " + std::to_string(pr[bad_p][0]) + " has too large a working set";
+        return false;
+    }
+    std::vector<int32_t>().swap(order);
+    std::vector<int64_t>().swap(vs_off);
+
+    const int64_t NI = int64_t(K) + NP;
+    hm.blk_off.assign(size_t(NI) + 1, 0);
+    int64_t run = 0;
+    hm.ext_total = 0;
+    hm.halo_total = 0;
+    for (int64_t i = 0; i < NI; ++i) {
+        const ClusterStat &s = hm.stats[i];
+        hm.blk_off[i] = run;
+        run += blk_words(s.nv_loc, s.n_ext, s.n_own, s.n_halo, s.n_bnd, s.xmap);
+        if (i < K) {
+            hm.ext_total += s.n_ext;
+            hm.halo_total += s.n_halo;
+        }
+    }
+    hm.blk_off[NI] = run;
+    hm.blocks_words = run;
+    if (!hm.alloc_blocks(run)) {
+        err = "host allocation of the cluster blocks failed";
+        return false;
+    }
+    parallel_dynamic(NI, P, 16, [&](int64_t i, int) {
+        const WSet w = i < K ? cluster_set(int32_t(i)) : part_set(int32_t(i - K));
+        ws_fill(w, hm.stats[i], vmaps[i], hm.blocks + hm.blk_off[i], hm.blk_off[i + 1] - hm.blk_off[i]);
     });
     hm.host_seconds = std::chrono::duration<double>(clk::now() - t0).count();
     return true;

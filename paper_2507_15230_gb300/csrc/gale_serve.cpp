@@ -191,7 +191,7 @@ struct Serve {
     // launch mode
     WorkItem *d_batch = nullptr;   // [kRingCap] device work items
     int32_t *d_border = nullptr;   // [kRingCap] per-bin order
-    int32_t *d_tick = nullptr;     // [64] tickets
+    int32_t *d_tick = nullptr;     // [kMaxBins] tickets
     WorkItem *h_batch = nullptr;   // pinned staging
     int32_t *h_border = nullptr;
     cudaEvent_t batch_event = nullptr;
@@ -287,7 +287,7 @@ gale_status Serve::init(gale_ctx *c) {
     d_err = static_cast<int32_t *>(ctx->dalloc(64));
     d_batch = static_cast<WorkItem *>(ctx->dalloc(sizeof(WorkItem) * kRingCap));
     d_border = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * kRingCap));
-    d_tick = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * 64));
+    d_tick = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * kMaxBins));
     if (!d_next || !d_err || !d_batch || !d_border || !d_tick)
         return fail(GALE_ENOMEM, "device allocation for the serving loop failed");
     if (ctx->spill_bytes > 0) {

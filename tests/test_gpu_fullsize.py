@@ -74,11 +74,15 @@ def sample_clusters(ctx, canon, rng, extra):
     size = np.diff(I_V)
     K = size.size
     ks = {0, K - 1, int(size.argmax()), int(size.argmin())}
-    # one member of every size bin
+    # one cluster of every size bin (members above K are parts of cut
+    # clusters, whose own bins list the clusters)
     order = ctx.bin_members()
     start = 0
     for b in ctx.bins():
-        ks.add(int(order[start]))
+        mem = order[start:start + b["clusters"]]
+        mem = mem[mem < K]
+        if mem.size:
+            ks.add(int(mem[0]))
         start += b["clusters"]
     ks.update(int(k) for k in rng.choice(K, extra, replace=False))
     return sorted(ks)
@@ -112,20 +116,21 @@ def test_grid256_full_size():
 
 def test_delaunay_2m_full_size():
     """Besides the whole-output properties and sampled clusters, the largest
-    clusters that still fit shared memory, which share one persistent launch
-    with each cluster under its own plan, are checked in the batched,
-    per-cluster and served forms."""
+    clusters - cut into parts that batched builds run one CTA each - are
+    checked in the batched, per-cluster and served forms."""
     import threading
     m = gen.delaunay_mesh(2_000_000, seed=5, with_field=False)
     with gale.Context.load(m, device=0, cache_budget_bytes=1 << 30) as ctx:
         bins0 = ctx.bins()
-        pi = [i for i, b in enumerate(bins0) if b["per_item"]]
-        assert pi, bins0
+        assert ctx.info().nparts > 0, bins0
+        assert any(b["parts"] > 0 for b in bins0), bins0
+        cut = [i for i, b in enumerate(bins0) if b["parts"] == -1]
+        assert cut, bins0
         members = ctx.bin_members()
         starts = np.concatenate([[0], np.cumsum([b["clusters"] for b in bins0])])
-        pi_ids = np.concatenate([members[starts[i]:starts[i + 1]] for i in pi])
+        pi_ids = np.concatenate([members[starts[i]:starts[i + 1]] for i in cut])
         ctx.autotune(gale.ALL, reps=1)
-        assert [b["per_item"] for b in ctx.bins()] == [b["per_item"] for b in bins0]
+        assert [b["parts"] for b in ctx.bins()] == [b["parts"] for b in bins0]
         for _ in range(2):
             ctx.build(None, gale.ALL, gale.MODE_BATCHED)
         ctx.synchronize()

@@ -161,7 +161,9 @@ def test_delaunay_uneven_clusters(npts, seed):
     canon, rel = oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
     with gale.Context.load(m, device=0) as ctx:
         bins = ctx.bins()
-        assert sum(b["clusters"] for b in bins) == m.nclusters
+        # members: every cluster, and the parts of the clusters cut for
+        # batched builds
+        assert sum(b["clusters"] for b in bins) == m.nclusters + ctx.info().nparts
         assert any(b["spill"] for b in bins), bins
         _, _, sizes = ctx.intervals()
         assert np.array_equal(sizes, oracle.cluster_sizes(rel, canon))
@@ -183,7 +185,8 @@ def test_autotune_keeps_parity(which):
         best = ctx.autotune(gale.ALL, reps=1)
         after = ctx.bins()
         assert len(best) == len(before) == len(after)
-        assert all(ms > 0 for ms in best)
+        # bins of cut clusters are not timed (batched builds run their parts)
+        assert all(ms > 0 for ms, b in zip(best, after) if b["parts"] != -1)
         for b0, b1 in zip(before, after):
             assert b1["clusters"] == b0["clusters"] and b1["spill"] == b0["spill"]
             assert b1["threads"] in (128, 256, 384, 512, 768, 1024)
@@ -253,16 +256,21 @@ def test_high_degree_vertex(K, seed):
 
 @pytest.mark.parametrize("mask", [gale.VT, gale.VV, gale.ET, gale.TT, gale.VT | gale.ET])
 def test_spill_bins_every_mask(mask):
-    """Clusters too large for shared memory (global-scratch bins) under every
-    relation mask, batched and one launch per cluster."""
+    """Clusters too large for shared memory under every relation mask,
+    batched and one launch per cluster: with the default cut, batched builds
+    run their parts and the per-cluster form their global-scratch bins; with
+    cutting off, batched builds run the global-scratch bins too."""
     m = gen.delaunay_mesh(60000, seed=11, with_field=False)
     canon, rel = oracle.build_all(m.nv, m.tv, m.seg, m.nclusters)
-    with gale.Context.load(m, device=0) as ctx:
-        assert any(b["spill"] for b in ctx.bins())
-        for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
-            ctx.build(None, mask, mode)
-            ctx.synchronize()
-            assert_bulk_equal(ctx.export(mask), expected_bulk(rel, canon, range(m.nclusters), mask))
+    want = expected_bulk(rel, canon, range(m.nclusters), mask)
+    for pv in (0, -1):
+        with gale.Context.load(m, device=0, part_vertices=pv) as ctx:
+            assert any(b["spill"] for b in ctx.bins())
+            assert (ctx.info().nparts > 0) == (pv == 0)
+            for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
+                ctx.build(None, mask, mode)
+                ctx.synchronize()
+                assert_bulk_equal(ctx.export(mask), want)
 
 
 def test_non_manifold_input():
