@@ -212,6 +212,8 @@ constexpr int kMaxBins = 64;
 // estimate exceeds kCutBytes (both overridable at load time).
 constexpr int32_t kPartVertices = 256;
 constexpr int64_t kCutBytes = 160 * 1024;
+// ... and into twice as many parts while some part's estimate exceeds this.
+constexpr int64_t kPartFitBytes = 200 * 1024;
 
 // Kernel launchers (gale_kernels.cu).  All asynchronous on `stream`.
 struct DevMesh {

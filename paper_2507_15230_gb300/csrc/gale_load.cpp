@@ -428,28 +428,141 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
     }
 
     // Clusters whose working set would not fit one CTA's shared memory are
-    // also cut into parts of about part_v own vertices (contiguous ranges),
-    // whose working sets do; batched builds run the parts, each on its own
-    // CTA, instead of the cluster.
+    // also cut into parts of about part_v own vertices (contiguous ranges);
+    // batched builds run the parts, each on its own CTA, instead of the
+    // cluster.  A cluster whose parts would still not fit is cut again into
+    // twice as many.
     const int32_t part_v = d.part_vertices > 0 ? d.part_vertices : kPartVertices;
     const int64_t cut_bytes = d.cut_bytes > 0 ? d.cut_bytes : kCutBytes;
-    hm.part_first.assign(size_t(K) + 1, 0);
-    std::vector<std::array<int32_t, 3>> pr;  // (cluster, first own vertex, end)
+    std::vector<int32_t> cutk;
     for (int32_t k = 0; k < K; ++k) {
-        hm.part_first[k] = int32_t(pr.size());
         const ClusterStat &s = hm.stats[k];
-        if (d.part_vertices < 0 || s.nv_own < 2 || estimate_smem(s, 512) <= cut_bytes) continue;
-        const int32_t S = std::max(2, (s.nv_own + part_v - 1) / part_v), v0 = hm.I_V[k];
-        for (int32_t j = 0; j < S; ++j)
-            pr.push_back({k, v0 + int32_t(int64_t(s.nv_own) * j / S), v0 + int32_t(int64_t(s.nv_own) * (j + 1) / S)});
+        if (d.part_vertices >= 0 && s.nv_own >= 2 && estimate_smem(s, 512) > cut_bytes) cutk.push_back(k);
     }
-    hm.part_first[K] = int32_t(pr.size());
-    const int32_t NP = int32_t(pr.size());
+    struct PartBuild {
+        int32_t a0 = 0, a1 = 0, n_rows = 0;
+        std::vector<int32_t> ext, in, halo, vm;
+        ClusterStat s{};
+    };
+    std::vector<std::vector<PartBuild>> built(cutk.size());
+    std::atomic<int64_t> bad_p{-1};
+    // part [a0, a1) of cluster k: its working set and block facts
+    auto make_part = [&](int32_t k, int32_t a0, int32_t a1, int32_t part_tag, PartBuild &pb) -> bool {
+        pb = PartBuild{};
+        pb.a0 = a0;
+        pb.a1 = a1;
+        auto touches = [&](int32_t t) {
+            const int32_t *r = rows + 4 * int64_t(t);
+            return (r[0] >= a0 && r[0] < a1) || (r[1] >= a0 && r[1] < a1) || (r[2] >= a0 && r[2] < a1) ||
+                   (r[3] >= a0 && r[3] < a1);
+        };
+        for (int64_t i = hm.ext_off[k]; i < hm.ext_off[k + 1]; ++i)
+            if (touches(hm.ext[i])) pb.ext.push_back(hm.ext[i]);
+        for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t)
+            if (touches(t)) {
+                pb.in.push_back(t);
+                const int32_t *r = rows + 4 * int64_t(t);
+                pb.n_rows += (r[0] >= a0 && r[0] < a1);
+            }
+        if (want_tt) {
+            // tets across the face (b, c, d) of a row's tet (a, b, c, d) when
+            // that face has no vertex in the part and they have none either
+            for (int32_t t : pb.in) {
+                const int32_t *r = rows + 4 * int64_t(t);
+                if (r[0] < a0 || r[0] >= a1 || r[1] < a1) continue;
+                const int32_t b = r[1], c = r[2], dd = r[3];
+                for (int64_t q = vs_off[b]; q < vs_off[b + 1]; ++q) {
+                    const int32_t u = order[q] >> 2;
+                    if (u == t) continue;
+                    const int32_t *ru = rows + 4 * int64_t(u);
+                    bool hc = false, hd = false, inp = false;
+                    for (int j = 0; j < 4; ++j) {
+                        hc |= ru[j] == c;
+                        hd |= ru[j] == dd;
+                        inp |= ru[j] >= a0 && ru[j] < a1;
+                    }
+                    if (hc && hd && !inp) pb.halo.push_back(u);
+                }
+            }
+            std::sort(pb.halo.begin(), pb.halo.end());
+            pb.halo.erase(std::unique(pb.halo.begin(), pb.halo.end()), pb.halo.end());
+        }
+        WSet w;
+        w.v0 = a0;
+        w.v1 = a1;
+        w.ext = pb.ext.data();
+        w.n_ext = int64_t(pb.ext.size());
+        w.ilist = pb.in.data();
+        w.n_int = int64_t(pb.in.size());
+        w.halo = pb.halo.data();
+        w.n_halo = int64_t(pb.halo.size());
+        w.part = part_tag;
+        w.t_base = hm.I_T[k];
+        return ws_scan(w, pb.s, pb.vm) == 0;
+    };
+    parallel_dynamic(int64_t(cutk.size()), P, 1, [&](int64_t i, int) {
+        const int32_t k = cutk[i], v0 = hm.I_V[k], nvo = hm.stats[k].nv_own;
+        int32_t S = std::max(2, (nvo + part_v - 1) / part_v);
+        for (;;) {
+            std::vector<PartBuild> &pbs = built[i];
+            pbs.assign(size_t(S), PartBuild{});
+            bool fit = true;
+            for (int32_t j = 0; j < S; ++j) {
+                const int32_t a0 = v0 + int32_t(int64_t(nvo) * j / S), a1 = v0 + int32_t(int64_t(nvo) * (j + 1) / S);
+                if (!make_part(k, a0, a1, 1, pbs[j])) {
+                    bad_p = k;
+                    return;
+                }
+                fit &= estimate_smem(pbs[j].s, 512) <= kPartFitBytes;
+            }
+            if (fit || S >= nvo) break;
+            S = std::min(nvo, 2 * S);
+        }
+    });
+    if (bad_p >= 0) {
+        err = "a part of cluster " + std::to_string(bad_p.load()) + " has too large a working set";
+        return false;
+    }
+    // parts numbered cluster by cluster, in vertex order
+    hm.part_first.assign(size_t(K) + 1, 0);
+    int32_t NP = 0;
+    {
+        size_t c = 0;
+        for (int32_t k = 0; k < K; ++k) {
+            hm.part_first[k] = NP;
+            if (c < cutk.size() && cutk[c] == k) NP += int32_t(built[c++].size());
+        }
+        hm.part_first[K] = NP;
+    }
     hm.NP = NP;
     hm.parts.assign(size_t(NP), PartInfo{});
     hm.stats.resize(size_t(K) + NP);
     vmaps.resize(size_t(K) + NP);
     std::vector<std::vector<int32_t>> pext(NP), pint(NP), phalo(NP);
+    std::vector<std::array<int32_t, 3>> pr(NP);  // (cluster, first own vertex, end)
+    for (size_t c = 0; c < cutk.size(); ++c) {
+        const int32_t k = cutk[c];
+        for (size_t j = 0; j < built[c].size(); ++j) {
+            PartBuild &pb = built[c][j];
+            const int32_t p = hm.part_first[k] + int32_t(j);
+            pr[p] = {k, pb.a0, pb.a1};
+            pb.s.xmap = pb.s.n_own;
+            hm.stats[size_t(K) + p] = pb.s;
+            vmaps[size_t(K) + p].swap(pb.vm);
+            pext[p].swap(pb.ext);
+            pint[p].swap(pb.in);
+            phalo[p].swap(pb.halo);
+            PartInfo &pi = hm.parts[p];
+            pi.k = k;
+            pi.x0 = pb.a0 - hm.I_V[k];
+            pi.nvo = pb.a1 - pb.a0;
+            pi.last = j + 1 == built[c].size() ? 1 : 0;
+            pi.n_rows = pb.n_rows;
+            pi.n_own_c = hm.I_T[k + 1] - hm.I_T[k];
+            pi.t_base_c = hm.I_T[k];
+        }
+    }
+    std::vector<std::vector<PartBuild>>().swap(built);
     auto part_set = [&](int32_t p) {
         WSet w;
         w.v0 = pr[p][1];
@@ -464,61 +577,6 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         w.t_base = hm.I_T[pr[p][0]];
         return w;
     };
-    std::atomic<int64_t> bad_p{-1};
-    parallel_dynamic(NP, P, 4, [&](int64_t p, int) {
-        const int32_t k = pr[p][0], a0 = pr[p][1], a1 = pr[p][2];
-        auto touches = [&](int32_t t) {
-            const int32_t *r = rows + 4 * int64_t(t);
-            return (r[0] >= a0 && r[0] < a1) || (r[1] >= a0 && r[1] < a1) || (r[2] >= a0 && r[2] < a1) ||
-                   (r[3] >= a0 && r[3] < a1);
-        };
-        for (int64_t i = hm.ext_off[k]; i < hm.ext_off[k + 1]; ++i)
-            if (touches(hm.ext[i])) pext[p].push_back(hm.ext[i]);
-        int32_t n_rows = 0;
-        for (int32_t t = hm.I_T[k]; t < hm.I_T[k + 1]; ++t)
-            if (touches(t)) {
-                pint[p].push_back(t);
-                const int32_t *r = rows + 4 * int64_t(t);
-                n_rows += (r[0] >= a0 && r[0] < a1);
-            }
-        if (want_tt) {
-            // tets across the face (b, c, d) of a row's tet (a, b, c, d) when
-            // that face has no vertex in the part and they have none either
-            std::vector<int32_t> &hp = phalo[p];
-            for (int32_t t : pint[p]) {
-                const int32_t *r = rows + 4 * int64_t(t);
-                if (r[0] < a0 || r[0] >= a1 || r[1] < a1) continue;
-                const int32_t b = r[1], c = r[2], dd = r[3];
-                for (int64_t q = vs_off[b]; q < vs_off[b + 1]; ++q) {
-                    const int32_t u = order[q] >> 2;
-                    if (u == t) continue;
-                    const int32_t *ru = rows + 4 * int64_t(u);
-                    bool hc = false, hd = false, inp = false;
-                    for (int j = 0; j < 4; ++j) {
-                        hc |= ru[j] == c;
-                        hd |= ru[j] == dd;
-                        inp |= ru[j] >= a0 && ru[j] < a1;
-                    }
-                    if (hc && hd && !inp) hp.push_back(u);
-                }
-            }
-            std::sort(hp.begin(), hp.end());
-            hp.erase(std::unique(hp.begin(), hp.end()), hp.end());
-        }
-        if (ws_scan(part_set(int32_t(p)), hm.stats[size_t(K) + p], vmaps[size_t(K) + p]) != 0) bad_p = p;
-        PartInfo &pi = hm.parts[p];
-        pi.k = k;
-        pi.x0 = a0 - hm.I_V[k];
-        pi.nvo = a1 - a0;
-        pi.last = int32_t(p) + 1 == hm.part_first[k + 1] ? 1 : 0;
-        pi.n_rows = n_rows;
-        pi.n_own_c = hm.I_T[k + 1] - hm.I_T[k];
-        pi.t_base_c = hm.I_T[k];
-    });
-    if (bad_p >= 0) {
-        err = "a part of cluster " + std::to_string(pr[bad_p][0]) + " has too large a working set";
-        return false;
-    }
     std::vector<int32_t>().swap(order);
     std::vector<int64_t>().swap(vs_off);
 
