@@ -792,9 +792,10 @@ def torch_sm_count() -> int:
 
 def coboundary_leg(args, gale, gen):
     """VE, VF, EF, FT (gale_build_coboundary) on a grid of the same recipe,
-    in sorted enumeration ids: device time of the whole pass (the VT + VV
-    build it starts with, the count and fill kernels), output bytes over that
-    time against the HBM copy peak, and the oracle timed on a 12^3 sample."""
+    in sorted enumeration ids: device time of the whole pass (count, scan,
+    fill and row-sort kernels over the enumeration and the tet rows), output
+    bytes over that time against the HBM copy peak, and the oracle timed on a
+    12^3 sample."""
     import torch
     n = args.coboundary_grid
     mesh = gen.freudenthal_mesh(n, 512, seed=3, field_seed=4, jitter=0.3, with_field=False)
@@ -836,8 +837,8 @@ def gradient_leg(args, gale, gen):
     """The discrete gradient of a Gaussian-mixture field on a grid of the
     same recipe (Section 5.1, DiscreteGradient): wall time of each step -
     the enumeration with its lists fetched into host arrays, VE + VF on the
-    GPU (with the VT + VV + ET build the pass starts with) and their copy to
-    the host, the VT export with the TV rows, and the consumer threads
+    GPU and their copy to the host, the VT build and export with the TV
+    rows, and the consumer threads
     (which answer FE / TF themselves) - and the oracle on an 8^3 sample."""
     import torch
     import consumers
@@ -860,6 +861,8 @@ def gradient_leg(args, gale, gen):
         t["ve_vf_gpu_and_copy_s"] = time.perf_counter() - t0
         t0 = time.perf_counter()
         I_V, _, _ = c.intervals()
+        c.build(None, gale.VT, gale.MODE_BATCHED)
+        c.synchronize()
         b = c.export(gale.VT)
         vt = consumers.csr_from_bulk(b["vt_off"], b["vt_val"], I_V)
         rows = c.rows()

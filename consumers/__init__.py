@@ -190,14 +190,16 @@ def lower_stars_into(out, f_c, inid_c, v_begin, v_end, ve, vf, vt, ev, fv, tv):
 def gather_gradient_relations(ctx, order=None):
     """The relations the discrete gradient reads, from a loaded context:
     the enumeration (gale_enumerate), VE and VF from the GPU coboundary pass,
-    VT from the bulk build that pass leaves behind, and TV.  (FE and TF are
-    looked up by the consumer itself.)  Returns a dict of host arrays."""
+    VT from a batched build, and TV.  (FE and TF are looked up by the
+    consumer itself.)  Returns a dict of host arrays."""
     import paper_2507_15230_gb300 as gale
     en = ctx.enumerate(order) if order is not None else None
     cb = ctx.coboundary(gale.CB_VE | gale.CB_VF)
     if en is None:
         en = ctx.enumeration()
     I_V, _, _ = ctx.intervals()
+    ctx.build(None, gale.VT, gale.MODE_BATCHED)
+    ctx.synchronize()
     b = ctx.export(gale.VT)
     vt = csr_from_bulk(b["vt_off"], b["vt_val"], I_V)
     rows = ctx.rows()

@@ -439,16 +439,20 @@ gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, i
  *   GALE_CB_VF  rows = vertices: the triangles containing v
  *   GALE_CB_EF  rows = edges (enumeration ids): the triangles containing e
  *   GALE_CB_FT  rows = triangles: the canonical tets containing f
- * The pass first builds VT, VV and ET of every cluster (the bulk arrays are
- * replaced): an edge's tets are its ET row, since the sorted edge order of a
- * segment is the order of its cluster's ET rows.  Edges and triangles are
- * found through a per-vertex index of the enumeration in vertex-tuple order,
- * built on the device once per enumeration.  out receives, per relation in
- * the order VE, VF, EF, FT, the row count, the value count and DEVICE
+ * The pass reads only the enumeration and the canonical tet rows (the bulk
+ * arrays are left alone).  In vertex-tuple order a row's entries come as one
+ * contiguous range (VE(v): the edges with lower vertex v; EF(e): the
+ * triangles whose first two vertices are e; VF(v): the triangles with lowest
+ * vertex v) and the rest scattered from the simplices that hold the row's
+ * simplex elsewhere (edge (a, b) into VE(b); triangle (a, b, c) into
+ * EF(a, c), EF(b, c), VF(b), VF(c); a tet into FT of its faces), found
+ * through a per-vertex index of the enumeration built on the device once per
+ * enumeration; every row is then sorted by id.  out receives, per relation
+ * in the order VE, VF, EF, FT, the row count, the value count and DEVICE
  * pointers to int32 offsets[rows+1] and values, library-owned and valid
- * until the next call or gale_destroy.  EINVAL if VT, VV and ET are not all
- * in the precondition mask or the enumeration has 2^31 or more edges or
- * triangles, ENOTFOUND before gale_enumerate, EDEVICE if a lookup failed. */
+ * until the next call or gale_destroy.  EINVAL if the enumeration has 2^31
+ * or more edges or triangles (or a relation 2^31 or more entries), ENOTFOUND
+ * before gale_enumerate, EDEVICE if a lookup failed. */
 enum { GALE_CB_VE = 1, GALE_CB_VF = 2, GALE_CB_EF = 4, GALE_CB_FT = 8 };
 typedef struct {
     int64_t rows[4];

@@ -56,13 +56,13 @@ struct Cobound {
     int32_t *eo = nullptr, *ekw = nullptr, *feo = nullptr, *fkc = nullptr, *fo = nullptr;
     int32_t *e2s = nullptr, *f2s = nullptr;
     bool sorted_ids = false;
-    int64_t *base = nullptr;       // [K][10] bulk bases of every cluster's arrays
+
     int32_t *cnt = nullptr;        // counts of the largest relation
     int64_t *bsum = nullptr;       // scan block sums
     int64_t cnt_cap = 0, bsum_cap = 0;
     int32_t *off[4] = {}, *val[4] = {};
-    int32_t *ef_third = nullptr;   // per EF entry: the triangle's vertex off the edge
-    int64_t ef_third_cap = 0;
+    int32_t *scratch = nullptr;    // counters and lookups of the scatter passes
+    int64_t scratch_cap = 0;
     int64_t off_cap[4] = {}, val_cap[4] = {};
     int64_t rows_of[4] = {}, len[4] = {};
 };
@@ -85,28 +85,14 @@ struct CbMesh {
     const int32_t *E, *F, *ebk, *fbk;
     const int64_t *IE, *IF;
     const int32_t *eo, *ekw, *feo, *fkc, *e2s, *f2s;
-    const int32_t *vt_off, *vt_val, *vv_off, *vv_val, *et_w, *et_off, *et_val;
-    const int32_t *et_uoff;          // ET edges per own lower vertex (the sorted enumeration reads it)
-    const int32_t *ef_off, *ef_val;  // EF, once built (VF is read from it)
-    const int32_t *ve_off, *ve_val;  // VE in VV order, once built (VF is read from it)
-    const int32_t *ef_third;         // per EF entry: the triangle's vertex off the edge
-    int32_t *third_out;              // where the EF fill writes those
+    // the ET rows of a batched build (the sorted enumeration reads them)
+    const int32_t *et_w, *et_off, *et_val;
+    const int32_t *et_uoff;          // ET edges per own lower vertex
     const int64_t *base;
     const int64_t *sizes;  // [K][5] per-cluster entries: VT, VV, edges, ET, TT
     int64_t nv, nE, nF;
     bool sorted_ids;
 };
-
-// [b, e) of vertex v's row of a per-own-vertex bulk relation (VT or VV)
-__device__ __forceinline__ void vrow(const CbMesh &m, int32_t v, bool vv, int64_t &b, int64_t &e) {
-    const int32_t k = m.cluster_of[v];
-    const int32_t i = v - m.I_V[k];
-    const int32_t *off = vv ? m.vv_off : m.vt_off;
-    const int64_t *B = m.base + 10 * int64_t(k);
-    const int64_t ob = B[vv ? B_VV_OFF : B_VT_OFF], vb = B[vv ? B_VV_VAL : B_VT_VAL];
-    b = vb + off[ob + i];
-    e = vb + off[ob + i + 1];
-}
 
 __device__ __forceinline__ bool has4(const int4 r, int32_t x) { return r.x == x || r.y == x || r.z == x || r.w == x; }
 
@@ -135,12 +121,6 @@ __device__ int64_t fpos_at(const CbMesh &m, int64_t j, int32_t c) {
     return -1;
 }
 
-// sorted position of triangle (a, b, c), a < b < c, or -1
-__device__ int64_t fpos(const CbMesh &m, int32_t a, int32_t b, int32_t c) {
-    const int64_t j = epos(m, a, b);
-    return j < 0 ? -1 : fpos_at(m, j, c);
-}
-
 __device__ __forceinline__ void sort3(int32_t &a, int32_t &b, int32_t &c) {
     if (a > b) { const int32_t t = a; a = b; b = t; }
     if (b > c) { const int32_t t = b; b = c; c = t; }
@@ -163,197 +143,294 @@ __device__ bool et_row(const CbMesh &m, int64_t j, int32_t a, int32_t w, int64_t
 __device__ __forceinline__ int32_t edge_id(const CbMesh &m, int64_t j) { return m.sorted_ids ? int32_t(j) : m.ebk[j]; }
 __device__ __forceinline__ int32_t face_id(const CbMesh &m, int64_t p) { return m.sorted_ids ? int32_t(p) : m.fbk[p]; }
 
-// One row of relation REL: count (out == nullptr) or write its entries (at
-// most cap of them; the count is returned either way).
-template <int REL>
-__device__ int32_t row_entries(const CbMesh &m, int64_t row, int32_t *out, int32_t cap, int32_t *aux,
-                               int32_t *err) {
-    int32_t n = 0;
-    if (REL == REL_VE) {
-        const int32_t v = int32_t(row);
-        int64_t b, e;
-        vrow(m, v, true, b, e);
-        if (!out) return int32_t(e - b);
-        for (int64_t j = b; j < e; ++j) {
-            const int32_t w = m.vv_val[j];
-            const int64_t p = v < w ? epos(m, v, w) : epos(m, w, v);
-            if (p < 0) atomicOr(err, ERR_BAD_BLOCK);
-            if (n < cap) out[n] = p < 0 ? -1 : edge_id(m, p);
-            ++n;
-        }
-    } else if (REL == REL_VF) {
-        // every triangle through v has exactly two edges through v: take it
-        // from the one to its smaller other vertex.  With x ascending and
-        // EF rows ordered by third vertex, the sorted numbering's ids come
-        // out ascending.
-        // VE(v) is still in VV(v)'s order here: entry i is the edge to the
-        // i-th neighbour
-        const int32_t v = int32_t(row);
-        int64_t b, e;
-        vrow(m, v, true, b, e);
-        const int64_t vb = m.ve_off[v];
-        if (m.ve_off[v + 1] - vb != e - b) {
-            atomicOr(err, ERR_BAD_BLOCK);
-            return 0;
-        }
-        for (int64_t j = b; j < e; ++j) {
-            const int32_t x = m.vv_val[j];
-            const int32_t id = m.ve_val[vb + (j - b)];
-            if (id < 0) {
-                atomicOr(err, ERR_BAD_BLOCK);
-                return n;
-            }
-            const int32_t fb = m.ef_off[id], fe = m.ef_off[id + 1];
-            if (!out) {
-                n += fe - fb;  // halved below: each triangle is met twice
-                continue;
-            }
-            for (int32_t q = fb; q < fe; ++q)
-                if (m.ef_third[q] > x) {
-                    if (n < cap) out[n] = m.ef_val[q];
-                    ++n;
-                }
-        }
-        if (!out) n >>= 1;
-    } else if (REL == REL_EF) {
-        // the third vertices of the tets around e, sorted and deduplicated:
-        // with the sorted numbering, ascending third vertex is ascending id
-        const int64_t js = m.sorted_ids ? row : m.e2s[row];
-        const int32_t u = m.E[2 * row], w = m.E[2 * row + 1];
-        int64_t eb, ee;
-        if (!et_row(m, js, u, w, eb, ee)) {
-            atomicOr(err, ERR_BAD_BLOCK);
-            return 0;
-        }
-        constexpr int kCand = 32;
-        if (ee - eb <= kCand / 2) {
-            int32_t xs[kCand];
-            int c = 0;
-            for (int64_t j = eb; j < ee; ++j) {
-                const int4 r = m.rows[m.et_val[j]];
-#pragma unroll
-                for (int s2 = 0; s2 < 4; ++s2) {
-                    const int32_t x = s2 == 0 ? r.x : s2 == 1 ? r.y : s2 == 2 ? r.z : r.w;
-                    if (x == u || x == w || c >= kCand) continue;
-                    int q = c++;
-                    while (q > 0 && xs[q - 1] > x) {
-                        xs[q] = xs[q - 1];
-                        --q;
-                    }
-                    xs[q] = x;
-                }
-            }
-            for (int q = 0; q < c; ++q) {
-                if (q > 0 && xs[q] == xs[q - 1]) continue;
-                if (out && n < cap) {
-                    const int32_t x = xs[q];
-                    int64_t p;
-                    if (x > w) {
-                        p = fpos_at(m, js, x);  // (u, w, x): over this edge
-                    } else {
-                        int32_t a = u, bb = w, cc = x;
-                        sort3(a, bb, cc);
-                        p = fpos(m, a, bb, cc);
-                    }
-                    if (p < 0) atomicOr(err, ERR_BAD_BLOCK);
-                    out[n] = p < 0 ? -1 : face_id(m, p);
-                    if (aux) aux[n] = x;
-                }
-                ++n;
-            }
-            return n;
-        }
-        // many tets around the edge: first-occurrence test over the row
-        for (int64_t j = eb; j < ee; ++j) {
-            const int4 r = m.rows[m.et_val[j]];
-#pragma unroll
-            for (int s2 = 0; s2 < 4; ++s2) {
-                const int32_t x = s2 == 0 ? r.x : s2 == 1 ? r.y : s2 == 2 ? r.z : r.w;
-                if (x == u || x == w) continue;
-                bool first = true;
-                for (int64_t jj = eb; jj < j && first; ++jj) first = !has4(m.rows[m.et_val[jj]], x);
-                if (!first) continue;
-                if (out && n < cap) {
-                    int32_t a = u, bb = w, cc = x;
-                    sort3(a, bb, cc);
-                    const int64_t p = fpos(m, a, bb, cc);
-                    if (p < 0) atomicOr(err, ERR_BAD_BLOCK);
-                    out[n] = p < 0 ? -1 : face_id(m, p);
-                    if (aux) aux[n] = x;
-                }
-                ++n;
-            }
-        }
-    } else {
-        const int32_t a = m.F[3 * row], bb = m.F[3 * row + 1], cc = m.F[3 * row + 2];
-        const int64_t je = epos(m, a, bb);
-        int64_t eb, ee;
-        if (je < 0 || !et_row(m, je, a, bb, eb, ee)) {
-            atomicOr(err, ERR_BAD_BLOCK);
-            return 0;
-        }
-        for (int64_t j = eb; j < ee; ++j) {
-            const int32_t t = m.et_val[j];
-            if (has4(m.rows[t], cc)) {
-                if (out && n < cap) out[n] = t;
-                ++n;
-            }
-        }
-    }
-    return n;
-}
+// ---- the relations by scatter, over sorted positions ----
+// Every row is [scattered part | contiguous part].  The contiguous part is a
+// range the vertex-tuple order gives whole: for VE(v) the edges whose lower
+// vertex is v (sorted positions eo[v] ..), for EF(e) the triangles whose
+// first two vertices are e (feo[e] ..), for VF(v) the triangles whose lowest
+// vertex is v (fo[v] ..).  The other entries come from the edges, triangles
+// and tets that hold the row's simplex elsewhere than in front: an edge
+// (a, b) is in VE(b); a triangle (a, b, c) is in EF(a, c), EF(b, c), VF(b)
+// and VF(c); a tet is in FT of its four faces.  They take slots by atomic
+// counters, and a last pass sorts every row by id.  With the sorted
+// numbering the scattered ids all precede the contiguous ones, so only the
+// scattered prefix moves.
 
-template <int REL>
-__global__ void __launch_bounds__(kThreads) cb_count(CbMesh m, int64_t rows, int32_t *cnt, int32_t *err) {
-    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x)
-        cnt[r] = row_entries<REL>(m, r, nullptr, 0, nullptr, err);
-}
+__device__ __forceinline__ int64_t erow(const CbMesh &m, int64_t j) { return m.sorted_ids ? j : m.ebk[j]; }
+__device__ __forceinline__ int64_t frow(const CbMesh &m, int64_t p) { return m.sorted_ids ? p : m.fbk[p]; }
 
-template <int REL>
-__global__ void __launch_bounds__(kThreads) cb_fill(CbMesh m, int64_t rows, const int32_t *off, int32_t *val,
-                                                    int32_t *err) {
-    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
-        int32_t *o = val + off[r];
-        const int32_t len = off[r + 1] - off[r];
-        int32_t *ax = REL == REL_EF ? m.third_out + off[r] : nullptr;
-        const int32_t n = row_entries<REL>(m, r, o, len, ax, err);
-        if (n != len) {
-            atomicOr(err, ERR_BAD_BLOCK);
+struct Scatter {
+    int32_t *ve_n, *ve_fill;               // [nv] lower edges of v, and the cursor of their slots
+    int32_t *ef_lo, *ef_mid;               // [nE] (sorted positions) triangles (x, u, w), x < u, and
+                                           // (u, x, w), u < x < w, of edge (u, w)
+    int32_t *ef_lofill, *ef_midfill;       // [nE] cursors of their slots
+    int32_t *vf_n, *vf_fill;               // [nv] triangles with v as second or third vertex; cursor
+    int32_t *ft_fill;                      // [nF] (sorted positions) cursors of FT's slots
+    int32_t *tri_ac, *tri_bc;              // [nF] sorted positions of the edges (a, c), (b, c) of triangle p
+    int4 *tet_f;                           // [nT] sorted positions of a tet's faces abc, abd, acd, bcd
+    int2 *ef_tail;                         // [nE] (sorted numbering, VF gather) EF(j) after its lower part
+    int32_t *cnt;                          // row lengths of the relation being placed
+    const int32_t *ve_off, *ef_off, *vf_off, *ft_off;
+    int32_t *ve_val, *ef_val, *vf_val, *ft_val;
+};
+
+// edges: VE(b) of every edge (a, b); FILL also writes the contiguous parts
+template <bool FILL>
+__global__ void __launch_bounds__(kThreads) k_sc_edges(CbMesh m, Scatter sc, int32_t *err) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < m.nE; j += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t id = edge_id(m, j);
+        const int32_t a = m.E[2 * int64_t(id)], b = m.E[2 * int64_t(id) + 1];
+        if (!FILL) {
+            atomicAdd(&sc.ve_n[b], 1);
             continue;
         }
-        // VE stays in VV order until VF has read it (cb_sort_rows sorts it)
-        const bool need_sort = REL == REL_VF || REL == REL_EF;
-        if (need_sort)  // ids found by lookup: sort the row (insertion sort)
-            for (int32_t i = 1; i < n; ++i) {
-                const int32_t x = o[i];
-                const int32_t y = ax ? ax[i] : 0;
-                int32_t j = i - 1;
-                while (j >= 0 && o[j] > x) {
-                    o[j + 1] = o[j];
-                    if (ax) ax[j + 1] = ax[j];
-                    --j;
-                }
-                o[j + 1] = x;
-                if (ax) ax[j + 1] = y;
-            }
+        sc.ve_val[sc.ve_off[a] + sc.ve_n[a] + (j - m.eo[a])] = id;
+        sc.ve_val[atomicAdd(&sc.ve_fill[b], 1)] = id;
     }
 }
 
-// sort every row of a CSR relation in place (insertion sort; rows are short)
-__global__ void __launch_bounds__(kThreads) cb_sort_rows(int64_t rows, const int32_t *off, int32_t *val) {
-    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
-        int32_t *o = val + off[r];
-        const int32_t n = off[r + 1] - off[r];
-        for (int32_t i = 1; i < n; ++i) {
-            const int32_t x = o[i];
-            int32_t j = i - 1;
-            while (j >= 0 && o[j] > x) {
-                o[j + 1] = o[j];
-                --j;
+// triangles: EF(a, c), EF(b, c), VF(b), VF(c) of every triangle (a, b, c)
+template <bool FILL>
+__global__ void __launch_bounds__(kThreads) k_sc_tris(CbMesh m, Scatter sc, bool ef, bool vf, int32_t *err) {
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < m.nF; p += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t id = face_id(m, p);
+        const int32_t *t = m.F + 3 * int64_t(id);
+        const int32_t b = t[1], c = t[2];
+        if (!FILL) {
+            if (ef) {
+                const int32_t a = t[0];
+                const int64_t jac = epos(m, a, c), jbc = epos(m, b, c);
+                if (jac < 0 || jbc < 0) {
+                    atomicOr(err, ERR_BAD_BLOCK);
+                    sc.tri_ac[p] = sc.tri_bc[p] = -1;
+                } else {
+                    sc.tri_ac[p] = int32_t(jac);
+                    sc.tri_bc[p] = int32_t(jbc);
+                    atomicAdd(&sc.ef_mid[jac], 1);
+                    atomicAdd(&sc.ef_lo[jbc], 1);
+                }
             }
-            o[j + 1] = x;
+            if (vf) {
+                atomicAdd(&sc.vf_n[b], 1);
+                atomicAdd(&sc.vf_n[c], 1);
+            }
+            continue;
+        }
+        if (ef) {
+            const int32_t jac = sc.tri_ac[p], jbc = sc.tri_bc[p];
+            if (jac >= 0 && jbc >= 0) {
+                sc.ef_val[atomicAdd(&sc.ef_midfill[jac], 1)] = id;
+                sc.ef_val[atomicAdd(&sc.ef_lofill[jbc], 1)] = id;
+            }
+        }
+        if (vf) {
+            sc.vf_val[atomicAdd(&sc.vf_fill[b], 1)] = id;
+            sc.vf_val[atomicAdd(&sc.vf_fill[c], 1)] = id;
         }
     }
+}
+// tets: FT of the four faces of every tet (a, b, c, d)
+template <bool FILL>
+__global__ void __launch_bounds__(kThreads) k_sc_tets(CbMesh m, Scatter sc, int64_t nT, int32_t *err) {
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nT; t += int64_t(gridDim.x) * blockDim.x) {
+        int4 f;
+        if (!FILL) {
+            const int4 r = m.rows[t];
+            const int64_t jab = epos(m, r.x, r.y), jac = epos(m, r.x, r.z), jbc = epos(m, r.y, r.z);
+            f.x = jab < 0 ? -1 : int32_t(fpos_at(m, jab, r.z));
+            f.y = jab < 0 ? -1 : int32_t(fpos_at(m, jab, r.w));
+            f.z = jac < 0 ? -1 : int32_t(fpos_at(m, jac, r.w));
+            f.w = jbc < 0 ? -1 : int32_t(fpos_at(m, jbc, r.w));
+            if (f.x < 0 || f.y < 0 || f.z < 0 || f.w < 0) {
+                atomicOr(err, ERR_BAD_BLOCK);
+                f = make_int4(-1, -1, -1, -1);
+            }
+            sc.tet_f[t] = f;
+            if (f.x >= 0) {
+                atomicAdd(&sc.cnt[frow(m, f.x)], 1);
+                atomicAdd(&sc.cnt[frow(m, f.y)], 1);
+                atomicAdd(&sc.cnt[frow(m, f.z)], 1);
+                atomicAdd(&sc.cnt[frow(m, f.w)], 1);
+            }
+            continue;
+        }
+        f = sc.tet_f[t];
+        if (f.x < 0) continue;
+        sc.ft_val[atomicAdd(&sc.ft_fill[f.x], 1)] = int32_t(t);
+        sc.ft_val[atomicAdd(&sc.ft_fill[f.y], 1)] = int32_t(t);
+        sc.ft_val[atomicAdd(&sc.ft_fill[f.z], 1)] = int32_t(t);
+        sc.ft_val[atomicAdd(&sc.ft_fill[f.w], 1)] = int32_t(t);
+    }
+}
+
+// row lengths: scattered part + contiguous part
+__global__ void __launch_bounds__(kThreads) k_len_ve(CbMesh m, Scatter sc) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < m.nv; v += int64_t(gridDim.x) * blockDim.x)
+        sc.cnt[v] = sc.ve_n[v] + (m.eo[v + 1] - m.eo[v]);
+}
+__global__ void __launch_bounds__(kThreads) k_len_vf(CbMesh m, Scatter sc, const int32_t *fo) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < m.nv; v += int64_t(gridDim.x) * blockDim.x)
+        sc.cnt[v] = sc.vf_n[v] + (fo[v + 1] - fo[v]);
+}
+__global__ void __launch_bounds__(kThreads) k_len_ef(CbMesh m, Scatter sc) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < m.nE; j += int64_t(gridDim.x) * blockDim.x)
+        sc.cnt[erow(m, j)] = sc.ef_lo[j] + sc.ef_mid[j] + (m.feo[j + 1] - m.feo[j]);
+}
+
+// Row sorts.  Only a row's first plen entries need ordering: with the
+// sorted numbering the scattered entries all precede (and are smaller than)
+// the contiguous part, so plen is the scattered count; otherwise it is the
+// whole row.
+enum { PL_VE = 0, PL_VF = 1, PL_EF = 2, PL_FULL = 3 };
+__device__ __forceinline__ void insertion_sort(int32_t *o, int32_t n) {
+    for (int32_t i = 1; i < n; ++i) {
+        const int32_t y = o[i];
+        int32_t j = i - 1;
+        while (j >= 0 && o[j] > y) {
+            o[j + 1] = o[j];
+            --j;
+        }
+        o[j + 1] = y;
+    }
+}
+
+// ascending bitonic sort of N values held in registers (all indices are
+// compile-time constants once unrolled)
+template <int N>
+__device__ __forceinline__ void bitonic_regs(int32_t (&x)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int32_t a = x[i], b = x[l];
+                    const bool asc = (i & k) == 0;
+                    x[i] = asc ? min(a, b) : max(a, b);
+                    x[l] = asc ? max(a, b) : min(a, b);
+                }
+            }
+}
+
+// one thread per row: prefixes of up to N entries are sorted in registers,
+// longer ones in place.  A block's rows are one contiguous span of the
+// values: it is staged through shared memory when it fits, so that loads
+// and stores are coalesced.  FRONT writes the row's contiguous part first
+// (EF: the triangles over the edge; VF: the triangles with lowest vertex v).
+enum { FRONT_NONE = 0, FRONT_EF = 1, FRONT_VF = 2 };
+// SPAN: int32 entries of a staged span (0: rows are sorted where they are).
+// With the sorted numbering, EF's sort also records for each edge the range
+// of its entries after the lower part (the VF gather reads them).
+template <int PL, int N, int FRONT, int SPAN>
+__global__ void __launch_bounds__(kThreads) k_sort_rows(CbMesh m, Scatter sc, int64_t rows, const int32_t *off,
+                                                        int32_t *val, const int32_t *fo) {
+    __shared__ int32_t s_val[SPAN > 0 ? SPAN : 1];
+    for (int64_t r0 = int64_t(blockIdx.x) * kThreads; r0 < rows; r0 += int64_t(gridDim.x) * kThreads) {
+        const int64_t r1 = min(rows, r0 + kThreads);
+        const int32_t base = off[r0], span = off[r1] - base;
+        const bool staged = SPAN > 0 && span <= SPAN;
+        if (staged) {
+            for (int32_t u = threadIdx.x; u < span; u += kThreads) s_val[u] = val[base + u];
+            __syncthreads();
+        }
+        const int64_t r = r0 + threadIdx.x;
+        if (r < r1) {
+            int32_t *o = staged ? s_val + (off[r] - base) : val + off[r];
+            const int32_t len = off[r + 1] - off[r];
+            if (FRONT == FRONT_EF) {
+                const int64_t j = m.sorted_ids ? r : m.e2s[r];
+                if (m.sorted_ids && sc.ef_tail) sc.ef_tail[j] = make_int2(off[r] + sc.ef_lo[j], off[r + 1]);
+                int32_t *f = o + sc.ef_lo[j] + sc.ef_mid[j];
+                const int32_t p0 = m.feo[j], p1 = m.feo[j + 1];
+                for (int32_t p = p0; p < p1; ++p) f[p - p0] = face_id(m, p);
+            } else if (FRONT == FRONT_VF) {
+                int32_t *f = o + sc.vf_n[r];
+                const int32_t p0 = fo[r], p1 = fo[r + 1];
+                for (int32_t p = p0; p < p1; ++p) f[p - p0] = face_id(m, p);
+            }
+            int32_t n;
+            if (!m.sorted_ids || PL == PL_FULL) n = len;
+            else if (PL == PL_VE) n = sc.ve_n[r];
+            else if (PL == PL_VF) n = sc.vf_n[r];
+            else n = sc.ef_lo[r] + sc.ef_mid[r];
+            if (n > N) {
+                insertion_sort(o, n);
+            } else if (n >= 2) {
+                int32_t x[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) x[i] = i < n ? o[i] : INT32_MAX;
+                bitonic_regs<N>(x);
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+                    if (i < n) o[i] = x[i];
+            }
+        }
+        if (staged) {
+            __syncthreads();
+            for (int32_t u = threadIdx.x; u < span; u += kThreads) val[base + u] = s_val[u];
+            __syncthreads();
+        }
+    }
+}
+
+// VF with the sorted numbering, from VE and EF (both sorted): the triangles
+// through v whose lowest vertex a is not v are, for the lower edges (a, v)
+// in ascending a, EF(a, v) after its lower part - its middle part (a, x, v)
+// and its contiguous part (a, v, x) - already in id order; the triangles
+// with lowest vertex v follow.
+// counts: edge (a, b) gives VF(b) its middle and contiguous EF entries
+__global__ void __launch_bounds__(kThreads) k_vf_count_sorted(CbMesh m, Scatter sc) {
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < m.nE; j += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t b = m.E[2 * j + 1];  // sorted numbering: edge id j is sorted position j
+        atomicAdd(&sc.vf_n[b], sc.ef_mid[j] + (m.feo[j + 1] - m.feo[j]));
+    }
+}
+constexpr int kGatherSpan = 12288;
+__global__ void __launch_bounds__(kThreads) k_vf_gather(CbMesh m, Scatter sc, const int32_t *fo) {
+    __shared__ int32_t s_val[kGatherSpan];  // the block's rows, stored coalesced
+    for (int64_t v0 = int64_t(blockIdx.x) * kThreads; v0 < m.nv; v0 += int64_t(gridDim.x) * kThreads) {
+        const int64_t v1 = min(m.nv, v0 + kThreads);
+        const int32_t base = sc.vf_off[v0], span = sc.vf_off[v1] - base;
+        const bool staged = span <= kGatherSpan;
+        const int64_t v = v0 + threadIdx.x;
+        if (v < v1) {
+            const int32_t *ve = sc.ve_val + sc.ve_off[v];
+            const int32_t nl = sc.ve_n[v];
+            int32_t *o = staged ? s_val + (sc.vf_off[v] - base) : sc.vf_val + sc.vf_off[v];
+            for (int32_t q = 0; q < nl; ++q) {
+                const int2 t = sc.ef_tail[ve[q]];
+                for (int32_t i = t.x; i < t.y; ++i) *o++ = sc.ef_val[i];
+            }
+            const int32_t p0 = fo[v], p1 = fo[v + 1];
+            for (int32_t p = p0; p < p1; ++p) *o++ = p;
+        }
+        if (staged) {
+            __syncthreads();
+            for (int32_t u = threadIdx.x; u < span; u += kThreads) sc.vf_val[base + u] = s_val[u];
+            __syncthreads();
+        }
+    }
+}
+
+// fill cursors: every scattered part's first slot, so that a scatter is
+// one atomic and one store
+__global__ void __launch_bounds__(kThreads) k_cursors(CbMesh m, Scatter sc, bool ve, bool vf, bool ef, bool ft) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int64_t v = t0; v < m.nv; v += stride) {
+        if (ve) sc.ve_fill[v] = sc.ve_off[v];
+        if (vf) sc.vf_fill[v] = sc.vf_off[v];
+    }
+    if (ef)
+        for (int64_t j = t0; j < m.nE; j += stride) {
+            const int32_t o = sc.ef_off[erow(m, j)];
+            sc.ef_lofill[j] = o;
+            sc.ef_midfill[j] = o + sc.ef_lo[j];
+        }
+    if (ft)
+        for (int64_t p = t0; p < m.nF; p += stride) sc.ft_fill[p] = sc.ft_off[frow(m, p)];
 }
 
 // ---- sorted enumeration on the device ----
@@ -524,63 +601,98 @@ __global__ void __launch_bounds__(kThreads) k_feo(CbMesh m, const int32_t *fo, i
     }
 }
 
-// exclusive scan of cnt[0..n) into off[0..n]: block sums, one pass over the
-// block sums, then the per-block scans
-__global__ void __launch_bounds__(kThreads) scan_sums(const int32_t *cnt, int64_t n, int64_t *bsum) {
-    __shared__ int64_t s[kThreads];
-    const int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    s[threadIdx.x] = i < n ? cnt[i] : 0;
-    __syncthreads();
-    for (int o = kThreads / 2; o > 0; o >>= 1) {
-        if (int(threadIdx.x) < o) s[threadIdx.x] += s[threadIdx.x + o];
-        __syncthreads();
+// exclusive scan of cnt[0..n) into off[0..n], in tiles of kScanTile counts
+// (kScanItems consecutive ones per thread): tile sums, one pass over the
+// tile sums, then the per-tile scans
+constexpr int kScanItems = 16;
+constexpr int64_t kScanTile = int64_t(kThreads) * kScanItems;
+inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+// the sum of a thread's kScanItems counts, from i0
+__device__ __forceinline__ int64_t items_sum(const int32_t *cnt, int64_t n, int64_t i0) {
+    int64_t t = 0;
+    if (i0 + kScanItems <= n && (i0 & 3) == 0) {
+        const int4 *q = reinterpret_cast<const int4 *>(cnt + i0);
+#pragma unroll
+        for (int u = 0; u < kScanItems / 4; ++u) {
+            const int4 v = q[u];
+            t += int64_t(v.x) + v.y + v.z + v.w;
+        }
+    } else {
+        for (int64_t i = i0; i < min(n, i0 + kScanItems); ++i) t += cnt[i];
     }
-    if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
+    return t;
 }
 
-// exclusive scan of the nb block sums in place (bsum[nb] = total), one
+// block-wide inclusive scan of one int64 per thread
+__device__ __forceinline__ int64_t block_incl_scan(int64_t x, int64_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < kThreads / 32 ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    return x + (warp > 0 ? s_warp[warp - 1] : 0);
+}
+
+__global__ void __launch_bounds__(kThreads) scan_sums(const int32_t *cnt, int64_t n, int64_t *bsum) {
+    __shared__ int64_t s_warp[kThreads / 32];
+    const int64_t i0 = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
+    const int64_t tot = block_incl_scan(items_sum(cnt, n, i0), s_warp);
+    if (threadIdx.x == kThreads - 1) bsum[blockIdx.x] = tot;
+}
+
+// exclusive scan of the nb tile sums in place (bsum[nb] = total), one
 // block: each thread sums a contiguous chunk, the chunk totals are scanned,
 // then each thread rewrites its chunk
 __global__ void __launch_bounds__(kThreads) scan_bsums(int64_t *bsum, int64_t nb) {
-    __shared__ int64_t s[kThreads];
+    __shared__ int64_t s_warp[kThreads / 32];
     const int64_t per = (nb + kThreads - 1) / kThreads;
     const int64_t b0 = min(nb, int64_t(threadIdx.x) * per), b1 = min(nb, b0 + per);
     int64_t sum = 0;
     for (int64_t b = b0; b < b1; ++b) sum += bsum[b];
-    s[threadIdx.x] = sum;
-    __syncthreads();
-    for (int o = 1; o < kThreads; o <<= 1) {
-        const int64_t y = int(threadIdx.x) >= o ? s[threadIdx.x - o] : 0;
-        __syncthreads();
-        s[threadIdx.x] += y;
-        __syncthreads();
-    }
-    int64_t run = s[threadIdx.x] - sum;
+    const int64_t incl = block_incl_scan(sum, s_warp);
+    int64_t run = incl - sum;
     for (int64_t b = b0; b < b1; ++b) {
         const int64_t x = bsum[b];
         bsum[b] = run;
         run += x;
     }
-    if (threadIdx.x == kThreads - 1) bsum[nb] = s[kThreads - 1];
+    if (threadIdx.x == kThreads - 1) bsum[nb] = incl;
 }
 
 __global__ void __launch_bounds__(kThreads) scan_write(const int32_t *cnt, int64_t n, const int64_t *bsum,
                                                        int32_t *off, int64_t nb, int32_t *err) {
-    __shared__ int64_t s[kThreads];
-    const int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-    const int64_t x = i < n ? cnt[i] : 0;
-    s[threadIdx.x] = x;
-    __syncthreads();
-    for (int o = 1; o < kThreads; o <<= 1) {
-        const int64_t y = int(threadIdx.x) >= o ? s[threadIdx.x - o] : 0;
-        __syncthreads();
-        s[threadIdx.x] += y;
-        __syncthreads();
+    __shared__ int64_t s_warp[kThreads / 32];
+    __shared__ int32_t s_out[kScanTile];  // the tile's offsets, stored coalesced
+    const int64_t t0 = int64_t(blockIdx.x) * kScanTile;
+    const int64_t i0 = t0 + int64_t(threadIdx.x) * kScanItems;
+    const int64_t mine = items_sum(cnt, n, i0);
+    int64_t run = bsum[blockIdx.x] + block_incl_scan(mine, s_warp) - mine;
+    bool big = false;
+    for (int u = 0; u < kScanItems; ++u) {
+        const int64_t i = i0 + u;
+        big |= run > INT32_MAX;
+        s_out[threadIdx.x * kScanItems + u] = int32_t(run);
+        if (i < n) run += cnt[i];
     }
-    const int64_t ex = bsum[blockIdx.x] + s[threadIdx.x] - x;
-    if (ex > INT32_MAX) atomicOr(err, ERR_CAPACITY);
-    if (i < n) off[i] = int32_t(ex);
-    if (i == 0) {
+    if (big) atomicOr(err, ERR_CAPACITY);
+    __syncthreads();
+    const int64_t m = min(kScanTile, n - t0);
+    for (int64_t u = threadIdx.x; u < m; u += kThreads) off[t0 + u] = s_out[u];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t tot = bsum[nb];
         if (tot > INT32_MAX) atomicOr(err, ERR_CAPACITY);
         off[n] = int32_t(tot);
@@ -665,7 +777,7 @@ gale_status enumerate_sorted_device(gale_ctx *ctx, uint64_t gen, std::vector<int
     int32_t *d_nf = static_cast<int32_t *>(dal(size_t(nE) * 4 + 4));
     int32_t *d_FS = static_cast<int32_t *>(dal((size_t(nE) + 1) * 4));
     int64_t *d_IF = static_cast<int64_t *>(dal((size_t(K) + 1) * 8));
-    const int64_t nb = (nE + kThreads - 1) / kThreads;
+    const int64_t nb = scan_tiles(nE);
     int64_t *d_bsum = static_cast<int64_t *>(dal((size_t(nb) + 1) * 8));
     if (!d_base || !d_IE || !d_E || !d_nf || !d_FS || !d_IF || !d_bsum) {
         release();
@@ -765,17 +877,11 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
     if (which == 0 || (which & ~uint32_t(GALE_CB_VE | GALE_CB_VF | GALE_CB_EF | GALE_CB_FT)))
         return fail(GALE_EINVAL, "which must be a non-empty set of GALE_CB_* bits");
-    const uint32_t need = GALE_VT | GALE_VV | GALE_ET;
-    if ((ctx->precond & need) != need)
-        return fail(GALE_EINVAL, "coboundary relations need VT, VV and ET in the precondition mask");
     EnumView ev{};
     if (!enumeration_view(ctx, &ev)) return fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
     const int64_t nE = ev.nE, nF = ev.nF;
     const uint64_t gen = ev.gen;
     if (nE >= INT32_MAX || nF >= INT32_MAX) return fail(GALE_EINVAL, "more than 2^31 - 1 edges or triangles");
-    // the stars, neighbour sets and edge stars of every vertex
-    gale_status st = gale_build_clusters(ctx, nullptr, 0, need, GALE_MODE_BATCHED);
-    if (st != GALE_OK) return st;
     std::lock_guard<std::mutex> lock(ctx->mu);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(GALE_ECUDA, "cudaSetDevice");
     cudaStream_t s = ctx->stream;
@@ -788,16 +894,27 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
         cb.cluster_of = upload(ctx, hm.cluster_of, s);
         if (!cb.rows || !cb.cluster_of) return fail(GALE_ENOMEM, "device allocation of the mesh rows failed");
     }
-    // bases of every cluster's segments in the bulk arrays
-    std::vector<int64_t> base(ctx->bulk_offs.begin(), ctx->bulk_offs.begin() + size_t(10) * K);
-    if (cb.base) ctx->dfree(cb.base);
-    cb.base = upload(ctx, base, s);
-    if (!cb.base) return fail(GALE_ENOMEM, "device allocation failed");
-    CbMesh m{reinterpret_cast<const int4 *>(cb.rows), cb.cluster_of, ctx->d_I_V, cb.E, cb.F, cb.ebk, cb.fbk,
-             cb.IE, cb.IF, cb.eo, cb.ekw, cb.feo, cb.fkc, cb.e2s, cb.f2s,
-             ctx->bulk[B_VT_OFF], ctx->bulk[B_VT_VAL], ctx->bulk[B_VV_OFF], ctx->bulk[B_VV_VAL],
-             ctx->bulk[B_ET_W], ctx->bulk[B_ET_OFF], ctx->bulk[B_ET_VAL], ctx->bulk[B_ET_UOFF], nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cb.base, ctx->d_sizes,
-             hm.nv, nE, nF, cb.sorted_ids};
+    // the pass reads the enumeration, its index and the canonical tet rows
+    CbMesh m{};
+    m.rows = reinterpret_cast<const int4 *>(cb.rows);
+    m.cluster_of = cb.cluster_of;
+    m.I_V = ctx->d_I_V;
+    m.E = cb.E;
+    m.F = cb.F;
+    m.ebk = cb.ebk;
+    m.fbk = cb.fbk;
+    m.IE = cb.IE;
+    m.IF = cb.IF;
+    m.eo = cb.eo;
+    m.ekw = cb.ekw;
+    m.feo = cb.feo;
+    m.fkc = cb.fkc;
+    m.e2s = cb.e2s;
+    m.f2s = cb.f2s;
+    m.nv = hm.nv;
+    m.nE = nE;
+    m.nF = nF;
+    m.sorted_ids = cb.sorted_ids;
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 1;
     auto grid_for = [&](int64_t n) {
         return int(std::min<int64_t>(std::max<int64_t>((n + kThreads - 1) / kThreads, 1), int64_t(sms) * 16));
@@ -865,29 +982,74 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     m.e2s = cb.e2s;
     m.f2s = cb.f2s;
     m.sorted_ids = cb.sorted_ids;
+    const int64_t nT = hm.nt;
     const int64_t rows_of[4] = {hm.nv, hm.nv, nE, nF};
-    // VF is read from VE (in VV order) and EF: those two first, and built
-    // whenever VF is asked for
-    const uint32_t build = which | ((which & GALE_CB_VF) ? uint32_t(GALE_CB_VE | GALE_CB_EF) : 0u);
-    m.ef_off = nullptr;
-    m.ef_val = nullptr;
-    m.ve_off = nullptr;
-    m.ve_val = nullptr;
-    m.ef_third = nullptr;
-    m.third_out = nullptr;
-    for (int rel : {int(REL_VE), int(REL_EF), int(REL_VF), int(REL_FT)}) {
-        if (!(build & (1u << rel))) continue;
+    // entries: every edge is in two VE rows, every triangle in three VF and
+    // three EF rows, every tet in four FT rows
+    const int64_t len_of[4] = {2 * nE, 3 * nF, 3 * nF, 4 * nT};
+    for (int rel = 0; rel < 4; ++rel)
+        if (len_of[rel] >= INT32_MAX) return fail(GALE_EINVAL, "a coboundary relation has 2^31 or more entries");
+    const bool wVF = which & GALE_CB_VF, wFT = which & GALE_CB_FT;
+    // with the sorted numbering VF is gathered from VE and EF, which are then
+    // built whether asked for or not; otherwise it is scattered like them
+    const bool vf_gather = wVF && cb.sorted_ids;
+    const bool wVE = (which & GALE_CB_VE) || vf_gather, wEF = (which & GALE_CB_EF) || vf_gather;
+    const uint32_t place = (wVE ? GALE_CB_VE : 0u) | (wVF ? GALE_CB_VF : 0u) | (wEF ? GALE_CB_EF : 0u) |
+                           (wFT ? GALE_CB_FT : 0u);
+    // scratch: counters (zeroed), then the triangles' edge positions and the
+    // tets' face positions
+    auto al = [](int64_t x) { return (x + 3) & ~int64_t(3); };
+    const int64_t n_ctr = 4 * al(hm.nv) + 4 * al(nE) + al(nF);
+    const int64_t n_scr = n_ctr + 2 * al(nF) + 4 * al(nT) + (vf_gather ? 2 * al(nE) : 0);
+    if (!grow(ctx, cb.scratch, cb.scratch_cap, std::max<int64_t>(n_scr, 4)) ||
+        !grow(ctx, cb.cnt, cb.cnt_cap, std::max<int64_t>({hm.nv, nE, nF, int64_t(1)})))
+        return fail(GALE_ENOMEM, "device allocation of coboundary scratch failed");
+    Scatter sc{};
+    {
+        int32_t *q = cb.scratch;
+        auto take = [&](int64_t n) {
+            int32_t *r = q;
+            q += al(n);
+            return r;
+        };
+        sc.ve_n = take(hm.nv);
+        sc.ve_fill = take(hm.nv);
+        sc.vf_n = take(hm.nv);
+        sc.vf_fill = take(hm.nv);
+        sc.ef_lo = take(nE);
+        sc.ef_mid = take(nE);
+        sc.ef_lofill = take(nE);
+        sc.ef_midfill = take(nE);
+        sc.ft_fill = take(nF);
+        sc.tri_ac = take(nF);
+        sc.tri_bc = take(nF);
+        sc.tet_f = reinterpret_cast<int4 *>(take(4 * nT));
+        sc.ef_tail = vf_gather ? reinterpret_cast<int2 *>(take(2 * nE)) : nullptr;
+    }
+    sc.cnt = cb.cnt;
+    if (cudaMemsetAsync(cb.scratch, 0, sizeof(int32_t) * size_t(n_ctr), s) != cudaSuccess)
+        return fail(GALE_ECUDA, "cudaMemsetAsync");
+    // counts of the scattered parts
+    if (wVE) k_sc_edges<false><<<grid_for(nE), kThreads, 0, s>>>(m, sc, ctx->d_err);
+    if (wEF || wVF) k_sc_tris<false><<<grid_for(nF), kThreads, 0, s>>>(m, sc, wEF, wVF && !vf_gather, ctx->d_err);
+    if (vf_gather) k_vf_count_sorted<<<grid_for(nE), kThreads, 0, s>>>(m, sc);
+    // row offsets, one relation at a time through the shared count array
+    for (int rel : {int(REL_VE), int(REL_VF), int(REL_EF), int(REL_FT)}) {
+        if (!(place & (1u << rel))) continue;
         const int64_t n = rows_of[rel];
-        const int64_t nb = (n + kThreads - 1) / kThreads;
-        if (!grow(ctx, cb.cnt, cb.cnt_cap, std::max<int64_t>(n, 1)) ||
-            !grow(ctx, cb.bsum, cb.bsum_cap, nb + 1) || !grow(ctx, cb.off[rel], cb.off_cap[rel], n + 1))
-            return fail(GALE_ENOMEM, "device allocation of coboundary counts failed");
+        const int64_t nb = scan_tiles(n);
+        if (!grow(ctx, cb.bsum, cb.bsum_cap, nb + 1) || !grow(ctx, cb.off[rel], cb.off_cap[rel], n + 1) ||
+            !grow(ctx, cb.val[rel], cb.val_cap[rel], std::max<int64_t>(len_of[rel], 1)))
+            return fail(GALE_ENOMEM, "device allocation of coboundary rows failed");
         const int grid = grid_for(n);
         switch (rel) {
-            case REL_VE: cb_count<REL_VE><<<grid, kThreads, 0, s>>>(m, n, cb.cnt, ctx->d_err); break;
-            case REL_VF: cb_count<REL_VF><<<grid, kThreads, 0, s>>>(m, n, cb.cnt, ctx->d_err); break;
-            case REL_EF: cb_count<REL_EF><<<grid, kThreads, 0, s>>>(m, n, cb.cnt, ctx->d_err); break;
-            default: cb_count<REL_FT><<<grid, kThreads, 0, s>>>(m, n, cb.cnt, ctx->d_err); break;
+            case REL_VE: k_len_ve<<<grid, kThreads, 0, s>>>(m, sc); break;
+            case REL_VF: k_len_vf<<<grid, kThreads, 0, s>>>(m, sc, cb.fo); break;
+            case REL_EF: k_len_ef<<<grid, kThreads, 0, s>>>(m, sc); break;
+            default:
+                cudaMemsetAsync(cb.cnt, 0, sizeof(int32_t) * size_t(std::max<int64_t>(n, 1)), s);
+                k_sc_tets<false><<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
+                break;
         }
         if (nb > 0) {
             scan_sums<<<int(nb), kThreads, 0, s>>>(cb.cnt, n, cb.bsum);
@@ -896,48 +1058,38 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
         } else {
             cudaMemsetAsync(cb.off[rel], 0, sizeof(int32_t), s);
         }
-        int32_t total = 0;
-        if (cudaMemcpyAsync(&total, cb.off[rel] + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return fail(GALE_ECUDA, "coboundary count pass failed");
-        int32_t e = 0;
-        cudaMemcpy(&e, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
-        if (e) {
-            cudaMemset(ctx->d_err, 0, sizeof(int32_t));
-            return fail(GALE_EDEVICE, "coboundary count pass: error word " + std::to_string(e));
-        }
-        if (!grow(ctx, cb.val[rel], cb.val_cap[rel], std::max<int64_t>(total, 1)) ||
-            (rel == REL_EF && !grow(ctx, cb.ef_third, cb.ef_third_cap, std::max<int64_t>(total, 1))))
-            return fail(GALE_ENOMEM, "device allocation of coboundary values failed");
-        m.third_out = cb.ef_third;
-        switch (rel) {
-            case REL_VE: cb_fill<REL_VE><<<grid, kThreads, 0, s>>>(m, n, cb.off[rel], cb.val[rel], ctx->d_err); break;
-            case REL_VF: cb_fill<REL_VF><<<grid, kThreads, 0, s>>>(m, n, cb.off[rel], cb.val[rel], ctx->d_err); break;
-            case REL_EF: cb_fill<REL_EF><<<grid, kThreads, 0, s>>>(m, n, cb.off[rel], cb.val[rel], ctx->d_err); break;
-            default: cb_fill<REL_FT><<<grid, kThreads, 0, s>>>(m, n, cb.off[rel], cb.val[rel], ctx->d_err); break;
-        }
-        if (cudaGetLastError() != cudaSuccess) return fail(GALE_ECUDA, "coboundary launch failed");
         cb.rows_of[rel] = n;
-        cb.len[rel] = total;
-        if (rel == REL_EF) {
-            m.ef_off = cb.off[REL_EF];
-            m.ef_val = cb.val[REL_EF];
-            m.ef_third = cb.ef_third;
-        }
-        if (rel == REL_VE) {
-            m.ve_off = cb.off[REL_VE];
-            m.ve_val = cb.val[REL_VE];
-        }
+        cb.len[rel] = len_of[rel];
     }
-    // VE rows are ascending already with the sorted numbering
-    if ((build & GALE_CB_VE) && !cb.sorted_ids && hm.nv > 0)
-        cb_sort_rows<<<grid_for(hm.nv), kThreads, 0, s>>>(hm.nv, cb.off[REL_VE], cb.val[REL_VE]);
+    sc.ve_off = cb.off[REL_VE];
+    sc.vf_off = cb.off[REL_VF];
+    sc.ef_off = cb.off[REL_EF];
+    sc.ft_off = cb.off[REL_FT];
+    sc.ve_val = cb.val[REL_VE];
+    sc.vf_val = cb.val[REL_VF];
+    sc.ef_val = cb.val[REL_EF];
+    sc.ft_val = cb.val[REL_FT];
+    // values: cursors, scattered parts, then every row's contiguous part and
+    // its order by id (sorted numbering: the scattered prefix only)
+    k_cursors<<<grid_for(std::max({hm.nv, nE, nF})), kThreads, 0, s>>>(m, sc, wVE, wVF, wEF, wFT);
+    if (wVE) k_sc_edges<true><<<grid_for(nE), kThreads, 0, s>>>(m, sc, ctx->d_err);
+    if (wEF || wVF)
+        k_sc_tris<true><<<grid_for(nF), kThreads, 0, s>>>(m, sc, wEF, wVF && !vf_gather, ctx->d_err);
+    if (wFT) k_sc_tets<true><<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
+    const int32_t *fo = cb.fo;
+    if (wVE) k_sort_rows<PL_VE, 16, FRONT_NONE, 6144><<<grid_for(hm.nv), kThreads, 0, s>>>(m, sc, hm.nv, sc.ve_off, sc.ve_val, fo);
+    if (wEF) k_sort_rows<PL_EF, 8, FRONT_EF, 0><<<grid_for(nE), kThreads, 0, s>>>(m, sc, nE, sc.ef_off, sc.ef_val, fo);
+    if (vf_gather) k_vf_gather<<<grid_for(hm.nv), kThreads, 0, s>>>(m, sc, fo);
+    else if (wVF)
+        k_sort_rows<PL_VF, 32, FRONT_VF, 12288><<<grid_for(hm.nv), kThreads, 0, s>>>(m, sc, hm.nv, sc.vf_off, sc.vf_val, fo);
+    if (wFT) k_sort_rows<PL_FULL, 8, FRONT_NONE, 0><<<grid_for(nF), kThreads, 0, s>>>(m, sc, nF, sc.ft_off, sc.ft_val, fo);
+    if (cudaGetLastError() != cudaSuccess) return fail(GALE_ECUDA, "coboundary launch failed");
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GALE_ECUDA, "cudaStreamSynchronize");
     int32_t e = 0;
     cudaMemcpy(&e, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e) {
         cudaMemset(ctx->d_err, 0, sizeof(int32_t));
-        return fail(GALE_EDEVICE, "coboundary fill pass: error word " + std::to_string(e));
+        return fail(GALE_EDEVICE, "coboundary pass: error word " + std::to_string(e));
     }
     for (int rel = 0; rel < 4; ++rel) {
         const bool have = (which & (1u << rel)) != 0;
