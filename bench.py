@@ -267,7 +267,7 @@ def main():
                     help="skip the irregular batched leg (2M-point Delaunay, uneven kd leaves)")
     ap.add_argument("--serve-sweep", action="store_true",
                     help="also sweep serving prefetch depth x cache budget on the 256^3 mesh (minutes)")
-    ap.add_argument("--coboundary", action="store_true", help="also time VE, VF, EF, FT")
+    ap.add_argument("--no-coboundary", action="store_true", help="skip timing VE, VF, EF, FT (128^3 grid)")
     ap.add_argument("--coboundary-grid", type=int, default=128)
     ap.add_argument("--discrete-gradient", action="store_true",
                     help="also time the discrete-gradient consumer and the relations it reads")
@@ -443,7 +443,7 @@ def main():
     if rank == 0 and args.serve_sweep:
         sweep = serve_sweep_leg(args, mesh, ctx, gale)
     cobound = None
-    if rank == 0 and args.coboundary:
+    if rank == 0 and not args.no_coboundary:
         cobound = coboundary_leg(args, gale, gen)
     dgrad = None
     if rank == 0 and args.discrete_gradient:
@@ -816,6 +816,8 @@ def coboundary_leg(args, gale, gen):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
         out_bytes = int(sum(4 * (cb.rows[i] + 1 + cb.len[i]) for i in range(4)))
+        # what the pass must read: the enumeration's lists and the tet rows
+        in_bytes = 4 * (2 * int(cb.rows[2]) + 3 * int(cb.rows[3]) + 4 * mesh.nt)
     peak, _ = load_peaks()
     # the oracle on a small sample of the same recipe
     import oracle
@@ -828,7 +830,9 @@ def coboundary_leg(args, gale, gen):
             "ms": ms, "tets_per_s": mesh.nt / (ms / 1e3), "host_enumeration_s": enum_s,
             "roofline": {"bound": "hbm", "achieved": out_bytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": out_bytes / (ms / 1e3) / 1e9 / peak,
-                         "algorithmic_bytes": out_bytes, "note": "output bytes only"},
+                         "algorithmic_bytes": out_bytes, "note": "output bytes only",
+                         "frac_reads_and_writes": (out_bytes + in_bytes) / (ms / 1e3) / 1e9 / peak,
+                         "read_bytes": in_bytes},
             "oracle": {"sample": f"grid12^3 ({small.nt} tets), enumeration + coboundary, Python, single thread",
                        "tets_per_s": small.nt / osec}}
 

@@ -165,9 +165,8 @@ struct Scatter {
                                            // (u, x, w), u < x < w, of edge (u, w)
     int32_t *ef_lofill, *ef_midfill;       // [nE] cursors of their slots
     int32_t *vf_n, *vf_fill;               // [nv] triangles with v as second or third vertex; cursor
-    int32_t *ft_fill;                      // [nF] (sorted positions) cursors of FT's slots
     int32_t *tri_ac, *tri_bc;              // [nF] sorted positions of the edges (a, c), (b, c) of triangle p
-    int4 *tet_f;                           // [nT] sorted positions of a tet's faces abc, abd, acd, bcd
+    int2 *ft_slot;                         // [nF] (sorted positions) the one or two tets of a triangle
     int2 *ef_tail;                         // [nE] (sorted numbering, VF gather) EF(j) after its lower part
     int32_t *cnt;                          // row lengths of the relation being placed
     const int32_t *ve_off, *ef_off, *vf_off, *ft_off;
@@ -229,37 +228,46 @@ __global__ void __launch_bounds__(kThreads) k_sc_tris(CbMesh m, Scatter sc, bool
         }
     }
 }
-// tets: FT of the four faces of every tet (a, b, c, d)
-template <bool FILL>
-__global__ void __launch_bounds__(kThreads) k_sc_tets(CbMesh m, Scatter sc, int64_t nT, int32_t *err) {
+// FT: a triangle lies in one or two tets, so each has two slots (sorted
+// position order); every tet claims a slot of each of its four faces, and
+// a pass over the triangles writes the rows (smaller tet first)
+__device__ __forceinline__ void ft_claim(int2 *slot, int32_t q, int32_t t, int32_t *err) {
+    if (atomicCAS(&slot[q].x, -1, t) == -1) return;
+    if (atomicCAS(&slot[q].y, -1, t) != -1) atomicOr(err, ERR_NONMANIFOLD);
+}
+__global__ void __launch_bounds__(kThreads) k_ft_tets(CbMesh m, Scatter sc, int64_t nT, int32_t *err) {
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nT; t += int64_t(gridDim.x) * blockDim.x) {
-        int4 f;
-        if (!FILL) {
-            const int4 r = m.rows[t];
-            const int64_t jab = epos(m, r.x, r.y), jac = epos(m, r.x, r.z), jbc = epos(m, r.y, r.z);
-            f.x = jab < 0 ? -1 : int32_t(fpos_at(m, jab, r.z));
-            f.y = jab < 0 ? -1 : int32_t(fpos_at(m, jab, r.w));
-            f.z = jac < 0 ? -1 : int32_t(fpos_at(m, jac, r.w));
-            f.w = jbc < 0 ? -1 : int32_t(fpos_at(m, jbc, r.w));
-            if (f.x < 0 || f.y < 0 || f.z < 0 || f.w < 0) {
-                atomicOr(err, ERR_BAD_BLOCK);
-                f = make_int4(-1, -1, -1, -1);
-            }
-            sc.tet_f[t] = f;
-            if (f.x >= 0) {
-                atomicAdd(&sc.cnt[frow(m, f.x)], 1);
-                atomicAdd(&sc.cnt[frow(m, f.y)], 1);
-                atomicAdd(&sc.cnt[frow(m, f.z)], 1);
-                atomicAdd(&sc.cnt[frow(m, f.w)], 1);
-            }
+        const int4 r = m.rows[t];
+        const int64_t jab = epos(m, r.x, r.y), jac = epos(m, r.x, r.z), jbc = epos(m, r.y, r.z);
+        const int64_t f0 = jab < 0 ? -1 : fpos_at(m, jab, r.z), f1 = jab < 0 ? -1 : fpos_at(m, jab, r.w);
+        const int64_t f2 = jac < 0 ? -1 : fpos_at(m, jac, r.w), f3 = jbc < 0 ? -1 : fpos_at(m, jbc, r.w);
+        if (f0 < 0 || f1 < 0 || f2 < 0 || f3 < 0) {
+            atomicOr(err, ERR_BAD_BLOCK);
             continue;
         }
-        f = sc.tet_f[t];
-        if (f.x < 0) continue;
-        sc.ft_val[atomicAdd(&sc.ft_fill[f.x], 1)] = int32_t(t);
-        sc.ft_val[atomicAdd(&sc.ft_fill[f.y], 1)] = int32_t(t);
-        sc.ft_val[atomicAdd(&sc.ft_fill[f.z], 1)] = int32_t(t);
-        sc.ft_val[atomicAdd(&sc.ft_fill[f.w], 1)] = int32_t(t);
+        ft_claim(sc.ft_slot, int32_t(f0), int32_t(t), err);
+        ft_claim(sc.ft_slot, int32_t(f1), int32_t(t), err);
+        ft_claim(sc.ft_slot, int32_t(f2), int32_t(t), err);
+        ft_claim(sc.ft_slot, int32_t(f3), int32_t(t), err);
+    }
+}
+__global__ void __launch_bounds__(kThreads) k_len_ft(CbMesh m, Scatter sc, int32_t *err) {
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < m.nF; p += int64_t(gridDim.x) * blockDim.x) {
+        const int2 q = sc.ft_slot[p];
+        if (q.x < 0) atomicOr(err, ERR_BAD_BLOCK);  // a triangle in no tet
+        sc.cnt[frow(m, p)] = (q.x >= 0) + (q.y >= 0);
+    }
+}
+__global__ void __launch_bounds__(kThreads) k_ft_write(CbMesh m, Scatter sc) {
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < m.nF; p += int64_t(gridDim.x) * blockDim.x) {
+        const int2 q = sc.ft_slot[p];
+        int32_t *o = sc.ft_val + sc.ft_off[frow(m, p)];
+        if (q.y < 0) {
+            if (q.x >= 0) o[0] = q.x;
+        } else {
+            o[0] = min(q.x, q.y);
+            o[1] = max(q.x, q.y);
+        }
     }
 }
 
@@ -416,7 +424,7 @@ __global__ void __launch_bounds__(kThreads) k_vf_gather(CbMesh m, Scatter sc, co
 
 // fill cursors: every scattered part's first slot, so that a scatter is
 // one atomic and one store
-__global__ void __launch_bounds__(kThreads) k_cursors(CbMesh m, Scatter sc, bool ve, bool vf, bool ef, bool ft) {
+__global__ void __launch_bounds__(kThreads) k_cursors(CbMesh m, Scatter sc, bool ve, bool vf, bool ef) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     for (int64_t v = t0; v < m.nv; v += stride) {
@@ -429,8 +437,6 @@ __global__ void __launch_bounds__(kThreads) k_cursors(CbMesh m, Scatter sc, bool
             sc.ef_lofill[j] = o;
             sc.ef_midfill[j] = o + sc.ef_lo[j];
         }
-    if (ft)
-        for (int64_t p = t0; p < m.nF; p += stride) sc.ft_fill[p] = sc.ft_off[frow(m, p)];
 }
 
 // ---- sorted enumeration on the device ----
@@ -999,8 +1005,8 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     // scratch: counters (zeroed), then the triangles' edge positions and the
     // tets' face positions
     auto al = [](int64_t x) { return (x + 3) & ~int64_t(3); };
-    const int64_t n_ctr = 4 * al(hm.nv) + 4 * al(nE) + al(nF);
-    const int64_t n_scr = n_ctr + 2 * al(nF) + 4 * al(nT) + (vf_gather ? 2 * al(nE) : 0);
+    const int64_t n_ctr = 4 * al(hm.nv) + 4 * al(nE);
+    const int64_t n_scr = n_ctr + 2 * al(nF) + 2 * al(nF) + (vf_gather ? 2 * al(nE) : 0);
     if (!grow(ctx, cb.scratch, cb.scratch_cap, std::max<int64_t>(n_scr, 4)) ||
         !grow(ctx, cb.cnt, cb.cnt_cap, std::max<int64_t>({hm.nv, nE, nF, int64_t(1)})))
         return fail(GALE_ENOMEM, "device allocation of coboundary scratch failed");
@@ -1020,10 +1026,9 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
         sc.ef_mid = take(nE);
         sc.ef_lofill = take(nE);
         sc.ef_midfill = take(nE);
-        sc.ft_fill = take(nF);
         sc.tri_ac = take(nF);
         sc.tri_bc = take(nF);
-        sc.tet_f = reinterpret_cast<int4 *>(take(4 * nT));
+        sc.ft_slot = reinterpret_cast<int2 *>(take(2 * nF));
         sc.ef_tail = vf_gather ? reinterpret_cast<int2 *>(take(2 * nE)) : nullptr;
     }
     sc.cnt = cb.cnt;
@@ -1033,6 +1038,10 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     if (wVE) k_sc_edges<false><<<grid_for(nE), kThreads, 0, s>>>(m, sc, ctx->d_err);
     if (wEF || wVF) k_sc_tris<false><<<grid_for(nF), kThreads, 0, s>>>(m, sc, wEF, wVF && !vf_gather, ctx->d_err);
     if (vf_gather) k_vf_count_sorted<<<grid_for(nE), kThreads, 0, s>>>(m, sc);
+    if (wFT) {
+        cudaMemsetAsync(sc.ft_slot, 0xff, sizeof(int2) * size_t(std::max<int64_t>(nF, 1)), s);
+        k_ft_tets<<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
+    }
     // row offsets, one relation at a time through the shared count array
     for (int rel : {int(REL_VE), int(REL_VF), int(REL_EF), int(REL_FT)}) {
         if (!(place & (1u << rel))) continue;
@@ -1046,10 +1055,7 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
             case REL_VE: k_len_ve<<<grid, kThreads, 0, s>>>(m, sc); break;
             case REL_VF: k_len_vf<<<grid, kThreads, 0, s>>>(m, sc, cb.fo); break;
             case REL_EF: k_len_ef<<<grid, kThreads, 0, s>>>(m, sc); break;
-            default:
-                cudaMemsetAsync(cb.cnt, 0, sizeof(int32_t) * size_t(std::max<int64_t>(n, 1)), s);
-                k_sc_tets<false><<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
-                break;
+            default: k_len_ft<<<grid, kThreads, 0, s>>>(m, sc, ctx->d_err); break;
         }
         if (nb > 0) {
             scan_sums<<<int(nb), kThreads, 0, s>>>(cb.cnt, n, cb.bsum);
@@ -1071,18 +1077,17 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     sc.ft_val = cb.val[REL_FT];
     // values: cursors, scattered parts, then every row's contiguous part and
     // its order by id (sorted numbering: the scattered prefix only)
-    k_cursors<<<grid_for(std::max({hm.nv, nE, nF})), kThreads, 0, s>>>(m, sc, wVE, wVF, wEF, wFT);
+    k_cursors<<<grid_for(std::max(hm.nv, nE)), kThreads, 0, s>>>(m, sc, wVE, wVF, wEF);
     if (wVE) k_sc_edges<true><<<grid_for(nE), kThreads, 0, s>>>(m, sc, ctx->d_err);
     if (wEF || wVF)
         k_sc_tris<true><<<grid_for(nF), kThreads, 0, s>>>(m, sc, wEF, wVF && !vf_gather, ctx->d_err);
-    if (wFT) k_sc_tets<true><<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
+    if (wFT) k_ft_write<<<grid_for(nF), kThreads, 0, s>>>(m, sc);
     const int32_t *fo = cb.fo;
     if (wVE) k_sort_rows<PL_VE, 16, FRONT_NONE, 6144><<<grid_for(hm.nv), kThreads, 0, s>>>(m, sc, hm.nv, sc.ve_off, sc.ve_val, fo);
     if (wEF) k_sort_rows<PL_EF, 8, FRONT_EF, 0><<<grid_for(nE), kThreads, 0, s>>>(m, sc, nE, sc.ef_off, sc.ef_val, fo);
     if (vf_gather) k_vf_gather<<<grid_for(hm.nv), kThreads, 0, s>>>(m, sc, fo);
     else if (wVF)
         k_sort_rows<PL_VF, 32, FRONT_VF, 12288><<<grid_for(hm.nv), kThreads, 0, s>>>(m, sc, hm.nv, sc.vf_off, sc.vf_val, fo);
-    if (wFT) k_sort_rows<PL_FULL, 8, FRONT_NONE, 0><<<grid_for(nF), kThreads, 0, s>>>(m, sc, nF, sc.ft_off, sc.ft_val, fo);
     if (cudaGetLastError() != cudaSuccess) return fail(GALE_ECUDA, "coboundary launch failed");
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GALE_ECUDA, "cudaStreamSynchronize");
     int32_t e = 0;
