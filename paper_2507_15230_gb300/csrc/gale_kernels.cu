@@ -285,7 +285,9 @@ constexpr uint32_t kMatch = 1u << 20;
 // and phase are the CTA's block-copy barrier and its next parity.  Returns
 // false when a bounded wait ran out (the CTA must stop).
 // ---------------------------------------------------------------------------
-template <bool COUNT, bool SPILL>
+// PART: the item is a part of a cut cluster (block header part != 0); the
+// whole-cluster instances carry none of the part logic.
+template <bool COUNT, bool SPILL, bool PART>
 __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, int64_t words,
                             uint32_t mask, const WorkItem *it, int64_t *sizes_out, int32_t *err, uint64_t *bar,
                             uint32_t &phase) {
@@ -332,7 +334,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     }
     const BlockHdr h = *reinterpret_cast<const BlockHdr *>(S.blk);
     // a part block: its record, and the extra tmap words of its internal tets
-    const PartInfo *part = (h.part > 0 && h.part <= m.NP) ? m.parts + (h.part - 1) : nullptr;
+    const PartInfo *part = (PART && h.part > 0 && h.part <= m.NP) ? m.parts + (h.part - 1) : nullptr;
     const int32_t xmap = part ? h.n_own : 0;
     {
         const int64_t n_tot = int64_t(h.n_ext) + h.n_own + h.n_halo;
@@ -340,7 +342,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                         h.nv_own >= 0 && h.nv_nb >= 0 && h.n_bnd >= 0 && n_tot <= caps.n_tot &&
                         h.n_own <= caps.n_own && h.nv_loc <= caps.nv_loc && h.nv_own <= caps.nv_own &&
                         h.nv_nb <= caps.nv_nb && h.nv_nb <= h.nv_loc && int64_t(h.own_lo) + h.nv_own <= h.nv_nb &&
-                        2 * int64_t(h.n_bnd) + 1 <= caps.hcap && (h.part == 0 || part != nullptr) &&
+                        2 * int64_t(h.n_bnd) + 1 <= caps.hcap && (PART ? part != nullptr : h.part == 0) &&
                         blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo, h.n_bnd, xmap) == words;
         if (!ok) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
@@ -910,6 +912,15 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     return true;
 }
 
+// A work item: a whole cluster, or (id >= K) a part of a cut cluster.
+template <bool COUNT, bool SPILL>
+__device__ __forceinline__ bool run_item(bool part, const DevMesh &m, const SmemPlan &plan, const Smem &S,
+                                         int64_t blk_word, int64_t words, uint32_t mask, const WorkItem *it,
+                                         int64_t *sizes_out, int32_t *err, uint64_t *bar, uint32_t &phase) {
+    if (part) return run_cluster<COUNT, SPILL, true>(m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
+    return run_cluster<COUNT, SPILL, false>(m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
+}
+
 // SPILL: the cluster's regions live in a per-CTA slice of global scratch
 // (clusters whose working set exceeds shared memory); otherwise in dynamic
 // shared memory.
@@ -951,7 +962,7 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan 
         }
         if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
         __syncthreads();
-        if (!run_cluster<true, SPILL>(m, plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr, s_sizes,
+        if (!run_item<true, SPILL>(k >= m.K, m, plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr, s_sizes,
                                       err, &s_bar, phase))
             return;
         __syncthreads();
@@ -993,7 +1004,7 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel(DevMesh m, SmemPlan 
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
-        if (!run_cluster<false, SPILL>(m, plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
+        if (!run_item<false, SPILL>(k >= m.K, m, plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
                                        nullptr, err, &s_bar, phase))
             return;
     }
@@ -1014,7 +1025,7 @@ __global__ void __launch_bounds__(kMaxThreads) build_one_kernel(DevMesh m, SmemP
         if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
         return;
     }
-    run_cluster<false, SPILL>(m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k], s_item.mask,
+    run_cluster<false, SPILL, false>(m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k], s_item.mask,
                               &s_item, nullptr, err, &s_bar, phase);
 }
 
@@ -1057,7 +1068,7 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel_pi(DevMesh m, const 
         if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
         __syncthreads();
         const Smem S = carve(smem, s_plan);
-        if (!run_cluster<true, false>(m, s_plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr,
+        if (!run_item<true, false>(k >= m.K, m, s_plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr,
                                       s_sizes, err, &s_bar, phase))
             return;
         __syncthreads();
@@ -1101,7 +1112,7 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel_pi(DevMesh m, const 
         load_plan(s_plan, plans + k);
         __syncthreads();
         const Smem S = carve(smem, s_plan);
-        if (!run_cluster<false, false>(m, s_plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
+        if (!run_item<false, false>(k >= m.K, m, s_plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
                                        nullptr, err, &s_bar, phase))
             return;
     }
@@ -1183,7 +1194,7 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, const SmemPlan *
             load_plan(s_plan, plans + s_item.k);  // the cluster's own plan
             __syncthreads();
             const Smem S = carve(smem, s_plan);
-            go_on = run_cluster<false, false>(m, s_plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
+            go_on = run_cluster<false, false, false>(m, s_plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
                                               s_item.mask, &s_item, nullptr, err, &s_bar, phase);
         } else if (threadIdx.x == 0) {
             atomicOr(err, ERR_BAD_ITEM);
