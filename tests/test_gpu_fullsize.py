@@ -53,6 +53,85 @@ def check_tt_symmetric(d, I_T):
     return int(val.numel())
 
 
+def _chunks(n, step=1 << 26):
+    for a in range(0, n, step):
+        yield a, min(n, a + step)
+
+
+def _strictly_ascending_rows(owner, val):
+    """Within every row (equal owner), values strictly ascending."""
+    if val.numel() < 2:
+        return True
+    same = owner[1:] == owner[:-1]
+    return bool((val[1:][same] > val[:-1][same]).all())
+
+
+def check_exact(ctx, d, m):
+    """Whole-output exactness of VT, VV, ET and TT, every row: each listed
+    entry is valid (its tet contains the row's vertex or edge; its face
+    neighbour shares three vertices), entries are distinct (rows strictly
+    ascending), and the totals are the closed forms (every tet in four VT
+    rows and six ET rows; VV pairs with the larger vertex second are exactly
+    the ET edges; TT symmetric).  Valid and distinct entries in the right
+    number leave no room for a wrong one."""
+    I_V, I_T, sizes = ctx.intervals()
+    nv, nt = int(I_V[-1]), int(I_T[-1])
+    dev = d["vt_val"].device
+    rows = torch.from_numpy(np.ascontiguousarray(ctx.rows())).to(dev).view(nt, 4)
+    nvo = np.diff(I_V)
+    verts = torch.arange(nv, device=dev)
+
+    def contains(t, v):
+        return bool((rows[t.long()] == v.view(-1, 1).int()).any(1).all())
+
+    # VT: every entry a tet holding the row's vertex, rows strictly ascending
+    vt_owner = torch.repeat_interleave(verts, global_rows(d["vt_off"], nvo))
+    vt = d["vt_val"]
+    assert vt_owner.numel() == vt.numel() == 4 * nt
+    assert bool((torch.bincount(vt.long(), minlength=nt) == 4).all())  # every tet in four rows
+    for a, b in _chunks(vt.numel()):
+        assert contains(vt[a:b], vt_owner[a:b])
+    assert _strictly_ascending_rows(vt_owner, vt)
+    del vt_owner
+    # ET: the edge list (lower vertex u from et_uoff, upper w), then every ET
+    # entry a tet holding both endpoints
+    e_u = torch.repeat_interleave(verts, global_rows(d["et_uoff"], nvo))
+    e_w = d["et_w"].long()
+    E = e_w.numel()
+    assert e_u.numel() == E and bool((e_w > e_u).all())
+    ekey = e_u * nv + e_w
+    assert bool((ekey[1:] > ekey[:-1]).all())  # edges distinct, in (u, w) order
+    et_len = global_rows(d["et_off"], sizes[:, 2].astype(np.int64))
+    assert et_len.numel() == E and int(et_len.min()) >= 1  # every listed edge lies in some tet
+    et_owner = torch.repeat_interleave(torch.arange(E, device=dev), et_len)
+    et = d["et_val"]
+    assert et_owner.numel() == et.numel() == 6 * nt
+    for a, b in _chunks(et.numel()):
+        o = et_owner[a:b]
+        assert contains(et[a:b], e_u[o]) and contains(et[a:b], e_w[o])
+    assert _strictly_ascending_rows(et_owner, et)
+    del et_owner
+    # VV: symmetric, no self loops, rows strictly ascending, and the pairs
+    # (v, u) with u > v are exactly the ET edges
+    vv_owner = torch.repeat_interleave(verts, global_rows(d["vv_off"], nvo))
+    vv = d["vv_val"].long()
+    assert vv_owner.numel() == vv.numel() == 2 * E
+    assert bool((vv != vv_owner).all()) and _strictly_ascending_rows(vv_owner, vv)
+    up = vv > vv_owner
+    assert torch.equal(torch.sort(vv_owner[up] * nv + vv[up]).values, ekey)
+    assert torch.equal(torch.sort(vv_owner * nv + vv).values, torch.sort(vv * nv + vv_owner).values)
+    del vv_owner, vv, up
+    # TT: every entry shares a face (three vertices) with its row's tet
+    tt_owner = torch.repeat_interleave(torch.arange(nt, device=dev), global_rows(d["tt_off"], np.diff(I_T)))
+    tt = d["tt_val"]
+    for a, b in _chunks(tt.numel()):
+        r0, r1 = rows[tt_owner[a:b]], rows[tt[a:b].long()]
+        common = (r0.unsqueeze(2) == r1.unsqueeze(1)).any(2).sum(1)
+        assert bool((common == 3).all())
+    assert _strictly_ascending_rows(tt_owner, tt)
+    return E
+
+
 def check_vt_counts(d, nt):
     cnt = torch.bincount(d["vt_val"].long(), minlength=nt)
     assert cnt.numel() == nt and bool((cnt == 4).all())
@@ -107,6 +186,7 @@ def test_grid256_full_size():
         I_V, I_T, _ = ctx.intervals()
         check_vt_counts(d, T)
         check_tt_symmetric(d, I_T)
+        assert check_exact(ctx, d, m) == E
         del d
         torch.cuda.empty_cache()
         canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
@@ -147,6 +227,7 @@ def test_delaunay_2m_full_size():
         # all, so F = 4T - sum|TT|/2; a triangulated ball has V - E + F - T = 1
         F = 4 * T - sum_tt // 2
         assert V - E + F - T == 1
+        assert check_exact(ctx, d, m) == E
         del d
         torch.cuda.empty_cache()
         canon = oracle.canonicalize(m.nv, m.tv, m.seg, m.nclusters)
@@ -183,3 +264,40 @@ def test_delaunay_2m_full_size():
         for t in th:
             t.join()
         assert not errors, errors
+
+
+def test_exactness_checks_catch_planted_mistakes():
+    """The whole-output checks above pass on a correct build and fail on
+    copies of it with one planted mistake each: a VT entry moved to another
+    tet, two ET entries swapped across rows, a VV entry replaced, a TT
+    neighbour replaced."""
+    m = gen.small_grid(with_field=False)
+    with gale.Context.load(m, device=0) as ctx:
+        ctx.build(None, gale.ALL, gale.MODE_BATCHED)
+        ctx.synchronize()
+        d = {n: t.clone() for n, t in device_arrays(ctx).items()}
+        check_exact(ctx, d, m)
+
+        def planted(name, fn):
+            bad = {n: t.clone() for n, t in d.items()}
+            fn(bad[name])
+            with pytest.raises(AssertionError):
+                check_exact(ctx, bad, m)
+
+        def vt_move(a):
+            a[10] = (a[10] + 1) % m.tv.shape[0]
+
+        def et_swap(a):
+            i, j = 3, a.numel() // 2
+            a[i], a[j] = a[j].clone(), a[i].clone()
+
+        def vv_replace(a):
+            a[7] = a[8]
+
+        def tt_replace(a):
+            a[5] = (a[5] + 7) % m.tv.shape[0]
+
+        planted("vt_val", vt_move)
+        planted("et_val", et_swap)
+        planted("vv_val", vv_replace)
+        planted("tt_val", tt_replace)
