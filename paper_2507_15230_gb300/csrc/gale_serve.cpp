@@ -811,9 +811,20 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
     // first time (so that its own entry is admitted and published without a
     // hand-off):
     // consumer threads that compute between requests can fill every core
+    //
+    // While the entry builds in the device loop, the waiter watches its own
+    // done flag (mapped host memory) without the lock, yielding the core,
+    // and completes the entry itself as soon as the flag is set: timed
+    // waits of a few microseconds last tens of microseconds under the
+    // default timer slack, and the leader may not be running.
     constexpr int64_t kLeaderGapNs = 20000;
+    constexpr int64_t kWatchNs = 64000;
+    auto own_done = [&] {
+        return e->state == St::Building && e->ticket >= 0 &&
+               __atomic_load_n(s->h_done + (e->ticket % gale::kRingCap), __ATOMIC_ACQUIRE) == e->ticket;
+    };
     for (bool first = true; !ready(); first = false) {
-        if (first || gale::now_ns() - s->last_leader_ns > kLeaderGapNs) {
+        if (first || own_done() || gale::now_ns() - s->last_leader_ns > kLeaderGapNs) {
             s->pump();
             s->stats.requester_pumps++;
         }
@@ -823,7 +834,16 @@ gale_status gale_request(gale_ctx *ctx, int32_t cluster_id, uint32_t mask, int64
             s->stats.t_wait_ns += gale::now_ns() - t0;
             return fail(GALE_ETIMEOUT, "request timed out");
         }
-        e->cv.wait_for(lk, std::chrono::microseconds(20));
+        if (e->state == St::Building && e->ticket >= 0) {
+            const long long tk = e->ticket;  // the entry stays: this thread holds a reference
+            lk.unlock();
+            const int64_t until = gale::now_ns() + kWatchNs;
+            while (__atomic_load_n(s->h_done + (tk % gale::kRingCap), __ATOMIC_ACQUIRE) != tk && gale::now_ns() < until)
+                std::this_thread::yield();
+            lk.lock();
+        } else {
+            e->cv.wait_for(lk, std::chrono::microseconds(20));
+        }
     }
     if (e->state == St::Failed) {
         const gale_status f = e->fail;
