@@ -305,31 +305,42 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         if (int64_t(vm.size()) > kMaxLocal || ntot > kMaxLocal - 1) return 1;
         // degrees and distinct upper neighbours of own vertices over
         // [external | internal]
-        const int32_t own_lo = int32_t(below);
-        auto loc = [&](int32_t v) -> int32_t {
-            if (v >= v0 && v < v1) return own_lo + (v - v0);
-            return int32_t(std::lower_bound(vm.begin(), vm.begin() + nv_nb, v) - vm.begin());
-        };
         const int32_t nvo = v1 - v0;
-        std::vector<int32_t> deg(static_cast<size_t>(nvo), 0);
-        std::vector<std::vector<int32_t>> up(static_cast<size_t>(nvo));
-        auto count_row = [&](int32_t t) {
-            const int32_t *r = rows + 4 * int64_t(t);
-            for (int j = 0; j < 4; ++j)
-                if (r[j] >= v0 && r[j] < v1) {
-                    deg[r[j] - v0]++;
-                    for (int q = j + 1; q < 4; ++q) up[r[j] - v0].push_back(loc(r[q]));
-                }
-        };
-        for (int64_t i = 0; i < w.n_ext; ++i) count_row(w.ext[i]);
-        for (int64_t i = 0; i < w.n_int; ++i) count_row(w.itet(i));
+        std::vector<int32_t> vm_up, ufill(static_cast<size_t>(v1 - v0) + 1, 0);
+        // per own vertex: its incidences, and its upper neighbours (canonical
+        // ids; only their number of distinct values matters) bucketed in one
+        // array by a counting pass and a fill pass
+        std::vector<int32_t> deg(static_cast<size_t>(nvo), 0), uoff(static_cast<size_t>(nvo) + 1, 0);
+        for (int pass = 0; pass < 2; ++pass) {
+            auto row = [&](int32_t t) {
+                const int32_t *r = rows + 4 * int64_t(t);
+                for (int j = 0; j < 4; ++j)
+                    if (r[j] >= v0 && r[j] < v1) {
+                        const int32_t x = r[j] - v0;
+                        if (pass == 0) {
+                            deg[x]++;
+                            uoff[x + 1] += 3 - j;
+                        } else {
+                            for (int q = j + 1; q < 4; ++q) vm_up[uoff[x]++] = r[q];
+                        }
+                    }
+            };
+            if (pass == 1) {
+                for (int32_t x = 0; x < nvo; ++x) uoff[x + 1] += uoff[x];
+                vm_up.resize(size_t(uoff[nvo]));
+                std::copy(uoff.begin(), uoff.end() - 1, ufill.begin());
+                std::swap(uoff, ufill);  // uoff: fill cursors; ufill: row starts
+            }
+            for (int64_t i = 0; i < w.n_ext; ++i) row(w.ext[i]);
+            for (int64_t i = 0; i < w.n_int; ++i) row(w.itet(i));
+        }
         int32_t nvt = 0, mx = 0, mu = 0, ne = 0;
-        for (int32_t i = 0; i < nvo; ++i) {
-            nvt += deg[i];
-            mx = std::max(mx, deg[i]);
-            auto &u = up[i];
-            std::sort(u.begin(), u.end());
-            const int32_t nu = int32_t(std::unique(u.begin(), u.end()) - u.begin());
+        for (int32_t x = 0; x < nvo; ++x) {
+            nvt += deg[x];
+            mx = std::max(mx, deg[x]);
+            int32_t *b = vm_up.data() + ufill[x], *e = vm_up.data() + uoff[x];
+            std::sort(b, e);
+            const int32_t nu = int32_t(std::unique(b, e) - b);
             mu = std::max(mu, nu);
             ne += nu;
         }
