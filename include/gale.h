@@ -467,7 +467,20 @@ gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale_coboundary
  * size bin) and CTAs per SM of the persistent grid (0 = as many as fit). */
 gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm);
 
-/* Size bins: for each bin (up to max_bins) eight int32 values - members,
+/* Several small clusters per CTA (no counterpart in the paper, which runs a
+ * fixed 32 threads per segment; Section 4.6, Appendix A): every size bin of
+ * whole clusters in shared memory (not global-scratch, per-item or cut-
+ * cluster bins, nor bins of parts) whose plan at team_threads fits `teams`
+ * times in one CTA's shared memory is launched, in batched builds, with
+ * `teams` teams of team_threads threads per CTA, each team taking clusters
+ * on its own with barriers of its own.  team_threads: a multiple of 32;
+ * teams: 2..15 with team_threads * teams <= 512; teams = 0 turns it off.
+ * gale_get_bins reports it; gale_autotune also tries it.  The per-cluster
+ * form, serving and the allocation-free build still run one cluster per
+ * CTA under the same plan.  EINVAL on bad sizes. */
+gale_status gale_set_teams(gale_ctx *ctx, int32_t team_threads, int32_t teams);
+
+/* Size bins: for each bin (up to max_bins) nine int32 values - members,
  * threads per CTA, bytes of per-CTA working memory, CTAs per SM, persistent
  * grid size, 1 if the working memory is global scratch (too large for
  * shared memory) else 0, 1 if every member runs under its own shared-memory
@@ -475,8 +488,9 @@ gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm)
  * number of members that are parts of cut clusters (gale_mesh_desc
  * part_vertices), or -1 for a bin of cut clusters themselves, which batched
  * builds skip (they build the parts) and the per-cluster form, serving and
- * gale_build_clusters_noalloc use - into out[8*i .. 8*i+7].  Returns the
- * number of bins in *nbins. */
+ * gale_build_clusters_noalloc use, and the teams per CTA of its batched
+ * launches (0: one cluster per CTA; gale_set_teams) - into
+ * out[9*i .. 9*i+8].  Returns the number of bins in *nbins. */
 gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t *nbins);
 
 /* Members of the size bins: the work item ids of bin 0, then bin 1, ...

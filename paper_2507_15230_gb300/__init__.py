@@ -87,7 +87,7 @@ class ServeStats(ctypes.Structure):
 EXPORTS = ("gale_load_mesh", "gale_build_clusters", "gale_build_clusters_noalloc", "gale_synchronize", "gale_bulk_view", "gale_bulk_arrays",
            "gale_bulk_export", "gale_copy_to_host", "gale_build_export", "gale_request", "gale_release", "gale_serve_stats_get", "gale_get_permutations",
            "gale_get_intervals", "gale_get_rows", "gale_get_working_set", "gale_get_info", "gale_set_tuning",
-           "gale_autotune", "gale_get_bins", "gale_get_bin_members", "gale_enumerate", "gale_get_enumeration",
+           "gale_autotune", "gale_get_bins", "gale_get_bin_members", "gale_set_teams", "gale_enumerate", "gale_get_enumeration",
            "gale_boundary", "gale_build_coboundary", "gale_serve_configure", "gale_serve_set_lease", "gale_stream", "gale_last_launch_count", "gale_destroy", "gale_last_error")
 
 _lib = None
@@ -125,6 +125,7 @@ def load_library(build: bool = True):
     lib.gale_get_working_set.argtypes = [P, i32, P, ctypes.POINTER(i64), P, ctypes.POINTER(i64)]
     lib.gale_get_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.gale_set_tuning.argtypes = [P, i32, i32]
+    lib.gale_set_teams.argtypes = [P, i32, i32]
     lib.gale_autotune.argtypes = [P, u32, i32, P, i32]
     lib.gale_get_bin_members.argtypes = [P, P]
     lib.gale_enumerate.argtypes = [P, i32]
@@ -434,13 +435,19 @@ class Context:
         grid, spill (1: working memory in global scratch), per_item (1: each
         member runs under its own plan), parts (members that are parts of cut
         clusters; -1: a bin of the cut clusters themselves, which batched
-        builds skip)."""
+        builds skip), teams (clusters per CTA of its batched launches; 0:
+        one)."""
         n = ctypes.c_int32(0)
         _check(self._lib.gale_get_bins(self._h, None, 0, ctypes.byref(n)))
-        out = np.zeros(8 * max(n.value, 1), np.int32)
+        out = np.zeros(9 * max(n.value, 1), np.int32)
         _check(self._lib.gale_get_bins(self._h, _p(out), n.value, ctypes.byref(n)))
-        keys = ("clusters", "threads", "bytes", "ctas_per_sm", "grid", "spill", "per_item", "parts")
-        return [dict(zip(keys, out[8 * i:8 * i + 8].tolist())) for i in range(n.value)]
+        keys = ("clusters", "threads", "bytes", "ctas_per_sm", "grid", "spill", "per_item", "parts", "teams")
+        return [dict(zip(keys, out[9 * i:9 * i + 9].tolist())) for i in range(n.value)]
+
+    def set_teams(self, team_threads: int, teams: int):
+        """gale_set_teams: several small clusters per CTA in batched builds
+        (teams of team_threads threads; teams = 0 turns it off)."""
+        _check(self._lib.gale_set_teams(self._h, team_threads, teams))
 
     def bin_members(self) -> np.ndarray:
         """Work item ids of bin 0, bin 1, ... in launch order: clusters

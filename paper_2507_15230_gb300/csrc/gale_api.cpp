@@ -255,6 +255,19 @@ gale::Caps bin_caps(const gale_ctx *ctx, int32_t k) {
     return gale::caps_of(ctx->hm.stats[k], ctx->sizes.data() + size_t(5) * k);
 }
 const gale::SmemPlan *plans_of(gale_ctx *ctx, const gale::Bin &b) { return b.per_item ? ctx->d_plans : nullptr; }
+// persistent grid of a launch over n members (a team launch holds `teams` of them per CTA)
+int grid_of(const gale::Bin &b, int32_t n) {
+    const int32_t need = b.teams > 0 ? (n + b.teams - 1) / b.teams : n;
+    return std::max(1, std::min<int>(b.grid, need));
+}
+// bins whose batched launches may run several clusters per CTA: small
+// whole clusters under one merged plan in shared memory
+bool team_eligible(const gale_ctx *ctx, const gale::Bin &b) {
+    if (b.spill || b.per_item || b.cut) return false;
+    for (int32_t k : b.clusters)
+        if (k >= ctx->hm.K) return false;
+    return true;
+}
 
 }  // namespace
 
@@ -873,8 +886,9 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
                 const gale::Bin &bin = ctx->bins[b];
                 if (bin.cut) continue;  // its clusters' parts are in other bins
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b],
-                                        int32_t(bin.clusters.size()), ctx->d_err, ctx->d_tickets + b, bin.grid,
-                                        ctx->stream, scratch_of(ctx, bin), plans_of(ctx, bin));
+                                        int32_t(bin.clusters.size()), ctx->d_err, ctx->d_tickets + b,
+                                        grid_of(bin, int32_t(bin.clusters.size())), ctx->stream, scratch_of(ctx, bin),
+                                        plans_of(ctx, bin), bin.teams);
             }
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
             if (rc != 0) return cuda_fail(cudaError_t(rc), "capturing the batched build");
@@ -924,8 +938,8 @@ gale_status gale_build_clusters(gale_ctx *ctx, const int32_t *ids, int32_t n, ui
                 if (nb == 0) continue;
                 const gale::Bin &bin = ctx->bins[b];
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items, ctx->d_order_part + off[b], nb, ctx->d_err,
-                                        ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream,
-                                        scratch_of(ctx, bin), plans_of(ctx, bin));
+                                        ctx->d_tickets + b, grid_of(bin, nb), ctx->stream, scratch_of(ctx, bin),
+                                        plans_of(ctx, bin), bin.teams);
                 if (rc != 0) return cuda_fail(cudaError_t(rc), "batched launch");
                 ++launches;
             }
@@ -1124,8 +1138,8 @@ gale_status gale_build_export(gale_ctx *ctx, const int32_t *ids, int32_t n, uint
                 if (nb == 0) continue;
                 const gale::Bin &bin = ctx->bins[b];
                 rc = gale::launch_build(dm, bin.plan, ctx->d_items + j0, ctx->d_order_part + boff[c][b], nb,
-                                        ctx->d_err, ctx->d_tickets + b, std::min(bin.grid, nb), ctx->stream,
-                                        scratch_of(ctx, bin), plans_of(ctx, bin));
+                                        ctx->d_err, ctx->d_tickets + b, grid_of(bin, nb), ctx->stream,
+                                        scratch_of(ctx, bin), plans_of(ctx, bin), bin.teams);
                 if (rc != 0) return cuda_fail(cudaError_t(rc), "batched launch");
                 ++launches;
             }
@@ -1240,6 +1254,42 @@ gale_status gale_set_tuning(gale_ctx *ctx, int32_t threads, int32_t ctas_per_sm)
             g = nullptr;
         }
     return st;
+}
+
+gale_status gale_set_teams(gale_ctx *ctx, int32_t team_threads, int32_t teams) {
+    if (!ctx) return fail(GALE_EINVAL, "NULL context");
+    if (teams != 0 && (teams < 2 || teams > 15 || team_threads < 32 || team_threads % 32 != 0 ||
+                       team_threads * teams > 512))
+        return fail(GALE_EINVAL, "teams must be 0, or 2..15 teams of a multiple of 32 threads, at most 512 in all");
+    if (ctx->device < 0) return GALE_OK;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    const int smem_limit = gale::dynamic_smem_limit();
+    int max_total = 0;
+    for (auto &b : ctx->bins) {
+        if (!team_eligible(ctx, b)) continue;
+        if (teams == 0) {
+            b.teams = 0;
+            continue;
+        }
+        const gale::SmemPlan p = gale::plan_smem(b.plan.caps, team_threads);
+        if (int64_t(p.total) * teams > smem_limit) continue;
+        max_total = std::max(max_total, p.total * teams);
+        if (!gale::prepare_kernels(max_total)) return fail(GALE_ECUDA, "setting the kernels' shared memory limit failed");
+        const int per = gale::max_ctas_per_sm_teams(p, teams);
+        if (per < 1) continue;
+        b.plan = p;
+        b.teams = teams;
+        b.ctas_per_sm = per;
+        b.grid = std::max(1, per * ctx->sm_count);
+    }
+    for (auto &g : ctx->graphs)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return GALE_OK;
 }
 
 gale_status gale_get_bin_members(gale_ctx *ctx, int32_t *out) {
@@ -1374,10 +1424,52 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
                 }
             }
         }
+        // several clusters per CTA, one team of T threads each
+        int best_teams = 0;
+        if (team_eligible(ctx, bin)) {
+            for (int T : {32, 64, 128})
+                for (int tm : {2, 4, 8}) {
+                    if (T * tm > 512) continue;
+                    const gale::SmemPlan plan = gale::plan_smem(bin.plan.caps, T);
+                    if (int64_t(plan.total) * tm > smem_limit) continue;
+                    const int per = gale::max_ctas_per_sm_teams(plan, tm);
+                    if (per < 1) continue;
+                    gale::Bin probe;
+                    probe.teams = tm;
+                    probe.grid = per * ctx->sm_count;
+                    const int grid = grid_of(probe, nb);
+                    auto launch = [&]() {
+                        return gale::launch_build(dm, plan, ctx->d_items, ctx->d_order_all + ctx->order_all_off[b],
+                                                  nb, ctx->d_err, ctx->d_tickets + b, grid, ctx->stream, nullptr,
+                                                  nullptr, tm);
+                    };
+                    rc = launch();
+                    CUDA_TRY(cudaEventRecord(e0, ctx->stream));
+                    for (int r = 0; rc == 0 && r < reps; ++r) rc = launch();
+                    CUDA_TRY(cudaEventRecord(e1, ctx->stream));
+                    if (rc != 0) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return cuda_fail(cudaError_t(rc), "autotune launch");
+                    }
+                    CUDA_TRY(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                    ms /= float(reps);
+                    if (best < 0.f || ms < best) {
+                        best = ms;
+                        best_plan = plan;
+                        best_grid = probe.grid;
+                        best_per = per;
+                        best_teams = tm;
+                    }
+                }
+        }
         if (best >= 0.f) {
             bin.plan = best_plan;
             bin.grid = best_grid;
             bin.ctas_per_sm = best_per;
+            bin.teams = best_teams;
         }
         if (bin.per_item && !best_members.empty()) {
             for (size_t i = 0; i < bin.clusters.size(); ++i) ctx->h_plans[bin.clusters[i]] = best_members[i];
@@ -1391,7 +1483,7 @@ gale_status gale_autotune(gale_ctx *ctx, uint32_t mask, int32_t reps, float *bes
     cudaEventDestroy(e1);
     int max_total = 0;
     for (auto &bin : ctx->bins)
-        if (!bin.spill) max_total = std::max(max_total, bin.plan.total);
+        if (!bin.spill) max_total = std::max(max_total, bin.plan.total * std::max(1, bin.teams));
     gale::prepare_kernels(max_total);
     for (auto &g : ctx->graphs)
         if (g) {
@@ -1407,16 +1499,18 @@ gale_status gale_get_bins(gale_ctx *ctx, int32_t *out, int32_t max_bins, int32_t
     *nbins = int32_t(ctx->bins.size());
     for (int32_t b = 0; b < *nbins && b < max_bins && out; ++b) {
         const gale::Bin &bin = ctx->bins[b];
-        out[8 * b + 0] = int32_t(bin.clusters.size());
-        out[8 * b + 1] = bin.plan.threads;
-        out[8 * b + 2] = bin.plan.total;
-        out[8 * b + 3] = bin.ctas_per_sm;
-        out[8 * b + 4] = bin.grid;
-        out[8 * b + 5] = bin.spill ? 1 : 0;
-        out[8 * b + 6] = bin.per_item ? 1 : 0;
+        int32_t *o = out + 9 * b;
+        o[0] = int32_t(bin.clusters.size());
+        o[1] = bin.plan.threads;
+        o[2] = bin.plan.total;
+        o[3] = bin.ctas_per_sm;
+        o[4] = bin.grid;
+        o[5] = bin.spill ? 1 : 0;
+        o[6] = bin.per_item ? 1 : 0;
         int32_t parts = 0;
         for (int32_t k : bin.clusters) parts += k >= ctx->hm.K;
-        out[8 * b + 7] = bin.cut ? -1 : parts;
+        o[7] = bin.cut ? -1 : parts;
+        o[8] = bin.teams;
     }
     return GALE_OK;
 }

@@ -27,6 +27,8 @@ struct Bin {
                                     // launch envelope: block size and the largest member's shared memory
     bool cut = false;               // members are clusters cut into parts: batched builds run the parts
                                     // (items K..K+NP-1, in other bins) instead; the other forms use this bin
+    int teams = 0;                  // > 0: batched builds run `teams` clusters per CTA at once, one team of
+                                    // plan.threads threads each (the other forms run one per CTA)
 };
 
 struct DevAlloc {

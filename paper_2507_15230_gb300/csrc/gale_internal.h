@@ -246,9 +246,12 @@ int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids
 int bases_scratch_words(int32_t n);
 int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t *sizes, uint32_t mask,
                  const WorkItem *arrays_base, WorkItem *items, int64_t *totals_out, int64_t *bsum, void *stream);
+// teams > 0: several clusters per CTA, one team of plan.threads threads each
+// (`teams` of them per CTA, each with plan.total bytes of shared memory);
+// never with plans or gscratch.
 int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
                  int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch,
-                 const SmemPlan *plans = nullptr);
+                 const SmemPlan *plans = nullptr, int teams = 0);
 // One launch, one CTA, one work item (the per-cluster baseline form).
 int launch_build_one(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, int32_t index, int32_t *err,
                      void *stream, char *gscratch);
@@ -273,6 +276,8 @@ int serve_ctas_per_sm(const SmemPlan &plan);
 
 int kernel_smem_limit();
 int max_ctas_per_sm(const SmemPlan &plan, bool spill, bool per_item = false);
+// CTAs per SM of a team launch (0 if it cannot launch)
+int max_ctas_per_sm_teams(const SmemPlan &plan, int teams);
 // Sets the dynamic shared memory limit of the cluster kernels to smem
 // (clamped to dynamic_smem_limit()); false if the runtime refused.
 bool prepare_kernels(int smem);

@@ -157,37 +157,66 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
-// Exclusive scan of one value per thread over the block (any multiple of 32
-// threads up to 1024); scr needs 33 words.  Two __syncthreads.
-__device__ __forceinline__ int block_scan_thread(int v, int32_t *scr, int *total) {
-    const int nw = blockDim.x >> 5;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Who builds a cluster: the whole CTA, or a team - a warp-aligned slice of
+// it with a named barrier of its own (several small clusters per CTA).
+struct BlockTeam {
+    __device__ __forceinline__ int nt() const { return blockDim.x; }
+    __device__ __forceinline__ int tid() const { return threadIdx.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ int sync_or(int p) const { return __syncthreads_or(p); }
+};
+struct SliceTeam {
+    int n;    // threads (a multiple of 32)
+    int t;    // this thread's index in the team
+    int bar;  // named barrier id (1..15; 0 is __syncthreads')
+    __device__ __forceinline__ int nt() const { return n; }
+    __device__ __forceinline__ int tid() const { return t; }
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory"); }
+    __device__ __forceinline__ int sync_or(int p) const {
+        int r;
+        asm volatile(
+            "{\n\t.reg .pred pin, pout;\n\tsetp.ne.s32 pin, %1, 0;\n\t"
+            "bar.red.or.pred pout, %2, %3, pin;\n\tselp.s32 %0, 1, 0, pout;\n\t}"
+            : "=r"(r)
+            : "r"(p), "r"(bar), "r"(n)
+            : "memory");
+        return r;
+    }
+};
+
+// Exclusive scan of one value per thread over the team (any multiple of 32
+// threads up to 1024); scr needs 33 words.  Two team barriers.
+template <class Team>
+__device__ __forceinline__ int block_scan_thread(const Team &tm, int v, int32_t *scr, int *total) {
+    const int nw = tm.nt() >> 5;
+    const int lane = tm.tid() & 31, warp = tm.tid() >> 5;
     const int incl = warp_incl_scan(v, lane);
     if (lane == 31) scr[warp] = incl;
-    __syncthreads();
+    tm.sync();
     if (warp == 0) {
         const int w = lane < nw ? scr[lane] : 0;
         const int wi = warp_incl_scan(w, lane);
         if (lane < nw) scr[lane] = wi - w;
         if (lane == 31) scr[32] = wi;
     }
-    __syncthreads();
+    tm.sync();
     *total = scr[32];
     return scr[warp] + incl - v;
 }
 
-// Exclusive scans of three values per thread over the block, in place;
+// Exclusive scans of three values per thread over the team, in place;
 // totals to t[0..2].  scr needs 99 words.  Ends synced.
-__device__ __forceinline__ void block_scan3(int &a, int &b, int &c, int32_t *scr, int *t) {
-    const int nw = blockDim.x >> 5;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+template <class Team>
+__device__ __forceinline__ void block_scan3(const Team &tm, int &a, int &b, int &c, int32_t *scr, int *t) {
+    const int nw = tm.nt() >> 5;
+    const int lane = tm.tid() & 31, warp = tm.tid() >> 5;
     const int ia = warp_incl_scan(a, lane), ib = warp_incl_scan(b, lane), ic = warp_incl_scan(c, lane);
     if (lane == 31) {
         scr[warp] = ia;
         scr[33 + warp] = ib;
         scr[66 + warp] = ic;
     }
-    __syncthreads();
+    tm.sync();
     if (warp == 0) {
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
@@ -197,29 +226,30 @@ __device__ __forceinline__ void block_scan3(int &a, int &b, int &c, int32_t *scr
             if (lane == 31) scr[33 * s + 32] = wi;
         }
     }
-    __syncthreads();
+    tm.sync();
     t[0] = scr[32];
     t[1] = scr[65];
     t[2] = scr[98];
     a = scr[warp] + ia - a;
     b = scr[33 + warp] + ib - b;
     c = scr[66 + warp] + ic - c;
-    __syncthreads();
+    tm.sync();
 }
 
 // Length of each thread's contiguous range when n items are split over the
-// block: odd, so that neighbouring threads start in different banks.
-__device__ __forceinline__ int range_len(int n) {
-    const int per = (n + int(blockDim.x) - 1) / int(blockDim.x);
+// team: odd, so that neighbouring threads start in different banks.
+template <class Team>
+__device__ __forceinline__ int range_len(const Team &tm, int n) {
+    const int per = (n + tm.nt() - 1) / tm.nt();
     return per > 1 ? (per | 1) : per;
 }
 
-// dst[j] = f(j) for j < n over the block, four loads in flight per thread
+// dst[j] = f(j) for j < n over the team, four loads in flight per thread
 // before their stores (the values come through L2 from the block's maps).
-template <typename F>
-__device__ __forceinline__ void copy_out(int32_t *__restrict__ dst, int n, F f) {
-    const int NT = blockDim.x;
-    int j = threadIdx.x;
+template <class Team, typename F>
+__device__ __forceinline__ void copy_out(const Team &tm, int32_t *__restrict__ dst, int n, F f) {
+    const int NT = tm.nt();
+    int j = tm.tid();
     for (; j + 3 * NT < n; j += 4 * NT) {
         const int32_t a = f(j), b = f(j + NT), c = f(j + 2 * NT), d = f(j + 3 * NT);
         dst[j] = a;
@@ -231,20 +261,21 @@ __device__ __forceinline__ void copy_out(int32_t *__restrict__ dst, int n, F f) 
 }
 
 // Exclusive scan in place of a[0..n); returns the total.  Ends synced.
-__device__ int block_scan_array(int32_t *a, int n, int32_t *scr) {
-    const int per = range_len(n);
-    const int b = min(n, int(threadIdx.x) * per);
+template <class Team>
+__device__ int block_scan_array(const Team &tm, int32_t *a, int n, int32_t *scr) {
+    const int per = range_len(tm, n);
+    const int b = min(n, tm.tid() * per);
     const int e = min(n, b + per);
     int s = 0;
     for (int i = b; i < e; ++i) s += a[i];
     int total;
-    int run = block_scan_thread(s, scr, &total);
+    int run = block_scan_thread(tm, s, scr, &total);
     for (int i = b; i < e; ++i) {
         const int v = a[i];
         a[i] = run;
         run += v;
     }
-    __syncthreads();
+    tm.sync();
     return total;
 }
 
@@ -287,12 +318,12 @@ constexpr uint32_t kMatch = 1u << 20;
 // ---------------------------------------------------------------------------
 // PART: the item is a part of a cut cluster (block header part != 0); the
 // whole-cluster instances carry none of the part logic.
-template <bool COUNT, bool SPILL, bool PART>
-__device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, int64_t words,
+template <bool COUNT, bool SPILL, bool PART, class Team>
+__device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, int64_t words,
                             uint32_t mask, const WorkItem *it, int64_t *sizes_out, int32_t *err, uint64_t *bar,
                             uint32_t &phase) {
-    const int NT = blockDim.x, NWARP = NT >> 5;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NT = tm.nt(), NWARP = NT >> 5;
+    const int tid = tm.tid(), lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const Caps &caps = plan.caps;
     const int32_t *__restrict__ g = m.blocks + blk_word;
@@ -310,11 +341,11 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         flag[0] = fits;
         flag[1] = issued;
     }
-    __syncthreads();
+    tm.sync();
     const bool fits = flag[0] != 0, issued = flag[1] != 0;
     if (!fits) {
         if (tid == 0) atomicOr(err, ERR_CAPACITY);
-        __syncthreads();
+        tm.sync();
         return true;
     }
     if (SPILL) {
@@ -322,10 +353,10 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         int4 *dst = reinterpret_cast<int4 *>(S.blk);
         const int n4 = int(words >> 2);
         for (int i = tid; i < n4; i += NT) dst[i] = __ldg(src + i);
-        __syncthreads();
+        tm.sync();
     } else if (issued) {
         bool ok = mbar_wait(bar, phase);
-        if (__syncthreads_or(!ok)) {
+        if (tm.sync_or(!ok)) {
             if (tid == 0) atomicOr(err, ERR_TIMEOUT);
             if (!ok) mbar_wait(bar, phase);  // the copy may still be in flight
             return false;
@@ -346,7 +377,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                         blk_words(h.nv_loc, h.n_ext, h.n_own, h.n_halo, h.n_bnd, xmap) == words;
         if (!ok) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
-            __syncthreads();
+            tm.sync();
             return true;
         }
     }
@@ -399,7 +430,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             if (!(i & 1)) cw32[i >> 1] = 0u;
             mk[i] = 0u;
         }
-        __syncthreads();
+        tm.sync();
         for (int i = c0 + lane; i < c1; i += 32) {
             const uint2 r = rows[i];
 #pragma unroll
@@ -408,15 +439,15 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 if (d < nvo_u) atomicAdd(&cw32[(warp * pad + int(d)) >> 1], 1u << (16 * (d & 1u)));
             }
         }
-        __syncthreads();
+        tm.sync();
         // row lengths -> offsets; every (warp, vertex) gets its first position
         for (int v = tid; v < nvo; v += NT) {
             int tot = 0;
             for (int w = 0; w < NWARP; ++w) tot += int(cw[w * pad + v]);
             S.vt_off[v] = tot;
         }
-        __syncthreads();
-        vt_total = block_scan_array(S.vt_off, nvo, S.scan);
+        tm.sync();
+        vt_total = block_scan_array(tm, S.vt_off, nvo, S.scan);
         bool bad = vt_total > caps.n_vt;
         for (int v = tid; v < nvo; v += NT) {
             const int d = (v + 1 < nvo ? S.vt_off[v + 1] : vt_total) - S.vt_off[v];
@@ -429,7 +460,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             }
         }
         if (tid == 0) S.vt_off[nvo] = vt_total;
-        if (__syncthreads_or(bad)) {
+        if (tm.sync_or(bad)) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             return true;
         }
@@ -466,12 +497,12 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 }
             __syncwarp();
         }
-        __syncthreads();
+        tm.sync();
         if (COUNT) {
             if (tid == 0) sizes_out[SZ_VT] = vt_total;
         } else if ((mask & R_VT) && !vt_copy_later) {
             for (int i = tid; i <= nvo; i += NT) it->vt_off[i] = S.vt_off[i] + b_vt;
-            copy_out(it->vt_val, vt_total, [&](int j) { return gtet(S.vt_list[j]); });
+            copy_out(tm, it->vt_val, vt_total, [&](int j) { return gtet(S.vt_list[j]); });
         }
     }
     if (!(COUNT || do_vv || do_et || want_tt)) return true;
@@ -486,7 +517,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         uint32_t *nb32 = reinterpret_cast<uint32_t *>(S.nbr);
         for (int i = tid; i < 2 * n_own; i += NT) nb32[i] = FULL;
     }
-    __syncthreads();
+    tm.sync();
     int etv = 0;  // ET entries: each own vertex of a tet, once per vertex above it
     for (int i = tid; i < n_vtets; i += NT) {
         const uint2 r = rows[i];
@@ -523,7 +554,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             atomicOr(row + (v2 >> 5), 1u << (v2 & 31));
         }
     }
-    __syncthreads();
+    tm.sync();
 
     // ---------------- C2. VV rows and owned edges, per own vertex ----------
     int tot[3];  // VV entries, owned edges, ET entries
@@ -542,10 +573,10 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             S.c_vv[x] = cv;
             S.c_e[x] = ce;
         }
-        __syncthreads();
+        tm.sync();
         // exclusive scans of both count arrays, and the ET total
         {
-            const int per = range_len(nvo);
+            const int per = range_len(tm, nvo);
             const int x0 = min(nvo, tid * per), x1 = min(nvo, x0 + per);
             int sv = 0, se = 0;
             for (int x = x0; x < x1; ++x) {
@@ -553,7 +584,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 se += S.c_e[x];
             }
             int et0 = etv;
-            block_scan3(sv, se, et0, S.scan, tot);
+            block_scan3(tm, sv, se, et0, S.scan, tot);
             for (int x = x0; x < x1; ++x) {
                 const int a = S.c_vv[x], b = S.c_e[x];
                 S.c_vv[x] = sv;
@@ -570,7 +601,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             return true;
         }
-        __syncthreads();
+        tm.sync();
         if (vt_copy_later && warp >= copy_warp0) {
             // VT out, on the warps the per-vertex loop below leaves idle
             const int t0 = tid - copy_warp0 * 32, nt = NT - copy_warp0 * 32;
@@ -626,7 +657,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             }
             bad |= erun - e_first > 255;
         }
-        if (__syncthreads_or(bad)) {
+        if (tm.sync_or(bad)) {
             if (tid == 0) atomicOr(err, ERR_CAPACITY);
             return true;
         }
@@ -637,11 +668,11 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         if (do_vv) {
             for (int i = tid; i <= nvo; i += NT) it->vv_off[i] = S.c_vv[i] + b_vv;
-            copy_out(it->vv_val, tot[0], [&](int j) { return vmap[S.st_v[j]]; });
+            copy_out(tm, it->vv_val, tot[0], [&](int j) { return vmap[S.st_v[j]]; });
         }
         if (do_et) {
             for (int i = tid; i <= nvo; i += NT) it->eu_off[i] = S.c_e[i] + b_e;
-            copy_out(it->e_w, tot[1], [&](int e) { return vmap[S.st_w[e]]; });
+            copy_out(tm, it->e_w, tot[1], [&](int e) { return vmap[S.st_w[e]]; });
             if (tid == 0) it->et_off[tot[1]] = tot[2] + b_et;
         }
     }
@@ -649,9 +680,9 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
     const int tot_e = tot[1], tot_etv = tot[2];
     const int nch = plan.nch;
     uint32_t *em = S.emask;
-    __syncthreads();  // VV and endpoint staging are dead: r2 takes the edge masks
+    tm.sync();  // VV and endpoint staging are dead: r2 takes the edge masks
     for (int i = tid; i < tot_e * nch; i += NT) em[i] = 0u;
-    __syncthreads();
+    tm.sync();
 
     // ---------------- C3. edge tet masks, per tet ----------------
     // bit j of mask(x, w): the j-th tet of VT(x) contains w; every own
@@ -690,7 +721,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             if (x2 < nvo_u) mark(x2, v3, j2);
         }
     }
-    __syncthreads();
+    tm.sync();
 
     // ---------------- C5. TT links of faces with an own lowest vertex ------
     if (want_tt) {
@@ -735,21 +766,21 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         }
         if (flags) atomicOr(err, flags);
     }
-    __syncthreads();  // bitmaps and rank prefixes are dead: r1 takes the ET staging
+    tm.sync();  // bitmaps and rank prefixes are dead: r1 takes the ET staging
 
     // ---------------- C4. ET rows, per edge ----------------
     if (do_et) {
         uint16_t *st_et = S.st_et;
-        const int per = range_len(tot_e);
+        const int per = range_len(tm, tot_e);
         const int e0 = min(tot_e, tid * per), e1 = min(tot_e, e0 + per);
         int cnt = 0;
         for (int e = e0; e < e1; ++e)
             for (int c = 0; c < nch; ++c) cnt += __popc(em[e * nch + c]);
         int total;
-        int run = block_scan_thread(cnt, S.scan, &total);
+        int run = block_scan_thread(tm, cnt, S.scan, &total);
         if (total != tot_etv) {  // every (own vertex, tet, upper vertex) sets one distinct bit
             if (tid == 0) atomicOr(err, ERR_BAD_BLOCK);
-            __syncthreads();
+            tm.sync();
             return true;
         }
         // own vertex holding edge e0: the largest x with c_e[x] <= e0
@@ -776,10 +807,10 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             }
             em[e * nch] = uint32_t(t0);  // the edge's first mask word now holds its row offset
         }
-        __syncthreads();
+        tm.sync();
         for (int e = tid; e < tot_e; e += NT) it->et_off[e] = int32_t(em[e * nch]) + b_et;
-        copy_out(it->et_val, tot_etv, [&](int j) { return gtet(st_et[j]); });
-        __syncthreads();  // ET staging is dead: r1 takes the face hash
+        copy_out(tm, it->et_val, tot_etv, [&](int j) { return gtet(st_et[j]); });
+        tm.sync();  // ET staging is dead: r1 takes the face hash
     }
 
     if (want_tt) {
@@ -787,7 +818,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
         const uint32_t hmask = uint32_t(caps.hcap - 1);
         uint32_t *hash = S.hash;
         for (int i = tid; i < caps.hcap; i += NT) hash[i] = 0u;
-        __syncthreads();
+        tm.sync();
         int32_t flags = 0;
         // the internal tets whose face (b, c, d) has no own vertex
         const uint16_t *bnd =
@@ -812,7 +843,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             }
             if (probe == caps.hcap) flags |= ERR_HASH_FULL;
         }
-        __syncthreads();
+        tm.sync();
         const int n_halo = h.n_halo;
         for (int j = tid; j < 4 * n_halo; j += NT) {  // one (halo tet, face) per step
             const int tl = n_vtets + (j >> 2);
@@ -831,7 +862,7 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             }
         }
         if (flags) atomicOr(err, flags);
-        __syncthreads();
+        tm.sync();
         // ---------------- E. TT rows ----------------
         int32_t *tcnt = S.tcnt;
         for (int i = tid; i < n_own; i += NT) {
@@ -839,14 +870,14 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
             tcnt[i] = ((nb.x & 0xffffu) != 0xffffu) + ((nb.x >> 16) != 0xffffu) + ((nb.y & 0xffffu) != 0xffffu) +
                       ((nb.y >> 16) != 0xffffu);
         }
-        __syncthreads();
+        tm.sync();
         if (COUNT && part) {
             // row lengths of the part's own internal tets, by canonical id
             for (int i = tid; i < n_own; i += NT)
                 if ((rows[n_ext + i].x & 0xffffu) - uint32_t(lo) < nvo_u) m.tt_pos[gtet(n_ext + i)] = tcnt[i];
-            __syncthreads();
+            tm.sync();
         }
-        const int tot_tt = block_scan_array(tcnt, n_own, S.scan);
+        const int tot_tt = block_scan_array(tm, tcnt, n_own, S.scan);
         if (COUNT) {
             if (tid == 0) sizes_out[SZ_TT] = tot_tt;
         } else if (part) {
@@ -904,11 +935,11 @@ __device__ bool run_cluster(const DevMesh &m, const SmemPlan &plan, const Smem &
                 if (w3 != INT32_MAX) o[3] = uint16_t(l3);
             }
             if (tid == 0) it->tt_off[n_own] = tot_tt;
-            __syncthreads();
-            copy_out(it->tt_val, tot_tt, [&](int j) { return gtet(S.st_tt[j]); });
+            tm.sync();
+            copy_out(tm, it->tt_val, tot_tt, [&](int j) { return gtet(S.st_tt[j]); });
         }
     }
-    __syncthreads();
+    tm.sync();
     return true;
 }
 
@@ -917,8 +948,9 @@ template <bool COUNT, bool SPILL>
 __device__ __forceinline__ bool run_item(bool part, const DevMesh &m, const SmemPlan &plan, const Smem &S,
                                          int64_t blk_word, int64_t words, uint32_t mask, const WorkItem *it,
                                          int64_t *sizes_out, int32_t *err, uint64_t *bar, uint32_t &phase) {
-    if (part) return run_cluster<COUNT, SPILL, true>(m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
-    return run_cluster<COUNT, SPILL, false>(m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
+    const BlockTeam tm;
+    if (part) return run_cluster<COUNT, SPILL, true>(tm, m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
+    return run_cluster<COUNT, SPILL, false>(tm, m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
 }
 
 // SPILL: the cluster's regions live in a per-CTA slice of global scratch
@@ -1025,8 +1057,53 @@ __global__ void __launch_bounds__(kMaxThreads) build_one_kernel(DevMesh m, SmemP
         if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
         return;
     }
-    run_cluster<false, SPILL, false>(m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k], s_item.mask,
+    run_cluster<false, SPILL, false>(BlockTeam{}, m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k], s_item.mask,
                               &s_item, nullptr, err, &s_bar, phase);
+}
+
+// ---------------------------------------------------------------------------
+// Several small clusters per CTA.  Each team of team_n threads (a multiple
+// of 32; the block holds blockDim.x / team_n teams) takes clusters from the
+// ticket on its own and builds each in its own slice of the dynamic shared
+// memory, with a named barrier and a bulk-copy barrier of its own, so a
+// small cluster's barriers involve only its team.
+// ---------------------------------------------------------------------------
+constexpr int kMaxTeams = 15;  // named barriers 1..15
+constexpr int kMaxTeamBlock = 512;
+
+__global__ void __launch_bounds__(kMaxTeamBlock) build_kernel_team(DevMesh m, SmemPlan plan, const WorkItem *items,
+                                                                const int32_t *order, int32_t n, int32_t *err,
+                                                                int32_t *ticket, int team_n) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int32_t s_idx[kMaxTeams];
+    __shared__ WorkItem s_item[kMaxTeams];
+    __shared__ __align__(8) uint64_t s_bar[kMaxTeams];
+    const int g = int(threadIdx.x) / team_n;
+    if (g >= kMaxTeams) return;  // (the host never launches more teams)
+    const SliceTeam tm{team_n, int(threadIdx.x) - g * team_n, 1 + g};
+    const Smem S = carve(smem + size_t(g) * size_t(plan.total), plan);
+    if (tm.tid() == 0) mbar_init(&s_bar[g]);
+    tm.sync();
+    uint32_t phase = 0;
+    for (;;) {
+        if (tm.tid() == 0) {
+            const int idx = atomicAdd(ticket, 1);
+            s_idx[g] = idx;
+            if (idx < n) s_item[g] = items[order ? order[idx] : idx];
+        }
+        tm.sync();
+        if (s_idx[g] >= n) break;
+        const int k = s_item[g].k;
+        if (k < 0 || k >= m.K) {
+            if (tm.tid() == 0) atomicOr(err, ERR_BAD_ITEM);
+            tm.sync();
+            continue;
+        }
+        if (!run_cluster<false, false, false>(tm, m, plan, S, s_item[g].blk, m.blk_off[k + 1] - m.blk_off[k],
+                                              s_item[g].mask, &s_item[g], nullptr, err, &s_bar[g], phase))
+            return;
+        tm.sync();  // the next claim rewrites this team's item
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1194,7 +1271,7 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, const SmemPlan *
             load_plan(s_plan, plans + s_item.k);  // the cluster's own plan
             __syncthreads();
             const Smem S = carve(smem, s_plan);
-            go_on = run_cluster<false, false, false>(m, s_plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
+            go_on = run_cluster<false, false, false>(BlockTeam{}, m, s_plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
                                               s_item.mask, &s_item, nullptr, err, &s_bar, phase);
         } else if (threadIdx.x == 0) {
             atomicOr(err, ERR_BAD_ITEM);
@@ -1475,6 +1552,7 @@ int dynamic_smem_limit() {
     if (cudaFuncGetAttributes(&a, serve_kernel) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
     if (cudaFuncGetAttributes(&a, build_kernel_pi) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
     if (cudaFuncGetAttributes(&a, count_kernel_pi) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
+    if (cudaFuncGetAttributes(&a, build_kernel_team) == cudaSuccess) stat = std::max(stat, int(a.sharedSizeBytes));
     cudaGetLastError();
     return optin - stat;
 }
@@ -1497,6 +1575,7 @@ bool prepare_kernels(int smem) {
     ok &= cudaFuncSetAttribute(count_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     ok &= cudaFuncSetAttribute(build_kernel_pi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     ok &= cudaFuncSetAttribute(count_kernel_pi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(build_kernel_team, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     cudaGetLastError();
     if (ok) granted[d] = smem;
     return ok;
@@ -1517,6 +1596,17 @@ int max_ctas_per_sm(const SmemPlan &plan, bool spill, bool per_item) {
     }
     if (e1 != cudaSuccess || e2 != cudaSuccess) return 0;
     return a < b ? a : b;
+}
+
+int max_ctas_per_sm_teams(const SmemPlan &plan, int teams) {
+    if (teams < 1 || teams > kMaxTeams || plan.threads % 32 || plan.threads * teams > kMaxTeamBlock) return 0;
+    int a = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, build_kernel_team, plan.threads * teams,
+                                                      size_t(plan.total) * teams) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return a;
 }
 
 int launch_count_pass(const DevMesh &m, const SmemPlan &plan, const int32_t *ids, int32_t n, int64_t *sizes_out,
@@ -1548,10 +1638,16 @@ int launch_bases(const DevMesh &m, const int32_t *ids, int32_t n, const int64_t 
 }
 
 int launch_build(const DevMesh &m, const SmemPlan &plan, const WorkItem *items, const int32_t *order, int32_t n,
-                 int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, const SmemPlan *plans) {
+                 int32_t *err, int32_t *ticket, int grid, void *stream, char *gscratch, const SmemPlan *plans,
+                 int teams) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(ticket, 0, sizeof(int32_t), s);
-    if (plans) build_kernel_pi<<<grid, plan.threads, plan.total, s>>>(m, plans, items, order, n, err, ticket);
+    if (teams > 0) {
+        if (plans || gscratch || teams > kMaxTeams || plan.threads * teams > kMaxTeamBlock)
+            return int(cudaErrorInvalidValue);
+        build_kernel_team<<<grid, plan.threads * teams, size_t(plan.total) * teams, s>>>(m, plan, items, order, n, err,
+                                                                                        ticket, plan.threads);
+    } else if (plans) build_kernel_pi<<<grid, plan.threads, plan.total, s>>>(m, plans, items, order, n, err, ticket);
     else if (gscratch) build_kernel<true><<<grid, plan.threads, 0, s>>>(m, plan, items, order, n, err, ticket, gscratch);
     else build_kernel<false><<<grid, plan.threads, plan.total, s>>>(m, plan, items, order, n, err, ticket, nullptr);
     return int(cudaGetLastError());
