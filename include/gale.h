@@ -207,10 +207,14 @@ typedef struct {
  *     cluster (a counting pass on the GPU), used for output placement and
  *     cache admission.
  * The cluster working sets are copied to device memory once, as the paper
- * copies its initialised arrays to GPU global memory.  TT needs a manifold
- * mesh (no triangle in more than two tets): with GALE_TT in the precondition
- * mask, a non-manifold mesh fails with EDEVICE (non-manifold bit); without
- * it, VT, VV and ET of such a mesh are built as usual.
+ * copies its initialised arrays to GPU global memory.  TT of a non-manifold
+ * mesh (a triangle in three or more tets) is built as defined: every tet
+ * sharing three vertices with t.  A cluster with such a triangle among its
+ * internal tets' faces finds its TT rows by a slower pass over its block.
+ * The one exception is a cluster cut into parts (too large for one CTA):
+ * with GALE_TT in the precondition mask it fails with EDEVICE (non-manifold
+ * bit), since parts assume at most one partner per face; without GALE_TT,
+ * or with cutting off (part_vertices < 0), the mesh loads.
  * On success *out owns all of it; release with gale_destroy.
  */
 gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out);

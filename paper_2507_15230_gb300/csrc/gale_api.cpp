@@ -87,7 +87,9 @@ int threads_for(const gale_ctx *ctx, const gale::ClusterStat &s) {
 // occupancy tier (4, 3, 2, 1 CTAs per SM).  Items whose plan exceeds the
 // shared memory of one CTA go to spill bins: the same kernel with its
 // regions in a per-CTA slice of global scratch.  Cut clusters get bins of
-// their own, which batched builds skip (they run the parts).
+// their own, which batched builds skip (they run the parts).  Non-manifold
+// clusters (the counting pass marks them) get per-item bins of their own:
+// the hot shared-memory kernel leaves out the general TT pass they need.
 gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     const int32_t K = ctx->hm.K;
     const int32_t NI = K + ctx->hm.NP;
@@ -101,7 +103,7 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         return gale::caps_of(ctx->hm.stats[k], with_sizes ? ctx->sizes.data() + size_t(5) * k : nullptr);
     };
     std::vector<int32_t> need(NI), thr(NI);
-    std::vector<uint8_t> big(NI), cut(NI, 0);
+    std::vector<uint8_t> big(NI), cut(NI, 0), gen(NI, 0);
     for (int32_t k = 0; k < NI; ++k) {
         if (ctx->hm.stats[k].max_up > 255)
             return fail(GALE_EINVAL, "cluster " + std::to_string(k < K ? k : ctx->hm.parts[k - K].k) +
@@ -110,12 +112,14 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         need[k] = gale::plan_smem(caps_k(k), thr[k]).total;
         big[k] = need[k] > smem_cta;
         if (k < K) cut[k] = ctx->hm.part_first[k + 1] > ctx->hm.part_first[k];
+        if (with_sizes && k < K && size_t(k) < ctx->tt_general.size()) gen[k] = ctx->tt_general[k] != 0 && !big[k];
     }
     std::vector<int32_t> idx(NI);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
         if (cut[a] != cut[b]) return cut[a] < cut[b];
         if (big[a] != big[b]) return big[a] < big[b];
+        if (gen[a] != gen[b]) return gen[a] < gen[b];
         return thr[a] != thr[b] ? thr[a] < thr[b] : need[a] < need[b];
     });
     std::vector<int> tiers;
@@ -124,7 +128,7 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
     ctx->bin_of.assign(NI, -1);
     size_t tier = 0;
     int cur_thr = 0;
-    bool cur_big = false, cur_cut = false;
+    bool cur_big = false, cur_cut = false, cur_gen = false;
     gale::Caps cur{};
     std::vector<int32_t> members;
     auto close = [&]() {
@@ -133,6 +137,7 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         b.plan = gale::plan_smem(cur, cur_thr);
         b.spill = cur_big;
         b.cut = cur_cut;
+        b.tt_general = cur_gen;
         std::stable_sort(members.begin(), members.end(),
                          [&](int32_t a, int32_t c) { return need[a] > need[c]; });  // largest first
         b.clusters = members;
@@ -142,13 +147,15 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         cur = gale::Caps{};
     };
     for (int32_t k : idx) {
-        if (!members.empty() && (thr[k] != cur_thr || bool(big[k]) != cur_big || bool(cut[k]) != cur_cut)) {
+        if (!members.empty() && (thr[k] != cur_thr || bool(big[k]) != cur_big || bool(cut[k]) != cur_cut ||
+                                 bool(gen[k]) != cur_gen)) {
             close();
             tier = 0;
         }
         cur_thr = thr[k];
         cur_big = big[k];
         cur_cut = cut[k];
+        cur_gen = gen[k];
         gale::Caps m = members.empty() ? caps_k(k) : merge(cur, caps_k(k));
         if (!cur_big) {
             int tot = gale::plan_smem(m, cur_thr).total;
@@ -180,10 +187,16 @@ gale_status plan_bins(gale_ctx *ctx, bool with_sizes) {
         using Key = std::pair<int, bool>;
         std::map<Key, int> ntop;
         for (auto &b : ctx->bins)
-            if (!b.spill && b.plan.total > tiers[2]) ntop[Key(b.plan.threads, b.cut)]++;
+            if (!b.spill && !b.tt_general && b.plan.total > tiers[2]) ntop[Key(b.plan.threads, b.cut)]++;
         std::vector<gale::Bin> kept;
         std::map<Key, gale::Bin> top;  // merged bins
         for (auto &b : ctx->bins) {
+            if (b.tt_general) {  // each member under its own plan, in build_kernel_pi
+                for (int32_t k : b.clusters) ctx->h_plans[k] = gale::plan_smem(caps_k(k), b.plan.threads);
+                b.per_item = true;
+                kept.push_back(std::move(b));
+                continue;
+            }
             if (b.spill || b.plan.total <= tiers[2] || ntop[Key(b.plan.threads, b.cut)] < 2) {
                 kept.push_back(std::move(b));
                 continue;
@@ -357,6 +370,7 @@ gale::DevMesh dev_mesh(gale_ctx *ctx) {
     m.NP = ctx->hm.NP;
     m.parts = ctx->d_parts;
     m.tt_pos = ctx->d_tt_pos;
+    m.tt_general = ctx->d_tt_general;
     return m;
 }
 
@@ -394,6 +408,7 @@ gale_status check_device_error(gale_ctx *ctx) {
 gale_status count_pass(gale_ctx *ctx) {
     const int32_t K = ctx->hm.K, NP = ctx->hm.NP, NI = K + NP;
     CUDA_TRY(cudaMemsetAsync(ctx->d_sizes, 0, sizeof(int64_t) * 5 * NI, ctx->stream));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_tt_general, 0, sizeof(int32_t) * std::max(K, 1), ctx->stream));
     for (size_t b = 0; b < ctx->bins.size(); ++b) {
         const gale::Bin &bin = ctx->bins[b];
         int rc = gale::launch_count_pass(dev_mesh(ctx), bin.plan, ctx->d_order_ids + ctx->order_all_off[b],
@@ -407,6 +422,10 @@ gale_status count_pass(gale_ctx *ctx) {
     ctx->sizes.resize(size_t(5) * NI);
     CUDA_TRY(cudaMemcpyAsync(ctx->sizes.data(), ctx->d_sizes, sizeof(int64_t) * 5 * NI, cudaMemcpyDeviceToHost,
                              ctx->stream));
+    ctx->tt_general.assign(size_t(K), 0);
+    if (K > 0)
+        CUDA_TRY(cudaMemcpyAsync(ctx->tt_general.data(), ctx->d_tt_general, sizeof(int32_t) * K,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     for (int a = 0; a < 5; ++a) ctx->totals[a] = 0;
     for (int32_t k = 0; k < K; ++k)
@@ -772,6 +791,7 @@ gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out) {
     ctx->d_I_V = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * (K + 1)));
     ctx->d_I_T = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * (K + 1)));
     ctx->d_sizes = static_cast<int64_t *>(ctx->dalloc(sizeof(int64_t) * 5 * NI));
+    ctx->d_tt_general = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * std::max(K, 1)));
     ctx->d_err = static_cast<int32_t *>(ctx->dalloc(64));
     ctx->d_tickets = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * gale::kMaxBins));
     ctx->d_ids = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * NI));
@@ -787,7 +807,8 @@ gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out) {
         ctx->d_tt_pos = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * std::max<int64_t>(1, hm.nt)));
         ctx->d_all_items = static_cast<int32_t *>(ctx->dalloc(sizeof(int32_t) * ctx->all_items.size()));
     }
-    if (!ctx->d_blocks || !ctx->d_blk_off || !ctx->d_I_V || !ctx->d_I_T || !ctx->d_sizes || !ctx->d_err ||
+    if (!ctx->d_blocks || !ctx->d_blk_off || !ctx->d_I_V || !ctx->d_I_T || !ctx->d_sizes || !ctx->d_tt_general ||
+        !ctx->d_err ||
         !ctx->d_tickets || !ctx->d_ids || !ctx->d_order_all || !ctx->d_order_ids || !ctx->d_order_part ||
         !ctx->d_items || !ctx->d_arrays_base || !ctx->d_totals || !ctx->d_bsum ||
         (NP > 0 && (!ctx->d_parts || !ctx->d_tt_pos || !ctx->d_all_items))) {

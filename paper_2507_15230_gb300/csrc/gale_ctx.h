@@ -29,6 +29,8 @@ struct Bin {
                                     // (items K..K+NP-1, in other bins) instead; the other forms use this bin
     int teams = 0;                  // > 0: batched builds run `teams` clusters per CTA at once, one team of
                                     // plan.threads threads each (the other forms run one per CTA)
+    bool tt_general = false;        // members are non-manifold clusters: their TT rows take the general
+                                    // pass, which the per-item and global-scratch kernels carry
 };
 
 struct DevAlloc {
@@ -58,6 +60,7 @@ struct gale_ctx {
     int64_t *d_sizes = nullptr;  // [(K+NP)*5] clusters, then parts
     gale::PartInfo *d_parts = nullptr;  // [NP]
     int32_t *d_tt_pos = nullptr;        // [nt] TT row offsets of the cut clusters' internal tets
+    int32_t *d_tt_general = nullptr;    // [K] counting pass: 1 where a cluster's TT takes the general pass
     int32_t *d_all_items = nullptr;     // [n_all] the full build's item list (cut clusters replaced by their parts)
     std::vector<int32_t> all_items;     // host copy
     std::vector<int32_t> pos_all;       // [K+NP] position of each item in all_items (-1: a cut cluster)
@@ -76,6 +79,7 @@ struct gale_ctx {
     std::vector<gale::SmemPlan> h_plans;    // host copy
     int64_t spill_bytes = 0;
     std::vector<int64_t> sizes;             // host [(K+NP)*5]
+    std::vector<int32_t> tt_general;        // host [K]: 1 where the cluster is non-manifold (TT general pass)
     int64_t totals[5] = {0, 0, 0, 0, 0};
     double device_seconds = 0;
 

@@ -83,6 +83,9 @@ constexpr int32_t kMaxLocal = 65535;
 
 // Per-cluster sizes (entries) found by the counting pass.
 enum { SZ_VT = 0, SZ_VV = 1, SZ_E = 2, SZ_ET = 3, SZ_TT = 4, SZ_N = 5 };
+// counting pass only, one past the sizes: 1 when the cluster's TT rows take
+// the general pass (a triangle of the cluster lies in three or more tets)
+constexpr int SZ_GENERAL = SZ_N;
 
 // Relation mask bits (same values as the public GALE_* bits).
 enum : uint32_t { R_VT = 1u, R_VV = 2u, R_ET = 4u, R_TT = 8u };
@@ -227,6 +230,8 @@ struct DevMesh {
     int32_t *tt_pos;            // [nt] per internal tet of a cut cluster: its TT row's
                                 // offset in the cluster (the counting pass writes
                                 // the row lengths here first)
+    int32_t *tt_general;        // [K] the counting pass writes 1 where the cluster's TT
+                                // rows take the general pass (non-manifold), else 0
 };
 
 // Persistent launch over n clusters: ids[i] (count pass) or items[order[i]]

@@ -294,6 +294,18 @@ __device__ __forceinline__ uint32_t face_hash(uint64_t key, uint32_t mask) {
 }
 
 // compare-exchange of keys a, b carrying payloads pa, pb
+// number of local vertex ids two packed rows have in common
+__device__ __forceinline__ int shared_vertices(uint2 a, uint2 b) {
+    const uint32_t b0 = b.x & 0xffffu, b1 = b.x >> 16, b2 = b.y & 0xffffu, b3 = b.y >> 16;
+    int c = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const uint32_t v = vtx(a, s);
+        c += (v == b0) + (v == b1) + (v == b2) + (v == b3);
+    }
+    return c;
+}
+
 __device__ __forceinline__ void cswap2(int32_t &a, int32_t &b, uint32_t &pa, uint32_t &pb) {
     const bool sw = b < a;
     const int32_t ka = sw ? b : a, kb = sw ? a : b;
@@ -309,6 +321,71 @@ __device__ __forceinline__ void cswap2(int32_t &a, int32_t &b, uint32_t &pa, uin
 constexpr uint32_t kRefMask = (1u << 20) - 1u;
 constexpr uint32_t kMatch = 1u << 20;
 
+// ---------------- E'. TT of a non-manifold cluster ----------------
+// A triangle of the block lies in three or more tets, so a face may have
+// more than one partner.  Every tet of the block holding a face of an
+// internal tet is in its TT row, and the block holds them all: such a tet
+// holds an own vertex of the face (working set) or lies across a face
+// without one (face halo).  Each row is found by comparing vertex triples
+// with every tet of the block and sorted by canonical id.  Runs only for
+// the clusters the face links mark.  Ends synced.
+template <bool COUNT, class Team>
+__device__ __forceinline__ void tt_general(const Team &tm, const Smem &S, const uint2 *rows, const int32_t *tmap,
+                                        int32_t t_base, int n_ext, int n_own, int n_all, int32_t max_tt,
+                                        const WorkItem *it, int64_t *sizes_out, int32_t *err) {
+    const int NT = tm.nt(), tid = tm.tid();
+    const int n_vtets = n_ext + n_own;
+    auto gtet = [&](int loc) -> int32_t {
+        if (loc < n_ext) return tmap[loc];
+        if (loc < n_vtets) return t_base + (loc - n_ext);
+        return tmap[loc - n_own];
+    };
+    int32_t *tcnt = S.tcnt;
+    for (int i = tid; i < n_own; i += NT) {
+        const int li = n_ext + i;
+        const uint2 r = rows[li];
+        int c = 0;
+        for (int u = 0; u < n_all; ++u) c += (u != li && shared_vertices(rows[u], r) == 3);
+        tcnt[i] = c;
+    }
+    tm.sync();
+    const int tot_tt = block_scan_array(tm, tcnt, n_own, S.scan);
+    if (COUNT) {
+        if (tid == 0) {
+            sizes_out[SZ_TT] = tot_tt;
+            sizes_out[SZ_GENERAL] = 1;
+        }
+    } else {
+        if (tot_tt > max_tt) {
+            if (tid == 0) atomicOr(err, ERR_CAPACITY);
+            tm.sync();
+            return;
+        }
+        for (int i = tid; i < n_own; i += NT) {
+            const int li = n_ext + i;
+            const uint2 r = rows[li];
+            const int p = tcnt[i];
+            uint16_t *o = S.st_tt + p;
+            int c = 0;
+            for (int u = 0; u < n_all; ++u) {
+                if (u == li || shared_vertices(rows[u], r) != 3) continue;
+                const int32_t gu = gtet(u);
+                int q = c++;
+                while (q > 0 && gtet(o[q - 1]) > gu) {
+                    o[q] = o[q - 1];
+                    --q;
+                }
+                o[q] = uint16_t(u);
+            }
+            it->tt_off[i] = p;
+        }
+        if (tid == 0) it->tt_off[n_own] = tot_tt;
+        tm.sync();
+        copy_out(tm, it->tt_val, tot_tt, [&](int j) { return gtet(S.st_tt[j]); });
+    }
+    tm.sync();
+}
+
 // ---------------------------------------------------------------------------
 // One cluster.  COUNT: no output writes; sizes -> sizes_out[5].  SPILL: the
 // regions are global scratch and the rows arrive by vector loads instead of
@@ -318,7 +395,7 @@ constexpr uint32_t kMatch = 1u << 20;
 // ---------------------------------------------------------------------------
 // PART: the item is a part of a cut cluster (block header part != 0); the
 // whole-cluster instances carry none of the part logic.
-template <bool COUNT, bool SPILL, bool PART, class Team>
+template <bool COUNT, bool SPILL, bool PART, bool GEN, class Team>
 __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &plan, const Smem &S, int64_t blk_word, int64_t words,
                             uint32_t mask, const WorkItem *it, int64_t *sizes_out, int32_t *err, uint64_t *bar,
                             uint32_t &phase) {
@@ -327,7 +404,7 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
     const uint32_t lt = (1u << lane) - 1u;
     const Caps &caps = plan.caps;
     const int32_t *__restrict__ g = m.blocks + blk_word;
-    int32_t *flag = S.scan + 120;  // [0] block fits, [1] bulk copy issued
+    int32_t *flag = S.scan + 120;  // [0] block fits, [1] bulk copy issued, [2] non-manifold
     const bool jp16 = plan.jpos16 != 0;
 
     // ---------------- A. the block, by one bulk copy ----------------
@@ -340,6 +417,7 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
         }
         flag[0] = fits;
         flag[1] = issued;
+        flag[2] = 0;
     }
     tm.sync();
     const bool fits = flag[0] != 0, issued = flag[1] != 0;
@@ -764,6 +842,10 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
             const uint32_t b = v1 - uint32_t(lo);
             if (b < nvo_u) link(rank(b, v2), rank(b, v3), S.vt_off[b], jb, 0);
         }
+        if (GEN && !PART && (flags & ERR_NONMANIFOLD)) {  // TT of this cluster takes the general pass (E')
+            flag[2] = 1;
+            flags &= ~ERR_NONMANIFOLD;
+        }
         if (flags) atomicOr(err, flags);
     }
     tm.sync();  // bitmaps and rank prefixes are dead: r1 takes the ET staging
@@ -861,8 +943,17 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
                 hp = (hp + 1u) & hmask;
             }
         }
+        if (GEN && !PART && (flags & ERR_NONMANIFOLD)) {
+            flag[2] = 1;
+            flags &= ~ERR_NONMANIFOLD;
+        }
         if (flags) atomicOr(err, flags);
         tm.sync();
+        if (GEN && !PART && flag[2] != 0) {
+            tt_general<COUNT>(tm, S, rows, tmap, t_base, n_ext, n_own, n_vtets + h.n_halo, caps.max_tt, it,
+                              sizes_out, err);
+            return true;
+        }
         // ---------------- E. TT rows ----------------
         int32_t *tcnt = S.tcnt;
         for (int i = tid; i < n_own; i += NT) {
@@ -943,14 +1034,19 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
     return true;
 }
 
-// A work item: a whole cluster, or (id >= K) a part of a cut cluster.
-template <bool COUNT, bool SPILL>
+// A work item: a whole cluster, or (id >= K) a part of a cut cluster.  GEN:
+// the whole-cluster instance carries the general TT pass (E'); the hot
+// shared-memory kernel leaves it out, and the clusters that need it (the
+// counting pass marks them) run from per-item bins.
+template <bool COUNT, bool SPILL, bool GEN>
 __device__ __forceinline__ bool run_item(bool part, const DevMesh &m, const SmemPlan &plan, const Smem &S,
                                          int64_t blk_word, int64_t words, uint32_t mask, const WorkItem *it,
                                          int64_t *sizes_out, int32_t *err, uint64_t *bar, uint32_t &phase) {
     const BlockTeam tm;
-    if (part) return run_cluster<COUNT, SPILL, true>(tm, m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
-    return run_cluster<COUNT, SPILL, false>(tm, m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
+    if (part)
+        return run_cluster<COUNT, SPILL, true, false>(tm, m, plan, S, blk_word, words, mask, it, sizes_out, err, bar,
+                                                      phase);
+    return run_cluster<COUNT, SPILL, false, GEN>(tm, m, plan, S, blk_word, words, mask, it, sizes_out, err, bar, phase);
 }
 
 // SPILL: the cluster's regions live in a per-CTA slice of global scratch
@@ -977,7 +1073,7 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan 
     extern __shared__ __align__(16) char smem[];
     const Smem S = carve(region_base<SPILL>(smem, gscratch, plan), plan);
     __shared__ int32_t s_idx;
-    __shared__ int64_t s_sizes[SZ_N];
+    __shared__ int64_t s_sizes[SZ_N + 1];
     __shared__ __align__(8) uint64_t s_bar;
     init_barrier<SPILL>(&s_bar);
     uint32_t phase = 0;
@@ -992,13 +1088,14 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel(DevMesh m, SmemPlan 
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
-        if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
+        if (threadIdx.x <= SZ_N) s_sizes[threadIdx.x] = 0;
         __syncthreads();
-        if (!run_item<true, SPILL>(k >= m.K, m, plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr, s_sizes,
+        if (!run_item<true, SPILL, true>(k >= m.K, m, plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr, s_sizes,
                                       err, &s_bar, phase))
             return;
         __syncthreads();
         if (threadIdx.x < SZ_N) sizes[int64_t(k) * SZ_N + threadIdx.x] = s_sizes[threadIdx.x];
+        if (threadIdx.x == 0 && k < m.K && m.tt_general) m.tt_general[k] = int32_t(s_sizes[SZ_GENERAL]);
     }
 }
 
@@ -1036,7 +1133,7 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel(DevMesh m, SmemPlan 
             if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
             continue;
         }
-        if (!run_item<false, SPILL>(k >= m.K, m, plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
+        if (!run_item<false, SPILL, SPILL>(k >= m.K, m, plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
                                        nullptr, err, &s_bar, phase))
             return;
     }
@@ -1057,7 +1154,7 @@ __global__ void __launch_bounds__(kMaxThreads) build_one_kernel(DevMesh m, SmemP
         if (threadIdx.x == 0) atomicOr(err, ERR_BAD_ITEM);
         return;
     }
-    run_cluster<false, SPILL, false>(BlockTeam{}, m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k], s_item.mask,
+    run_cluster<false, SPILL, false, true>(BlockTeam{}, m, plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k], s_item.mask,
                               &s_item, nullptr, err, &s_bar, phase);
 }
 
@@ -1099,7 +1196,7 @@ __global__ void __launch_bounds__(kMaxTeamBlock) build_kernel_team(DevMesh m, Sm
             tm.sync();
             continue;
         }
-        if (!run_cluster<false, false, false>(tm, m, plan, S, s_item[g].blk, m.blk_off[k + 1] - m.blk_off[k],
+        if (!run_cluster<false, false, false, false>(tm, m, plan, S, s_item[g].blk, m.blk_off[k + 1] - m.blk_off[k],
                                               s_item[g].mask, &s_item[g], nullptr, err, &s_bar[g], phase))
             return;
         tm.sync();  // the next claim rewrites this team's item
@@ -1125,7 +1222,7 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel_pi(DevMesh m, const 
                                                               uint32_t mask) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int32_t s_idx;
-    __shared__ int64_t s_sizes[SZ_N];
+    __shared__ int64_t s_sizes[SZ_N + 1];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(16) SmemPlan s_plan;
     init_barrier<false>(&s_bar);
@@ -1142,14 +1239,15 @@ __global__ void __launch_bounds__(kMaxThreads) count_kernel_pi(DevMesh m, const 
             continue;
         }
         load_plan(s_plan, plans + k);
-        if (threadIdx.x < SZ_N) s_sizes[threadIdx.x] = 0;
+        if (threadIdx.x <= SZ_N) s_sizes[threadIdx.x] = 0;
         __syncthreads();
         const Smem S = carve(smem, s_plan);
-        if (!run_item<true, false>(k >= m.K, m, s_plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr,
+        if (!run_item<true, false, true>(k >= m.K, m, s_plan, S, m.blk_off[k], m.blk_off[k + 1] - m.blk_off[k], mask, nullptr,
                                       s_sizes, err, &s_bar, phase))
             return;
         __syncthreads();
         if (threadIdx.x < SZ_N) sizes[int64_t(k) * SZ_N + threadIdx.x] = s_sizes[threadIdx.x];
+        if (threadIdx.x == 0 && k < m.K && m.tt_general) m.tt_general[k] = int32_t(s_sizes[SZ_GENERAL]);
     }
 }
 
@@ -1189,7 +1287,7 @@ __global__ void __launch_bounds__(kMaxThreads) build_kernel_pi(DevMesh m, const 
         load_plan(s_plan, plans + k);
         __syncthreads();
         const Smem S = carve(smem, s_plan);
-        if (!run_item<false, false>(k >= m.K, m, s_plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
+        if (!run_item<false, false, true>(k >= m.K, m, s_plan, S, s_item.blk, m.blk_off[k + 1] - m.blk_off[k], s_item.mask, &s_item,
                                        nullptr, err, &s_bar, phase))
             return;
     }
@@ -1271,7 +1369,7 @@ __global__ void __launch_bounds__(1024) serve_kernel(DevMesh m, const SmemPlan *
             load_plan(s_plan, plans + s_item.k);  // the cluster's own plan
             __syncthreads();
             const Smem S = carve(smem, s_plan);
-            go_on = run_cluster<false, false, false>(BlockTeam{}, m, s_plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
+            go_on = run_cluster<false, false, false, true>(BlockTeam{}, m, s_plan, S, s_item.blk, m.blk_off[s_item.k + 1] - m.blk_off[s_item.k],
                                               s_item.mask, &s_item, nullptr, err, &s_bar, phase);
         } else if (threadIdx.x == 0) {
             atomicOr(err, ERR_BAD_ITEM);

@@ -271,23 +271,3 @@ def test_spill_bins_every_mask(mask):
                 ctx.build(None, mask, mode)
                 ctx.synchronize()
                 assert_bulk_equal(ctx.export(mask), want)
-
-
-def test_non_manifold_input():
-    """Three tets on one triangle: TT needs a manifold mesh, so loading with
-    TT in the precondition mask fails with EDEVICE; without it, VT, VV and ET
-    equal the oracle's."""
-    xyz = np.random.default_rng(0).random((6, 3)).astype(np.float32)
-    tv = np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]], np.int32)
-    seg = np.array([0, 0, 1, 1, 0, 1], np.int32)
-    m = gen.Mesh(xyz, tv, seg, 2)
-    canon, rel = oracle.build_all(m.nv, m.tv, m.seg, 2)
-    with pytest.raises(gale.GaleError) as ei:
-        gale.Context.load(m, device=0)
-    assert gale.STATUS[ei.value.status] == "EDEVICE" and "manifold" in str(ei.value)
-    pre = gale.VT | gale.VV | gale.ET
-    with gale.Context.load(m, device=0, precondition_mask=pre) as ctx:
-        for mode in (gale.MODE_BATCHED, gale.MODE_PER_CLUSTER):
-            ctx.build(None, pre, mode)
-            ctx.synchronize()
-            assert_bulk_equal(ctx.export(pre), expected_bulk(rel, canon, range(2), pre))
