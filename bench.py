@@ -684,7 +684,10 @@ def config3_leg(args, gale, gen):
     peak, _ = load_peaks()
     return {"workload": f"delaunay 2M points (70% 8 Gaussians, 30% uniform): {mesh.nv} vertices, {mesh.nt} tets, "
                         f"{mesh.nclusters} kd leaves of {int(leaf.min())}..{int(leaf.max())} vertices",
-            "generation_s": gen_s, "ms_per_step": ms, "tets_per_s": mesh.nt / (ms / 1e3),
+            "generation_s": gen_s,
+            "load_seconds": {"host": info.load_host_seconds, "device": info.load_device_seconds,
+                             "parts": int(info.nparts)},
+            "ms_per_step": ms, "tets_per_s": mesh.nt / (ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / (ms / 1e3) / 1e9 / peak, "algorithmic_bytes_per_launch": alg},
             "per_cluster_launch": {"ms": pms, "tets_per_s": mesh.nt / (pms / 1e3), "launches": int(mesh.nclusters)},

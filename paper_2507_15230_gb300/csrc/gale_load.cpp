@@ -60,6 +60,57 @@ void counting_sort(int64_t n, int32_t nkeys, int nthreads, Key key, int32_t *out
 
 }  // namespace
 
+// The distinct values of a stream of non-negative ids, in first-seen order,
+// each with its dense index (its position in that order): an open-addressing
+// table that grows at half load, reused across calls, so a cluster costs
+// O(entries) instead of a sort of all of them.
+struct DistinctIds {
+    std::vector<int32_t> tab, at, vals;
+    uint32_t mask = 0;
+    void reset(size_t expect) {
+        size_t cap = 64;
+        while (cap < 2 * expect) cap <<= 1;
+        if (tab.size() != cap) {
+            tab.resize(cap);
+            at.resize(cap);
+        }
+        std::fill(tab.begin(), tab.end(), -1);
+        mask = uint32_t(cap - 1);
+        vals.clear();
+    }
+    void add(int32_t v) {
+        uint32_t h = slot(v);
+        if (tab[h] == v) return;
+        tab[h] = v;
+        at[h] = int32_t(vals.size());
+        vals.push_back(v);
+        if (2 * vals.size() > tab.size()) grow();
+    }
+    // dense index of v, -1 when absent
+    int32_t index(int32_t v) const {
+        const uint32_t h = slot(v);
+        return tab[h] == v ? at[h] : -1;
+    }
+
+  private:
+    // v's slot, or the empty slot where it would go
+    uint32_t slot(int32_t v) const {
+        uint32_t h = (uint32_t(v) * 2654435761u) & mask;
+        while (tab[h] != v && tab[h] >= 0) h = (h + 1) & mask;
+        return h;
+    }
+    void grow() {
+        tab.assign(2 * tab.size(), -1);
+        at.resize(tab.size());
+        mask = uint32_t(tab.size() - 1);
+        for (size_t i = 0; i < vals.size(); ++i) {
+            const uint32_t h = slot(vals[i]);
+            tab[h] = vals[i];
+            at[h] = int32_t(i);
+        }
+    }
+};
+
 int host_threads(int requested) {
     if (requested > 0) return requested;
     unsigned h = std::thread::hardware_concurrency();
@@ -201,12 +252,27 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
     hm.halo_off.assign(size_t(K) + 1, 0);
     hm.halo.clear();
     const bool want_tt = (d.precondition_mask & 8u) != 0;
-    // vertex stars over canonical tets (ascending), kept for the parts' halos
-    std::vector<int32_t> order;
-    std::vector<int64_t> vs_off;  // star of c: order[vs_off[c] .. vs_off[c+1]) / 4
+    // vertex stars (the tets of each vertex, in no particular order: both
+    // users sort what they collect), kept for the parts' halos.  Counted and
+    // filled with atomic cursors: a stable counting sort over nv keys would
+    // need per-thread histograms of nv entries.
+    std::vector<int32_t> order;   // star of c: order[vs_off[c] .. vs_off[c+1]), tet ids
+    std::vector<int64_t> vs_off;
     if (want_tt && nt > 0) {
         order.resize(size_t(4) * nt);
-        counting_sort(4 * nt, int32_t(nv), P, [&](int64_t i) { return rows[i]; }, order.data(), vs_off);
+        vs_off.assign(size_t(nv) + 1, 0);
+        parallel_for(4 * nt, P, [&](int64_t b, int64_t e, int) {
+            for (int64_t i = b; i < e; ++i) __atomic_fetch_add(&vs_off[size_t(rows[i]) + 1], int64_t(1), __ATOMIC_RELAXED);
+        });
+        for (int64_t v = 0; v < nv; ++v) vs_off[v + 1] += vs_off[v];
+        {
+            std::vector<int64_t> cur(vs_off.begin(), vs_off.end() - 1);
+            parallel_for(4 * nt, P, [&](int64_t b, int64_t e, int) {
+                for (int64_t i = b; i < e; ++i)
+                    order[size_t(__atomic_fetch_add(&cur[size_t(rows[i])], int64_t(1), __ATOMIC_RELAXED))] =
+                        int32_t(i >> 2);
+            });
+        }
         std::vector<std::vector<int32_t>> halo_k(K);
         parallel_dynamic(K, P, 16, [&](int64_t k, int) {
             std::vector<int32_t> &hk = halo_k[k];
@@ -215,16 +281,18 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
                 if (cl[r[1]] == int32_t(k)) continue;  // face bcd has a vertex in k
                 const int32_t b = r[1], c = r[2], dd = r[3];
                 for (int64_t q = vs_off[b]; q < vs_off[b + 1]; ++q) {
-                    const int32_t u = order[q] >> 2;
+                    const int32_t u = order[q];
                     if (u == t) continue;
                     const int32_t *ru = rows + 4 * int64_t(u);
-                    bool hc = false, hd = false, ink = false;
+                    bool hc = false, hd = false;
                     for (int j = 0; j < 4; ++j) {
                         hc |= ru[j] == c;
                         hd |= ru[j] == dd;
-                        ink |= cl[ru[j]] == int32_t(k);
                     }
-                    if (hc && hd && !ink) hk.push_back(u);
+                    if (!hc || !hd) continue;
+                    bool ink = false;
+                    for (int j = 0; j < 4; ++j) ink |= cl[ru[j]] == int32_t(k);
+                    if (!ink) hk.push_back(u);
                 }
             }
             std::sort(hk.begin(), hk.end());
@@ -267,24 +335,22 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         const int32_t v0 = w.v0, v1 = w.v1;
         // neighbour universe: vertices of [external | internal] tets plus the
         // own interval, ascending; then halo-only vertices, ascending
+        thread_local DistinctIds seen;
         std::vector<int32_t> nb, ho;
-        auto add_row = [&](std::vector<int32_t> &dst, int32_t t) {
+        seen.reset(size_t(v1 - v0) * 2 + 64);
+        auto add_row = [&](int32_t t) {
             const int32_t *r = rows + 4 * int64_t(t);
             for (int j = 0; j < 4; ++j)
-                if (r[j] < v0 || r[j] >= v1) dst.push_back(r[j]);
+                if (r[j] < v0 || r[j] >= v1) seen.add(r[j]);
         };
-        for (int64_t i = 0; i < w.n_ext; ++i) add_row(nb, w.ext[i]);
-        for (int64_t i = 0; i < w.n_int; ++i) add_row(nb, w.itet(i));
+        for (int64_t i = 0; i < w.n_ext; ++i) add_row(w.ext[i]);
+        for (int64_t i = 0; i < w.n_int; ++i) add_row(w.itet(i));
+        nb = seen.vals;
         std::sort(nb.begin(), nb.end());
-        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
-        for (int64_t i = 0; i < w.n_halo; ++i) add_row(ho, w.halo[i]);
+        const size_t n_nb = seen.vals.size();
+        for (int64_t i = 0; i < w.n_halo; ++i) add_row(w.halo[i]);
+        ho.assign(seen.vals.begin() + int64_t(n_nb), seen.vals.end());  // halo-only: not seen before
         std::sort(ho.begin(), ho.end());
-        ho.erase(std::unique(ho.begin(), ho.end()), ho.end());
-        {
-            std::vector<int32_t> only;
-            std::set_difference(ho.begin(), ho.end(), nb.begin(), nb.end(), std::back_inserter(only));
-            ho.swap(only);
-        }
         const int64_t below = std::lower_bound(nb.begin(), nb.end(), v0) - nb.begin();
         vm.clear();
         vm.reserve(nb.size() + (v1 - v0) + ho.size());
@@ -307,9 +373,10 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         // [external | internal]
         const int32_t nvo = v1 - v0;
         std::vector<int32_t> vm_up, ufill(static_cast<size_t>(v1 - v0) + 1, 0);
-        // per own vertex: its incidences, and its upper neighbours (canonical
-        // ids; only their number of distinct values matters) bucketed in one
-        // array by a counting pass and a fill pass
+        // per own vertex: its incidences, and its upper neighbours bucketed
+        // in one array by a counting pass and a fill pass, as dense ids
+        // (own vertex v0 + i -> n_nb + i, any other -> its index among the
+        // neighbour universe; only their number of distinct values matters)
         std::vector<int32_t> deg(static_cast<size_t>(nvo), 0), uoff(static_cast<size_t>(nvo) + 1, 0);
         for (int pass = 0; pass < 2; ++pass) {
             auto row = [&](int32_t t) {
@@ -321,7 +388,8 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
                             deg[x]++;
                             uoff[x + 1] += 3 - j;
                         } else {
-                            for (int q = j + 1; q < 4; ++q) vm_up[uoff[x]++] = r[q];
+                            for (int q = j + 1; q < 4; ++q)
+                                vm_up[uoff[x]++] = r[q] < v1 ? int32_t(n_nb) + (r[q] - v0) : seen.index(r[q]);
                         }
                     }
             };
@@ -335,12 +403,17 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
             for (int64_t i = 0; i < w.n_int; ++i) row(w.itet(i));
         }
         int32_t nvt = 0, mx = 0, mu = 0, ne = 0;
+        thread_local std::vector<int32_t> stamp;
+        stamp.assign(n_nb + size_t(nvo), -1);
         for (int32_t x = 0; x < nvo; ++x) {
             nvt += deg[x];
             mx = std::max(mx, deg[x]);
-            int32_t *b = vm_up.data() + ufill[x], *e = vm_up.data() + uoff[x];
-            std::sort(b, e);
-            const int32_t nu = int32_t(std::unique(b, e) - b);
+            int32_t nu = 0;
+            for (int32_t i = ufill[x]; i < uoff[x]; ++i) {
+                int32_t &st = stamp[size_t(vm_up[i])];
+                nu += st != x;
+                st = x;
+            }
             mu = std::max(mu, nu);
             ne += nu;
         }
@@ -356,13 +429,19 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
             nbnd += (r[0] >= v0 && r[0] < v1 && r[1] >= v1);
         }
         s.n_bnd = nbnd;
-        // two tets with the same vertex set have the same owner
+        // two tets with the same vertex set have the same owner and the same
+        // lowest vertex: compare the rows of each own vertex's internal tets
         if (!w.part && w.n_int > 1) {
-            std::vector<std::array<int32_t, 4>> own(size_t(w.n_int));
-            for (int64_t i = 0; i < w.n_int; ++i) memcpy(own[i].data(), rows + 4 * int64_t(w.itet(i)), 16);
-            std::sort(own.begin(), own.end());
-            for (size_t i = 1; i < own.size(); ++i)
-                if (own[i] == own[i - 1]) return 2;
+            std::vector<int32_t> first(size_t(nvo), -1), next(size_t(w.n_int), -1);
+            for (int64_t i = 0; i < w.n_int; ++i) {
+                const int32_t *r = rows + 4 * int64_t(w.itet(i));
+                const int32_t x = r[0] - v0;
+                if (x < 0 || x >= nvo) continue;
+                for (int32_t q = first[x]; q >= 0; q = next[q])
+                    if (memcmp(r, rows + 4 * int64_t(w.itet(q)), 16) == 0) return 2;
+                next[i] = first[x];
+                first[x] = int32_t(i);
+            }
         }
         return 0;
     };
@@ -381,11 +460,13 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         if (w.part)
             for (int64_t i = 0; i < w.n_int; ++i) tmap[w.n_ext + w.n_halo + i] = w.itet(i);
         uint16_t *lrows = reinterpret_cast<uint16_t *>(blk + blk_rows_off(s.nv_loc, s.n_ext, s.n_halo, s.xmap));
+        // local id = position in vm: a table of vm's values in order
+        thread_local DistinctIds pos;
+        pos.reset(vm.size());
+        for (int32_t v : vm) pos.add(v);
         auto local = [&](int32_t v) -> uint16_t {
             if (v >= v0 && v < v0 + s.nv_own) return uint16_t(own_lo + (v - v0));
-            auto it = std::lower_bound(vm.begin(), vm.begin() + s.nv_nb, v);
-            if (it != vm.begin() + s.nv_nb && *it == v) return uint16_t(it - vm.begin());
-            return uint16_t(std::lower_bound(vm.begin() + s.nv_nb, vm.end(), v) - vm.begin());
+            return uint16_t(pos.index(v));
         };
         int64_t li = 0;
         auto put = [&](int32_t t) {
@@ -483,7 +564,7 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
                 if (r[0] < a0 || r[0] >= a1 || r[1] < a1) continue;
                 const int32_t b = r[1], c = r[2], dd = r[3];
                 for (int64_t q = vs_off[b]; q < vs_off[b + 1]; ++q) {
-                    const int32_t u = order[q] >> 2;
+                    const int32_t u = order[q];
                     if (u == t) continue;
                     const int32_t *ru = rows + 4 * int64_t(u);
                     bool hc = false, hd = false, inp = false;
