@@ -1017,17 +1017,17 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
                 uint32_t l0 = n0, l1 = n1, l2 = n2, l3 = n3;
                 cswap2(w0, w1, l0, l1); cswap2(w2, w3, l2, l3); cswap2(w0, w2, l0, l2); cswap2(w1, w3, l1, l3);
                 cswap2(w1, w2, l1, l2);
+                // canonical ids straight out: a warp's rows are adjacent, so
+                // its four stores cover one contiguous span
                 const int p = tcnt[i];
                 it->tt_off[i] = p;
-                uint16_t *o = S.st_tt + p;
-                if (w0 != INT32_MAX) o[0] = uint16_t(l0);
-                if (w1 != INT32_MAX) o[1] = uint16_t(l1);
-                if (w2 != INT32_MAX) o[2] = uint16_t(l2);
-                if (w3 != INT32_MAX) o[3] = uint16_t(l3);
+                int32_t *o = it->tt_val + p;
+                if (w0 != INT32_MAX) o[0] = w0;
+                if (w1 != INT32_MAX) o[1] = w1;
+                if (w2 != INT32_MAX) o[2] = w2;
+                if (w3 != INT32_MAX) o[3] = w3;
             }
             if (tid == 0) it->tt_off[n_own] = tot_tt;
-            tm.sync();
-            copy_out(tm, it->tt_val, tot_tt, [&](int j) { return gtet(S.st_tt[j]); });
         }
     }
     tm.sync();
