@@ -293,7 +293,6 @@ __device__ __forceinline__ uint32_t face_hash(uint64_t key, uint32_t mask) {
     return uint32_t((key * 0x9E3779B97F4A7C15ull) >> 40) & mask;
 }
 
-// compare-exchange of keys a, b carrying payloads pa, pb
 // number of local vertex ids two packed rows have in common
 __device__ __forceinline__ int shared_vertices(uint2 a, uint2 b) {
     const uint32_t b0 = b.x & 0xffffu, b1 = b.x >> 16, b2 = b.y & 0xffffu, b3 = b.y >> 16;
@@ -306,6 +305,7 @@ __device__ __forceinline__ int shared_vertices(uint2 a, uint2 b) {
     return c;
 }
 
+// compare-exchange of keys a, b carrying payloads pa, pb
 __device__ __forceinline__ void cswap2(int32_t &a, int32_t &b, uint32_t &pa, uint32_t &pb) {
     const bool sw = b < a;
     const int32_t ka = sw ? b : a, kb = sw ? a : b;
