@@ -236,6 +236,17 @@ __device__ __forceinline__ void block_scan3(const Team &tm, int &a, int &b, int 
     tm.sync();
 }
 
+// p[0 .. n) = v over the team, 16 bytes a store (p is 16-byte aligned: every
+// region of the plan is).
+template <class Team>
+__device__ __forceinline__ void fill_words(const Team &tm, uint32_t *p, int n, uint32_t v) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    const int n4 = n >> 2;
+    const uint4 v4 = make_uint4(v, v, v, v);
+    for (int i = tm.tid(); i < n4; i += tm.nt()) q[i] = v4;
+    for (int i = 4 * n4 + tm.tid(); i < n; i += tm.nt()) p[i] = v;
+}
+
 // Length of each thread's contiguous range when n items are split over the
 // team: odd, so that neighbouring threads start in different banks.
 template <class Team>
@@ -504,10 +515,8 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
         uint32_t *mk = S.mk;  // [warp][v]: lanes holding v
         const int chunk = ((n_vtets + NWARP - 1) / NWARP + 31) & ~31;
         const int c0 = min(n_vtets, warp * chunk), c1 = min(n_vtets, c0 + chunk);
-        for (int i = tid; i < NWARP * pad; i += NT) {
-            if (!(i & 1)) cw32[i >> 1] = 0u;
-            mk[i] = 0u;
-        }
+        fill_words(tm, cw32, (NWARP * pad) >> 1, 0u);  // pad is even
+        fill_words(tm, mk, NWARP * pad, 0u);
         tm.sync();
         for (int i = c0 + lane; i < c1; i += 32) {
             const uint2 r = rows[i];
@@ -590,10 +599,10 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
     const int WP = W | 1;                // row stride (odd: rows start in different banks)
     uint32_t *bm = S.bm;
     uint8_t *pre = S.pre;
-    for (int i = tid; i < nvo * WP; i += NT) bm[i] = 0u;
+    fill_words(tm, bm, nvo * WP, 0u);
     if (want_tt) {
         uint32_t *nb32 = reinterpret_cast<uint32_t *>(S.nbr);
-        for (int i = tid; i < 2 * n_own; i += NT) nb32[i] = FULL;
+        fill_words(tm, nb32, 2 * n_own, FULL);
     }
     tm.sync();
     int etv = 0;  // ET entries: each own vertex of a tet, once per vertex above it
@@ -759,7 +768,7 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
     const int nch = plan.nch;
     uint32_t *em = S.emask;
     tm.sync();  // VV and endpoint staging are dead: r2 takes the edge masks
-    for (int i = tid; i < tot_e * nch; i += NT) em[i] = 0u;
+    fill_words(tm, em, tot_e * nch, 0u);
     tm.sync();
 
     // ---------------- C3. edge tet masks, per tet ----------------
@@ -899,7 +908,7 @@ __device__ bool run_cluster(const Team &tm, const DevMesh &m, const SmemPlan &pl
         // ---------------- D. faces with no own vertex, against the halo ----
         const uint32_t hmask = uint32_t(caps.hcap - 1);
         uint32_t *hash = S.hash;
-        for (int i = tid; i < caps.hcap; i += NT) hash[i] = 0u;
+        fill_words(tm, hash, caps.hcap, 0u);
         tm.sync();
         int32_t flags = 0;
         // the internal tets whose face (b, c, d) has no own vertex
