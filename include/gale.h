@@ -456,7 +456,9 @@ gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, i
  * pointers to int32 offsets[rows+1] and values, library-owned and valid
  * until the next call or gale_destroy.  EINVAL if the enumeration has 2^31
  * or more edges or triangles (or a relation 2^31 or more entries), ENOTFOUND
- * before gale_enumerate, EDEVICE if a lookup failed. */
+ * before gale_enumerate, EDEVICE if a lookup failed or, with GALE_CB_FT, if
+ * a triangle lies in three or more tets (FT keeps two slots per triangle;
+ * VE, VF and EF have no such limit). */
 enum { GALE_CB_VE = 1, GALE_CB_VF = 2, GALE_CB_EF = 4, GALE_CB_FT = 8 };
 typedef struct {
     int64_t rows[4];
