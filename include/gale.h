@@ -456,9 +456,11 @@ gale_status gale_boundary(gale_ctx *ctx, int32_t relation, const int64_t *ids, i
  * pointers to int32 offsets[rows+1] and values, library-owned and valid
  * until the next call or gale_destroy.  EINVAL if the enumeration has 2^31
  * or more edges or triangles (or a relation 2^31 or more entries), ENOTFOUND
- * before gale_enumerate, EDEVICE if a lookup failed or, with GALE_CB_FT, if
- * a triangle lies in three or more tets (FT keeps two slots per triangle;
- * VE, VF and EF have no such limit). */
+ * before gale_enumerate, EDEVICE if a lookup failed.  FT takes two slots
+ * per triangle; on a non-manifold mesh (a triangle in three or more tets:
+ * known at load when GALE_TT is preconditioned, else found when the slots
+ * overflow, and the pass then runs again) it counts each triangle's tets,
+ * places them by cursors and sorts the rows. */
 enum { GALE_CB_VE = 1, GALE_CB_VF = 2, GALE_CB_EF = 4, GALE_CB_FT = 8 };
 typedef struct {
     int64_t rows[4];

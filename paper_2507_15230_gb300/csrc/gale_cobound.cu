@@ -65,6 +65,7 @@ struct Cobound {
     int64_t scratch_cap = 0;
     int64_t off_cap[4] = {}, val_cap[4] = {};
     int64_t rows_of[4] = {}, len[4] = {};
+    bool ft_general = false;       // FT by counts and cursors: some triangle lies in three or more tets
 };
 
 void cobound_destroy(gale_ctx *ctx) {
@@ -235,6 +236,12 @@ __device__ __forceinline__ void ft_claim(int2 *slot, int32_t q, int32_t t, int32
     if (atomicCAS(&slot[q].x, -1, t) == -1) return;
     if (atomicCAS(&slot[q].y, -1, t) != -1) atomicOr(err, ERR_NONMANIFOLD);
 }
+// MODE: FT_SLOTS claims the two slots; FT_COUNT counts each triangle's tets
+// (sc.cnt, by row); FT_FILL places them by cursors (sc.cnt zeroed) in rows
+// that a sort then orders - the form for a mesh with a triangle in three
+// or more tets.
+enum { FT_SLOTS = 0, FT_COUNT = 1, FT_FILL = 2 };
+template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_ft_tets(CbMesh m, Scatter sc, int64_t nT, int32_t *err) {
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nT; t += int64_t(gridDim.x) * blockDim.x) {
         const int4 r = m.rows[t];
@@ -245,10 +252,17 @@ __global__ void __launch_bounds__(kThreads) k_ft_tets(CbMesh m, Scatter sc, int6
             atomicOr(err, ERR_BAD_BLOCK);
             continue;
         }
-        ft_claim(sc.ft_slot, int32_t(f0), int32_t(t), err);
-        ft_claim(sc.ft_slot, int32_t(f1), int32_t(t), err);
-        ft_claim(sc.ft_slot, int32_t(f2), int32_t(t), err);
-        ft_claim(sc.ft_slot, int32_t(f3), int32_t(t), err);
+        const int64_t f[4] = {f0, f1, f2, f3};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (MODE == FT_SLOTS) {
+                ft_claim(sc.ft_slot, int32_t(f[q]), int32_t(t), err);
+            } else {
+                const int64_t row = frow(m, f[q]);
+                const int32_t c = atomicAdd(&sc.cnt[row], 1);
+                if (MODE == FT_FILL) sc.ft_val[sc.ft_off[row] + c] = int32_t(t);
+            }
+        }
     }
 }
 __global__ void __launch_bounds__(kThreads) k_len_ft(CbMesh m, Scatter sc, int32_t *err) {
@@ -875,21 +889,11 @@ gale_status enumerate_sorted_device(gale_ctx *ctx, uint64_t gen, std::vector<int
     return GALE_OK;
 }
 
-}  // namespace gale
-
-extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale_coboundary *out) {
-    using namespace gale;
-    if (!ctx || !out) return fail(GALE_EINVAL, "NULL argument");
-    if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
-    if (which == 0 || (which & ~uint32_t(GALE_CB_VE | GALE_CB_VF | GALE_CB_EF | GALE_CB_FT)))
-        return fail(GALE_EINVAL, "which must be a non-empty set of GALE_CB_* bits");
-    EnumView ev{};
-    if (!enumeration_view(ctx, &ev)) return fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
+// One coboundary pass over the current enumeration (the caller holds the
+// context's lock).  *err_word receives the device error word.
+gale_status run_pass(gale_ctx *ctx, uint32_t which, const EnumView &ev, int32_t *err_word) {
     const int64_t nE = ev.nE, nF = ev.nF;
     const uint64_t gen = ev.gen;
-    if (nE >= INT32_MAX || nF >= INT32_MAX) return fail(GALE_EINVAL, "more than 2^31 - 1 edges or triangles");
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(GALE_ECUDA, "cudaSetDevice");
     cudaStream_t s = ctx->stream;
     const HostMesh &hm = ctx->hm;
     const int32_t K = hm.K;
@@ -1038,9 +1042,10 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     if (wVE) k_sc_edges<false><<<grid_for(nE), kThreads, 0, s>>>(m, sc, ctx->d_err);
     if (wEF || wVF) k_sc_tris<false><<<grid_for(nF), kThreads, 0, s>>>(m, sc, wEF, wVF && !vf_gather, ctx->d_err);
     if (vf_gather) k_vf_count_sorted<<<grid_for(nE), kThreads, 0, s>>>(m, sc);
-    if (wFT) {
+    const bool ft_gen = wFT && cb.ft_general;
+    if (wFT && !ft_gen) {
         cudaMemsetAsync(sc.ft_slot, 0xff, sizeof(int2) * size_t(std::max<int64_t>(nF, 1)), s);
-        k_ft_tets<<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
+        k_ft_tets<FT_SLOTS><<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
     }
     // row offsets, one relation at a time through the shared count array
     for (int rel : {int(REL_VE), int(REL_VF), int(REL_EF), int(REL_FT)}) {
@@ -1055,7 +1060,14 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
             case REL_VE: k_len_ve<<<grid, kThreads, 0, s>>>(m, sc); break;
             case REL_VF: k_len_vf<<<grid, kThreads, 0, s>>>(m, sc, cb.fo); break;
             case REL_EF: k_len_ef<<<grid, kThreads, 0, s>>>(m, sc); break;
-            default: k_len_ft<<<grid, kThreads, 0, s>>>(m, sc, ctx->d_err); break;
+            default:
+                if (ft_gen) {
+                    cudaMemsetAsync(sc.cnt, 0, sizeof(int32_t) * size_t(std::max<int64_t>(nF, 1)), s);
+                    k_ft_tets<FT_COUNT><<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
+                } else {
+                    k_len_ft<<<grid, kThreads, 0, s>>>(m, sc, ctx->d_err);
+                }
+                break;
         }
         if (nb > 0) {
             scan_sums<<<int(nb), kThreads, 0, s>>>(cb.cnt, n, cb.bsum);
@@ -1081,8 +1093,14 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     if (wVE) k_sc_edges<true><<<grid_for(nE), kThreads, 0, s>>>(m, sc, ctx->d_err);
     if (wEF || wVF)
         k_sc_tris<true><<<grid_for(nF), kThreads, 0, s>>>(m, sc, wEF, wVF && !vf_gather, ctx->d_err);
-    if (wFT) k_ft_write<<<grid_for(nF), kThreads, 0, s>>>(m, sc);
     const int32_t *fo = cb.fo;
+    if (ft_gen) {
+        cudaMemsetAsync(sc.cnt, 0, sizeof(int32_t) * size_t(std::max<int64_t>(nF, 1)), s);
+        k_ft_tets<FT_FILL><<<grid_for(nT), kThreads, 0, s>>>(m, sc, nT, ctx->d_err);
+        k_sort_rows<PL_FULL, 4, FRONT_NONE, 0><<<grid_for(nF), kThreads, 0, s>>>(m, sc, nF, sc.ft_off, sc.ft_val, fo);
+    } else if (wFT) {
+        k_ft_write<<<grid_for(nF), kThreads, 0, s>>>(m, sc);
+    }
     if (wVE) k_sort_rows<PL_VE, 16, FRONT_NONE, 6144><<<grid_for(hm.nv), kThreads, 0, s>>>(m, sc, hm.nv, sc.ve_off, sc.ve_val, fo);
     if (wEF) k_sort_rows<PL_EF, 8, FRONT_EF, 0><<<grid_for(nE), kThreads, 0, s>>>(m, sc, nE, sc.ef_off, sc.ef_val, fo);
     if (vf_gather) k_vf_gather<<<grid_for(hm.nv), kThreads, 0, s>>>(m, sc, fo);
@@ -1092,10 +1110,40 @@ extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GALE_ECUDA, "cudaStreamSynchronize");
     int32_t e = 0;
     cudaMemcpy(&e, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    *err_word = e;
     if (e) {
         cudaMemset(ctx->d_err, 0, sizeof(int32_t));
         return fail(GALE_EDEVICE, "coboundary pass: error word " + std::to_string(e));
     }
+    return GALE_OK;
+}
+
+}  // namespace gale
+
+extern "C" gale_status gale_build_coboundary(gale_ctx *ctx, uint32_t which, gale_coboundary *out) {
+    using namespace gale;
+    if (!ctx || !out) return fail(GALE_EINVAL, "NULL argument");
+    if (ctx->device < 0) return fail(GALE_EINVAL, "host-only context");
+    if (which == 0 || (which & ~uint32_t(GALE_CB_VE | GALE_CB_VF | GALE_CB_EF | GALE_CB_FT)))
+        return fail(GALE_EINVAL, "which must be a non-empty set of GALE_CB_* bits");
+    EnumView ev{};
+    if (!enumeration_view(ctx, &ev)) return fail(GALE_ENOTFOUND, "no enumeration: call gale_enumerate first");
+    if (ev.nE >= INT32_MAX || ev.nF >= INT32_MAX) return fail(GALE_EINVAL, "more than 2^31 - 1 edges or triangles");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(GALE_ECUDA, "cudaSetDevice");
+    if (!ctx->cb) ctx->cb = new Cobound();
+    Cobound &cb = *ctx->cb;
+    // a mesh the counting pass found non-manifold takes the general FT form
+    // at once; otherwise a third tet on a triangle (the slots overflow)
+    // switches this context to it and the pass runs again
+    for (int32_t g : ctx->tt_general) cb.ft_general |= g != 0;
+    int32_t e = 0;
+    gale_status st = run_pass(ctx, which, ev, &e);
+    if (st == GALE_EDEVICE && e == ERR_NONMANIFOLD && (which & GALE_CB_FT) && !cb.ft_general) {
+        cb.ft_general = true;
+        st = run_pass(ctx, which, ev, &e);
+    }
+    if (st != GALE_OK) return st;
     for (int rel = 0; rel < 4; ++rel) {
         const bool have = (which & (1u << rel)) != 0;
         out->rows[rel] = have ? cb.rows_of[rel] : 0;
