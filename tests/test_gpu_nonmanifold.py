@@ -230,3 +230,18 @@ def test_non_manifold_coboundary(order, oname, pre):
                     rows = want[name]
                     assert off.tolist() == np.concatenate([[0], np.cumsum([len(r) for r in rows])]).tolist(), name
                     assert val.tolist() == [x for r in rows for x in r], name
+
+
+def test_non_manifold_noalloc():
+    """The allocation-free build into caller-owned arrays runs the marked
+    clusters from their per-item bins too, and equals the oracle."""
+    import torch
+    m, (canon, rel) = _grid()
+    rng = np.random.default_rng(11)
+    with gale.Context.load(m, device=0) as ctx:
+        for ids in (np.arange(m.nclusters, dtype=np.int32), rng.permutation(m.nclusters)[:40].astype(np.int32)):
+            want = expected_bulk(rel, canon, ids)
+            out = {n: torch.full((max(int(a.size), 1),), -7, dtype=torch.int32, device="cuda") for n, a in want.items()}
+            ctx.build_noalloc(ids, gale.ALL, out)
+            got = {n: out[n][:a.size].cpu().numpy() for n, a in want.items()}
+            assert_bulk_equal(got, want)
