@@ -115,3 +115,24 @@ def test_copy_to_host_refuses_host_only_and_null(small_mesh):
         assert lib.gale_copy_to_host(None, buf.ctypes.data, 1, 16) == 1  # EINVAL
         with pytest.raises(gale.GaleError):
             ctx.copy_to_host(1 << 20, 4, out=buf)
+
+
+def test_host_init_local_id_limits():
+    """A cluster's working set is packed with 16-bit local ids: at most
+    65535 local vertices and 65534 tets.  A single cluster just under the
+    tet limit loads; one over it, or one with more local vertices than
+    the limit, is rejected with EINVAL naming the cluster."""
+    def one_cluster(tv, nv):
+        return gen.Mesh(None, tv.astype(np.int32), np.zeros(nv, np.int32), 1)
+
+    _, tv = gen.freudenthal_grid(22, permute=True, seed=3)  # 63,888 tets
+    host_ctx(one_cluster(tv, 23 ** 3)).close()
+    _, tv = gen.freudenthal_grid(23, permute=True, seed=3)  # 73,002 tets
+    with pytest.raises(gale.GaleError) as ei:
+        host_ctx(one_cluster(tv, 24 ** 3))
+    assert ei.value.status == 1 and "cluster 0" in str(ei.value)
+    nt = 16_400  # disjoint tets: 65,600 vertices
+    tv = np.arange(4 * nt, dtype=np.int32).reshape(nt, 4)
+    with pytest.raises(gale.GaleError) as ei:
+        host_ctx(one_cluster(tv, 4 * nt))
+    assert ei.value.status == 1 and "65535" in str(ei.value)
