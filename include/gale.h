@@ -215,6 +215,10 @@ typedef struct {
  * with GALE_TT in the precondition mask it fails with EDEVICE (non-manifold
  * bit), since parts assume at most one partner per face; without GALE_TT,
  * or with cutting off (part_vertices < 0), the mesh loads.
+ * Size limits, each EINVAL with the cluster named: a cluster's working set
+ * (its tets, external tets and halo) holds at most 65534 tets and 65535
+ * vertices (16-bit local ids), and no vertex may have more than 255
+ * distinct neighbours above it (8-bit edge ranks); use smaller clusters.
  * On success *out owns all of it; release with gale_destroy.
  */
 gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out);

@@ -271,3 +271,13 @@ def test_spill_bins_every_mask(mask):
                 ctx.build(None, mask, mode)
                 ctx.synchronize()
                 assert_bulk_equal(ctx.export(mask), want)
+
+
+def test_more_than_255_upper_neighbours_is_rejected():
+    """A vertex with more than 255 distinct upper neighbours (its edges'
+    positions are kept in 8 bits) is rejected at load with EINVAL."""
+    xyz, tv = fan_mesh(300)
+    m = gen.Mesh(xyz, tv, np.zeros(xyz.shape[0], np.int32), 1)
+    with pytest.raises(gale.GaleError) as ei:
+        gale.Context.load(m, device=0)
+    assert gale.STATUS[ei.value.status] == "EINVAL" and "255" in str(ei.value)
