@@ -211,10 +211,11 @@ typedef struct {
  * mesh (a triangle in three or more tets) is built as defined: every tet
  * sharing three vertices with t.  A cluster with such a triangle among its
  * internal tets' faces finds its TT rows by a slower pass over its block.
- * The one exception is a cluster cut into parts (too large for one CTA):
- * with GALE_TT in the precondition mask it fails with EDEVICE (non-manifold
- * bit), since parts assume at most one partner per face; without GALE_TT,
- * or with cutting off (part_vertices < 0), the mesh loads.
+ * Parts of a cut cluster (too large for one CTA) assume at most one
+ * partner per face: when the counting pass finds such a triangle in a cut
+ * cluster (GALE_TT preconditioned), the load starts again with cutting off
+ * (as part_vertices < 0), and the large clusters run whole from global
+ * scratch.
  * Size limits, each EINVAL with the cluster named: a cluster's working set
  * (its tets, external tets and halo) holds at most 65534 tets and 65535
  * vertices (16-bit local ids), and no vertex may have more than 255

@@ -393,12 +393,13 @@ gale_status check_device_error(gale_ctx *ctx) {
     int32_t e = 0;
     CUDA_TRY(cudaMemcpyAsync(&e, ctx->d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->last_err_word = e;
     if (e == 0) return GALE_OK;
     CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     std::string msg = "kernel error word " + std::to_string(e) + ":";
     if (e & gale::ERR_CAPACITY) msg += " cluster exceeded its launch capacities;";
-    if (e & gale::ERR_NONMANIFOLD) msg += " a triangle is shared by more than two tets (TT needs a manifold mesh);";
+    if (e & gale::ERR_NONMANIFOLD) msg += " a triangle of a cluster cut into parts lies in more than two tets (parts need a manifold mesh);";
     if (e & gale::ERR_HASH_FULL) msg += " face hash overflow;";
     if (e & gale::ERR_BAD_ITEM) msg += " bad cluster id in a work item;";
     if (e & gale::ERR_TIMEOUT) msg += " a device wait timed out;";
@@ -842,7 +843,18 @@ gale_status gale_load_mesh(const gale_mesh_desc *desc, gale_ctx **out) {
     if (st == GALE_OK) st = upload_orders(ctx.get());
     if (st != GALE_OK) {
         std::string keep = gale::t_error;
+        // A cluster cut into parts holds a triangle in three or more tets:
+        // parts assume one partner per face, so the mesh loads again with no
+        // cluster cut (the large ones then run whole, from global scratch,
+        // with the general TT pass).
+        const bool uncut = st == GALE_EDEVICE && ctx->last_err_word == gale::ERR_NONMANIFOLD && ctx->hm.NP > 0 &&
+                           desc->part_vertices >= 0;
         gale_destroy(ctx.release());
+        if (uncut) {
+            gale_mesh_desc whole = *desc;
+            whole.part_vertices = -1;
+            return gale_load_mesh(&whole, out);
+        }
         return fail(st, keep);
     }
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));

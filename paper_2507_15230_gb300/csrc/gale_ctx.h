@@ -65,6 +65,7 @@ struct gale_ctx {
     std::vector<int32_t> all_items;     // host copy
     std::vector<int32_t> pos_all;       // [K+NP] position of each item in all_items (-1: a cut cluster)
     int32_t *d_err = nullptr;
+    int32_t last_err_word = 0;          // the device error word check_device_error last read
     int32_t *d_tickets = nullptr;  // one per bin (+ spare)
     int32_t *d_ids = nullptr;      // [K+NP] item ids of a partial build
     int32_t *d_order_all = nullptr;   // [K+NP] per bin: positions in all_items (largest first)
