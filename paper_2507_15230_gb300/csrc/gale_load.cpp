@@ -78,13 +78,16 @@ struct DistinctIds {
         mask = uint32_t(cap - 1);
         vals.clear();
     }
-    void add(int32_t v) {
+    // v's dense index, v added first if absent
+    int32_t add(int32_t v) {
         uint32_t h = slot(v);
-        if (tab[h] == v) return;
+        if (tab[h] == v) return at[h];
+        const int32_t i = int32_t(vals.size());
         tab[h] = v;
-        at[h] = int32_t(vals.size());
+        at[h] = i;
         vals.push_back(v);
         if (2 * vals.size() > tab.size()) grow();
+        return i;
     }
     // dense index of v, -1 when absent
     int32_t index(int32_t v) const {
@@ -223,7 +226,23 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
                 per[t + 1] = (cl[r[1]] != cl[r[0]]) + (cl[r[2]] != cl[r[1]]) + (cl[r[3]] != cl[r[2]]);
             }
         });
-        for (int64_t t = 0; t < nt; ++t) per[t + 1] += per[t];
+        {  // inclusive prefix over the chunks of parallel_for: sums, then runs
+            const int pc = int(std::max<int64_t>(1, std::min<int64_t>(P, nt)));
+            std::vector<int64_t> csum(size_t(pc) + 1, 0);
+            parallel_for(nt, pc, [&](int64_t b, int64_t e, int c) {
+                int64_t x = 0;
+                for (int64_t t = b; t < e; ++t) x += per[t + 1];
+                csum[size_t(c) + 1] = x;
+            });
+            for (int c = 0; c < pc; ++c) csum[size_t(c) + 1] += csum[size_t(c)];
+            parallel_for(nt, pc, [&](int64_t b, int64_t e, int c) {
+                int64_t x = csum[size_t(c)];
+                for (int64_t t = b; t < e; ++t) {
+                    x += per[t + 1];
+                    per[t + 1] = x;
+                }
+            });
+        }
         const int64_t ninc = per[nt];
         std::vector<int32_t> inc_c(ninc), inc_t(ninc);
         parallel_for(nt, P, [&](int64_t b, int64_t e, int) {
@@ -338,17 +357,24 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         thread_local DistinctIds seen;
         std::vector<int32_t> nb, ho;
         seen.reset(size_t(v1 - v0) * 2 + 64);
-        auto add_row = [&](int32_t t) {
+        // each row entry's dense index among the non-own vertices, kept for
+        // the upper-neighbour count below (own vertices: -1 - offset)
+        thread_local std::vector<int32_t> code;
+        code.resize(size_t(4) * size_t(w.n_ext + w.n_int));
+        auto add_row = [&](int32_t t, int32_t *c) {
             const int32_t *r = rows + 4 * int64_t(t);
-            for (int j = 0; j < 4; ++j)
-                if (r[j] < v0 || r[j] >= v1) seen.add(r[j]);
+            for (int j = 0; j < 4; ++j) {
+                const bool own = r[j] >= v0 && r[j] < v1;
+                const int32_t d = own ? -1 - (r[j] - v0) : seen.add(r[j]);
+                if (c) c[j] = d;
+            }
         };
-        for (int64_t i = 0; i < w.n_ext; ++i) add_row(w.ext[i]);
-        for (int64_t i = 0; i < w.n_int; ++i) add_row(w.itet(i));
+        for (int64_t i = 0; i < w.n_ext; ++i) add_row(w.ext[i], code.data() + 4 * i);
+        for (int64_t i = 0; i < w.n_int; ++i) add_row(w.itet(i), code.data() + 4 * (w.n_ext + i));
         nb = seen.vals;
         std::sort(nb.begin(), nb.end());
         const size_t n_nb = seen.vals.size();
-        for (int64_t i = 0; i < w.n_halo; ++i) add_row(w.halo[i]);
+        for (int64_t i = 0; i < w.n_halo; ++i) add_row(w.halo[i], nullptr);
         ho.assign(seen.vals.begin() + int64_t(n_nb), seen.vals.end());  // halo-only: not seen before
         std::sort(ho.begin(), ho.end());
         const int64_t below = std::lower_bound(nb.begin(), nb.end(), v0) - nb.begin();
@@ -379,17 +405,17 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
         // neighbour universe; only their number of distinct values matters)
         std::vector<int32_t> deg(static_cast<size_t>(nvo), 0), uoff(static_cast<size_t>(nvo) + 1, 0);
         for (int pass = 0; pass < 2; ++pass) {
-            auto row = [&](int32_t t) {
-                const int32_t *r = rows + 4 * int64_t(t);
+            auto row = [&](int64_t i) {
+                const int32_t *c = code.data() + 4 * i;
                 for (int j = 0; j < 4; ++j)
-                    if (r[j] >= v0 && r[j] < v1) {
-                        const int32_t x = r[j] - v0;
+                    if (c[j] < 0) {
+                        const int32_t x = -1 - c[j];
                         if (pass == 0) {
                             deg[x]++;
                             uoff[x + 1] += 3 - j;
                         } else {
                             for (int q = j + 1; q < 4; ++q)
-                                vm_up[uoff[x]++] = r[q] < v1 ? int32_t(n_nb) + (r[q] - v0) : seen.index(r[q]);
+                                vm_up[uoff[x]++] = c[q] < 0 ? int32_t(n_nb) - 1 - c[q] : c[q];
                         }
                     }
             };
@@ -399,8 +425,7 @@ bool prepare_host(const gale_mesh_desc &d, HostMesh &hm, std::string &err) {
                 std::copy(uoff.begin(), uoff.end() - 1, ufill.begin());
                 std::swap(uoff, ufill);  // uoff: fill cursors; ufill: row starts
             }
-            for (int64_t i = 0; i < w.n_ext; ++i) row(w.ext[i]);
-            for (int64_t i = 0; i < w.n_int; ++i) row(w.itet(i));
+            for (int64_t i = 0; i < w.n_ext + w.n_int; ++i) row(i);
         }
         int32_t nvt = 0, mx = 0, mu = 0, ne = 0;
         thread_local std::vector<int32_t> stamp;
