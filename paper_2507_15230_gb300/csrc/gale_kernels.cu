@@ -7,8 +7,9 @@
 // local rows - arrive in shared memory by one bulk copy, and every relation
 // is built there.  Each phase spreads its work evenly over all threads of the
 // block (over tets, bitmap words, VT incidences, edges or internal tets), so
-// the block size is free of the cluster's vertex count; every output leaves
-// through shared-memory staging with one thread per element (coalesced).
+// the block size is free of the cluster's vertex count; the outputs leave
+// through shared-memory staging with one thread per element (coalesced),
+// except TT's rows of at most four entries, stored straight out.
 //
 //  B. VT (Section 4.6 / Algorithm 1: iterate the segment's tets and test
 //     each vertex against the segment interval).  Each warp takes a
@@ -36,7 +37,13 @@
 //  D. TT (Table 1; the paper gives no kernel for it) for the faces (b, c, d)
 //     of internal tets (a, b, c, d) with no own vertex: a small
 //     open-addressing hash of those faces is probed with the faces of the
-//     halo tets.  A face met a third time is reported (non-manifold input).
+//     halo tets.
+//  E. TT rows from the four face links, sorted by canonical id.  A face with
+//     a second partner (a triangle in three or more tets) marks the cluster
+//     instead, whose rows then come from E', a general pass over the block
+//     (compiled into every kernel but the hot shared-memory one: the
+//     counting pass reports such clusters and the host runs them from
+//     per-item bins).  Parts of cut clusters report it as an error.
 //
 // The counting mode runs the same passes without writes and returns the
 // exact sizes the host uses to place outputs and to admit cache entries.
