@@ -2,9 +2,10 @@
 // enumeration (Section 4.4: coboundary relations are computed by the GPU for
 // whole segments; Section 5 evaluates VE, VF, EF and FT among them).
 //
-// Inputs on the device: the canonical tet rows, each vertex's cluster, the
-// enumeration (E, F, I_E, I_F and each segment's ids in vertex-tuple order)
-// and the VT, VV and ET rows of every cluster from a batched build.
+// Inputs on the device: the canonical tet rows, each vertex's cluster and
+// the enumeration (E, F, I_E, I_F and each segment's ids in vertex-tuple
+// order).  The enumeration itself, when made on the device, reads every
+// cluster's ET rows from a batched build (enumerate_sorted_device).
 //
 // Lookup structure, built once per enumeration: the edges and triangles in
 // vertex-tuple ("sorted") order, with
@@ -15,22 +16,17 @@
 //   fkc[p]   third vertex of the p-th sorted triangle,
 //   e2s, f2s the sorted position of every edge / triangle id.
 // An edge (a, b) is then found among a's few upper edges and a triangle
-// (a, b, c) among the few triangles over its edge (a, b).  Within a segment
-// the sorted edge order is the order of the cluster's ET rows (own lower
-// vertex, then upper vertex), so the tets around the j-th sorted edge are
-// the ET row at j - I_E[k] of its cluster k.
+// (a, b, c) among the few triangles over its edge (a, b).
 //
-// One thread per output row, two passes (count, then fill after an
-// exclusive scan):
-//   VE(v)  the edges {v, w} for w in VV(v);
-//   EF(e)  the triangles (u, w, x) for the distinct third vertices x of the
-//          tets of ET(e);
-//   VF(v)  read from EF: a triangle through v has two edges through v, and
-//          is taken from the one to its smaller other vertex (so EF is built
-//          first, and whenever VF is asked for);
-//   FT(f)  for f = (a, b, c): the tets of ET(a, b) that contain c.
-// With the sorted numbering every row comes out ascending; otherwise rows
-// whose ids come from lookups are sorted in place.
+// The relations are scattered from the simplices (details at the scatter
+// kernels below): every row is a contiguous range of the sorted order (VE(v):
+// v's upper edges; EF(e): the triangles over e; VF(v): the triangles with
+// lowest vertex v) plus entries that other edges and triangles place by
+// atomic cursors after counts and an exclusive scan; FT takes two slots per
+// triangle that its tets claim (a counted form with cursors and row sorts
+// when a triangle lies in three or more tets).  With the sorted numbering
+// only each row's scattered prefix needs sorting, and VF is gathered from VE
+// and EF; otherwise rows are sorted whole.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
