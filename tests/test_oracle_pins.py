@@ -503,3 +503,30 @@ def test_coboundary_closed_forms_and_transposes(order, n, K, seed):
         mid = int(np.argmin(np.abs(xyz - xyz.mean(axis=0)).sum(axis=1)))
         v = int(canon["cid"][mid])
         assert len(cb["VE"][v]) == 14 and len(cb["VF"][v]) == 36
+
+
+@pytest.mark.parametrize("order", ["sorted", "first"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_coboundary_brute_force_soups(order, seed):
+    """On random tet soups over a few vertices (triangles in up to a dozen
+    tets: non-manifold), the enumeration holds exactly the vertex pairs and
+    triples of the tets, and VE, VF, EF, FT equal containment tests over
+    every simplex, written without the oracle's code."""
+    from itertools import combinations
+    rng = np.random.default_rng(500 + seed)
+    nv = int(rng.integers(8, 13))
+    tv, seg = random_soup(rng, nv, int(rng.integers(20, 60)), int(rng.integers(1, 4)))
+    K = int(seg.max()) + 1
+    canon = oracle.canonicalize(nv, tv, seg, K)
+    en = oracle.enumerate_simplices(canon, order)
+    cb = oracle.coboundary(canon, en)
+    rows = [tuple(r) for r in canon["rows"].tolist()]
+    E = [tuple(e) for e in en["E"]]
+    F = [tuple(f) for f in en["F"]]
+    assert sorted(E) == sorted({p for r in rows for p in combinations(r, 2)})
+    assert sorted(F) == sorted({q for r in rows for q in combinations(r, 3)})
+    assert cb["VE"] == [[i for i, e in enumerate(E) if v in e] for v in range(nv)]
+    assert cb["VF"] == [[i for i, f in enumerate(F) if v in f] for v in range(nv)]
+    assert cb["EF"] == [[i for i, f in enumerate(F) if set(e) <= set(f)] for e in E]
+    assert cb["FT"] == [[t for t, r in enumerate(rows) if set(f) <= set(r)] for f in F]
+    assert max(len(r) for r in cb["FT"]) >= 3
