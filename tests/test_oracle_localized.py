@@ -46,3 +46,31 @@ def test_digest_sees_a_planted_mistake():
         assert oracle.relation_digest(bad) != d, n
         bad[n] = np.concatenate([v[n], [0]])  # one entry too many
         assert oracle.relation_digest(bad) != d, n
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_localized_equals_global_on_non_manifold_soups(seed):
+    """Random tet soups over a few vertices, with triangles in many tets:
+    the localized producer's TT rows (from each cluster's working set and
+    face halo) equal the global definition's."""
+    rng = np.random.default_rng(900 + seed)
+    nv, nt, K = int(rng.integers(8, 11)), int(rng.integers(40, 60)), int(rng.integers(2, 5))
+    seen, tv = set(), []
+    while len(tv) < nt:
+        q = tuple(sorted(rng.choice(nv, 4, replace=False).tolist()))
+        if q not in seen:
+            seen.add(q)
+            tv.append(list(rng.permutation(q)))
+    seg = rng.integers(0, K, nv)
+    seg[:K] = np.arange(K)
+    rng.shuffle(seg)
+    tv, seg = np.array(tv, np.int32), seg.astype(np.int32)
+    canon, rel = oracle.build_all(nv, tv, seg, K)
+    assert np.diff(rel["tt_off"]).max() > 4
+    sizes, dig, _ = oracle.localized_build(canon, 2)
+    assert np.array_equal(sizes, oracle.cluster_sizes(rel, canon))
+    for k in range(K):
+        assert int(dig[k]) == oracle.relation_digest(oracle.cluster_view(rel, canon, k))
+        got, want = oracle.localized_cluster(canon, k), oracle.cluster_view(rel, canon, k)
+        for n in KEYS:
+            assert np.array_equal(got[n], want[n]), (k, n)
